@@ -1,0 +1,412 @@
+#!/usr/bin/env python
+"""Benchmark: isosurfaces of a block-compressed 512^3 volume on one GB300.
+
+Workload (a stand-in for the paper's Plasma 512^3, Table "mc_benchmark_data"):
+512^3 float32 six-octave gradient noise (seed 1), compressed at 8 bits per
+value in 4^3 blocks (128 MiB), isovalues -1, -0.5, 0, 0.5, 1 extracted one
+after another.  One step = drop the decoded-block cache, then extract the
+five surfaces in order (the first decodes every active block, the later
+ones reuse what the cache holds, as in the paper's sweep benchmarks).
+
+Metric: triangles/s (whole step, all five surfaces), with voxels/s
+(5 * 512^3 per step) and the p50/p99 latency of one isovalue change.
+
+  value    device-resident volume; each surface written into a
+           preallocated device buffer (iso_extract_into); CUDA events on
+           the library's stream around each step; L2 flushed between steps
+  e2e      the same step through the public API from host memory: upload
+           the compressed volume and ranges from pinned host buffers
+           (iso_load_volume), five iso_extract calls (library-allocated
+           meshes), read back the counts, release
+  roofline the dominant stage's kernel: algorithmic bytes per launch over
+           its CUDA-event duration, against the measured HBM copy peak
+  cpu_baseline  the plain CPU oracle on a bounded window of the same field
+
+--impl reference times the CPU oracle alone (the reference arm: there is no
+other implementation of this method to run).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DIMS = (512, 512, 512)
+RATE = 8
+SEED = 1
+ISOS = (-1.0, -0.5, 0.0, 0.5, 1.0)
+METRIC = "triangles/s and voxels/s per isosurface on 1 GB300; p50/p99 isovalue-change latency"
+WORKLOAD = ("noise512: 512^3 float32 6-octave gradient noise (seed 1), fixed rate 8 bits/value in 4^3 blocks, "
+            "isovalues -1,-0.5,0,0.5,1 extracted in sequence from a cold decoded-block cache")
+CPU_WINDOW = (256, 256, 128)      # oracle sample: a window of the same field
+CPU_ORIGIN = (128, 128, 192)
+REF_WINDOW = (128, 128, 64)       # per-step sample of the reference arm
+L2_FLUSH_BYTES = 512 << 20
+CTL_BYTES = 104                   # control block read back once per surface
+KERNELS_PER_SURFACE = 6           # prep, cull, lru_a, lru_b, decode, mc
+KERNELS_PER_RESET = 2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi sampled every 100 ms while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 8:
+                    rows.append(parts)
+        except OSError:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[4:8]) if v.lower() == "active"})
+        busy = sorted(sm)[len(sm) // 4:] if len(sm) > 4 else sm     # drop idle samples at the edges
+        return {"sm_mhz": statistics.median(busy) if busy else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- helpers
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return None
+
+
+def profile_traffic(kernel_file, kernel):
+    """dram bytes per launch from the committed ncu summary, if it was taken
+    on the current source of the kernel (else None)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_noise512.md")
+    src = os.path.join(ROOT, "paper_2009_03254_gb300", "csrc", kernel_file)
+    try:
+        text = open(path).read()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    for line in text.splitlines():
+        if line.startswith("traffic_per_launch_bytes:"):
+            parts = line.split()
+            if len(parts) >= 4 and parts[2] == "source_sha256_16:" and parts[3] == sha:
+                return float(parts[1])
+    return None
+
+
+def stage_bytes(stats, rate, nb):
+    """Algorithmic bytes each stage must move for one surface."""
+    na, nn, T = stats["n_active"], stats["n_new"], stats["num_triangles"]
+    return {
+        "cull": 8 * nb + nb / 8 + 4 * na + 4 * nn,                  # block hulls, mask, I_active, I_new
+        "cache_update": 0.0,
+        "decode": nn * (8 * rate + 256 + 8),                         # compressed in, decoded out, I_new + slot
+        "triangles": na * (256 + 4) + 48 * T,                        # decoded tiles in, vertices out
+    }
+
+
+# ---------------------------------------------------------------- CPU oracle baseline
+
+def cpu_oracle_sample(window, origin, isos):
+    import oracle
+    from synth import fields
+    f = fields.gradient_noise(*window, SEED, origin=origin)
+    bits, bmin, bmax = oracle.encode_volume(f, RATE)
+    tris, t = 0, 0.0
+    for iso in isos:
+        t0 = time.perf_counter()
+        r = oracle.extract(bits, window, RATE, bmin, bmax, iso)
+        t += time.perf_counter() - t0
+        tris += r["num_triangles"]
+    return tris, t
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from synth import fields
+    f = fields.gradient_noise(*REF_WINDOW, SEED, origin=CPU_ORIGIN)
+    bits, bmin, bmax = oracle.encode_volume(f, RATE)
+    vox = int(np.prod(REF_WINDOW))
+
+    def step():
+        n = 0
+        for iso in ISOS:
+            n += oracle.extract(bits, REF_WINDOW, RATE, bmin, bmax, iso)["num_triangles"]
+        return n
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    tris = 0
+    for _ in range(args.steps):
+        tris += step()
+    dt = time.perf_counter() - t0
+    value = tris / dt
+    sample = (f"{REF_WINDOW[0]}x{REF_WINDOW[1]}x{REF_WINDOW[2]} window at {CPU_ORIGIN} of the 512^3 field, "
+              f"5 isovalues per step, single-threaded plain C oracle (decode all blocks, range test, block MC)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "triangles/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "voxels_per_s": 5 * vox * args.steps / dt,
+            "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "triangles/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "triangles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2009_03254_gb300 as bc
+    import synth.gpu as sg
+
+    nb = int(np.prod(bc.block_dims(DIMS)))
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        field = sg.gradient_noise(*DIMS, SEED)
+        bits, bmin, bmax = bc.encode_field(field, RATE)
+        torch.cuda.synchronize()
+        del field
+        vol = bc.Volume(bits, DIMS, RATE, bmin, bmax)
+        # size the output buffer from one pass over the isovalues
+        tmax = 0
+        per_iso = []
+        for iso in ISOS:
+            m = vol.extract(iso)
+            tmax = max(tmax, m.num_triangles)
+            per_iso.append(m.stats)
+            m.release()
+        out = torch.empty((tmax + 1024, 3, 4), dtype=torch.float32, device="cuda")
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+        lat = []
+
+        def step(record=None):
+            vol.cache_reset()
+            tris = 0
+            stats = []
+            for iso in ISOS:
+                t0 = time.perf_counter()
+                st = vol.extract_into(iso, out)
+                if record is not None:
+                    record.append(time.perf_counter() - t0)
+                tris += st["num_triangles"]
+                stats.append(st)
+            return tris, stats
+
+        for _ in range(max(3, args.warmup)):
+            step()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        total_tris = 0
+        with ClockSampler(local) as clk:
+            for i in range(args.steps):
+                flush.zero_()
+                torch.cuda.synchronize()
+                ev[i][0].record(stream)
+                tris, stats = step(lat)
+                ev[i][1].record(stream)
+                total_tris += tris
+            torch.cuda.synchronize()
+        step_ms = [a.elapsed_time(b) for a, b in ev]
+        total_s = sum(step_ms) / 1000.0
+        if world > 1:
+            t = torch.tensor([total_s], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_s = float(t.item())
+            n = torch.tensor([total_tris], device="cuda", dtype=torch.float64)
+            dist.all_reduce(n)
+            total_tris = float(n.item())
+
+        # per-stage durations (same steps, events between the stages)
+        vol.set_profiling(True)
+        stage_ms = {k: 0.0 for k in bc.Volume.STAGES}
+        stage_b = {"cull": 0.0, "cache_update": 0.0, "decode": 0.0, "triangles": 0.0}
+        prof_steps = max(1, min(args.steps, 5))
+        launches = {"decode": 0, "triangles": 0}
+        for _ in range(prof_steps):
+            flush.zero_()
+            vol.cache_reset()
+            for iso in ISOS:
+                st = vol.extract_into(iso, out)
+                ms = vol.stage_times()
+                for k in stage_ms:
+                    stage_ms[k] += ms[k]
+                for k, b in stage_bytes(st, RATE, nb).items():
+                    stage_b[k] += b
+                launches["decode"] += 1
+                launches["triangles"] += 1
+        vol.set_profiling(False)
+
+        # end to end through the public API from pinned host memory
+        e2e = None
+        if not args.no_e2e:
+            h_bits = bits.cpu().pin_memory()
+            h_min = bmin.cpu().pin_memory()
+            h_max = bmax.cpu().pin_memory()
+            h2d = h_bits.numel() * 8 + h_min.numel() * 4 + h_max.numel() * 4
+            e2e_steps = max(1, min(args.steps, 5))
+
+            def e2e_step():
+                v = bc.Volume(h_bits, DIMS, RATE, h_min, h_max)
+                n = 0
+                for iso in ISOS:
+                    m = v.extract(iso)
+                    n += m.num_triangles
+                    m.release()
+                v.release()
+                return n
+
+            e2e_step()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            n_e2e = 0
+            for _ in range(e2e_steps):
+                n_e2e += e2e_step()
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            e2e = {"value": n_e2e / dt, "unit": "triangles/s", "h2d_bytes_per_step": h2d,
+                   "d2h_bytes_per_step": CTL_BYTES * len(ISOS), "ms_per_step": 1000 * dt / e2e_steps,
+                   "includes": "iso_load_volume from pinned host (upload + allocation + block hulls), "
+                               "5 x iso_extract (device-allocated meshes), count readback, release"}
+        vol.release()
+
+    if rank != 0:
+        dist.barrier() if world > 1 else None
+        return
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    peak_src = "measured" if peaks else "fallback"
+    dominant = max(("cull", "cache_update", "decode", "triangles"), key=lambda k: stage_ms[k])
+    kernel_of = {"cull": "cull_kernel", "cache_update": "lru_kernels", "decode": "decode_new_kernel",
+                 "triangles": "mc_kernel"}
+    file_of = {"cull": "extract.cu", "cache_update": "extract.cu", "decode": "extract.cu", "triangles": "extract.cu"}
+    n_launch = prof_steps * len(ISOS)
+    ach = stage_b[dominant] / n_launch / (stage_ms[dominant] / n_launch / 1000.0) / 1e9
+    stages = {}
+    for k in ("cull", "cache_update", "decode", "triangles"):
+        ms = stage_ms[k] / n_launch
+        gbs = (stage_b[k] / n_launch) / (ms / 1000.0) / 1e9 if ms > 0 and stage_b[k] > 0 else None
+        stages[k] = {"ms_per_surface": ms, "alg_bytes_per_surface": stage_b[k] / n_launch,
+                     "GBps": gbs, "frac_of_measured_hbm": (gbs / peak) if gbs else None}
+    stages["prep"] = {"ms_per_surface": stage_ms["prep"] / n_launch}
+    lat_ms = sorted(1000 * x for x in lat)
+    value = total_tris / total_s
+    ms_per_step = 1000 * total_s / args.steps
+    line = {
+        "metric": METRIC, "value": value, "unit": "triangles/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "voxels_per_s": len(ISOS) * float(np.prod(DIMS)) * args.steps * world / total_s,
+        "latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99)),
+                       "what": "host time of one iso_extract_into call (cache update, decode, triangles, count readback)"},
+        "config": {"workload": WORKLOAD, "dims": list(DIMS), "rate_bits": RATE, "isovalues": list(ISOS),
+                   "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MB write, untimed)",
+                   "triangles_per_surface": [s["num_triangles"] for s in per_iso],
+                   "active_blocks_per_surface": [s["n_active"] for s in per_iso],
+                   "parallelism": f"{world} independent replica(s)"},
+        "roofline": {"bound": "hbm", "kernel": kernel_of[dominant], "achieved": ach, "peak": peak, "unit": "GB/s",
+                     "frac": ach / peak, "peak_source": f"{peak_src} hbm_gbs (copy)",
+                     "traffic": profile_traffic(file_of[dominant], kernel_of[dominant]),
+                     "alg_bytes_per_launch": stage_b[dominant] / n_launch},
+        "stages": stages,
+        "gpu_launches": args.steps * (KERNELS_PER_RESET + KERNELS_PER_SURFACE * len(ISOS)),
+        "clocks": clk.summary(),
+        "e2e": e2e,
+    }
+    if world > 1:
+        dist.barrier()
+    if not args.no_cpu_baseline and world == 1:
+        tris, dt = cpu_oracle_sample(CPU_WINDOW, CPU_ORIGIN, ISOS)
+        line["cpu_baseline"] = {
+            "value": tris / dt, "unit": "triangles/s", "cores": 1, "kind": "oracle",
+            "sample": f"{CPU_WINDOW[0]}x{CPU_WINDOW[1]}x{CPU_WINDOW[2]} window at {CPU_ORIGIN} of the same field, "
+                      f"5 isovalues, {dt:.1f} s single-threaded (decode every block, range test, block MC)",
+            "voxels_per_s": len(ISOS) * float(np.prod(CPU_WINDOW)) / dt}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

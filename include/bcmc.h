@@ -1,0 +1,214 @@
+/*
+ * bcmc.h -- C ABI of the GB300 block-compressed marching-cubes library.
+ *
+ * The library computes isosurfaces of a volume that is held on the GPU in
+ * a fixed-rate block-compressed form, following the method of Usher and
+ * Pascucci, "Interactive Visualization of Terascale Data in the Browser:
+ * Fact or Fiction?" (arXiv 2009.03254), Section 4:
+ *   - select the 4x4x4 blocks whose value range, or whose range joined
+ *     with a neighbour's, contains the isovalue (Section 4.1);
+ *   - find which of them are in a GPU-resident LRU cache of decoded
+ *     blocks, give the others the least recently used free slots, and
+ *     decode them into those slots (Section 4.2, Algorithm 1; 4.2.1);
+ *   - run marching cubes over each active block and its +x/+y/+z halo
+ *     (Section 4.3), count triangles per block and prefix-sum the counts
+ *     into output offsets (Section 4.4), and write the triangles
+ *     (Section 4.5).
+ * Everything runs on the device; one small readback returns the counts.
+ *
+ * Conventions used throughout:
+ *   - volumes are nx*ny*nz float32 samples, x fastest; the sample (x,y,z)
+ *     is at x + nx*(y + ny*z);
+ *   - blocks are 4x4x4 samples; nbx = ceil(nx/4) etc.; block (bx,by,bz)
+ *     has id bx + nbx*(by + nby*bz); inside a block, sample (i,j,k) is at
+ *     i + 4*j + 16*k; samples past the volume edge repeat the last one;
+ *   - the compressed volume is nb = nbx*nby*nbz blocks of exactly
+ *     rate*64 bits (rate 64-bit little-endian words) each, block b at word
+ *     b*rate; the bit format is the library's ZFP-style fixed-rate format
+ *     (block exponent, reversible integer lifting, sequency order,
+ *     negabinary, group-tested bit planes), not libzfp's;
+ *   - a cell is classified with bit c set iff its corner c =
+ *     (c&1, (c>>1)&1, (c>>2)&1) is < iso; a value equal to iso is "above";
+ *   - vertices are float4 {x, y, z, w}: x,y,z in [0,4] relative to the
+ *     block origin 4*(bx,by,bz), w = the block id as uint32 bits; three
+ *     consecutive vertices form one triangle whose right-hand normal
+ *     points toward increasing values; triangles are ordered by block id,
+ *     then cell (x fastest), then case-table order.
+ *
+ * Errors: every int-returning call returns ISO_OK or one of ISO_ERR_*;
+ * no call throws or aborts.  A failed call leaves its outputs unspecified
+ * and the volume usable, except ISO_ERR_CUDA, after which the CUDA context
+ * may be unusable.
+ *
+ * Threads and streams: a volume is used by one host thread at a time.  All
+ * of its device work is issued on the stream given at load (or set with
+ * iso_set_stream).  Blocking calls synchronise that stream only.
+ */
+#ifndef BCMC_H
+#define BCMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ISO_OK 0
+#define ISO_ERR_INVALID_ARG 1  /* bad pointer, size, rate, dims or a non-finite isovalue */
+#define ISO_ERR_OOM 2          /* a device or pinned-host allocation failed */
+#define ISO_ERR_BUDGET 3       /* the active blocks do not fit in the cache budget */
+#define ISO_ERR_CUDA 4         /* a CUDA runtime call failed */
+#define ISO_ERR_TIMEOUT 5      /* a device-side wait gave up (bounded spin) */
+#define ISO_ERR_CAPACITY 6     /* the caller's vertex buffer is too small */
+
+/* iso_options.flags */
+#define ISO_INPUT_ON_DEVICE 1u /* compressed/block_min/block_max are device pointers */
+#define ISO_DEBUG 2u           /* keep per-stage debug copies (see iso_debug_get) */
+
+typedef struct iso_volume iso_volume;
+
+typedef struct iso_options {
+    uint32_t flags;            /* ISO_INPUT_ON_DEVICE | ISO_DEBUG */
+    uint32_t reserved;
+    void *stream;              /* cudaStream_t for all device work; NULL = default stream */
+    double initial_cache_fraction; /* initial slots as a fraction of nb; <= 0 means 0.1 (Section 4.2) */
+    uint64_t cache_budget_bytes;   /* cap on decoded-block storage (256 B per slot); 0 = nb slots */
+} iso_options;
+
+typedef struct iso_stats {
+    uint64_t num_triangles;    /* T: triangles of this surface */
+    uint32_t n_active;         /* blocks selected by the range test (Section 4.1) */
+    uint32_t n_new;            /* active blocks that were not cached and were decoded */
+    uint32_t n_occupied;       /* active blocks that emit at least one triangle */
+    uint32_t n_slots;          /* cache slots in use after growth */
+    uint64_t cache_bytes;      /* n_slots * 256 */
+    uint32_t epoch;            /* 1-based count of extractions on this volume */
+    uint32_t reruns;           /* 1 if the triangle stage ran twice to fit the output */
+} iso_stats;
+
+typedef struct iso_mesh {
+    float *d_vertices;         /* device float4[3 * num_triangles], owned by the library */
+    uint64_t num_triangles;
+    uint64_t capacity_triangles;
+    iso_stats stats;
+    void *priv;                /* library bookkeeping; do not touch */
+} iso_mesh;
+
+/* Upload a compressed volume and set up its cache (Section 4: "uploading
+ * the ZFP fixed-rate compressed data to the GPU"; Section 4.1: "precompute
+ * and store the value range of each block when loading the data").
+ *   compressed       nb*rate uint64 words (layout above), compressed_bytes
+ *                    must equal nb*rate*8
+ *   nx, ny, nz       volume size in samples, each >= 1
+ *   rate_bits        bits per sample, 1..32
+ *   block_min/max    per-block range over the block's in-volume samples AS
+ *                    DECODED (nb floats each); the block method reproduces
+ *                    full-volume marching cubes of the decoded field only
+ *                    with ranges of the decoded values
+ *   opt              may be NULL (defaults above)
+ * Host inputs are copied; the caller keeps ownership.  With
+ * ISO_INPUT_ON_DEVICE they are copied device-to-device.  On success *out
+ * owns all device state until iso_release.  Blocks until the upload is done. */
+int iso_load_volume(iso_volume **out, const void *compressed, size_t compressed_bytes,
+                    uint32_t nx, uint32_t ny, uint32_t nz, uint32_t rate_bits,
+                    const float *block_min, const float *block_max, const iso_options *opt);
+
+/* Compute the isosurface at `isovalue` (Sections 4.1-4.5).  The vertex
+ * buffer is allocated by the library (stream-ordered) and owned by
+ * *out until iso_mesh_release.  Blocks until the counts are known.  If
+ * the first guess of the output size is too small, the triangle stage runs
+ * again into a larger buffer (stats.reruns = 1).  isovalue must be finite. */
+int iso_extract(iso_volume *v, float isovalue, iso_mesh *out);
+
+/* As iso_extract, but writes into a caller-owned device buffer of
+ * capacity_triangles triangles (float4[3 * capacity]).  If T exceeds it,
+ * only the first `capacity` triangles are written, stats->num_triangles
+ * holds T and ISO_ERR_CAPACITY is returned (the cache update stands). */
+int iso_extract_into(iso_volume *v, float isovalue, float *d_vertices, uint64_t capacity_triangles,
+                     iso_stats *stats);
+
+/* Free a mesh's vertex buffer (stream-ordered on the volume's stream that
+ * made it).  The volume must still be alive.  Safe on a zeroed mesh. */
+int iso_mesh_release(iso_volume *v, iso_mesh *m);
+
+/* Free every device and host resource of the volume. NULL is a no-op. */
+void iso_release(iso_volume *v);
+
+/* Change the stream used by later calls on v (the previous stream is
+ * synchronised first). */
+int iso_set_stream(iso_volume *v, void *stream);
+
+/* Drop every cached block (all slots empty, epoch kept): the next
+ * extraction decodes all of its active blocks. */
+int iso_cache_reset(iso_volume *v);
+
+/* Per-stage timing.  With profiling on, each extraction records CUDA
+ * events on the volume's stream between its stages; iso_stage_times then
+ * returns the last extraction's durations in milliseconds, in this order:
+ *   0 prep (counters and descriptors), 1 cull (Section 4.1 and the
+ *   hit/new split of Algorithm 1), 2 cache update (rest of Algorithm 1),
+ *   3 decode (Section 4.2.1), 4 triangles (Sections 4.3-4.5).
+ * ms must hold n >= 5 floats.  Profiling off (the default) records
+ * nothing. */
+#define ISO_NUM_STAGES 5
+int iso_set_profiling(iso_volume *v, int on);
+int iso_stage_times(iso_volume *v, float *ms, int n);
+
+/* Human-readable text for a status code (static storage). */
+const char *iso_error_string(int status);
+
+/* The library's marching-cubes case table (host-only, needs no GPU).  The
+ * paper cites Lorensen and Cline's marching cubes without a table; this
+ * one is generated by a face rule: on every cell face, each run of
+ * below-iso corners (counter-clockwise, seen from outside) is cut off by
+ * one segment, so a face with two diagonal below corners cuts them off
+ * separately and adjacent cells always agree; the segments form cycles,
+ * taken by smallest edge number and fanned from it.  num_tri receives 256
+ * counts (at most 5); tri_edges receives 256 rows of 16 bytes, three edge
+ * numbers per triangle.  Edge 4*a + j lies along axis a (0=x,1=y,2=z) at
+ * offsets (j&1, j>>1) on the other two axes in increasing axis order. */
+int iso_mc_case_table(uint8_t *num_tri, uint8_t *tri_edges);
+
+/* Encode a device-resident float32 volume into the fixed-rate format on
+ * the GPU (for producing test and benchmark inputs; the paper's method
+ * itself only decodes).  d_field is nx*ny*nz floats (x fastest);
+ * d_bits receives nb*rate words; d_bmin/d_bmax receive each block's range
+ * over its decoded in-volume samples.  All pointers are device pointers;
+ * the work is queued on `stream` and the call does not block.
+ * Non-finite samples are not allowed (the output is then unspecified). */
+int iso_encode_field(const float *d_field, uint32_t nx, uint32_t ny, uint32_t nz, uint32_t rate_bits,
+                     uint64_t *d_bits, float *d_bmin, float *d_bmax, void *stream);
+
+/* Decode blocks ids[0..n) of a device-resident compressed volume into
+ * out (n*64 floats, block-local order), device pointers, queued on
+ * `stream` (Section 4.2.1 applied to an explicit list). */
+int iso_decode_blocks(const uint64_t *d_bits, uint32_t rate_bits, const uint32_t *d_ids, uint64_t n,
+                      float *d_out, void *stream);
+
+/* ---- debug and parity access (volumes loaded with ISO_DEBUG) ---------
+ * Copies a per-stage array of the LAST extraction into host memory.
+ * `bytes` is the size of host_dst; *count receives the number of elements
+ * available (and copied, if they fit; otherwise ISO_ERR_CAPACITY). */
+#define ISO_DBG_ACTIVE_IDS 1   /* uint32[n_active]  I_active, ascending */
+#define ISO_DBG_NEW_IDS 2      /* uint32[n_new]     I_new, ascending */
+#define ISO_DBG_SLOT_OF_BLOCK 3 /* int32[nb]        I_slot (-1 = not cached) */
+#define ISO_DBG_BLOCK_OF_SLOT 4 /* int32[n_slots]   S_block (-1 = empty) */
+#define ISO_DBG_SLOT_LAST_USE 5 /* uint32[n_slots]  epoch of last use (0 = never) */
+#define ISO_DBG_ACTIVE_MASK 6  /* uint32[ceil(nb/32)] M_active bitmask */
+#define ISO_DBG_CELL_CASES 7   /* uint8[n_active*64] case of each cell of each active block */
+#define ISO_DBG_BLOCK_TRIS 8   /* uint32[n_active]  triangles per active block */
+#define ISO_DBG_BLOCK_OFFSETS 9 /* uint64[n_active] exclusive prefix of BLOCK_TRIS */
+#define ISO_DBG_EDGE_IDS 10    /* uint64[3*T]       global edge id of each vertex:
+                                  3*(x + nx*(y + ny*z)) + axis of its lower sample */
+int iso_debug_get(iso_volume *v, int which, void *host_dst, size_t bytes, uint64_t *count);
+
+/* Copy the decoded samples of cached blocks ids[0..n) (host array) to
+ * host_out (n*64 floats).  Returns ISO_ERR_INVALID_ARG if a block is not
+ * cached. */
+int iso_debug_read_blocks(iso_volume *v, const uint32_t *ids, uint64_t n, float *host_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BCMC_H */

@@ -1,0 +1,296 @@
+"""GB300 block-compressed marching cubes.
+
+Thin Python binding over the C ABI of ``libbcmc.so`` (declared in
+``include/bcmc.h``).  It only marshals arguments: every step of the
+isosurface pipeline runs in the library's CUDA kernels.  PyTorch supplies
+device memory and streams.  There is no CPU fallback: if the compiled
+library is missing, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libbcmc.so")
+
+ISO_OK = 0
+ISO_ERR_INVALID_ARG = 1
+ISO_ERR_OOM = 2
+ISO_ERR_BUDGET = 3
+ISO_ERR_CUDA = 4
+ISO_ERR_TIMEOUT = 5
+ISO_ERR_CAPACITY = 6
+
+ISO_INPUT_ON_DEVICE = 1
+ISO_DEBUG = 2
+
+DBG = {
+    "active_ids": (1, np.uint32), "new_ids": (2, np.uint32), "slot_of_block": (3, np.int32),
+    "block_of_slot": (4, np.int32), "slot_last_use": (5, np.uint32), "active_mask": (6, np.uint32),
+    "cell_cases": (7, np.uint8), "block_tris": (8, np.uint32), "block_offsets": (9, np.uint64),
+    "edge_ids": (10, np.uint64),
+}
+
+
+class IsoError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {error_string(code)} (status {code})")
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("stream", ctypes.c_void_p),
+                ("initial_cache_fraction", ctypes.c_double), ("cache_budget_bytes", ctypes.c_uint64)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("num_triangles", ctypes.c_uint64), ("n_active", ctypes.c_uint32), ("n_new", ctypes.c_uint32),
+                ("n_occupied", ctypes.c_uint32), ("n_slots", ctypes.c_uint32), ("cache_bytes", ctypes.c_uint64),
+                ("epoch", ctypes.c_uint32), ("reruns", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {name: int(getattr(self, name)) for name, _ in self._fields_}
+
+
+class _Mesh(ctypes.Structure):
+    _fields_ = [("d_vertices", ctypes.c_void_p), ("num_triangles", ctypes.c_uint64),
+                ("capacity_triangles", ctypes.c_uint64), ("stats", _Stats), ("priv", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libbcmc.so (built by ``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build the CUDA library first (__graft_entry__.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        P, u32, u64, sz = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_size_t
+        i32 = ctypes.c_int
+        sig = {
+            "iso_load_volume": (i32, [ctypes.POINTER(P), P, sz, u32, u32, u32, u32, P, P, ctypes.POINTER(_Options)]),
+            "iso_extract": (i32, [P, ctypes.c_float, ctypes.POINTER(_Mesh)]),
+            "iso_extract_into": (i32, [P, ctypes.c_float, P, u64, ctypes.POINTER(_Stats)]),
+            "iso_mesh_release": (i32, [P, ctypes.POINTER(_Mesh)]),
+            "iso_release": (None, [P]),
+            "iso_set_stream": (i32, [P, P]),
+            "iso_cache_reset": (i32, [P]),
+            "iso_error_string": (ctypes.c_char_p, [i32]),
+            "iso_mc_case_table": (i32, [P, P]),
+            "iso_encode_field": (i32, [P, u32, u32, u32, u32, P, P, P, P]),
+            "iso_decode_blocks": (i32, [P, u32, P, u64, P, P]),
+            "iso_debug_get": (i32, [P, i32, P, sz, ctypes.POINTER(u64)]),
+            "iso_debug_read_blocks": (i32, [P, P, u64, P]),
+            "iso_set_profiling": (i32, [P, i32]),
+            "iso_stage_times": (i32, [P, ctypes.POINTER(ctypes.c_float), i32]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def error_string(code):
+    return lib().iso_error_string(int(code)).decode()
+
+
+def _check(rc, where):
+    if rc != ISO_OK:
+        raise IsoError(rc, where)
+
+
+def _current_stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(x):
+    """device pointer of a torch tensor, host pointer of a numpy array"""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return ctypes.c_void_p(x.ctypes.data)
+    return ctypes.c_void_p(x.data_ptr())
+
+
+def block_dims(dims):
+    nx, ny, nz = dims
+    return (nx + 3) // 4, (ny + 3) // 4, (nz + 3) // 4
+
+
+def mc_case_table():
+    """The library's 256-case table: (num_tri uint8[256], tri_edges uint8[256, 16])."""
+    num = np.zeros(256, np.uint8)
+    tri = np.zeros((256, 16), np.uint8)
+    _check(lib().iso_mc_case_table(_ptr(num), _ptr(tri)), "iso_mc_case_table")
+    return num, tri
+
+
+class _DeviceArray:
+    """CUDA array interface over library-owned memory (no copy)."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": shape, "typestr": typestr, "data": (ptr, False),
+                                         "version": 3, "strides": None}
+
+
+class Mesh:
+    """A surface computed by Volume.extract.  `vertices` is a (3T, 4) float32
+    CUDA tensor viewing library-owned memory: valid until release()."""
+
+    def __init__(self, volume, m):
+        self._volume = volume
+        self._m = m
+        self.num_triangles = int(m.num_triangles)
+        self.stats = m.stats.as_dict()
+
+    @property
+    def vertices(self):
+        import torch
+        if not self._m.d_vertices:
+            return torch.zeros((0, 4), dtype=torch.float32, device="cuda")
+        arr = _DeviceArray(int(self._m.d_vertices), (3 * self.num_triangles, 4), "<f4")
+        return torch.as_tensor(arr, device="cuda")
+
+    def release(self):
+        if self._m is not None and self._m.d_vertices:
+            _check(lib().iso_mesh_release(self._volume._h, ctypes.byref(self._m)), "iso_mesh_release")
+        self._m = None
+
+    def __del__(self):
+        try:
+            if self._volume is not None and self._volume._h:
+                self.release()
+        except Exception:
+            pass
+
+
+class Volume:
+    """A compressed volume resident on the GPU with its decoded-block cache.
+
+    bits       uint64 words (nb*rate), numpy (host) or a CUDA tensor
+    dims       (nx, ny, nz)
+    rate       bits per sample
+    bmin/bmax  per-block ranges of the decoded samples (nb floats each)
+    """
+
+    def __init__(self, bits, dims, rate, bmin, bmax, *, stream=None, debug=False, initial_cache_fraction=0.1,
+                 cache_budget_bytes=0):
+        self._h = None
+        on_device = not isinstance(bits, np.ndarray) and bool(getattr(bits, "is_cuda", False))
+        if not isinstance(bits, np.ndarray) and not on_device:       # CPU (e.g. pinned) torch tensors
+            bits, bmin, bmax = bits.contiguous(), bmin.contiguous(), bmax.contiguous()
+        elif not on_device:
+            bits = np.ascontiguousarray(bits, np.uint64)
+            bmin = np.ascontiguousarray(bmin, np.float32)
+            bmax = np.ascontiguousarray(bmax, np.float32)
+        self.dims = tuple(int(d) for d in dims)
+        self.rate = int(rate)
+        self.nb = int(np.prod(block_dims(self.dims)))
+        opt = _Options()
+        opt.flags = (ISO_INPUT_ON_DEVICE if on_device else 0) | (ISO_DEBUG if debug else 0)
+        opt.stream = stream if stream is not None else _current_stream()
+        opt.initial_cache_fraction = float(initial_cache_fraction)
+        opt.cache_budget_bytes = int(cache_budget_bytes)
+        nbytes = bits.nbytes if isinstance(bits, np.ndarray) else bits.numel() * bits.element_size()
+        h = ctypes.c_void_p()
+        nx, ny, nz = self.dims
+        _check(lib().iso_load_volume(ctypes.byref(h), _ptr(bits), nbytes, nx, ny, nz, self.rate,
+                                     _ptr(bmin), _ptr(bmax), ctypes.byref(opt)), "iso_load_volume")
+        self._h = h
+        self.debug_enabled = bool(debug)
+
+    def extract(self, iso):
+        m = _Mesh()
+        _check(lib().iso_extract(self._h, ctypes.c_float(iso), ctypes.byref(m)), "iso_extract")
+        return Mesh(self, m)
+
+    def extract_into(self, iso, out, check=True):
+        """Write the surface into `out`, a CUDA float32 tensor of shape (3C, 4)
+        or (C, 3, 4) for C triangles.  Returns the stats dict."""
+        cap = out.numel() // 12
+        st = _Stats()
+        rc = lib().iso_extract_into(self._h, ctypes.c_float(iso), _ptr(out), cap, ctypes.byref(st))
+        if check:
+            _check(rc, "iso_extract_into")
+        d = st.as_dict()
+        d["status"] = rc
+        return d
+
+    STAGES = ("prep", "cull", "cache_update", "decode", "triangles")
+
+    def set_profiling(self, on=True):
+        _check(lib().iso_set_profiling(self._h, 1 if on else 0), "iso_set_profiling")
+
+    def stage_times(self):
+        """ms per stage of the last extraction (profiling on)"""
+        buf = (ctypes.c_float * 5)()
+        _check(lib().iso_stage_times(self._h, buf, 5), "iso_stage_times")
+        return dict(zip(self.STAGES, [float(x) for x in buf]))
+
+    def cache_reset(self):
+        _check(lib().iso_cache_reset(self._h), "iso_cache_reset")
+
+    def set_stream(self, stream):
+        _check(lib().iso_set_stream(self._h, stream), "iso_set_stream")
+
+    def debug(self, name):
+        which, dtype = DBG[name]
+        cnt = ctypes.c_uint64()
+        rc = lib().iso_debug_get(self._h, which, None, 0, ctypes.byref(cnt))
+        if rc not in (ISO_OK, ISO_ERR_CAPACITY):
+            _check(rc, "iso_debug_get")
+        out = np.zeros(int(cnt.value), dtype)
+        if out.size:
+            _check(lib().iso_debug_get(self._h, which, _ptr(out), out.nbytes, ctypes.byref(cnt)), "iso_debug_get")
+        return out
+
+    def read_blocks(self, ids):
+        ids = np.ascontiguousarray(ids, np.uint32)
+        out = np.zeros((len(ids), 64), np.float32)
+        _check(lib().iso_debug_read_blocks(self._h, _ptr(ids), len(ids), _ptr(out)), "iso_debug_read_blocks")
+        return out
+
+    def release(self):
+        if self._h:
+            lib().iso_release(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
+
+
+def encode_field(field, rate, stream=None):
+    """Encode a CUDA float32 tensor of shape (nz, ny, nx) on the GPU.
+    Returns (bits uint64-as-int64 tensor (nb, rate), bmin, bmax) on the same device."""
+    import torch
+    assert field.is_cuda and field.dtype == torch.float32 and field.is_contiguous()
+    nz, ny, nx = field.shape
+    nb = int(np.prod(block_dims((nx, ny, nz))))
+    bits = torch.empty((nb, rate), dtype=torch.int64, device=field.device)
+    bmin = torch.empty(nb, dtype=torch.float32, device=field.device)
+    bmax = torch.empty(nb, dtype=torch.float32, device=field.device)
+    _check(lib().iso_encode_field(_ptr(field), nx, ny, nz, rate, _ptr(bits), _ptr(bmin), _ptr(bmax),
+                                  stream if stream is not None else _current_stream()), "iso_encode_field")
+    return bits, bmin, bmax
+
+
+def decode_blocks(bits, rate, ids, stream=None):
+    """Decode blocks `ids` (CUDA uint32-as-int32 tensor) of a CUDA bitstream tensor.
+    Returns a (n, 64) float32 CUDA tensor."""
+    import torch
+    n = ids.numel()
+    out = torch.empty((n, 64), dtype=torch.float32, device=bits.device)
+    _check(lib().iso_decode_blocks(_ptr(bits), rate, _ptr(ids), n, _ptr(out),
+                                   stream if stream is not None else _current_stream()), "iso_decode_blocks")
+    return out

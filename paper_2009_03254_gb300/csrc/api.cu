@@ -1,0 +1,544 @@
+// Host side of the C ABI declared in include/bcmc.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "bcmc.h"
+#include "common.cuh"
+#include "kernels.cuh"
+#include "mc_tables.cuh"
+
+using namespace bcmc;
+
+struct iso_volume {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    Geom g{};
+    uint32_t flags = 0;
+    DevState s{};
+    Grids grids{};
+    uint32_t cap = 0;                 // physical slots
+    uint32_t n_cull_desc = 0, n_lru_desc = 0;
+    Ctl *host_ctl = nullptr;          // pinned mirror for the one readback
+    // owned device allocations
+    uint64_t *bits = nullptr;
+    float *bmin = nullptr, *bmax = nullptr;
+    float2 *hull = nullptr;
+    uint8_t *tables = nullptr;
+    unsigned long long dbg_edges_cap = 0;   // in vertices
+    bool profiling = false;
+    cudaEvent_t ev[ISO_NUM_STAGES + 1] = {};
+    float stage_ms[ISO_NUM_STAGES] = {};
+    unsigned long long last_tris = 0;
+    uint32_t last_n_active = 0, last_n_new = 0, last_slots = 0;
+};
+
+namespace {
+
+#define CK(call)                                                  \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) {                                  \
+            (void)cudaGetLastError();                             \
+            return e_ == cudaErrorMemoryAllocation ? ISO_ERR_OOM : ISO_ERR_CUDA; \
+        }                                                         \
+    } while (0)
+
+template <typename T>
+int dalloc(T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    CK(cudaMalloc((void **)p, count * sizeof(T)));
+    return ISO_OK;
+}
+
+void dfree(void *p) {
+    if (p) cudaFree(p);
+}
+
+int geometry(uint32_t nx, uint32_t ny, uint32_t nz, uint32_t rate, Geom *g) {
+    if (nx == 0 || ny == 0 || nz == 0 || rate < 1 || rate > 32) return ISO_ERR_INVALID_ARG;
+    const uint64_t nbx = (nx + 3ull) / 4, nby = (ny + 3ull) / 4, nbz = (nz + 3ull) / 4;
+    const uint64_t nb = nbx * nby * nbz;
+    if (nb >= (1ull << 31)) return ISO_ERR_INVALID_ARG;   // ids and packed counters are 31-bit
+    *g = Geom{nx, ny, nz, (uint32_t)nbx, (uint32_t)nby, (uint32_t)nbz, (uint32_t)nb, rate};
+    return ISO_OK;
+}
+
+int free_volume(iso_volume *v) {
+    if (!v) return ISO_OK;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaSetDevice(v->device);
+    if (v->stream) cudaStreamSynchronize(v->stream);
+    DevState &s = v->s;
+    void *ptrs[] = {v->bits, v->bmin, v->bmax, v->hull, v->tables, s.mactive, s.iactive, s.inew, s.islot, s.slast,
+                    s.sblock, s.lbuf[0], s.lbuf[1], s.newslot, s.slots, s.desc_cull, s.desc_lru_a, s.desc_lru_b,
+                    s.desc_mc, s.ctl, s.dbg_cases, s.dbg_btri, s.dbg_boff, s.dbg_edges};
+    for (void *p : ptrs) dfree(p);
+    if (v->host_ctl) cudaFreeHost(v->host_ctl);
+    for (cudaEvent_t &e : v->ev)
+        if (e) cudaEventDestroy(e);
+    cudaSetDevice(dev);
+    delete v;
+    return ISO_OK;
+}
+
+struct DeviceGuard {              // make the volume's device current for the call
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// After a timeout the cache bookkeeping may be inconsistent: empty it so
+// the next extraction starts from a clean state.
+int status_to_error(iso_volume *v, uint32_t st) {
+    if (st & kStatusTimeout) {
+        launch_reset_cache(v->s, v->stream);
+        cudaStreamSynchronize(v->stream);
+        (void)cudaGetLastError();
+        return ISO_ERR_TIMEOUT;
+    }
+    if (st & kStatusBudget) return ISO_ERR_BUDGET;
+    return ISO_OK;
+}
+
+// queue the whole pipeline; the caller reads the control block afterwards
+int enqueue_extract(iso_volume *v, float iso, float4 *out, unsigned long long cap_tris) {
+    const bool debug = (v->flags & ISO_DEBUG) != 0;
+    const bool prof = v->profiling;
+    if (prof) cudaEventRecord(v->ev[0], v->stream);
+    launch_prep(v->s, v->n_cull_desc, v->n_lru_desc, cap_tris, false, v->grids.prep, v->stream);
+    if (prof) cudaEventRecord(v->ev[1], v->stream);
+    launch_cull(v->s, v->g, iso, v->grids.cull, v->stream);
+    if (prof) cudaEventRecord(v->ev[2], v->stream);
+    launch_lru(v->s, v->grids.lru_a, v->grids.lru_b, v->stream);
+    if (prof) cudaEventRecord(v->ev[3], v->stream);
+    launch_decode_new(v->s, v->g, v->grids.decode, v->stream);
+    if (prof) cudaEventRecord(v->ev[4], v->stream);
+    launch_mc(v->s, v->g, iso, out, debug, v->grids.mc, v->stream);
+    if (prof) cudaEventRecord(v->ev[5], v->stream);
+    CK(cudaGetLastError());
+    return ISO_OK;
+}
+
+void collect_stage_times(iso_volume *v) {
+    if (!v->profiling) return;
+    for (int k = 0; k < ISO_NUM_STAGES; k++) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, v->ev[k], v->ev[k + 1]) != cudaSuccess) {
+            (void)cudaGetLastError();
+            ms = -1.0f;
+        }
+        v->stage_ms[k] = ms;
+    }
+}
+
+int enqueue_mc_again(iso_volume *v, float iso, float4 *out, unsigned long long cap_tris) {
+    const bool debug = (v->flags & ISO_DEBUG) != 0;
+    launch_prep(v->s, v->n_cull_desc, v->n_lru_desc, cap_tris, true, v->grids.prep, v->stream);
+    launch_mc(v->s, v->g, iso, out, debug, v->grids.mc, v->stream);
+    CK(cudaGetLastError());
+    return ISO_OK;
+}
+
+int read_ctl(iso_volume *v) {
+    CK(cudaMemcpyAsync(v->host_ctl, v->s.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, v->stream));
+    CK(cudaStreamSynchronize(v->stream));
+    return ISO_OK;
+}
+
+void fill_stats(const iso_volume *v, iso_stats *st, uint32_t reruns) {
+    const Ctl &c = *v->host_ctl;
+    st->num_triangles = c.n_tri;
+    st->n_active = c.n_active;
+    st->n_new = c.n_new;
+    st->n_occupied = c.n_occ;
+    st->n_slots = c.S;
+    st->cache_bytes = (uint64_t)c.S * 256ull;
+    st->epoch = c.epoch;
+    st->reruns = reruns;
+}
+
+// debug mode: make sure the per-vertex edge-id buffer can hold T triangles
+int ensure_debug_edges(iso_volume *v, unsigned long long tris) {
+    if (!(v->flags & ISO_DEBUG) || 3ull * tris <= v->dbg_edges_cap) return ISO_OK;
+    CK(cudaStreamSynchronize(v->stream));
+    dfree(v->s.dbg_edges);
+    v->s.dbg_edges = nullptr;
+    const unsigned long long want = std::max(3ull * tris, 3ull * 1024);
+    int rc = dalloc(&v->s.dbg_edges, want);
+    if (rc) { v->dbg_edges_cap = 0; return rc; }
+    v->dbg_edges_cap = want;
+    return ISO_OK;
+}
+
+// run the pipeline into `out` (capacity cap_tris); returns the error of
+// the run, with the control block mirrored on the host
+int run(iso_volume *v, float iso, float4 *out, unsigned long long cap_tris) {
+    int rc = ensure_debug_edges(v, cap_tris);
+    if (rc) return rc;
+    rc = enqueue_extract(v, iso, out, cap_tris);
+    if (rc) return rc;
+    rc = read_ctl(v);
+    if (rc) return rc;
+    collect_stage_times(v);
+    v->last_tris = v->host_ctl->n_tri;
+    v->last_n_active = v->host_ctl->n_active;
+    v->last_n_new = v->host_ctl->n_new;
+    v->last_slots = v->host_ctl->S;
+    return status_to_error(v, v->host_ctl->status);
+}
+
+int rerun_mc(iso_volume *v, float iso, float4 *out, unsigned long long cap_tris) {
+    int rc = ensure_debug_edges(v, cap_tris);
+    if (rc) return rc;
+    rc = enqueue_mc_again(v, iso, out, cap_tris);
+    if (rc) return rc;
+    rc = read_ctl(v);
+    if (rc) return rc;
+    v->last_tris = v->host_ctl->n_tri;
+    return status_to_error(v, v->host_ctl->status);
+}
+
+bool build_tables_once(McTables *t) {
+    static McTables cached;
+    static int state = 0;     // 0 unbuilt, 1 ok, -1 failed
+    if (state == 0) state = build_mc_tables(&cached) && cached.max_tri <= kMaxTriPerCell ? 1 : -1;
+    if (state < 0) return false;
+    *t = cached;
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *iso_error_string(int status) {
+    switch (status) {
+        case ISO_OK: return "ok";
+        case ISO_ERR_INVALID_ARG: return "invalid argument";
+        case ISO_ERR_OOM: return "out of memory";
+        case ISO_ERR_BUDGET: return "active blocks exceed the cache budget";
+        case ISO_ERR_CUDA: return "CUDA runtime error";
+        case ISO_ERR_TIMEOUT: return "device-side wait timed out";
+        case ISO_ERR_CAPACITY: return "output buffer too small";
+        default: return "unknown status";
+    }
+}
+
+int iso_mc_case_table(uint8_t *num_tri, uint8_t *tri_edges) {
+    if (!num_tri || !tri_edges) return ISO_ERR_INVALID_ARG;
+    McTables t;
+    if (!build_tables_once(&t)) return ISO_ERR_INVALID_ARG;
+    std::memcpy(num_tri, t.num_tri, 256);
+    std::memcpy(tri_edges, t.tri_edges, 256 * 16);
+    return ISO_OK;
+}
+
+int iso_load_volume(iso_volume **out, const void *compressed, size_t compressed_bytes, uint32_t nx, uint32_t ny,
+                    uint32_t nz, uint32_t rate_bits, const float *block_min, const float *block_max,
+                    const iso_options *opt) {
+    if (!out || !compressed || !block_min || !block_max) return ISO_ERR_INVALID_ARG;
+    *out = nullptr;
+    Geom g;
+    int rc = geometry(nx, ny, nz, rate_bits, &g);
+    if (rc) return rc;
+    if (compressed_bytes != (size_t)g.nb * g.rate * 8) return ISO_ERR_INVALID_ARG;
+    iso_options o{};
+    if (opt) o = *opt;
+    double frac = o.initial_cache_fraction > 0 ? o.initial_cache_fraction : 0.1;
+
+    iso_volume *v = new (std::nothrow) iso_volume();
+    if (!v) return ISO_ERR_OOM;
+    if (cudaGetDevice(&v->device) != cudaSuccess) { (void)cudaGetLastError(); delete v; return ISO_ERR_CUDA; }
+    v->stream = (cudaStream_t)o.stream;
+    v->g = g;
+    v->flags = o.flags;
+    uint64_t cap = g.nb;
+    if (o.cache_budget_bytes) cap = std::min<uint64_t>(cap, o.cache_budget_bytes / 256);
+    if (cap == 0) { delete v; return ISO_ERR_BUDGET; }
+    v->cap = (uint32_t)cap;
+    uint32_t s0 = (uint32_t)std::min<double>((double)cap, std::ceil(frac * g.nb));
+    s0 = std::max<uint32_t>(s0, 1);
+
+#define TRY(x)                              \
+    do {                                    \
+        rc = (x);                           \
+        if (rc) { free_volume(v); return rc; } \
+    } while (0)
+
+    DevState &s = v->s;
+    const size_t words = (size_t)g.nb * g.rate;
+    const uint32_t nwords = (g.nb + 31) / 32;
+    v->n_cull_desc = (g.nb + kScanTile - 1) / kScanTile;
+    v->n_lru_desc = (v->cap + kScanTile - 1) / kScanTile;
+    const uint32_t n_mc_desc = (g.nb + kMcTileBlocks - 1) / kMcTileBlocks;
+    TRY(dalloc(&v->bits, words));
+    TRY(dalloc(&v->bmin, g.nb));
+    TRY(dalloc(&v->bmax, g.nb));
+    TRY(dalloc(&v->hull, g.nb));
+    TRY(dalloc(&v->tables, 256 + 256 * 16));
+    TRY(dalloc(&s.mactive, nwords));
+    TRY(dalloc(&s.iactive, g.nb));
+    TRY(dalloc(&s.inew, g.nb));
+    TRY(dalloc(&s.islot, g.nb));
+    TRY(dalloc(&s.slast, v->cap));
+    TRY(dalloc(&s.sblock, v->cap));
+    TRY(dalloc(&s.lbuf[0], v->cap));
+    TRY(dalloc(&s.lbuf[1], v->cap));
+    TRY(dalloc(&s.newslot, v->cap));
+    TRY(dalloc(&s.slots, (size_t)v->cap * 64));
+    TRY(dalloc(&s.desc_cull, v->n_cull_desc));
+    TRY(dalloc(&s.desc_lru_a, v->n_lru_desc));
+    TRY(dalloc(&s.desc_lru_b, v->n_lru_desc));
+    TRY(dalloc(&s.desc_mc, n_mc_desc));
+    TRY(dalloc(&s.ctl, 1));
+    if (v->flags & ISO_DEBUG) {
+        TRY(dalloc(&s.dbg_cases, (size_t)g.nb * 64));
+        TRY(dalloc(&s.dbg_btri, g.nb));
+        TRY(dalloc(&s.dbg_boff, g.nb));
+    }
+    if (cudaMallocHost((void **)&v->host_ctl, sizeof(Ctl)) != cudaSuccess) {
+        (void)cudaGetLastError();
+        v->host_ctl = nullptr;
+        free_volume(v);
+        return ISO_ERR_OOM;
+    }
+    s.bits = v->bits;
+    s.hull = v->hull;
+    s.tables = v->tables;
+
+    McTables t;
+    if (!build_tables_once(&t)) { free_volume(v); return ISO_ERR_CUDA; }
+    uint8_t table_bytes[256 + 256 * 16];
+    std::memcpy(table_bytes, t.num_tri, 256);
+    std::memcpy(table_bytes + 256, t.tri_edges, 256 * 16);
+
+    const cudaMemcpyKind kind = (o.flags & ISO_INPUT_ON_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    cudaStream_t st = v->stream;
+#define TRYC(x)                                                            \
+    do {                                                                   \
+        cudaError_t e_ = (x);                                              \
+        if (e_ != cudaSuccess) { (void)cudaGetLastError(); free_volume(v); \
+            return e_ == cudaErrorMemoryAllocation ? ISO_ERR_OOM : ISO_ERR_CUDA; } \
+    } while (0)
+    TRYC(cudaMemcpyAsync(v->bits, compressed, words * 8, kind, st));
+    TRYC(cudaMemcpyAsync(v->bmin, block_min, (size_t)g.nb * 4, kind, st));
+    TRYC(cudaMemcpyAsync(v->bmax, block_max, (size_t)g.nb * 4, kind, st));
+    TRYC(cudaMemcpyAsync(v->tables, table_bytes, sizeof(table_bytes), cudaMemcpyHostToDevice, st));
+    TRYC(cudaMemsetAsync(s.islot, 0xFF, (size_t)g.nb * 4, st));
+    TRYC(cudaMemsetAsync(s.sblock, 0xFF, (size_t)v->cap * 4, st));
+    TRYC(cudaMemsetAsync(s.slast, 0, (size_t)v->cap * 4, st));
+    TRYC(cudaMemsetAsync(s.mactive, 0, (size_t)nwords * 4, st));
+    TRYC(cudaMemsetAsync(s.desc_mc, 0, (size_t)n_mc_desc * 8, st));
+    // index lists start as valid ids, so that even a pass cut short by a
+    // device-side timeout only ever indexes inside the volume and the cache
+    TRYC(cudaMemsetAsync(s.iactive, 0, (size_t)g.nb * 4, st));
+    TRYC(cudaMemsetAsync(s.inew, 0, (size_t)g.nb * 4, st));
+    TRYC(cudaMemsetAsync(s.newslot, 0, (size_t)v->cap * 4, st));
+    TRYC(cudaMemsetAsync(s.lbuf[0], 0, (size_t)v->cap * 4, st));
+    TRYC(cudaMemsetAsync(s.lbuf[1], 0, (size_t)v->cap * 4, st));
+    Ctl c0{};
+    c0.S = s0;
+    c0.cap = v->cap;
+    *v->host_ctl = c0;
+    TRYC(cudaMemcpyAsync(s.ctl, v->host_ctl, sizeof(Ctl), cudaMemcpyHostToDevice, st));
+    launch_hull(v->bmin, v->bmax, v->hull, g, st);
+    TRYC(cudaGetLastError());
+    TRYC(cudaStreamSynchronize(st));
+    int sms = 0;
+    TRYC(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, v->device));
+    v->grids = compute_grids(sms);
+    TRYC(cudaGetLastError());
+    *out = v;
+    return ISO_OK;
+#undef TRY
+#undef TRYC
+}
+
+int iso_extract_into(iso_volume *v, float isovalue, float *d_vertices, uint64_t capacity_triangles,
+                     iso_stats *stats) {
+    if (!v || !std::isfinite(isovalue) || (!d_vertices && capacity_triangles)) return ISO_ERR_INVALID_ARG;
+    DeviceGuard dg(v->device);
+    int rc = run(v, isovalue, reinterpret_cast<float4 *>(d_vertices), capacity_triangles);
+    if (stats) fill_stats(v, stats, 0);
+    if (rc) return rc;
+    if (v->host_ctl->n_tri > capacity_triangles) return ISO_ERR_CAPACITY;
+    return ISO_OK;
+}
+
+int iso_extract(iso_volume *v, float isovalue, iso_mesh *out) {
+    if (!v || !out || !std::isfinite(isovalue)) return ISO_ERR_INVALID_ARG;
+    DeviceGuard dg(v->device);
+    std::memset(out, 0, sizeof(*out));
+    // first guess: the last surface's size plus a margin, else 2 per block
+    unsigned long long guess = v->last_tris ? v->last_tris + v->last_tris / 4 + 4096 : 2ull * v->g.nb + 4096;
+    float4 *buf = nullptr;
+    CK(cudaMallocAsync((void **)&buf, guess * 3 * sizeof(float4), v->stream));
+    int rc = run(v, isovalue, buf, guess);
+    uint32_t reruns = 0;
+    if (rc == ISO_OK && v->host_ctl->n_tri > guess) {
+        const unsigned long long need = v->host_ctl->n_tri;
+        cudaFreeAsync(buf, v->stream);
+        buf = nullptr;
+        CK(cudaMallocAsync((void **)&buf, std::max(need, 1ull) * 3 * sizeof(float4), v->stream));
+        guess = std::max(need, 1ull);
+        rc = rerun_mc(v, isovalue, buf, guess);
+        reruns = 1;
+    }
+    if (rc) {
+        cudaFreeAsync(buf, v->stream);
+        cudaStreamSynchronize(v->stream);
+        fill_stats(v, &out->stats, reruns);
+        return rc;
+    }
+    out->d_vertices = reinterpret_cast<float *>(buf);
+    out->num_triangles = v->host_ctl->n_tri;
+    out->capacity_triangles = guess;
+    fill_stats(v, &out->stats, reruns);
+    return ISO_OK;
+}
+
+int iso_mesh_release(iso_volume *v, iso_mesh *m) {
+    if (!m) return ISO_ERR_INVALID_ARG;
+    if (!m->d_vertices) return ISO_OK;
+    if (!v) return ISO_ERR_INVALID_ARG;
+    DeviceGuard dg(v->device);
+    CK(cudaFreeAsync(m->d_vertices, v->stream));
+    m->d_vertices = nullptr;
+    m->num_triangles = 0;
+    m->capacity_triangles = 0;
+    return ISO_OK;
+}
+
+void iso_release(iso_volume *v) { free_volume(v); }
+
+int iso_set_stream(iso_volume *v, void *stream) {
+    if (!v) return ISO_ERR_INVALID_ARG;
+    DeviceGuard dg(v->device);
+    CK(cudaStreamSynchronize(v->stream));
+    v->stream = (cudaStream_t)stream;
+    return ISO_OK;
+}
+
+int iso_set_profiling(iso_volume *v, int on) {
+    if (!v) return ISO_ERR_INVALID_ARG;
+    DeviceGuard dg(v->device);
+    if (on && !v->ev[0]) {
+        for (cudaEvent_t &e : v->ev) CK(cudaEventCreate(&e));
+    }
+    v->profiling = on != 0;
+    return ISO_OK;
+}
+
+int iso_stage_times(iso_volume *v, float *ms, int n) {
+    if (!v || !ms || n < ISO_NUM_STAGES) return ISO_ERR_INVALID_ARG;
+    for (int k = 0; k < ISO_NUM_STAGES; k++) ms[k] = v->profiling ? v->stage_ms[k] : 0.0f;
+    return ISO_OK;
+}
+
+int iso_cache_reset(iso_volume *v) {
+    if (!v) return ISO_ERR_INVALID_ARG;
+    DeviceGuard dg(v->device);
+    launch_reset_cache(v->s, v->stream);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(v->stream));
+    return ISO_OK;
+}
+
+int iso_encode_field(const float *d_field, uint32_t nx, uint32_t ny, uint32_t nz, uint32_t rate_bits,
+                     uint64_t *d_bits, float *d_bmin, float *d_bmax, void *stream) {
+    if (!d_field || !d_bits || !d_bmin || !d_bmax) return ISO_ERR_INVALID_ARG;
+    Geom g;
+    int rc = geometry(nx, ny, nz, rate_bits, &g);
+    if (rc) return rc;
+    launch_encode(d_field, g, d_bits, d_bmin, d_bmax, (cudaStream_t)stream);
+    CK(cudaGetLastError());
+    return ISO_OK;
+}
+
+int iso_decode_blocks(const uint64_t *d_bits, uint32_t rate_bits, const uint32_t *d_ids, uint64_t n, float *d_out,
+                      void *stream) {
+    if (rate_bits < 1 || rate_bits > 32) return ISO_ERR_INVALID_ARG;
+    if (n == 0) return ISO_OK;
+    if (!d_bits || !d_ids || !d_out) return ISO_ERR_INVALID_ARG;
+    launch_decode_list(d_bits, rate_bits, d_ids, n, d_out, (cudaStream_t)stream);
+    CK(cudaGetLastError());
+    return ISO_OK;
+}
+
+int iso_debug_get(iso_volume *v, int which, void *host_dst, size_t bytes, uint64_t *count) {
+    if (!v || !count) return ISO_ERR_INVALID_ARG;
+    DeviceGuard dg(v->device);
+    const bool dbg = (v->flags & ISO_DEBUG) != 0;
+    const void *src = nullptr;
+    uint64_t n = 0;
+    size_t elem = 0;
+    switch (which) {
+        case ISO_DBG_ACTIVE_IDS: src = v->s.iactive; n = v->last_n_active; elem = 4; break;
+        case ISO_DBG_NEW_IDS: src = v->s.inew; n = v->last_n_new; elem = 4; break;
+        case ISO_DBG_SLOT_OF_BLOCK: src = v->s.islot; n = v->g.nb; elem = 4; break;
+        case ISO_DBG_BLOCK_OF_SLOT: src = v->s.sblock; n = v->last_slots; elem = 4; break;
+        case ISO_DBG_SLOT_LAST_USE: src = v->s.slast; n = v->last_slots; elem = 4; break;
+        case ISO_DBG_ACTIVE_MASK: src = v->s.mactive; n = (v->g.nb + 31) / 32; elem = 4; break;
+        case ISO_DBG_CELL_CASES: if (!dbg) return ISO_ERR_INVALID_ARG; src = v->s.dbg_cases; n = 64ull * v->last_n_active; elem = 1; break;
+        case ISO_DBG_BLOCK_TRIS: if (!dbg) return ISO_ERR_INVALID_ARG; src = v->s.dbg_btri; n = v->last_n_active; elem = 4; break;
+        case ISO_DBG_BLOCK_OFFSETS: if (!dbg) return ISO_ERR_INVALID_ARG; src = v->s.dbg_boff; n = v->last_n_active; elem = 8; break;
+        case ISO_DBG_EDGE_IDS:
+            if (!dbg) return ISO_ERR_INVALID_ARG;
+            src = v->s.dbg_edges;
+            n = std::min<unsigned long long>(3ull * v->last_tris, v->dbg_edges_cap);
+            elem = 8;
+            break;
+        default: return ISO_ERR_INVALID_ARG;
+    }
+    *count = n;
+    if (n == 0) return ISO_OK;
+    if (!host_dst || bytes < n * elem) return ISO_ERR_CAPACITY;
+    CK(cudaStreamSynchronize(v->stream));
+    CK(cudaMemcpy(host_dst, src, n * elem, cudaMemcpyDeviceToHost));
+    return ISO_OK;
+}
+
+int iso_debug_read_blocks(iso_volume *v, const uint32_t *ids, uint64_t n, float *host_out) {
+    if (!v || (n && (!ids || !host_out))) return ISO_ERR_INVALID_ARG;
+    if (n == 0) return ISO_OK;
+    DeviceGuard dg(v->device);
+    for (uint64_t i = 0; i < n; i++)
+        if (ids[i] >= v->g.nb) return ISO_ERR_INVALID_ARG;
+    uint32_t *d_ids = nullptr;
+    float *d_out = nullptr;
+    int32_t *d_missing = nullptr;
+    int rc = dalloc(&d_ids, n);
+    if (!rc) rc = dalloc(&d_out, n * 64);
+    if (!rc) rc = dalloc(&d_missing, 1);
+    int32_t missing = 0;
+    if (!rc && (cudaMemcpy(d_ids, ids, n * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+                cudaMemset(d_missing, 0, 4) != cudaSuccess))
+        rc = ISO_ERR_CUDA;
+    if (!rc) {
+        launch_gather_slots(v->s.slots, v->s.islot, d_ids, n, d_out, d_missing, v->stream);
+        if (cudaStreamSynchronize(v->stream) != cudaSuccess ||
+            cudaMemcpy(host_out, d_out, n * 64 * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(&missing, d_missing, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+            rc = ISO_ERR_CUDA;
+    }
+    (void)cudaGetLastError();
+    dfree(d_ids);
+    dfree(d_out);
+    dfree(d_missing);
+    if (rc) return rc;
+    return missing ? ISO_ERR_INVALID_ARG : ISO_OK;
+}
+
+}  // extern "C"

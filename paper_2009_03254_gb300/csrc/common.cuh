@@ -1,0 +1,167 @@
+// Shared device-side definitions of the block-compressed marching-cubes
+// library: volume geometry, the per-volume control block, the single-pass
+// decoupled look-back scan used by every compaction, and small bit tools.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace bcmc {
+
+// ---------------------------------------------------------------- geometry
+
+struct Geom {
+    uint32_t nx, ny, nz;      // samples
+    uint32_t nbx, nby, nbz;   // blocks per axis
+    uint32_t nb;              // total blocks (< 2^31, checked at load)
+    uint32_t rate;            // bits per sample = 64-bit words per block
+};
+
+// ---------------------------------------------------------------- control block
+
+enum Status : uint32_t {
+    kStatusTimeout = 1u,      // a bounded device wait gave up
+    kStatusBudget = 2u,       // new blocks do not fit in the slot cap
+};
+
+enum TileCounter { kCtrCull = 0, kCtrLruA = 1, kCtrLruB = 2, kCtrMc = 3, kNumCtr = 4 };
+
+// One per volume, in device memory.  Written only by the kernels of one
+// extraction at a time (stream order), read back once per extraction.
+struct Ctl {
+    uint32_t epoch;           // extraction count; S_last values are epochs
+    uint32_t n_active;        // |I_active|
+    uint32_t n_new;           // |I_new|
+    uint32_t n_assign;        // new blocks given a slot (n_new, or 0 on budget failure)
+    uint32_t S;               // slots in the LRU
+    uint32_t u;               // slots [0,u) have been used; [u,S) never
+    uint32_t cap;             // physical slot capacity
+    uint32_t lpar;            // which of the two list buffers holds the used-slot list
+    uint32_t S_next, u_next;  // committed by the decode kernel
+    uint32_t from_unused;     // assignments taken from [u, S_next)
+    uint32_t from_used;       // assignments taken from the used list
+    uint32_t keep_base;       // length of the surviving part of the used list
+    uint32_t n_occ;           // occupied blocks
+    uint32_t status;          // Status bits
+    uint32_t mc_tiles;        // tiles the triangle kernel used (descriptors to clear)
+    uint32_t ctr[kNumCtr];    // dynamic tile counters
+    unsigned long long n_tri; // triangles of the surface
+    unsigned long long tri_cap; // output capacity in triangles
+};
+
+// ---------------------------------------------------------------- memory-model helpers
+
+__device__ __forceinline__ void st_relaxed(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// ---------------------------------------------------------------- decoupled look-back
+//
+// Single-pass exclusive scan across tiles (Merrill and Garland's decoupled
+// look-back).  A descriptor is 64 bits: the top two bits say whether the
+// low 62 bits hold nothing yet (0), the tile's own aggregate (1) or the
+// inclusive prefix through the tile (2).  Values are sums of non-negative
+// counters, possibly two 31-bit counters packed side by side.
+// Tiles are handed out in order by an atomic counter, so every tile that a
+// waiter depends on belongs to a block that is already running; the wait
+// is still bounded: after kSpinLimit polls the tile reports a timeout in
+// Ctl::status and proceeds with what it has.
+
+constexpr unsigned long long kFlagAgg = 1ull << 62;
+constexpr unsigned long long kFlagPrefix = 2ull << 62;
+constexpr unsigned long long kValueMask = (1ull << 62) - 1;
+constexpr int kSpinLimit = 1 << 20;
+
+// Called by all 32 lanes of one warp.  Returns the exclusive prefix of
+// `tile` (same value in every lane) and publishes the inclusive one.
+__device__ __forceinline__ unsigned long long lookback_exclusive(unsigned long long *desc, uint32_t tile,
+                                                                  unsigned long long aggregate,
+                                                                  uint32_t *status) {
+    const int lane = threadIdx.x & 31;
+    if (tile == 0) {
+        if (lane == 0) st_relaxed(desc, kFlagPrefix | aggregate);
+        return 0;
+    }
+    if (lane == 0) st_relaxed(desc + tile, kFlagAgg | aggregate);
+    unsigned long long excl = 0;
+    long long base = (long long)tile - 1;
+    int spins = 0;
+    unsigned sleep_ns = 32;
+    while (true) {
+        long long idx = base - lane;
+        unsigned long long d = idx >= 0 ? ld_relaxed(desc + idx) : kFlagPrefix;
+        unsigned flag = (unsigned)(d >> 62);
+        unsigned ready = __ballot_sync(0xffffffffu, flag != 0);
+        unsigned pref = __ballot_sync(0xffffffffu, flag == 2);
+        unsigned need = pref ? ((pref & (0u - pref)) << 1) - 1u : 0xffffffffu; // lanes up to the first prefix
+        if ((ready & need) != need) {
+            if (++spins > kSpinLimit) {
+                if (lane == 0) atomicOr(status, (uint32_t)kStatusTimeout);
+                break;
+            }
+            __nanosleep(sleep_ns);
+            if (sleep_ns < 1024) sleep_ns <<= 1;
+            continue;
+        }
+        unsigned long long v = ((need >> lane) & 1u) ? (d & kValueMask) : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        excl += v;
+        if (pref) break;
+        base -= 32;
+    }
+    if (lane == 0) st_relaxed(desc + tile, kFlagPrefix | (excl + aggregate));
+    return excl;
+}
+
+// ---------------------------------------------------------------- bit tools
+
+// In-place transpose of a 32x32 bit matrix held in 32 words: afterwards
+// bit j of a[i] is what bit i of a[j] was.  Five rounds of swapping the
+// off-diagonal sub-blocks (16x16, 8x8, ..., 1x1).
+__device__ __forceinline__ void transpose32(uint32_t (&a)[32]) {
+    const uint32_t masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int r = 0; r < 5; r++) {
+        const int s = 16 >> r;
+        const uint32_t m = masks[r];
+#pragma unroll
+        for (int j = 0; j < 32; j++) {
+            if (j & s) continue;
+            uint32_t t = ((a[j] >> s) ^ a[j + s]) & m;
+            a[j + s] ^= t;
+            a[j] ^= t << s;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- coefficient order
+//
+// Sequency of a transform coefficient along one axis: index 0 is the
+// coarse average, 1 the coarse detail, 2 and 3 the fine details.  Codes
+// list coefficients by the sum of the three sequencies, then by linear
+// index (x fastest).
+struct CodingOrder {
+    int perm[64];             // perm[p] = linear index of the p-th coded coefficient
+};
+
+__host__ __device__ constexpr int axis_sequency(int i) { return i == 0 ? 0 : (i == 1 ? 1 : 2); }
+
+__host__ __device__ constexpr CodingOrder make_coding_order() {
+    CodingOrder o{};
+    int n = 0;
+    for (int level = 0; level <= 6; level++)
+        for (int l = 0; l < 64; l++)
+            if (axis_sequency(l & 3) + axis_sequency((l >> 2) & 3) + axis_sequency(l >> 4) == level) o.perm[n++] = l;
+    return o;
+}
+
+constexpr int kPrecision = 27;        // integer bits of the block-floating-point form
+constexpr uint32_t kNegaMask = 0xAAAAAAAAu;
+
+}  // namespace bcmc

@@ -1,0 +1,650 @@
+// The per-extraction pipeline (paper Section 4, Fig. "algorithm_sketch"):
+//
+//   prep    clear counters and look-back descriptors, advance the epoch
+//   cull    Section 4.1 + the first step of Algorithm 1: mark active blocks,
+//           compact I_active and I_new in one pass, stamp cache hits
+//   lru_a   Algorithm 1 (grow, select least recently used free slots,
+//           assign, evict) over the used-slot list
+//   lru_b   append this epoch's slots to the list (most recent last)
+//   decode  Section 4.2.1: decode each new block into its slot
+//   mc      Sections 4.3-4.5: halo staging, classification, per-block
+//           counts, single-pass prefix over blocks, vertex output
+//
+// Sizes that only the device knows (n_active, n_new, ...) never come back
+// to the host between kernels: the kernels are persistent and take their
+// work from counters in the control block.
+#include <algorithm>
+#include <cstdint>
+
+#include "codec.cuh"
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace bcmc {
+
+// ================================================================ prep
+
+__global__ void __launch_bounds__(kThreads) prep_kernel(DevState s, uint32_t n_cull_desc, uint32_t n_lru_desc,
+                                                         unsigned long long tri_cap, int mc_only) {
+    Ctl *c = s.ctl;
+    const uint32_t n_mc_desc = c->mc_tiles;   // descriptors the last triangle pass used
+    const uint32_t stride = gridDim.x * blockDim.x;
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    for (uint32_t i = tid; i < n_mc_desc; i += stride) s.desc_mc[i] = 0;
+    if (!mc_only) {
+        for (uint32_t i = tid; i < n_cull_desc; i += stride) s.desc_cull[i] = 0;
+        for (uint32_t i = tid; i < n_lru_desc; i += stride) {
+            s.desc_lru_a[i] = 0;
+            s.desc_lru_b[i] = 0;
+        }
+    }
+    if (tid == 0) {
+        if (!mc_only) {
+            c->epoch += 1;
+            c->n_active = 0;
+            c->n_new = 0;
+            c->n_assign = 0;
+            c->status = 0;
+            for (int k = 0; k < kNumCtr; k++) c->ctr[k] = 0;
+        }
+        c->ctr[kCtrMc] = 0;
+        c->n_occ = 0;
+        c->n_tri = 0;
+        c->tri_cap = tri_cap;
+    }
+}
+
+// ================================================================ tile scan helpers
+//
+// A tile is kScanTile entries handled by 256 threads in 8 rounds; entry
+// tile*2048 + r*256 + threadIdx.x belongs to round r.  Per (round, warp)
+// the warp's ballot gives its 32 flags; a warp-0 scan over the 64
+// (round, warp) counts gives each group's offset inside the tile.
+
+struct TileScan {
+    uint32_t cnt[8][8];               // per (round, warp): packed counts, then exclusive offsets
+    unsigned long long excl;          // tile's exclusive prefix (look-back)
+    uint32_t tile;
+};
+
+// warp 0: turn s.cnt into exclusive offsets (packed 16-bit fields add
+// without carries: a tile holds at most 2048 entries) and return the
+// tile's packed total in every lane
+__device__ __forceinline__ uint32_t scan_tile_counts(TileScan &ts) {
+    const int lane = threadIdx.x & 31;
+    uint32_t *flat = &ts.cnt[0][0];
+    const uint32_t a = flat[2 * lane], b = flat[2 * lane + 1];
+    uint32_t incl = a + b;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const uint32_t excl = incl - (a + b);
+    flat[2 * lane] = excl;
+    flat[2 * lane + 1] = excl + a;
+    return __shfl_sync(0xffffffffu, incl, 31);
+}
+
+// ================================================================ cull (Section 4.1)
+//
+// Active test: the union of a block's range with each neighbour's range
+// contains iso (lo < iso <= hi) for some neighbour or the block itself.
+// That holds exactly when lo < iso <= hi for the min/max taken over the
+// whole 3x3x3 block neighbourhood, which the loader precomputes (`hull`).
+// Active blocks that have a slot are cache hits (slot stamped with the
+// epoch: "reset the age"); the others are new.
+
+__global__ void __launch_bounds__(kThreads) cull_kernel(DevState s, Geom g, float iso, uint32_t ntiles) {
+    __shared__ TileScan ts;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t epoch = s.ctl->epoch;
+    const uint32_t lt = (1u << lane) - 1u;
+    while (true) {
+        if (threadIdx.x == 0) ts.tile = atomicAdd(&s.ctl->ctr[kCtrCull], 1u);
+        __syncthreads();
+        const uint32_t tile = ts.tile;
+        if (tile >= ntiles) break;
+        uint32_t act_bits[8], new_bits[8];
+#pragma unroll
+        for (int r = 0; r < 8; r++) {
+            const uint32_t b = tile * kScanTile + r * kThreads + threadIdx.x;
+            bool act = false, nw = false;
+            if (b < g.nb) {
+                const float2 h = __ldg(s.hull + b);
+                act = (h.x < iso) && (iso <= h.y);
+                if (act) {
+                    const int32_t sl = s.islot[b];
+                    if (sl >= 0) s.slast[sl] = epoch;
+                    else nw = true;
+                }
+            }
+            act_bits[r] = __ballot_sync(0xffffffffu, act);
+            new_bits[r] = __ballot_sync(0xffffffffu, nw);
+            if (lane == 0) {
+                ts.cnt[r][warp] = ((uint32_t)__popc(act_bits[r]) << 16) | (uint32_t)__popc(new_bits[r]);
+                const uint32_t first = tile * kScanTile + r * kThreads + warp * 32;
+                if (first < g.nb) s.mactive[first >> 5] = act_bits[r];
+            }
+        }
+        __syncthreads();
+        if (warp == 0) {
+            const uint32_t tot = scan_tile_counts(ts);
+            const unsigned long long agg = ((unsigned long long)(tot >> 16) << 31) | (tot & 0xFFFFu);
+            const unsigned long long excl = lookback_exclusive(s.desc_cull, tile, agg, &s.ctl->status);
+            if (lane == 0) {
+                ts.excl = excl;
+                if (tile == ntiles - 1) {
+                    const unsigned long long incl = excl + agg;
+                    s.ctl->n_active = (uint32_t)(incl >> 31);
+                    s.ctl->n_new = (uint32_t)(incl & 0x7FFFFFFFu);
+                }
+            }
+        }
+        __syncthreads();
+        const uint32_t act_base = (uint32_t)(ts.excl >> 31), new_base = (uint32_t)(ts.excl & 0x7FFFFFFFu);
+#pragma unroll
+        for (int r = 0; r < 8; r++) {
+            const uint32_t b = tile * kScanTile + r * kThreads + threadIdx.x;
+            const uint32_t off = ts.cnt[r][warp];
+            if ((act_bits[r] >> lane) & 1u) s.iactive[act_base + (off >> 16) + __popc(act_bits[r] & lt)] = b;
+            if ((new_bits[r] >> lane) & 1u) s.inew[new_base + (off & 0xFFFFu) + __popc(new_bits[r] & lt)] = b;
+        }
+        __syncthreads();
+    }
+}
+
+// ================================================================ cache update (Algorithm 1)
+//
+// The paper keeps an age per slot, sorts the free slots by age and hands
+// the oldest to the new blocks.  Here a slot stores the epoch of its last
+// use (S_last; age = epoch - S_last), and the sort is replaced by a list
+// kept in least-recently-used order: slots [u, S) have never been used
+// (S_last = 0, the oldest, in index order) and lbuf[lpar][0..u) lists the
+// used slots by (S_last, index).  Each update:
+//   lru_a  keeps the list's entries that were not hit this epoch, in
+//          order; the first `from_used` of them (after the never-used
+//          slots) go to the new blocks, the rest move to the new list;
+//   lru_b  appends every slot stamped this epoch, by index.
+// The new list is again ordered by (S_last, index), so the slots handed
+// out are exactly those a stable sort by descending age would put first.
+// Growth (more new blocks than free slots) extends [u, S) to
+// max(2S, S + n_new - n_avail) slots, capped; new slots count as never
+// used, i.e. they have the highest age.
+
+__device__ __forceinline__ void assign_slot(const DevState &s, uint32_t slot, uint32_t r, uint32_t epoch) {
+    const uint32_t b = s.inew[r];
+    const int32_t old = s.sblock[slot];
+    if (old >= 0) s.islot[old] = -1;           // evict
+    s.sblock[slot] = (int32_t)b;
+    s.islot[b] = (int32_t)slot;
+    s.slast[slot] = epoch;
+    s.newslot[r] = slot;
+}
+
+__global__ void __launch_bounds__(kThreads) lru_a_kernel(DevState s) {
+    __shared__ TileScan ts;
+    __shared__ uint32_t s_status;
+    Ctl *c = s.ctl;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    if (threadIdx.x == 0) s_status = c->status;
+    __syncthreads();
+    if (s_status & kStatusTimeout) {           // counts from the cull may be short: change nothing
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            c->S_next = c->S;
+            c->u_next = c->u;
+            c->n_assign = 0;
+        }
+        return;
+    }
+    const uint32_t epoch = c->epoch, n_active = c->n_active, n_new = c->n_new;
+    const uint32_t S = c->S, u = c->u, cap = c->cap, lpar = c->lpar;
+    const uint32_t n_hit = n_active - n_new;
+    const uint32_t n_avail = S - n_hit;
+    uint32_t S2 = S;
+    if (n_new > n_avail) S2 = min(cap, max(2u * S, S + (n_new - n_avail)));
+    const bool fits = n_new <= S2 - n_hit;
+    const uint32_t n_assign = fits ? n_new : 0u;
+    const uint32_t from_unused = min(n_assign, S2 - u);
+    const uint32_t from_used = n_assign - from_unused;
+    const uint32_t avail_used = u - n_hit;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        c->S_next = S2;
+        c->u_next = u + from_unused;
+        c->from_unused = from_unused;
+        c->from_used = from_used;
+        c->keep_base = avail_used - from_used;
+        c->n_assign = n_assign;
+        if (!fits) atomicOr(&c->status, (uint32_t)kStatusBudget);
+    }
+    const uint32_t *L = s.lbuf[lpar];
+    uint32_t *Ln = s.lbuf[lpar ^ 1u];
+    const uint32_t ntiles = (u + kScanTile - 1) / kScanTile;
+    while (true) {
+        if (threadIdx.x == 0) ts.tile = atomicAdd(&c->ctr[kCtrLruA], 1u);
+        __syncthreads();
+        const uint32_t tile = ts.tile;
+        if (tile >= ntiles) break;
+        uint32_t bits[8], slot[8];
+#pragma unroll
+        for (int r = 0; r < 8; r++) {
+            const uint32_t i = tile * kScanTile + r * kThreads + threadIdx.x;
+            bool av = false;
+            slot[r] = 0;
+            if (i < u) {
+                slot[r] = L[i];
+                av = s.slast[slot[r]] != epoch;
+            }
+            bits[r] = __ballot_sync(0xffffffffu, av);
+            if (lane == 0) ts.cnt[r][warp] = (uint32_t)__popc(bits[r]);
+        }
+        __syncthreads();
+        if (warp == 0) {
+            const uint32_t tot = scan_tile_counts(ts);
+            const unsigned long long excl = lookback_exclusive(s.desc_lru_a, tile, tot, &c->status);
+            if (lane == 0) ts.excl = excl;
+        }
+        __syncthreads();
+        const uint32_t base = (uint32_t)ts.excl;
+#pragma unroll
+        for (int r = 0; r < 8; r++) {
+            if (!((bits[r] >> lane) & 1u)) continue;
+            const uint32_t rank = base + ts.cnt[r][warp] + __popc(bits[r] & lt);
+            if (rank < from_used) assign_slot(s, slot[r], from_unused + rank, epoch);
+            else Ln[rank - from_used] = slot[r];
+        }
+        __syncthreads();
+    }
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < from_unused; r += gridDim.x * blockDim.x)
+        assign_slot(s, u + r, r, epoch);
+}
+
+__global__ void __launch_bounds__(kThreads) lru_b_kernel(DevState s) {
+    __shared__ TileScan ts;
+    __shared__ uint32_t s_status;
+    Ctl *c = s.ctl;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    if (threadIdx.x == 0) s_status = c->status;
+    __syncthreads();
+    if (s_status & kStatusTimeout) return;
+    const uint32_t epoch = c->epoch, S2 = c->S_next, keep = c->keep_base;
+    uint32_t *Ln = s.lbuf[c->lpar ^ 1u];
+    const uint32_t ntiles = (S2 + kScanTile - 1) / kScanTile;
+    while (true) {
+        if (threadIdx.x == 0) ts.tile = atomicAdd(&c->ctr[kCtrLruB], 1u);
+        __syncthreads();
+        const uint32_t tile = ts.tile;
+        if (tile >= ntiles) break;
+        uint32_t bits[8];
+#pragma unroll
+        for (int r = 0; r < 8; r++) {
+            const uint32_t i = tile * kScanTile + r * kThreads + threadIdx.x;
+            const bool used_now = i < S2 && s.slast[i] == epoch;
+            bits[r] = __ballot_sync(0xffffffffu, used_now);
+            if (lane == 0) ts.cnt[r][warp] = (uint32_t)__popc(bits[r]);
+        }
+        __syncthreads();
+        if (warp == 0) {
+            const uint32_t tot = scan_tile_counts(ts);
+            const unsigned long long excl = lookback_exclusive(s.desc_lru_b, tile, tot, &c->status);
+            if (lane == 0) ts.excl = excl;
+        }
+        __syncthreads();
+        const uint32_t base = keep + (uint32_t)ts.excl;
+#pragma unroll
+        for (int r = 0; r < 8; r++) {
+            if (!((bits[r] >> lane) & 1u)) continue;
+            const uint32_t i = tile * kScanTile + r * kThreads + threadIdx.x;
+            Ln[base + ts.cnt[r][warp] + __popc(bits[r] & lt)] = i;
+        }
+        __syncthreads();
+    }
+}
+
+// ================================================================ decode (Section 4.2.1)
+
+__global__ void __launch_bounds__(kThreads) decode_new_kernel(DevState s, Geom g) {
+    Ctl *c = s.ctl;
+    if (c->status & kStatusTimeout) return;      // no barrier in this kernel: per-thread exit is safe
+    const uint32_t n = c->n_assign;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {   // commit the cache update
+        c->S = c->S_next;
+        c->u = c->u_next;
+        c->lpar ^= 1u;
+    }
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        const uint32_t b = s.inew[r];
+        const uint32_t slot = s.newslot[r];
+        float v[64];
+        decode_block(s.bits + (size_t)b * g.rate, g.rate, v);
+        float4 *dst = reinterpret_cast<float4 *>(s.slots + (size_t)slot * 64);
+#pragma unroll
+        for (int i = 0; i < 16; i++) dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+    }
+}
+
+// ================================================================ triangles (Sections 4.3-4.5)
+//
+// One tile = 32 consecutive entries of I_active, 8 warps.
+//  A  per block: look up its slot and its +x/+y/+z face, edge and corner
+//     neighbours.  A crossing cell needs all of them active (a crossing
+//     between two samples makes every block of its 2x2x2 block group
+//     active), so a block with an existing but inactive +neighbour has no
+//     crossing cell and is skipped: this is where the paper shrinks the
+//     block's extent back to 4.
+//  B  stage each block's 5x5x5 samples (own 64 + up to 61 halo) in shared
+//     memory.
+//  C  one warp per block, two cells per lane: case index, triangle count,
+//     block total.
+//  D  block totals -> tile total -> decoupled look-back over tiles: the
+//     prefix sum over per-block counts of Section 4.4 in one pass.
+//  E  per block: exclusive scan of the cell counts, then each lane writes
+//     whole float4 vertices so that a warp's 32 stores are contiguous.
+
+struct McSmem {
+    float halo[kMcTileBlocks][128];
+    int32_t nslot[kMcTileBlocks][8];
+    uint32_t bid[kMcTileBlocks];
+    uint8_t cases[kMcTileBlocks][64];
+    uint32_t btri[kMcTileBlocks];
+    uint32_t boff[kMcTileBlocks];
+    uint8_t tricell[kThreads / 32][320];
+    uint16_t celloff[kThreads / 32][64];
+    uint8_t num_tri[256];
+    uint8_t tri_edges[256][16];
+    unsigned long long tile_base;
+    uint32_t tile;
+};
+
+__device__ __forceinline__ int halo_index(int x, int y, int z) { return x + 5 * y + 25 * z; }
+
+__global__ void __launch_bounds__(kThreads) mc_kernel(DevState s, Geom g, float iso, float4 *__restrict__ out,
+                                                      int debug) {
+    __shared__ McSmem sm;
+    __shared__ uint32_t s_status;
+    Ctl *c = s.ctl;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < 256; i += kThreads) sm.num_tri[i] = s.tables[i];
+    for (int i = threadIdx.x; i < 256 * 16; i += kThreads) (&sm.tri_edges[0][0])[i] = s.tables[256 + i];
+    if (threadIdx.x == 0) s_status = c->status;
+    __syncthreads();
+    const uint32_t n_active = c->n_active;
+    const uint32_t ntiles = (n_active + kMcTileBlocks - 1) / kMcTileBlocks;
+    const unsigned long long tri_cap = c->tri_cap;
+    const bool failed = (s_status & (kStatusBudget | kStatusTimeout)) != 0;   // same value in the whole block
+    if (blockIdx.x == 0 && threadIdx.x == 0) c->mc_tiles = failed ? 0u : ntiles;
+    if (failed) return;
+    const uint32_t slab = g.nbx * g.nby;
+    while (true) {
+        if (threadIdx.x == 0) sm.tile = atomicAdd(&c->ctr[kCtrMc], 1u);
+        __syncthreads();
+        const uint32_t tile = sm.tile;
+        if (tile >= ntiles) break;
+        const uint32_t base = tile * kMcTileBlocks;
+        const uint32_t nblk = min((uint32_t)kMcTileBlocks, n_active - base);
+
+        // ---- A: neighbours
+        if (threadIdx.x < nblk) {
+            const int t = threadIdx.x;
+            const uint32_t b = s.iactive[base + t];
+            const uint32_t bx = b % g.nbx, by = (b / g.nbx) % g.nby, bz = b / slab;
+            const bool ex = bx + 1 < g.nbx, ey = by + 1 < g.nby, ez = bz + 1 < g.nbz;
+            bool complete = true;
+            sm.nslot[t][0] = s.islot[b];
+#pragma unroll
+            for (int o = 1; o < 8; o++) {
+                int32_t sl = -1;
+                if ((!(o & 1) || ex) && (!(o & 2) || ey) && (!(o & 4) || ez)) {
+                    const uint32_t nb = b + ((o & 1) ? 1u : 0u) + ((o & 2) ? g.nbx : 0u) + ((o & 4) ? slab : 0u);
+                    if ((s.mactive[nb >> 5] >> (nb & 31)) & 1u) sl = s.islot[nb];
+                    else complete = false;
+                }
+                sm.nslot[t][o] = sl;
+            }
+            if (!complete) sm.nslot[t][0] = -2;
+            sm.bid[t] = b;
+        }
+        __syncthreads();
+
+        // ---- B: stage samples
+        for (uint32_t idx = threadIdx.x; idx < nblk * 125u; idx += kThreads) {
+            const uint32_t t = idx / 125u, h = idx - t * 125u;
+            const uint32_t hx = h % 5u, hy = (h / 5u) % 5u, hz = h / 25u;
+            const int o = (hx == 4) | ((hy == 4) << 1) | ((hz == 4) << 2);
+            const int32_t self = sm.nslot[t][0];
+            const int32_t sl = self == -2 ? -1 : sm.nslot[t][o];
+            float v = 0.0f;
+            if (sl >= 0) v = s.slots[(size_t)sl * 64 + (hx & 3u) + 4u * (hy & 3u) + 16u * (hz & 3u)];
+            sm.halo[t][h] = v;
+        }
+        __syncthreads();
+
+        // ---- C: classify and count
+        for (uint32_t t = warp; t < nblk; t += kThreads / 32) {
+            const uint32_t b = sm.bid[t];
+            const bool skip = sm.nslot[t][0] == -2;
+            const uint32_t bx = b % g.nbx, by = (b / g.nbx) % g.nby, bz = b / slab;
+            uint32_t cnt = 0;
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int cell = lane + 32 * h;
+                const int cx = cell & 3, cy = (cell >> 2) & 3, cz = cell >> 4;
+                const bool valid = !skip && 4 * bx + cx + 1 < g.nx && 4 * by + cy + 1 < g.ny && 4 * bz + cz + 1 < g.nz;
+                uint32_t cs = 0;
+                if (valid) {
+                    const float *hb = sm.halo[t];
+#pragma unroll
+                    for (int k = 0; k < 8; k++) {
+                        const float v = hb[halo_index(cx + (k & 1), cy + ((k >> 1) & 1), cz + (k >> 2))];
+                        cs |= (v < iso ? 1u : 0u) << k;
+                    }
+                }
+                sm.cases[t][cell] = (uint8_t)cs;
+                cnt += sm.num_tri[cs];
+                if (debug) s.dbg_cases[(size_t)(base + t) * 64 + cell] = (uint8_t)cs;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+            if (lane == 0) sm.btri[t] = cnt;
+        }
+        __syncthreads();
+
+        // ---- D: prefix over blocks
+        if (warp == 0) {
+            const uint32_t mine = (uint32_t)lane < nblk ? sm.btri[lane] : 0u;
+            uint32_t incl = mine;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const uint32_t agg = __shfl_sync(0xffffffffu, incl, 31);
+            if ((uint32_t)lane < nblk) sm.boff[lane] = incl - mine;
+            const unsigned occ = __ballot_sync(0xffffffffu, mine > 0);
+            const unsigned long long excl = lookback_exclusive(s.desc_mc, tile, agg, &c->status);
+            if (lane == 0) {
+                sm.tile_base = excl;
+                if (tile == ntiles - 1) c->n_tri = excl + agg;
+                if (occ) atomicAdd(&c->n_occ, (uint32_t)__popc(occ));
+            }
+            if (debug && (uint32_t)lane < nblk) {
+                s.dbg_btri[base + lane] = mine;
+                s.dbg_boff[base + lane] = excl + (incl - mine);
+            }
+        }
+        __syncthreads();
+
+        // ---- E: vertices
+        for (uint32_t t = warp; t < nblk; t += kThreads / 32) {
+            const uint32_t tb = sm.btri[t];
+            if (tb == 0) continue;
+            const uint32_t b = sm.bid[t];
+            const uint32_t n0 = sm.num_tri[sm.cases[t][lane]], n1 = sm.num_tri[sm.cases[t][lane + 32]];
+            uint32_t i0 = n0, i1 = n1;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t a0 = __shfl_up_sync(0xffffffffu, i0, o), a1 = __shfl_up_sync(0xffffffffu, i1, o);
+                if (lane >= o) { i0 += a0; i1 += a1; }
+            }
+            const uint32_t tot0 = __shfl_sync(0xffffffffu, i0, 31);
+            const uint32_t o0 = i0 - n0, o1 = tot0 + i1 - n1;
+            sm.celloff[warp][lane] = (uint16_t)o0;
+            sm.celloff[warp][lane + 32] = (uint16_t)o1;
+            for (uint32_t k = 0; k < n0; k++) sm.tricell[warp][o0 + k] = (uint8_t)lane;
+            for (uint32_t k = 0; k < n1; k++) sm.tricell[warp][o1 + k] = (uint8_t)(lane + 32);
+            __syncwarp();
+            const unsigned long long gbase = sm.tile_base + sm.boff[t];
+            const uint32_t bx = b % g.nbx, by = (b / g.nbx) % g.nby, bz = b / slab;
+            const float *hb = sm.halo[t];
+            const float wbits = __uint_as_float(b);
+            for (uint32_t v = lane; v < 3 * tb; v += 32) {
+                const uint32_t tri = v / 3u, j = v - 3u * tri;
+                const uint32_t cell = sm.tricell[warp][tri];
+                const uint32_t k = tri - sm.celloff[warp][cell];
+                const uint32_t e = sm.tri_edges[sm.cases[t][cell]][3 * k + j];
+                const int a = (int)(e >> 2), j0 = (int)(e & 1u), j1 = (int)((e >> 1) & 1u);
+                const int px = (int)(cell & 3u) + (a == 0 ? 0 : j0);
+                const int py = (int)((cell >> 2) & 3u) + (a == 0 ? j0 : (a == 1 ? 0 : j1));
+                const int pz = (int)(cell >> 4) + (a == 2 ? 0 : j1);
+                const float vlo = hb[halo_index(px, py, pz)];
+                const float vhi = hb[halo_index(px + (a == 0), py + (a == 1), pz + (a == 2))];
+                const float tt = __fdiv_rn(__fsub_rn(iso, vlo), __fsub_rn(vhi, vlo));
+                float4 p = make_float4((float)px, (float)py, (float)pz, wbits);
+                if (a == 0) p.x = __fadd_rn(p.x, tt);
+                else if (a == 1) p.y = __fadd_rn(p.y, tt);
+                else p.z = __fadd_rn(p.z, tt);
+                const unsigned long long gt = gbase + tri;
+                if (gt < tri_cap) {
+                    out[gt * 3 + j] = p;
+                    if (debug) {
+                        const unsigned long long vox = (unsigned long long)(4 * bx + px) +
+                            (unsigned long long)g.nx * ((unsigned long long)(4 * by + py) +
+                                                        (unsigned long long)g.ny * (unsigned long long)(4 * bz + pz));
+                        s.dbg_edges[gt * 3 + j] = 3ull * vox + (unsigned long long)a;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+    }
+}
+
+// ================================================================ load-time and utility kernels
+
+// per block: min/max of the block ranges over its 3x3x3 block neighbourhood
+__global__ void hull_kernel(const float *__restrict__ bmin, const float *__restrict__ bmax, float2 *hull, Geom g) {
+    const uint32_t slab = g.nbx * g.nby;
+    for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < g.nb; b += gridDim.x * blockDim.x) {
+        const int bx = (int)(b % g.nbx), by = (int)((b / g.nbx) % g.nby), bz = (int)(b / slab);
+        float lo = bmin[b], hi = bmax[b];
+        for (int dz = -1; dz <= 1; dz++) {
+            const int z = bz + dz;
+            if (z < 0 || z >= (int)g.nbz) continue;
+            for (int dy = -1; dy <= 1; dy++) {
+                const int y = by + dy;
+                if (y < 0 || y >= (int)g.nby) continue;
+                for (int dx = -1; dx <= 1; dx++) {
+                    const int x = bx + dx;
+                    if (x < 0 || x >= (int)g.nbx) continue;
+                    const uint32_t n = (uint32_t)x + g.nbx * ((uint32_t)y + g.nby * (uint32_t)z);
+                    lo = fminf(lo, bmin[n]);
+                    hi = fmaxf(hi, bmax[n]);
+                }
+            }
+        }
+        hull[b] = make_float2(lo, hi);
+    }
+}
+
+__global__ void reset_cache_kernel(DevState s) {
+    Ctl *c = s.ctl;
+    const uint32_t cap = c->cap;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += gridDim.x * blockDim.x) {
+        const int32_t b = s.sblock[i];
+        if (b >= 0) s.islot[b] = -1;
+        s.sblock[i] = -1;
+        s.slast[i] = 0;
+    }
+}
+
+__global__ void reset_ctl_kernel(DevState s) {
+    s.ctl->u = 0;
+    s.ctl->lpar = 0;
+}
+
+__global__ void gather_slots_kernel(const float *__restrict__ slots, const int32_t *__restrict__ islot,
+                                    const uint32_t *__restrict__ ids, uint64_t n, float *out, int32_t *missing) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n * 64; i += (uint64_t)gridDim.x * blockDim.x) {
+        const int32_t sl = islot[ids[i / 64]];
+        if (sl < 0) {
+            *missing = 1;
+            out[i] = 0.0f;
+        } else {
+            out[i] = slots[(size_t)sl * 64 + (i % 64)];
+        }
+    }
+}
+
+// ================================================================ launchers
+
+void launch_prep(const DevState &s, uint32_t n_cull_desc, uint32_t n_lru_desc, unsigned long long tri_cap,
+                 bool mc_only, int grid, cudaStream_t st) {
+    prep_kernel<<<grid, kThreads, 0, st>>>(s, n_cull_desc, n_lru_desc, tri_cap, mc_only ? 1 : 0);
+}
+
+void launch_cull(const DevState &s, const Geom &g, float iso, int grid, cudaStream_t st) {
+    const uint32_t ntiles = (g.nb + kScanTile - 1) / kScanTile;
+    cull_kernel<<<(int)std::min<uint32_t>(ntiles, (uint32_t)grid), kThreads, 0, st>>>(s, g, iso, ntiles);
+}
+
+void launch_lru(const DevState &s, int grid_a, int grid_b, cudaStream_t st) {
+    lru_a_kernel<<<grid_a, kThreads, 0, st>>>(s);
+    lru_b_kernel<<<grid_b, kThreads, 0, st>>>(s);
+}
+
+void launch_decode_new(const DevState &s, const Geom &g, int grid, cudaStream_t st) {
+    decode_new_kernel<<<grid, kThreads, 0, st>>>(s, g);
+}
+
+void launch_mc(const DevState &s, const Geom &g, float iso, float4 *out, bool debug, int grid, cudaStream_t st) {
+    mc_kernel<<<grid, kThreads, 0, st>>>(s, g, iso, out, debug ? 1 : 0);
+}
+
+void launch_hull(const float *bmin, const float *bmax, float2 *hull, const Geom &g, cudaStream_t st) {
+    const uint32_t blocks = std::min<uint32_t>((g.nb + 255) / 256, 65535u * 4);
+    hull_kernel<<<blocks, 256, 0, st>>>(bmin, bmax, hull, g);
+}
+
+void launch_reset_cache(const DevState &s, cudaStream_t st) {
+    reset_cache_kernel<<<1024, 256, 0, st>>>(s);
+    reset_ctl_kernel<<<1, 1, 0, st>>>(s);
+}
+
+void launch_gather_slots(const float *slots, const int32_t *islot, const uint32_t *ids, uint64_t n, float *out,
+                         int32_t *missing, cudaStream_t st) {
+    if (n == 0) return;
+    const uint64_t blocks = std::min<uint64_t>((n * 64 + 255) / 256, 65535u);
+    gather_slots_kernel<<<(unsigned)blocks, 256, 0, st>>>(slots, islot, ids, n, out, missing);
+}
+
+Grids compute_grids(int sm_count) {
+    Grids gr{};
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cull_kernel, kThreads, 0);
+    gr.cull = std::max(1, occ) * sm_count;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lru_a_kernel, kThreads, 0);
+    gr.lru_a = std::max(1, occ) * sm_count;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lru_b_kernel, kThreads, 0);
+    gr.lru_b = std::max(1, occ) * sm_count;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, decode_new_kernel, kThreads, 0);
+    gr.decode = std::max(1, occ) * sm_count;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mc_kernel, kThreads, 0);
+    gr.mc = std::max(1, occ) * sm_count;
+    gr.prep = 2 * sm_count;
+    return gr;
+}
+
+}  // namespace bcmc

@@ -1,0 +1,322 @@
+"""GPU parity: every stage of the CUDA path against the CPU oracle.
+
+Integer, index and bit results (decoded samples, bitstreams, active and new
+block lists, cell cases, per-block counts and offsets, cache slot
+assignment, triangle edge ids and their order) must match bit for bit.
+Vertex positions must agree within 1e-5 voxel units: the oracle
+interpolates in float64, the GPU in float32 with IEEE division; with
+block-local coordinates in [0, 4] the float32 result is within a few ulp
+of 4 (~1e-6), so 1e-5 is a bound with margin, not a fit.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from synth import fields
+
+pytestmark = pytest.mark.gpu
+
+POS_TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def pkg():
+    import paper_2009_03254_gb300 as p
+    return p
+
+
+def torch():
+    import torch as t
+    return t
+
+
+def make_field(kind, dims, seed=0):
+    nx, ny, nz = dims
+    rng = np.random.default_rng(seed)
+    if kind == "noise":
+        return fields.gradient_noise(nx, ny, nz, seed + 1, octaves=4, base_period=16)
+    if kind == "sphere":
+        return fields.sphere_sdf(nx, ny, nz, 0.3 * min(dims))
+    if kind == "random":
+        return rng.standard_normal((nz, ny, nx)).astype(np.float32)
+    if kind == "special":   # zeros of both signs, subnormals, huge and tiny magnitudes
+        vals = np.array([0.0, -0.0, 1e-45, -3e-39, 1e-38, 1.5, -2.25, 1e30, -7e29, 3.4e-20, 65504.0], np.float32)
+        f = rng.choice(vals, size=(nz, ny, nx)).astype(np.float32)
+        f *= rng.choice(np.array([1.0, 0.5, 2.0], np.float32), size=f.shape)
+        return f
+    if kind == "checker":
+        return rng.integers(0, 2, (nz, ny, nx)).astype(np.float32)
+    raise ValueError(kind)
+
+
+def to_dev(a):
+    t = torch()
+    a = np.ascontiguousarray(a)
+    if a.dtype == np.uint64:
+        a = a.view(np.int64)
+    elif a.dtype == np.uint32:
+        a = a.view(np.int32)
+    return t.from_numpy(a).cuda()
+
+
+# ---------------------------------------------------------------- codec
+
+DECODE_CASES = [("noise", (37, 21, 14)), ("sphere", (20, 20, 20)), ("random", (9, 13, 7)), ("special", (16, 12, 8))]
+
+
+@pytest.mark.parametrize("rate", [1, 2, 3, 4, 8, 12, 16, 24, 32])
+@pytest.mark.parametrize("kind,dims", DECODE_CASES)
+def test_decode_blocks_bit_exact(kind, dims, rate):
+    f = make_field(kind, dims, 3)
+    bits, _, _ = oracle.encode_volume(f, rate)
+    ids = np.arange(bits.shape[0], dtype=np.uint32)
+    want = oracle.decode_blocks(bits, rate, ids)
+    got = pkg().decode_blocks(to_dev(bits), rate, to_dev(ids)).cpu().numpy()
+    assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+
+
+@pytest.mark.parametrize("rate", [1, 2, 5, 8, 16])
+def test_decode_corrupt_streams_bit_exact(rate):
+    rng = np.random.default_rng(rate)
+    bits = rng.integers(0, 1 << 63, (3000, rate), dtype=np.uint64) * np.uint64(2) + rng.integers(0, 2, (3000, rate), dtype=np.uint64)
+    bits[::7, 0] |= np.uint64(1)
+    ids = np.arange(3000, dtype=np.uint32)
+    want = oracle.decode_blocks(bits, rate, ids)
+    got = pkg().decode_blocks(to_dev(bits), rate, to_dev(ids)).cpu().numpy()
+    assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+
+
+@pytest.mark.parametrize("rate", [1, 2, 4, 7, 8, 16, 32])
+@pytest.mark.parametrize("kind,dims", DECODE_CASES + [("sphere", (1, 1, 1)), ("noise", (5, 3, 2))])
+def test_encode_field_bit_exact(kind, dims, rate):
+    f = make_field(kind, dims, 5)
+    want_bits, want_min, want_max = oracle.encode_volume(f, rate)
+    bits, bmin, bmax = pkg().encode_field(to_dev(f), rate)
+    torch().cuda.synchronize()
+    assert np.array_equal(bits.cpu().numpy().view(np.uint64), want_bits)
+    assert np.array_equal(bmin.cpu().numpy(), want_min)
+    assert np.array_equal(bmax.cpu().numpy(), want_max)
+
+
+def test_gpu_generators_match_numpy():
+    import synth.gpu as sg
+    sg.build()
+    for dims, origin, seed in (((40, 24, 20), (0, 0, 0), 1), ((33, 17, 9), (100, 260, 31), 9)):
+        want = fields.gradient_noise(*dims, seed, origin=origin)
+        got = sg.gradient_noise(*dims, seed, origin=origin).cpu().numpy()
+        assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+    want = fields.sphere_sdf(30, 26, 22, 9.5, center=(14.5, 12.0, 10.25), origin=(3, 4, 5))
+    got = sg.sphere_sdf(30, 26, 22, 9.5, center=(14.5, 12.0, 10.25), origin=(3, 4, 5)).cpu().numpy()
+    assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+
+
+# ---------------------------------------------------------------- extraction
+
+def check_surface(vol, bits, dims, rate, bmin, bmax, iso, mesh=None):
+    p = pkg()
+    if mesh is None:
+        mesh = vol.extract(iso)
+    ref = oracle.extract(bits, dims, rate, bmin, bmax, iso)
+    assert mesh.num_triangles == ref["num_triangles"]
+    act = vol.debug("active_ids")
+    assert np.array_equal(act, np.nonzero(ref["active"])[0].astype(np.uint32))
+    mask = vol.debug("active_mask")
+    bitsv = np.unpackbits(mask.view(np.uint8), bitorder="little")[:len(ref["active"])].astype(bool)
+    assert np.array_equal(bitsv, ref["active"])
+    cases = vol.debug("cell_cases").reshape(-1, 64)
+    comp = ref["complete"]
+    assert np.array_equal(cases[comp], ref["cases"][comp])
+    assert np.array_equal(vol.debug("block_tris"), ref["block_tri"])
+    assert np.array_equal(vol.debug("block_offsets"), ref["block_off"])
+    assert mesh.stats["n_occupied"] == int((ref["block_tri"] > 0).sum())
+    assert mesh.stats["n_active"] == len(act)
+    if len(act):
+        got_blocks = vol.read_blocks(act)
+        assert np.array_equal(got_blocks.view(np.uint32), oracle.decode_blocks(bits, rate, act).view(np.uint32))
+    if ref["num_triangles"]:
+        edges = vol.debug("edge_ids").reshape(-1, 3)
+        assert np.array_equal(edges, ref["edge_ids"])
+        v = mesh.vertices.cpu().numpy().reshape(-1, 3, 4)
+        err = np.abs(v[:, :, :3].astype(np.float64) - ref["local_pos"]).max()
+        assert err < POS_TOL, err
+        assert np.array_equal(v[:, :, 3].view(np.uint32), np.repeat(ref["tri_block"][:, None], 3, axis=1))
+        assert (v[:, :, :3] >= 0).all() and (v[:, :, :3] <= 4).all()
+    mesh.release()
+    return ref
+
+
+EXTRACT_CASES = [("sphere", (64, 64, 64), 16), ("noise", (37, 21, 14), 8), ("random", (13, 9, 6), 4),
+                 ("noise", (33, 20, 17), 12), ("random", (5, 5, 5), 3), ("random", (2, 3, 5), 8),
+                 ("noise", (4, 4, 4), 2), ("random", (3, 2, 2), 16), ("sphere", (33, 2, 9), 8),
+                 ("random", (1, 1, 1), 8), ("special", (18, 10, 9), 16), ("checker", (11, 9, 7), 8)]
+
+
+@pytest.mark.parametrize("kind,dims,rate", EXTRACT_CASES)
+def test_extract_matches_oracle(kind, dims, rate):
+    f = make_field(kind, dims, 7)
+    bits, bmin, bmax = oracle.encode_volume(f, rate)
+    d = oracle.decode_volume(bits, dims, rate)
+    isos = [0.0, float(np.median(d)), float(np.quantile(d, 0.2)), float(d.min()), float(d.max()), 1.0, -1e9, 1e9]
+    vol = pkg().Volume(bits, dims, rate, bmin, bmax, debug=True)
+    try:
+        for iso in isos:
+            check_surface(vol, bits, dims, rate, bmin, bmax, iso)
+    finally:
+        vol.release()
+
+
+def test_sphere64_closed_surface_on_gpu():
+    # the 64^3 sphere distance field at 16 bits/value: watertight, genus 0
+    f = fields.sphere_sdf(64, 64, 64, 20.0)
+    bits, bmin, bmax = oracle.encode_volume(f, 16)
+    vol = pkg().Volume(bits, (64, 64, 64), 16, bmin, bmax, debug=True)
+    try:
+        mesh = vol.extract(0.0)
+        e = vol.debug("edge_ids").reshape(-1, 3)
+        und = {}
+        for t in e:
+            for i in range(3):
+                a, b = int(t[i]), int(t[(i + 1) % 3])
+                und[(a, b)] = und.get((a, b), 0) + 1
+        assert all(k == 1 and und.get((b, a)) == 1 for (a, b), k in und.items())
+        V = len(set(e.ravel().tolist()))
+        assert V - len(und) // 2 + len(e) == 2
+        mesh.release()
+    finally:
+        vol.release()
+
+
+@pytest.mark.parametrize("kind", ["random", "up", "down"])
+def test_cache_matches_algorithm1(kind):
+    dims, rate = (48, 40, 36), 8
+    f = make_field("noise", dims, 11)
+    bits, bmin, bmax = oracle.encode_volume(f, rate)
+    d = oracle.decode_volume(bits, dims, rate)
+    nb = bits.shape[0]
+    frac = 0.02
+    vol = pkg().Volume(bits, dims, rate, bmin, bmax, debug=True, initial_cache_fraction=frac)
+    cache = oracle.LRUCache(nb, int(np.ceil(frac * nb)), nb)
+    lo, hi = np.quantile(d, [0.05, 0.95])
+    rng = np.random.default_rng(21)
+    if kind == "random":
+        isos = rng.uniform(lo, hi, 70)
+    elif kind == "up":
+        isos = np.linspace(lo, hi, 65)
+    else:
+        isos = np.linspace(hi, lo, 65)
+    nbd = oracle.block_dims(dims)
+    try:
+        for iso in isos.astype(np.float32):
+            mesh = vol.extract(float(iso))
+            act = oracle.active_blocks(bmin, bmax, nbd, float(iso))
+            I_new, _ = cache.update(act)
+            assert np.array_equal(vol.debug("new_ids"), I_new.astype(np.uint32))
+            assert mesh.stats["n_slots"] == cache.num_slots
+            assert np.array_equal(vol.debug("slot_of_block"), cache.I_slot.astype(np.int32))
+            assert np.array_equal(vol.debug("block_of_slot"), cache.S_block.astype(np.int32))
+            assert np.array_equal(vol.debug("slot_last_use"), cache.last_use().astype(np.uint32))
+            mesh.release()
+        # the surface is still exact after all the evictions
+        check_surface(vol, bits, dims, rate, bmin, bmax, float(np.median(d)))
+    finally:
+        vol.release()
+
+
+def test_budget_exceeded_then_recovers():
+    p = pkg()
+    dims, rate = (40, 40, 40), 8
+    f = make_field("noise", dims, 2)
+    bits, bmin, bmax = oracle.encode_volume(f, rate)
+    d = oracle.decode_volume(bits, dims, rate)
+    vol = p.Volume(bits, dims, rate, bmin, bmax, debug=True, cache_budget_bytes=40 * 256)
+    try:
+        with pytest.raises(p.IsoError) as e:
+            vol.extract(float(np.median(d)))
+        assert e.value.code == p.ISO_ERR_BUDGET
+        # a surface whose active set fits still comes out exact
+        iso = float(d.max()) - 1e-3 * float(d.max() - d.min())
+        ref = oracle.extract(bits, dims, rate, bmin, bmax, iso)
+        if ref["active"].sum() <= 40:
+            check_surface(vol, bits, dims, rate, bmin, bmax, iso)
+    finally:
+        vol.release()
+
+
+def test_extract_into_capacity_and_rerun():
+    p = pkg()
+    t = torch()
+    dims, rate = (32, 32, 32), 8
+    f = fields.gradient_noise(*dims, 3, octaves=3, base_period=8)
+    bits, bmin, bmax = oracle.encode_volume(f, rate)
+    ref = oracle.extract(bits, dims, rate, bmin, bmax, 0.0)
+    T = ref["num_triangles"]
+    assert T > 2 * bits.shape[0] + 4096        # larger than the library's first guess
+    vol = p.Volume(bits, dims, rate, bmin, bmax)
+    try:
+        mesh = vol.extract(0.0)                # first guess too small: the triangle stage reruns
+        assert mesh.stats["reruns"] == 1 and mesh.num_triangles == T
+        v = mesh.vertices.cpu().numpy().reshape(-1, 3, 4)
+        assert np.abs(v[:, :, :3] - ref["local_pos"]).max() < POS_TOL
+        mesh.release()
+        small = t.zeros((100, 3, 4), dtype=t.float32, device="cuda")
+        with pytest.raises(p.IsoError) as e:
+            vol.extract_into(0.0, small)
+        assert e.value.code == p.ISO_ERR_CAPACITY
+        st = vol.extract_into(0.0, small, check=False)
+        assert st["num_triangles"] == T
+        w = small.cpu().numpy()
+        assert np.abs(w[:, :, :3] - ref["local_pos"][:100]).max() < POS_TOL
+        big = t.zeros((T, 3, 4), dtype=t.float32, device="cuda")
+        st = vol.extract_into(0.0, big)
+        assert st["num_triangles"] == T and st["n_new"] == 0   # all hits the second time
+        assert np.abs(big.cpu().numpy()[:, :, :3] - ref["local_pos"]).max() < POS_TOL
+    finally:
+        vol.release()
+
+
+def test_cache_reset_and_side_stream():
+    p = pkg()
+    t = torch()
+    dims, rate = (30, 26, 22), 8
+    f = make_field("noise", dims, 4)
+    bits, bmin, bmax = oracle.encode_volume(f, rate)
+    s = t.cuda.Stream()
+    with t.cuda.stream(s):
+        vol = p.Volume(bits, dims, rate, bmin, bmax, debug=True)
+        try:
+            m = vol.extract(0.1)
+            assert m.stats["n_new"] == m.stats["n_active"] > 0
+            m.release()
+            m = vol.extract(0.1)
+            assert m.stats["n_new"] == 0
+            m.release()
+            vol.cache_reset()
+            m = vol.extract(0.1)
+            assert m.stats["n_new"] == m.stats["n_active"]
+            m.release()
+            check_surface(vol, bits, dims, rate, bmin, bmax, 0.1)
+        finally:
+            vol.release()
+
+
+def test_invalid_arguments():
+    p = pkg()
+    dims, rate = (8, 8, 8), 4
+    bits, bmin, bmax = oracle.encode_volume(make_field("noise", dims), rate)
+    vol = p.Volume(bits, dims, rate, bmin, bmax)
+    try:
+        for bad in (float("nan"), float("inf"), -float("inf")):
+            with pytest.raises(p.IsoError) as e:
+                vol.extract(bad)
+            assert e.value.code == p.ISO_ERR_INVALID_ARG
+    finally:
+        vol.release()
+    with pytest.raises(p.IsoError):
+        p.Volume(bits, dims, 0, bmin, bmax)
+    with pytest.raises(p.IsoError):
+        p.Volume(bits[:-1], dims, rate, bmin, bmax)
