@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--dims", type=int, default=512,
+                    help="cube edge of the noise volume (default 512; smaller sizes are for profiling captures)")
     return ap.parse_args()
 
 
@@ -401,7 +403,11 @@ def run_ours(args):
 
 
 def main():
+    global DIMS, WORKLOAD
     args = parse()
+    if args.dims != 512:
+        DIMS = (args.dims,) * 3
+        WORKLOAD = WORKLOAD.replace("noise512: 512^3", f"noise{args.dims}: {args.dims}^3")
     if args.impl == "reference":
         run_reference(args)
     else:
