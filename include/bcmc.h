@@ -186,6 +186,32 @@ int iso_encode_field(const float *d_field, uint32_t nx, uint32_t ny, uint32_t nz
 int iso_decode_blocks(const uint64_t *d_bits, uint32_t rate_bits, const uint32_t *d_ids, uint64_t n,
                       float *d_out, void *stream);
 
+/* Active-block selection without any allocation.  The paper has no
+ * counterpart: this exists for callers that cannot allocate device memory
+ * -- code running while its stream is captured into a CUDA graph, plug-ins
+ * inside an application whose allocator already owns the device memory,
+ * and latency-critical loops that must not meet an allocation's implicit
+ * synchronisation.
+ * It performs the range test of the cull stage (a block is active when
+ * lo < iso <= hi for the min/max of block_min/block_max over its 3x3x3
+ * block neighbourhood) and writes the active block ids in ascending order,
+ * like the ids iso_extract selects for the same ranges.
+ *   d_bmin, d_bmax  device, nb floats each (ranges of the decoded samples)
+ *   d_ids           device, room for `capacity` ids; ids past it are dropped
+ *   d_count         device uint32: the number of active blocks (may exceed
+ *                   capacity), or 0xFFFFFFFF if a device-side wait timed out
+ * Its scratch is a fixed file-scope device array of about 256 KiB, held by
+ * every GPU that loads the library until the process exits; volumes of
+ * more than 2^26 blocks (2^32 samples) are refused with
+ * ISO_ERR_INVALID_ARG.  The first call on a device looks the array's
+ * address up with that device current: make that first call before any
+ * stream capture.  All calls share the array and it keeps the previous
+ * call's contents; each call clears what it needs, so calls that overlap
+ * on the GPU (different streams at once) race and must be avoided.  The
+ * work is queued on `stream`; the call does not block. */
+int iso_active_blocks_static(const float *d_bmin, const float *d_bmax, uint32_t nx, uint32_t ny, uint32_t nz,
+                             float isovalue, uint32_t *d_ids, uint64_t capacity, uint32_t *d_count, void *stream);
+
 /* ---- debug and parity access (volumes loaded with ISO_DEBUG) ---------
  * Copies a per-stage array of the LAST extraction into host memory.
  * `bytes` is the size of host_dst; *count receives the number of elements

@@ -87,6 +87,7 @@ def lib():
             "iso_debug_get": (i32, [P, i32, P, sz, ctypes.POINTER(u64)]),
             "iso_debug_read_blocks": (i32, [P, P, u64, P]),
             "iso_set_profiling": (i32, [P, i32]),
+            "iso_active_blocks_static": (i32, [P, P, u32, u32, u32, ctypes.c_float, P, u64, P, P]),
             "iso_stage_times": (i32, [P, ctypes.POINTER(ctypes.c_float), i32]),
         }
         for name, (res, args) in sig.items():
@@ -283,6 +284,28 @@ def encode_field(field, rate, stream=None):
     _check(lib().iso_encode_field(_ptr(field), nx, ny, nz, rate, _ptr(bits), _ptr(bmin), _ptr(bmax),
                                   stream if stream is not None else _current_stream()), "iso_encode_field")
     return bits, bmin, bmax
+
+
+def active_blocks_static(bmin, bmax, dims, iso, ids=None, count=None, stream=None):
+    """Active block ids for `iso` from device ranges, through the entry point
+    that allocates nothing (its scratch is a fixed device array inside the
+    library).  For callers that cannot allocate device memory, `ids` (CUDA
+    int32 tensor with room for every block) and `count` (CUDA int32, one
+    element) may be passed in; when omitted they are made here by torch,
+    outside the library call.  Returns (ids, count) tensors; count holds the
+    number of active blocks."""
+    import torch
+    nx, ny, nz = dims
+    nb = int(np.prod(block_dims(dims)))
+    if ids is None:
+        ids = torch.empty(max(nb, 1), dtype=torch.int32, device=bmin.device)
+    if count is None:
+        count = torch.empty(1, dtype=torch.int32, device=bmin.device)
+    _check(lib().iso_active_blocks_static(_ptr(bmin), _ptr(bmax), nx, ny, nz, ctypes.c_float(iso), _ptr(ids),
+                                          ids.numel(), _ptr(count),
+                                          stream if stream is not None else _current_stream()),
+           "iso_active_blocks_static")
+    return ids, count
 
 
 def decode_blocks(bits, rate, ids, stream=None):
