@@ -31,7 +31,7 @@ DBG = {
     "active_ids": (1, np.uint32), "new_ids": (2, np.uint32), "slot_of_block": (3, np.int32),
     "block_of_slot": (4, np.int32), "slot_last_use": (5, np.uint32), "active_mask": (6, np.uint32),
     "cell_cases": (7, np.uint8), "block_tris": (8, np.uint32), "block_offsets": (9, np.uint64),
-    "edge_ids": (10, np.uint64),
+    "edge_ids": (10, np.uint64), "candidates": (11, np.uint32),
 }
 
 

@@ -26,14 +26,14 @@ struct iso_volume {
     // owned device allocations
     uint64_t *bits = nullptr;
     float *bmin = nullptr, *bmax = nullptr;
-    float2 *hull = nullptr;
+    float2 *hull = nullptr, *hull8 = nullptr;
     uint8_t *tables = nullptr;
     unsigned long long dbg_edges_cap = 0;   // in vertices
     bool profiling = false;
     cudaEvent_t ev[ISO_NUM_STAGES + 1] = {};
     float stage_ms[ISO_NUM_STAGES] = {};
     unsigned long long last_tris = 0;
-    uint32_t last_n_active = 0, last_n_new = 0, last_slots = 0;
+    uint32_t last_n_active = 0, last_n_new = 0, last_n_cand = 0, last_slots = 0;
 };
 
 namespace {
@@ -75,9 +75,9 @@ int free_volume(iso_volume *v) {
     cudaSetDevice(v->device);
     if (v->stream) cudaStreamSynchronize(v->stream);
     DevState &s = v->s;
-    void *ptrs[] = {v->bits, v->bmin, v->bmax, v->hull, v->tables, s.mactive, s.iactive, s.inew, s.islot, s.slast,
-                    s.sblock, s.lbuf[0], s.lbuf[1], s.newslot, s.slots, s.desc_cull, s.desc_lru_a, s.desc_lru_b,
-                    s.desc_mc, s.ctl, s.dbg_cases, s.dbg_btri, s.dbg_boff, s.dbg_edges};
+    void *ptrs[] = {v->bits, v->bmin, v->bmax, v->hull, v->hull8, v->tables, s.mactive, s.iactive, s.inew, s.icand,
+                    s.islot, s.slast, s.sblock, s.lbuf[0], s.lbuf[1], s.newslot, s.slots, s.desc_cull, s.desc_cand,
+                    s.desc_lru_a, s.desc_lru_b, s.desc_mc, s.ctl, s.dbg_cases, s.dbg_btri, s.dbg_boff, s.dbg_edges};
     for (void *p : ptrs) dfree(p);
     if (v->host_ctl) cudaFreeHost(v->host_ctl);
     for (cudaEvent_t &e : v->ev)
@@ -195,6 +195,7 @@ int run(iso_volume *v, float iso, float4 *out, unsigned long long cap_tris) {
     v->last_tris = v->host_ctl->n_tri;
     v->last_n_active = v->host_ctl->n_active;
     v->last_n_new = v->host_ctl->n_new;
+    v->last_n_cand = v->host_ctl->n_cand;
     v->last_slots = v->host_ctl->S;
     return status_to_error(v, v->host_ctl->status);
 }
@@ -282,15 +283,17 @@ int iso_load_volume(iso_volume **out, const void *compressed, size_t compressed_
     const uint32_t nwords = (g.nb + 31) / 32;
     v->n_cull_desc = (g.nb + kScanTile - 1) / kScanTile;
     v->n_lru_desc = (v->cap + kScanTile - 1) / kScanTile;
-    const uint32_t n_mc_desc = (g.nb + kMcTileBlocks - 1) / kMcTileBlocks;
+    const uint32_t n_mc_desc = (g.nb + kMcTileBlocks - 1) / kMcTileBlocks * kMcWarpTiles;
     TRY(dalloc(&v->bits, words));
     TRY(dalloc(&v->bmin, g.nb));
     TRY(dalloc(&v->bmax, g.nb));
     TRY(dalloc(&v->hull, g.nb));
+    TRY(dalloc(&v->hull8, g.nb));
     TRY(dalloc(&v->tables, 256 + 256 * 16));
     TRY(dalloc(&s.mactive, nwords));
     TRY(dalloc(&s.iactive, g.nb));
     TRY(dalloc(&s.inew, g.nb));
+    TRY(dalloc(&s.icand, g.nb));
     TRY(dalloc(&s.islot, g.nb));
     TRY(dalloc(&s.slast, v->cap));
     TRY(dalloc(&s.sblock, v->cap));
@@ -299,6 +302,7 @@ int iso_load_volume(iso_volume **out, const void *compressed, size_t compressed_
     TRY(dalloc(&s.newslot, v->cap));
     TRY(dalloc(&s.slots, (size_t)v->cap * 64));
     TRY(dalloc(&s.desc_cull, v->n_cull_desc));
+    TRY(dalloc(&s.desc_cand, v->n_cull_desc));
     TRY(dalloc(&s.desc_lru_a, v->n_lru_desc));
     TRY(dalloc(&s.desc_lru_b, v->n_lru_desc));
     TRY(dalloc(&s.desc_mc, n_mc_desc));
@@ -316,6 +320,7 @@ int iso_load_volume(iso_volume **out, const void *compressed, size_t compressed_
     }
     s.bits = v->bits;
     s.hull = v->hull;
+    s.hull8 = v->hull8;
     s.tables = v->tables;
 
     McTables t;
@@ -345,6 +350,7 @@ int iso_load_volume(iso_volume **out, const void *compressed, size_t compressed_
     // device-side timeout only ever indexes inside the volume and the cache
     TRYC(cudaMemsetAsync(s.iactive, 0, (size_t)g.nb * 4, st));
     TRYC(cudaMemsetAsync(s.inew, 0, (size_t)g.nb * 4, st));
+    TRYC(cudaMemsetAsync(s.icand, 0, (size_t)g.nb * 4, st));
     TRYC(cudaMemsetAsync(s.newslot, 0, (size_t)v->cap * 4, st));
     TRYC(cudaMemsetAsync(s.lbuf[0], 0, (size_t)v->cap * 4, st));
     TRYC(cudaMemsetAsync(s.lbuf[1], 0, (size_t)v->cap * 4, st));
@@ -353,7 +359,7 @@ int iso_load_volume(iso_volume **out, const void *compressed, size_t compressed_
     c0.cap = v->cap;
     *v->host_ctl = c0;
     TRYC(cudaMemcpyAsync(s.ctl, v->host_ctl, sizeof(Ctl), cudaMemcpyHostToDevice, st));
-    launch_hull(v->bmin, v->bmax, v->hull, g, st);
+    launch_hull(v->bmin, v->bmax, v->hull, v->hull8, g, st);
     TRYC(cudaGetLastError());
     TRYC(cudaStreamSynchronize(st));
     int sms = 0;
@@ -491,9 +497,10 @@ int iso_debug_get(iso_volume *v, int which, void *host_dst, size_t bytes, uint64
         case ISO_DBG_BLOCK_OF_SLOT: src = v->s.sblock; n = v->last_slots; elem = 4; break;
         case ISO_DBG_SLOT_LAST_USE: src = v->s.slast; n = v->last_slots; elem = 4; break;
         case ISO_DBG_ACTIVE_MASK: src = v->s.mactive; n = (v->g.nb + 31) / 32; elem = 4; break;
-        case ISO_DBG_CELL_CASES: if (!dbg) return ISO_ERR_INVALID_ARG; src = v->s.dbg_cases; n = 64ull * v->last_n_active; elem = 1; break;
-        case ISO_DBG_BLOCK_TRIS: if (!dbg) return ISO_ERR_INVALID_ARG; src = v->s.dbg_btri; n = v->last_n_active; elem = 4; break;
-        case ISO_DBG_BLOCK_OFFSETS: if (!dbg) return ISO_ERR_INVALID_ARG; src = v->s.dbg_boff; n = v->last_n_active; elem = 8; break;
+        case ISO_DBG_CELL_CASES: if (!dbg) return ISO_ERR_INVALID_ARG; src = v->s.dbg_cases; n = 64ull * v->last_n_cand; elem = 1; break;
+        case ISO_DBG_BLOCK_TRIS: if (!dbg) return ISO_ERR_INVALID_ARG; src = v->s.dbg_btri; n = v->last_n_cand; elem = 4; break;
+        case ISO_DBG_BLOCK_OFFSETS: if (!dbg) return ISO_ERR_INVALID_ARG; src = v->s.dbg_boff; n = v->last_n_cand; elem = 8; break;
+        case ISO_DBG_CANDIDATES: src = v->s.icand; n = v->last_n_cand; elem = 4; break;
         case ISO_DBG_EDGE_IDS:
             if (!dbg) return ISO_ERR_INVALID_ARG;
             src = v->s.dbg_edges;

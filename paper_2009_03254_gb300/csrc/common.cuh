@@ -32,6 +32,7 @@ struct Ctl {
     uint32_t epoch;           // extraction count; S_last values are epochs
     uint32_t n_active;        // |I_active|
     uint32_t n_new;           // |I_new|
+    uint32_t n_cand;          // |I_cand|
     uint32_t n_assign;        // new blocks given a slot (n_new, or 0 on budget failure)
     uint32_t S;               // slots in the LRU
     uint32_t u;               // slots [0,u) have been used; [u,S) never
@@ -43,7 +44,7 @@ struct Ctl {
     uint32_t keep_base;       // length of the surviving part of the used list
     uint32_t n_occ;           // occupied blocks
     uint32_t status;          // Status bits
-    uint32_t mc_tiles;        // tiles the triangle kernel used (descriptors to clear)
+    uint32_t mc_tiles;        // look-back descriptors the triangle kernel used (to clear)
     uint32_t ctr[kNumCtr];    // dynamic tile counters
     unsigned long long n_tri; // triangles of the surface
     unsigned long long tri_cap; // output capacity in triangles

@@ -7,8 +7,8 @@
 //           assign, evict) over the used-slot list
 //   lru_b   append this epoch's slots to the list (most recent last)
 //   decode  Section 4.2.1: decode each new block into its slot
-//   mc      Sections 4.3-4.5: halo staging, classification, per-block
-//           counts, single-pass prefix over blocks, vertex output
+//   mc      Sections 4.3-4.5 (mc.cu): halo staging, classification,
+//           per-block counts, single-pass prefix over blocks, vertices
 //
 // Sizes that only the device knows (n_active, n_new, ...) never come back
 // to the host between kernels: the kernels are persistent and take their
@@ -32,7 +32,10 @@ __global__ void __launch_bounds__(kThreads) prep_kernel(DevState s, uint32_t n_c
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
     for (uint32_t i = tid; i < n_mc_desc; i += stride) s.desc_mc[i] = 0;
     if (!mc_only) {
-        for (uint32_t i = tid; i < n_cull_desc; i += stride) s.desc_cull[i] = 0;
+        for (uint32_t i = tid; i < n_cull_desc; i += stride) {
+            s.desc_cull[i] = 0;
+            s.desc_cand[i] = 0;
+        }
         for (uint32_t i = tid; i < n_lru_desc; i += stride) {
             s.desc_lru_a[i] = 0;
             s.desc_lru_b[i] = 0;
@@ -43,6 +46,7 @@ __global__ void __launch_bounds__(kThreads) prep_kernel(DevState s, uint32_t n_c
             c->epoch += 1;
             c->n_active = 0;
             c->n_new = 0;
+            c->n_cand = 0;
             c->n_assign = 0;
             c->status = 0;
             for (int k = 0; k < kNumCtr; k++) c->ctr[k] = 0;
@@ -93,10 +97,13 @@ __device__ __forceinline__ uint32_t scan_tile_counts(TileScan &ts) {
 // That holds exactly when lo < iso <= hi for the min/max taken over the
 // whole 3x3x3 block neighbourhood, which the loader precomputes (`hull`).
 // Active blocks that have a slot are cache hits (slot stamped with the
-// epoch: "reset the age"); the others are new.
+// epoch: "reset the age"); the others are new.  Active blocks whose
+// 2x2x2 +group range (`hull8`) also contains iso are the candidates the
+// triangle stage visits; I_cand holds their positions in I_active.
 
 __global__ void __launch_bounds__(kThreads) cull_kernel(DevState s, Geom g, float iso, uint32_t ntiles) {
     __shared__ TileScan ts;
+    __shared__ TileScan tc;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t epoch = s.ctl->epoch;
     const uint32_t lt = (1u << lane) - 1u;
@@ -105,15 +112,17 @@ __global__ void __launch_bounds__(kThreads) cull_kernel(DevState s, Geom g, floa
         __syncthreads();
         const uint32_t tile = ts.tile;
         if (tile >= ntiles) break;
-        uint32_t act_bits[8], new_bits[8];
+        uint32_t act_bits[8], new_bits[8], cand_bits[8];
 #pragma unroll
         for (int r = 0; r < 8; r++) {
             const uint32_t b = tile * kScanTile + r * kThreads + threadIdx.x;
-            bool act = false, nw = false;
+            bool act = false, nw = false, cand = false;
             if (b < g.nb) {
                 const float2 h = __ldg(s.hull + b);
                 act = (h.x < iso) && (iso <= h.y);
                 if (act) {
+                    const float2 h8 = __ldg(s.hull8 + b);
+                    cand = (h8.x < iso) && (iso <= h8.y);
                     const int32_t sl = s.islot[b];
                     if (sl >= 0) s.slast[sl] = epoch;
                     else nw = true;
@@ -121,8 +130,10 @@ __global__ void __launch_bounds__(kThreads) cull_kernel(DevState s, Geom g, floa
             }
             act_bits[r] = __ballot_sync(0xffffffffu, act);
             new_bits[r] = __ballot_sync(0xffffffffu, nw);
+            cand_bits[r] = __ballot_sync(0xffffffffu, cand);
             if (lane == 0) {
                 ts.cnt[r][warp] = ((uint32_t)__popc(act_bits[r]) << 16) | (uint32_t)__popc(new_bits[r]);
+                tc.cnt[r][warp] = (uint32_t)__popc(cand_bits[r]);
                 const uint32_t first = tile * kScanTile + r * kThreads + warp * 32;
                 if (first < g.nb) s.mactive[first >> 5] = act_bits[r];
             }
@@ -130,24 +141,33 @@ __global__ void __launch_bounds__(kThreads) cull_kernel(DevState s, Geom g, floa
         __syncthreads();
         if (warp == 0) {
             const uint32_t tot = scan_tile_counts(ts);
+            const uint32_t totc = scan_tile_counts(tc);
             const unsigned long long agg = ((unsigned long long)(tot >> 16) << 31) | (tot & 0xFFFFu);
             const unsigned long long excl = lookback_exclusive(s.desc_cull, tile, agg, &s.ctl->status);
+            const unsigned long long exclc = lookback_exclusive(s.desc_cand, tile, totc, &s.ctl->status);
             if (lane == 0) {
                 ts.excl = excl;
+                tc.excl = exclc;
                 if (tile == ntiles - 1) {
                     const unsigned long long incl = excl + agg;
                     s.ctl->n_active = (uint32_t)(incl >> 31);
                     s.ctl->n_new = (uint32_t)(incl & 0x7FFFFFFFu);
+                    s.ctl->n_cand = (uint32_t)(exclc + totc);
                 }
             }
         }
         __syncthreads();
         const uint32_t act_base = (uint32_t)(ts.excl >> 31), new_base = (uint32_t)(ts.excl & 0x7FFFFFFFu);
+        const uint32_t cand_base = (uint32_t)tc.excl;
 #pragma unroll
         for (int r = 0; r < 8; r++) {
             const uint32_t b = tile * kScanTile + r * kThreads + threadIdx.x;
             const uint32_t off = ts.cnt[r][warp];
-            if ((act_bits[r] >> lane) & 1u) s.iactive[act_base + (off >> 16) + __popc(act_bits[r] & lt)] = b;
+            if ((act_bits[r] >> lane) & 1u) {
+                const uint32_t ai = act_base + (off >> 16) + __popc(act_bits[r] & lt);
+                s.iactive[ai] = b;
+                if ((cand_bits[r] >> lane) & 1u) s.icand[cand_base + tc.cnt[r][warp] + __popc(cand_bits[r] & lt)] = ai;
+            }
             if ((new_bits[r] >> lane) & 1u) s.inew[new_base + (off & 0xFFFFu) + __popc(new_bits[r] & lt)] = b;
         }
         __syncthreads();
@@ -325,221 +345,16 @@ __global__ void __launch_bounds__(kThreads) decode_new_kernel(DevState s, Geom g
     }
 }
 
-// ================================================================ triangles (Sections 4.3-4.5)
-//
-// One tile = 32 consecutive entries of I_active, 8 warps.
-//  A  per block: look up its slot and its +x/+y/+z face, edge and corner
-//     neighbours.  A crossing cell needs all of them active (a crossing
-//     between two samples makes every block of its 2x2x2 block group
-//     active), so a block with an existing but inactive +neighbour has no
-//     crossing cell and is skipped: this is where the paper shrinks the
-//     block's extent back to 4.
-//  B  stage each block's 5x5x5 samples (own 64 + up to 61 halo) in shared
-//     memory.
-//  C  one warp per block, two cells per lane: case index, triangle count,
-//     block total.
-//  D  block totals -> tile total -> decoupled look-back over tiles: the
-//     prefix sum over per-block counts of Section 4.4 in one pass.
-//  E  per block: exclusive scan of the cell counts, then each lane writes
-//     whole float4 vertices so that a warp's 32 stores are contiguous.
-
-struct McSmem {
-    float halo[kMcTileBlocks][128];
-    int32_t nslot[kMcTileBlocks][8];
-    uint32_t bid[kMcTileBlocks];
-    uint8_t cases[kMcTileBlocks][64];
-    uint32_t btri[kMcTileBlocks];
-    uint32_t boff[kMcTileBlocks];
-    uint8_t tricell[kThreads / 32][320];
-    uint16_t celloff[kThreads / 32][64];
-    uint8_t num_tri[256];
-    uint8_t tri_edges[256][16];
-    unsigned long long tile_base;
-    uint32_t tile;
-};
-
-__device__ __forceinline__ int halo_index(int x, int y, int z) { return x + 5 * y + 25 * z; }
-
-__global__ void __launch_bounds__(kThreads) mc_kernel(DevState s, Geom g, float iso, float4 *__restrict__ out,
-                                                      int debug) {
-    __shared__ McSmem sm;
-    __shared__ uint32_t s_status;
-    Ctl *c = s.ctl;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i = threadIdx.x; i < 256; i += kThreads) sm.num_tri[i] = s.tables[i];
-    for (int i = threadIdx.x; i < 256 * 16; i += kThreads) (&sm.tri_edges[0][0])[i] = s.tables[256 + i];
-    if (threadIdx.x == 0) s_status = c->status;
-    __syncthreads();
-    const uint32_t n_active = c->n_active;
-    const uint32_t ntiles = (n_active + kMcTileBlocks - 1) / kMcTileBlocks;
-    const unsigned long long tri_cap = c->tri_cap;
-    const bool failed = (s_status & (kStatusBudget | kStatusTimeout)) != 0;   // same value in the whole block
-    if (blockIdx.x == 0 && threadIdx.x == 0) c->mc_tiles = failed ? 0u : ntiles;
-    if (failed) return;
-    const uint32_t slab = g.nbx * g.nby;
-    while (true) {
-        if (threadIdx.x == 0) sm.tile = atomicAdd(&c->ctr[kCtrMc], 1u);
-        __syncthreads();
-        const uint32_t tile = sm.tile;
-        if (tile >= ntiles) break;
-        const uint32_t base = tile * kMcTileBlocks;
-        const uint32_t nblk = min((uint32_t)kMcTileBlocks, n_active - base);
-
-        // ---- A: neighbours
-        if (threadIdx.x < nblk) {
-            const int t = threadIdx.x;
-            const uint32_t b = s.iactive[base + t];
-            const uint32_t bx = b % g.nbx, by = (b / g.nbx) % g.nby, bz = b / slab;
-            const bool ex = bx + 1 < g.nbx, ey = by + 1 < g.nby, ez = bz + 1 < g.nbz;
-            bool complete = true;
-            sm.nslot[t][0] = s.islot[b];
-#pragma unroll
-            for (int o = 1; o < 8; o++) {
-                int32_t sl = -1;
-                if ((!(o & 1) || ex) && (!(o & 2) || ey) && (!(o & 4) || ez)) {
-                    const uint32_t nb = b + ((o & 1) ? 1u : 0u) + ((o & 2) ? g.nbx : 0u) + ((o & 4) ? slab : 0u);
-                    if ((s.mactive[nb >> 5] >> (nb & 31)) & 1u) sl = s.islot[nb];
-                    else complete = false;
-                }
-                sm.nslot[t][o] = sl;
-            }
-            if (!complete) sm.nslot[t][0] = -2;
-            sm.bid[t] = b;
-        }
-        __syncthreads();
-
-        // ---- B: stage samples
-        for (uint32_t idx = threadIdx.x; idx < nblk * 125u; idx += kThreads) {
-            const uint32_t t = idx / 125u, h = idx - t * 125u;
-            const uint32_t hx = h % 5u, hy = (h / 5u) % 5u, hz = h / 25u;
-            const int o = (hx == 4) | ((hy == 4) << 1) | ((hz == 4) << 2);
-            const int32_t self = sm.nslot[t][0];
-            const int32_t sl = self == -2 ? -1 : sm.nslot[t][o];
-            float v = 0.0f;
-            if (sl >= 0) v = s.slots[(size_t)sl * 64 + (hx & 3u) + 4u * (hy & 3u) + 16u * (hz & 3u)];
-            sm.halo[t][h] = v;
-        }
-        __syncthreads();
-
-        // ---- C: classify and count
-        for (uint32_t t = warp; t < nblk; t += kThreads / 32) {
-            const uint32_t b = sm.bid[t];
-            const bool skip = sm.nslot[t][0] == -2;
-            const uint32_t bx = b % g.nbx, by = (b / g.nbx) % g.nby, bz = b / slab;
-            uint32_t cnt = 0;
-#pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const int cell = lane + 32 * h;
-                const int cx = cell & 3, cy = (cell >> 2) & 3, cz = cell >> 4;
-                const bool valid = !skip && 4 * bx + cx + 1 < g.nx && 4 * by + cy + 1 < g.ny && 4 * bz + cz + 1 < g.nz;
-                uint32_t cs = 0;
-                if (valid) {
-                    const float *hb = sm.halo[t];
-#pragma unroll
-                    for (int k = 0; k < 8; k++) {
-                        const float v = hb[halo_index(cx + (k & 1), cy + ((k >> 1) & 1), cz + (k >> 2))];
-                        cs |= (v < iso ? 1u : 0u) << k;
-                    }
-                }
-                sm.cases[t][cell] = (uint8_t)cs;
-                cnt += sm.num_tri[cs];
-                if (debug) s.dbg_cases[(size_t)(base + t) * 64 + cell] = (uint8_t)cs;
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-            if (lane == 0) sm.btri[t] = cnt;
-        }
-        __syncthreads();
-
-        // ---- D: prefix over blocks
-        if (warp == 0) {
-            const uint32_t mine = (uint32_t)lane < nblk ? sm.btri[lane] : 0u;
-            uint32_t incl = mine;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += t;
-            }
-            const uint32_t agg = __shfl_sync(0xffffffffu, incl, 31);
-            if ((uint32_t)lane < nblk) sm.boff[lane] = incl - mine;
-            const unsigned occ = __ballot_sync(0xffffffffu, mine > 0);
-            const unsigned long long excl = lookback_exclusive(s.desc_mc, tile, agg, &c->status);
-            if (lane == 0) {
-                sm.tile_base = excl;
-                if (tile == ntiles - 1) c->n_tri = excl + agg;
-                if (occ) atomicAdd(&c->n_occ, (uint32_t)__popc(occ));
-            }
-            if (debug && (uint32_t)lane < nblk) {
-                s.dbg_btri[base + lane] = mine;
-                s.dbg_boff[base + lane] = excl + (incl - mine);
-            }
-        }
-        __syncthreads();
-
-        // ---- E: vertices
-        for (uint32_t t = warp; t < nblk; t += kThreads / 32) {
-            const uint32_t tb = sm.btri[t];
-            if (tb == 0) continue;
-            const uint32_t b = sm.bid[t];
-            const uint32_t n0 = sm.num_tri[sm.cases[t][lane]], n1 = sm.num_tri[sm.cases[t][lane + 32]];
-            uint32_t i0 = n0, i1 = n1;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t a0 = __shfl_up_sync(0xffffffffu, i0, o), a1 = __shfl_up_sync(0xffffffffu, i1, o);
-                if (lane >= o) { i0 += a0; i1 += a1; }
-            }
-            const uint32_t tot0 = __shfl_sync(0xffffffffu, i0, 31);
-            const uint32_t o0 = i0 - n0, o1 = tot0 + i1 - n1;
-            sm.celloff[warp][lane] = (uint16_t)o0;
-            sm.celloff[warp][lane + 32] = (uint16_t)o1;
-            for (uint32_t k = 0; k < n0; k++) sm.tricell[warp][o0 + k] = (uint8_t)lane;
-            for (uint32_t k = 0; k < n1; k++) sm.tricell[warp][o1 + k] = (uint8_t)(lane + 32);
-            __syncwarp();
-            const unsigned long long gbase = sm.tile_base + sm.boff[t];
-            const uint32_t bx = b % g.nbx, by = (b / g.nbx) % g.nby, bz = b / slab;
-            const float *hb = sm.halo[t];
-            const float wbits = __uint_as_float(b);
-            for (uint32_t v = lane; v < 3 * tb; v += 32) {
-                const uint32_t tri = v / 3u, j = v - 3u * tri;
-                const uint32_t cell = sm.tricell[warp][tri];
-                const uint32_t k = tri - sm.celloff[warp][cell];
-                const uint32_t e = sm.tri_edges[sm.cases[t][cell]][3 * k + j];
-                const int a = (int)(e >> 2), j0 = (int)(e & 1u), j1 = (int)((e >> 1) & 1u);
-                const int px = (int)(cell & 3u) + (a == 0 ? 0 : j0);
-                const int py = (int)((cell >> 2) & 3u) + (a == 0 ? j0 : (a == 1 ? 0 : j1));
-                const int pz = (int)(cell >> 4) + (a == 2 ? 0 : j1);
-                const float vlo = hb[halo_index(px, py, pz)];
-                const float vhi = hb[halo_index(px + (a == 0), py + (a == 1), pz + (a == 2))];
-                const float tt = __fdiv_rn(__fsub_rn(iso, vlo), __fsub_rn(vhi, vlo));
-                float4 p = make_float4((float)px, (float)py, (float)pz, wbits);
-                if (a == 0) p.x = __fadd_rn(p.x, tt);
-                else if (a == 1) p.y = __fadd_rn(p.y, tt);
-                else p.z = __fadd_rn(p.z, tt);
-                const unsigned long long gt = gbase + tri;
-                if (gt < tri_cap) {
-                    out[gt * 3 + j] = p;
-                    if (debug) {
-                        const unsigned long long vox = (unsigned long long)(4 * bx + px) +
-                            (unsigned long long)g.nx * ((unsigned long long)(4 * by + py) +
-                                                        (unsigned long long)g.ny * (unsigned long long)(4 * bz + pz));
-                        s.dbg_edges[gt * 3 + j] = 3ull * vox + (unsigned long long)a;
-                    }
-                }
-            }
-            __syncwarp();
-        }
-        __syncthreads();
-    }
-}
-
 // ================================================================ load-time and utility kernels
 
 // per block: min/max of the block ranges over its 3x3x3 block neighbourhood
-__global__ void hull_kernel(const float *__restrict__ bmin, const float *__restrict__ bmax, float2 *hull, Geom g) {
+// (hull) and over its 2x2x2 +group (hull8)
+__global__ void hull_kernel(const float *__restrict__ bmin, const float *__restrict__ bmax, float2 *hull,
+                            float2 *hull8, Geom g) {
     const uint32_t slab = g.nbx * g.nby;
     for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < g.nb; b += gridDim.x * blockDim.x) {
         const int bx = (int)(b % g.nbx), by = (int)((b / g.nbx) % g.nby), bz = (int)(b / slab);
-        float lo = bmin[b], hi = bmax[b];
+        float lo = bmin[b], hi = bmax[b], lo8 = lo, hi8 = hi;
         for (int dz = -1; dz <= 1; dz++) {
             const int z = bz + dz;
             if (z < 0 || z >= (int)g.nbz) continue;
@@ -552,10 +367,15 @@ __global__ void hull_kernel(const float *__restrict__ bmin, const float *__restr
                     const uint32_t n = (uint32_t)x + g.nbx * ((uint32_t)y + g.nby * (uint32_t)z);
                     lo = fminf(lo, bmin[n]);
                     hi = fmaxf(hi, bmax[n]);
+                    if (dx >= 0 && dy >= 0 && dz >= 0) {
+                        lo8 = fminf(lo8, bmin[n]);
+                        hi8 = fmaxf(hi8, bmax[n]);
+                    }
                 }
             }
         }
         hull[b] = make_float2(lo, hi);
+        hull8[b] = make_float2(lo8, hi8);
     }
 }
 
@@ -609,13 +429,10 @@ void launch_decode_new(const DevState &s, const Geom &g, int grid, cudaStream_t 
     decode_new_kernel<<<grid, kThreads, 0, st>>>(s, g);
 }
 
-void launch_mc(const DevState &s, const Geom &g, float iso, float4 *out, bool debug, int grid, cudaStream_t st) {
-    mc_kernel<<<grid, kThreads, 0, st>>>(s, g, iso, out, debug ? 1 : 0);
-}
-
-void launch_hull(const float *bmin, const float *bmax, float2 *hull, const Geom &g, cudaStream_t st) {
+void launch_hull(const float *bmin, const float *bmax, float2 *hull, float2 *hull8, const Geom &g,
+                 cudaStream_t st) {
     const uint32_t blocks = std::min<uint32_t>((g.nb + 255) / 256, 65535u * 4);
-    hull_kernel<<<blocks, 256, 0, st>>>(bmin, bmax, hull, g);
+    hull_kernel<<<blocks, 256, 0, st>>>(bmin, bmax, hull, hull8, g);
 }
 
 void launch_reset_cache(const DevState &s, cudaStream_t st) {
@@ -641,8 +458,7 @@ Grids compute_grids(int sm_count) {
     gr.lru_b = std::max(1, occ) * sm_count;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, decode_new_kernel, kThreads, 0);
     gr.decode = std::max(1, occ) * sm_count;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mc_kernel, kThreads, 0);
-    gr.mc = std::max(1, occ) * sm_count;
+    gr.mc = std::max(1, mc_occupancy()) * sm_count;
     gr.prep = 2 * sm_count;
     return gr;
 }

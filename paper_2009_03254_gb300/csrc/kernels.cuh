@@ -13,21 +13,23 @@ namespace bcmc {
 struct DevState {
     const uint64_t *bits;      // nb * rate words
     const float2 *hull;        // per block: min/max over its 3x3x3 block neighbourhood
+    const float2 *hull8;       // per block: min/max over its 2x2x2 +group
     uint32_t *mactive;         // M_active bitmask, ceil(nb/32) words
     uint32_t *iactive;         // I_active
     uint32_t *inew;            // I_new
+    uint32_t *icand;           // candidates: positions in I_active of blocks the triangle stage visits
     int32_t *islot;            // I_slot: block -> slot or -1
     uint32_t *slast;           // S_last: slot -> epoch of last use (0 = never)
     int32_t *sblock;           // S_block: slot -> block or -1
     uint32_t *lbuf[2];         // used-slot list, least recently used first (double buffered)
     uint32_t *newslot;         // slot given to I_new[r]
     float *slots;              // decoded blocks, 64 floats per slot
-    unsigned long long *desc_cull, *desc_lru_a, *desc_lru_b, *desc_mc;
+    unsigned long long *desc_cull, *desc_cand, *desc_lru_a, *desc_lru_b, *desc_mc;
     Ctl *ctl;
     const uint8_t *tables;     // num_tri[256] then tri_edges[256][16]
     // debug copies (null unless the volume was loaded with ISO_DEBUG)
-    uint8_t *dbg_cases;        // 64 per active block
-    uint32_t *dbg_btri;        // per active block
+    uint8_t *dbg_cases;        // 64 per candidate block
+    uint32_t *dbg_btri;        // per candidate block
     unsigned long long *dbg_boff;
     unsigned long long *dbg_edges;
 };
@@ -38,7 +40,8 @@ struct Grids {                 // CTAs per launch, from occupancy at load time
 
 constexpr int kThreads = 256;
 constexpr int kScanTile = 2048;          // entries per tile of the cull / cache scans
-constexpr int kMcTileBlocks = 32;        // active blocks per tile of the triangle kernel
+constexpr int kMcTileBlocks = 32;        // candidate blocks per tile of the triangle kernel (4 per warp)
+constexpr int kMcWarpTiles = 8;          // look-back descriptors per tile (one per warp)
 
 void launch_prep(const DevState &s, uint32_t n_cull_desc, uint32_t n_lru_desc, unsigned long long tri_cap,
                  bool mc_only, int grid, cudaStream_t st);
@@ -46,7 +49,8 @@ void launch_cull(const DevState &s, const Geom &g, float iso, int grid, cudaStre
 void launch_lru(const DevState &s, int grid_a, int grid_b, cudaStream_t st);
 void launch_decode_new(const DevState &s, const Geom &g, int grid, cudaStream_t st);
 void launch_mc(const DevState &s, const Geom &g, float iso, float4 *out, bool debug, int grid, cudaStream_t st);
-void launch_hull(const float *bmin, const float *bmax, float2 *hull, const Geom &g, cudaStream_t st);
+void launch_hull(const float *bmin, const float *bmax, float2 *hull, float2 *hull8, const Geom &g,
+                 cudaStream_t st);
 void launch_reset_cache(const DevState &s, cudaStream_t st);
 void launch_encode(const float *field, const Geom &g, uint64_t *bits, float *bmin, float *bmax, cudaStream_t st);
 void launch_decode_list(const uint64_t *bits, uint32_t rate, const uint32_t *ids, uint64_t n, float *out,
@@ -56,5 +60,7 @@ void launch_gather_slots(const float *slots, const int32_t *islot, const uint32_
 
 // occupancy-derived persistent grid sizes
 Grids compute_grids(int sm_count);
+int mc_occupancy();          // also raises the triangle kernel's dynamic shared-memory limit
+size_t mc_smem_bytes();
 
 }  // namespace bcmc

@@ -117,6 +117,23 @@ def test_gpu_generators_match_numpy():
 
 # ---------------------------------------------------------------- extraction
 
+def plus_group_candidates(bmin, bmax, dims, iso, active):
+    """Active blocks whose 2x2x2 +group (block and +x/+y/+z neighbours that
+    exist) has a range containing iso: the only blocks that can emit."""
+    nbx, nby, nbz = oracle.block_dims(dims)
+    lo = bmin.reshape(nbz, nby, nbx).astype(np.float64)
+    hi = bmax.reshape(nbz, nby, nbx).astype(np.float64)
+    lo8, hi8 = lo.copy(), hi.copy()
+    for dz in (0, 1):
+        for dy in (0, 1):
+            for dx in (0, 1):
+                sl = (slice(0, nbz - dz), slice(0, nby - dy), slice(0, nbx - dx))
+                sh = (slice(dz, nbz), slice(dy, nby), slice(dx, nbx))
+                lo8[sl] = np.minimum(lo8[sl], lo[sh])
+                hi8[sl] = np.maximum(hi8[sl], hi[sh])
+    return active & ((lo8 < iso) & (iso <= hi8)).ravel()
+
+
 def check_surface(vol, bits, dims, rate, bmin, bmax, iso, mesh=None):
     p = pkg()
     if mesh is None:
@@ -128,11 +145,18 @@ def check_surface(vol, bits, dims, rate, bmin, bmax, iso, mesh=None):
     mask = vol.debug("active_mask")
     bitsv = np.unpackbits(mask.view(np.uint8), bitorder="little")[:len(ref["active"])].astype(bool)
     assert np.array_equal(bitsv, ref["active"])
+    # the triangle stage visits exactly the candidates; every block the
+    # oracle finds occupied is one of them, and none of them needed an
+    # extent reset
+    cand = vol.debug("candidates").astype(np.int64)
+    want_cand = plus_group_candidates(bmin, bmax, dims, iso, ref["active"])
+    assert np.array_equal(act[cand], np.nonzero(want_cand)[0].astype(np.uint32))
+    assert set(ref["ids"][ref["block_tri"] > 0].tolist()) <= set(act[cand].tolist())
+    assert ref["complete"][cand].all()
     cases = vol.debug("cell_cases").reshape(-1, 64)
-    comp = ref["complete"]
-    assert np.array_equal(cases[comp], ref["cases"][comp])
-    assert np.array_equal(vol.debug("block_tris"), ref["block_tri"])
-    assert np.array_equal(vol.debug("block_offsets"), ref["block_off"])
+    assert np.array_equal(cases, ref["cases"][cand])
+    assert np.array_equal(vol.debug("block_tris"), ref["block_tri"][cand])
+    assert np.array_equal(vol.debug("block_offsets"), ref["block_off"][cand])
     assert mesh.stats["n_occupied"] == int((ref["block_tri"] > 0).sum())
     assert mesh.stats["n_active"] == len(act)
     if len(act):
