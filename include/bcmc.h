@@ -65,11 +65,13 @@ extern "C" {
 /* iso_options.flags */
 #define ISO_INPUT_ON_DEVICE 1u /* compressed/block_min/block_max are device pointers */
 #define ISO_DEBUG 2u           /* keep per-stage debug copies (see iso_debug_get) */
+#define ISO_NO_GRAPH 4u        /* launch each extraction's kernels one by one instead of
+                                  replaying the CUDA graph captured at the first extraction */
 
 typedef struct iso_volume iso_volume;
 
 typedef struct iso_options {
-    uint32_t flags;            /* ISO_INPUT_ON_DEVICE | ISO_DEBUG */
+    uint32_t flags;            /* ISO_INPUT_ON_DEVICE | ISO_DEBUG | ISO_NO_GRAPH */
     uint32_t reserved;
     void *stream;              /* cudaStream_t for all device work; NULL = default stream */
     double initial_cache_fraction; /* initial slots as a fraction of nb; <= 0 means 0.1 (Section 4.2) */

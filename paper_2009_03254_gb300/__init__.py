@@ -26,6 +26,7 @@ ISO_ERR_CAPACITY = 6
 
 ISO_INPUT_ON_DEVICE = 1
 ISO_DEBUG = 2
+ISO_NO_GRAPH = 4
 
 DBG = {
     "active_ids": (1, np.uint32), "new_ids": (2, np.uint32), "slot_of_block": (3, np.int32),
@@ -183,7 +184,7 @@ class Volume:
     """
 
     def __init__(self, bits, dims, rate, bmin, bmax, *, stream=None, debug=False, initial_cache_fraction=0.1,
-                 cache_budget_bytes=0):
+                 cache_budget_bytes=0, graph=True):
         self._h = None
         on_device = not isinstance(bits, np.ndarray) and bool(getattr(bits, "is_cuda", False))
         if not isinstance(bits, np.ndarray) and not on_device:       # CPU (e.g. pinned) torch tensors
@@ -196,7 +197,8 @@ class Volume:
         self.rate = int(rate)
         self.nb = int(np.prod(block_dims(self.dims)))
         opt = _Options()
-        opt.flags = (ISO_INPUT_ON_DEVICE if on_device else 0) | (ISO_DEBUG if debug else 0)
+        opt.flags = (ISO_INPUT_ON_DEVICE if on_device else 0) | (ISO_DEBUG if debug else 0) | \
+            (0 if graph else ISO_NO_GRAPH)
         opt.stream = stream if stream is not None else _current_stream()
         opt.initial_cache_fraction = float(initial_cache_fraction)
         opt.cache_budget_bytes = int(cache_budget_bytes)

@@ -23,6 +23,11 @@ struct iso_volume {
     uint32_t cap = 0;                 // physical slots
     uint32_t n_cull_desc = 0, n_lru_desc = 0;
     Ctl *host_ctl = nullptr;          // pinned mirror for the one readback
+    Params *host_params = nullptr;    // pinned: this extraction's isovalue, output and capacity
+    cudaStream_t capture_stream = nullptr;
+    cudaGraph_t graph = nullptr;      // one extraction: params copy, six kernels, count readback
+    cudaGraphExec_t gexec = nullptr;
+    bool use_graph = true;
     // owned device allocations
     uint64_t *bits = nullptr;
     float *bmin = nullptr, *bmax = nullptr;
@@ -80,6 +85,10 @@ int free_volume(iso_volume *v) {
                     s.desc_lru_a, s.desc_lru_b, s.desc_mc, s.ctl, s.dbg_cases, s.dbg_btri, s.dbg_boff, s.dbg_edges};
     for (void *p : ptrs) dfree(p);
     if (v->host_ctl) cudaFreeHost(v->host_ctl);
+    if (v->host_params) cudaFreeHost(v->host_params);
+    if (v->gexec) cudaGraphExecDestroy(v->gexec);
+    if (v->graph) cudaGraphDestroy(v->graph);
+    if (v->capture_stream) cudaStreamDestroy(v->capture_stream);
     for (cudaEvent_t &e : v->ev)
         if (e) cudaEventDestroy(e);
     cudaSetDevice(dev);
@@ -112,22 +121,54 @@ int status_to_error(iso_volume *v, uint32_t st) {
     return ISO_OK;
 }
 
-// queue the whole pipeline; the caller reads the control block afterwards
-int enqueue_extract(iso_volume *v, float iso, float4 *out, unsigned long long cap_tris) {
+// Queue one extraction on `st`: copy the parameters in, run the stages,
+// copy the control block out.  With mc_only, only the triangle stage runs
+// again (after a larger output buffer was supplied).  Events between the
+// stages are recorded when profiling (never inside a captured graph).
+int enqueue_pipeline(iso_volume *v, cudaStream_t st, bool mc_only, bool prof) {
     const bool debug = (v->flags & ISO_DEBUG) != 0;
-    const bool prof = v->profiling;
-    if (prof) cudaEventRecord(v->ev[0], v->stream);
-    launch_prep(v->s, v->n_cull_desc, v->n_lru_desc, cap_tris, false, v->grids.prep, v->stream);
-    if (prof) cudaEventRecord(v->ev[1], v->stream);
-    launch_cull(v->s, v->g, iso, v->grids.cull, v->stream);
-    if (prof) cudaEventRecord(v->ev[2], v->stream);
-    launch_lru(v->s, v->grids.lru_a, v->grids.lru_b, v->stream);
-    if (prof) cudaEventRecord(v->ev[3], v->stream);
-    launch_decode_new(v->s, v->g, v->grids.decode, v->stream);
-    if (prof) cudaEventRecord(v->ev[4], v->stream);
-    launch_mc(v->s, v->g, iso, out, debug, v->grids.mc, v->stream);
-    if (prof) cudaEventRecord(v->ev[5], v->stream);
+    CK(cudaMemcpyAsync(&v->s.ctl->params, v->host_params, sizeof(Params), cudaMemcpyHostToDevice, st));
+    if (prof) cudaEventRecord(v->ev[0], st);
+    launch_prep(v->s, v->n_cull_desc, v->n_lru_desc, mc_only, v->grids.prep, st);
+    if (prof) cudaEventRecord(v->ev[1], st);
+    if (!mc_only) {
+        launch_cull(v->s, v->g, v->grids.cull, st);
+        if (prof) cudaEventRecord(v->ev[2], st);
+        launch_lru(v->s, v->grids.lru_a, v->grids.lru_b, st);
+        if (prof) cudaEventRecord(v->ev[3], st);
+        launch_decode_new(v->s, v->g, v->grids.decode, st);
+        if (prof) cudaEventRecord(v->ev[4], st);
+    }
+    launch_mc(v->s, v->g, debug, v->grids.mc, st);
+    if (prof) cudaEventRecord(v->ev[5], st);
+    CK(cudaMemcpyAsync(v->host_ctl, v->s.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
     CK(cudaGetLastError());
+    return ISO_OK;
+}
+
+// Capture the extraction once per volume (on a private stream: the legacy
+// default stream cannot be captured); launches then go to the volume's
+// stream.  Every per-extraction input comes through Params, so the graph
+// never needs updating.
+int ensure_graph(iso_volume *v) {
+    if (v->gexec) return ISO_OK;
+    CK(cudaStreamCreateWithFlags(&v->capture_stream, cudaStreamNonBlocking));
+    CK(cudaStreamBeginCapture(v->capture_stream, cudaStreamCaptureModeThreadLocal));
+    const int rc = enqueue_pipeline(v, v->capture_stream, false, false);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(v->capture_stream, &g);
+    if (rc != ISO_OK || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        (void)cudaGetLastError();
+        return rc != ISO_OK ? rc : ISO_ERR_CUDA;
+    }
+    if (cudaGraphInstantiate(&v->gexec, g, 0) != cudaSuccess) {
+        cudaGraphDestroy(g);
+        v->gexec = nullptr;
+        (void)cudaGetLastError();
+        return ISO_ERR_CUDA;
+    }
+    v->graph = g;
     return ISO_OK;
 }
 
@@ -141,20 +182,6 @@ void collect_stage_times(iso_volume *v) {
         }
         v->stage_ms[k] = ms;
     }
-}
-
-int enqueue_mc_again(iso_volume *v, float iso, float4 *out, unsigned long long cap_tris) {
-    const bool debug = (v->flags & ISO_DEBUG) != 0;
-    launch_prep(v->s, v->n_cull_desc, v->n_lru_desc, cap_tris, true, v->grids.prep, v->stream);
-    launch_mc(v->s, v->g, iso, out, debug, v->grids.mc, v->stream);
-    CK(cudaGetLastError());
-    return ISO_OK;
-}
-
-int read_ctl(iso_volume *v) {
-    CK(cudaMemcpyAsync(v->host_ctl, v->s.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, v->stream));
-    CK(cudaStreamSynchronize(v->stream));
-    return ISO_OK;
 }
 
 void fill_stats(const iso_volume *v, iso_stats *st, uint32_t reruns) {
@@ -184,29 +211,26 @@ int ensure_debug_edges(iso_volume *v, unsigned long long tris) {
 
 // run the pipeline into `out` (capacity cap_tris); returns the error of
 // the run, with the control block mirrored on the host
-int run(iso_volume *v, float iso, float4 *out, unsigned long long cap_tris) {
+int run(iso_volume *v, float iso, float4 *out, unsigned long long cap_tris, bool mc_only) {
     int rc = ensure_debug_edges(v, cap_tris);
     if (rc) return rc;
-    rc = enqueue_extract(v, iso, out, cap_tris);
-    if (rc) return rc;
-    rc = read_ctl(v);
-    if (rc) return rc;
-    collect_stage_times(v);
-    v->last_tris = v->host_ctl->n_tri;
-    v->last_n_active = v->host_ctl->n_active;
-    v->last_n_new = v->host_ctl->n_new;
-    v->last_n_cand = v->host_ctl->n_cand;
-    v->last_slots = v->host_ctl->S;
-    return status_to_error(v, v->host_ctl->status);
-}
-
-int rerun_mc(iso_volume *v, float iso, float4 *out, unsigned long long cap_tris) {
-    int rc = ensure_debug_edges(v, cap_tris);
-    if (rc) return rc;
-    rc = enqueue_mc_again(v, iso, out, cap_tris);
-    if (rc) return rc;
-    rc = read_ctl(v);
-    if (rc) return rc;
+    *v->host_params = Params{iso, 0u, cap_tris, (unsigned long long)(uintptr_t)out};
+    const bool graph = !mc_only && v->use_graph && !(v->flags & ISO_DEBUG) && !v->profiling;
+    if (graph && ensure_graph(v) != ISO_OK) v->use_graph = false;   // fall back to plain launches
+    if (graph && v->gexec) {
+        CK(cudaGraphLaunch(v->gexec, v->stream));
+    } else {
+        rc = enqueue_pipeline(v, v->stream, mc_only, v->profiling && !mc_only);
+        if (rc) return rc;
+    }
+    CK(cudaStreamSynchronize(v->stream));
+    if (!mc_only) {
+        collect_stage_times(v);
+        v->last_n_active = v->host_ctl->n_active;
+        v->last_n_new = v->host_ctl->n_new;
+        v->last_n_cand = v->host_ctl->n_cand;
+        v->last_slots = v->host_ctl->S;
+    }
     v->last_tris = v->host_ctl->n_tri;
     return status_to_error(v, v->host_ctl->status);
 }
@@ -312,12 +336,13 @@ int iso_load_volume(iso_volume **out, const void *compressed, size_t compressed_
         TRY(dalloc(&s.dbg_btri, g.nb));
         TRY(dalloc(&s.dbg_boff, g.nb));
     }
-    if (cudaMallocHost((void **)&v->host_ctl, sizeof(Ctl)) != cudaSuccess) {
+    if (cudaMallocHost((void **)&v->host_ctl, sizeof(Ctl)) != cudaSuccess ||
+        cudaMallocHost((void **)&v->host_params, sizeof(Params)) != cudaSuccess) {
         (void)cudaGetLastError();
-        v->host_ctl = nullptr;
         free_volume(v);
         return ISO_ERR_OOM;
     }
+    v->use_graph = !(o.flags & ISO_NO_GRAPH);
     s.bits = v->bits;
     s.hull = v->hull;
     s.hull8 = v->hull8;
@@ -376,7 +401,7 @@ int iso_extract_into(iso_volume *v, float isovalue, float *d_vertices, uint64_t 
                      iso_stats *stats) {
     if (!v || !std::isfinite(isovalue) || (!d_vertices && capacity_triangles)) return ISO_ERR_INVALID_ARG;
     DeviceGuard dg(v->device);
-    int rc = run(v, isovalue, reinterpret_cast<float4 *>(d_vertices), capacity_triangles);
+    int rc = run(v, isovalue, reinterpret_cast<float4 *>(d_vertices), capacity_triangles, false);
     if (stats) fill_stats(v, stats, 0);
     if (rc) return rc;
     if (v->host_ctl->n_tri > capacity_triangles) return ISO_ERR_CAPACITY;
@@ -391,7 +416,7 @@ int iso_extract(iso_volume *v, float isovalue, iso_mesh *out) {
     unsigned long long guess = v->last_tris ? v->last_tris + v->last_tris / 4 + 4096 : 2ull * v->g.nb + 4096;
     float4 *buf = nullptr;
     CK(cudaMallocAsync((void **)&buf, guess * 3 * sizeof(float4), v->stream));
-    int rc = run(v, isovalue, buf, guess);
+    int rc = run(v, isovalue, buf, guess, false);
     uint32_t reruns = 0;
     if (rc == ISO_OK && v->host_ctl->n_tri > guess) {
         const unsigned long long need = v->host_ctl->n_tri;
@@ -399,7 +424,7 @@ int iso_extract(iso_volume *v, float isovalue, iso_mesh *out) {
         buf = nullptr;
         CK(cudaMallocAsync((void **)&buf, std::max(need, 1ull) * 3 * sizeof(float4), v->stream));
         guess = std::max(need, 1ull);
-        rc = rerun_mc(v, isovalue, buf, guess);
+        rc = run(v, isovalue, buf, guess, true);
         reruns = 1;
     }
     if (rc) {

@@ -13,6 +13,7 @@ namespace bcmc {
 // get the block's range over its in-volume decoded samples.
 __global__ void __launch_bounds__(128) encode_kernel(const float *__restrict__ field, Geom g, uint64_t *bits,
                                                      float *bmin, float *bmax) {
+    __shared__ uint64_t planes[32 * 128];
     const uint32_t slab = g.nbx * g.nby;
     for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < g.nb; b += gridDim.x * blockDim.x) {
         const uint32_t bx = b % g.nbx, by = (b / g.nbx) % g.nby, bz = b / slab;
@@ -30,7 +31,7 @@ __global__ void __launch_bounds__(128) encode_kernel(const float *__restrict__ f
         uint64_t *w = bits + (size_t)b * g.rate;
         encode_block(v, g.rate, w);
         float d[64];
-        decode_block<false>(w, g.rate, d);   // just written by this thread
+        decode_block<false>(w, g.rate, d, planes + threadIdx.x, blockDim.x);   // just written by this thread
         float lo = __int_as_float(0x7F800000), hi = __int_as_float(0xFF800000);   // +inf, -inf
 #pragma unroll
         for (int k = 0; k < 4; k++)
@@ -50,9 +51,10 @@ __global__ void __launch_bounds__(128) encode_kernel(const float *__restrict__ f
 
 __global__ void __launch_bounds__(128) decode_list_kernel(const uint64_t *__restrict__ bits, uint32_t rate,
                                                           const uint32_t *__restrict__ ids, uint64_t n, float *out) {
+    __shared__ uint64_t planes[32 * 128];
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
         float v[64];
-        decode_block(bits + (size_t)ids[i] * rate, rate, v);
+        decode_block(bits + (size_t)ids[i] * rate, rate, v, planes + threadIdx.x, blockDim.x);
         float4 *dst = reinterpret_cast<float4 *>(out + i * 64);
 #pragma unroll
         for (int q = 0; q < 16; q++) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);

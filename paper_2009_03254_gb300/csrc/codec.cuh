@@ -35,15 +35,37 @@ __device__ __forceinline__ uint64_t load_word(const uint64_t *p) {
     else return *p;
 }
 
-// 64 bits of the block starting at bit `pos`; bits past the block read as 0
+// A 128-bit window over a block's stream: bits [base, base+128) of the
+// block in two words, refilled one word at a time, so each word of the
+// block is loaded once.
 template <bool kReadOnly>
-__device__ __forceinline__ uint64_t peek64(const uint64_t *__restrict__ w, uint32_t nwords, uint32_t pos) {
-    const uint32_t wi = pos >> 6, sh = pos & 63;
-    const uint64_t lo = wi < nwords ? load_word<kReadOnly>(w + wi) : 0ull;
-    if (sh == 0) return lo;
-    const uint64_t hi = wi + 1 < nwords ? load_word<kReadOnly>(w + wi + 1) : 0ull;
-    return (lo >> sh) | (hi << (64 - sh));
-}
+struct BitWindow {
+    const uint64_t *w;
+    uint32_t nwords, next, base;
+    uint64_t w0, w1;
+    __device__ __forceinline__ void init(const uint64_t *words, uint32_t n) {
+        w = words;
+        nwords = n;
+        w0 = load_word<kReadOnly>(w);
+        w1 = n > 1 ? load_word<kReadOnly>(w + 1) : 0ull;
+        next = 2;
+        base = 0;
+    }
+    // 64 bits starting at pos (pos - base < 64 is kept by advance)
+    __device__ __forceinline__ uint64_t peek(uint32_t pos) const {
+        const uint32_t sh = pos - base;
+        return sh ? (w0 >> sh) | (w1 << (64 - sh)) : w0;
+    }
+    // call after pos moved forward by at most 64 bits
+    __device__ __forceinline__ void advance(uint32_t pos) {
+        if (pos - base >= 64) {
+            w0 = w1;
+            w1 = next < nwords ? load_word<kReadOnly>(w + next) : 0ull;
+            next++;
+            base += 64;
+        }
+    }
+};
 
 // inverse of one two-level S-transform step on (ll, hh, h0, h1) -> (a, b, c, d)
 __device__ __forceinline__ void inv_lift4(int32_t &p0, int32_t &p1, int32_t &p2, int32_t &p3) {
@@ -75,63 +97,72 @@ __device__ __forceinline__ float scale_pow2(int32_t q, int e) {
 }
 
 // Decode one block of `rate` words into out[64] (block-local order).
+// `planes` is this thread's column of a shared-memory scratch area:
+// plane k lives at planes[k * stride].
 template <bool kReadOnly = true>
-__device__ __forceinline__ void decode_block(const uint64_t *__restrict__ w, uint32_t rate, float (&out)[64]) {
-    const uint64_t head = load_word<kReadOnly>(w);
-    if (!(head & 1ull)) {
+__device__ __forceinline__ void decode_block(const uint64_t *__restrict__ w, uint32_t rate, float (&out)[64],
+                                             uint64_t *planes, uint32_t stride) {
+    BitWindow<kReadOnly> bw;
+    bw.init(w, rate);
+    if (!(bw.w0 & 1ull)) {
 #pragma unroll
         for (int i = 0; i < 64; i++) out[i] = 0.0f;
         return;
     }
-    const int emax = (int)((head >> 1) & 0xFFu) - 127;
+    const int emax = (int)((bw.w0 >> 1) & 0xFFu) - 127;
     const uint32_t end = rate * 64u;
     uint32_t pos = 9;
     uint32_t n = 0;                        // coefficients reached by the group tests
-    uint32_t lo[32], hi[32];               // plane words: lo[k]/hi[k] = plane k, coefficients 0-31 / 32-63
-#pragma unroll
-    for (int j = 0; j < 32; j++) {
-        const int k = 31 - j;              // plane number, most significant first
+    int k = 31;                            // plane number, most significant first
+    for (; k >= 0 && pos < end; k--) {
         uint64_t x = 0;
-        if (pos < end) {
-            const uint32_t m = min(n, end - pos);
-            if (m) {
-                x = peek64<kReadOnly>(w, rate, pos) & low_mask(m);
-                pos += m;
-            }
-            while (n < 64 && pos < end) {
-                const uint64_t win = peek64<kReadOnly>(w, rate, pos);
-                pos += 1;
-                if (!(win & 1ull)) break;  // no later coefficient has a one here
-                const uint32_t limit = 63u - n;                 // bits that may be sent
-                const uint32_t cnt = min(limit, end - pos);
-                const uint64_t y = (win >> 1) & low_mask(cnt);
-                if (y) {
-                    const uint32_t z = (uint32_t)__ffsll((long long)y) - 1u;
-                    pos += z + 1;
-                    n += z;
-                    x |= 1ull << n;
-                    n += 1;
-                } else if (cnt == limit) {
-                    pos += limit;
-                    x |= 1ull << 63;
-                    n = 64;
-                } else {
-                    pos = end;             // the budget ran out inside the scan
-                }
-            }
+        const uint32_t m = min(n, end - pos);
+        if (m) {
+            x = bw.peek(pos) & low_mask(m);
+            pos += m;
+            bw.advance(pos);
         }
-        lo[k] = (uint32_t)x;
-        hi[k] = (uint32_t)(x >> 32);
+        while (n < 64 && pos < end) {
+            const uint64_t win = bw.peek(pos);
+            pos += 1;
+            if (!(win & 1ull)) {           // no later coefficient has a one here
+                bw.advance(pos);
+                break;
+            }
+            const uint32_t limit = 63u - n;                 // bits that may be sent
+            const uint32_t cnt = min(limit, end - pos);
+            const uint64_t y = (win >> 1) & low_mask(cnt);
+            if (y) {
+                const uint32_t z = (uint32_t)__ffsll((long long)y) - 1u;
+                pos += z + 1;
+                n += z;
+                x |= 1ull << n;
+                n += 1;
+            } else if (cnt == limit) {
+                pos += limit;
+                x |= 1ull << 63;
+                n = 64;
+            } else {
+                pos = end;                 // the budget ran out inside the scan
+            }
+            bw.advance(pos);
+        }
+        planes[(uint32_t)k * stride] = x;
     }
-    transpose32(lo);                       // lo[i] = negabinary coefficient i
-    transpose32(hi);                       // hi[i] = coefficient 32 + i
+    for (; k >= 0; k--) planes[(uint32_t)k * stride] = 0ull;
     constexpr CodingOrder order = make_coding_order();
     int32_t q[64];
+    uint32_t a[32];
 #pragma unroll
-    for (int p = 0; p < 64; p++) {
-        const uint32_t u = p < 32 ? lo[p] : hi[p - 32];
-        q[order.perm[p]] = (int32_t)((u ^ kNegaMask) - kNegaMask);
-    }
+    for (int j = 0; j < 32; j++) a[j] = (uint32_t)planes[(uint32_t)j * stride];
+    transpose32(a);                        // a[i] = negabinary coefficient i
+#pragma unroll
+    for (int p = 0; p < 32; p++) q[order.perm[p]] = (int32_t)((a[p] ^ kNegaMask) - kNegaMask);
+#pragma unroll
+    for (int j = 0; j < 32; j++) a[j] = (uint32_t)(planes[(uint32_t)j * stride] >> 32);
+    transpose32(a);                        // a[i] = coefficient 32 + i
+#pragma unroll
+    for (int p = 0; p < 32; p++) q[order.perm[32 + p]] = (int32_t)((a[p] ^ kNegaMask) - kNegaMask);
 #pragma unroll
     for (int i = 0; i < 16; i++) inv_lift4(q[i], q[i + 16], q[i + 32], q[i + 48]);             // z
 #pragma unroll

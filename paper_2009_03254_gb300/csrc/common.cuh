@@ -26,9 +26,19 @@ enum Status : uint32_t {
 
 enum TileCounter { kCtrCull = 0, kCtrLruA = 1, kCtrLruB = 2, kCtrMc = 3, kNumCtr = 4 };
 
+// Per-extraction inputs, copied from pinned host memory by the first
+// operation of each extraction (so a captured graph never changes).
+struct Params {
+    float iso;
+    uint32_t reserved;
+    unsigned long long tri_cap;   // output capacity in triangles
+    unsigned long long out;       // float4 * vertex buffer
+};
+
 // One per volume, in device memory.  Written only by the kernels of one
 // extraction at a time (stream order), read back once per extraction.
 struct Ctl {
+    Params params;
     uint32_t epoch;           // extraction count; S_last values are epochs
     uint32_t n_active;        // |I_active|
     uint32_t n_new;           // |I_new|
@@ -47,7 +57,6 @@ struct Ctl {
     uint32_t mc_tiles;        // look-back descriptors the triangle kernel used (to clear)
     uint32_t ctr[kNumCtr];    // dynamic tile counters
     unsigned long long n_tri; // triangles of the surface
-    unsigned long long tri_cap; // output capacity in triangles
 };
 
 // ---------------------------------------------------------------- memory-model helpers

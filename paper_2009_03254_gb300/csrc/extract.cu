@@ -25,7 +25,7 @@ namespace bcmc {
 // ================================================================ prep
 
 __global__ void __launch_bounds__(kThreads) prep_kernel(DevState s, uint32_t n_cull_desc, uint32_t n_lru_desc,
-                                                         unsigned long long tri_cap, int mc_only) {
+                                                         int mc_only) {
     Ctl *c = s.ctl;
     const uint32_t n_mc_desc = c->mc_tiles;   // descriptors the last triangle pass used
     const uint32_t stride = gridDim.x * blockDim.x;
@@ -54,7 +54,6 @@ __global__ void __launch_bounds__(kThreads) prep_kernel(DevState s, uint32_t n_c
         c->ctr[kCtrMc] = 0;
         c->n_occ = 0;
         c->n_tri = 0;
-        c->tri_cap = tri_cap;
     }
 }
 
@@ -101,11 +100,12 @@ __device__ __forceinline__ uint32_t scan_tile_counts(TileScan &ts) {
 // 2x2x2 +group range (`hull8`) also contains iso are the candidates the
 // triangle stage visits; I_cand holds their positions in I_active.
 
-__global__ void __launch_bounds__(kThreads) cull_kernel(DevState s, Geom g, float iso, uint32_t ntiles) {
+__global__ void __launch_bounds__(kThreads) cull_kernel(DevState s, Geom g, uint32_t ntiles) {
     __shared__ TileScan ts;
     __shared__ TileScan tc;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t epoch = s.ctl->epoch;
+    const float iso = s.ctl->params.iso;
     const uint32_t lt = (1u << lane) - 1u;
     while (true) {
         if (threadIdx.x == 0) ts.tile = atomicAdd(&s.ctl->ctr[kCtrCull], 1u);
@@ -325,7 +325,10 @@ __global__ void __launch_bounds__(kThreads) lru_b_kernel(DevState s) {
 
 // ================================================================ decode (Section 4.2.1)
 
-__global__ void __launch_bounds__(kThreads) decode_new_kernel(DevState s, Geom g) {
+constexpr int kDecodeThreads = 128;
+
+__global__ void __launch_bounds__(kDecodeThreads) decode_new_kernel(DevState s, Geom g) {
+    __shared__ uint64_t planes[32 * kDecodeThreads];
     Ctl *c = s.ctl;
     if (c->status & kStatusTimeout) return;      // no barrier in this kernel: per-thread exit is safe
     const uint32_t n = c->n_assign;
@@ -338,7 +341,7 @@ __global__ void __launch_bounds__(kThreads) decode_new_kernel(DevState s, Geom g
         const uint32_t b = s.inew[r];
         const uint32_t slot = s.newslot[r];
         float v[64];
-        decode_block(s.bits + (size_t)b * g.rate, g.rate, v);
+        decode_block(s.bits + (size_t)b * g.rate, g.rate, v, planes + threadIdx.x, kDecodeThreads);
         float4 *dst = reinterpret_cast<float4 *>(s.slots + (size_t)slot * 64);
 #pragma unroll
         for (int i = 0; i < 16; i++) dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
@@ -410,14 +413,14 @@ __global__ void gather_slots_kernel(const float *__restrict__ slots, const int32
 
 // ================================================================ launchers
 
-void launch_prep(const DevState &s, uint32_t n_cull_desc, uint32_t n_lru_desc, unsigned long long tri_cap,
-                 bool mc_only, int grid, cudaStream_t st) {
-    prep_kernel<<<grid, kThreads, 0, st>>>(s, n_cull_desc, n_lru_desc, tri_cap, mc_only ? 1 : 0);
+void launch_prep(const DevState &s, uint32_t n_cull_desc, uint32_t n_lru_desc, bool mc_only, int grid,
+                 cudaStream_t st) {
+    prep_kernel<<<grid, kThreads, 0, st>>>(s, n_cull_desc, n_lru_desc, mc_only ? 1 : 0);
 }
 
-void launch_cull(const DevState &s, const Geom &g, float iso, int grid, cudaStream_t st) {
+void launch_cull(const DevState &s, const Geom &g, int grid, cudaStream_t st) {
     const uint32_t ntiles = (g.nb + kScanTile - 1) / kScanTile;
-    cull_kernel<<<(int)std::min<uint32_t>(ntiles, (uint32_t)grid), kThreads, 0, st>>>(s, g, iso, ntiles);
+    cull_kernel<<<(int)std::min<uint32_t>(ntiles, (uint32_t)grid), kThreads, 0, st>>>(s, g, ntiles);
 }
 
 void launch_lru(const DevState &s, int grid_a, int grid_b, cudaStream_t st) {
@@ -426,7 +429,7 @@ void launch_lru(const DevState &s, int grid_a, int grid_b, cudaStream_t st) {
 }
 
 void launch_decode_new(const DevState &s, const Geom &g, int grid, cudaStream_t st) {
-    decode_new_kernel<<<grid, kThreads, 0, st>>>(s, g);
+    decode_new_kernel<<<grid, kDecodeThreads, 0, st>>>(s, g);
 }
 
 void launch_hull(const float *bmin, const float *bmax, float2 *hull, float2 *hull8, const Geom &g,
@@ -456,7 +459,7 @@ Grids compute_grids(int sm_count) {
     gr.lru_a = std::max(1, occ) * sm_count;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lru_b_kernel, kThreads, 0);
     gr.lru_b = std::max(1, occ) * sm_count;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, decode_new_kernel, kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, decode_new_kernel, kDecodeThreads, 0);
     gr.decode = std::max(1, occ) * sm_count;
     gr.mc = std::max(1, mc_occupancy()) * sm_count;
     gr.prep = 2 * sm_count;

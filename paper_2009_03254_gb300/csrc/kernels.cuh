@@ -43,12 +43,13 @@ constexpr int kScanTile = 2048;          // entries per tile of the cull / cache
 constexpr int kMcTileBlocks = 32;        // candidate blocks per tile of the triangle kernel (4 per warp)
 constexpr int kMcWarpTiles = 8;          // look-back descriptors per tile (one per warp)
 
-void launch_prep(const DevState &s, uint32_t n_cull_desc, uint32_t n_lru_desc, unsigned long long tri_cap,
-                 bool mc_only, int grid, cudaStream_t st);
-void launch_cull(const DevState &s, const Geom &g, float iso, int grid, cudaStream_t st);
+// The isovalue, output buffer and its capacity are read from Ctl::params.
+void launch_prep(const DevState &s, uint32_t n_cull_desc, uint32_t n_lru_desc, bool mc_only, int grid,
+                 cudaStream_t st);
+void launch_cull(const DevState &s, const Geom &g, int grid, cudaStream_t st);
 void launch_lru(const DevState &s, int grid_a, int grid_b, cudaStream_t st);
 void launch_decode_new(const DevState &s, const Geom &g, int grid, cudaStream_t st);
-void launch_mc(const DevState &s, const Geom &g, float iso, float4 *out, bool debug, int grid, cudaStream_t st);
+void launch_mc(const DevState &s, const Geom &g, bool debug, int grid, cudaStream_t st);
 void launch_hull(const float *bmin, const float *bmax, float2 *hull, float2 *hull8, const Geom &g,
                  cudaStream_t st);
 void launch_reset_cache(const DevState &s, cudaStream_t st);

@@ -91,8 +91,7 @@ __device__ __forceinline__ int halo_off(int s) { return (s % 5) + 8 * ((s / 5) %
 
 }  // namespace
 
-__global__ void __launch_bounds__(kThreads) mc_kernel(DevState s, Geom g, float iso, float4 *__restrict__ out,
-                                                      int debug) {
+__global__ void __launch_bounds__(kThreads) mc_kernel(DevState s, Geom g, int debug) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
     Ctl *c = s.ctl;
@@ -113,7 +112,9 @@ __global__ void __launch_bounds__(kThreads) mc_kernel(DevState s, Geom g, float 
     __syncthreads();
     const uint32_t n_cand = c->n_cand;
     const uint32_t ntiles = (n_cand + kTile - 1) / kTile;
-    const unsigned long long tri_cap = c->tri_cap;
+    const float iso = c->params.iso;
+    const unsigned long long tri_cap = c->params.tri_cap;
+    float4 *__restrict__ out = reinterpret_cast<float4 *>(c->params.out);
     const bool failed = (sm.status & (kStatusBudget | kStatusTimeout)) != 0;
     if (blockIdx.x == 0 && threadIdx.x == 0) c->mc_tiles = failed ? 0u : ntiles * kWarps;
     if (failed) return;
@@ -310,8 +311,8 @@ __global__ void __launch_bounds__(kThreads) mc_kernel(DevState s, Geom g, float 
 
 size_t mc_smem_bytes() { return sizeof(Smem); }
 
-void launch_mc(const DevState &s, const Geom &g, float iso, float4 *out, bool debug, int grid, cudaStream_t st) {
-    mc_kernel<<<grid, kThreads, sizeof(Smem), st>>>(s, g, iso, out, debug ? 1 : 0);
+void launch_mc(const DevState &s, const Geom &g, bool debug, int grid, cudaStream_t st) {
+    mc_kernel<<<grid, kThreads, sizeof(Smem), st>>>(s, g, debug ? 1 : 0);
 }
 
 int mc_occupancy() {
