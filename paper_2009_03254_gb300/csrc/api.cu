@@ -4,6 +4,7 @@
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "bcmc.h"
@@ -52,16 +53,54 @@ namespace {
         }                                                         \
     } while (0)
 
+// Device memory comes from one library-owned, stream-ordered pool per
+// device that keeps freed memory for reuse (release threshold raised), so
+// loading and releasing volumes repeatedly does not pay for cudaMalloc and
+// cudaFree (which synchronises the device) each time.
+constexpr int kMaxPoolDevices = 64;
+std::mutex g_pool_mutex;
+cudaMemPool_t g_pool[kMaxPoolDevices] = {};
+
+cudaMemPool_t device_pool(int dev) {
+    if (dev < 0 || dev >= kMaxPoolDevices) return nullptr;
+    std::lock_guard<std::mutex> lock(g_pool_mutex);
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return nullptr;
+        }
+        uint64_t keep = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        g_pool[dev] = pool;
+    }
+    return g_pool[dev];
+}
+
+// the stream every allocation and free of a volume is ordered on
+thread_local cudaStream_t t_alloc_stream = nullptr;
+thread_local int t_alloc_device = 0;
+
 template <typename T>
 int dalloc(T **p, size_t count) {
     *p = nullptr;
     if (count == 0) count = 1;
-    CK(cudaMalloc((void **)p, count * sizeof(T)));
+    cudaMemPool_t pool = device_pool(t_alloc_device);
+    if (pool) {
+        CK(cudaMallocFromPoolAsync((void **)p, count * sizeof(T), pool, t_alloc_stream));
+    } else {
+        CK(cudaMalloc((void **)p, count * sizeof(T)));
+    }
     return ISO_OK;
 }
 
 void dfree(void *p) {
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, t_alloc_stream);
 }
 
 int geometry(uint32_t nx, uint32_t ny, uint32_t nz, uint32_t rate, Geom *g) {
@@ -78,12 +117,15 @@ int free_volume(iso_volume *v) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaSetDevice(v->device);
-    if (v->stream) cudaStreamSynchronize(v->stream);
+    t_alloc_stream = v->stream;
+    t_alloc_device = v->device;
     DevState &s = v->s;
     void *ptrs[] = {v->bits, v->bmin, v->bmax, v->hull, v->hull8, v->tables, s.mactive, s.iactive, s.inew, s.icand,
                     s.islot, s.slast, s.sblock, s.lbuf[0], s.lbuf[1], s.newslot, s.slots, s.desc_cull, s.desc_cand,
                     s.desc_lru_a, s.desc_lru_b, s.desc_mc, s.ctl, s.dbg_cases, s.dbg_btri, s.dbg_boff, s.dbg_edges};
     for (void *p : ptrs) dfree(p);
+    cudaStreamSynchronize(v->stream);
+    (void)cudaGetLastError();
     if (v->host_ctl) cudaFreeHost(v->host_ctl);
     if (v->host_params) cudaFreeHost(v->host_params);
     if (v->gexec) cudaGraphExecDestroy(v->gexec);
@@ -200,6 +242,8 @@ void fill_stats(const iso_volume *v, iso_stats *st, uint32_t reruns) {
 int ensure_debug_edges(iso_volume *v, unsigned long long tris) {
     if (!(v->flags & ISO_DEBUG) || 3ull * tris <= v->dbg_edges_cap) return ISO_OK;
     CK(cudaStreamSynchronize(v->stream));
+    t_alloc_stream = v->stream;
+    t_alloc_device = v->device;
     dfree(v->s.dbg_edges);
     v->s.dbg_edges = nullptr;
     const unsigned long long want = std::max(3ull * tris, 3ull * 1024);
@@ -287,6 +331,8 @@ int iso_load_volume(iso_volume **out, const void *compressed, size_t compressed_
     if (!v) return ISO_ERR_OOM;
     if (cudaGetDevice(&v->device) != cudaSuccess) { (void)cudaGetLastError(); delete v; return ISO_ERR_CUDA; }
     v->stream = (cudaStream_t)o.stream;
+    t_alloc_stream = v->stream;
+    t_alloc_device = v->device;
     v->g = g;
     v->flags = o.flags;
     uint64_t cap = g.nb;
@@ -307,7 +353,7 @@ int iso_load_volume(iso_volume **out, const void *compressed, size_t compressed_
     const uint32_t nwords = (g.nb + 31) / 32;
     v->n_cull_desc = (g.nb + kScanTile - 1) / kScanTile;
     v->n_lru_desc = (v->cap + kScanTile - 1) / kScanTile;
-    const uint32_t n_mc_desc = (g.nb + kMcTileBlocks - 1) / kMcTileBlocks * kMcWarpTiles;
+    const uint32_t n_mc_desc = (g.nb + kMcTileBlocks - 1) / kMcTileBlocks;
     TRY(dalloc(&v->bits, words));
     TRY(dalloc(&v->bmin, g.nb));
     TRY(dalloc(&v->bmax, g.nb));
@@ -415,14 +461,22 @@ int iso_extract(iso_volume *v, float isovalue, iso_mesh *out) {
     // first guess: the last surface's size plus a margin, else 2 per block
     unsigned long long guess = v->last_tris ? v->last_tris + v->last_tris / 4 + 4096 : 2ull * v->g.nb + 4096;
     float4 *buf = nullptr;
-    CK(cudaMallocAsync((void **)&buf, guess * 3 * sizeof(float4), v->stream));
+    t_alloc_stream = v->stream;
+    t_alloc_device = v->device;
+    {
+        const int arc = dalloc(&buf, guess * 3);
+        if (arc) return arc;
+    }
     int rc = run(v, isovalue, buf, guess, false);
     uint32_t reruns = 0;
     if (rc == ISO_OK && v->host_ctl->n_tri > guess) {
         const unsigned long long need = v->host_ctl->n_tri;
         cudaFreeAsync(buf, v->stream);
         buf = nullptr;
-        CK(cudaMallocAsync((void **)&buf, std::max(need, 1ull) * 3 * sizeof(float4), v->stream));
+        {
+            const int arc = dalloc(&buf, std::max(need, 1ull) * 3);
+            if (arc) return arc;
+        }
         guess = std::max(need, 1ull);
         rc = run(v, isovalue, buf, guess, true);
         reruns = 1;
@@ -551,9 +605,12 @@ int iso_debug_read_blocks(iso_volume *v, const uint32_t *ids, uint64_t n, float 
     uint32_t *d_ids = nullptr;
     float *d_out = nullptr;
     int32_t *d_missing = nullptr;
+    t_alloc_stream = v->stream;
+    t_alloc_device = v->device;
     int rc = dalloc(&d_ids, n);
     if (!rc) rc = dalloc(&d_out, n * 64);
     if (!rc) rc = dalloc(&d_missing, 1);
+    if (!rc && cudaStreamSynchronize(v->stream) != cudaSuccess) rc = ISO_ERR_CUDA;
     int32_t missing = 0;
     if (!rc && (cudaMemcpy(d_ids, ids, n * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
                 cudaMemset(d_missing, 0, 4) != cudaSuccess))
@@ -569,6 +626,7 @@ int iso_debug_read_blocks(iso_volume *v, const uint32_t *ids, uint64_t n, float 
     dfree(d_ids);
     dfree(d_out);
     dfree(d_missing);
+    cudaStreamSynchronize(v->stream);
     if (rc) return rc;
     return missing ? ISO_ERR_INVALID_ARG : ISO_OK;
 }

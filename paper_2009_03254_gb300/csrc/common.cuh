@@ -88,7 +88,12 @@ constexpr unsigned long long kValueMask = (1ull << 62) - 1;
 constexpr int kSpinLimit = 1 << 20;
 
 // Called by all 32 lanes of one warp.  Returns the exclusive prefix of
-// `tile` (same value in every lane) and publishes the inclusive one.
+// `tile` (same value in every lane) and publishes the inclusive one.  Each
+// poll reads a window of 32 x kLookbackPerLane predecessors (lane l reads
+// the kLookbackPerLane nearest-first descriptors of its slice) and stops at
+// the nearest inclusive prefix, summing the aggregates after it.
+constexpr int kLookbackPerLane = 4;
+
 __device__ __forceinline__ unsigned long long lookback_exclusive(unsigned long long *desc, uint32_t tile,
                                                                   unsigned long long aggregate,
                                                                   uint32_t *status) {
@@ -103,13 +108,26 @@ __device__ __forceinline__ unsigned long long lookback_exclusive(unsigned long l
     int spins = 0;
     unsigned sleep_ns = 32;
     while (true) {
-        long long idx = base - lane;
-        unsigned long long d = idx >= 0 ? ld_relaxed(desc + idx) : kFlagPrefix;
-        unsigned flag = (unsigned)(d >> 62);
-        unsigned ready = __ballot_sync(0xffffffffu, flag != 0);
-        unsigned pref = __ballot_sync(0xffffffffu, flag == 2);
-        unsigned need = pref ? ((pref & (0u - pref)) << 1) - 1u : 0xffffffffu; // lanes up to the first prefix
-        if ((ready & need) != need) {
+        unsigned long long d[kLookbackPerLane];
+#pragma unroll
+        for (int k = 0; k < kLookbackPerLane; k++) {
+            const long long idx = base - (long long)lane * kLookbackPerLane - k;
+            d[k] = idx >= 0 ? ld_relaxed(desc + idx) : kFlagPrefix;
+        }
+        bool ready = true, has_prefix = false;
+        unsigned long long v = 0;
+#pragma unroll
+        for (int k = 0; k < kLookbackPerLane; k++) {
+            if (has_prefix) continue;
+            const unsigned flag = (unsigned)(d[k] >> 62);
+            if (flag == 0) ready = false;
+            v += d[k] & kValueMask;
+            if (flag == 2) has_prefix = true;
+        }
+        const unsigned rdy = __ballot_sync(0xffffffffu, ready);
+        const unsigned pref = __ballot_sync(0xffffffffu, has_prefix && ready);
+        const unsigned need = pref ? ((pref & (0u - pref)) << 1) - 1u : 0xffffffffu;   // lanes up to the first prefix
+        if ((rdy & need) != need) {
             if (++spins > kSpinLimit) {
                 if (lane == 0) atomicOr(status, (uint32_t)kStatusTimeout);
                 break;
@@ -118,12 +136,12 @@ __device__ __forceinline__ unsigned long long lookback_exclusive(unsigned long l
             if (sleep_ns < 1024) sleep_ns <<= 1;
             continue;
         }
-        unsigned long long v = ((need >> lane) & 1u) ? (d & kValueMask) : 0ull;
+        v = ((need >> lane) & 1u) ? v : 0ull;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         excl += v;
         if (pref) break;
-        base -= 32;
+        base -= 32 * kLookbackPerLane;
     }
     if (lane == 0) st_relaxed(desc + tile, kFlagPrefix | (excl + aggregate));
     return excl;

@@ -139,21 +139,24 @@ __global__ void __launch_bounds__(kThreads) cull_kernel(DevState s, Geom g, uint
             }
         }
         __syncthreads();
-        if (warp == 0) {
+        if (warp == 0) {                       // active and new counts
             const uint32_t tot = scan_tile_counts(ts);
-            const uint32_t totc = scan_tile_counts(tc);
             const unsigned long long agg = ((unsigned long long)(tot >> 16) << 31) | (tot & 0xFFFFu);
             const unsigned long long excl = lookback_exclusive(s.desc_cull, tile, agg, &s.ctl->status);
-            const unsigned long long exclc = lookback_exclusive(s.desc_cand, tile, totc, &s.ctl->status);
             if (lane == 0) {
                 ts.excl = excl;
-                tc.excl = exclc;
                 if (tile == ntiles - 1) {
                     const unsigned long long incl = excl + agg;
                     s.ctl->n_active = (uint32_t)(incl >> 31);
                     s.ctl->n_new = (uint32_t)(incl & 0x7FFFFFFFu);
-                    s.ctl->n_cand = (uint32_t)(exclc + totc);
                 }
+            }
+        } else if (warp == 1) {                // candidate count, in parallel
+            const uint32_t totc = scan_tile_counts(tc);
+            const unsigned long long exclc = lookback_exclusive(s.desc_cand, tile, totc, &s.ctl->status);
+            if (lane == 0) {
+                tc.excl = exclc;
+                if (tile == ntiles - 1) s.ctl->n_cand = (uint32_t)(exclc + totc);
             }
         }
         __syncthreads();

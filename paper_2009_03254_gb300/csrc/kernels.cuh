@@ -41,7 +41,6 @@ struct Grids {                 // CTAs per launch, from occupancy at load time
 constexpr int kThreads = 256;
 constexpr int kScanTile = 2048;          // entries per tile of the cull / cache scans
 constexpr int kMcTileBlocks = 32;        // candidate blocks per tile of the triangle kernel (4 per warp)
-constexpr int kMcWarpTiles = 8;          // look-back descriptors per tile (one per warp)
 
 // The isovalue, output buffer and its capacity are read from Ctl::params.
 void launch_prep(const DevState &s, uint32_t n_cull_desc, uint32_t n_lru_desc, bool mc_only, int grid,

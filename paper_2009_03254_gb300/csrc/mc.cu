@@ -9,16 +9,18 @@
 // as possible ("checking which side the neighbor was on").
 //
 // Work split: a CTA takes a tile of 32 consecutive candidates from a
-// counter; each of its 8 warps owns 4 consecutive candidates and runs
-// every phase on them without waiting for the other warps:
+// counter; each of its 8 warps owns 4 consecutive candidates and runs the
+// phases on them, meeting the other warps only for the tile's offset:
 //   A  slots of each block's 8 blocks of the +group (8 lanes per block)
 //   B  stage the 5x5x5 samples in shared memory: 16 float4 rows of the
 //      block, its +x face, +y/+z rows, edges and corner (50 loads per
 //      block, 2 per lane, issued together)
 //   C  classify: four ballots give the 125 below-iso bits; each cell's
 //      case is 8 bits picked from them; counts from the case table
-//   D  per-block counts -> this warp's total -> decoupled look-back over
-//      warp tiles: the prefix sum over blocks of Section 4.4 in one pass
+//   D  per-block counts -> warp totals -> tile total -> one decoupled
+//      look-back per tile: the prefix sum over blocks of Section 4.4 in
+//      one pass (per-tile rather than per-warp descriptors keep the walk
+//      back short: only the tiles in flight, one per CTA, are pending)
 //   E  per-cell offsets (Section 4.5) by two packed warp scans, a
 //      triangle -> (block, cell, k) map, then each lane writes whole
 //      float4 vertices: a warp's stores cover one contiguous range.
@@ -49,6 +51,8 @@ struct Smem {
     uint8_t num_tri[256];
     uint8_t tri_edges[256][16];
     uint32_t edge_info[12];
+    uint32_t wtot[kWarps];                            // triangles of each warp's blocks in this tile
+    unsigned long long tile_base;                     // triangles before this tile
     uint32_t tile[2];
     uint32_t occ;
     uint32_t status;
@@ -91,7 +95,7 @@ __device__ __forceinline__ int halo_off(int s) { return (s % 5) + 8 * ((s / 5) %
 
 }  // namespace
 
-__global__ void __launch_bounds__(kThreads) mc_kernel(DevState s, Geom g, int debug) {
+__global__ void __launch_bounds__(kThreads, 4) mc_kernel(DevState s, Geom g, int debug) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
     Ctl *c = s.ctl;
@@ -116,7 +120,7 @@ __global__ void __launch_bounds__(kThreads) mc_kernel(DevState s, Geom g, int de
     const unsigned long long tri_cap = c->params.tri_cap;
     float4 *__restrict__ out = reinterpret_cast<float4 *>(c->params.out);
     const bool failed = (sm.status & (kStatusBudget | kStatusTimeout)) != 0;
-    if (blockIdx.x == 0 && threadIdx.x == 0) c->mc_tiles = failed ? 0u : ntiles * kWarps;
+    if (blockIdx.x == 0 && threadIdx.x == 0) c->mc_tiles = failed ? 0u : ntiles;
     if (failed) return;
     const uint32_t slab = g.nbx * g.nby;
 
@@ -241,11 +245,25 @@ __global__ void __launch_bounds__(kThreads) mc_kernel(DevState s, Geom g, int de
             wtot += btot[q];
         }
 
-        // ---- D: prefix over warp tiles
-        const uint32_t wtile = tile * kWarps + warp;
-        const unsigned long long wbase = lookback_exclusive(s.desc_mc, wtile, wtot, &c->status);
+        // ---- D: prefix over tiles: warp totals -> tile total -> one
+        // decoupled look-back per tile (warp 0), then each warp's base
+        if (lane == 0) sm.wtot[warp] = wtot;
+        __syncthreads();
+        if (warp == 0) {
+            const uint32_t mine = lane < kWarps ? sm.wtot[lane] : 0u;
+            uint32_t tot = mine;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+            const unsigned long long excl = lookback_exclusive(s.desc_mc, tile, tot, &c->status);
+            if (lane == 0) {
+                sm.tile_base = excl;
+                if (tile == ntiles - 1) c->n_tri = excl + tot;
+            }
+        }
+        __syncthreads();
+        unsigned long long wbase = sm.tile_base;
+        for (int w = 0; w < warp; w++) wbase += sm.wtot[w];
         if (lane == 0) {
-            if (wtile == ntiles * kWarps - 1) c->n_tri = wbase + wtot;
             uint32_t occ = 0;
 #pragma unroll
             for (int q = 0; q < kBlocksPerWarp; q++) occ += btot[q] > 0;
