@@ -159,12 +159,12 @@ def profile_traffic(kernel_file, kernel):
 
 def stage_bytes(stats, rate, nb):
     """Algorithmic bytes each stage must move for one surface."""
-    na, nn, T = stats["n_active"], stats["n_new"], stats["num_triangles"]
+    na, nn, nc, T = stats["n_active"], stats["n_new"], stats["n_candidates"], stats["num_triangles"]
     return {
-        "cull": 8 * nb + nb / 8 + 4 * na + 4 * nn,                  # block hulls, mask, I_active, I_new
+        "cull": 8 * nb + nb / 8 + 4 * na + 4 * nn + 8 * na + 4 * nc,   # hulls, mask, I_active, I_new, +group hulls, I_cand
         "cache_update": 0.0,
-        "decode": nn * (8 * rate + 256 + 8),                         # compressed in, decoded out, I_new + slot
-        "triangles": na * (256 + 4) + 48 * T,                        # decoded tiles in, vertices out
+        "decode": nn * (8 * rate + 256 + 8),                           # compressed in, decoded out, I_new + slot
+        "triangles": nc * (256 + 8 + 12) + 48 * T,                     # decoded candidate tiles in, ids, counts/offsets, vertices out
     }
 
 

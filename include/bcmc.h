@@ -87,6 +87,9 @@ typedef struct iso_stats {
     uint64_t cache_bytes;      /* n_slots * 256 */
     uint32_t epoch;            /* 1-based count of extractions on this volume */
     uint32_t reruns;           /* 1 if the triangle stage ran twice to fit the output */
+    uint32_t n_candidates;     /* active blocks whose 2x2x2 +group range contains iso: the
+                                  blocks the triangle stage visits */
+    uint32_t reserved;
 } iso_stats;
 
 typedef struct iso_mesh {

@@ -122,7 +122,7 @@ int free_volume(iso_volume *v) {
     DevState &s = v->s;
     void *ptrs[] = {v->bits, v->bmin, v->bmax, v->hull, v->hull8, v->tables, s.mactive, s.iactive, s.inew, s.icand,
                     s.islot, s.slast, s.sblock, s.lbuf[0], s.lbuf[1], s.newslot, s.slots, s.desc_cull, s.desc_cand,
-                    s.desc_lru_a, s.desc_lru_b, s.desc_mc, s.ctl, s.dbg_cases, s.dbg_btri, s.dbg_boff, s.dbg_edges};
+                    s.desc_lru_a, s.desc_lru_b, s.desc_mc, s.ctl, s.counts, s.offsets, s.dbg_cases, s.dbg_edges};
     for (void *p : ptrs) dfree(p);
     cudaStreamSynchronize(v->stream);
     (void)cudaGetLastError();
@@ -171,7 +171,7 @@ int enqueue_pipeline(iso_volume *v, cudaStream_t st, bool mc_only, bool prof) {
     const bool debug = (v->flags & ISO_DEBUG) != 0;
     CK(cudaMemcpyAsync(&v->s.ctl->params, v->host_params, sizeof(Params), cudaMemcpyHostToDevice, st));
     if (prof) cudaEventRecord(v->ev[0], st);
-    launch_prep(v->s, v->n_cull_desc, v->n_lru_desc, mc_only, v->grids.prep, st);
+    if (!mc_only) launch_prep(v->s, v->n_cull_desc, v->n_lru_desc, false, v->grids.prep, st);
     if (prof) cudaEventRecord(v->ev[1], st);
     if (!mc_only) {
         launch_cull(v->s, v->g, v->grids.cull, st);
@@ -181,7 +181,7 @@ int enqueue_pipeline(iso_volume *v, cudaStream_t st, bool mc_only, bool prof) {
         launch_decode_new(v->s, v->g, v->grids.decode, st);
         if (prof) cudaEventRecord(v->ev[4], st);
     }
-    launch_mc(v->s, v->g, debug, v->grids.mc, st);
+    launch_mc(v->s, v->g, debug, mc_only, v->grids, st);
     if (prof) cudaEventRecord(v->ev[5], st);
     CK(cudaMemcpyAsync(v->host_ctl, v->s.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
     CK(cudaGetLastError());
@@ -236,6 +236,8 @@ void fill_stats(const iso_volume *v, iso_stats *st, uint32_t reruns) {
     st->cache_bytes = (uint64_t)c.S * 256ull;
     st->epoch = c.epoch;
     st->reruns = reruns;
+    st->n_candidates = c.n_cand;
+    st->reserved = 0;
 }
 
 // debug mode: make sure the per-vertex edge-id buffer can hold T triangles
@@ -353,7 +355,7 @@ int iso_load_volume(iso_volume **out, const void *compressed, size_t compressed_
     const uint32_t nwords = (g.nb + 31) / 32;
     v->n_cull_desc = (g.nb + kScanTile - 1) / kScanTile;
     v->n_lru_desc = (v->cap + kScanTile - 1) / kScanTile;
-    const uint32_t n_mc_desc = (g.nb + kMcTileBlocks - 1) / kMcTileBlocks;
+    const uint32_t n_mc_desc = (v->cap + 2047) / 2048;   // scan tiles over the candidates (<= cap)
     TRY(dalloc(&v->bits, words));
     TRY(dalloc(&v->bmin, g.nb));
     TRY(dalloc(&v->bmax, g.nb));
@@ -377,11 +379,9 @@ int iso_load_volume(iso_volume **out, const void *compressed, size_t compressed_
     TRY(dalloc(&s.desc_lru_b, v->n_lru_desc));
     TRY(dalloc(&s.desc_mc, n_mc_desc));
     TRY(dalloc(&s.ctl, 1));
-    if (v->flags & ISO_DEBUG) {
-        TRY(dalloc(&s.dbg_cases, (size_t)g.nb * 64));
-        TRY(dalloc(&s.dbg_btri, g.nb));
-        TRY(dalloc(&s.dbg_boff, g.nb));
-    }
+    TRY(dalloc(&s.counts, v->cap));
+    TRY(dalloc(&s.offsets, v->cap));
+    if (v->flags & ISO_DEBUG) TRY(dalloc(&s.dbg_cases, (size_t)g.nb * 64));
     if (cudaMallocHost((void **)&v->host_ctl, sizeof(Ctl)) != cudaSuccess ||
         cudaMallocHost((void **)&v->host_params, sizeof(Params)) != cudaSuccess) {
         (void)cudaGetLastError();
@@ -577,8 +577,8 @@ int iso_debug_get(iso_volume *v, int which, void *host_dst, size_t bytes, uint64
         case ISO_DBG_SLOT_LAST_USE: src = v->s.slast; n = v->last_slots; elem = 4; break;
         case ISO_DBG_ACTIVE_MASK: src = v->s.mactive; n = (v->g.nb + 31) / 32; elem = 4; break;
         case ISO_DBG_CELL_CASES: if (!dbg) return ISO_ERR_INVALID_ARG; src = v->s.dbg_cases; n = 64ull * v->last_n_cand; elem = 1; break;
-        case ISO_DBG_BLOCK_TRIS: if (!dbg) return ISO_ERR_INVALID_ARG; src = v->s.dbg_btri; n = v->last_n_cand; elem = 4; break;
-        case ISO_DBG_BLOCK_OFFSETS: if (!dbg) return ISO_ERR_INVALID_ARG; src = v->s.dbg_boff; n = v->last_n_cand; elem = 8; break;
+        case ISO_DBG_BLOCK_TRIS: src = v->s.counts; n = v->last_n_cand; elem = 4; break;
+        case ISO_DBG_BLOCK_OFFSETS: src = v->s.offsets; n = v->last_n_cand; elem = 8; break;
         case ISO_DBG_CANDIDATES: src = v->s.icand; n = v->last_n_cand; elem = 4; break;
         case ISO_DBG_EDGE_IDS:
             if (!dbg) return ISO_ERR_INVALID_ARG;

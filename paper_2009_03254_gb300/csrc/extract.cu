@@ -464,7 +464,7 @@ Grids compute_grids(int sm_count) {
     gr.lru_b = std::max(1, occ) * sm_count;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, decode_new_kernel, kDecodeThreads, 0);
     gr.decode = std::max(1, occ) * sm_count;
-    gr.mc = std::max(1, mc_occupancy()) * sm_count;
+    mc_grids(sm_count, &gr);
     gr.prep = 2 * sm_count;
     return gr;
 }

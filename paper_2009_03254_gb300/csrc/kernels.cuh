@@ -27,20 +27,19 @@ struct DevState {
     unsigned long long *desc_cull, *desc_cand, *desc_lru_a, *desc_lru_b, *desc_mc;
     Ctl *ctl;
     const uint8_t *tables;     // num_tri[256] then tri_edges[256][16]
+    uint32_t *counts;          // triangles of each candidate
+    unsigned long long *offsets; // exclusive prefix of counts: first triangle of each candidate
     // debug copies (null unless the volume was loaded with ISO_DEBUG)
     uint8_t *dbg_cases;        // 64 per candidate block
-    uint32_t *dbg_btri;        // per candidate block
-    unsigned long long *dbg_boff;
     unsigned long long *dbg_edges;
 };
 
 struct Grids {                 // CTAs per launch, from occupancy at load time
-    int prep, cull, lru_a, lru_b, decode, mc;
+    int prep, cull, lru_a, lru_b, decode, mc_count, mc_scan, mc_emit;
 };
 
 constexpr int kThreads = 256;
 constexpr int kScanTile = 2048;          // entries per tile of the cull / cache scans
-constexpr int kMcTileBlocks = 32;        // candidate blocks per tile of the triangle kernel (4 per warp)
 
 // The isovalue, output buffer and its capacity are read from Ctl::params.
 void launch_prep(const DevState &s, uint32_t n_cull_desc, uint32_t n_lru_desc, bool mc_only, int grid,
@@ -48,7 +47,8 @@ void launch_prep(const DevState &s, uint32_t n_cull_desc, uint32_t n_lru_desc, b
 void launch_cull(const DevState &s, const Geom &g, int grid, cudaStream_t st);
 void launch_lru(const DevState &s, int grid_a, int grid_b, cudaStream_t st);
 void launch_decode_new(const DevState &s, const Geom &g, int grid, cudaStream_t st);
-void launch_mc(const DevState &s, const Geom &g, bool debug, int grid, cudaStream_t st);
+// triangle stage: count, scan, emit (emit_only: just the last, into a new output)
+void launch_mc(const DevState &s, const Geom &g, bool debug, bool emit_only, const Grids &gr, cudaStream_t st);
 void launch_hull(const float *bmin, const float *bmax, float2 *hull, float2 *hull8, const Geom &g,
                  cudaStream_t st);
 void launch_reset_cache(const DevState &s, cudaStream_t st);
@@ -60,7 +60,6 @@ void launch_gather_slots(const float *slots, const int32_t *islot, const uint32_
 
 // occupancy-derived persistent grid sizes
 Grids compute_grids(int sm_count);
-int mc_occupancy();          // also raises the triangle kernel's dynamic shared-memory limit
-size_t mc_smem_bytes();
+void mc_grids(int sm_count, Grids *gr);   // also raises the emit kernel's shared-memory limit
 
 }  // namespace bcmc
