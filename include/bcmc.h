@@ -232,9 +232,9 @@ int iso_active_blocks_static(const float *d_bmin, const float *d_bmax, uint32_t 
 #define ISO_DBG_BLOCK_OFFSETS 9 /* uint64[n_cand]   exclusive prefix of BLOCK_TRIS */
 #define ISO_DBG_EDGE_IDS 10    /* uint64[3*T]       global edge id of each vertex:
                                   3*(x + nx*(y + ny*z)) + axis of its lower sample */
-#define ISO_DBG_CANDIDATES 11  /* uint32[n_cand]    candidate blocks, as positions in I_active: the
-                                  active blocks whose 2x2x2 +group range contains
-                                  iso (the only blocks that can emit triangles) */
+#define ISO_DBG_CANDIDATES 11  /* uint32[n_cand]    candidate block ids, ascending: the active
+                                  blocks whose 2x2x2 +group range contains iso (the
+                                  only blocks that can emit triangles) */
 int iso_debug_get(iso_volume *v, int which, void *host_dst, size_t bytes, uint64_t *count);
 
 /* Copy the decoded samples of cached blocks ids[0..n) (host array) to

@@ -108,7 +108,8 @@ int geometry(uint32_t nx, uint32_t ny, uint32_t nz, uint32_t rate, Geom *g) {
     const uint64_t nbx = (nx + 3ull) / 4, nby = (ny + 3ull) / 4, nbz = (nz + 3ull) / 4;
     const uint64_t nb = nbx * nby * nbz;
     if (nb >= (1ull << 31)) return ISO_ERR_INVALID_ARG;   // ids and packed counters are 31-bit
-    *g = Geom{nx, ny, nz, (uint32_t)nbx, (uint32_t)nby, (uint32_t)nbz, (uint32_t)nb, rate};
+    *g = Geom{nx, ny, nz, (uint32_t)nbx, (uint32_t)nby, (uint32_t)nbz, (uint32_t)nb, rate,
+              div_magic((uint32_t)nbx), div_magic((uint32_t)nby)};
     return ISO_OK;
 }
 

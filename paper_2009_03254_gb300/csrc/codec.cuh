@@ -113,41 +113,53 @@ __device__ __forceinline__ void decode_block(const uint64_t *__restrict__ w, uin
     const uint32_t end = rate * 64u;
     uint32_t pos = 9;
     uint32_t n = 0;                        // coefficients reached by the group tests
+    // One step per iteration: either the verbatim bits that open plane k or
+    // one group test with its unary run.  Lanes of a warp decode different
+    // blocks; stepping them through a single loop keeps them together even
+    // when their planes hold different numbers of group tests.
     int k = 31;                            // plane number, most significant first
-    for (; k >= 0 && pos < end; k--) {
-        uint64_t x = 0;
-        const uint32_t m = min(n, end - pos);
-        if (m) {
-            x = bw.peek(pos) & low_mask(m);
+    uint64_t x = 0;
+    bool opening = true;
+    while (k >= 0 && pos < end) {
+        bool plane_done;
+        if (opening) {
+            const uint32_t m = min(n, end - pos);
+            x = m ? (bw.peek(pos) & low_mask(m)) : 0ull;
             pos += m;
             bw.advance(pos);
-        }
-        while (n < 64 && pos < end) {
+            opening = false;
+            plane_done = n >= 64 || pos >= end;
+        } else {
             const uint64_t win = bw.peek(pos);
             pos += 1;
             if (!(win & 1ull)) {           // no later coefficient has a one here
-                bw.advance(pos);
-                break;
-            }
-            const uint32_t limit = 63u - n;                 // bits that may be sent
-            const uint32_t cnt = min(limit, end - pos);
-            const uint64_t y = (win >> 1) & low_mask(cnt);
-            if (y) {
-                const uint32_t z = (uint32_t)__ffsll((long long)y) - 1u;
-                pos += z + 1;
-                n += z;
-                x |= 1ull << n;
-                n += 1;
-            } else if (cnt == limit) {
-                pos += limit;
-                x |= 1ull << 63;
-                n = 64;
+                plane_done = true;
             } else {
-                pos = end;                 // the budget ran out inside the scan
+                const uint32_t limit = 63u - n;                 // bits that may be sent
+                const uint32_t cnt = min(limit, end - pos);
+                const uint64_t y = (win >> 1) & low_mask(cnt);
+                if (y) {
+                    const uint32_t z = (uint32_t)__ffsll((long long)y) - 1u;
+                    pos += z + 1;
+                    n += z;
+                    x |= 1ull << n;
+                    n += 1;
+                } else if (cnt == limit) {
+                    pos += limit;
+                    x |= 1ull << 63;
+                    n = 64;
+                } else {
+                    pos = end;             // the budget ran out inside the scan
+                }
+                plane_done = n >= 64 || pos >= end;
             }
             bw.advance(pos);
         }
-        planes[(uint32_t)k * stride] = x;
+        if (plane_done) {
+            planes[(uint32_t)k * stride] = x;
+            k--;
+            opening = true;
+        }
     }
     for (; k >= 0; k--) planes[(uint32_t)k * stride] = 0ull;
     constexpr CodingOrder order = make_coding_order();

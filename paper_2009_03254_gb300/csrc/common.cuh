@@ -15,7 +15,30 @@ struct Geom {
     uint32_t nbx, nby, nbz;   // blocks per axis
     uint32_t nb;              // total blocks (< 2^31, checked at load)
     uint32_t rate;            // bits per sample = 64-bit words per block
+    unsigned long long inv_nbx, inv_nby;   // floor(2^64 / d) + 1 (0 for d = 1): see block_coords
 };
+
+// Reciprocal for dividing 32-bit numbers by d with one 64-bit multiply:
+// for n < 2^32, floor(n / d) = high 64 bits of n * (floor(2^64/d) + 1),
+// since the error term n * (M - 2^64/d) / 2^64 < 2^-32 < 1/d cannot carry
+// n/d past the next integer.
+__host__ __device__ inline unsigned long long div_magic(uint32_t d) {
+    // floor((2^64-1)/d) + 1: floor(2^64/d) + 1, or exactly 2^64/d when d is a
+    // power of two (then the product is exact); both satisfy the bound above
+    return d <= 1 ? 0ull : ~0ull / d + 1ull;
+}
+
+__device__ __forceinline__ uint32_t div_by(uint32_t n, uint32_t d, unsigned long long magic) {
+    return d <= 1 ? n : (uint32_t)__umul64hi((unsigned long long)n, magic);
+}
+
+// block id -> (bx, by, bz)
+__device__ __forceinline__ void block_coords(const Geom &g, uint32_t b, uint32_t &bx, uint32_t &by, uint32_t &bz) {
+    const uint32_t q = div_by(b, g.nbx, g.inv_nbx);
+    bx = b - q * g.nbx;
+    bz = div_by(q, g.nby, g.inv_nby);
+    by = q - bz * g.nby;
+}
 
 // ---------------------------------------------------------------- control block
 
@@ -85,7 +108,7 @@ __device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long lon
 constexpr unsigned long long kFlagAgg = 1ull << 62;
 constexpr unsigned long long kFlagPrefix = 2ull << 62;
 constexpr unsigned long long kValueMask = (1ull << 62) - 1;
-constexpr int kSpinLimit = 1 << 20;
+constexpr int kSpinLimit = 1 << 23;   // with at most 128 ns between polls: about a second
 
 // Called by all 32 lanes of one warp.  Returns the exclusive prefix of
 // `tile` (same value in every lane) and publishes the inclusive one.  Each
@@ -106,7 +129,7 @@ __device__ __forceinline__ unsigned long long lookback_exclusive(unsigned long l
     unsigned long long excl = 0;
     long long base = (long long)tile - 1;
     int spins = 0;
-    unsigned sleep_ns = 32;
+    unsigned sleep_ns = 16;
     while (true) {
         unsigned long long d[kLookbackPerLane];
 #pragma unroll
@@ -133,7 +156,7 @@ __device__ __forceinline__ unsigned long long lookback_exclusive(unsigned long l
                 break;
             }
             __nanosleep(sleep_ns);
-            if (sleep_ns < 1024) sleep_ns <<= 1;
+            if (sleep_ns < 128) sleep_ns <<= 1;
             continue;
         }
         v = ((need >> lane) & 1u) ? v : 0ull;

@@ -59,33 +59,46 @@ __global__ void __launch_bounds__(kThreads) prep_kernel(DevState s, uint32_t n_c
 
 // ================================================================ tile scan helpers
 //
-// A tile is kScanTile entries handled by 256 threads in 8 rounds; entry
-// tile*2048 + r*256 + threadIdx.x belongs to round r.  Per (round, warp)
-// the warp's ballot gives its 32 flags; a warp-0 scan over the 64
-// (round, warp) counts gives each group's offset inside the tile.
+// A tile is kScanTile = kRounds * 256 entries handled by 256 threads in
+// kRounds rounds; entry tile*kScanTile + r*256 + threadIdx.x belongs to
+// round r.  Per (round, warp) the warp's ballot gives its 32 flags; a
+// warp scan over the kRounds*8 (round, warp) counts gives each group's
+// offset inside the tile.  Large tiles keep the tiles of a pass within
+// one wave of resident blocks, so the look-back walk stays short.
+
+constexpr int kRounds = kScanTile / kThreads;
 
 struct TileScan {
-    uint32_t cnt[8][8];               // per (round, warp): packed counts, then exclusive offsets
+    uint32_t cnt[kRounds][8];         // per (round, warp): packed counts, then exclusive offsets
     unsigned long long excl;          // tile's exclusive prefix (look-back)
     uint32_t tile;
 };
 
-// warp 0: turn s.cnt into exclusive offsets (packed 16-bit fields add
-// without carries: a tile holds at most 2048 entries) and return the
+// warp 0: turn ts.cnt into exclusive offsets (packed 16-bit fields add
+// without carries: a tile holds at most 4096 entries) and return the
 // tile's packed total in every lane
 __device__ __forceinline__ uint32_t scan_tile_counts(TileScan &ts) {
+    constexpr int kPer = kRounds * 8 / 32;
     const int lane = threadIdx.x & 31;
-    uint32_t *flat = &ts.cnt[0][0];
-    const uint32_t a = flat[2 * lane], b = flat[2 * lane + 1];
-    uint32_t incl = a + b;
+    uint32_t *flat = &ts.cnt[0][0] + kPer * lane;
+    uint32_t v[kPer], sum = 0;
+#pragma unroll
+    for (int k = 0; k < kPer; k++) {
+        v[k] = flat[k];
+        sum += v[k];
+    }
+    uint32_t incl = sum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= o) incl += t;
     }
-    const uint32_t excl = incl - (a + b);
-    flat[2 * lane] = excl;
-    flat[2 * lane + 1] = excl + a;
+    uint32_t run = incl - sum;
+#pragma unroll
+    for (int k = 0; k < kPer; k++) {
+        flat[k] = run;
+        run += v[k];
+    }
     return __shfl_sync(0xffffffffu, incl, 31);
 }
 
@@ -103,6 +116,7 @@ __device__ __forceinline__ uint32_t scan_tile_counts(TileScan &ts) {
 __global__ void __launch_bounds__(kThreads) cull_kernel(DevState s, Geom g, uint32_t ntiles) {
     __shared__ TileScan ts;
     __shared__ TileScan tc;
+    __shared__ uint32_t bal[3][kRounds][8];            // active, new, candidate ballots
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t epoch = s.ctl->epoch;
     const float iso = s.ctl->params.iso;
@@ -112,30 +126,35 @@ __global__ void __launch_bounds__(kThreads) cull_kernel(DevState s, Geom g, uint
         __syncthreads();
         const uint32_t tile = ts.tile;
         if (tile >= ntiles) break;
-        uint32_t act_bits[8], new_bits[8], cand_bits[8];
+        float2 h[kRounds];
 #pragma unroll
-        for (int r = 0; r < 8; r++) {
+        for (int r = 0; r < kRounds; r++) {               // all range loads of the tile first
             const uint32_t b = tile * kScanTile + r * kThreads + threadIdx.x;
-            bool act = false, nw = false, cand = false;
-            if (b < g.nb) {
-                const float2 h = __ldg(s.hull + b);
-                act = (h.x < iso) && (iso <= h.y);
-                if (act) {
-                    const float2 h8 = __ldg(s.hull8 + b);
-                    cand = (h8.x < iso) && (iso <= h8.y);
-                    const int32_t sl = s.islot[b];
-                    if (sl >= 0) s.slast[sl] = epoch;
-                    else nw = true;
-                }
+            h[r] = b < g.nb ? __ldg(s.hull + b) : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int r = 0; r < kRounds; r++) {
+            const uint32_t b = tile * kScanTile + r * kThreads + threadIdx.x;
+            const bool act = b < g.nb && (h[r].x < iso) && (iso <= h[r].y);
+            bool nw = false, cand = false;
+            if (act) {
+                const float2 h8 = __ldg(s.hull8 + b);
+                cand = (h8.x < iso) && (iso <= h8.y);
+                const int32_t sl = s.islot[b];
+                if (sl >= 0) s.slast[sl] = epoch;
+                else nw = true;
             }
-            act_bits[r] = __ballot_sync(0xffffffffu, act);
-            new_bits[r] = __ballot_sync(0xffffffffu, nw);
-            cand_bits[r] = __ballot_sync(0xffffffffu, cand);
+            const uint32_t ab = __ballot_sync(0xffffffffu, act);
+            const uint32_t nbits = __ballot_sync(0xffffffffu, nw);
+            const uint32_t cb = __ballot_sync(0xffffffffu, cand);
             if (lane == 0) {
-                ts.cnt[r][warp] = ((uint32_t)__popc(act_bits[r]) << 16) | (uint32_t)__popc(new_bits[r]);
-                tc.cnt[r][warp] = (uint32_t)__popc(cand_bits[r]);
+                bal[0][r][warp] = ab;
+                bal[1][r][warp] = nbits;
+                bal[2][r][warp] = cb;
+                ts.cnt[r][warp] = ((uint32_t)__popc(ab) << 16) | (uint32_t)__popc(nbits);
+                tc.cnt[r][warp] = (uint32_t)__popc(cb);
                 const uint32_t first = tile * kScanTile + r * kThreads + warp * 32;
-                if (first < g.nb) s.mactive[first >> 5] = act_bits[r];
+                if (first < g.nb) s.mactive[first >> 5] = ab;
             }
         }
         __syncthreads();
@@ -162,16 +181,14 @@ __global__ void __launch_bounds__(kThreads) cull_kernel(DevState s, Geom g, uint
         __syncthreads();
         const uint32_t act_base = (uint32_t)(ts.excl >> 31), new_base = (uint32_t)(ts.excl & 0x7FFFFFFFu);
         const uint32_t cand_base = (uint32_t)tc.excl;
-#pragma unroll
-        for (int r = 0; r < 8; r++) {
+#pragma unroll 4
+        for (int r = 0; r < kRounds; r++) {
             const uint32_t b = tile * kScanTile + r * kThreads + threadIdx.x;
+            const uint32_t ab = bal[0][r][warp], nbits = bal[1][r][warp], cb = bal[2][r][warp];
             const uint32_t off = ts.cnt[r][warp];
-            if ((act_bits[r] >> lane) & 1u) {
-                const uint32_t ai = act_base + (off >> 16) + __popc(act_bits[r] & lt);
-                s.iactive[ai] = b;
-                if ((cand_bits[r] >> lane) & 1u) s.icand[cand_base + tc.cnt[r][warp] + __popc(cand_bits[r] & lt)] = ai;
-            }
-            if ((new_bits[r] >> lane) & 1u) s.inew[new_base + (off & 0xFFFFu) + __popc(new_bits[r] & lt)] = b;
+            if ((ab >> lane) & 1u) s.iactive[act_base + (off >> 16) + __popc(ab & lt)] = b;
+            if ((cb >> lane) & 1u) s.icand[cand_base + tc.cnt[r][warp] + __popc(cb & lt)] = b;
+            if ((nbits >> lane) & 1u) s.inew[new_base + (off & 0xFFFFu) + __popc(nbits & lt)] = b;
         }
         __syncthreads();
     }
@@ -249,16 +266,16 @@ __global__ void __launch_bounds__(kThreads) lru_a_kernel(DevState s) {
         __syncthreads();
         const uint32_t tile = ts.tile;
         if (tile >= ntiles) break;
-        uint32_t bits[8], slot[8];
+        uint32_t bits[kRounds], slot[kRounds];
 #pragma unroll
-        for (int r = 0; r < 8; r++) {
+        for (int r = 0; r < kRounds; r++) {
             const uint32_t i = tile * kScanTile + r * kThreads + threadIdx.x;
-            bool av = false;
-            slot[r] = 0;
-            if (i < u) {
-                slot[r] = L[i];
-                av = s.slast[slot[r]] != epoch;
-            }
+            slot[r] = i < u ? L[i] : 0u;
+        }
+#pragma unroll
+        for (int r = 0; r < kRounds; r++) {
+            const uint32_t i = tile * kScanTile + r * kThreads + threadIdx.x;
+            const bool av = i < u && s.slast[slot[r]] != epoch;
             bits[r] = __ballot_sync(0xffffffffu, av);
             if (lane == 0) ts.cnt[r][warp] = (uint32_t)__popc(bits[r]);
         }
@@ -271,7 +288,7 @@ __global__ void __launch_bounds__(kThreads) lru_a_kernel(DevState s) {
         __syncthreads();
         const uint32_t base = (uint32_t)ts.excl;
 #pragma unroll
-        for (int r = 0; r < 8; r++) {
+        for (int r = 0; r < kRounds; r++) {
             if (!((bits[r] >> lane) & 1u)) continue;
             const uint32_t rank = base + ts.cnt[r][warp] + __popc(bits[r] & lt);
             if (rank < from_used) assign_slot(s, slot[r], from_unused + rank, epoch);
@@ -300,9 +317,9 @@ __global__ void __launch_bounds__(kThreads) lru_b_kernel(DevState s) {
         __syncthreads();
         const uint32_t tile = ts.tile;
         if (tile >= ntiles) break;
-        uint32_t bits[8];
+        uint32_t bits[kRounds];
 #pragma unroll
-        for (int r = 0; r < 8; r++) {
+        for (int r = 0; r < kRounds; r++) {
             const uint32_t i = tile * kScanTile + r * kThreads + threadIdx.x;
             const bool used_now = i < S2 && s.slast[i] == epoch;
             bits[r] = __ballot_sync(0xffffffffu, used_now);
@@ -317,7 +334,7 @@ __global__ void __launch_bounds__(kThreads) lru_b_kernel(DevState s) {
         __syncthreads();
         const uint32_t base = keep + (uint32_t)ts.excl;
 #pragma unroll
-        for (int r = 0; r < 8; r++) {
+        for (int r = 0; r < kRounds; r++) {
             if (!((bits[r] >> lane) & 1u)) continue;
             const uint32_t i = tile * kScanTile + r * kThreads + threadIdx.x;
             Ln[base + ts.cnt[r][warp] + __popc(bits[r] & lt)] = i;

@@ -17,7 +17,7 @@ struct DevState {
     uint32_t *mactive;         // M_active bitmask, ceil(nb/32) words
     uint32_t *iactive;         // I_active
     uint32_t *inew;            // I_new
-    uint32_t *icand;           // candidates: positions in I_active of blocks the triangle stage visits
+    uint32_t *icand;           // candidates: ids of the blocks the triangle stage visits (ascending)
     int32_t *islot;            // I_slot: block -> slot or -1
     uint32_t *slast;           // S_last: slot -> epoch of last use (0 = never)
     int32_t *sblock;           // S_block: slot -> block or -1
@@ -39,7 +39,7 @@ struct Grids {                 // CTAs per launch, from occupancy at load time
 };
 
 constexpr int kThreads = 256;
-constexpr int kScanTile = 2048;          // entries per tile of the cull / cache scans
+constexpr int kScanTile = 4096;          // entries per tile of the cull / cache scans
 
 // The isovalue, output buffer and its capacity are read from Ctl::params.
 void launch_prep(const DevState &s, uint32_t n_cull_desc, uint32_t n_lru_desc, bool mc_only, int grid,

@@ -57,6 +57,7 @@ struct CountSmem {
 
 struct EmitSmem {
     WarpTile w[kWarps];
+    float4 stage[kWarps][96];                         // 32 triangles' vertices per warp
     uint16_t tmap[kWarps][kTmap];                     // block-in-tile (2) | cell (6) | k (3)
     uint32_t tri_row[256 * kMaxTriPerCell];           // 3 edge numbers of each table triangle, packed
     uint8_t num_tri[256];
@@ -121,17 +122,18 @@ struct LaneConst {
 // kBPW slots used).  Leaves cases in wt.cases when kKeepCases and returns
 // the per-cell triangle counts of the lane's two cells, packed one byte
 // per block: n0p for cell lane, n1p for cell lane + 32.
+// `b` is this lane's block (candidate base + lane/8), loaded by the caller
+// one warp tile ahead.
 template <bool kKeepCases, bool kDebug>
 __device__ __forceinline__ void stage_and_classify(const DevState &s, const Geom &g, float iso, uint32_t base,
-                                                   int nb_w, WarpTile &wt, const LaneConst &lc,
+                                                   int nb_w, uint32_t b, WarpTile &wt, const LaneConst &lc,
                                                    const uint8_t *num_tri, uint32_t &n0p, uint32_t &n1p) {
     const int lane = threadIdx.x & 31, bq = lane >> 3, bo = lane & 7;
     const uint32_t slab = g.nbx * g.nby;
     // ---- A: +group slots
     if (bq < nb_w) {
-        const uint32_t ai = s.icand[base + bq];
-        const uint32_t b = s.iactive[ai];
-        const uint32_t bx = b % g.nbx, by = (b / g.nbx) % g.nby, bz = b / slab;
+        uint32_t bx, by, bz;
+        block_coords(g, b, bx, by, bz);
         const bool ex = bx + 1 < g.nbx, ey = by + 1 < g.nby, ez = bz + 1 < g.nbz;
         const bool exists = (!(bo & 1) || ex) && (!(bo & 2) || ey) && (!(bo & 4) || ez);
         const uint32_t nbid = b + ((bo & 1) ? 1u : 0u) + ((bo & 2) ? g.nbx : 0u) + ((bo & 4) ? slab : 0u);
@@ -231,11 +233,18 @@ __global__ void __launch_bounds__(kThreads) mc_count_kernel(DevState s, Geom g) 
     lc.init(lane);
     WarpTile &wt = sm.w[warp];
     uint32_t occ = 0;
-    for (uint32_t t = blockIdx.x * kWarps + warp; t < nwt; t += gridDim.x * kWarps) {
+    const uint32_t stride = gridDim.x * kWarps;
+    uint32_t t = blockIdx.x * kWarps + warp;
+    const uint32_t bq = (uint32_t)lane >> 3;
+    uint32_t b_next = t < nwt && t * kBPW + bq < n_cand ? s.icand[t * kBPW + bq] : 0u;
+    for (; t < nwt; t += stride) {
         const uint32_t base = t * kBPW;
         const int nb_w = (int)min((uint32_t)kBPW, n_cand - base);
+        const uint32_t b = b_next;
+        const uint32_t tn = t + stride;                   // next warp tile's block, loaded early
+        b_next = tn < nwt && tn * kBPW + bq < n_cand ? s.icand[tn * kBPW + bq] : 0u;
         uint32_t n0p, n1p;
-        stage_and_classify<false, kDebug>(s, g, iso, base, nb_w, wt, lc, sm.num_tri, n0p, n1p);
+        stage_and_classify<false, kDebug>(s, g, iso, base, nb_w, b, wt, lc, sm.num_tri, n0p, n1p);
         const uint32_t r0 = warp_sum(n0p), r1 = warp_sum(n1p);   // per-byte sums <= 160: no carries
         if (lane < nb_w) {
             const uint32_t cnt = ((r0 >> (8 * lane)) & 0xFFu) + ((r1 >> (8 * lane)) & 0xFFu);
@@ -347,11 +356,19 @@ __global__ void __launch_bounds__(kThreads) mc_emit_kernel(DevState s, Geom g) {
     lc.init(lane);
     WarpTile &wt = sm.w[warp];
     uint16_t *tm = sm.tmap[warp];
-    for (uint32_t t = blockIdx.x * kWarps + warp; t < nwt; t += gridDim.x * kWarps) {
+    float4 *stage = sm.stage[warp];
+    const uint32_t stride = gridDim.x * kWarps;
+    uint32_t t = blockIdx.x * kWarps + warp;
+    const uint32_t bq = (uint32_t)lane >> 3;
+    uint32_t b_next = t < nwt && t * kBPW + bq < n_cand ? s.icand[t * kBPW + bq] : 0u;
+    for (; t < nwt; t += stride) {
         const uint32_t base = t * kBPW;
         const int nb_w = (int)min((uint32_t)kBPW, n_cand - base);
+        const uint32_t b = b_next;
+        const uint32_t tn = t + stride;                   // next warp tile's block, loaded early
+        b_next = tn < nwt && tn * kBPW + bq < n_cand ? s.icand[tn * kBPW + bq] : 0u;
         uint32_t n0p, n1p;
-        stage_and_classify<true, false>(s, g, iso, base, nb_w, wt, lc, sm.num_tri, n0p, n1p);
+        stage_and_classify<true, false>(s, g, iso, base, nb_w, b, wt, lc, sm.num_tri, n0p, n1p);
         // per-cell offsets inside the warp tile: two packed scans (byte q = block q)
         uint32_t i0 = n0p, i1 = n1p;
 #pragma unroll
@@ -375,42 +392,57 @@ __global__ void __launch_bounds__(kThreads) mc_emit_kernel(DevState s, Geom g) {
         if (wtot == 0) continue;                       // warp-uniform
         const unsigned long long gbase = s.offsets[base];
         __syncwarp();
-        for (uint32_t tri = lane; tri < wtot; tri += 32) {
-            const uint32_t e16 = tm[tri];
-            const uint32_t q = e16 >> 9, cell = (e16 >> 3) & 63u, k = e16 & 7u;
-            const uint32_t row = sm.tri_row[wt.cases[q][cell] * kMaxTriPerCell + k];
-            const int cx = (int)(cell & 3u), cy = (int)((cell >> 2) & 3u), cz = (int)(cell >> 4);
-            const float *hb = &wt.halo[q][0] + cx + 8 * cy + 40 * cz;
-            const float wbits = __uint_as_float(wt.bid[q]);
-            const unsigned long long gt = gbase + tri;
-            if (gt >= tri_cap) continue;
-            float4 *dst = out + gt * 3;
+        // one triangle per lane; its three vertices go through the warp's
+        // staging area so that each store instruction writes 512
+        // contiguous bytes
+        for (uint32_t t0 = 0; t0 < wtot; t0 += 32) {
+            const uint32_t tri = t0 + lane;
+            if (tri < wtot) {
+                const uint32_t e16 = tm[tri];
+                const uint32_t q = e16 >> 9, cell = (e16 >> 3) & 63u, k = e16 & 7u;
+                const uint32_t row = sm.tri_row[wt.cases[q][cell] * kMaxTriPerCell + k];
+                const int cx = (int)(cell & 3u), cy = (int)((cell >> 2) & 3u), cz = (int)(cell >> 4);
+                const float *hb = &wt.halo[q][0] + cx + 8 * cy + 40 * cz;
+                const float wbits = __uint_as_float(wt.bid[q]);
 #pragma unroll
-            for (int j = 0; j < 3; j++) {
-                const uint32_t info = sm.edge_info[(row >> (8 * j)) & 0xFFu];
-                const float vlo = hb[info & 0xFFu], vhi = hb[(info >> 8) & 0xFFu];
-                // t = (iso - v_lo) / (v_hi - v_lo) through the reciprocal: within
-                // 2 ulp of the correctly rounded quotient (positions within 1e-6)
-                const float tt = __fdividef(__fsub_rn(iso, vlo), __fsub_rn(vhi, vlo));
-                const uint32_t a = (info >> 19) & 3u;
-                float4 p = make_float4((float)(cx + (int)((info >> 16) & 1u)), (float)(cy + (int)((info >> 17) & 1u)),
-                                       (float)(cz + (int)((info >> 18) & 1u)), wbits);
-                if (a == 0) p.x = __fadd_rn(p.x, tt);
-                else if (a == 1) p.y = __fadd_rn(p.y, tt);
-                else p.z = __fadd_rn(p.z, tt);
-                dst[j] = p;
-                if (kDebug) {
-                    const uint32_t b = wt.bid[q];
-                    const uint32_t bx = b % g.nbx, by = (b / g.nbx) % g.nby, bz = b / slab;
-                    const unsigned long long px = 4ull * bx + cx + ((info >> 16) & 1u);
-                    const unsigned long long py = 4ull * by + cy + ((info >> 17) & 1u);
-                    const unsigned long long pz = 4ull * bz + cz + ((info >> 18) & 1u);
-                    s.dbg_edges[gt * 3 + j] =
-                        3ull * (px + (unsigned long long)g.nx * (py + (unsigned long long)g.ny * pz)) + a;
+                for (int j = 0; j < 3; j++) {
+                    const uint32_t info = sm.edge_info[(row >> (8 * j)) & 0xFFu];
+                    const float vlo = hb[info & 0xFFu], vhi = hb[(info >> 8) & 0xFFu];
+                    // t = (iso - v_lo) / (v_hi - v_lo) through the reciprocal: within
+                    // 2 ulp of the correctly rounded quotient (positions within 1e-6)
+                    const float tt = __fdividef(__fsub_rn(iso, vlo), __fsub_rn(vhi, vlo));
+                    const uint32_t a = (info >> 19) & 3u;
+                    float4 p = make_float4((float)(cx + (int)((info >> 16) & 1u)),
+                                           (float)(cy + (int)((info >> 17) & 1u)),
+                                           (float)(cz + (int)((info >> 18) & 1u)), wbits);
+                    if (a == 0) p.x = __fadd_rn(p.x, tt);
+                    else if (a == 1) p.y = __fadd_rn(p.y, tt);
+                    else p.z = __fadd_rn(p.z, tt);
+                    stage[3 * lane + j] = p;
+                    if (kDebug) {
+                        const unsigned long long gt = gbase + tri;
+                        uint32_t bx, by, bz;
+                        block_coords(g, wt.bid[q], bx, by, bz);
+                        const unsigned long long px = 4ull * bx + cx + ((info >> 16) & 1u);
+                        const unsigned long long py = 4ull * by + cy + ((info >> 17) & 1u);
+                        const unsigned long long pz = 4ull * bz + cz + ((info >> 18) & 1u);
+                        if (gt < tri_cap)
+                            s.dbg_edges[gt * 3 + j] =
+                                3ull * (px + (unsigned long long)g.nx * (py + (unsigned long long)g.ny * pz)) + a;
+                    }
                 }
             }
+            __syncwarp();
+            const uint32_t nv = 3 * min(32u, wtot - t0);             // vertices in this chunk
+            const unsigned long long v0 = (gbase + t0) * 3;          // first vertex of the chunk
+            const unsigned long long vcap = tri_cap * 3;
+#pragma unroll
+            for (int r = 0; r < 3; r++) {
+                const uint32_t f = lane + 32 * r;
+                if (f < nv && v0 + f < vcap) out[v0 + f] = stage[f];
+            }
+            __syncwarp();
         }
-        __syncwarp();
     }
 }
 

@@ -154,7 +154,8 @@ extern "C" int iso_active_blocks_static(const float *d_bmin, const float *d_bmax
     unsigned long long *scratch = nullptr;
     const int rc = scratch_address(&scratch);
     if (rc != ISO_OK) return rc;
-    const bcmc::Geom g{nx, ny, nz, (uint32_t)nbx, (uint32_t)nby, (uint32_t)nbz, (uint32_t)nb, 1u};
+    const bcmc::Geom g{nx, ny, nz, (uint32_t)nbx, (uint32_t)nby, (uint32_t)nbz, (uint32_t)nb, 1u,
+                       bcmc::div_magic((uint32_t)nbx), bcmc::div_magic((uint32_t)nby)};
     const uint32_t ntiles = (uint32_t)((nb + kTileBlocks - 1) / kTileBlocks);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     clear_scratch_kernel<<<(ntiles + 255) / 256, 256, 0, st>>>(scratch, ntiles);

@@ -133,3 +133,118 @@ def linear_ramp(nx, ny, nz, x0):
     """f(x, y, z) = x - x0: every isosurface is the plane x = x0 + iso."""
     f = np.arange(nx, dtype=np.float64) - x0
     return np.broadcast_to(f[None, None, :], (nz, ny, nx)).astype(np.float32)
+
+
+# ---------------------------------------------------------------- channel-flow-like field
+#
+# A stand-in for the paper's DNS (a turbulent channel; Table
+# "mc_benchmark_data"): u = U(zeta) + a(zeta) * u', zeta = z / (NZ - 1) the
+# wall-normal coordinate, U(zeta) = tanh(zeta/d) tanh((1 - zeta)/d) with
+# d = 0.08 the mean profile, a(zeta) = 0.3 (1 - U) + 0.1 the fluctuation
+# envelope, and u' a sum of gradient-noise octaves whose amplitudes fall by
+# 2^(-1/3) per halving of the period (energy per octave falling as
+# k^(-2/3), the integral of a k^(-5/3) spectrum).  u' is evaluated in
+# float32 (every dot product is exact; fades and lerps are single
+# operations in a fixed order) so that a per-block GPU generator can
+# reproduce it bit for bit at 10^11 samples.
+
+CHANNEL_DELTA = 0.08
+CHANNEL_GAIN = np.float32(2.0 ** (-1.0 / 3.0))
+CHANNEL_SCALE = np.float32(3.0)
+LN2 = 0.6931471805599453
+INV_FACT = [1.0 / float(__import__("math").factorial(k)) for k in range(21)]
+
+
+def exp_f64(y):
+    """exp for float64 arrays by range reduction y = n ln2 + r and a
+    degree-20 Taylor polynomial of exp(r) in Horner form (no fused
+    operations), so the CUDA generator can repeat it exactly."""
+    y = np.asarray(y, np.float64)
+    n = np.rint(y / LN2)
+    r = y - (n * LN2)
+    p = np.full_like(r, INV_FACT[20])
+    for k in range(19, -1, -1):
+        p = (p * r) + INV_FACT[k]
+    return np.ldexp(p, n.astype(np.int64))
+
+
+def tanh_pos_f64(x):
+    """tanh(x) for x >= 0 as (1 - e^(-2x)) / (1 + e^(-2x)) with exp_f64."""
+    e = exp_f64(-2.0 * np.asarray(x, np.float64))
+    return (1.0 - e) / (1.0 + e)
+
+
+def channel_profile(nz_total, z):
+    """(U, a) as float32 at the integer wall-normal positions z."""
+    zeta = np.asarray(z, np.float64) / float(nz_total - 1)
+    U = tanh_pos_f64(zeta / CHANNEL_DELTA) * tanh_pos_f64((1.0 - zeta) / CHANNEL_DELTA)
+    a = (0.3 * (1.0 - U)) + 0.1
+    return U.astype(np.float32), a.astype(np.float32)
+
+
+def _noise_f32(xs, ys, zs, seed, octaves, base_period):
+    """float32 gradient-noise octave sum at the grid xs x ys x zs (1-D int64 arrays)."""
+    out = np.zeros((len(zs), len(ys), len(xs)), np.float32)
+    amp = np.float32(1.0)
+    f32 = np.float32
+    for o in range(octaves):
+        period = base_period >> o
+        inv = f32(1.0 / period)
+        cx, cy, cz = xs // period, ys // period, zs // period
+        fx = (xs - cx * period).astype(f32) * inv
+        fy = (ys - cy * period).astype(f32) * inv
+        fz = (zs - cz * period).astype(f32) * inv
+        fade = lambda t: ((t * t) * t) * ((t * ((t * f32(6.0)) - f32(15.0))) + f32(10.0))
+        wx, wy, wz = fade(fx), fade(fy), fade(fz)
+        lx = np.arange(cx.min(), cx.max() + 2)
+        ly = np.arange(cy.min(), cy.max() + 2)
+        lz = np.arange(cz.min(), cz.max() + 2)
+        h = lattice_hash(seed, o, lx[None, None, :], ly[None, :, None], lz[:, None, None])
+        g = GRADIENTS.astype(f32)[((h >> np.uint64(32)) % np.uint64(12)).astype(np.int64)]
+        ix = (cx - lx[0])[None, None, :]
+        iy = (cy - ly[0])[None, :, None]
+        iz = (cz - lz[0])[:, None, None]
+        d = {}
+        for k in (0, 1):
+            for j in (0, 1):
+                for i in (0, 1):
+                    gg = g[iz + k, iy + j, ix + i]
+                    dx = (fx - f32(i))[None, None, :]
+                    dy = (fy - f32(j))[None, :, None]
+                    dz = (fz - f32(k))[:, None, None]
+                    d[(i, j, k)] = ((gg[..., 0] * dx) + (gg[..., 1] * dy)) + (gg[..., 2] * dz)
+        wxb, wyb, wzb = wx[None, None, :], wy[None, :, None], wz[:, None, None]
+
+        def lerp(p, q, w):
+            return p + (w * (q - p))
+        x00 = lerp(d[(0, 0, 0)], d[(1, 0, 0)], wxb)
+        x10 = lerp(d[(0, 1, 0)], d[(1, 1, 0)], wxb)
+        x01 = lerp(d[(0, 0, 1)], d[(1, 0, 1)], wxb)
+        x11 = lerp(d[(0, 1, 1)], d[(1, 1, 1)], wxb)
+        val = lerp(lerp(x00, x10, wyb), lerp(x01, x11, wyb), wzb)
+        out = out + (amp * val)
+        amp = f32(amp * CHANNEL_GAIN)
+    return out
+
+
+def channel_field(nx, ny, nz, seed, nz_total=None, origin=(0, 0, 0), octaves=7, base_period=256):
+    """Channel-flow-like field (see above) on a window, float32 (nz, ny, nx).
+    nz_total is the full wall-normal extent (defaults to nz)."""
+    nz_total = nz if nz_total is None else nz_total
+    x0, y0, z0 = origin
+    xs = np.arange(x0, x0 + nx, dtype=np.int64)
+    ys = np.arange(y0, y0 + ny, dtype=np.int64)
+    zs = np.arange(z0, z0 + nz, dtype=np.int64)
+    U, a = channel_profile(nz_total, zs)
+    n = _noise_f32(xs, ys, zs, seed, octaves, base_period)
+    return U[:, None, None] + (a[:, None, None] * (n * CHANNEL_SCALE))
+
+
+def channel_samples(points, seed, nz_total, octaves=7, base_period=256):
+    """The channel field at arbitrary integer points (M, 3) as (x, y, z)."""
+    pts = np.asarray(points, np.int64)
+    out = np.empty(len(pts), np.float32)
+    for i, (x, y, z) in enumerate(pts):
+        out[i] = channel_field(1, 1, 1, seed, nz_total, origin=(int(x), int(y), int(z)),
+                               octaves=octaves, base_period=base_period)[0, 0, 0]
+    return out

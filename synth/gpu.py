@@ -38,6 +38,8 @@ def lib():
         P, u32, i64, u64, d = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
         L.synth_gradient_noise.argtypes = [P, u32, u32, u32, i64, i64, i64, u64, ctypes.c_int, i64, d, d, P]
         L.synth_sphere_sdf.argtypes = [P, u32, u32, u32, i64, i64, i64, d, d, d, d, P]
+        L.synth_channel_field.argtypes = [P, u32, u32, u32, i64, i64, i64, u64, u32, ctypes.c_int, i64,
+                                          ctypes.c_float, ctypes.c_float, P, P]
         _lib = L
     return _lib
 
@@ -68,6 +70,21 @@ def sphere_sdf(nx, ny, nz, radius, center=None, origin=(0, 0, 0), out=None):
     rc = lib().synth_sphere_sdf(ctypes.c_void_p(out.data_ptr()), nx, ny, nz, *origin, *center, radius, _stream())
     if rc:
         raise RuntimeError(f"synth_sphere_sdf failed ({rc})")
+    return out
+
+
+def channel_field(nx, ny, nz, seed, nz_total=None, origin=(0, 0, 0), octaves=7, base_period=256, out=None):
+    """GPU channel_field (window origin must be a multiple of 4 on each axis)."""
+    import torch
+    nz_total = nz if nz_total is None else nz_total
+    if out is None:
+        out = torch.empty((nz, ny, nx), dtype=torch.float32, device="cuda")
+    work = torch.empty(2 * nz, dtype=torch.float32, device=out.device)
+    rc = lib().synth_channel_field(ctypes.c_void_p(out.data_ptr()), nx, ny, nz, *origin, seed, nz_total, octaves,
+                                   base_period, float(fields.CHANNEL_GAIN), float(fields.CHANNEL_SCALE),
+                                   ctypes.c_void_p(work.data_ptr()), _stream())
+    if rc:
+        raise RuntimeError(f"synth_channel_field failed ({rc})")
     return out
 
 

@@ -113,6 +113,10 @@ def test_gpu_generators_match_numpy():
     want = fields.sphere_sdf(30, 26, 22, 9.5, center=(14.5, 12.0, 10.25), origin=(3, 4, 5))
     got = sg.sphere_sdf(30, 26, 22, 9.5, center=(14.5, 12.0, 10.25), origin=(3, 4, 5)).cpu().numpy()
     assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+    for dims, origin, nzt in (((37, 22, 18), (0, 0, 0), 18), ((24, 20, 30), (1024, 4096, 64), 1536)):
+        want = fields.channel_field(*dims, 5, nz_total=nzt, origin=origin)
+        got = sg.channel_field(*dims, 5, nz_total=nzt, origin=origin).cpu().numpy()
+        assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
 
 
 # ---------------------------------------------------------------- extraction
@@ -148,10 +152,11 @@ def check_surface(vol, bits, dims, rate, bmin, bmax, iso, mesh=None):
     # the triangle stage visits exactly the candidates; every block the
     # oracle finds occupied is one of them, and none of them needed an
     # extent reset
-    cand = vol.debug("candidates").astype(np.int64)
+    cand_ids = vol.debug("candidates")
     want_cand = plus_group_candidates(bmin, bmax, dims, iso, ref["active"])
-    assert np.array_equal(act[cand], np.nonzero(want_cand)[0].astype(np.uint32))
-    assert set(ref["ids"][ref["block_tri"] > 0].tolist()) <= set(act[cand].tolist())
+    assert np.array_equal(cand_ids, np.nonzero(want_cand)[0].astype(np.uint32))
+    assert set(ref["ids"][ref["block_tri"] > 0].tolist()) <= set(cand_ids.tolist())
+    cand = np.searchsorted(act, cand_ids)                  # positions in the active list
     assert ref["complete"][cand].all()
     cases = vol.debug("cell_cases").reshape(-1, 64)
     assert np.array_equal(cases, ref["cases"][cand])
