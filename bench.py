@@ -53,9 +53,13 @@ CPU_WINDOW = (256, 256, 128)      # oracle sample: a window of the same field
 CPU_ORIGIN = (128, 128, 192)
 REF_WINDOW = (128, 128, 64)       # per-step sample of the reference arm
 L2_FLUSH_BYTES = 512 << 20
-CTL_BYTES = 104                   # control block read back once per surface
-KERNELS_PER_SURFACE = 6           # prep, cull, lru_a, lru_b, decode, mc
+CTL_BYTES = 120                   # control block read back once per surface
+KERNELS_PER_SURFACE = 8           # prep, cull, lru_a, lru_b, decode, count, scan, emit
 KERNELS_PER_RESET = 2
+KERNELS = ("cull", "cache_update", "decode", "count", "scan", "emit")
+KERNEL_OF = {"cull": ("cull_kernel", "extract.cu"), "cache_update": ("lru_a_kernel+lru_b_kernel", "extract.cu"),
+             "decode": ("decode_new_kernel", "extract.cu"), "count": ("mc_count_kernel", "mc.cu"),
+             "scan": ("mc_scan_kernel", "mc.cu"), "emit": ("mc_emit_kernel", "mc.cu")}
 
 
 def parse():
@@ -66,6 +70,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-volume batch comparison")
     ap.add_argument("--dims", type=int, default=512,
                     help="cube edge of the noise volume (default 512; smaller sizes are for profiling captures)")
     return ap.parse_args()
@@ -158,14 +163,22 @@ def profile_traffic(kernel_file, kernel):
 
 
 def stage_bytes(stats, rate, nb):
-    """Algorithmic bytes each stage must move for one surface."""
+    """Algorithmic bytes each kernel must move for one surface."""
     na, nn, nc, T = stats["n_active"], stats["n_new"], stats["n_candidates"], stats["num_triangles"]
     return {
         "cull": 8 * nb + nb / 8 + 4 * na + 4 * nn + 8 * na + 4 * nc,   # hulls, mask, I_active, I_new, +group hulls, I_cand
         "cache_update": 0.0,
         "decode": nn * (8 * rate + 256 + 8),                           # compressed in, decoded out, I_new + slot
-        "triangles": nc * (256 + 8 + 12) + 48 * T,                     # decoded candidate tiles in, ids, counts/offsets, vertices out
+        "count": nc * (256 + 4 + 4),                                   # decoded tiles in, id in, count out
+        "scan": nc * (4 + 8),                                          # counts in, offsets out
+        "emit": nc * (256 + 4 + 8) + 48 * T,                           # decoded tiles, id, offset in; vertices out
     }
+
+
+def bytes_bj(stats, rate):
+    """Bytes the method must move per extraction by the headline formula:
+    compressed blocks read + decoded blocks written + vertices written."""
+    return stats["n_new"] * (8 * rate + 256) + 48 * stats["num_triangles"]
 
 
 # ---------------------------------------------------------------- CPU oracle baseline
@@ -218,6 +231,71 @@ def run_reference(args):
             "cpu_baseline": {"value": value, "unit": "triangles/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "triangles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- batch of 64 volumes
+
+def measure_batch64(bc, sg, torch, stream, flush, steps):
+    """64 volumes of uneven size (each axis log-uniform in [32, 256]), each
+    with its own isovalue: one batch (one launch per stage for all volumes,
+    replayed as a CUDA graph) against 64 iso_extract_into calls (the plain
+    per-request path), from cold caches and from warm ones."""
+    from synth import recipes
+    recs = recipes.batch64_recipes()
+    vols = []
+    for r in recs:
+        f = sg.generate(r)
+        bits, bmin, bmax = bc.encode_field(f, r.rate)
+        torch.cuda.synchronize()
+        del f
+        vols.append(bc.Volume(bits, r.dims, r.rate, bmin, bmax))
+    isos = np.array([r.isovalues[0] for r in recs], np.float32)
+    voxels = float(sum(np.prod(r.dims) for r in recs))
+    b = bc.Batch(vols)
+    _, offs, _ = b.extract(isos)
+    total = int(offs[-1])
+    out = torch.empty((total + 1024, 3, 4), dtype=torch.float32, device="cuda")
+    parts = [out[int(offs[i]):int(offs[i + 1])] for i in range(len(vols))]
+
+    def timed(fn, cold):
+        ms = []
+        for _ in range(max(3, steps) + 2):
+            if cold:
+                for v in vols:
+                    v.cache_reset()
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return float(np.median(ms[2:]))
+
+    def batch_call():
+        b.extract_into(isos, out)
+
+    def plain_calls():
+        for i, v in enumerate(vols):
+            v.extract_into(float(isos[i]), parts[i])
+
+    res = {"volumes": len(vols), "voxels": voxels, "triangles": total}
+    for cold in (True, False):
+        key = "cold" if cold else "warm"
+        tb, tp = timed(batch_call, cold), timed(plain_calls, cold)
+        res[key] = {"batch_ms": tb, "plain_ms": tp, "speedup": tp / tb,
+                    "batch_triangles_per_s": total / (tb / 1000.0), "plain_triangles_per_s": total / (tp / 1000.0)}
+    tune = b.tune(isos, out, trials=2)
+    tb = timed(batch_call, True)
+    res["tuned"] = {"shape": tune["shape"], "cold_batch_ms": tb, "tuner_default_ms": tune["default_ms"],
+                    "tuner_tuned_ms": tune["tuned_ms"], "cold_speedup_vs_plain": res["cold"]["plain_ms"] / tb}
+    res["what"] = ("batch: iso_batch_extract (one launch per stage over all 64 volumes, CUDA graph); plain: 64 "
+                   "iso_extract_into calls in sequence; device time (CUDA events) per whole batch, median")
+    b.release()
+    for v in vols:
+        v.release()
+    return res
 
 
 # ---------------------------------------------------------------- our arm
@@ -294,12 +372,11 @@ def run_ours(args):
             dist.all_reduce(n)
             total_tris = float(n.item())
 
-        # per-stage durations (same steps, events between the stages)
+        # per-kernel durations (same steps, events between the kernels)
         vol.set_profiling(True)
         stage_ms = {k: 0.0 for k in bc.Volume.STAGES}
-        stage_b = {"cull": 0.0, "cache_update": 0.0, "decode": 0.0, "triangles": 0.0}
+        stage_b = {k: 0.0 for k in KERNELS}
         prof_steps = max(1, min(args.steps, 5))
-        launches = {"decode": 0, "triangles": 0}
         for _ in range(prof_steps):
             flush.zero_()
             vol.cache_reset()
@@ -308,11 +385,27 @@ def run_ours(args):
                 ms = vol.stage_times()
                 for k in stage_ms:
                     stage_ms[k] += ms[k]
-                for k, b in stage_bytes(st, RATE, nb).items():
-                    stage_b[k] += b
-                launches["decode"] += 1
-                launches["triangles"] += 1
+                for k, nbytes in stage_bytes(st, RATE, nb).items():
+                    stage_b[k] += nbytes
         vol.set_profiling(False)
+
+        # whole extractions from a cold cache (every active block decoded),
+        # against the bytes the method must move
+        cold_ms, cold_b, cold_t = 0.0, 0.0, 0
+        for _ in range(prof_steps):
+            for iso in ISOS:
+                vol.cache_reset()
+                flush.zero_()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                st = vol.extract_into(iso, out)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                cold_ms += e0.elapsed_time(e1)
+                cold_b += bytes_bj(st, RATE)
+                cold_t += st["num_triangles"]
+        n_cold = prof_steps * len(ISOS)
 
         # end to end through the public API from pinned host memory
         e2e = None
@@ -346,6 +439,7 @@ def run_ours(args):
                    "includes": "iso_load_volume from pinned host (upload + allocation + block hulls), "
                                "5 x iso_extract (device-allocated meshes), count readback, release"}
         vol.release()
+        batch = None if args.no_batch else measure_batch64(bc, sg, torch, stream, flush, args.steps)
 
     if rank != 0:
         dist.barrier() if world > 1 else None
@@ -353,19 +447,21 @@ def run_ours(args):
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     peak_src = "measured" if peaks else "fallback"
-    dominant = max(("cull", "cache_update", "decode", "triangles"), key=lambda k: stage_ms[k])
-    kernel_of = {"cull": "cull_kernel", "cache_update": "lru_kernels", "decode": "decode_new_kernel",
-                 "triangles": "mc_kernel"}
-    file_of = {"cull": "extract.cu", "cache_update": "extract.cu", "decode": "extract.cu", "triangles": "extract.cu"}
+    dominant = max(KERNELS, key=lambda k: stage_ms[k])
     n_launch = prof_steps * len(ISOS)
     ach = stage_b[dominant] / n_launch / (stage_ms[dominant] / n_launch / 1000.0) / 1e9
     stages = {}
-    for k in ("cull", "cache_update", "decode", "triangles"):
+    for k in KERNELS:
         ms = stage_ms[k] / n_launch
         gbs = (stage_b[k] / n_launch) / (ms / 1000.0) / 1e9 if ms > 0 and stage_b[k] > 0 else None
-        stages[k] = {"ms_per_surface": ms, "alg_bytes_per_surface": stage_b[k] / n_launch,
+        stages[k] = {"kernel": KERNEL_OF[k][0], "ms_per_surface": ms, "alg_bytes_per_surface": stage_b[k] / n_launch,
                      "GBps": gbs, "frac_of_measured_hbm": (gbs / peak) if gbs else None}
     stages["prep"] = {"ms_per_surface": stage_ms["prep"] / n_launch}
+    cold_gbs = cold_b / (cold_ms / 1000.0) / 1e9
+    cold = {"ms_per_surface": cold_ms / n_cold, "bytes_per_surface": cold_b / n_cold, "GBps": cold_gbs,
+            "frac": cold_gbs / peak, "triangles_per_s": cold_t / (cold_ms / 1000.0),
+            "bytes": "n_new*(8R + 256) + 48T: compressed blocks read, decoded blocks written, vertices written",
+            "what": "one whole extraction (all kernels, count readback) from an empty cache, device time"}
     lat_ms = sorted(1000 * x for x in lat)
     value = total_tris / total_s
     ms_per_step = 1000 * total_s / args.steps
@@ -381,10 +477,12 @@ def run_ours(args):
                    "triangles_per_surface": [s["num_triangles"] for s in per_iso],
                    "active_blocks_per_surface": [s["n_active"] for s in per_iso],
                    "parallelism": f"{world} independent replica(s)"},
-        "roofline": {"bound": "hbm", "kernel": kernel_of[dominant], "achieved": ach, "peak": peak, "unit": "GB/s",
+        "roofline": {"bound": "hbm", "kernel": KERNEL_OF[dominant][0], "achieved": ach, "peak": peak, "unit": "GB/s",
                      "frac": ach / peak, "peak_source": f"{peak_src} hbm_gbs (copy)",
-                     "traffic": profile_traffic(file_of[dominant], kernel_of[dominant]),
+                     "traffic": profile_traffic(KERNEL_OF[dominant][1], KERNEL_OF[dominant][0]),
                      "alg_bytes_per_launch": stage_b[dominant] / n_launch},
+        "roofline_cold_extraction": cold,
+        "batch64": batch,
         "stages": stages,
         "gpu_launches": args.steps * (KERNELS_PER_RESET + KERNELS_PER_SURFACE * len(ISOS)),
         "clocks": clk.summary(),

@@ -149,14 +149,15 @@ int iso_set_stream(iso_volume *v, void *stream);
 int iso_cache_reset(iso_volume *v);
 
 /* Per-stage timing.  With profiling on, each extraction records CUDA
- * events on the volume's stream between its stages; iso_stage_times then
+ * events on the volume's stream between its kernels; iso_stage_times then
  * returns the last extraction's durations in milliseconds, in this order:
  *   0 prep (counters and descriptors), 1 cull (Section 4.1 and the
  *   hit/new split of Algorithm 1), 2 cache update (rest of Algorithm 1),
- *   3 decode (Section 4.2.1), 4 triangles (Sections 4.3-4.5).
- * ms must hold n >= 5 floats.  Profiling off (the default) records
+ *   3 decode (Section 4.2.1), 4 count (Sections 4.3-4.4: per-block
+ *   triangle counts), 5 scan (Section 4.4: offsets), 6 emit (Section 4.5).
+ * ms must hold n >= 7 floats.  Profiling off (the default) records
  * nothing. */
-#define ISO_NUM_STAGES 5
+#define ISO_NUM_STAGES 7
 int iso_set_profiling(iso_volume *v, int on);
 int iso_stage_times(iso_volume *v, float *ms, int n);
 
@@ -216,6 +217,79 @@ int iso_decode_blocks(const uint64_t *d_bits, uint32_t rate_bits, const uint32_t
  * work is queued on `stream`; the call does not block. */
 int iso_active_blocks_static(const float *d_bmin, const float *d_bmax, uint32_t nx, uint32_t ny, uint32_t nz,
                              float isovalue, uint32_t *d_ids, uint64_t capacity, uint32_t *d_count, void *stream);
+
+/* ---- batches: many volumes in the same launches ---------------------
+ * A batch extracts one surface from each of n loaded volumes, each at its
+ * own isovalue, with every stage of Sections 4.1-4.5 running as ONE
+ * persistent launch over all n volumes (work items numbered volume after
+ * volume), the whole sequence replayed as one CUDA graph.  Each volume
+ * keeps its own cache (Algorithm 1 runs per volume), so a volume's
+ * surface, statistics and cache state after a batch extraction are
+ * exactly those of extracting it alone at the same isovalue.
+ *
+ * The batch does not own its volumes: they must outlive it, must all live
+ * on the current device, may not be loaded with ISO_DEBUG, may appear
+ * only once, and may not be used by another call while a batch call runs
+ * (batch calls block until they are done, so sequential use from one host
+ * thread is safe).  Device work is issued on the batch's stream. */
+typedef struct iso_batch iso_batch;
+
+/* How the launches of a batch run.  For each persistent kernel: CTAs per
+ * SM (0 = the kernel's occupancy limit, the default; larger values are
+ * clamped to it) and, where the kernel has a choice, its tile size (0 =
+ * default).  Every setting computes the same results. */
+typedef struct iso_launch_shape {
+    uint32_t cull_ctas;          /* Section 4.1 */
+    uint32_t cull_tile;          /* block ranges per cull tile: 2048 or 4096 (default) */
+    uint32_t cache_update_ctas;  /* Algorithm 1 (both cache-update kernels) */
+    uint32_t decode_ctas;        /* Section 4.2.1 */
+    uint32_t decode_tile;        /* new blocks per decode CTA: 64, 128 (default) or 256 */
+    uint32_t count_ctas;         /* Section 4.4: per-block triangle counts */
+    uint32_t count_tile;         /* candidate blocks per count CTA: 16, 32 (default) or 64 */
+    uint32_t scan_ctas;          /* Section 4.4: offsets */
+    uint32_t scan_tile;          /* counts per offset-scan tile: 1024, 2048 (default) or 4096 */
+    uint32_t emit_ctas;          /* Section 4.5 */
+    uint32_t emit_tile;          /* candidate blocks per emit CTA: 16, 32 (default) or 64 */
+} iso_launch_shape;
+
+/* volumes[0..n), 1 <= n <= 1024; stream: cudaStream_t (NULL = default). */
+int iso_batch_create(iso_batch **out, iso_volume *const *volumes, uint32_t n, void *stream);
+
+/* Extract surface i of volume i at isovalues[i] (host array, all finite).
+ * Surfaces are written one after another into the caller's device buffer
+ * d_vertices (float4[3 * capacity_triangles]): surface i occupies
+ * triangles [tri_offsets[i], tri_offsets[i+1]).  tri_offsets (host,
+ * n+1 entries) is always filled; if the total exceeds the capacity, only
+ * triangles below it are written and ISO_ERR_CAPACITY is returned (the
+ * caches are updated: calling again with a larger buffer repeats the same
+ * surfaces from a warm cache).  stats (host, n entries) and status (host,
+ * n entries: ISO_OK, ISO_ERR_BUDGET or ISO_ERR_TIMEOUT per volume) may be
+ * NULL.  Returns the first volume error, else the capacity check's. */
+int iso_batch_extract(iso_batch *b, const float *isovalues, float *d_vertices, uint64_t capacity_triangles,
+                      uint64_t *tri_offsets, iso_stats *stats, int *status);
+
+/* Set or read the batch's launch shape (the graph is re-captured).  A
+ * tile size the kernels are not compiled for gives ISO_ERR_INVALID_ARG.
+ * get_shape reports what runs: CTAs per SM after clamping, tile sizes. */
+int iso_batch_set_shape(iso_batch *b, const iso_launch_shape *shape);
+int iso_batch_get_shape(const iso_batch *b, iso_launch_shape *shape);
+
+/* Autotune the launch shape on the given isovalues.  For each tile-size
+ * variant i (0, 1, 2: the sizes listed above, smallest first; kernels
+ * with fewer variants keep their last) and each k from 1 to the largest
+ * occupancy limit, every kernel runs at variant i with min(k, its limit)
+ * CTAs per SM; each setting is timed `trials` times (CUDA events between
+ * the kernels, caches emptied before each run so that every run decodes
+ * the same blocks) and each kernel keeps its fastest (tile, CTAs) pair.
+ * The chosen shape is applied if the whole batch runs faster with it than
+ * with the defaults, and returned in *best; best_ms[0] and best_ms[1] (may
+ * be NULL) receive the cold-cache batch time of the default shape and of
+ * the applied one.  The caches are left empty. */
+int iso_batch_tune(iso_batch *b, const float *isovalues, float *d_vertices, uint64_t capacity_triangles,
+                   int trials, iso_launch_shape *best, float *best_ms);
+
+/* Free the batch (not its volumes).  NULL is a no-op. */
+void iso_batch_release(iso_batch *b);
 
 /* ---- debug and parity access (volumes loaded with ISO_DEBUG) ---------
  * Copies a per-stage array of the LAST extraction into host memory.

@@ -57,6 +57,15 @@ class _Stats(ctypes.Structure):
         return {name: int(getattr(self, name)) for name, _ in self._fields_}
 
 
+class _Shape(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_uint32) for name in (
+        "cull_ctas", "cull_tile", "cache_update_ctas", "decode_ctas", "decode_tile", "count_ctas", "count_tile",
+        "scan_ctas", "scan_tile", "emit_ctas", "emit_tile")]
+
+    def as_dict(self):
+        return {name: int(getattr(self, name)) for name, _ in self._fields_}
+
+
 class _Mesh(ctypes.Structure):
     _fields_ = [("d_vertices", ctypes.c_void_p), ("num_triangles", ctypes.c_uint64),
                 ("capacity_triangles", ctypes.c_uint64), ("stats", _Stats), ("priv", ctypes.c_void_p)]
@@ -91,6 +100,12 @@ def lib():
             "iso_set_profiling": (i32, [P, i32]),
             "iso_active_blocks_static": (i32, [P, P, u32, u32, u32, ctypes.c_float, P, u64, P, P]),
             "iso_stage_times": (i32, [P, ctypes.POINTER(ctypes.c_float), i32]),
+            "iso_batch_create": (i32, [ctypes.POINTER(P), P, u32, P]),
+            "iso_batch_extract": (i32, [P, P, P, u64, P, P, P]),
+            "iso_batch_set_shape": (i32, [P, ctypes.POINTER(_Shape)]),
+            "iso_batch_get_shape": (i32, [P, ctypes.POINTER(_Shape)]),
+            "iso_batch_tune": (i32, [P, P, P, u64, i32, ctypes.POINTER(_Shape), P]),
+            "iso_batch_release": (None, [P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -228,15 +243,16 @@ class Volume:
         d["status"] = rc
         return d
 
-    STAGES = ("prep", "cull", "cache_update", "decode", "triangles")
+    STAGES = ("prep", "cull", "cache_update", "decode", "count", "scan", "emit")
 
     def set_profiling(self, on=True):
         _check(lib().iso_set_profiling(self._h, 1 if on else 0), "iso_set_profiling")
 
     def stage_times(self):
         """ms per stage of the last extraction (profiling on)"""
-        buf = (ctypes.c_float * 5)()
-        _check(lib().iso_stage_times(self._h, buf, 5), "iso_stage_times")
+        n = len(self.STAGES)
+        buf = (ctypes.c_float * n)()
+        _check(lib().iso_stage_times(self._h, buf, n), "iso_stage_times")
         return dict(zip(self.STAGES, [float(x) for x in buf]))
 
     def cache_reset(self):
@@ -265,6 +281,95 @@ class Volume:
     def release(self):
         if self._h:
             lib().iso_release(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Several loaded volumes extracted together, each at its own isovalue,
+    with one launch per stage for all of them (replayed as a CUDA graph).
+    Each volume keeps its own cache; its surface equals extracting it alone.
+    The volumes must outlive the batch and be on the current device."""
+
+    def __init__(self, volumes, *, stream=None):
+        self._h = None
+        self.volumes = list(volumes)
+        n = len(self.volumes)
+        arr = (ctypes.c_void_p * max(n, 1))(*[v._h.value if v._h else None for v in self.volumes])
+        h = ctypes.c_void_p()
+        _check(lib().iso_batch_create(ctypes.byref(h), ctypes.cast(arr, ctypes.c_void_p), n,
+                                      stream if stream is not None else _current_stream()), "iso_batch_create")
+        self._h = h
+        self.n = n
+        self._last_total = 0
+
+    def extract_into(self, isos, out, check=True):
+        """Write the surfaces into `out` (CUDA float32, 12 floats per triangle).
+        Returns a dict: offsets (uint64[n+1], surface i = triangles
+        offsets[i]:offsets[i+1]), stats (list of dicts), status (list), rc."""
+        isos = np.ascontiguousarray(isos, np.float32)
+        if isos.shape != (self.n,):
+            raise ValueError(f"need {self.n} isovalues")
+        cap = out.numel() // 12 if out is not None else 0
+        offsets = np.zeros(self.n + 1, np.uint64)
+        stats = (_Stats * self.n)()
+        status = np.zeros(self.n, np.int32)
+        rc = lib().iso_batch_extract(self._h, _ptr(isos), _ptr(out) if cap else None, cap, _ptr(offsets),
+                                     ctypes.cast(stats, ctypes.c_void_p), _ptr(status))
+        if check:
+            _check(rc, "iso_batch_extract")
+        self._last_total = int(offsets[-1])
+        return {"offsets": offsets, "stats": [st.as_dict() for st in stats], "status": status.tolist(), "rc": rc}
+
+    def extract(self, isos):
+        """Surfaces into a new CUDA tensor.  Returns (vertices (3T, 4) tensor,
+        offsets uint64[n+1], stats list).  A first guess too small is
+        retried once with the exact size (from a warm cache)."""
+        import torch
+        guess = self._last_total + self._last_total // 4 + 4096 if self._last_total else \
+            sum(2 * v.nb for v in self.volumes) + 4096
+        out = torch.empty((3 * guess, 4), dtype=torch.float32, device="cuda")
+        r = self.extract_into(isos, out, check=False)
+        if r["rc"] == ISO_ERR_CAPACITY:
+            total = int(r["offsets"][-1])
+            out = torch.empty((3 * max(total, 1), 4), dtype=torch.float32, device="cuda")
+            r = self.extract_into(isos, out, check=False)
+        _check(r["rc"], "iso_batch_extract")
+        total = int(r["offsets"][-1])
+        return out[:3 * total], r["offsets"], r["stats"]
+
+    @property
+    def shape(self):
+        sh = _Shape()
+        _check(lib().iso_batch_get_shape(self._h, ctypes.byref(sh)), "iso_batch_get_shape")
+        return sh.as_dict()
+
+    def set_shape(self, **shape):
+        """CTAs per SM (``*_ctas``) and tile sizes (``*_tile``) per kernel; 0 or
+        absent = default.  See iso_launch_shape in include/bcmc.h."""
+        sh = _Shape(**{k: int(v) for k, v in shape.items()})
+        _check(lib().iso_batch_set_shape(self._h, ctypes.byref(sh)), "iso_batch_set_shape")
+
+    def tune(self, isos, out, trials=3):
+        """Autotune each kernel's tile size and CTAs per SM on these isovalues
+        (caches are emptied before each timed run and left empty).  Returns a
+        dict with the applied shape and the cold batch time (ms) of the
+        default shape and of the applied one."""
+        isos = np.ascontiguousarray(isos, np.float32)
+        sh = _Shape()
+        ms = np.zeros(2, np.float32)
+        _check(lib().iso_batch_tune(self._h, _ptr(isos), _ptr(out), out.numel() // 12, int(trials),
+                                    ctypes.byref(sh), _ptr(ms)), "iso_batch_tune")
+        return {"shape": sh.as_dict(), "default_ms": float(ms[0]), "tuned_ms": float(ms[1])}
+
+    def release(self):
+        if self._h:
+            lib().iso_batch_release(self._h)
             self._h = None
 
     def __del__(self):

@@ -6,6 +6,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <vector>
 
 #include "bcmc.h"
 #include "common.cuh"
@@ -14,44 +15,11 @@
 
 using namespace bcmc;
 
-struct iso_volume {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    Geom g{};
-    uint32_t flags = 0;
-    DevState s{};
-    Grids grids{};
-    uint32_t cap = 0;                 // physical slots
-    uint32_t n_cull_desc = 0, n_lru_desc = 0;
-    Ctl *host_ctl = nullptr;          // pinned mirror for the one readback
-    Params *host_params = nullptr;    // pinned: this extraction's isovalue, output and capacity
-    cudaStream_t capture_stream = nullptr;
-    cudaGraph_t graph = nullptr;      // one extraction: params copy, six kernels, count readback
-    cudaGraphExec_t gexec = nullptr;
-    bool use_graph = true;
-    // owned device allocations
-    uint64_t *bits = nullptr;
-    float *bmin = nullptr, *bmax = nullptr;
-    float2 *hull = nullptr, *hull8 = nullptr;
-    uint8_t *tables = nullptr;
-    unsigned long long dbg_edges_cap = 0;   // in vertices
-    bool profiling = false;
-    cudaEvent_t ev[ISO_NUM_STAGES + 1] = {};
-    float stage_ms[ISO_NUM_STAGES] = {};
-    unsigned long long last_tris = 0;
-    uint32_t last_n_active = 0, last_n_new = 0, last_n_cand = 0, last_slots = 0;
-};
+#include "volume.cuh"
 
-namespace {
+using namespace bcmc_host;
 
-#define CK(call)                                                  \
-    do {                                                          \
-        cudaError_t e_ = (call);                                  \
-        if (e_ != cudaSuccess) {                                  \
-            (void)cudaGetLastError();                             \
-            return e_ == cudaErrorMemoryAllocation ? ISO_ERR_OOM : ISO_ERR_CUDA; \
-        }                                                         \
-    } while (0)
+namespace bcmc_host {
 
 // Device memory comes from one library-owned, stream-ordered pool per
 // device that keeps freed memory for reuse (release threshold raised), so
@@ -60,6 +28,12 @@ namespace {
 constexpr int kMaxPoolDevices = 64;
 std::mutex g_pool_mutex;
 cudaMemPool_t g_pool[kMaxPoolDevices] = {};
+struct OccEntry {
+    int device;
+    int key[6];                   // tile sizes and single/batch
+    Plan limits;
+};
+std::vector<OccEntry> g_occ;      // occupancy limits per (device, tile variants)
 
 cudaMemPool_t device_pool(int dev) {
     if (dev < 0 || dev >= kMaxPoolDevices) return nullptr;
@@ -82,25 +56,111 @@ cudaMemPool_t device_pool(int dev) {
     return g_pool[dev];
 }
 
-// the stream every allocation and free of a volume is ordered on
-thread_local cudaStream_t t_alloc_stream = nullptr;
-thread_local int t_alloc_device = 0;
-
-template <typename T>
-int dalloc(T **p, size_t count) {
+int dalloc_bytes(void **p, size_t bytes, int dev, cudaStream_t st) {
     *p = nullptr;
-    if (count == 0) count = 1;
-    cudaMemPool_t pool = device_pool(t_alloc_device);
+    if (bytes == 0) bytes = 1;
+    cudaMemPool_t pool = device_pool(dev);
     if (pool) {
-        CK(cudaMallocFromPoolAsync((void **)p, count * sizeof(T), pool, t_alloc_stream));
+        ISO_CK(cudaMallocFromPoolAsync(p, bytes, pool, st));
     } else {
-        CK(cudaMalloc((void **)p, count * sizeof(T)));
+        ISO_CK(cudaMalloc(p, bytes));
     }
     return ISO_OK;
 }
 
-void dfree(void *p) {
-    if (p) cudaFreeAsync(p, t_alloc_stream);
+void dfree_on(void *p, cudaStream_t st) {
+    if (p) cudaFreeAsync(p, st);
+}
+
+Plan default_tiles(const Plan *want) {
+    Plan t{};
+    t.cull_tile = want && want->cull_tile ? want->cull_tile : kDefaultCullTile;
+    t.decode_tile = want && want->decode_tile ? want->decode_tile : kDefaultDecodeTile;
+    t.count_tile = want && want->count_tile ? want->count_tile : kDefaultCountTile;
+    t.scan_tile = want && want->scan_tile ? want->scan_tile : kDefaultScanTile;
+    t.emit_tile = want && want->emit_tile ? want->emit_tile : kDefaultEmitTile;
+    return t;
+}
+
+Plan occupancy_limits_of(int device, const Plan &tiles, bool single) {
+    const int key[6] = {tiles.cull_tile, tiles.decode_tile, tiles.count_tile, tiles.scan_tile, tiles.emit_tile,
+                        single ? 1 : 0};
+    std::lock_guard<std::mutex> lock(g_pool_mutex);
+    for (const OccEntry &e : g_occ)
+        if (e.device == device && std::equal(key, key + 6, e.key)) return e.limits;
+    OccEntry e{device, {key[0], key[1], key[2], key[3], key[4], key[5]}, occupancy_limits(tiles, single)};
+    g_occ.push_back(e);
+    return e.limits;
+}
+
+Plan launch_plan(const Plan *want, int device, uint64_t total_blocks, uint64_t total_slots, uint32_t n_vols,
+                 bool single) {
+    const Plan tiles = default_tiles(want);
+    const Plan lim = occupancy_limits_of(device, tiles, single);
+    Plan use = lim;
+    if (want) {
+        int *dst = &use.prep;
+        const int *src = &want->prep, *mx = &lim.prep;
+        for (int k = 0; k < 8; k++) dst[k] = src[k] > 0 ? std::min(src[k], mx[k]) : mx[k];
+    }
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms <= 0) {
+        (void)cudaGetLastError();
+        sms = 1;
+    }
+    int *ctas = &use.prep;
+    for (int k = 0; k < 8; k++) ctas[k] = std::max(1, ctas[k]) * sms;
+    // no more CTAs than work items (each bound holds for any isovalue)
+    auto clamp = [](int &grid, uint64_t items) {
+        grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)grid, items));
+    };
+    auto tiles_of = [&](uint64_t n, int tile) { return (n + tile - 1) / tile + n_vols; };
+    clamp(use.cull, tiles_of(total_blocks, use.cull_tile));
+    clamp(use.lru_a, 2 * tiles_of(total_slots, kScanTile) + n_vols);
+    clamp(use.lru_b, tiles_of(total_slots, kScanTile));
+    clamp(use.decode, tiles_of(total_slots, use.decode_tile));
+    clamp(use.mc_count, tiles_of(total_slots, use.count_tile));
+    clamp(use.mc_emit, tiles_of(total_slots, use.emit_tile));
+    clamp(use.mc_scan, tiles_of(total_slots, use.scan_tile));
+    return use;
+}
+
+// After a timeout the cache bookkeeping may be inconsistent: empty it so
+// the next extraction starts from a clean state.
+int status_to_error(iso_volume *v, uint32_t st) {
+    if (st & kStatusAnyTimeout) {
+        launch_reset_cache(v->s, v->stream);
+        cudaStreamSynchronize(v->stream);
+        (void)cudaGetLastError();
+        return ISO_ERR_TIMEOUT;
+    }
+    if (st & kStatusBudget) return ISO_ERR_BUDGET;
+    return ISO_OK;
+}
+
+void fill_stats(const Ctl &c, iso_stats *st, uint32_t reruns) {
+    st->num_triangles = c.n_tri;
+    st->n_active = c.n_active;
+    st->n_new = c.n_new;
+    st->n_occupied = c.n_occ;
+    st->n_slots = c.S;
+    st->cache_bytes = (uint64_t)c.S * 256ull;
+    st->epoch = c.epoch;
+    st->reruns = reruns;
+    st->n_candidates = c.n_cand;
+    st->reserved = 0;
+}
+
+}  // namespace bcmc_host
+
+namespace {
+
+#define CK(call) ISO_CK(call)
+
+// allocations of a volume are ordered on its stream
+template <typename T>
+int dalloc(iso_volume *v, T **p, size_t count) {
+    return dalloc_on(p, count, v->device, v->stream);
 }
 
 int geometry(uint32_t nx, uint32_t ny, uint32_t nz, uint32_t rate, Geom *g) {
@@ -118,13 +178,11 @@ int free_volume(iso_volume *v) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaSetDevice(v->device);
-    t_alloc_stream = v->stream;
-    t_alloc_device = v->device;
     DevState &s = v->s;
     void *ptrs[] = {v->bits, v->bmin, v->bmax, v->hull, v->hull8, v->tables, s.mactive, s.iactive, s.inew, s.icand,
                     s.islot, s.slast, s.sblock, s.lbuf[0], s.lbuf[1], s.newslot, s.slots, s.desc_cull, s.desc_cand,
                     s.desc_lru_a, s.desc_lru_b, s.desc_mc, s.ctl, s.counts, s.offsets, s.dbg_cases, s.dbg_edges};
-    for (void *p : ptrs) dfree(p);
+    for (void *p : ptrs) dfree_on(p, v->stream);
     cudaStreamSynchronize(v->stream);
     (void)cudaGetLastError();
     if (v->host_ctl) cudaFreeHost(v->host_ctl);
@@ -139,51 +197,24 @@ int free_volume(iso_volume *v) {
     return ISO_OK;
 }
 
-struct DeviceGuard {              // make the volume's device current for the call
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard() {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
-
-// After a timeout the cache bookkeeping may be inconsistent: empty it so
-// the next extraction starts from a clean state.
-int status_to_error(iso_volume *v, uint32_t st) {
-    if (st & kStatusTimeout) {
-        launch_reset_cache(v->s, v->stream);
-        cudaStreamSynchronize(v->stream);
-        (void)cudaGetLastError();
-        return ISO_ERR_TIMEOUT;
-    }
-    if (st & kStatusBudget) return ISO_ERR_BUDGET;
-    return ISO_OK;
-}
-
 // Queue one extraction on `st`: copy the parameters in, run the stages,
 // copy the control block out.  With mc_only, only the triangle stage runs
 // again (after a larger output buffer was supplied).  Events between the
 // stages are recorded when profiling (never inside a captured graph).
 int enqueue_pipeline(iso_volume *v, cudaStream_t st, bool mc_only, bool prof) {
     const bool debug = (v->flags & ISO_DEBUG) != 0;
+    const Launch L{nullptr, 1u, single_counters(v), VolEntry{v->s, v->g, v->n_cull_desc, v->n_lru_desc}};
     CK(cudaMemcpyAsync(&v->s.ctl->params, v->host_params, sizeof(Params), cudaMemcpyHostToDevice, st));
     if (prof) cudaEventRecord(v->ev[0], st);
-    if (!mc_only) launch_prep(v->s, v->n_cull_desc, v->n_lru_desc, false, v->grids.prep, st);
-    if (prof) cudaEventRecord(v->ev[1], st);
     if (!mc_only) {
-        launch_cull(v->s, v->g, v->grids.cull, st);
-        if (prof) cudaEventRecord(v->ev[2], st);
-        launch_lru(v->s, v->grids.lru_a, v->grids.lru_b, st);
-        if (prof) cudaEventRecord(v->ev[3], st);
-        launch_decode_new(v->s, v->g, v->grids.decode, st);
-        if (prof) cudaEventRecord(v->ev[4], st);
+        launch_front(L, v->plan, st, prof ? v->ev : nullptr);
+        launch_mc_count(L, debug, v->plan, st);
+        if (prof) cudaEventRecord(v->ev[5], st);
+        launch_mc_scan(L, v->plan, st);
+        if (prof) cudaEventRecord(v->ev[6], st);
     }
-    launch_mc(v->s, v->g, debug, mc_only, v->grids, st);
-    if (prof) cudaEventRecord(v->ev[5], st);
+    launch_mc_emit(L, debug, v->plan, st);
+    if (prof) cudaEventRecord(v->ev[7], st);
     CK(cudaMemcpyAsync(v->host_ctl, v->s.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
     CK(cudaGetLastError());
     return ISO_OK;
@@ -227,30 +258,14 @@ void collect_stage_times(iso_volume *v) {
     }
 }
 
-void fill_stats(const iso_volume *v, iso_stats *st, uint32_t reruns) {
-    const Ctl &c = *v->host_ctl;
-    st->num_triangles = c.n_tri;
-    st->n_active = c.n_active;
-    st->n_new = c.n_new;
-    st->n_occupied = c.n_occ;
-    st->n_slots = c.S;
-    st->cache_bytes = (uint64_t)c.S * 256ull;
-    st->epoch = c.epoch;
-    st->reruns = reruns;
-    st->n_candidates = c.n_cand;
-    st->reserved = 0;
-}
-
 // debug mode: make sure the per-vertex edge-id buffer can hold T triangles
 int ensure_debug_edges(iso_volume *v, unsigned long long tris) {
     if (!(v->flags & ISO_DEBUG) || 3ull * tris <= v->dbg_edges_cap) return ISO_OK;
     CK(cudaStreamSynchronize(v->stream));
-    t_alloc_stream = v->stream;
-    t_alloc_device = v->device;
-    dfree(v->s.dbg_edges);
+    dfree_on(v->s.dbg_edges, v->stream);
     v->s.dbg_edges = nullptr;
     const unsigned long long want = std::max(3ull * tris, 3ull * 1024);
-    int rc = dalloc(&v->s.dbg_edges, want);
+    int rc = dalloc(v, &v->s.dbg_edges, want);
     if (rc) { v->dbg_edges_cap = 0; return rc; }
     v->dbg_edges_cap = want;
     return ISO_OK;
@@ -334,8 +349,6 @@ int iso_load_volume(iso_volume **out, const void *compressed, size_t compressed_
     if (!v) return ISO_ERR_OOM;
     if (cudaGetDevice(&v->device) != cudaSuccess) { (void)cudaGetLastError(); delete v; return ISO_ERR_CUDA; }
     v->stream = (cudaStream_t)o.stream;
-    t_alloc_stream = v->stream;
-    t_alloc_device = v->device;
     v->g = g;
     v->flags = o.flags;
     uint64_t cap = g.nb;
@@ -354,35 +367,36 @@ int iso_load_volume(iso_volume **out, const void *compressed, size_t compressed_
     DevState &s = v->s;
     const size_t words = (size_t)g.nb * g.rate;
     const uint32_t nwords = (g.nb + 31) / 32;
-    v->n_cull_desc = (g.nb + kScanTile - 1) / kScanTile;
+    // descriptors for the smallest tile of each scan (any plan may run)
+    v->n_cull_desc = (g.nb + kMinCullTile - 1) / kMinCullTile;
     v->n_lru_desc = (v->cap + kScanTile - 1) / kScanTile;
-    const uint32_t n_mc_desc = (v->cap + 2047) / 2048;   // scan tiles over the candidates (<= cap)
-    TRY(dalloc(&v->bits, words));
-    TRY(dalloc(&v->bmin, g.nb));
-    TRY(dalloc(&v->bmax, g.nb));
-    TRY(dalloc(&v->hull, g.nb));
-    TRY(dalloc(&v->hull8, g.nb));
-    TRY(dalloc(&v->tables, 256 + 256 * 16));
-    TRY(dalloc(&s.mactive, nwords));
-    TRY(dalloc(&s.iactive, g.nb));
-    TRY(dalloc(&s.inew, g.nb));
-    TRY(dalloc(&s.icand, g.nb));
-    TRY(dalloc(&s.islot, g.nb));
-    TRY(dalloc(&s.slast, v->cap));
-    TRY(dalloc(&s.sblock, v->cap));
-    TRY(dalloc(&s.lbuf[0], v->cap));
-    TRY(dalloc(&s.lbuf[1], v->cap));
-    TRY(dalloc(&s.newslot, v->cap));
-    TRY(dalloc(&s.slots, (size_t)v->cap * 64));
-    TRY(dalloc(&s.desc_cull, v->n_cull_desc));
-    TRY(dalloc(&s.desc_cand, v->n_cull_desc));
-    TRY(dalloc(&s.desc_lru_a, v->n_lru_desc));
-    TRY(dalloc(&s.desc_lru_b, v->n_lru_desc));
-    TRY(dalloc(&s.desc_mc, n_mc_desc));
-    TRY(dalloc(&s.ctl, 1));
-    TRY(dalloc(&s.counts, v->cap));
-    TRY(dalloc(&s.offsets, v->cap));
-    if (v->flags & ISO_DEBUG) TRY(dalloc(&s.dbg_cases, (size_t)g.nb * 64));
+    const uint32_t n_mc_desc = (v->cap + kMinMcScanTile - 1) / kMinMcScanTile;   // candidates <= cap
+    TRY(dalloc(v, &v->bits, words));
+    TRY(dalloc(v, &v->bmin, g.nb));
+    TRY(dalloc(v, &v->bmax, g.nb));
+    TRY(dalloc(v, &v->hull, g.nb));
+    TRY(dalloc(v, &v->hull8, g.nb));
+    TRY(dalloc(v, &v->tables, 256 + 256 * 16));
+    TRY(dalloc(v, &s.mactive, nwords));
+    TRY(dalloc(v, &s.iactive, g.nb));
+    TRY(dalloc(v, &s.inew, g.nb));
+    TRY(dalloc(v, &s.icand, g.nb));
+    TRY(dalloc(v, &s.islot, g.nb));
+    TRY(dalloc(v, &s.slast, v->cap));
+    TRY(dalloc(v, &s.sblock, v->cap));
+    TRY(dalloc(v, &s.lbuf[0], v->cap));
+    TRY(dalloc(v, &s.lbuf[1], v->cap));
+    TRY(dalloc(v, &s.newslot, v->cap));
+    TRY(dalloc(v, &s.slots, (size_t)v->cap * 64));
+    TRY(dalloc(v, &s.desc_cull, v->n_cull_desc));
+    TRY(dalloc(v, &s.desc_cand, v->n_cull_desc));
+    TRY(dalloc(v, &s.desc_lru_a, v->n_lru_desc));
+    TRY(dalloc(v, &s.desc_lru_b, v->n_lru_desc));
+    TRY(dalloc(v, &s.desc_mc, n_mc_desc));
+    TRY(dalloc(v, &s.ctl, 1));
+    TRY(dalloc(v, &s.counts, v->cap));
+    TRY(dalloc(v, &s.offsets, v->cap));
+    if (v->flags & ISO_DEBUG) TRY(dalloc(v, &s.dbg_cases, (size_t)g.nb * 64));
     if (cudaMallocHost((void **)&v->host_ctl, sizeof(Ctl)) != cudaSuccess ||
         cudaMallocHost((void **)&v->host_params, sizeof(Params)) != cudaSuccess) {
         (void)cudaGetLastError();
@@ -434,9 +448,7 @@ int iso_load_volume(iso_volume **out, const void *compressed, size_t compressed_
     launch_hull(v->bmin, v->bmax, v->hull, v->hull8, g, st);
     TRYC(cudaGetLastError());
     TRYC(cudaStreamSynchronize(st));
-    int sms = 0;
-    TRYC(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, v->device));
-    v->grids = compute_grids(sms);
+    v->plan = launch_plan(nullptr, v->device, g.nb, v->cap, 1, true);
     TRYC(cudaGetLastError());
     *out = v;
     return ISO_OK;
@@ -449,7 +461,7 @@ int iso_extract_into(iso_volume *v, float isovalue, float *d_vertices, uint64_t 
     if (!v || !std::isfinite(isovalue) || (!d_vertices && capacity_triangles)) return ISO_ERR_INVALID_ARG;
     DeviceGuard dg(v->device);
     int rc = run(v, isovalue, reinterpret_cast<float4 *>(d_vertices), capacity_triangles, false);
-    if (stats) fill_stats(v, stats, 0);
+    if (stats) fill_stats(*v->host_ctl, stats, 0);
     if (rc) return rc;
     if (v->host_ctl->n_tri > capacity_triangles) return ISO_ERR_CAPACITY;
     return ISO_OK;
@@ -462,10 +474,8 @@ int iso_extract(iso_volume *v, float isovalue, iso_mesh *out) {
     // first guess: the last surface's size plus a margin, else 2 per block
     unsigned long long guess = v->last_tris ? v->last_tris + v->last_tris / 4 + 4096 : 2ull * v->g.nb + 4096;
     float4 *buf = nullptr;
-    t_alloc_stream = v->stream;
-    t_alloc_device = v->device;
     {
-        const int arc = dalloc(&buf, guess * 3);
+        const int arc = dalloc(v, &buf, guess * 3);
         if (arc) return arc;
     }
     int rc = run(v, isovalue, buf, guess, false);
@@ -475,7 +485,7 @@ int iso_extract(iso_volume *v, float isovalue, iso_mesh *out) {
         cudaFreeAsync(buf, v->stream);
         buf = nullptr;
         {
-            const int arc = dalloc(&buf, std::max(need, 1ull) * 3);
+            const int arc = dalloc(v, &buf, std::max(need, 1ull) * 3);
             if (arc) return arc;
         }
         guess = std::max(need, 1ull);
@@ -485,13 +495,13 @@ int iso_extract(iso_volume *v, float isovalue, iso_mesh *out) {
     if (rc) {
         cudaFreeAsync(buf, v->stream);
         cudaStreamSynchronize(v->stream);
-        fill_stats(v, &out->stats, reruns);
+        fill_stats(*v->host_ctl, &out->stats, reruns);
         return rc;
     }
     out->d_vertices = reinterpret_cast<float *>(buf);
     out->num_triangles = v->host_ctl->n_tri;
     out->capacity_triangles = guess;
-    fill_stats(v, &out->stats, reruns);
+    fill_stats(*v->host_ctl, &out->stats, reruns);
     return ISO_OK;
 }
 
@@ -606,11 +616,9 @@ int iso_debug_read_blocks(iso_volume *v, const uint32_t *ids, uint64_t n, float 
     uint32_t *d_ids = nullptr;
     float *d_out = nullptr;
     int32_t *d_missing = nullptr;
-    t_alloc_stream = v->stream;
-    t_alloc_device = v->device;
-    int rc = dalloc(&d_ids, n);
-    if (!rc) rc = dalloc(&d_out, n * 64);
-    if (!rc) rc = dalloc(&d_missing, 1);
+    int rc = dalloc(v, &d_ids, n);
+    if (!rc) rc = dalloc(v, &d_out, n * 64);
+    if (!rc) rc = dalloc(v, &d_missing, 1);
     if (!rc && cudaStreamSynchronize(v->stream) != cudaSuccess) rc = ISO_ERR_CUDA;
     int32_t missing = 0;
     if (!rc && (cudaMemcpy(d_ids, ids, n * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -624,9 +632,9 @@ int iso_debug_read_blocks(iso_volume *v, const uint32_t *ids, uint64_t n, float 
             rc = ISO_ERR_CUDA;
     }
     (void)cudaGetLastError();
-    dfree(d_ids);
-    dfree(d_out);
-    dfree(d_missing);
+    dfree_on(d_ids, v->stream);
+    dfree_on(d_out, v->stream);
+    dfree_on(d_missing, v->stream);
     cudaStreamSynchronize(v->stream);
     if (rc) return rc;
     return missing ? ISO_ERR_INVALID_ARG : ISO_OK;

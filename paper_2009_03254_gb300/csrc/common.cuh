@@ -42,12 +42,19 @@ __device__ __forceinline__ void block_coords(const Geom &g, uint32_t b, uint32_t
 
 // ---------------------------------------------------------------- control block
 
+// A bounded device wait that gives up sets the bit of its stage.  Each
+// kernel sizes its work only from bits set before it starts, so all of
+// its blocks agree on the sizes even when one of them times out.
 enum Status : uint32_t {
-    kStatusTimeout = 1u,      // a bounded device wait gave up
+    kStatusTimeout = 1u,      // cull look-back gave up
     kStatusBudget = 2u,       // new blocks do not fit in the slot cap
+    kStatusTimeoutLru = 4u,   // cache-update look-back gave up
+    kStatusTimeoutScan = 8u,  // triangle-offset look-back gave up
 };
+constexpr uint32_t kStatusAnyTimeout = kStatusTimeout | kStatusTimeoutLru | kStatusTimeoutScan;
 
-enum TileCounter { kCtrCull = 0, kCtrLruA = 1, kCtrLruB = 2, kCtrMc = 3, kNumCtr = 4 };
+// dynamic work counters of one launch sequence (tiles handed out in order)
+enum LaunchCounter { kLcCull = 0, kLcLruA = 1, kLcLruB = 2, kLcScan = 3, kNumLaunchCounters = 4 };
 
 // Per-extraction inputs, copied from pinned host memory by the first
 // operation of each extraction (so a captured graph never changes).
@@ -78,7 +85,7 @@ struct Ctl {
     uint32_t n_occ;           // occupied blocks
     uint32_t status;          // Status bits
     uint32_t mc_tiles;        // look-back descriptors the triangle kernel used (to clear)
-    uint32_t ctr[kNumCtr];    // dynamic tile counters
+    uint32_t ctr[kNumLaunchCounters];   // work counters when the volume is extracted alone
     unsigned long long n_tri; // triangles of the surface
 };
 
@@ -102,7 +109,7 @@ __device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long lon
 // counters, possibly two 31-bit counters packed side by side.
 // Tiles are handed out in order by an atomic counter, so every tile that a
 // waiter depends on belongs to a block that is already running; the wait
-// is still bounded: after kSpinLimit polls the tile reports a timeout in
+// is still bounded: after kSpinLimit polls the tile sets `timeout_bit` in
 // Ctl::status and proceeds with what it has.
 
 constexpr unsigned long long kFlagAgg = 1ull << 62;
@@ -119,7 +126,7 @@ constexpr int kLookbackPerLane = 4;
 
 __device__ __forceinline__ unsigned long long lookback_exclusive(unsigned long long *desc, uint32_t tile,
                                                                   unsigned long long aggregate,
-                                                                  uint32_t *status) {
+                                                                  uint32_t *status, uint32_t timeout_bit) {
     const int lane = threadIdx.x & 31;
     if (tile == 0) {
         if (lane == 0) st_relaxed(desc, kFlagPrefix | aggregate);
@@ -152,7 +159,7 @@ __device__ __forceinline__ unsigned long long lookback_exclusive(unsigned long l
         const unsigned need = pref ? ((pref & (0u - pref)) << 1) - 1u : 0xffffffffu;   // lanes up to the first prefix
         if ((rdy & need) != need) {
             if (++spins > kSpinLimit) {
-                if (lane == 0) atomicOr(status, (uint32_t)kStatusTimeout);
+                if (lane == 0) atomicOr(status, timeout_bit);
                 break;
             }
             __nanosleep(sleep_ns);

@@ -2,83 +2,86 @@
 //
 //   prep    clear counters and look-back descriptors, advance the epoch
 //   cull    Section 4.1 + the first step of Algorithm 1: mark active blocks,
-//           compact I_active and I_new in one pass, stamp cache hits
+//           compact I_active, I_new and the candidates in one pass, stamp
+//           cache hits
 //   lru_a   Algorithm 1 (grow, select least recently used free slots,
 //           assign, evict) over the used-slot list
 //   lru_b   append this epoch's slots to the list (most recent last)
 //   decode  Section 4.2.1: decode each new block into its slot
-//   mc      Sections 4.3-4.5 (mc.cu): halo staging, classification,
-//           per-block counts, single-pass prefix over blocks, vertices
+//   mc      Sections 4.3-4.5 (mc.cu): count, scan, emit
 //
 // Sizes that only the device knows (n_active, n_new, ...) never come back
 // to the host between kernels: the kernels are persistent and take their
-// work from counters in the control block.
+// work from the volumes' control blocks.  Every kernel runs over a Launch
+// (launch.cuh): one volume, or a batch of volumes in the same launches.
+// The work a kernel assigns to each volume is computed only from values
+// no kernel of the same launch changes, so all blocks agree on it.
 #include <algorithm>
 #include <cstdint>
 
 #include "codec.cuh"
 #include "common.cuh"
 #include "kernels.cuh"
+#include "launch.cuh"
 
 namespace bcmc {
 
 // ================================================================ prep
 
-__global__ void __launch_bounds__(kThreads) prep_kernel(DevState s, uint32_t n_cull_desc, uint32_t n_lru_desc,
-                                                         int mc_only) {
-    Ctl *c = s.ctl;
-    const uint32_t n_mc_desc = c->mc_tiles;   // descriptors the last triangle pass used
+template <bool kOne>
+__global__ void __launch_bounds__(kThreads) prep_kernel(Launch L) {
     const uint32_t stride = gridDim.x * blockDim.x;
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
-    for (uint32_t i = tid; i < n_mc_desc; i += stride) s.desc_mc[i] = 0;
-    if (!mc_only) {
-        for (uint32_t i = tid; i < n_cull_desc; i += stride) {
+    for (uint32_t v = 0; v < L.n; v++) {
+        const VolEntry &e = vol_of<kOne>(L, v);
+        const DevState &s = e.s;
+        const uint32_t n_mc_desc = s.ctl->mc_tiles;   // descriptors the last triangle pass used
+        for (uint32_t i = tid; i < n_mc_desc; i += stride) s.desc_mc[i] = 0;
+        for (uint32_t i = tid; i < e.n_cull_desc; i += stride) {
             s.desc_cull[i] = 0;
             s.desc_cand[i] = 0;
         }
-        for (uint32_t i = tid; i < n_lru_desc; i += stride) {
+        for (uint32_t i = tid; i < e.n_lru_desc; i += stride) {
             s.desc_lru_a[i] = 0;
             s.desc_lru_b[i] = 0;
         }
     }
-    if (tid == 0) {
-        if (!mc_only) {
-            c->epoch += 1;
-            c->n_active = 0;
-            c->n_new = 0;
-            c->n_cand = 0;
-            c->n_assign = 0;
-            c->status = 0;
-            for (int k = 0; k < kNumCtr; k++) c->ctr[k] = 0;
-        }
-        c->ctr[kCtrMc] = 0;
+    for (uint32_t v = tid; v < L.n; v += stride) {
+        Ctl *c = vol_of<kOne>(L, v).s.ctl;
+        c->epoch += 1;
+        c->n_active = 0;
+        c->n_new = 0;
+        c->n_cand = 0;
+        c->n_assign = 0;
+        c->status = 0;
         c->n_occ = 0;
         c->n_tri = 0;
     }
+    if (tid < kNumLaunchCounters) L.ctr[tid] = 0;
 }
 
 // ================================================================ tile scan helpers
 //
-// A tile is kScanTile = kRounds * 256 entries handled by 256 threads in
-// kRounds rounds; entry tile*kScanTile + r*256 + threadIdx.x belongs to
-// round r.  Per (round, warp) the warp's ballot gives its 32 flags; a
+// A tile is kR * 256 entries handled by 256 threads in kR rounds; entry
+// tile*kR*256 + r*256 + threadIdx.x belongs to round r.  Per (round, warp) the warp's ballot gives its 32 flags; a
 // warp scan over the kRounds*8 (round, warp) counts gives each group's
 // offset inside the tile.  Large tiles keep the tiles of a pass within
 // one wave of resident blocks, so the look-back walk stays short.
 
-constexpr int kRounds = kScanTile / kThreads;
+constexpr int kRounds = kScanTile / kThreads;   // rounds of a cache-update tile
 
+template <int kR>
 struct TileScan {
-    uint32_t cnt[kRounds][8];         // per (round, warp): packed counts, then exclusive offsets
+    uint32_t cnt[kR][8];              // per (round, warp): packed counts, then exclusive offsets
     unsigned long long excl;          // tile's exclusive prefix (look-back)
-    uint32_t tile;
 };
 
 // warp 0: turn ts.cnt into exclusive offsets (packed 16-bit fields add
 // without carries: a tile holds at most 4096 entries) and return the
 // tile's packed total in every lane
-__device__ __forceinline__ uint32_t scan_tile_counts(TileScan &ts) {
-    constexpr int kPer = kRounds * 8 / 32;
+template <int kR>
+__device__ __forceinline__ uint32_t scan_tile_counts(TileScan<kR> &ts) {
+    constexpr int kPer = kR * 8 / 32;
     const int lane = threadIdx.x & 31;
     uint32_t *flat = &ts.cnt[0][0] + kPer * lane;
     uint32_t v[kPer], sum = 0;
@@ -102,6 +105,15 @@ __device__ __forceinline__ uint32_t scan_tile_counts(TileScan &ts) {
     return __shfl_sync(0xffffffffu, incl, 31);
 }
 
+// block-wide: take the next work item from a launch counter
+__device__ __forceinline__ uint32_t next_item(uint32_t *ctr, uint32_t *slot) {
+    if (threadIdx.x == 0) *slot = atomicAdd(ctr, 1u);
+    __syncthreads();
+    const uint32_t x = *slot;
+    __syncthreads();                  // all have read it before thread 0 may overwrite it
+    return x;
+}
+
 // ================================================================ cull (Section 4.1)
 //
 // Active test: the union of a block's range with each neighbour's range
@@ -111,86 +123,102 @@ __device__ __forceinline__ uint32_t scan_tile_counts(TileScan &ts) {
 // Active blocks that have a slot are cache hits (slot stamped with the
 // epoch: "reset the age"); the others are new.  Active blocks whose
 // 2x2x2 +group range (`hull8`) also contains iso are the candidates the
-// triangle stage visits; I_cand holds their positions in I_active.
+// triangle stage visits (ascending block ids).
 
-__global__ void __launch_bounds__(kThreads) cull_kernel(DevState s, Geom g, uint32_t ntiles) {
-    __shared__ TileScan ts;
-    __shared__ TileScan tc;
-    __shared__ uint32_t bal[3][kRounds][8];            // active, new, candidate ballots
+template <int kR>
+struct CullSmem {
+    TileScan<kR> ts, tc;
+    uint32_t bal[3][kR][8];           // active, new, candidate ballots
+};
+
+template <int kR>
+__device__ __forceinline__ void cull_tile(const DevState &s, const Geom &g, uint32_t tile, uint32_t ntiles,
+                                          CullSmem<kR> &sm) {
+    constexpr uint32_t kTile = kR * kThreads;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
     const uint32_t epoch = s.ctl->epoch;
     const float iso = s.ctl->params.iso;
-    const uint32_t lt = (1u << lane) - 1u;
-    while (true) {
-        if (threadIdx.x == 0) ts.tile = atomicAdd(&s.ctl->ctr[kCtrCull], 1u);
-        __syncthreads();
-        const uint32_t tile = ts.tile;
-        if (tile >= ntiles) break;
-        float2 h[kRounds];
+    float2 h[kR];
 #pragma unroll
-        for (int r = 0; r < kRounds; r++) {               // all range loads of the tile first
-            const uint32_t b = tile * kScanTile + r * kThreads + threadIdx.x;
-            h[r] = b < g.nb ? __ldg(s.hull + b) : make_float2(0.f, 0.f);
-        }
+    for (int r = 0; r < kR; r++) {                    // all range loads of the tile first
+        const uint32_t b = tile * kTile + r * kThreads + threadIdx.x;
+        h[r] = b < g.nb ? __ldg(s.hull + b) : make_float2(0.f, 0.f);
+    }
 #pragma unroll
-        for (int r = 0; r < kRounds; r++) {
-            const uint32_t b = tile * kScanTile + r * kThreads + threadIdx.x;
-            const bool act = b < g.nb && (h[r].x < iso) && (iso <= h[r].y);
-            bool nw = false, cand = false;
-            if (act) {
-                const float2 h8 = __ldg(s.hull8 + b);
-                cand = (h8.x < iso) && (iso <= h8.y);
-                const int32_t sl = s.islot[b];
-                if (sl >= 0) s.slast[sl] = epoch;
-                else nw = true;
-            }
-            const uint32_t ab = __ballot_sync(0xffffffffu, act);
-            const uint32_t nbits = __ballot_sync(0xffffffffu, nw);
-            const uint32_t cb = __ballot_sync(0xffffffffu, cand);
-            if (lane == 0) {
-                bal[0][r][warp] = ab;
-                bal[1][r][warp] = nbits;
-                bal[2][r][warp] = cb;
-                ts.cnt[r][warp] = ((uint32_t)__popc(ab) << 16) | (uint32_t)__popc(nbits);
-                tc.cnt[r][warp] = (uint32_t)__popc(cb);
-                const uint32_t first = tile * kScanTile + r * kThreads + warp * 32;
-                if (first < g.nb) s.mactive[first >> 5] = ab;
+    for (int r = 0; r < kR; r++) {
+        const uint32_t b = tile * kTile + r * kThreads + threadIdx.x;
+        const bool act = b < g.nb && (h[r].x < iso) && (iso <= h[r].y);
+        bool nw = false, cand = false;
+        if (act) {
+            const float2 h8 = __ldg(s.hull8 + b);
+            cand = (h8.x < iso) && (iso <= h8.y);
+            const int32_t sl = s.islot[b];
+            if (sl >= 0) s.slast[sl] = epoch;
+            else nw = true;
+        }
+        const uint32_t ab = __ballot_sync(0xffffffffu, act);
+        const uint32_t nbits = __ballot_sync(0xffffffffu, nw);
+        const uint32_t cb = __ballot_sync(0xffffffffu, cand);
+        if (lane == 0) {
+            sm.bal[0][r][warp] = ab;
+            sm.bal[1][r][warp] = nbits;
+            sm.bal[2][r][warp] = cb;
+            sm.ts.cnt[r][warp] = ((uint32_t)__popc(ab) << 16) | (uint32_t)__popc(nbits);
+            sm.tc.cnt[r][warp] = (uint32_t)__popc(cb);
+            const uint32_t first = tile * kTile + r * kThreads + warp * 32;
+            if (first < g.nb) s.mactive[first >> 5] = ab;
+        }
+    }
+    __syncthreads();
+    if (warp == 0) {                       // active and new counts
+        const uint32_t tot = scan_tile_counts(sm.ts);
+        const unsigned long long agg = ((unsigned long long)(tot >> 16) << 31) | (tot & 0xFFFFu);
+        const unsigned long long excl = lookback_exclusive(s.desc_cull, tile, agg, &s.ctl->status, kStatusTimeout);
+        if (lane == 0) {
+            sm.ts.excl = excl;
+            if (tile == ntiles - 1) {
+                const unsigned long long incl = excl + agg;
+                s.ctl->n_active = (uint32_t)(incl >> 31);
+                s.ctl->n_new = (uint32_t)(incl & 0x7FFFFFFFu);
             }
         }
-        __syncthreads();
-        if (warp == 0) {                       // active and new counts
-            const uint32_t tot = scan_tile_counts(ts);
-            const unsigned long long agg = ((unsigned long long)(tot >> 16) << 31) | (tot & 0xFFFFu);
-            const unsigned long long excl = lookback_exclusive(s.desc_cull, tile, agg, &s.ctl->status);
-            if (lane == 0) {
-                ts.excl = excl;
-                if (tile == ntiles - 1) {
-                    const unsigned long long incl = excl + agg;
-                    s.ctl->n_active = (uint32_t)(incl >> 31);
-                    s.ctl->n_new = (uint32_t)(incl & 0x7FFFFFFFu);
-                }
-            }
-        } else if (warp == 1) {                // candidate count, in parallel
-            const uint32_t totc = scan_tile_counts(tc);
-            const unsigned long long exclc = lookback_exclusive(s.desc_cand, tile, totc, &s.ctl->status);
-            if (lane == 0) {
-                tc.excl = exclc;
-                if (tile == ntiles - 1) s.ctl->n_cand = (uint32_t)(exclc + totc);
-            }
+    } else if (warp == 1) {                // candidate count, in parallel
+        const uint32_t totc = scan_tile_counts(sm.tc);
+        const unsigned long long exclc = lookback_exclusive(s.desc_cand, tile, totc, &s.ctl->status, kStatusTimeout);
+        if (lane == 0) {
+            sm.tc.excl = exclc;
+            if (tile == ntiles - 1) s.ctl->n_cand = (uint32_t)(exclc + totc);
         }
-        __syncthreads();
-        const uint32_t act_base = (uint32_t)(ts.excl >> 31), new_base = (uint32_t)(ts.excl & 0x7FFFFFFFu);
-        const uint32_t cand_base = (uint32_t)tc.excl;
+    }
+    __syncthreads();
+    const uint32_t act_base = (uint32_t)(sm.ts.excl >> 31), new_base = (uint32_t)(sm.ts.excl & 0x7FFFFFFFu);
+    const uint32_t cand_base = (uint32_t)sm.tc.excl;
 #pragma unroll 4
-        for (int r = 0; r < kRounds; r++) {
-            const uint32_t b = tile * kScanTile + r * kThreads + threadIdx.x;
-            const uint32_t ab = bal[0][r][warp], nbits = bal[1][r][warp], cb = bal[2][r][warp];
-            const uint32_t off = ts.cnt[r][warp];
-            if ((ab >> lane) & 1u) s.iactive[act_base + (off >> 16) + __popc(ab & lt)] = b;
-            if ((cb >> lane) & 1u) s.icand[cand_base + tc.cnt[r][warp] + __popc(cb & lt)] = b;
-            if ((nbits >> lane) & 1u) s.inew[new_base + (off & 0xFFFFu) + __popc(nbits & lt)] = b;
-        }
-        __syncthreads();
+    for (int r = 0; r < kR; r++) {
+        const uint32_t b = tile * kTile + r * kThreads + threadIdx.x;
+        const uint32_t ab = sm.bal[0][r][warp], nbits = sm.bal[1][r][warp], cb = sm.bal[2][r][warp];
+        const uint32_t off = sm.ts.cnt[r][warp];
+        if ((ab >> lane) & 1u) s.iactive[act_base + (off >> 16) + __popc(ab & lt)] = b;
+        if ((cb >> lane) & 1u) s.icand[cand_base + sm.tc.cnt[r][warp] + __popc(cb & lt)] = b;
+        if ((nbits >> lane) & 1u) s.inew[new_base + (off & 0xFFFFu) + __popc(nbits & lt)] = b;
+    }
+    __syncthreads();
+}
+
+template <int kR, bool kOne>
+__global__ void __launch_bounds__(kThreads) cull_kernel(Launch L) {
+    __shared__ CullSmem<kR> sm;
+    __shared__ uint32_t pre[kMaxBatch + 1];
+    __shared__ uint32_t slot_x;
+    const uint32_t total = launch_prefix<kOne>(
+        L, [&](uint32_t v) { return ceil_div(vol_of<kOne>(L, v).g.nb, kR * kThreads); }, pre);
+    while (true) {
+        const uint32_t x = next_item(&L.ctr[kLcCull], &slot_x);
+        if (x >= total) break;
+        const uint32_t v = item_vol<kOne>(pre, L.n, x);
+        const VolEntry &e = vol_of<kOne>(L, v);
+        cull_tile(e.s, e.g, x - item_base<kOne>(pre, v), vol_items<kOne>(pre, v, total), sm);
     }
 }
 
@@ -222,101 +250,140 @@ __device__ __forceinline__ void assign_slot(const DevState &s, uint32_t slot, ui
     s.newslot[r] = slot;
 }
 
-__global__ void __launch_bounds__(kThreads) lru_a_kernel(DevState s) {
-    __shared__ TileScan ts;
-    __shared__ uint32_t s_status;
-    Ctl *c = s.ctl;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t lt = (1u << lane) - 1u;
-    if (threadIdx.x == 0) s_status = c->status;
-    __syncthreads();
-    if (s_status & kStatusTimeout) {           // counts from the cull may be short: change nothing
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            c->S_next = c->S;
-            c->u_next = c->u;
-            c->n_assign = 0;
-        }
-        return;
-    }
-    const uint32_t epoch = c->epoch, n_active = c->n_active, n_new = c->n_new;
-    const uint32_t S = c->S, u = c->u, cap = c->cap, lpar = c->lpar;
+struct LruPlan {
+    uint32_t S2, n_assign, from_unused, from_used, avail_used;
+    bool fits;
+};
+
+// the update's sizes, from values the cull fixed
+__device__ __forceinline__ LruPlan lru_plan(const Ctl *c) {
+    LruPlan p;
+    const uint32_t n_active = c->n_active, n_new = c->n_new, S = c->S, u = c->u, cap = c->cap;
     const uint32_t n_hit = n_active - n_new;
     const uint32_t n_avail = S - n_hit;
-    uint32_t S2 = S;
-    if (n_new > n_avail) S2 = min(cap, max(2u * S, S + (n_new - n_avail)));
-    const bool fits = n_new <= S2 - n_hit;
-    const uint32_t n_assign = fits ? n_new : 0u;
-    const uint32_t from_unused = min(n_assign, S2 - u);
-    const uint32_t from_used = n_assign - from_unused;
-    const uint32_t avail_used = u - n_hit;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        c->S_next = S2;
-        c->u_next = u + from_unused;
-        c->from_unused = from_unused;
-        c->from_used = from_used;
-        c->keep_base = avail_used - from_used;
-        c->n_assign = n_assign;
-        if (!fits) atomicOr(&c->status, (uint32_t)kStatusBudget);
-    }
-    const uint32_t *L = s.lbuf[lpar];
-    uint32_t *Ln = s.lbuf[lpar ^ 1u];
-    const uint32_t ntiles = (u + kScanTile - 1) / kScanTile;
-    while (true) {
-        if (threadIdx.x == 0) ts.tile = atomicAdd(&c->ctr[kCtrLruA], 1u);
-        __syncthreads();
-        const uint32_t tile = ts.tile;
-        if (tile >= ntiles) break;
-        uint32_t bits[kRounds], slot[kRounds];
-#pragma unroll
-        for (int r = 0; r < kRounds; r++) {
-            const uint32_t i = tile * kScanTile + r * kThreads + threadIdx.x;
-            slot[r] = i < u ? L[i] : 0u;
-        }
-#pragma unroll
-        for (int r = 0; r < kRounds; r++) {
-            const uint32_t i = tile * kScanTile + r * kThreads + threadIdx.x;
-            const bool av = i < u && s.slast[slot[r]] != epoch;
-            bits[r] = __ballot_sync(0xffffffffu, av);
-            if (lane == 0) ts.cnt[r][warp] = (uint32_t)__popc(bits[r]);
-        }
-        __syncthreads();
-        if (warp == 0) {
-            const uint32_t tot = scan_tile_counts(ts);
-            const unsigned long long excl = lookback_exclusive(s.desc_lru_a, tile, tot, &c->status);
-            if (lane == 0) ts.excl = excl;
-        }
-        __syncthreads();
-        const uint32_t base = (uint32_t)ts.excl;
-#pragma unroll
-        for (int r = 0; r < kRounds; r++) {
-            if (!((bits[r] >> lane) & 1u)) continue;
-            const uint32_t rank = base + ts.cnt[r][warp] + __popc(bits[r] & lt);
-            if (rank < from_used) assign_slot(s, slot[r], from_unused + rank, epoch);
-            else Ln[rank - from_used] = slot[r];
-        }
-        __syncthreads();
-    }
-    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < from_unused; r += gridDim.x * blockDim.x)
-        assign_slot(s, u + r, r, epoch);
+    p.S2 = S;
+    if (n_new > n_avail) p.S2 = min(cap, max(2u * S, S + (n_new - n_avail)));
+    p.fits = n_new <= p.S2 - n_hit;
+    p.n_assign = p.fits ? n_new : 0u;
+    p.from_unused = min(p.n_assign, p.S2 - u);
+    p.from_used = p.n_assign - p.from_unused;
+    p.avail_used = u - n_hit;
+    return p;
 }
 
-__global__ void __launch_bounds__(kThreads) lru_b_kernel(DevState s) {
-    __shared__ TileScan ts;
-    __shared__ uint32_t s_status;
-    Ctl *c = s.ctl;
+// Work items of a volume in lru_a: [plan] [tiles of the used-slot list]
+// [chunks of direct assignments from never-used slots].  After a cull
+// timeout the counts may be short: only the plan item runs (no change).
+constexpr uint32_t kAssignChunk = 1024;
+
+__device__ __forceinline__ uint32_t lru_a_items(const Ctl *c) {
+    if (c->status & kStatusTimeout) return 1u;
+    const LruPlan p = lru_plan(c);
+    return 1u + ceil_div(c->u, kScanTile) + ceil_div(p.from_unused, kAssignChunk);
+}
+
+template <bool kOne>
+__global__ void __launch_bounds__(kThreads) lru_a_kernel(Launch L) {
+    __shared__ TileScan<kRounds> ts;
+    __shared__ uint32_t pre[kMaxBatch + 1];
+    __shared__ uint32_t slot_x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
-    if (threadIdx.x == 0) s_status = c->status;
-    __syncthreads();
-    if (s_status & kStatusTimeout) return;
-    const uint32_t epoch = c->epoch, S2 = c->S_next, keep = c->keep_base;
-    uint32_t *Ln = s.lbuf[c->lpar ^ 1u];
-    const uint32_t ntiles = (S2 + kScanTile - 1) / kScanTile;
+    const uint32_t total =
+        launch_prefix<kOne>(L, [&](uint32_t v) { return lru_a_items(vol_of<kOne>(L, v).s.ctl); }, pre);
     while (true) {
-        if (threadIdx.x == 0) ts.tile = atomicAdd(&c->ctr[kCtrLruB], 1u);
-        __syncthreads();
-        const uint32_t tile = ts.tile;
-        if (tile >= ntiles) break;
+        const uint32_t x = next_item(&L.ctr[kLcLruA], &slot_x);
+        if (x >= total) break;
+        const uint32_t v = item_vol<kOne>(pre, L.n, x);
+        const DevState &s = vol_of<kOne>(L, v).s;
+        Ctl *c = s.ctl;
+        const uint32_t item = x - item_base<kOne>(pre, v);
+        const uint32_t epoch = c->epoch, u = c->u;
+        if (item == 0) {                                // the plan
+            if (threadIdx.x == 0) {
+                if (c->status & kStatusTimeout) {
+                    c->S_next = c->S;
+                    c->u_next = u;
+                    c->n_assign = 0;
+                    c->keep_base = 0;
+                } else {
+                    const LruPlan p = lru_plan(c);
+                    c->S_next = p.S2;
+                    c->u_next = u + p.from_unused;
+                    c->from_unused = p.from_unused;
+                    c->from_used = p.from_used;
+                    c->keep_base = p.avail_used - p.from_used;
+                    c->n_assign = p.n_assign;
+                    if (!p.fits) atomicOr(&c->status, (uint32_t)kStatusBudget);
+                }
+            }
+            continue;                                   // block-uniform
+        }
+        const LruPlan p = lru_plan(c);
+        const uint32_t ntiles = ceil_div(u, kScanTile);
+        if (item <= ntiles) {                           // a tile of the used-slot list
+            const uint32_t tile = item - 1;
+            const uint32_t *Lst = s.lbuf[c->lpar];
+            uint32_t *Ln = s.lbuf[c->lpar ^ 1u];
+            uint32_t bits[kRounds], slot[kRounds];
+#pragma unroll
+            for (int r = 0; r < kRounds; r++) {
+                const uint32_t i = tile * kScanTile + r * kThreads + threadIdx.x;
+                slot[r] = i < u ? Lst[i] : 0u;
+            }
+#pragma unroll
+            for (int r = 0; r < kRounds; r++) {
+                const uint32_t i = tile * kScanTile + r * kThreads + threadIdx.x;
+                const bool av = i < u && s.slast[slot[r]] != epoch;
+                bits[r] = __ballot_sync(0xffffffffu, av);
+                if (lane == 0) ts.cnt[r][warp] = (uint32_t)__popc(bits[r]);
+            }
+            __syncthreads();
+            if (warp == 0) {
+                const uint32_t tot = scan_tile_counts(ts);
+                const unsigned long long excl = lookback_exclusive(s.desc_lru_a, tile, tot, &c->status, kStatusTimeoutLru);
+                if (lane == 0) ts.excl = excl;
+            }
+            __syncthreads();
+            const uint32_t base = (uint32_t)ts.excl;
+#pragma unroll
+            for (int r = 0; r < kRounds; r++) {
+                if (!((bits[r] >> lane) & 1u)) continue;
+                const uint32_t rank = base + ts.cnt[r][warp] + __popc(bits[r] & lt);
+                if (rank < p.from_used) assign_slot(s, slot[r], p.from_unused + rank, epoch);
+                else Ln[rank - p.from_used] = slot[r];
+            }
+            __syncthreads();
+        } else {                                        // never-used slots go straight to new blocks
+            const uint32_t r0 = (item - 1 - ntiles) * kAssignChunk, r1 = min(p.from_unused, r0 + kAssignChunk);
+            for (uint32_t r = r0 + threadIdx.x; r < r1; r += kThreads) assign_slot(s, u + r, r, epoch);
+        }
+    }
+}
+
+template <bool kOne>
+__global__ void __launch_bounds__(kThreads) lru_b_kernel(Launch L) {
+    __shared__ TileScan<kRounds> ts;
+    __shared__ uint32_t pre[kMaxBatch + 1];
+    __shared__ uint32_t slot_x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    // after a cull timeout the volume's cache is emptied by the host: no tiles
+    const uint32_t total = launch_prefix<kOne>(
+        L, [&](uint32_t v) {
+            const Ctl *c = vol_of<kOne>(L, v).s.ctl;
+            return (c->status & kStatusTimeout) ? 0u : ceil_div(c->S_next, kScanTile);
+        },
+        pre);
+    while (true) {
+        const uint32_t x = next_item(&L.ctr[kLcLruB], &slot_x);
+        if (x >= total) break;
+        const uint32_t v = item_vol<kOne>(pre, L.n, x);
+        const DevState &s = vol_of<kOne>(L, v).s;
+        Ctl *c = s.ctl;
+        const uint32_t tile = x - item_base<kOne>(pre, v);
+        const uint32_t epoch = c->epoch, S2 = c->S_next, keep = c->keep_base;
+        uint32_t *Ln = s.lbuf[c->lpar ^ 1u];
         uint32_t bits[kRounds];
 #pragma unroll
         for (int r = 0; r < kRounds; r++) {
@@ -328,7 +395,7 @@ __global__ void __launch_bounds__(kThreads) lru_b_kernel(DevState s) {
         __syncthreads();
         if (warp == 0) {
             const uint32_t tot = scan_tile_counts(ts);
-            const unsigned long long excl = lookback_exclusive(s.desc_lru_b, tile, tot, &c->status);
+            const unsigned long long excl = lookback_exclusive(s.desc_lru_b, tile, tot, &c->status, kStatusTimeoutLru);
             if (lane == 0) ts.excl = excl;
         }
         __syncthreads();
@@ -344,28 +411,90 @@ __global__ void __launch_bounds__(kThreads) lru_b_kernel(DevState s) {
 }
 
 // ================================================================ decode (Section 4.2.1)
+//
+// Chunks of kDecodeThreads new blocks, one block per thread.  Chunk 0 of
+// every volume (each volume has at least one) also commits the volume's
+// cache update.
 
-constexpr int kDecodeThreads = 128;
-
-__global__ void __launch_bounds__(kDecodeThreads) decode_new_kernel(DevState s, Geom g) {
-    __shared__ uint64_t planes[32 * kDecodeThreads];
-    Ctl *c = s.ctl;
-    if (c->status & kStatusTimeout) return;      // no barrier in this kernel: per-thread exit is safe
-    const uint32_t n = c->n_assign;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {   // commit the cache update
-        c->S = c->S_next;
-        c->u = c->u_next;
-        c->lpar ^= 1u;
-    }
-    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+template <int kDecodeThreads, bool kOne>
+__global__ void __launch_bounds__(kDecodeThreads) decode_new_kernel(Launch L) {
+    extern __shared__ uint64_t planes[];              // 32 * kDecodeThreads words (dynamic)
+    __shared__ uint32_t pre[kMaxBatch + 1];
+    const uint32_t total = launch_prefix<kOne>(
+        L, [&](uint32_t v) { return max(1u, ceil_div(vol_of<kOne>(L, v).s.ctl->n_assign, kDecodeThreads)); },
+        pre);
+    for (uint32_t x = blockIdx.x; x < total; x += gridDim.x) {
+        const uint32_t v = item_vol<kOne>(pre, L.n, x);
+        const DevState &s = vol_of<kOne>(L, v).s;
+        Ctl *c = s.ctl;
+        const uint32_t chunk = x - item_base<kOne>(pre, v);
+        if (c->status & kStatusAnyTimeout) continue;  // no barrier in this loop: per-thread skips are safe
+        if (chunk == 0 && threadIdx.x == 0) {         // commit the cache update
+            c->S = c->S_next;
+            c->u = c->u_next;
+            c->lpar ^= 1u;
+        }
+        const uint32_t r = chunk * kDecodeThreads + threadIdx.x;
+        if (r >= c->n_assign) continue;
+        const uint32_t rate = vol_of<kOne>(L, v).g.rate;
         const uint32_t b = s.inew[r];
         const uint32_t slot = s.newslot[r];
-        float v[64];
-        decode_block(s.bits + (size_t)b * g.rate, g.rate, v, planes + threadIdx.x, kDecodeThreads);
+        float val[64];
+        decode_block(s.bits + (size_t)b * rate, rate, val, planes + threadIdx.x, kDecodeThreads);
         float4 *dst = reinterpret_cast<float4 *>(s.slots + (size_t)slot * 64);
 #pragma unroll
-        for (int i = 0; i < 16; i++) dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+        for (int i = 0; i < 16; i++) dst[i] = make_float4(val[4 * i], val[4 * i + 1], val[4 * i + 2], val[4 * i + 3]);
     }
+}
+
+// ================================================================ batch bookkeeping
+
+__global__ void batch_params_kernel(Launch L, const float *__restrict__ iso) {
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < L.n; v += gridDim.x * blockDim.x)
+        L.vols[v].s.ctl->params.iso = iso[v];
+}
+
+// One block: place the volumes' surfaces one after another in the batch's
+// output (volume v starts after the triangles of volumes 0..v-1 and may
+// use the rest of the buffer).
+__global__ void __launch_bounds__(kThreads) batch_offsets_kernel(Launch L, const BatchOut *__restrict__ bo,
+                                                                 unsigned long long *tri_base) {
+    __shared__ unsigned long long warp_tot[kThreads / 32];
+    const uint32_t per = (L.n + kThreads - 1) / kThreads;
+    const uint32_t v0 = threadIdx.x * per;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long sum = 0;
+    for (uint32_t k = 0; k < per; k++)
+        if (v0 + k < L.n) sum += L.vols[v0 + k].s.ctl->n_tri;
+    unsigned long long incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    unsigned long long run = incl - sum;
+    for (int w = 0; w < warp; w++) run += warp_tot[w];
+    const unsigned long long out = bo->out, cap = bo->tri_cap;
+    for (uint32_t k = 0; k < per; k++) {
+        const uint32_t v = v0 + k;
+        if (v >= L.n) break;
+        Ctl *c = L.vols[v].s.ctl;
+        tri_base[v] = run;
+        c->params.out = out + run * 3 * sizeof(float4);
+        c->params.tri_cap = run < cap ? cap - run : 0ull;
+        run += c->n_tri;
+        if (v == L.n - 1) tri_base[L.n] = run;
+    }
+}
+
+// copy every volume's control block into one array (one readback)
+__global__ void batch_gather_kernel(Launch L, Ctl *dst) {
+    constexpr uint32_t kWords = sizeof(Ctl) / 4;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < L.n * kWords; i += gridDim.x * blockDim.x)
+        reinterpret_cast<uint32_t *>(dst)[i] =
+            reinterpret_cast<const uint32_t *>(L.vols[i / kWords].s.ctl)[i % kWords];
 }
 
 // ================================================================ load-time and utility kernels
@@ -433,23 +562,40 @@ __global__ void gather_slots_kernel(const float *__restrict__ slots, const int32
 
 // ================================================================ launchers
 
-void launch_prep(const DevState &s, uint32_t n_cull_desc, uint32_t n_lru_desc, bool mc_only, int grid,
-                 cudaStream_t st) {
-    prep_kernel<<<grid, kThreads, 0, st>>>(s, n_cull_desc, n_lru_desc, mc_only ? 1 : 0);
+constexpr size_t decode_smem(int threads) { return 32u * 8u * (size_t)threads; }
+
+template <bool kOne>
+void front(const Launch &L, const Plan &pl, cudaStream_t st, cudaEvent_t *ev) {
+    prep_kernel<kOne><<<pl.prep, kThreads, 0, st>>>(L);
+    if (ev) cudaEventRecord(ev[1], st);
+    if (pl.cull_tile == 2048) cull_kernel<8, kOne><<<pl.cull, kThreads, 0, st>>>(L);
+    else cull_kernel<16, kOne><<<pl.cull, kThreads, 0, st>>>(L);
+    if (ev) cudaEventRecord(ev[2], st);
+    lru_a_kernel<kOne><<<pl.lru_a, kThreads, 0, st>>>(L);
+    lru_b_kernel<kOne><<<pl.lru_b, kThreads, 0, st>>>(L);
+    if (ev) cudaEventRecord(ev[3], st);
+    if (pl.decode_tile == 64) decode_new_kernel<64, kOne><<<pl.decode, 64, decode_smem(64), st>>>(L);
+    else if (pl.decode_tile == 256) decode_new_kernel<256, kOne><<<pl.decode, 256, decode_smem(256), st>>>(L);
+    else decode_new_kernel<128, kOne><<<pl.decode, 128, decode_smem(128), st>>>(L);
+    if (ev) cudaEventRecord(ev[4], st);
 }
 
-void launch_cull(const DevState &s, const Geom &g, int grid, cudaStream_t st) {
-    const uint32_t ntiles = (g.nb + kScanTile - 1) / kScanTile;
-    cull_kernel<<<(int)std::min<uint32_t>(ntiles, (uint32_t)grid), kThreads, 0, st>>>(s, g, ntiles);
+void launch_front(const Launch &L, const Plan &pl, cudaStream_t st, cudaEvent_t *ev) {
+    if (L.vols) front<false>(L, pl, st, ev);
+    else front<true>(L, pl, st, ev);
 }
 
-void launch_lru(const DevState &s, int grid_a, int grid_b, cudaStream_t st) {
-    lru_a_kernel<<<grid_a, kThreads, 0, st>>>(s);
-    lru_b_kernel<<<grid_b, kThreads, 0, st>>>(s);
+void launch_batch_params(const Launch &L, const float *d_iso, cudaStream_t st) {
+    batch_params_kernel<<<(L.n + 255) / 256, 256, 0, st>>>(L, d_iso);
 }
 
-void launch_decode_new(const DevState &s, const Geom &g, int grid, cudaStream_t st) {
-    decode_new_kernel<<<grid, kDecodeThreads, 0, st>>>(s, g);
+void launch_batch_offsets(const Launch &L, const BatchOut *bo, unsigned long long *tri_base, cudaStream_t st) {
+    batch_offsets_kernel<<<1, kThreads, 0, st>>>(L, bo, tri_base);
+}
+
+void launch_batch_gather(const Launch &L, Ctl *dst, cudaStream_t st) {
+    const uint32_t words = L.n * (uint32_t)(sizeof(Ctl) / 4);
+    batch_gather_kernel<<<(words + 255) / 256, 256, 0, st>>>(L, dst);
 }
 
 void launch_hull(const float *bmin, const float *bmax, float2 *hull, float2 *hull8, const Geom &g,
@@ -470,20 +616,50 @@ void launch_gather_slots(const float *slots, const int32_t *islot, const uint32_
     gather_slots_kernel<<<(unsigned)blocks, 256, 0, st>>>(slots, islot, ids, n, out, missing);
 }
 
-Grids compute_grids(int sm_count) {
-    Grids gr{};
+template <bool kOne>
+void set_decode_attributes() {
+    cudaFuncSetAttribute(decode_new_kernel<64, kOne>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)decode_smem(64));
+    cudaFuncSetAttribute(decode_new_kernel<128, kOne>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)decode_smem(128));
+    cudaFuncSetAttribute(decode_new_kernel<256, kOne>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)decode_smem(256));
+}
+
+template <bool kOne>
+Plan limits_of(const Plan &tiles) {
+    Plan pl = tiles;
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cull_kernel, kThreads, 0);
-    gr.cull = std::max(1, occ) * sm_count;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lru_a_kernel, kThreads, 0);
-    gr.lru_a = std::max(1, occ) * sm_count;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lru_b_kernel, kThreads, 0);
-    gr.lru_b = std::max(1, occ) * sm_count;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, decode_new_kernel, kDecodeThreads, 0);
-    gr.decode = std::max(1, occ) * sm_count;
-    mc_grids(sm_count, &gr);
-    gr.prep = 2 * sm_count;
-    return gr;
+    if (tiles.cull_tile == 2048) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cull_kernel<8, kOne>, kThreads, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cull_kernel<16, kOne>, kThreads, 0);
+    pl.cull = std::max(1, occ);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lru_a_kernel<kOne>, kThreads, 0);
+    pl.lru_a = std::max(1, occ);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lru_b_kernel<kOne>, kThreads, 0);
+    pl.lru_b = std::max(1, occ);
+    set_decode_attributes<false>();
+    set_decode_attributes<true>();
+    if (tiles.decode_tile == 64)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, decode_new_kernel<64, kOne>, 64, decode_smem(64));
+    else if (tiles.decode_tile == 256)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, decode_new_kernel<256, kOne>, 256, decode_smem(256));
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, decode_new_kernel<128, kOne>, 128, decode_smem(128));
+    pl.decode = std::max(1, occ);
+    mc_occupancy(&pl, kOne);
+    pl.prep = 2;
+    return pl;
+}
+
+Plan occupancy_limits(const Plan &tiles, bool single) {
+    return single ? limits_of<true>(tiles) : limits_of<false>(tiles);
+}
+
+bool valid_tiles(const Plan &pl) {
+    return (pl.cull_tile == 2048 || pl.cull_tile == 4096) &&
+           (pl.decode_tile == 64 || pl.decode_tile == 128 || pl.decode_tile == 256) &&
+           (pl.count_tile == 16 || pl.count_tile == 32 || pl.count_tile == 64) &&
+           (pl.scan_tile == 1024 || pl.scan_tile == 2048 || pl.scan_tile == 4096) &&
+           (pl.emit_tile == 16 || pl.emit_tile == 32 || pl.emit_tile == 64);
 }
 
 }  // namespace bcmc

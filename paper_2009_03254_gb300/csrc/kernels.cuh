@@ -34,21 +34,69 @@ struct DevState {
     unsigned long long *dbg_edges;
 };
 
-struct Grids {                 // CTAs per launch, from occupancy at load time
-    int prep, cull, lru_a, lru_b, decode, mc_count, mc_scan, mc_emit;
+// One volume of a launch: its device state, geometry and the sizes of
+// its look-back descriptor arrays.  Kept in device memory (a table of one
+// entry for a single extraction, of many for a batch).
+struct VolEntry {
+    DevState s;
+    Geom g;
+    uint32_t n_cull_desc, n_lru_desc;
+};
+
+constexpr uint32_t kMaxBatch = 1024;     // volumes per launch
+
+// What every stage kernel receives: the volumes and the launch's work
+// counters (kNumLaunchCounters words, cleared by the prep kernel).  A
+// single volume travels by value in the launch parameters (`one`, with
+// vols == nullptr and n == 1), so its kernels read its pointers from the
+// constant bank; a batch passes a device table.
+struct Launch {
+    const VolEntry *vols;
+    uint32_t n;
+    uint32_t *ctr;
+    VolEntry one;
+};
+
+// How a launch sequence runs: the CTAs of each persistent kernel and the
+// tile size of each kernel that has a choice.  Any choice computes the
+// same results; the batch autotuner picks the fastest.
+struct Plan {
+    int prep, cull, lru_a, lru_b, decode, mc_count, mc_scan, mc_emit;   // CTAs per launch
+    int cull_tile;       // block ranges per cull tile: 2048 or 4096
+    int decode_tile;     // new blocks per decode CTA (one per thread): 64, 128 or 256
+    int count_tile;      // candidates per count CTA round (4 per warp): 16, 32 or 64
+    int scan_tile;       // counts per offset-scan tile: 1024, 2048 or 4096
+    int emit_tile;       // candidates per emit CTA round (4 per warp): 16, 32 or 64
 };
 
 constexpr int kThreads = 256;
-constexpr int kScanTile = 4096;          // entries per tile of the cull / cache scans
+constexpr int kScanTile = 4096;          // entries per tile of the cache-update scans
+constexpr int kMinCullTile = 2048;       // smallest cull tile (sizes the cull descriptors)
+constexpr int kMinMcScanTile = 1024;     // smallest offset-scan tile (sizes its descriptors)
+constexpr int kDefaultCullTile = 4096, kDefaultDecodeTile = 128, kDefaultCountTile = 32,
+              kDefaultScanTile = 2048, kDefaultEmitTile = 32;
 
 // The isovalue, output buffer and its capacity are read from Ctl::params.
-void launch_prep(const DevState &s, uint32_t n_cull_desc, uint32_t n_lru_desc, bool mc_only, int grid,
-                 cudaStream_t st);
-void launch_cull(const DevState &s, const Geom &g, int grid, cudaStream_t st);
-void launch_lru(const DevState &s, int grid_a, int grid_b, cudaStream_t st);
-void launch_decode_new(const DevState &s, const Geom &g, int grid, cudaStream_t st);
-// triangle stage: count, scan, emit (emit_only: just the last, into a new output)
-void launch_mc(const DevState &s, const Geom &g, bool debug, bool emit_only, const Grids &gr, cudaStream_t st);
+// Front of the pipeline: prep, cull, cache update (two kernels), decode.
+// With `ev`, events ev[1..4] are recorded after prep, cull, cache update
+// and decode.
+void launch_front(const Launch &L, const Plan &pl, cudaStream_t st, cudaEvent_t *ev);
+// triangle stage: count, scan, emit.  A batch places the volumes' outputs
+// between scan and emit; a rerun into a larger output runs emit alone.
+void launch_mc_count(const Launch &L, bool debug, const Plan &pl, cudaStream_t st);
+void launch_mc_scan(const Launch &L, const Plan &pl, cudaStream_t st);
+void launch_mc_emit(const Launch &L, bool debug, const Plan &pl, cudaStream_t st);
+// batches: per-volume isovalues from a packed array; the volumes' outputs
+// placed one after another in `bo->out` (tri_base[v] = first triangle of
+// volume v, tri_base[n] = total); control blocks gathered for one readback
+struct BatchOut {
+    unsigned long long out;        // float4 * vertex buffer
+    unsigned long long tri_cap;    // its capacity in triangles
+};
+void launch_batch_params(const Launch &L, const float *d_iso, cudaStream_t st);
+void launch_batch_offsets(const Launch &L, const BatchOut *bo, unsigned long long *tri_base, cudaStream_t st);
+void launch_batch_gather(const Launch &L, Ctl *dst, cudaStream_t st);
+
 void launch_hull(const float *bmin, const float *bmax, float2 *hull, float2 *hull8, const Geom &g,
                  cudaStream_t st);
 void launch_reset_cache(const DevState &s, cudaStream_t st);
@@ -58,8 +106,13 @@ void launch_decode_list(const uint64_t *bits, uint32_t rate, const uint32_t *ids
 void launch_gather_slots(const float *slots, const int32_t *islot, const uint32_t *ids, uint64_t n, float *out,
                          int32_t *missing, cudaStream_t st);
 
-// occupancy-derived persistent grid sizes
-Grids compute_grids(int sm_count);
-void mc_grids(int sm_count, Grids *gr);   // also raises the emit kernel's shared-memory limit
+// The most CTAs of each kernel one SM holds, for the tile variants in
+// `tiles`, in single-volume or batch launches (CTA fields of the result;
+// tile fields copied).  Also raises the shared-memory limits of every
+// kernel that needs more than the default.
+Plan occupancy_limits(const Plan &tiles, bool single);
+void mc_occupancy(Plan *pl, bool single);
+// tile sizes that the kernels are compiled for
+bool valid_tiles(const Plan &pl);
 
 }  // namespace bcmc

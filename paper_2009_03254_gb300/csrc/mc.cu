@@ -24,22 +24,24 @@
 //      per lane, issued together)
 //   C  classify: four ballots give the 125 below-iso bits; each cell's
 //      case is 8 bits picked from them; counts from the case table
+//
+// Over a batch, warp tiles are numbered volume after volume; a warp tile
+// never spans two volumes.
 #include <algorithm>
 #include <cstdint>
 
 #include "common.cuh"
 #include "kernels.cuh"
+#include "launch.cuh"
 #include "mc_tables.cuh"
 
 namespace bcmc {
 
 namespace {
 
-constexpr int kWarps = kThreads / 32;                 // 8
 constexpr int kBPW = 4;                               // candidates per warp tile
 constexpr int kHalo = 200;                            // x + 8y + 40z, x,y,z in [0,5)
 constexpr int kTmap = kBPW * 64 * 5;                  // triangles a warp tile can hold
-constexpr int kScanItems = 2048;                      // counts per scan tile
 
 struct WarpTile {                                     // one warp's shared-memory area
     float halo[kBPW][kHalo];
@@ -49,16 +51,17 @@ struct WarpTile {                                     // one warp's shared-memor
     uint8_t cases[kBPW][64];
 };
 
+template <int kW>                                     // warps per CTA
 struct CountSmem {
-    WarpTile w[kWarps];
+    WarpTile w[kW];
     uint8_t num_tri[256];
-    uint32_t occ;
 };
 
+template <int kW>
 struct EmitSmem {
-    WarpTile w[kWarps];
-    float4 stage[kWarps][96];                         // 32 triangles' vertices per warp
-    uint16_t tmap[kWarps][kTmap];                     // block-in-tile (2) | cell (6) | k (3)
+    WarpTile w[kW];
+    float4 stage[kW][96];                             // 32 triangles' vertices per warp
+    uint16_t tmap[kW][kTmap];                         // block-in-tile (2) | cell (6) | k (3)
     uint32_t tri_row[256 * kMaxTriPerCell];           // 3 edge numbers of each table triangle, packed
     uint8_t num_tri[256];
     uint32_t edge_info[12];
@@ -213,79 +216,119 @@ __device__ __forceinline__ uint32_t warp_sum(uint32_t x) {
     return x;
 }
 
+// candidates the triangle stage visits: none once the cache update failed
+// (both bits are final before the count kernel starts)
+__device__ __forceinline__ uint32_t mc_candidates(const Ctl *c) {
+    return (c->status & (kStatusBudget | kStatusTimeout | kStatusTimeoutLru)) ? 0u : c->n_cand;
+}
+
+// A warp tile located in the launch: volume, first candidate, candidates
+// used, and this lane's block id (candidate first + lane/8), read ahead.
+struct TileRef {
+    uint32_t v, base, nb_w, b;
+};
+
+template <bool kOne>
+__device__ __forceinline__ TileRef locate_tile(const Launch &L, const uint32_t *pre, uint32_t t, uint32_t total) {
+    TileRef r{0u, 0u, 0u, 0u};
+    if (t >= total) return r;
+    r.v = item_vol<kOne>(pre, L.n, t);
+    const DevState &s = vol_of<kOne>(L, r.v).s;
+    const uint32_t n_cand = s.ctl->n_cand;
+    r.base = (t - item_base<kOne>(pre, r.v)) * kBPW;
+    r.nb_w = min((uint32_t)kBPW, n_cand - r.base);
+    const uint32_t i = r.base + ((uint32_t)(threadIdx.x & 31) >> 3);
+    r.b = i < n_cand ? s.icand[i] : 0u;
+    return r;
+}
+
 }  // namespace
 
 // ================================================================ count (Section 4.4)
 
-template <bool kDebug>
-__global__ void __launch_bounds__(kThreads) mc_count_kernel(DevState s, Geom g) {
-    __shared__ CountSmem sm;
-    Ctl *c = s.ctl;
+template <int kW, bool kDebug, bool kOne>
+__global__ void __launch_bounds__(32 * kW) mc_count_kernel(Launch L) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    CountSmem<kW> &sm = *reinterpret_cast<CountSmem<kW> *>(smem_raw);
+    __shared__ uint32_t pre[kMaxBatch + 1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i = threadIdx.x; i < 256; i += kThreads) sm.num_tri[i] = s.tables[i];
-    if (threadIdx.x == 0) sm.occ = 0;
-    __syncthreads();
-    const bool failed = (c->status & (kStatusBudget | kStatusTimeout)) != 0;   // nothing below changes it
-    const uint32_t n_cand = failed ? 0u : c->n_cand;
-    const float iso = c->params.iso;
-    const uint32_t nwt = (n_cand + kBPW - 1) / kBPW;
+    const uint8_t *tables = vol_of<kOne>(L, 0).s.tables;
+    for (int i = threadIdx.x; i < 256; i += 32 * kW) sm.num_tri[i] = tables[i];
+    const uint32_t total = launch_prefix<kOne>(
+        L, [&](uint32_t v) { return ceil_div(mc_candidates(vol_of<kOne>(L, v).s.ctl), kBPW); }, pre);
+    __syncthreads();                                      // the table
     LaneConst lc;
     lc.init(lane);
     WarpTile &wt = sm.w[warp];
-    uint32_t occ = 0;
-    const uint32_t stride = gridDim.x * kWarps;
-    uint32_t t = blockIdx.x * kWarps + warp;
-    const uint32_t bq = (uint32_t)lane >> 3;
-    uint32_t b_next = t < nwt && t * kBPW + bq < n_cand ? s.icand[t * kBPW + bq] : 0u;
-    for (; t < nwt; t += stride) {
-        const uint32_t base = t * kBPW;
-        const int nb_w = (int)min((uint32_t)kBPW, n_cand - base);
-        const uint32_t b = b_next;
-        const uint32_t tn = t + stride;                   // next warp tile's block, loaded early
-        b_next = tn < nwt && tn * kBPW + bq < n_cand ? s.icand[tn * kBPW + bq] : 0u;
+    const uint32_t stride = gridDim.x * kW;
+    uint32_t t = blockIdx.x * kW + warp;
+    TileRef nxt = locate_tile<kOne>(L, pre, t, total);
+    uint32_t occ = 0, occ_v = nxt.v;
+    for (; t < total; t += stride) {
+        const TileRef cur = nxt;
+        nxt = locate_tile<kOne>(L, pre, t + stride, total);   // next warp tile's block, loaded early
+        if (!kOne && cur.v != occ_v) {                          // flush the previous volume's occupied count
+            occ = warp_sum(occ);
+            if (lane == 0 && occ) atomicAdd(&vol_of<kOne>(L, occ_v).s.ctl->n_occ, occ);
+            occ = 0;
+            occ_v = cur.v;
+        }
+        const DevState &s = vol_of<kOne>(L, cur.v).s;
+        const float iso = s.ctl->params.iso;
         uint32_t n0p, n1p;
-        stage_and_classify<false, kDebug>(s, g, iso, base, nb_w, b, wt, lc, sm.num_tri, n0p, n1p);
+        stage_and_classify<false, kDebug>(s, vol_of<kOne>(L, cur.v).g, iso, cur.base, (int)cur.nb_w, cur.b, wt, lc,
+                                          sm.num_tri, n0p, n1p);
         const uint32_t r0 = warp_sum(n0p), r1 = warp_sum(n1p);   // per-byte sums <= 160: no carries
-        if (lane < nb_w) {
+        if (lane < (int)cur.nb_w) {
             const uint32_t cnt = ((r0 >> (8 * lane)) & 0xFFu) + ((r1 >> (8 * lane)) & 0xFFu);
-            s.counts[base + lane] = cnt;
+            s.counts[cur.base + lane] = cnt;
             occ += cnt > 0;
         }
     }
     occ = warp_sum(occ);
-    if (lane == 0 && occ) atomicAdd(&sm.occ, occ);
-    __syncthreads();
-    if (threadIdx.x == 0 && sm.occ) atomicAdd(&c->n_occ, sm.occ);
+    if (lane == 0 && occ) atomicAdd(&vol_of<kOne>(L, occ_v).s.ctl->n_occ, occ);
 }
 
 // ================================================================ scan (Section 4.4)
 //
 // Exclusive prefix of the candidates' counts -> 64-bit offsets; the last
-// tile writes the total.  kScanItems counts per tile, 8 per thread.
+// tile of a volume writes its total.  kScanItems = 256 * kPT counts per
+// tile, kPT per thread.  Every volume has at least one item; its item 0
+// records how many look-back descriptors the volume used (the next prep
+// clears them).
 
-__global__ void __launch_bounds__(kThreads) mc_scan_kernel(DevState s) {
+template <int kPT, bool kOne>
+__global__ void __launch_bounds__(kThreads) mc_scan_kernel(Launch L) {
+    constexpr int kWarps = kThreads / 32;
+    constexpr uint32_t kScanItems = kThreads * kPT;
     __shared__ uint32_t wsum[kWarps];
     __shared__ unsigned long long s_excl;
-    __shared__ uint32_t s_tile, s_status;
-    Ctl *c = s.ctl;
+    __shared__ uint32_t pre[kMaxBatch + 1];
+    __shared__ uint32_t s_item;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (threadIdx.x == 0) s_status = c->status;      // one read per block: the loop below has barriers
-    __syncthreads();
-    const bool failed = (s_status & (kStatusBudget | kStatusTimeout)) != 0;
-    const uint32_t n = failed ? 0u : c->n_cand;
-    const uint32_t ntiles = (n + kScanItems - 1) / kScanItems;
-    if (blockIdx.x == 0 && threadIdx.x == 0) c->mc_tiles = ntiles;
+    const uint32_t total = launch_prefix<kOne>(
+        L, [&](uint32_t v) { return max(1u, ceil_div(mc_candidates(vol_of<kOne>(L, v).s.ctl), kScanItems)); },
+        pre);
     while (true) {
-        if (threadIdx.x == 0) s_tile = atomicAdd(&c->ctr[kCtrMc], 1u);
+        if (threadIdx.x == 0) s_item = atomicAdd(&L.ctr[kLcScan], 1u);
         __syncthreads();
-        const uint32_t tile = s_tile;
-        if (tile >= ntiles) break;
-        const uint32_t i0 = tile * kScanItems + threadIdx.x * 8;
-        uint32_t v[8], sum = 0;
+        const uint32_t x = s_item;
+        __syncthreads();
+        if (x >= total) break;
+        const uint32_t v = item_vol<kOne>(pre, L.n, x);
+        const DevState &s = vol_of<kOne>(L, v).s;
+        Ctl *c = s.ctl;
+        const uint32_t tile = x - item_base<kOne>(pre, v);
+        const uint32_t n = mc_candidates(c);
+        const uint32_t ntiles = ceil_div(n, kScanItems);
+        if (tile == 0 && threadIdx.x == 0) c->mc_tiles = ntiles;
+        if (ntiles == 0) continue;                        // block-uniform
+        const uint32_t i0 = tile * kScanItems + threadIdx.x * kPT;
+        uint32_t v8[kPT], sum = 0;
 #pragma unroll
-        for (int k = 0; k < 8; k++) {
-            v[k] = i0 + k < n ? s.counts[i0 + k] : 0u;
-            sum += v[k];
+        for (int k = 0; k < kPT; k++) {
+            v8[k] = i0 + k < n ? s.counts[i0 + k] : 0u;
+            sum += v8[k];
         }
         uint32_t incl = sum;
 #pragma unroll
@@ -305,7 +348,7 @@ __global__ void __launch_bounds__(kThreads) mc_scan_kernel(DevState s) {
             }
             const uint32_t tot = __shfl_sync(0xffffffffu, wi, kWarps - 1);
             if (lane < kWarps) wsum[lane] = wi - w;                      // exclusive warp offsets
-            const unsigned long long excl = lookback_exclusive(s.desc_mc, tile, tot, &c->status);
+            const unsigned long long excl = lookback_exclusive(s.desc_mc, tile, tot, &c->status, kStatusTimeoutScan);
             if (lane == 0) {
                 s_excl = excl;
                 if (tile == ntiles - 1) c->n_tri = excl + tot;
@@ -314,25 +357,25 @@ __global__ void __launch_bounds__(kThreads) mc_scan_kernel(DevState s) {
         __syncthreads();
         unsigned long long run = s_excl + wsum[warp] + (incl - sum);
 #pragma unroll
-        for (int k = 0; k < 8; k++) {
+        for (int k = 0; k < kPT; k++) {
             if (i0 + k < n) s.offsets[i0 + k] = run;
-            run += v[k];
+            run += v8[k];
         }
-        __syncthreads();
     }
 }
 
 // ================================================================ emit (Section 4.5)
 
-template <bool kDebug>
-__global__ void __launch_bounds__(kThreads) mc_emit_kernel(DevState s, Geom g) {
+template <int kW, bool kDebug, bool kOne>
+__global__ void __launch_bounds__(32 * kW) mc_emit_kernel(Launch L) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    EmitSmem &sm = *reinterpret_cast<EmitSmem *>(smem_raw);
-    Ctl *c = s.ctl;
+    EmitSmem<kW> &sm = *reinterpret_cast<EmitSmem<kW> *>(smem_raw);
+    __shared__ uint32_t pre[kMaxBatch + 1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i = threadIdx.x; i < 256; i += kThreads) sm.num_tri[i] = s.tables[i];
-    for (int i = threadIdx.x; i < 256 * kMaxTriPerCell; i += kThreads) {
-        const uint8_t *e = s.tables + 256 + (i / kMaxTriPerCell) * 16 + 3 * (i % kMaxTriPerCell);
+    const uint8_t *tables = vol_of<kOne>(L, 0).s.tables;
+    for (int i = threadIdx.x; i < 256; i += 32 * kW) sm.num_tri[i] = tables[i];
+    for (int i = threadIdx.x; i < 256 * kMaxTriPerCell; i += 32 * kW) {
+        const uint8_t *e = tables + 256 + (i / kMaxTriPerCell) * 16 + 3 * (i % kMaxTriPerCell);
         sm.tri_row[i] = (uint32_t)e[0] | ((uint32_t)e[1] << 8) | ((uint32_t)e[2] << 16);
     }
     if (threadIdx.x < 12) {
@@ -343,32 +386,35 @@ __global__ void __launch_bounds__(kThreads) mc_emit_kernel(DevState s, Geom g) {
         sm.edge_info[e] = (uint32_t)lo | ((uint32_t)hi << 8) | ((uint32_t)dx << 16) | ((uint32_t)dy << 17) |
                           ((uint32_t)dz << 18) | ((uint32_t)a << 19);
     }
-    __syncthreads();
-    const bool failed = (c->status & (kStatusBudget | kStatusTimeout)) != 0;
-    const uint32_t n_cand = failed ? 0u : c->n_cand;
-    const float iso = c->params.iso;
-    const unsigned long long tri_cap = c->params.tri_cap;
-    float4 *__restrict__ out = reinterpret_cast<float4 *>(c->params.out);
-    const uint32_t nwt = (n_cand + kBPW - 1) / kBPW;
-    const uint32_t slab = g.nbx * g.nby;
-    (void)slab;
+    // all failure bits are final before this kernel starts
+    const uint32_t total = launch_prefix<kOne>(
+        L, [&](uint32_t v) {
+            const Ctl *c = vol_of<kOne>(L, v).s.ctl;
+            return (c->status & (kStatusBudget | kStatusAnyTimeout)) ? 0u : ceil_div(c->n_cand, kBPW);
+        },
+        pre);
+    __syncthreads();                                      // the tables
     LaneConst lc;
     lc.init(lane);
     WarpTile &wt = sm.w[warp];
     uint16_t *tm = sm.tmap[warp];
     float4 *stage = sm.stage[warp];
-    const uint32_t stride = gridDim.x * kWarps;
-    uint32_t t = blockIdx.x * kWarps + warp;
-    const uint32_t bq = (uint32_t)lane >> 3;
-    uint32_t b_next = t < nwt && t * kBPW + bq < n_cand ? s.icand[t * kBPW + bq] : 0u;
-    for (; t < nwt; t += stride) {
-        const uint32_t base = t * kBPW;
-        const int nb_w = (int)min((uint32_t)kBPW, n_cand - base);
-        const uint32_t b = b_next;
-        const uint32_t tn = t + stride;                   // next warp tile's block, loaded early
-        b_next = tn < nwt && tn * kBPW + bq < n_cand ? s.icand[tn * kBPW + bq] : 0u;
+    const uint32_t stride = gridDim.x * kW;
+    uint32_t t = blockIdx.x * kW + warp;
+    TileRef nxt = locate_tile<kOne>(L, pre, t, total);
+    for (; t < total; t += stride) {
+        const TileRef cur = nxt;
+        nxt = locate_tile<kOne>(L, pre, t + stride, total);   // next warp tile's block, loaded early
+        const DevState &s = vol_of<kOne>(L, cur.v).s;
+        const Geom &g = vol_of<kOne>(L, cur.v).g;
+        const Ctl *c = s.ctl;
+        const float iso = c->params.iso;
+        const unsigned long long tri_cap = c->params.tri_cap;
+        float4 *__restrict__ out = reinterpret_cast<float4 *>(c->params.out);
+        const uint32_t base = cur.base;
+        const int nb_w = (int)cur.nb_w;
         uint32_t n0p, n1p;
-        stage_and_classify<true, false>(s, g, iso, base, nb_w, b, wt, lc, sm.num_tri, n0p, n1p);
+        stage_and_classify<true, false>(s, g, iso, base, nb_w, cur.b, wt, lc, sm.num_tri, n0p, n1p);
         // per-cell offsets inside the warp tile: two packed scans (byte q = block q)
         uint32_t i0 = n0p, i1 = n1p;
 #pragma unroll
@@ -448,26 +494,115 @@ __global__ void __launch_bounds__(kThreads) mc_emit_kernel(DevState s, Geom g) {
 
 // ================================================================ launchers
 
-void launch_mc(const DevState &s, const Geom &g, bool debug, bool emit_only, const Grids &gr, cudaStream_t st) {
-    if (!emit_only) {
-        if (debug) mc_count_kernel<true><<<gr.mc_count, kThreads, 0, st>>>(s, g);
-        else mc_count_kernel<false><<<gr.mc_count, kThreads, 0, st>>>(s, g);
-        mc_scan_kernel<<<gr.mc_scan, kThreads, 0, st>>>(s);
-    }
-    if (debug) mc_emit_kernel<true><<<gr.mc_emit, kThreads, sizeof(EmitSmem), st>>>(s, g);
-    else mc_emit_kernel<false><<<gr.mc_emit, kThreads, sizeof(EmitSmem), st>>>(s, g);
+namespace {
+
+template <int kW, bool kOne>
+void count_w(const Launch &L, bool debug, int grid, cudaStream_t st) {
+    if (debug) mc_count_kernel<kW, true, kOne><<<grid, 32 * kW, sizeof(CountSmem<kW>), st>>>(L);
+    else mc_count_kernel<kW, false, kOne><<<grid, 32 * kW, sizeof(CountSmem<kW>), st>>>(L);
 }
 
-void mc_grids(int sm_count, Grids *gr) {
+template <int kW, bool kOne>
+void emit_w(const Launch &L, bool debug, int grid, cudaStream_t st) {
+    if (debug) mc_emit_kernel<kW, true, kOne><<<grid, 32 * kW, sizeof(EmitSmem<kW>), st>>>(L);
+    else mc_emit_kernel<kW, false, kOne><<<grid, 32 * kW, sizeof(EmitSmem<kW>), st>>>(L);
+}
+
+template <class K>
+void raise_smem(K kernel, size_t bytes) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <int kW>
+int emit_occupancy(bool single) {
+    raise_smem(mc_emit_kernel<kW, false, false>, sizeof(EmitSmem<kW>));
+    raise_smem(mc_emit_kernel<kW, true, false>, sizeof(EmitSmem<kW>));
+    raise_smem(mc_emit_kernel<kW, false, true>, sizeof(EmitSmem<kW>));
+    raise_smem(mc_emit_kernel<kW, true, true>, sizeof(EmitSmem<kW>));
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mc_count_kernel<false>, kThreads, 0);
-    gr->mc_count = std::max(1, occ) * sm_count;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mc_scan_kernel, kThreads, 0);
-    gr->mc_scan = std::max(1, occ) * sm_count;
-    cudaFuncSetAttribute(mc_emit_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(EmitSmem));
-    cudaFuncSetAttribute(mc_emit_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(EmitSmem));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mc_emit_kernel<false>, kThreads, sizeof(EmitSmem));
-    gr->mc_emit = std::max(1, occ) * sm_count;
+    if (single)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mc_emit_kernel<kW, false, true>, 32 * kW,
+                                                      sizeof(EmitSmem<kW>));
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mc_emit_kernel<kW, false, false>, 32 * kW,
+                                                      sizeof(EmitSmem<kW>));
+    return occ;
+}
+
+template <int kW>
+int count_occupancy(bool single) {
+    raise_smem(mc_count_kernel<kW, false, false>, sizeof(CountSmem<kW>));
+    raise_smem(mc_count_kernel<kW, true, false>, sizeof(CountSmem<kW>));
+    raise_smem(mc_count_kernel<kW, false, true>, sizeof(CountSmem<kW>));
+    raise_smem(mc_count_kernel<kW, true, true>, sizeof(CountSmem<kW>));
+    int occ = 0;
+    if (single)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mc_count_kernel<kW, false, true>, 32 * kW,
+                                                      sizeof(CountSmem<kW>));
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mc_count_kernel<kW, false, false>, 32 * kW,
+                                                      sizeof(CountSmem<kW>));
+    return occ;
+}
+
+template <bool kOne>
+void count_any(const Launch &L, bool debug, const Plan &pl, cudaStream_t st) {
+    if (pl.count_tile == 16) count_w<4, kOne>(L, debug, pl.mc_count, st);
+    else if (pl.count_tile == 64) count_w<16, kOne>(L, debug, pl.mc_count, st);
+    else count_w<8, kOne>(L, debug, pl.mc_count, st);
+}
+
+template <bool kOne>
+void scan_any(const Launch &L, const Plan &pl, cudaStream_t st) {
+    if (pl.scan_tile == 1024) mc_scan_kernel<4, kOne><<<pl.mc_scan, kThreads, 0, st>>>(L);
+    else if (pl.scan_tile == 4096) mc_scan_kernel<16, kOne><<<pl.mc_scan, kThreads, 0, st>>>(L);
+    else mc_scan_kernel<8, kOne><<<pl.mc_scan, kThreads, 0, st>>>(L);
+}
+
+template <bool kOne>
+void emit_any(const Launch &L, bool debug, const Plan &pl, cudaStream_t st) {
+    if (pl.emit_tile == 16) emit_w<4, kOne>(L, debug, pl.mc_emit, st);
+    else if (pl.emit_tile == 64) emit_w<16, kOne>(L, debug, pl.mc_emit, st);
+    else emit_w<8, kOne>(L, debug, pl.mc_emit, st);
+}
+
+}  // namespace
+
+// tile = candidates per CTA round = 4 per warp
+void launch_mc_count(const Launch &L, bool debug, const Plan &pl, cudaStream_t st) {
+    if (L.vols) count_any<false>(L, debug, pl, st);
+    else count_any<true>(L, debug, pl, st);
+}
+
+void launch_mc_scan(const Launch &L, const Plan &pl, cudaStream_t st) {
+    if (L.vols) scan_any<false>(L, pl, st);
+    else scan_any<true>(L, pl, st);
+}
+
+void launch_mc_emit(const Launch &L, bool debug, const Plan &pl, cudaStream_t st) {
+    if (L.vols) emit_any<false>(L, debug, pl, st);
+    else emit_any<true>(L, debug, pl, st);
+}
+
+template <int kPT>
+int scan_occupancy(bool single) {
+    int occ = 0;
+    if (single) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mc_scan_kernel<kPT, true>, kThreads, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mc_scan_kernel<kPT, false>, kThreads, 0);
+    return occ;
+}
+
+void mc_occupancy(Plan *pl, bool single) {
+    // every variant's shared-memory limit is raised, whichever is asked for
+    const int e4 = emit_occupancy<4>(single), e8 = emit_occupancy<8>(single), e16 = emit_occupancy<16>(single);
+    pl->mc_emit = std::max(1, pl->emit_tile == 16 ? e4 : (pl->emit_tile == 64 ? e16 : e8));
+    const int c4 = count_occupancy<4>(single), c8 = count_occupancy<8>(single),
+              c16 = count_occupancy<16>(single);
+    pl->mc_count = std::max(1, pl->count_tile == 16 ? c4 : (pl->count_tile == 64 ? c16 : c8));
+    const int occ = pl->scan_tile == 1024 ? scan_occupancy<4>(single)
+                                          : (pl->scan_tile == 4096 ? scan_occupancy<16>(single)
+                                                                   : scan_occupancy<8>(single));
+    pl->mc_scan = std::max(1, occ);
 }
 
 }  // namespace bcmc

@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(256) select_static_kernel(const float *__restr
             flat[2 * lane] = incl - (a + c);
             flat[2 * lane + 1] = incl - c;
             const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
-            const unsigned long long excl = bcmc::lookback_exclusive(scratch, tile, tot, status);
+            const unsigned long long excl = bcmc::lookback_exclusive(scratch, tile, tot, status, bcmc::kStatusTimeout);
             if (lane == 0) {
                 s_excl = excl;
                 if (tile == ntiles - 1) *count = (*status != 0) ? 0xFFFFFFFFu : (uint32_t)(excl + tot);

@@ -1,0 +1,101 @@
+// Host-side state of a loaded volume and the helpers the C ABI's entry
+// points share (api.cu: single volumes; batch.cu: batches).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "bcmc.h"
+#include "common.cuh"
+#include "kernels.cuh"
+
+struct iso_volume {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bcmc::Geom g{};
+    uint32_t flags = 0;
+    bcmc::DevState s{};
+    bcmc::Plan plan{};                // CTAs and tile sizes of the launches
+    uint32_t cap = 0;                 // physical slots
+    uint32_t n_cull_desc = 0, n_lru_desc = 0;
+    bcmc::Ctl *host_ctl = nullptr;    // pinned mirror for the one readback
+    bcmc::Params *host_params = nullptr;   // pinned: this extraction's isovalue, output and capacity
+    cudaStream_t capture_stream = nullptr;
+    cudaGraph_t graph = nullptr;      // one extraction: params copy, the stage kernels, count readback
+    cudaGraphExec_t gexec = nullptr;
+    bool use_graph = true;
+    // owned device allocations
+    uint64_t *bits = nullptr;
+    float *bmin = nullptr, *bmax = nullptr;
+    float2 *hull = nullptr, *hull8 = nullptr;
+    uint8_t *tables = nullptr;
+    unsigned long long dbg_edges_cap = 0;   // in vertices
+    bool profiling = false;
+    cudaEvent_t ev[ISO_NUM_STAGES + 1] = {};
+    float stage_ms[ISO_NUM_STAGES] = {};
+    unsigned long long last_tris = 0;
+    uint32_t last_n_active = 0, last_n_new = 0, last_n_cand = 0, last_slots = 0;
+};
+
+namespace bcmc_host {
+
+#define ISO_CK(call)                                                          \
+    do {                                                                      \
+        cudaError_t e_ = (call);                                              \
+        if (e_ != cudaSuccess) {                                              \
+            (void)cudaGetLastError();                                         \
+            return e_ == cudaErrorMemoryAllocation ? ISO_ERR_OOM : ISO_ERR_CUDA; \
+        }                                                                     \
+    } while (0)
+
+// Stream-ordered allocation from the library's pool of `dev`, ordered on `st`.
+int dalloc_bytes(void **p, size_t bytes, int dev, cudaStream_t st);
+void dfree_on(void *p, cudaStream_t st);
+
+template <typename T>
+int dalloc_on(T **p, size_t count, int dev, cudaStream_t st) {
+    return dalloc_bytes(reinterpret_cast<void **>(p), count * sizeof(T), dev, st);
+}
+
+struct DeviceGuard {              // make a device current for the call
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// Error of an extraction from its status bits.  After a timeout the
+// volume's cache bookkeeping may be inconsistent: it is emptied on the
+// volume's stream (and that stream synchronised).
+int status_to_error(iso_volume *v, uint32_t st);
+
+void fill_stats(const bcmc::Ctl &c, iso_stats *st, uint32_t reruns);
+
+// The plan of launches over volumes with `total_blocks` blocks and
+// `total_slots` cache slots together.  `want` (may be NULL) gives CTAs per
+// SM per kernel (0 = the kernel's occupancy limit; larger values are
+// clamped to it) and tile sizes (0 = default); the result holds CTAs per
+// launch (times the SM count, but no more than the launch can have work
+// items) and the tile sizes.
+bcmc::Plan launch_plan(const bcmc::Plan *want, int device, uint64_t total_blocks, uint64_t total_slots,
+                       uint32_t n_vols, bool single);
+
+// the tile fields of `want`, defaults where 0
+bcmc::Plan default_tiles(const bcmc::Plan *want);
+
+// largest CTAs per SM of each kernel for these tile sizes, in single-volume
+// or batch launches (cached per device)
+bcmc::Plan occupancy_limits_of(int device, const bcmc::Plan &tiles, bool single);
+
+// device address of the single-volume work counters (inside the control block)
+inline uint32_t *single_counters(const iso_volume *v) {
+    return reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(v->s.ctl) + offsetof(bcmc::Ctl, ctr));
+}
+
+}  // namespace bcmc_host
