@@ -61,6 +61,7 @@ extern "C" {
 #define ISO_ERR_CUDA 4         /* a CUDA runtime call failed */
 #define ISO_ERR_TIMEOUT 5      /* a device-side wait gave up (bounded spin) */
 #define ISO_ERR_CAPACITY 6     /* the caller's vertex buffer is too small */
+#define ISO_PENDING 7          /* a served request is not finished yet (not an error) */
 
 /* iso_options.flags */
 #define ISO_INPUT_ON_DEVICE 1u /* compressed/block_min/block_max are device pointers */
@@ -290,6 +291,64 @@ int iso_batch_tune(iso_batch *b, const float *isovalues, float *d_vertices, uint
 
 /* Free the batch (not its volumes).  NULL is a no-op. */
 void iso_batch_release(iso_batch *b);
+
+/* ---- serving: a request queue on one resident volume ----------------
+ * Isovalue requests are queued with iso_server_submit and answered in
+ * ticks by iso_server_step.  A tick takes up to max_batch queued requests
+ * (first come, first served) and runs them together: one pass over the
+ * block ranges finds the union of their active blocks (Section 4.1) and
+ * each request's own candidates; one cache update and decode serves the
+ * union (Section 4.2, Algorithm 1); then counting, offsets and emission
+ * (Sections 4.3-4.5) run for all of the tick's requests in one launch
+ * each.  Decoded blocks and all metadata stay resident between ticks;
+ * every slot a request of the running tick reads is part of the union the
+ * tick's cache update protects, so no in-flight request loses a block.
+ * Admission: when the union's active blocks do not fit in the volume's
+ * cache budget, the tick's requests return to the queue and later ticks
+ * take half as many (down to one; a single request that does not fit
+ * finishes with ISO_ERR_BUDGET).  Meshes are allocated when the tick knows
+ * their sizes; a request whose mesh would take the bytes of finished,
+ * not yet taken meshes past vertex_budget_bytes waits for a later tick
+ * (with every request behind it), unless nothing else is held.  Every
+ * served mesh is identical, byte for byte, to iso_extract of the same
+ * isovalue on the same data.  The server uses the volume's device state:
+ * do not extract from the volume on another stream while a server call
+ * runs, and destroy the server before the volume. */
+typedef struct iso_server iso_server;
+
+typedef struct iso_server_options {
+    uint32_t max_batch;            /* requests per tick, 1..8; 0 = 4 */
+    uint32_t reserved;
+    uint64_t vertex_budget_bytes;  /* limit on held mesh bytes (48 per triangle); 0 = none */
+    void *stream;                  /* cudaStream_t of the server's device work; NULL = default */
+} iso_server_options;
+
+/* v must not be loaded with ISO_DEBUG.  Per request position of a tick the
+ * server keeps candidate, count and offset arrays of min(cache slots, nb)
+ * entries (16 bytes each). */
+int iso_server_create(iso_server **out, iso_volume *v, const iso_server_options *opt);
+
+/* Queue a request (host only, no device work); *ticket identifies it. */
+int iso_server_submit(iso_server *s, float isovalue, uint64_t *ticket);
+
+/* Run one tick (nothing if the queue is empty); blocks until it is done.
+ * *completed (may be NULL) receives the number of requests it finished. */
+int iso_server_step(iso_server *s, uint32_t *completed);
+
+/* Requests waiting in the queue. */
+int iso_server_queued(const iso_server *s, uint32_t *queued);
+
+/* Hand a finished request's mesh to the caller (release it with
+ * iso_mesh_release on the server's volume).  Returns ISO_PENDING if the
+ * request is still queued, the request's own status if it finished
+ * (ISO_OK, ISO_ERR_BUDGET, ISO_ERR_TIMEOUT, ISO_ERR_OOM; no mesh unless
+ * ISO_OK), ISO_ERR_INVALID_ARG for an unknown or already taken ticket.
+ * stats: n_active, n_new, n_slots, cache_bytes and epoch describe the
+ * tick's union; num_triangles, n_occupied, n_candidates the request. */
+int iso_server_take(iso_server *s, uint64_t ticket, iso_mesh *out);
+
+/* Free the server, its queue and any finished meshes not taken. */
+void iso_server_destroy(iso_server *s);
 
 /* ---- debug and parity access (volumes loaded with ISO_DEBUG) ---------
  * Copies a per-stage array of the LAST extraction into host memory.

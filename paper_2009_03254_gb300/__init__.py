@@ -23,6 +23,7 @@ ISO_ERR_BUDGET = 3
 ISO_ERR_CUDA = 4
 ISO_ERR_TIMEOUT = 5
 ISO_ERR_CAPACITY = 6
+ISO_PENDING = 7
 
 ISO_INPUT_ON_DEVICE = 1
 ISO_DEBUG = 2
@@ -66,6 +67,11 @@ class _Shape(ctypes.Structure):
         return {name: int(getattr(self, name)) for name, _ in self._fields_}
 
 
+class _ServerOptions(ctypes.Structure):
+    _fields_ = [("max_batch", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("vertex_budget_bytes", ctypes.c_uint64), ("stream", ctypes.c_void_p)]
+
+
 class _Mesh(ctypes.Structure):
     _fields_ = [("d_vertices", ctypes.c_void_p), ("num_triangles", ctypes.c_uint64),
                 ("capacity_triangles", ctypes.c_uint64), ("stats", _Stats), ("priv", ctypes.c_void_p)]
@@ -106,6 +112,12 @@ def lib():
             "iso_batch_get_shape": (i32, [P, ctypes.POINTER(_Shape)]),
             "iso_batch_tune": (i32, [P, P, P, u64, i32, ctypes.POINTER(_Shape), P]),
             "iso_batch_release": (None, [P]),
+            "iso_server_create": (i32, [ctypes.POINTER(P), P, ctypes.POINTER(_ServerOptions)]),
+            "iso_server_submit": (i32, [P, ctypes.c_float, ctypes.POINTER(u64)]),
+            "iso_server_step": (i32, [P, ctypes.POINTER(u32)]),
+            "iso_server_queued": (i32, [P, ctypes.POINTER(u32)]),
+            "iso_server_take": (i32, [P, u64, ctypes.POINTER(_Mesh)]),
+            "iso_server_destroy": (None, [P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -379,16 +391,79 @@ class Batch:
             pass
 
 
-def encode_field(field, rate, stream=None):
+class Server:
+    """Isovalue requests on one resident volume, answered in ticks: each
+    tick runs up to `max_batch` queued requests together (one cull pass for
+    all, one cache update for their union, one launch per triangle stage).
+    See iso_server_* in include/bcmc.h.  The volume must outlive the server."""
+
+    def __init__(self, volume, *, max_batch=4, vertex_budget_bytes=0, stream=None):
+        self._h = None
+        self.volume = volume
+        opt = _ServerOptions()
+        opt.max_batch = int(max_batch)
+        opt.vertex_budget_bytes = int(vertex_budget_bytes)
+        opt.stream = stream if stream is not None else _current_stream()
+        h = ctypes.c_void_p()
+        _check(lib().iso_server_create(ctypes.byref(h), volume._h, ctypes.byref(opt)), "iso_server_create")
+        self._h = h
+
+    def submit(self, iso):
+        t = ctypes.c_uint64()
+        _check(lib().iso_server_submit(self._h, ctypes.c_float(iso), ctypes.byref(t)), "iso_server_submit")
+        return int(t.value)
+
+    def step(self):
+        """Run one tick; returns the number of requests it finished."""
+        n = ctypes.c_uint32()
+        _check(lib().iso_server_step(self._h, ctypes.byref(n)), "iso_server_step")
+        return int(n.value)
+
+    def queued(self):
+        n = ctypes.c_uint32()
+        _check(lib().iso_server_queued(self._h, ctypes.byref(n)), "iso_server_queued")
+        return int(n.value)
+
+    def take(self, ticket):
+        """(status, Mesh or None): ISO_PENDING while queued; the mesh belongs
+        to the caller (release it) when status is ISO_OK."""
+        m = _Mesh()
+        rc = lib().iso_server_take(self._h, int(ticket), ctypes.byref(m))
+        if rc == ISO_ERR_INVALID_ARG:
+            raise IsoError(rc, "iso_server_take")
+        if rc != ISO_OK:
+            return rc, None
+        return rc, Mesh(self.volume, m)
+
+    def release(self):
+        if self._h:
+            lib().iso_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
+
+
+def encode_field(field, rate, stream=None, out=None):
     """Encode a CUDA float32 tensor of shape (nz, ny, nx) on the GPU.
-    Returns (bits uint64-as-int64 tensor (nb, rate), bmin, bmax) on the same device."""
+    Returns (bits uint64-as-int64 tensor (nb, rate), bmin, bmax) on the same
+    device, written into `out` = (bits, bmin, bmax) when given (contiguous,
+    of those shapes)."""
     import torch
     assert field.is_cuda and field.dtype == torch.float32 and field.is_contiguous()
     nz, ny, nx = field.shape
     nb = int(np.prod(block_dims((nx, ny, nz))))
-    bits = torch.empty((nb, rate), dtype=torch.int64, device=field.device)
-    bmin = torch.empty(nb, dtype=torch.float32, device=field.device)
-    bmax = torch.empty(nb, dtype=torch.float32, device=field.device)
+    if out is not None:
+        bits, bmin, bmax = out
+        assert bits.shape == (nb, rate) and bmin.numel() == nb and bmax.numel() == nb
+        assert bits.is_contiguous() and bmin.is_contiguous() and bmax.is_contiguous()
+    else:
+        bits = torch.empty((nb, rate), dtype=torch.int64, device=field.device)
+        bmin = torch.empty(nb, dtype=torch.float32, device=field.device)
+        bmax = torch.empty(nb, dtype=torch.float32, device=field.device)
     _check(lib().iso_encode_field(_ptr(field), nx, ny, nz, rate, _ptr(bits), _ptr(bmin), _ptr(bmax),
                                   stream if stream is not None else _current_stream()), "iso_encode_field")
     return bits, bmin, bmax

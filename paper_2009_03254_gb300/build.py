@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libbcmc.so")
-SOURCES = ["api.cu", "batch.cu", "extract.cu", "mc.cu", "codec.cu", "mc_tables.cu", "static_scratch.cu"]
+SOURCES = ["api.cu", "batch.cu", "serve.cu", "extract.cu", "mc.cu", "codec.cu", "mc_tables.cu", "static_scratch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", CSRC, "-I", os.path.join(ROOT, "include")]

@@ -319,6 +319,7 @@ const char *iso_error_string(int status) {
         case ISO_ERR_CUDA: return "CUDA runtime error";
         case ISO_ERR_TIMEOUT: return "device-side wait timed out";
         case ISO_ERR_CAPACITY: return "output buffer too small";
+        case ISO_PENDING: return "request not finished yet";
         default: return "unknown status";
     }
 }
@@ -371,9 +372,12 @@ int iso_load_volume(iso_volume **out, const void *compressed, size_t compressed_
     v->n_cull_desc = (g.nb + kMinCullTile - 1) / kMinCullTile;
     v->n_lru_desc = (v->cap + kScanTile - 1) / kScanTile;
     const uint32_t n_mc_desc = (v->cap + kMinMcScanTile - 1) / kMinMcScanTile;   // candidates <= cap
+    const bool on_device = (o.flags & ISO_INPUT_ON_DEVICE) != 0;
     TRY(dalloc(v, &v->bits, words));
-    TRY(dalloc(v, &v->bmin, g.nb));
-    TRY(dalloc(v, &v->bmax, g.nb));
+    if (!on_device) {                 // staging for host ranges (freed once the hulls exist)
+        TRY(dalloc(v, &v->bmin, g.nb));
+        TRY(dalloc(v, &v->bmax, g.nb));
+    }
     TRY(dalloc(v, &v->hull, g.nb));
     TRY(dalloc(v, &v->hull8, g.nb));
     TRY(dalloc(v, &v->tables, 256 + 256 * 16));
@@ -424,8 +428,10 @@ int iso_load_volume(iso_volume **out, const void *compressed, size_t compressed_
             return e_ == cudaErrorMemoryAllocation ? ISO_ERR_OOM : ISO_ERR_CUDA; } \
     } while (0)
     TRYC(cudaMemcpyAsync(v->bits, compressed, words * 8, kind, st));
-    TRYC(cudaMemcpyAsync(v->bmin, block_min, (size_t)g.nb * 4, kind, st));
-    TRYC(cudaMemcpyAsync(v->bmax, block_max, (size_t)g.nb * 4, kind, st));
+    if (!on_device) {
+        TRYC(cudaMemcpyAsync(v->bmin, block_min, (size_t)g.nb * 4, kind, st));
+        TRYC(cudaMemcpyAsync(v->bmax, block_max, (size_t)g.nb * 4, kind, st));
+    }
     TRYC(cudaMemcpyAsync(v->tables, table_bytes, sizeof(table_bytes), cudaMemcpyHostToDevice, st));
     TRYC(cudaMemsetAsync(s.islot, 0xFF, (size_t)g.nb * 4, st));
     TRYC(cudaMemsetAsync(s.sblock, 0xFF, (size_t)v->cap * 4, st));
@@ -445,8 +451,12 @@ int iso_load_volume(iso_volume **out, const void *compressed, size_t compressed_
     c0.cap = v->cap;
     *v->host_ctl = c0;
     TRYC(cudaMemcpyAsync(s.ctl, v->host_ctl, sizeof(Ctl), cudaMemcpyHostToDevice, st));
-    launch_hull(v->bmin, v->bmax, v->hull, v->hull8, g, st);
+    // the ranges are needed only for the hulls (device inputs are read in place)
+    launch_hull(on_device ? block_min : v->bmin, on_device ? block_max : v->bmax, v->hull, v->hull8, g, st);
     TRYC(cudaGetLastError());
+    dfree_on(v->bmin, st);
+    dfree_on(v->bmax, st);
+    v->bmin = v->bmax = nullptr;
     TRYC(cudaStreamSynchronize(st));
     v->plan = launch_plan(nullptr, v->device, g.nb, v->cap, 1, true);
     TRYC(cudaGetLastError());

@@ -23,6 +23,7 @@
 #include "common.cuh"
 #include "kernels.cuh"
 #include "launch.cuh"
+#include "tile_scan.cuh"
 
 namespace bcmc {
 
@@ -58,60 +59,6 @@ __global__ void __launch_bounds__(kThreads) prep_kernel(Launch L) {
         c->n_tri = 0;
     }
     if (tid < kNumLaunchCounters) L.ctr[tid] = 0;
-}
-
-// ================================================================ tile scan helpers
-//
-// A tile is kR * 256 entries handled by 256 threads in kR rounds; entry
-// tile*kR*256 + r*256 + threadIdx.x belongs to round r.  Per (round, warp) the warp's ballot gives its 32 flags; a
-// warp scan over the kRounds*8 (round, warp) counts gives each group's
-// offset inside the tile.  Large tiles keep the tiles of a pass within
-// one wave of resident blocks, so the look-back walk stays short.
-
-constexpr int kRounds = kScanTile / kThreads;   // rounds of a cache-update tile
-
-template <int kR>
-struct TileScan {
-    uint32_t cnt[kR][8];              // per (round, warp): packed counts, then exclusive offsets
-    unsigned long long excl;          // tile's exclusive prefix (look-back)
-};
-
-// warp 0: turn ts.cnt into exclusive offsets (packed 16-bit fields add
-// without carries: a tile holds at most 4096 entries) and return the
-// tile's packed total in every lane
-template <int kR>
-__device__ __forceinline__ uint32_t scan_tile_counts(TileScan<kR> &ts) {
-    constexpr int kPer = kR * 8 / 32;
-    const int lane = threadIdx.x & 31;
-    uint32_t *flat = &ts.cnt[0][0] + kPer * lane;
-    uint32_t v[kPer], sum = 0;
-#pragma unroll
-    for (int k = 0; k < kPer; k++) {
-        v[k] = flat[k];
-        sum += v[k];
-    }
-    uint32_t incl = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-    }
-    uint32_t run = incl - sum;
-#pragma unroll
-    for (int k = 0; k < kPer; k++) {
-        flat[k] = run;
-        run += v[k];
-    }
-    return __shfl_sync(0xffffffffu, incl, 31);
-}
-
-// block-wide: take the next work item from a launch counter
-__device__ __forceinline__ uint32_t next_item(uint32_t *ctr, uint32_t *slot) {
-    if (threadIdx.x == 0) *slot = atomicAdd(ctr, 1u);
-    __syncthreads();
-    const uint32_t x = *slot;
-    __syncthreads();                  // all have read it before thread 0 may overwrite it
-    return x;
 }
 
 // ================================================================ cull (Section 4.1)
@@ -564,13 +511,9 @@ __global__ void gather_slots_kernel(const float *__restrict__ slots, const int32
 
 constexpr size_t decode_smem(int threads) { return 32u * 8u * (size_t)threads; }
 
+// Algorithm 1 after the cull (both list kernels), then the decode
 template <bool kOne>
-void front(const Launch &L, const Plan &pl, cudaStream_t st, cudaEvent_t *ev) {
-    prep_kernel<kOne><<<pl.prep, kThreads, 0, st>>>(L);
-    if (ev) cudaEventRecord(ev[1], st);
-    if (pl.cull_tile == 2048) cull_kernel<8, kOne><<<pl.cull, kThreads, 0, st>>>(L);
-    else cull_kernel<16, kOne><<<pl.cull, kThreads, 0, st>>>(L);
-    if (ev) cudaEventRecord(ev[2], st);
+void cache_update(const Launch &L, const Plan &pl, cudaStream_t st, cudaEvent_t *ev) {
     lru_a_kernel<kOne><<<pl.lru_a, kThreads, 0, st>>>(L);
     lru_b_kernel<kOne><<<pl.lru_b, kThreads, 0, st>>>(L);
     if (ev) cudaEventRecord(ev[3], st);
@@ -580,9 +523,24 @@ void front(const Launch &L, const Plan &pl, cudaStream_t st, cudaEvent_t *ev) {
     if (ev) cudaEventRecord(ev[4], st);
 }
 
+template <bool kOne>
+void front(const Launch &L, const Plan &pl, cudaStream_t st, cudaEvent_t *ev) {
+    prep_kernel<kOne><<<pl.prep, kThreads, 0, st>>>(L);
+    if (ev) cudaEventRecord(ev[1], st);
+    if (pl.cull_tile == 2048) cull_kernel<8, kOne><<<pl.cull, kThreads, 0, st>>>(L);
+    else cull_kernel<16, kOne><<<pl.cull, kThreads, 0, st>>>(L);
+    if (ev) cudaEventRecord(ev[2], st);
+    cache_update<kOne>(L, pl, st, ev);
+}
+
 void launch_front(const Launch &L, const Plan &pl, cudaStream_t st, cudaEvent_t *ev) {
     if (L.vols) front<false>(L, pl, st, ev);
     else front<true>(L, pl, st, ev);
+}
+
+void launch_cache_update(const Launch &L, const Plan &pl, cudaStream_t st) {
+    if (L.vols) cache_update<false>(L, pl, st, nullptr);
+    else cache_update<true>(L, pl, st, nullptr);
 }
 
 void launch_batch_params(const Launch &L, const float *d_iso, cudaStream_t st) {

@@ -81,6 +81,8 @@ constexpr int kDefaultCullTile = 4096, kDefaultDecodeTile = 128, kDefaultCountTi
 // With `ev`, events ev[1..4] are recorded after prep, cull, cache update
 // and decode.
 void launch_front(const Launch &L, const Plan &pl, cudaStream_t st, cudaEvent_t *ev);
+// the cache update and decode alone (after a cull that set n_active/n_new)
+void launch_cache_update(const Launch &L, const Plan &pl, cudaStream_t st);
 // triangle stage: count, scan, emit.  A batch places the volumes' outputs
 // between scan and emit; a rerun into a larger output runs emit alone.
 void launch_mc_count(const Launch &L, bool debug, const Plan &pl, cudaStream_t st);

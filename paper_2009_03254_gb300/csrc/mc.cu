@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(32 * kW) mc_emit_kernel(Launch L) {
     const uint32_t total = launch_prefix<kOne>(
         L, [&](uint32_t v) {
             const Ctl *c = vol_of<kOne>(L, v).s.ctl;
-            return (c->status & (kStatusBudget | kStatusAnyTimeout)) ? 0u : ceil_div(c->n_cand, kBPW);
+            return (c->status & (kStatusBudget | kStatusAnyTimeout | kStatusSkip)) ? 0u : ceil_div(c->n_cand, kBPW);
         },
         pre);
     __syncthreads();                                      // the tables

@@ -27,7 +27,7 @@ struct iso_volume {
     bool use_graph = true;
     // owned device allocations
     uint64_t *bits = nullptr;
-    float *bmin = nullptr, *bmax = nullptr;
+    float *bmin = nullptr, *bmax = nullptr;   // staging of host block ranges during the load only
     float2 *hull = nullptr, *hull8 = nullptr;
     uint8_t *tables = nullptr;
     unsigned long long dbg_edges_cap = 0;   // in vertices

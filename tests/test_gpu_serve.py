@@ -1,0 +1,201 @@
+"""GPU parity of the serving path: requests answered in ticks on one
+resident volume must give meshes identical, byte for byte, to extracting
+each isovalue alone; admission splits ticks whose union of active blocks
+exceeds the cache budget, defers meshes past the vertex budget, and a
+single request over budget fails alone."""
+import numpy as np
+import pytest
+
+import oracle
+from synth import fields
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def pkg():
+    import paper_2009_03254_gb300 as p
+    return p
+
+
+def volume_pair(dims=(48, 40, 36), rate=8, seed=3, **kw):
+    f = fields.gradient_noise(*dims, seed, octaves=4, base_period=16)
+    bits, bmin, bmax = oracle.encode_volume(f, rate)
+    d = oracle.decode_volume(bits, dims, rate)
+    p = pkg()
+    return (bits, dims, rate, bmin, bmax, d), p.Volume(bits, dims, rate, bmin, bmax, **kw), \
+        p.Volume(bits, dims, rate, bmin, bmax)
+
+
+def same_mesh(m, ref):
+    assert m.num_triangles == ref.num_triangles
+    if m.num_triangles:
+        assert np.array_equal(m.vertices.cpu().numpy().view(np.uint32), ref.vertices.cpu().numpy().view(np.uint32))
+
+
+def drain(srv):
+    while srv.queued():
+        srv.step()
+
+
+def test_served_meshes_equal_alone():
+    p = pkg()
+    data, vol, alone = volume_pair()
+    d = data[5]
+    rng = np.random.default_rng(4)
+    isos = list(rng.uniform(*np.quantile(d, [0.1, 0.9]), 9).astype(np.float32))
+    isos += [isos[2], float(d.max()) + 1.0, float(d.min()) - 1.0]     # a repeat, two empty surfaces
+    srv = p.Server(vol, max_batch=4)
+    try:
+        tickets = [srv.submit(float(x)) for x in isos]
+        ticks = 0
+        while srv.queued():
+            srv.step()
+            ticks += 1
+        assert ticks == 3
+        for t, x in zip(tickets, isos):
+            status, m = srv.take(t)
+            assert status == p.ISO_OK
+            ref = alone.extract(float(x))
+            same_mesh(m, ref)
+            assert m.stats["n_candidates"] == ref.stats["n_candidates"]
+            assert m.stats["n_occupied"] == ref.stats["n_occupied"]
+            m.release()
+            ref.release()
+            with pytest.raises(p.IsoError):
+                srv.take(t)                                   # already taken
+    finally:
+        srv.release()
+        vol.release()
+        alone.release()
+
+
+def test_union_over_budget_splits_the_tick():
+    p = pkg()
+    dims, rate = (48, 40, 36), 8
+    f = fields.gradient_noise(*dims, 7, octaves=4, base_period=16)
+    bits, bmin, bmax = oracle.encode_volume(f, rate)
+    d = oracle.decode_volume(bits, dims, rate)
+    nbd = oracle.block_dims(dims)
+    lo, hi = np.quantile(d, [0.25, 0.75])
+    a1 = oracle.active_blocks(bmin, bmax, nbd, float(lo))
+    a2 = oracle.active_blocks(bmin, bmax, nbd, float(hi))
+    budget = int(max(a1.sum(), a2.sum()))
+    assert (a1 | a2).sum() > budget                           # together they do not fit
+    vol = p.Volume(bits, dims, rate, bmin, bmax, cache_budget_bytes=256 * budget, initial_cache_fraction=1.0)
+    alone = p.Volume(bits, dims, rate, bmin, bmax)
+    srv = p.Server(vol, max_batch=2)
+    try:
+        t1, t2 = srv.submit(float(lo)), srv.submit(float(hi))
+        assert srv.step() == 0 and srv.queued() == 2          # the union was refused: both wait
+        drain(srv)
+        for t, x in ((t1, lo), (t2, hi)):
+            status, m = srv.take(t)
+            assert status == p.ISO_OK
+            ref = alone.extract(float(x))
+            same_mesh(m, ref)
+            m.release()
+            ref.release()
+        # one request that alone exceeds the budget fails by itself
+        small = p.Volume(bits, dims, rate, bmin, bmax, cache_budget_bytes=256 * 10)
+        s2 = p.Server(small, max_batch=2)
+        t = s2.submit(float(np.median(d)))
+        s2.step()
+        status, m = s2.take(t)
+        assert status == p.ISO_ERR_BUDGET and m is None
+        s2.release()
+        small.release()
+    finally:
+        srv.release()
+        vol.release()
+        alone.release()
+
+
+def test_vertex_budget_defers_until_meshes_are_taken():
+    p = pkg()
+    data, vol, alone = volume_pair(seed=5)
+    d = data[5]
+    isos = [float(x) for x in np.quantile(d, [0.3, 0.5, 0.7])]
+    ref = [alone.extract(x) for x in isos]
+    budget = 48 * max(r.num_triangles for r in ref) + 48      # room for about one mesh
+    srv = p.Server(vol, max_batch=4, vertex_budget_bytes=budget)
+    try:
+        tickets = [srv.submit(x) for x in isos]
+        assert srv.step() == 1                                # the first fits (nothing held)
+        assert srv.queued() == 2
+        assert srv.step() == 0                                # the held mesh blocks the rest
+        st0, m0 = srv.take(tickets[0])
+        assert st0 == p.ISO_OK
+        same_mesh(m0, ref[0])
+        m0.release()
+        for i in (1, 2):
+            assert srv.take(tickets[i])[0] == p.ISO_PENDING
+            assert srv.step() == 1
+            st, m = srv.take(tickets[i])
+            assert st == p.ISO_OK
+            same_mesh(m, ref[i])
+            m.release()
+    finally:
+        for r in ref:
+            r.release()
+        srv.release()
+        vol.release()
+        alone.release()
+
+
+def test_server_invalid_arguments():
+    p = pkg()
+    data, vol, alone = volume_pair(dims=(20, 20, 20))
+    bits, dims, rate, bmin, bmax, _ = data
+    dbg = p.Volume(bits, dims, rate, bmin, bmax, debug=True)
+    try:
+        for kw, v in ((dict(), dbg), (dict(max_batch=9), vol)):
+            with pytest.raises(p.IsoError) as e:
+                p.Server(v, **kw)
+            assert e.value.code == p.ISO_ERR_INVALID_ARG
+        srv = p.Server(vol)
+        with pytest.raises(p.IsoError):
+            srv.submit(float("nan"))
+        with pytest.raises(p.IsoError):
+            srv.take(12345)
+        t = srv.submit(0.0)
+        assert srv.take(t) == (p.ISO_PENDING, None)
+        srv.step()
+        st, m = srv.take(t)
+        assert st == p.ISO_OK
+        m.release()
+        srv.release()
+    finally:
+        dbg.release()
+        vol.release()
+        alone.release()
+
+
+def test_request_loop_against_plain_path():
+    from paper_2009_03254_gb300 import serving
+    p = pkg()
+    data, vol, alone = volume_pair(dims=(64, 64, 48), seed=9)
+    d = data[5]
+    lo, hi = np.quantile(d, [0.05, 0.95])
+    n = 60
+    isos = serving.random_walk_isovalues(n, float(lo), float(hi), 5)
+    arrivals = serving.poisson_arrivals(n, 2000.0, 1)
+    srv = p.Server(vol, max_batch=8)
+    try:
+        res = serving.RequestLoop(srv, keep_meshes=True).run(arrivals, isos)
+        plain = serving.RequestLoop(serving.PlainBackend(alone), keep_meshes=True).run(arrivals, isos)
+        for a, b in zip(res, plain):
+            assert a["status"] == b["status"] == p.ISO_OK
+            same_mesh(a["mesh"], b["mesh"])
+            a["mesh"].release()
+            b["mesh"].release()
+        assert serving.latency_summary(res)["served"] == n
+    finally:
+        srv.release()
+        vol.release()
+        alone.release()
