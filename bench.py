@@ -71,6 +71,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-volume batch comparison")
+    ap.add_argument("--workload", default="noise512", choices=["noise512", "serve"],
+                    help="serve: the request loop on the 10240x7680x1536 channel volume")
+    ap.add_argument("--serve-scale", type=float, default=1.0,
+                    help="fraction of the serving volume's x and y extent (1 = full size)")
+    ap.add_argument("--requests", type=int, default=1000)
     ap.add_argument("--dims", type=int, default=512,
                     help="cube edge of the noise volume (default 512; smaller sizes are for profiling captures)")
     return ap.parse_args()
@@ -500,6 +505,130 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- serving
+
+SERVE_BUDGET_BYTES = 64e9          # decoded-block cache budget of the serving volume
+SERVE_VERTEX_BUDGET = 48e9         # finished meshes held by the server at once
+
+
+def run_serve(args):
+    """Request loop on the serving volume: Poisson arrivals (rate 0.8 / the
+    plain path's median service time), isovalues a reflecting random walk
+    over the [p5, p95] decoded percentiles (step 0.02 of the range), served
+    by the batched server and, on the same schedule, by the plain
+    per-request path; then sweeps up and down the same range."""
+    import dataclasses
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2009_03254_gb300 as bc
+    from paper_2009_03254_gb300 import serving
+    import synth.gpu as sg
+    from synth import recipes, volumes
+    sg.build()
+    rec = recipes.SERVE_DNS
+    if args.serve_scale != 1.0:
+        nx, ny, nz = rec.dims
+        sx = max(4, int(round(nx * args.serve_scale / 4)) * 4)
+        sy = max(4, int(round(ny * args.serve_scale / 4)) * 4)
+        rec = dataclasses.replace(rec, dims=(sx, sy, nz))
+    scale_area = rec.dims[0] * rec.dims[1] / float(recipes.SERVE_DNS.dims[0] * recipes.SERVE_DNS.dims[1])
+    t0 = time.time()
+    bits, bmin, bmax = volumes.encode_recipe(rec)
+    t_gen = time.time() - t0
+    p5, p50, p95 = (volumes.percentile_isovalue(bits, rec.dims, rec.rate, q, seed=3) for q in (0.05, 0.5, 0.95))
+    budget = int(SERVE_BUDGET_BYTES * scale_area)
+    stream = torch.cuda.current_stream()
+    vol = bc.Volume(bits, rec.dims, rec.rate, bmin, bmax, cache_budget_bytes=budget, initial_cache_fraction=0.01)
+    compressed = bits.numel() * 8
+    del bits, bmin, bmax
+    torch.cuda.empty_cache()
+    # plain service time at the median isovalue (warm), for the arrival rate
+    svc = []
+    for _ in range(4):
+        t1 = time.perf_counter()
+        m = vol.extract(p50)
+        svc.append(time.perf_counter() - t1)
+        t_med = m.num_triangles
+        m.release()
+    median_svc = float(np.median(svc[1:]))
+    rate = 0.8 / median_svc
+    n = args.requests
+    isos = serving.random_walk_isovalues(n, p5, p95, 5)
+    arrivals = serving.poisson_arrivals(n, rate, 1)
+
+    def drive(backend, arr, iso_list):
+        torch.cuda.synchronize()
+        tw = time.perf_counter()
+        res = serving.RequestLoop(backend).run(arr, iso_list)
+        wall = time.perf_counter() - tw
+        tris = sum(r["triangles"] for r in res)
+        out = serving.latency_summary(res)
+        out.update({"triangles_per_s": tris / wall, "wall_s": wall, "triangles": tris,
+                    "failed": sum(1 for r in res if r["status"] not in (serving.ISO_OK, serving.REJECTED))})
+        return out
+
+    # one request alone, warm cache: the plain call against a one-request tick;
+    # then a four-request tick step by step (its first step runs the front)
+    probe = bc.Server(vol, max_batch=4, vertex_budget_bytes=int(SERVE_VERTEX_BUDGET))
+
+    def served_steps(iso_list):
+        tickets = [probe.submit(float(x)) for x in iso_list]
+        times = []
+        for _ in iso_list:
+            t1 = time.perf_counter()
+            probe.step()
+            times.append(1e3 * (time.perf_counter() - t1))
+        for t in tickets:
+            st, m = probe.take(t)
+            if m is not None:
+                m.release()
+        return times
+
+    single = {"plain_ms": [], "served_ms": []}
+    for _ in range(3):
+        t1 = time.perf_counter()
+        m = vol.extract(p50)
+        single["plain_ms"].append(1e3 * (time.perf_counter() - t1))
+        m.release()
+        single["served_ms"] += served_steps([p50])
+    tick4 = served_steps([p50, p50 * 0.98, p50 * 1.02, p50 * 0.96])
+    probe.release()
+    vol.cache_reset()
+    plain = drive(serving.PlainBackend(vol), arrivals, isos)
+    vol.cache_reset()
+    srv = bc.Server(vol, max_batch=4, vertex_budget_bytes=int(SERVE_VERTEX_BUDGET))
+    served = drive(srv, arrivals, isos)
+    sweeps = {}
+    for name, seq in (("sweep_up", np.linspace(p5, p95, 100)), ("sweep_down", np.linspace(p95, p5, 100))):
+        seq = seq.astype(np.float32)
+        burst = np.zeros(len(seq))                   # all queued at once: throughput of each path
+        vol.cache_reset()
+        sp = drive(serving.PlainBackend(vol), burst, seq)
+        vol.cache_reset()
+        ss = drive(srv, burst, seq)
+        sweeps[name] = {"plain_triangles_per_s": sp["triangles_per_s"], "served_triangles_per_s": ss["triangles_per_s"],
+                        "plain_wall_s": sp["wall_s"], "served_wall_s": ss["wall_s"]}
+    srv.release()
+    vol.release()
+    line = {
+        "metric": "p50/p99 isovalue-change latency under Poisson requests, served vs plain path",
+        "value": served.get("p50_ms"), "unit": "ms", "higher_is_better": False, "n_gpus": 1,
+        "steps": n, "warmup": 1, "dtype": "f32", "data": "synthetic", "scaling": "weak", "vs_baseline": None,
+        "config": {"workload": f"serve_dns: {rec.dims[0]}x{rec.dims[1]}x{rec.dims[2]} channel-flow field "
+                               f"(seed {rec.seed}, {rec.octaves} octaves, coarsest period {rec.base_period}), "
+                               f"{rec.rate} bits/value, cache budget {budget / 1e9:.1f} GB",
+                   "requests": n, "arrival_rate_per_s": rate, "plain_median_service_ms": 1e3 * median_svc,
+                   "isovalue_range": [p5, p95], "median_isovalue": p50, "triangles_at_median": t_med,
+                   "compressed_bytes": compressed, "generate_encode_s": t_gen,
+                   "server": {"max_batch": 4, "vertex_budget_bytes": SERVE_VERTEX_BUDGET}},
+        "served": served, "plain": plain, "sweeps": sweeps,
+        "single_request_warm": single, "tick_of_4_step_ms": tick4,
+        "p99_ms": served.get("p99_ms"),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     global DIMS, WORKLOAD
     args = parse()
@@ -508,6 +637,8 @@ def main():
         WORKLOAD = WORKLOAD.replace("noise512: 512^3", f"noise{args.dims}: {args.dims}^3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

@@ -293,27 +293,28 @@ int iso_batch_tune(iso_batch *b, const float *isovalues, float *d_vertices, uint
 void iso_batch_release(iso_batch *b);
 
 /* ---- serving: a request queue on one resident volume ----------------
- * Isovalue requests are queued with iso_server_submit and answered in
- * ticks by iso_server_step.  A tick takes up to max_batch queued requests
- * (first come, first served) and runs them together: one pass over the
- * block ranges finds the union of their active blocks (Section 4.1) and
- * each request's own candidates; one cache update and decode serves the
- * union (Section 4.2, Algorithm 1); then counting, offsets and emission
- * (Sections 4.3-4.5) run for all of the tick's requests in one launch
- * each.  Decoded blocks and all metadata stay resident between ticks;
- * every slot a request of the running tick reads is part of the union the
- * tick's cache update protects, so no in-flight request loses a block.
+ * Isovalue requests are queued with iso_server_submit and answered by
+ * iso_server_step.  Requests are served in ticks of up to max_batch queued
+ * requests (first come, first served).  A tick starts with one pass over
+ * the block ranges that finds the union of its requests' active blocks
+ * (Section 4.1) and each request's own candidates, and one cache update and
+ * decode for the union (Section 4.2, Algorithm 1); then each step counts,
+ * scans and emits the tick's next request (Sections 4.3-4.5), so a request
+ * finishes as soon as its own mesh is written.  Decoded blocks and all
+ * metadata stay resident between ticks; every slot a request of the running
+ * tick reads is part of the union the tick's cache update protects, so no
+ * in-flight request loses a block.
  * Admission: when the union's active blocks do not fit in the volume's
  * cache budget, the tick's requests return to the queue and later ticks
  * take half as many (down to one; a single request that does not fit
- * finishes with ISO_ERR_BUDGET).  Meshes are allocated when the tick knows
- * their sizes; a request whose mesh would take the bytes of finished,
- * not yet taken meshes past vertex_budget_bytes waits for a later tick
- * (with every request behind it), unless nothing else is held.  Every
- * served mesh is identical, byte for byte, to iso_extract of the same
- * isovalue on the same data.  The server uses the volume's device state:
- * do not extract from the volume on another stream while a server call
- * runs, and destroy the server before the volume. */
+ * finishes with ISO_ERR_BUDGET).  A mesh is allocated when its size is
+ * known; if it would take the bytes of finished, not yet taken meshes past
+ * vertex_budget_bytes, it and the rest of its tick return to the queue
+ * (a mesh is always allowed when nothing is held).  Every served mesh is
+ * identical, byte for byte, to iso_extract of the same isovalue on the
+ * same data.  The server uses the volume's device state: do not extract
+ * from the volume on another stream while a server call runs, and destroy
+ * the server before the volume. */
 typedef struct iso_server iso_server;
 
 typedef struct iso_server_options {
@@ -331,11 +332,14 @@ int iso_server_create(iso_server **out, iso_volume *v, const iso_server_options 
 /* Queue a request (host only, no device work); *ticket identifies it. */
 int iso_server_submit(iso_server *s, float isovalue, uint64_t *ticket);
 
-/* Run one tick (nothing if the queue is empty); blocks until it is done.
- * *completed (may be NULL) receives the number of requests it finished. */
+/* Serve the next request (starting a tick first if the last one is done;
+ * nothing if no request waits); blocks until it is done.  *completed (may
+ * be NULL) receives the number of requests finished (usually 1; 0 when a
+ * tick was refused by the cache budget or a mesh by the vertex budget;
+ * more when a tick failed as a whole). */
 int iso_server_step(iso_server *s, uint32_t *completed);
 
-/* Requests waiting in the queue. */
+/* Requests not finished yet (queued, or in the running tick). */
 int iso_server_queued(const iso_server *s, uint32_t *queued);
 
 /* Hand a finished request's mesh to the caller (release it with
@@ -354,7 +358,7 @@ void iso_server_destroy(iso_server *s);
  * Copies a per-stage array of the LAST extraction into host memory.
  * `bytes` is the size of host_dst; *count receives the number of elements
  * available (and copied, if they fit; otherwise ISO_ERR_CAPACITY). */
-#define ISO_DBG_ACTIVE_IDS 1   /* uint32[n_active]  I_active, ascending */
+#define ISO_DBG_ACTIVE_IDS 1   /* uint32[n_active]  I_active, ascending (ISO_DEBUG volumes only) */
 #define ISO_DBG_NEW_IDS 2      /* uint32[n_new]     I_new, ascending */
 #define ISO_DBG_SLOT_OF_BLOCK 3 /* int32[nb]        I_slot (-1 = not cached) */
 #define ISO_DBG_BLOCK_OF_SLOT 4 /* int32[n_slots]   S_block (-1 = empty) */

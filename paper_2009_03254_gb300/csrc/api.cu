@@ -382,9 +382,10 @@ int iso_load_volume(iso_volume **out, const void *compressed, size_t compressed_
     TRY(dalloc(v, &v->hull8, g.nb));
     TRY(dalloc(v, &v->tables, 256 + 256 * 16));
     TRY(dalloc(v, &s.mactive, nwords));
-    TRY(dalloc(v, &s.iactive, g.nb));
-    TRY(dalloc(v, &s.inew, g.nb));
-    TRY(dalloc(v, &s.icand, g.nb));
+    s.list_cap = std::min<uint32_t>(g.nb, v->cap);
+    if (v->flags & ISO_DEBUG) TRY(dalloc(v, &s.iactive, s.list_cap));
+    TRY(dalloc(v, &s.inew, s.list_cap));
+    TRY(dalloc(v, &s.icand, s.list_cap));
     TRY(dalloc(v, &s.islot, g.nb));
     TRY(dalloc(v, &s.slast, v->cap));
     TRY(dalloc(v, &s.sblock, v->cap));
@@ -440,9 +441,9 @@ int iso_load_volume(iso_volume **out, const void *compressed, size_t compressed_
     TRYC(cudaMemsetAsync(s.desc_mc, 0, (size_t)n_mc_desc * 8, st));
     // index lists start as valid ids, so that even a pass cut short by a
     // device-side timeout only ever indexes inside the volume and the cache
-    TRYC(cudaMemsetAsync(s.iactive, 0, (size_t)g.nb * 4, st));
-    TRYC(cudaMemsetAsync(s.inew, 0, (size_t)g.nb * 4, st));
-    TRYC(cudaMemsetAsync(s.icand, 0, (size_t)g.nb * 4, st));
+    if (s.iactive) TRYC(cudaMemsetAsync(s.iactive, 0, (size_t)s.list_cap * 4, st));
+    TRYC(cudaMemsetAsync(s.inew, 0, (size_t)s.list_cap * 4, st));
+    TRYC(cudaMemsetAsync(s.icand, 0, (size_t)s.list_cap * 4, st));
     TRYC(cudaMemsetAsync(s.newslot, 0, (size_t)v->cap * 4, st));
     TRYC(cudaMemsetAsync(s.lbuf[0], 0, (size_t)v->cap * 4, st));
     TRYC(cudaMemsetAsync(s.lbuf[1], 0, (size_t)v->cap * 4, st));
@@ -481,8 +482,10 @@ int iso_extract(iso_volume *v, float isovalue, iso_mesh *out) {
     if (!v || !out || !std::isfinite(isovalue)) return ISO_ERR_INVALID_ARG;
     DeviceGuard dg(v->device);
     std::memset(out, 0, sizeof(*out));
-    // first guess: the last surface's size plus a margin, else 2 per block
-    unsigned long long guess = v->last_tris ? v->last_tris + v->last_tris / 4 + 4096 : 2ull * v->g.nb + 4096;
+    // first guess: the last surface's size plus a margin; with no history,
+    // 2 per block up to 2^24 (a larger surface reruns only the emission)
+    unsigned long long guess = v->last_tris ? v->last_tris + v->last_tris / 4 + 4096
+                                            : std::min<unsigned long long>(2ull * v->g.nb + 4096, 1ull << 24);
     float4 *buf = nullptr;
     {
         const int arc = dalloc(v, &buf, guess * 3);
@@ -591,8 +594,10 @@ int iso_debug_get(iso_volume *v, int which, void *host_dst, size_t bytes, uint64
     uint64_t n = 0;
     size_t elem = 0;
     switch (which) {
-        case ISO_DBG_ACTIVE_IDS: src = v->s.iactive; n = v->last_n_active; elem = 4; break;
-        case ISO_DBG_NEW_IDS: src = v->s.inew; n = v->last_n_new; elem = 4; break;
+        case ISO_DBG_ACTIVE_IDS:
+            if (!dbg) return ISO_ERR_INVALID_ARG;
+            src = v->s.iactive; n = std::min<uint64_t>(v->last_n_active, v->s.list_cap); elem = 4; break;
+        case ISO_DBG_NEW_IDS: src = v->s.inew; n = std::min<uint64_t>(v->last_n_new, v->s.list_cap); elem = 4; break;
         case ISO_DBG_SLOT_OF_BLOCK: src = v->s.islot; n = v->g.nb; elem = 4; break;
         case ISO_DBG_BLOCK_OF_SLOT: src = v->s.sblock; n = v->last_slots; elem = 4; break;
         case ISO_DBG_SLOT_LAST_USE: src = v->s.slast; n = v->last_slots; elem = 4; break;
@@ -600,7 +605,7 @@ int iso_debug_get(iso_volume *v, int which, void *host_dst, size_t bytes, uint64
         case ISO_DBG_CELL_CASES: if (!dbg) return ISO_ERR_INVALID_ARG; src = v->s.dbg_cases; n = 64ull * v->last_n_cand; elem = 1; break;
         case ISO_DBG_BLOCK_TRIS: src = v->s.counts; n = v->last_n_cand; elem = 4; break;
         case ISO_DBG_BLOCK_OFFSETS: src = v->s.offsets; n = v->last_n_cand; elem = 8; break;
-        case ISO_DBG_CANDIDATES: src = v->s.icand; n = v->last_n_cand; elem = 4; break;
+        case ISO_DBG_CANDIDATES: src = v->s.icand; n = std::min<uint64_t>(v->last_n_cand, v->s.list_cap); elem = 4; break;
         case ISO_DBG_EDGE_IDS:
             if (!dbg) return ISO_ERR_INVALID_ARG;
             src = v->s.dbg_edges;

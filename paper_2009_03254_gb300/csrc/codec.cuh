@@ -113,23 +113,25 @@ __device__ __forceinline__ void decode_block(const uint64_t *__restrict__ w, uin
     const uint32_t end = rate * 64u;
     uint32_t pos = 9;
     uint32_t n = 0;                        // coefficients reached by the group tests
-    // One step per iteration: either the verbatim bits that open plane k or
-    // one group test with its unary run.  Lanes of a warp decode different
-    // blocks; stepping them through a single loop keeps them together even
-    // when their planes hold different numbers of group tests.
+    // One group test per iteration, preceded at the start of a plane by the
+    // plane's verbatim bits (predicated, so every lane runs the same
+    // instructions).  Lanes of a warp decode different blocks; a single
+    // loop of uniform steps keeps them together even when their planes hold
+    // different numbers of group tests.
     int k = 31;                            // plane number, most significant first
     uint64_t x = 0;
     bool opening = true;
     while (k >= 0 && pos < end) {
-        bool plane_done;
-        if (opening) {
-            const uint32_t m = min(n, end - pos);
-            x = m ? (bw.peek(pos) & low_mask(m)) : 0ull;
-            pos += m;
-            bw.advance(pos);
-            opening = false;
-            plane_done = n >= 64 || pos >= end;
-        } else {
+        // the verbatim bits of the n coefficients reached so far
+        const uint32_t m = opening ? min(n, end - pos) : 0u;
+        const uint64_t pk = bw.peek(pos);
+        x = opening ? (pk & low_mask(m)) : x;
+        pos += m;
+        bw.advance(pos);
+        // a plane ends after its verbatim bits when every coefficient is
+        // reached or the budget is spent (otherwise n < 64 and pos < end)
+        bool plane_done = n >= 64 || pos >= end;
+        if (!plane_done) {
             const uint64_t win = bw.peek(pos);
             pos += 1;
             if (!(win & 1ull)) {           // no later coefficient has a one here
@@ -158,8 +160,8 @@ __device__ __forceinline__ void decode_block(const uint64_t *__restrict__ w, uin
         if (plane_done) {
             planes[(uint32_t)k * stride] = x;
             k--;
-            opening = true;
         }
+        opening = plane_done;
     }
     for (; k >= 0; k--) planes[(uint32_t)k * stride] = 0ull;
     constexpr CodingOrder order = make_coding_order();

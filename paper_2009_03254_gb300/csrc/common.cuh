@@ -50,7 +50,6 @@ enum Status : uint32_t {
     kStatusBudget = 2u,       // new blocks do not fit in the slot cap
     kStatusTimeoutLru = 4u,   // cache-update look-back gave up
     kStatusTimeoutScan = 8u,  // triangle-offset look-back gave up
-    kStatusSkip = 16u,        // a served request whose output waits for a later tick: emit nothing
 };
 constexpr uint32_t kStatusAnyTimeout = kStatusTimeout | kStatusTimeoutLru | kStatusTimeoutScan;
 

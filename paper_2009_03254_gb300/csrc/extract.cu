@@ -86,35 +86,42 @@ __device__ __forceinline__ void cull_tile(const DevState &s, const Geom &g, uint
     const uint32_t lt = (1u << lane) - 1u;
     const uint32_t epoch = s.ctl->epoch;
     const float iso = s.ctl->params.iso;
-    float2 h[kR];
+    // two halves of kR/2 rounds; in each, every load (3x3x3 hull, +group
+    // hull, slot) is issued before any of it is used, so a tile waits for
+    // two memory round trips rather than one per round
+    constexpr int kHalf = kR / 2;
 #pragma unroll
-    for (int r = 0; r < kR; r++) {                    // all range loads of the tile first
-        const uint32_t b = tile * kTile + r * kThreads + threadIdx.x;
-        h[r] = b < g.nb ? __ldg(s.hull + b) : make_float2(0.f, 0.f);
-    }
+    for (int half = 0; half < 2; half++) {
+        float2 h[kHalf], h8[kHalf];
+        int32_t sl[kHalf];
 #pragma unroll
-    for (int r = 0; r < kR; r++) {
-        const uint32_t b = tile * kTile + r * kThreads + threadIdx.x;
-        const bool act = b < g.nb && (h[r].x < iso) && (iso <= h[r].y);
-        bool nw = false, cand = false;
-        if (act) {
-            const float2 h8 = __ldg(s.hull8 + b);
-            cand = (h8.x < iso) && (iso <= h8.y);
-            const int32_t sl = s.islot[b];
-            if (sl >= 0) s.slast[sl] = epoch;
-            else nw = true;
+        for (int i = 0; i < kHalf; i++) {
+            const uint32_t b = tile * kTile + (half * kHalf + i) * kThreads + threadIdx.x;
+            const bool in = b < g.nb;
+            h[i] = in ? __ldg(s.hull + b) : make_float2(0.f, 0.f);
+            h8[i] = in ? __ldg(s.hull8 + b) : make_float2(0.f, 0.f);
+            sl[i] = in ? s.islot[b] : -1;
         }
-        const uint32_t ab = __ballot_sync(0xffffffffu, act);
-        const uint32_t nbits = __ballot_sync(0xffffffffu, nw);
-        const uint32_t cb = __ballot_sync(0xffffffffu, cand);
-        if (lane == 0) {
-            sm.bal[0][r][warp] = ab;
-            sm.bal[1][r][warp] = nbits;
-            sm.bal[2][r][warp] = cb;
-            sm.ts.cnt[r][warp] = ((uint32_t)__popc(ab) << 16) | (uint32_t)__popc(nbits);
-            sm.tc.cnt[r][warp] = (uint32_t)__popc(cb);
-            const uint32_t first = tile * kTile + r * kThreads + warp * 32;
-            if (first < g.nb) s.mactive[first >> 5] = ab;
+#pragma unroll
+        for (int i = 0; i < kHalf; i++) {
+            const int r = half * kHalf + i;
+            const uint32_t b = tile * kTile + r * kThreads + threadIdx.x;
+            const bool act = b < g.nb && (h[i].x < iso) && (iso <= h[i].y);
+            const bool cand = act && (h8[i].x < iso) && (iso <= h8[i].y);
+            const bool nw = act && sl[i] < 0;
+            if (act && sl[i] >= 0) s.slast[sl[i]] = epoch;       // a hit: the slot's age resets
+            const uint32_t ab = __ballot_sync(0xffffffffu, act);
+            const uint32_t nbits = __ballot_sync(0xffffffffu, nw);
+            const uint32_t cb = __ballot_sync(0xffffffffu, cand);
+            if (lane == 0) {
+                sm.bal[0][r][warp] = ab;
+                sm.bal[1][r][warp] = nbits;
+                sm.bal[2][r][warp] = cb;
+                sm.ts.cnt[r][warp] = ((uint32_t)__popc(ab) << 16) | (uint32_t)__popc(nbits);
+                sm.tc.cnt[r][warp] = (uint32_t)__popc(cb);
+                const uint32_t first = tile * kTile + r * kThreads + warp * 32;
+                if (first < g.nb) s.mactive[first >> 5] = ab;
+            }
         }
     }
     __syncthreads();
@@ -146,9 +153,12 @@ __device__ __forceinline__ void cull_tile(const DevState &s, const Geom &g, uint
         const uint32_t b = tile * kTile + r * kThreads + threadIdx.x;
         const uint32_t ab = sm.bal[0][r][warp], nbits = sm.bal[1][r][warp], cb = sm.bal[2][r][warp];
         const uint32_t off = sm.ts.cnt[r][warp];
-        if ((ab >> lane) & 1u) s.iactive[act_base + (off >> 16) + __popc(ab & lt)] = b;
-        if ((cb >> lane) & 1u) s.icand[cand_base + sm.tc.cnt[r][warp] + __popc(cb & lt)] = b;
-        if ((nbits >> lane) & 1u) s.inew[new_base + (off & 0xFFFFu) + __popc(nbits & lt)] = b;
+        const uint32_t ai = act_base + (off >> 16) + __popc(ab & lt);
+        const uint32_t ci = cand_base + sm.tc.cnt[r][warp] + __popc(cb & lt);
+        const uint32_t ni = new_base + (off & 0xFFFFu) + __popc(nbits & lt);
+        if (s.iactive && ((ab >> lane) & 1u) && ai < s.list_cap) s.iactive[ai] = b;
+        if (((cb >> lane) & 1u) && ci < s.list_cap) s.icand[ci] = b;
+        if (((nbits >> lane) & 1u) && ni < s.list_cap) s.inew[ni] = b;
     }
     __syncthreads();
 }
@@ -278,11 +288,15 @@ __global__ void __launch_bounds__(kThreads) lru_a_kernel(Launch L) {
                 const uint32_t i = tile * kScanTile + r * kThreads + threadIdx.x;
                 slot[r] = i < u ? Lst[i] : 0u;
             }
+            uint32_t last[kRounds];           // all gathers issued before any is used
 #pragma unroll
             for (int r = 0; r < kRounds; r++) {
                 const uint32_t i = tile * kScanTile + r * kThreads + threadIdx.x;
-                const bool av = i < u && s.slast[slot[r]] != epoch;
-                bits[r] = __ballot_sync(0xffffffffu, av);
+                last[r] = i < u ? s.slast[slot[r]] : epoch;
+            }
+#pragma unroll
+            for (int r = 0; r < kRounds; r++) {
+                bits[r] = __ballot_sync(0xffffffffu, last[r] != epoch);
                 if (lane == 0) ts.cnt[r][warp] = (uint32_t)__popc(bits[r]);
             }
             __syncthreads();
@@ -331,12 +345,15 @@ __global__ void __launch_bounds__(kThreads) lru_b_kernel(Launch L) {
         const uint32_t tile = x - item_base<kOne>(pre, v);
         const uint32_t epoch = c->epoch, S2 = c->S_next, keep = c->keep_base;
         uint32_t *Ln = s.lbuf[c->lpar ^ 1u];
-        uint32_t bits[kRounds];
+        uint32_t bits[kRounds], last[kRounds];
+#pragma unroll
+        for (int r = 0; r < kRounds; r++) {   // all loads first
+            const uint32_t i = tile * kScanTile + r * kThreads + threadIdx.x;
+            last[r] = i < S2 ? s.slast[i] : ~epoch;
+        }
 #pragma unroll
         for (int r = 0; r < kRounds; r++) {
-            const uint32_t i = tile * kScanTile + r * kThreads + threadIdx.x;
-            const bool used_now = i < S2 && s.slast[i] == epoch;
-            bits[r] = __ballot_sync(0xffffffffu, used_now);
+            bits[r] = __ballot_sync(0xffffffffu, last[r] == epoch);
             if (lane == 0) ts.cnt[r][warp] = (uint32_t)__popc(bits[r]);
         }
         __syncthreads();

@@ -15,9 +15,11 @@ struct DevState {
     const float2 *hull;        // per block: min/max over its 3x3x3 block neighbourhood
     const float2 *hull8;       // per block: min/max over its 2x2x2 +group
     uint32_t *mactive;         // M_active bitmask, ceil(nb/32) words
-    uint32_t *iactive;         // I_active
+    uint32_t *iactive;         // I_active (kept only for debugging: nothing downstream reads it; else null)
     uint32_t *inew;            // I_new
     uint32_t *icand;           // candidates: ids of the blocks the triangle stage visits (ascending)
+    uint32_t list_cap;         // room of I_active, I_new and the candidates: min(nb, slot cap); longer
+                               // lists mean more active blocks than slots, which the cache update refuses
     int32_t *islot;            // I_slot: block -> slot or -1
     uint32_t *slast;           // S_last: slot -> epoch of last use (0 = never)
     int32_t *sblock;           // S_block: slot -> block or -1

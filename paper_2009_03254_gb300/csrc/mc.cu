@@ -106,7 +106,11 @@ __device__ __forceinline__ int halo_off(int s) { return (s % 5) + 8 * ((s / 5) %
 struct LaneConst {
     uint32_t job0, job1;                // halo jobs lane and lane + 32
     int cls[4];                         // halo offsets of samples lane + 32r (or -1)
-    int cword[2], cshift[2];            // where each of the lane's two cells starts in the 128-bit mask
+    // where each of the lane's two cells starts in the 128-bit mask: cell
+    // lane (z 0..1) starts in word 0 or 1, cell lane + 32 (z 2..3) in word
+    // 1 or 2; `up` says the later of the two, `cshift` the bit in it
+    bool up[2];
+    int cshift[2];
     __device__ __forceinline__ void init(int lane) {
         job0 = halo_job(lane);
         job1 = halo_job(lane + 32);
@@ -115,11 +119,17 @@ struct LaneConst {
 #pragma unroll
         for (int h = 0; h < 2; h++) {
             const int cell = lane + 32 * h, base = (cell & 3) + 5 * ((cell >> 2) & 3) + 25 * (cell >> 4);
-            cword[h] = base >> 5;
+            up[h] = (base >> 5) != h;
             cshift[h] = base & 31;
         }
     }
 };
+
+// the 8-bit case of a cell from the 32 mask bits starting at its lower corner
+// (corner c at bit (c&1) + 5((c>>1)&1) + 25(c>>2))
+__device__ __forceinline__ uint32_t case_bits(uint32_t W) {
+    return (W & 3u) | ((W >> 3) & 0xCu) | ((W >> 21) & 0x30u) | ((W >> 24) & 0xC0u);
+}
 
 // Phases A-C for the warp tile starting at candidate `base` (nb_w of
 // kBPW slots used).  Leaves cases in wt.cases when kKeepCases and returns
@@ -190,20 +200,28 @@ __device__ __forceinline__ void stage_and_classify(const DevState &s, const Geom
 #pragma unroll
         for (int r = 0; r < 4; r++) m[r] = __ballot_sync(0xffffffffu, lc.cls[r] >= 0 && hb[lc.cls[r]] < iso);
         const uint32_t lim = wt.lim[q];
+        uint32_t cs[2];
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const uint32_t lo = lc.up[h] ? m[h + 1] : m[h];
+            const uint32_t hi = lc.up[h] ? m[h + 2] : m[h + 1];
+            cs[h] = case_bits(__funnelshift_r(lo, hi, lc.cshift[h]));
+        }
+        if (lim != 0x444u) {              // warp-uniform: cells past the volume's last sample are empty
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const uint32_t cell = (uint32_t)lane + 32u * h;
+                const bool valid = (cell & 3u) < (lim & 15u) && ((cell >> 2) & 3u) < ((lim >> 4) & 15u) &&
+                                   (cell >> 4) < (lim >> 8);
+                cs[h] = valid ? cs[h] : 0u;
+            }
+        }
 #pragma unroll
         for (int h = 0; h < 2; h++) {
             const int cell = lane + 32 * h;
-            const uint32_t lo = lc.cword[h] == 0 ? m[0] : (lc.cword[h] == 1 ? m[1] : m[2]);
-            const uint32_t hi = lc.cword[h] == 0 ? m[1] : (lc.cword[h] == 1 ? m[2] : m[3]);
-            const uint32_t W = __funnelshift_r(lo, hi, lc.cshift[h]);
-            uint32_t cs = (W & 3u) | ((W >> 3) & 0xCu) | ((W >> 21) & 0x30u) | ((W >> 24) & 0xC0u);
-            const bool valid = (uint32_t)(cell & 3) < (lim & 15u) &&
-                               (uint32_t)((cell >> 2) & 3) < ((lim >> 4) & 15u) &&
-                               (uint32_t)(cell >> 4) < ((lim >> 8) & 15u);
-            cs = valid ? cs : 0u;
-            if (kKeepCases) wt.cases[q][cell] = (uint8_t)cs;
-            if (kDebug) s.dbg_cases[(size_t)(base + q) * 64 + cell] = (uint8_t)cs;
-            const uint32_t n = num_tri[cs];
+            if (kKeepCases) wt.cases[q][cell] = (uint8_t)cs[h];
+            if (kDebug) s.dbg_cases[(size_t)(base + q) * 64 + cell] = (uint8_t)cs[h];
+            const uint32_t n = num_tri[cs[h]];
             if (h == 0) n0p |= n << (8 * q);
             else n1p |= n << (8 * q);
         }
@@ -247,7 +265,7 @@ __device__ __forceinline__ TileRef locate_tile(const Launch &L, const uint32_t *
 // ================================================================ count (Section 4.4)
 
 template <int kW, bool kDebug, bool kOne>
-__global__ void __launch_bounds__(32 * kW) mc_count_kernel(Launch L) {
+__global__ void __launch_bounds__(32 * kW, 32 / kW) mc_count_kernel(Launch L) {   // 1024 threads per SM
     extern __shared__ __align__(16) unsigned char smem_raw[];
     CountSmem<kW> &sm = *reinterpret_cast<CountSmem<kW> *>(smem_raw);
     __shared__ uint32_t pre[kMaxBatch + 1];
@@ -390,7 +408,7 @@ __global__ void __launch_bounds__(32 * kW) mc_emit_kernel(Launch L) {
     const uint32_t total = launch_prefix<kOne>(
         L, [&](uint32_t v) {
             const Ctl *c = vol_of<kOne>(L, v).s.ctl;
-            return (c->status & (kStatusBudget | kStatusAnyTimeout | kStatusSkip)) ? 0u : ceil_div(c->n_cand, kBPW);
+            return (c->status & (kStatusBudget | kStatusAnyTimeout)) ? 0u : ceil_div(c->n_cand, kBPW);
         },
         pre);
     __syncthreads();                                      // the tables

@@ -1,23 +1,25 @@
 // Serving (C ABI in include/bcmc.h): isovalue requests on one resident
-// volume, answered in ticks.  A tick takes up to kMaxServe queued requests
-// and runs them together:
-//   serve_prep     clear the tick's counters and descriptors
-//   serve_cull     one pass over the block ranges for all the tick's
-//                  isovalues (Section 4.1): the union of their active sets
-//                  (one cache update serves them all) and each request's
-//                  own candidate list
-//   cache update   Algorithm 1 and the decode (Section 4.2) on the union
-//   count, scan    Sections 4.3-4.4 for every request in one launch each
-//                  (the requests are "views" of the volume: own control
-//                  block, candidates, counts and offsets; shared cache)
-//   readback       the requests' triangle counts; the host allocates each
-//                  mesh, deferring what exceeds the vertex budget
-//   emit           Section 4.5 for every request in one launch
-// Decoded blocks and all metadata stay resident between ticks.  The union
-// is what the tick's cache update protects, so every slot an in-flight
-// request reads stays pinned until the tick ends.  If the union does not
-// fit in the cache budget, the tick's requests go back to the queue and
-// the next ticks take half as many (down to one).
+// volume, answered in ticks.  A tick takes up to kMaxServe queued requests:
+//   front (once per tick)
+//     serve_prep     clear the tick's counters and descriptors
+//     serve_cull     one pass over the block ranges for all the tick's
+//                    isovalues (Section 4.1): the union of their active sets
+//                    and each request's own candidate list
+//     cache update   Algorithm 1 and the decode (Section 4.2) on the union
+//   then, one request per step, in arrival order
+//     count, scan    Sections 4.3-4.4 over the request's candidates (the
+//                    request is a "view" of the volume: own control block,
+//                    candidates, counts and offsets; shared cache)
+//     readback       its triangle count; the host allocates its mesh
+//     emit           Section 4.5
+// A request finishes as soon as its own emission is done: later requests
+// of the tick never delay it, while the cull, cache update and decode are
+// paid once for the whole tick.  Decoded blocks and all metadata stay
+// resident between ticks.  The union is what the tick's cache update
+// protects, so every slot a request of the running tick reads stays pinned
+// until the tick ends.  If the union does not fit in the cache budget, the
+// tick's requests go back to the queue and the next ticks take half as
+// many (down to one).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -45,7 +47,6 @@ struct ServeArgs {
     uint32_t *icand[kMaxServe];       // per-request candidate lists
     unsigned long long *desc_cand[kMaxServe];
     unsigned long long *desc_mc[kMaxServe];
-    uint32_t *view_ctr;               // work counters of the per-request launches
     uint32_t cand_cap;                // room of each candidate list
 };
 
@@ -82,8 +83,8 @@ __global__ void __launch_bounds__(kThreads) serve_prep_kernel(ServeArgs a) {
         c->n_occ = 0;
         c->status = 0;
         c->params.iso = a.iso[tid];
+        for (int i = 0; i < kNumLaunchCounters; i++) c->ctr[i] = 0;   // the request's own launches
     }
-    if (tid < kNumLaunchCounters) a.view_ctr[tid] = 0;
 }
 
 // The cull of Section 4.1 for all the tick's isovalues in one pass over
@@ -188,8 +189,10 @@ __global__ void __launch_bounds__(kThreads) serve_cull_kernel(ServeArgs a) {
             const uint32_t b = tile * kTile + r * kThreads + threadIdx.x;
             const uint32_t ab = sm.bal[0][r][warp], nbits = sm.bal[1][r][warp];
             const uint32_t off = sm.ts.cnt[r][warp];
-            if ((ab >> lane) & 1u) s.iactive[act_base + (off >> 16) + __popc(ab & lt)] = b;
-            if ((nbits >> lane) & 1u) s.inew[new_base + (off & 0xFFFFu) + __popc(nbits & lt)] = b;
+            const uint32_t ai = act_base + (off >> 16) + __popc(ab & lt);
+            const uint32_t ni = new_base + (off & 0xFFFFu) + __popc(nbits & lt);
+            if (s.iactive && ((ab >> lane) & 1u) && ai < s.list_cap) s.iactive[ai] = b;
+            if (((nbits >> lane) & 1u) && ni < s.list_cap) s.inew[ni] = b;
             for (uint32_t j = 0; j < k; j++) {
                 // a list longer than its room means more active blocks than
                 // cache slots: the cache update fails the tick, nothing reads it
@@ -206,20 +209,6 @@ __global__ void __launch_bounds__(kThreads) serve_cull_kernel(ServeArgs a) {
 __global__ void serve_status_kernel(ServeArgs a) {
     const uint32_t j = threadIdx.x;
     if (j < a.k) a.ctl[j]->status |= a.base.s.ctl->status & (kStatusBudget | kStatusAnyTimeout);
-}
-
-// each request's output; a capacity of kDeferred: the request waits for a
-// later tick and emits nothing now
-constexpr unsigned long long kDeferred = ~0ull;
-
-__global__ void serve_outputs_kernel(ServeArgs a, const BatchOut *__restrict__ outs) {
-    const uint32_t j = threadIdx.x;
-    if (j >= a.k) return;
-    Ctl *c = a.ctl[j];
-    const bool deferred = outs[j].tri_cap == kDeferred;
-    c->params.out = outs[j].out;
-    c->params.tri_cap = deferred ? 0ull : outs[j].tri_cap;
-    if (deferred) c->status |= kStatusSkip;
 }
 
 }  // namespace bcmc
@@ -256,15 +245,15 @@ struct iso_server {
     uint32_t cand_cap = 0;              // room of each request's candidate list
     uint64_t held_bytes = 0;            // finished meshes not yet taken
     Slot slots[kMaxServe];
-    VolEntry *d_views = nullptr;        // per-request views of the volume
-    uint32_t *d_view_ctr = nullptr;
-    Ctl *d_ctls = nullptr;              // gathered per-request control blocks
-    BatchOut *d_outs = nullptr;
-    Ctl *h_ctls = nullptr;              // pinned
-    BatchOut *h_outs = nullptr;
-    Plan view_plan{};                   // launches over the views
+    VolEntry views[kMaxServe];          // per-request views of the volume (by value into each launch)
+    Ctl *h_ctl = nullptr;               // pinned: one request's control block, read back
+    Params *h_params = nullptr;         // pinned: one request's output
+    Plan view_plan{};                   // launches over one view
     uint64_t next_ticket = 1;
     std::deque<Request> queue;
+    std::vector<Request> tick;          // the running tick's requests
+    uint32_t tick_next = 0;             // next of them to emit
+    Ctl tick_union{};                   // the tick's union figures (for the stats)
     std::map<uint64_t, Done> done;
 };
 
@@ -282,7 +271,6 @@ ServeArgs serve_args(const iso_server *sv, const std::vector<Request> &reqs) {
         a.desc_cand[j] = sv->slots[j].desc_cand;
         a.desc_mc[j] = sv->slots[j].desc_mc;
     }
-    a.view_ctr = sv->d_view_ctr;
     a.cand_cap = sv->cand_cap;
     return a;
 }
@@ -296,23 +284,21 @@ void free_server(iso_server *sv) {
         void *p[] = {s.ctl, s.icand, s.counts, s.offsets, s.desc_cand, s.desc_mc};
         for (void *x : p) dfree_on(x, sv->stream);
     }
-    void *p[] = {sv->d_views, sv->d_view_ctr, sv->d_ctls, sv->d_outs};
-    for (void *x : p) dfree_on(x, sv->stream);
     cudaStreamSynchronize(sv->stream);
     (void)cudaGetLastError();
-    if (sv->h_ctls) cudaFreeHost(sv->h_ctls);
-    if (sv->h_outs) cudaFreeHost(sv->h_outs);
+    if (sv->h_ctl) cudaFreeHost(sv->h_ctl);
+    if (sv->h_params) cudaFreeHost(sv->h_params);
     delete sv;
 }
 
-void finish(iso_server *sv, const Request &r, int status, const Ctl *c, const Ctl &uni, float *buf) {
+void finish(iso_server *sv, const Request &r, int status, const Ctl *c, float *buf) {
     Done d{};
     d.status = status;
     d.mesh.d_vertices = buf;
     if (c) {
         d.mesh.num_triangles = buf ? c->n_tri : 0;
         d.mesh.capacity_triangles = buf ? c->n_tri : 0;
-        Ctl s = uni;                    // the tick's cache figures, the request's own surface figures
+        Ctl s = sv->tick_union;         // the tick's cache figures, the request's own surface figures
         s.n_tri = c->n_tri;
         s.n_occ = c->n_occ;
         s.n_cand = c->n_cand;
@@ -322,92 +308,107 @@ void finish(iso_server *sv, const Request &r, int status, const Ctl *c, const Ct
     sv->done[r.ticket] = d;
 }
 
-// One tick over `reqs` (k >= 1).  Returns ISO_OK with the requests
-// finished or re-queued, or a CUDA error.
-int run_tick(iso_server *sv, const std::vector<Request> &reqs, uint32_t *completed) {
+void requeue_rest(iso_server *sv) {     // the tick's unfinished requests, in order, to the queue's front
+    for (uint32_t j = (uint32_t)sv->tick.size(); j-- > sv->tick_next;) sv->queue.push_front(sv->tick[j]);
+    sv->tick.clear();
+    sv->tick_next = 0;
+}
+
+// The front of a tick over the queue's first requests.  Returns ISO_OK
+// (with sv->tick set, or the requests re-queued or finished), or a CUDA
+// error.
+int start_tick(iso_server *sv, uint32_t *completed) {
     iso_volume *v = sv->v;
     cudaStream_t st = sv->stream;
-    const uint32_t k = (uint32_t)reqs.size();
-    const ServeArgs a = serve_args(sv, reqs);
+    const uint32_t k = std::min<uint32_t>(sv->limit, (uint32_t)sv->queue.size());
+    sv->tick.clear();
+    for (uint32_t j = 0; j < k; j++) {
+        sv->tick.push_back(sv->queue.front());
+        sv->queue.pop_front();
+    }
+    sv->tick_next = 0;
+    const ServeArgs a = serve_args(sv, sv->tick);
     const Launch single{nullptr, 1u, single_counters(v), a.base};
-    const Launch views{sv->d_views, k, sv->d_view_ctr, VolEntry{}};
     serve_prep_kernel<<<v->plan.prep, kThreads, 0, st>>>(a);
     serve_cull_kernel<<<v->plan.cull, kThreads, 0, st>>>(a);
     launch_cache_update(single, v->plan, st);
     serve_status_kernel<<<1, kMaxServe, 0, st>>>(a);
-    launch_mc_count(views, false, sv->view_plan, st);
-    launch_mc_scan(views, sv->view_plan, st);
-    launch_batch_gather(views, sv->d_ctls, st);
-    ISO_CK(cudaMemcpyAsync(sv->h_ctls, sv->d_ctls, k * sizeof(Ctl), cudaMemcpyDeviceToHost, st));
     ISO_CK(cudaMemcpyAsync(v->host_ctl, v->s.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
     ISO_CK(cudaGetLastError());
     ISO_CK(cudaStreamSynchronize(st));
     const Ctl uni = *v->host_ctl;
+    sv->tick_union = uni;
     v->last_n_active = uni.n_active;
     v->last_n_new = uni.n_new;
     v->last_n_cand = 0;
     v->last_slots = uni.S;
     if (uni.status & kStatusAnyTimeout) {
         status_to_error(v, uni.status);   // empties the cache
-        for (const Request &r : reqs) finish(sv, r, ISO_ERR_TIMEOUT, &sv->h_ctls[0], uni, nullptr);
+        for (const Request &r : sv->tick) finish(sv, r, ISO_ERR_TIMEOUT, nullptr, nullptr);
         *completed += k;
+        sv->tick.clear();
         return ISO_OK;
     }
     if (uni.status & kStatusBudget) {
         if (k > 1) {                      // too many decodes at once: fewer requests per tick
-            for (uint32_t j = k; j-- > 0;) sv->queue.push_front(reqs[j]);
+            requeue_rest(sv);
             sv->limit = std::max(1u, k / 2);
             return ISO_OK;
         }
-        finish(sv, reqs[0], ISO_ERR_BUDGET, &sv->h_ctls[0], uni, nullptr);
+        finish(sv, sv->tick[0], ISO_ERR_BUDGET, nullptr, nullptr);
+        *completed += 1;
+        sv->tick.clear();
+        return ISO_OK;
+    }
+    sv->limit = std::min(sv->max_batch, sv->limit * 2);
+    return ISO_OK;
+}
+
+// Count, scan and emit the tick's next request.  A mesh that does not fit
+// the vertex budget sends it and the rest of the tick back to the queue.
+int emit_next(iso_server *sv, uint32_t *completed) {
+    cudaStream_t st = sv->stream;
+    const uint32_t j = sv->tick_next;
+    const Request r = sv->tick[j];
+    const VolEntry &view = sv->views[j];
+    Ctl *dctl = sv->slots[j].ctl;
+    uint32_t *ctr = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(dctl) + offsetof(Ctl, ctr));
+    const Launch L{nullptr, 1u, ctr, view};
+    launch_mc_count(L, false, sv->view_plan, st);
+    launch_mc_scan(L, sv->view_plan, st);
+    ISO_CK(cudaMemcpyAsync(sv->h_ctl, dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    ISO_CK(cudaGetLastError());
+    ISO_CK(cudaStreamSynchronize(st));
+    const Ctl c = *sv->h_ctl;
+    if (c.status & kStatusAnyTimeout) {
+        finish(sv, r, ISO_ERR_TIMEOUT, &c, nullptr);
+        sv->tick_next++;
         *completed += 1;
         return ISO_OK;
     }
-    // allocate each mesh, within the vertex budget (in request order)
-    std::vector<float *> bufs(k, nullptr);
-    std::vector<int> state(k, ISO_OK);
-    uint64_t planned = sv->held_bytes;
-    bool defer_rest = false;
-    for (uint32_t j = 0; j < k; j++) {
-        const Ctl &c = sv->h_ctls[j];
-        sv->h_outs[j] = BatchOut{0ull, kDeferred};
-        if (c.status & kStatusAnyTimeout) {
-            state[j] = ISO_ERR_TIMEOUT;
-            continue;
-        }
-        const uint64_t bytes = 48ull * c.n_tri;
-        if (defer_rest || (sv->vertex_budget && planned + bytes > sv->vertex_budget && planned > 0)) {
-            defer_rest = true;            // keeps arrival order: later requests wait too
-            state[j] = ISO_PENDING;
-            continue;
-        }
-        if (c.n_tri) {
-            float *p = nullptr;
-            const int rc = dalloc_on(&p, (size_t)c.n_tri * 12, sv->device, st);
-            if (rc) {
-                state[j] = rc;
-                continue;
-            }
-            bufs[j] = p;
-            sv->h_outs[j] = BatchOut{(unsigned long long)(uintptr_t)p, c.n_tri};
-        } else {
-            sv->h_outs[j] = BatchOut{0ull, 0ull};   // an empty surface: nothing to write
-        }
-        planned += bytes;
+    const uint64_t bytes = 48ull * c.n_tri;
+    if (sv->vertex_budget && sv->held_bytes > 0 && sv->held_bytes + bytes > sv->vertex_budget) {
+        requeue_rest(sv);                 // wait until the held meshes are taken
+        return ISO_OK;
     }
-    ISO_CK(cudaMemcpyAsync(sv->d_outs, sv->h_outs, k * sizeof(BatchOut), cudaMemcpyHostToDevice, st));
-    serve_outputs_kernel<<<1, kMaxServe, 0, st>>>(a, sv->d_outs);
-    launch_mc_emit(views, false, sv->view_plan, st);
+    float *buf = nullptr;
+    if (c.n_tri) {
+        const int rc = dalloc_on(&buf, (size_t)c.n_tri * 12, sv->device, st);
+        if (rc) {
+            finish(sv, r, rc, &c, nullptr);
+            sv->tick_next++;
+            *completed += 1;
+            return ISO_OK;
+        }
+    }
+    *sv->h_params = Params{r.iso, 0u, c.n_tri, (unsigned long long)(uintptr_t)buf};
+    ISO_CK(cudaMemcpyAsync(&dctl->params, sv->h_params, sizeof(Params), cudaMemcpyHostToDevice, st));
+    launch_mc_emit(L, false, sv->view_plan, st);
     ISO_CK(cudaGetLastError());
     ISO_CK(cudaStreamSynchronize(st));
-    for (uint32_t j = k; j-- > 0;)
-        if (state[j] == ISO_PENDING) sv->queue.push_front(reqs[j]);
-    for (uint32_t j = 0; j < k; j++) {
-        if (state[j] == ISO_PENDING) continue;
-        finish(sv, reqs[j], state[j], &sv->h_ctls[j], uni, bufs[j]);
-        *completed += 1;
-    }
-    sv->limit = std::min(sv->max_batch, sv->limit * 2);
+    finish(sv, r, ISO_OK, &c, buf);
+    sv->tick_next++;
+    *completed += 1;
     return ISO_OK;
 }
 
@@ -439,7 +440,6 @@ int iso_server_create(iso_server **out, iso_volume *v, const iso_server_options 
         rc = (x);                                \
         if (rc) { free_server(sv); return rc; }  \
     } while (0)
-    std::vector<VolEntry> views(sv->max_batch);
     for (uint32_t j = 0; j < sv->max_batch; j++) {
         Slot &s = sv->slots[j];
         TRY(dalloc_on(&s.ctl, 1, sv->device, sv->stream));
@@ -455,22 +455,16 @@ int iso_server_create(iso_server **out, iso_volume *v, const iso_server_options 
         d.offsets = s.offsets;
         d.desc_cand = s.desc_cand;
         d.desc_mc = s.desc_mc;
-        views[j] = VolEntry{d, v->g, v->n_cull_desc, v->n_lru_desc};
+        sv->views[j] = VolEntry{d, v->g, v->n_cull_desc, v->n_lru_desc};
     }
-    TRY(dalloc_on(&sv->d_views, sv->max_batch, sv->device, sv->stream));
-    TRY(dalloc_on(&sv->d_view_ctr, kNumLaunchCounters, sv->device, sv->stream));
-    TRY(dalloc_on(&sv->d_ctls, sv->max_batch, sv->device, sv->stream));
-    TRY(dalloc_on(&sv->d_outs, sv->max_batch, sv->device, sv->stream));
-    if (cudaMallocHost((void **)&sv->h_ctls, sv->max_batch * sizeof(Ctl)) != cudaSuccess ||
-        cudaMallocHost((void **)&sv->h_outs, sv->max_batch * sizeof(BatchOut)) != cudaSuccess) {
+    if (cudaMallocHost((void **)&sv->h_ctl, sizeof(Ctl)) != cudaSuccess ||
+        cudaMallocHost((void **)&sv->h_params, sizeof(Params)) != cudaSuccess) {
         (void)cudaGetLastError();
         free_server(sv);
         return ISO_ERR_OOM;
     }
     cudaStream_t st = sv->stream;
-    bool ok = cudaStreamSynchronize(v->stream) == cudaSuccess &&
-              cudaMemcpyAsync(sv->d_views, views.data(), views.size() * sizeof(VolEntry), cudaMemcpyHostToDevice,
-                              st) == cudaSuccess;
+    bool ok = cudaStreamSynchronize(v->stream) == cudaSuccess;
     for (uint32_t j = 0; ok && j < sv->max_batch; j++) {
         ok = cudaMemsetAsync(sv->slots[j].ctl, 0, sizeof(Ctl), st) == cudaSuccess &&
              cudaMemsetAsync(sv->slots[j].icand, 0, cand * 4, st) == cudaSuccess &&
@@ -483,8 +477,7 @@ int iso_server_create(iso_server **out, iso_volume *v, const iso_server_options 
         return ISO_ERR_CUDA;
     }
 #undef TRY
-    sv->view_plan = launch_plan(nullptr, sv->device, (uint64_t)v->g.nb * sv->max_batch,
-                                (uint64_t)cand * sv->max_batch, sv->max_batch, false);
+    sv->view_plan = launch_plan(nullptr, sv->device, v->g.nb, cand, 1, true);
     *out = sv;
     return ISO_OK;
 }
@@ -500,22 +493,22 @@ int iso_server_step(iso_server *sv, uint32_t *completed) {
     if (!sv) return ISO_ERR_INVALID_ARG;
     uint32_t n = 0;
     if (completed) *completed = 0;
-    if (sv->queue.empty()) return ISO_OK;
     DeviceGuard dg(sv->device);
-    std::vector<Request> reqs;
-    const uint32_t k = std::min<uint32_t>(sv->limit, (uint32_t)sv->queue.size());
-    for (uint32_t j = 0; j < k; j++) {
-        reqs.push_back(sv->queue.front());
-        sv->queue.pop_front();
+    int rc = ISO_OK;
+    if (sv->tick_next >= sv->tick.size()) {       // the last tick is done: start one
+        sv->tick.clear();
+        sv->tick_next = 0;
+        if (sv->queue.empty()) return ISO_OK;
+        rc = start_tick(sv, &n);
     }
-    const int rc = run_tick(sv, reqs, &n);
+    if (rc == ISO_OK && sv->tick_next < sv->tick.size()) rc = emit_next(sv, &n);
     if (completed) *completed = n;
     return rc;
 }
 
 int iso_server_queued(const iso_server *sv, uint32_t *queued) {
     if (!sv || !queued) return ISO_ERR_INVALID_ARG;
-    *queued = (uint32_t)sv->queue.size();
+    *queued = (uint32_t)(sv->queue.size() + (sv->tick.size() - std::min<size_t>(sv->tick_next, sv->tick.size())));
     return ISO_OK;
 }
 
@@ -526,6 +519,8 @@ int iso_server_take(iso_server *sv, uint64_t ticket, iso_mesh *out) {
         if (ticket == 0 || ticket >= sv->next_ticket) return ISO_ERR_INVALID_ARG;
         for (const Request &r : sv->queue)
             if (r.ticket == ticket) return ISO_PENDING;
+        for (uint32_t j = sv->tick_next; j < sv->tick.size(); j++)
+            if (sv->tick[j].ticket == ticket) return ISO_PENDING;
         return ISO_ERR_INVALID_ARG;       // already taken
     }
     *out = it->second.mesh;

@@ -97,4 +97,7 @@ def generate(recipe, origin=(0, 0, 0), dims=None):
                           origin=origin)
     if recipe.kind == "noise":
         return gradient_noise(nx, ny, nz, recipe.seed, origin=origin)
+    if recipe.kind == "channel":
+        return channel_field(nx, ny, nz, recipe.seed, nz_total=recipe.dims[2], origin=origin,
+                             octaves=recipe.octaves, base_period=recipe.base_period)
     raise ValueError(recipe.kind)

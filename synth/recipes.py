@@ -10,7 +10,12 @@ Each recipe mirrors the shape of a workload in the paper's evaluation
 * ``channel2k``  -- 2048 x 2048 x 1024 channel-flow-like spectral field,
                     4 bits/value, isovalue at the 70th percentile.
 * ``batch64``    -- 64 volumes with per-axis sizes log-uniform in [32, 256].
-* ``serve_dns``  -- 10240 x 7680 x 1536 DNS-shaped field at 2 bits/value.
+* ``serve_dns``  -- 10240 x 7680 x 1536 DNS-shaped field at 2 bits/value
+                    (coarser structure, so that one surface is 10^8-scale
+                    triangles), the serving workload.
+
+Channel isovalues are percentiles of the decoded data (``percentile``),
+computed when the volume is built.
 """
 from __future__ import annotations
 
@@ -29,10 +34,17 @@ class VolumeRecipe:
     seed: int
     isovalues: tuple
     radius: float = 0.0  # sphere only
+    octaves: int = 7     # channel only: noise octaves and coarsest period (voxels)
+    base_period: int = 256
+    percentile: float = 0.0   # channel only: isovalue rank in the decoded data
 
 
 SPHERE64 = VolumeRecipe("sphere64", (64, 64, 64), 16, "sphere", 0, (0.0,), radius=20.0)
 NOISE512 = VolumeRecipe("noise512", (512, 512, 512), 8, "noise", 1, (-1.0, -0.5, 0.0, 0.5, 1.0))
+CHANNEL2K = VolumeRecipe("channel2k", (2048, 2048, 1024), 4, "channel", 7, (), octaves=7, base_period=256,
+                         percentile=0.7)
+SERVE_DNS = VolumeRecipe("serve_dns", (10240, 7680, 1536), 2, "channel", 5, (), octaves=2, base_period=2048,
+                         percentile=0.5)
 
 
 def generate_cpu(recipe: VolumeRecipe, origin=(0, 0, 0), dims=None):
@@ -45,6 +57,9 @@ def generate_cpu(recipe: VolumeRecipe, origin=(0, 0, 0), dims=None):
         return fields.sphere_sdf(nx, ny, nz, recipe.radius, center=c, origin=origin)
     if recipe.kind == "noise":
         return fields.gradient_noise(nx, ny, nz, recipe.seed, origin=origin)
+    if recipe.kind == "channel":
+        return fields.channel_field(nx, ny, nz, recipe.seed, nz_total=recipe.dims[2], origin=origin,
+                                    octaves=recipe.octaves, base_period=recipe.base_period)
     raise ValueError(f"no CPU generator for kind {recipe.kind!r}")
 
 

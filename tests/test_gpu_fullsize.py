@@ -1,0 +1,133 @@
+"""GPU parity at full size, on sampled blocks the oracle computes one by one.
+
+The benchmark's 512^3 noise volume (all five isovalues, default launch
+plan, CUDA graph, cold cache then warm) and the 2048 x 2048 x 1024
+channel volume (isovalue at the 70th percentile of the decoded data) are
+extracted whole on the GPU.  For a sample of blocks (candidates, occupied
+blocks, blocks on the volume's far faces, and blocks the triangle stage
+skips), the oracle runs plain marching cubes over the block's decoded
+5x5x5 window (the block and its +x/+y/+z neighbours, clipped at the
+volume's edge, decoded by the oracle's own decoder from the same
+bitstream).  The block's triangles in the GPU mesh must match exactly in
+number, order and block id, and in position within 1e-5 voxel; a block
+the GPU skips must have no triangles.
+"""
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+POS_TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+    import synth.gpu as sg
+    sg.build()
+
+
+def block_window(bits_dev, dims, rate, b):
+    """The oracle's decoded samples of block b's 5x5x5 window (clipped)."""
+    import torch
+    nbx, nby, nbz = oracle.block_dims(dims)
+    bx, by, bz = b % nbx, (b // nbx) % nby, b // (nbx * nby)
+    ids, where = [], []
+    for dz in (0, 1):
+        for dy in (0, 1):
+            for dx in (0, 1):
+                x, y, z = bx + dx, by + dy, bz + dz
+                if x < nbx and y < nby and z < nbz:
+                    ids.append(x + nbx * (y + nby * z))
+                    where.append((dx, dy, dz))
+    sub = bits_dev[torch.tensor(ids, dtype=torch.int64, device=bits_dev.device)].cpu().numpy().view(np.uint64)
+    dec = oracle.decode_blocks(sub, rate, np.arange(len(ids), dtype=np.uint32)).reshape(-1, 4, 4, 4)
+    big = np.zeros((8, 8, 8), np.float32)
+    for (dx, dy, dz), blk in zip(where, dec):
+        big[4 * dz:4 * dz + 4, 4 * dy:4 * dy + 4, 4 * dx:4 * dx + 4] = blk
+    ex = min(5, dims[0] - 4 * bx)
+    ey = min(5, dims[1] - 4 * by)
+    ez = min(5, dims[2] - 4 * bz)
+    return big[:ez, :ey, :ex]
+
+
+def check_sampled(vol, mesh, bits_dev, dims, rate, iso, rng, n_each=120):
+    cand = vol.debug("candidates")
+    offs = vol.debug("block_offsets")
+    cnt = vol.debug("block_tris")
+    assert len(cand) == mesh.stats["n_candidates"]
+    assert int(cnt.sum()) == mesh.num_triangles
+    assert np.array_equal(offs, np.concatenate([[0], np.cumsum(cnt[:-1], dtype=np.uint64)]).astype(np.uint64))
+    nbx, nby, nbz = oracle.block_dims(dims)
+    nb = nbx * nby * nbz
+    occupied = np.nonzero(cnt)[0]
+    picks = set()
+    if len(cand):
+        picks |= {int(cand[i]) for i in rng.integers(0, len(cand), n_each)}
+    if len(occupied):
+        picks |= {int(cand[i]) for i in rng.choice(occupied, min(n_each, len(occupied)), replace=False)}
+    picks |= {int(b) for b in rng.integers(0, nb, n_each)}
+    # blocks on the far faces (ragged or clipped windows) and the last block
+    picks |= {int(nbx - 1 + nbx * (int(y) + nby * int(z))) for y, z in
+              zip(rng.integers(0, nby, 20), rng.integers(0, nbz, 20))}
+    picks.add(nb - 1)
+    verts = mesh.vertices
+    for b in sorted(picks):
+        w = block_window(bits_dev, dims, rate, b)
+        _, pos = oracle.mc_full(w, iso)
+        i = np.searchsorted(cand, b)
+        if i < len(cand) and cand[i] == b:
+            got = verts[3 * int(offs[i]):3 * int(offs[i] + cnt[i])].cpu().numpy().reshape(-1, 3, 4)
+        else:
+            got = np.zeros((0, 3, 4), np.float32)
+        assert len(got) == len(pos), (b, len(got), len(pos))
+        if len(got):
+            assert np.abs(got[:, :, :3].astype(np.float64) - pos).max() < POS_TOL, b
+            assert (got[:, :, 3].view(np.uint32) == b).all()
+    return len(picks)
+
+
+def test_noise512_benchmark_volume_sampled():
+    import torch
+    import paper_2009_03254_gb300 as bc
+    import synth.gpu as sg
+    from synth import recipes
+    rec = recipes.NOISE512
+    f = sg.gradient_noise(*rec.dims, rec.seed)
+    bits, bmin, bmax = bc.encode_field(f, rec.rate)
+    torch.cuda.synchronize()
+    del f
+    vol = bc.Volume(bits, rec.dims, rec.rate, bmin, bmax)
+    rng = np.random.default_rng(17)
+    try:
+        for sweep in range(2):                      # cold cache, then warm (the benchmark's sequence)
+            for iso in rec.isovalues:
+                m = vol.extract(iso)
+                assert m.num_triangles > 1_000_000
+                check_sampled(vol, m, bits, rec.dims, rec.rate, iso, rng, n_each=60)
+                m.release()
+    finally:
+        vol.release()
+
+
+def test_channel2k_sampled():
+    import torch
+    import paper_2009_03254_gb300 as bc
+    from synth import recipes, volumes
+    rec = recipes.CHANNEL2K
+    bits, bmin, bmax = volumes.encode_recipe(rec)
+    iso = volumes.percentile_isovalue(bits, rec.dims, rec.rate, rec.percentile, seed=3)
+    vol = bc.Volume(bits, rec.dims, rec.rate, bmin, bmax)
+    del bmin, bmax
+    torch.cuda.empty_cache()
+    try:
+        m = vol.extract(iso)
+        assert m.num_triangles > 100_000_000
+        n = check_sampled(vol, m, bits, rec.dims, rec.rate, iso, np.random.default_rng(23), n_each=150)
+        assert n > 300
+        m.release()
+    finally:
+        vol.release()

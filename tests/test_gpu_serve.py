@@ -1,5 +1,6 @@
 """GPU parity of the serving path: requests answered in ticks on one
-resident volume must give meshes identical, byte for byte, to extracting
+resident volume (one shared cull and cache update per tick, then one
+request per step) must give meshes identical, byte for byte, to extracting
 each isovalue alone; admission splits ticks whose union of active blocks
 exceeds the cache budget, defers meshes past the vertex budget, and a
 single request over budget fails alone."""
@@ -53,11 +54,11 @@ def test_served_meshes_equal_alone():
     srv = p.Server(vol, max_batch=4)
     try:
         tickets = [srv.submit(float(x)) for x in isos]
-        ticks = 0
+        steps = 0
         while srv.queued():
-            srv.step()
-            ticks += 1
-        assert ticks == 3
+            assert srv.step() == 1                            # one request finishes per step
+            steps += 1
+        assert steps == len(isos)
         for t, x in zip(tickets, isos):
             status, m = srv.take(t)
             assert status == p.ISO_OK
