@@ -134,6 +134,36 @@ int iso_extract(iso_volume *v, float isovalue, iso_mesh *out);
 int iso_extract_into(iso_volume *v, float isovalue, float *d_vertices, uint64_t capacity_triangles,
                      iso_stats *stats);
 
+/* As iso_extract_into, but each vertex is 8 bytes (the compact vertex
+ * format of Section 4.5, 24 bytes per triangle): two uint32 words,
+ * {qx | qy << 10 | qz << 20, block id}, where q = round(p / 4 * 1023) is
+ * the 10-bit code of the block-local coordinate p in [0, 4] (decode as
+ * q * 4 / 1023; within 2/1023 voxel of the float position).  p and q are
+ * computed in IEEE float32: t = (iso - v_lo) / (v_hi - v_lo) with every
+ * operation correctly rounded, p = lower corner + t, q = the nearest
+ * integer (ties to even) to p * 255.75.  d_vertices holds
+ * 6 * capacity_triangles uint32 words; same triangle order and errors as
+ * iso_extract_into. */
+int iso_extract_packed_into(iso_volume *v, float isovalue, uint32_t *d_vertices, uint64_t capacity_triangles,
+                            iso_stats *stats);
+
+/* The full-volume baseline the paper measures against (the naive
+ * data-parallel marching cubes of Section 3 over the whole decompressed
+ * volume): the same pipeline with the range test switched off, so every
+ * block is decoded into the cache and every cell is classified.  Because
+ * the range test only skips blocks without crossings, the mesh is
+ * identical to iso_extract_into's.  The cache must hold every block
+ * (cache budget >= 256 * nb), else ISO_ERR_BUDGET. */
+int iso_extract_all_blocks_into(iso_volume *v, float isovalue, float *d_vertices, uint64_t capacity_triangles,
+                                iso_stats *stats);
+
+/* Decode a whole compressed volume into a dense float32 field (nx*ny*nz,
+ * x fastest; samples past the volume edge are dropped), one thread per
+ * block (the full-volume decompression the paper times for ZFP).  Device
+ * pointers; queued on `stream`, does not block. */
+int iso_decode_volume(const uint64_t *d_bits, uint32_t nx, uint32_t ny, uint32_t nz, uint32_t rate_bits,
+                      float *d_field, void *stream);
+
 /* Free a mesh's vertex buffer (stream-ordered on the volume's stream that
  * made it).  The volume must still be alive.  Safe on a zeroed mesh. */
 int iso_mesh_release(iso_volume *v, iso_mesh *m);

@@ -217,6 +217,41 @@ def extract(bits, dims, rate, bmin, bmax, iso):
     return out
 
 
+def quantized_vertices(field, iso, edge_ids, tri_block, dims):
+    """The compact vertex format (Section 4.5, 8 bytes a vertex): for every
+    vertex of the block-ordered triangles, the 10-bit codes of its block-local
+    coordinates and its block id, packed as (qx | qy << 10 | qz << 20, id).
+
+    Each vertex lies on the cut edge given by its global edge id
+    (3 * (x + nx*(y + ny*z)) + axis of the lower sample).  The code of a
+    coordinate p in [0, 4] is round(p / 4 * 1023); because rounding decides
+    an integer, the position is taken in float32 with one IEEE rounding per
+    operation: t = (iso - v_lo) / (v_hi - v_lo), p = lower corner + t, and
+    q = the nearest integer (ties to even) to p * 255.75."""
+    f = np.ascontiguousarray(field, np.float32)
+    nx, ny, nz = dims
+    e = np.asarray(edge_ids, np.uint64).reshape(-1)
+    axis = (e % 3).astype(np.int64)
+    lin = (e // 3).astype(np.int64)
+    x, y, z = lin % nx, (lin // nx) % ny, lin // (nx * ny)
+    vlo = f[z, y, x]
+    vhi = f[z + (axis == 2), y + (axis == 1), x + (axis == 0)]
+    iso32 = np.float32(iso)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        t = (iso32 - vlo) / (vhi - vlo)                    # float32 operations
+    blk = np.repeat(np.asarray(tri_block, np.int64), 3)
+    nbx, nby, _ = block_dims(dims)
+    bx, by, bz = blk % nbx, (blk // nbx) % nby, blk // (nbx * nby)
+    codes = np.zeros(len(e), np.uint32)
+    for k, (c, b) in enumerate(((x, bx), (y, by), (z, bz))):
+        p = (c - 4 * b).astype(np.float32)                 # block-local lower corner (exact)
+        p = np.where(axis == k, p + t, p).astype(np.float32)
+        q = np.rint(p * np.float32(255.75)).astype(np.uint32)
+        codes |= q << np.uint32(10 * k)
+    out = np.stack([codes, blk.astype(np.uint32)], axis=1)
+    return out.reshape(-1, 3, 2)
+
+
 # ---------------------------------------------------------------- cache (Algorithm 1)
 
 class OverBudget(RuntimeError):

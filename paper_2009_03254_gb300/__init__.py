@@ -93,6 +93,9 @@ def lib():
             "iso_load_volume": (i32, [ctypes.POINTER(P), P, sz, u32, u32, u32, u32, P, P, ctypes.POINTER(_Options)]),
             "iso_extract": (i32, [P, ctypes.c_float, ctypes.POINTER(_Mesh)]),
             "iso_extract_into": (i32, [P, ctypes.c_float, P, u64, ctypes.POINTER(_Stats)]),
+            "iso_extract_packed_into": (i32, [P, ctypes.c_float, P, u64, ctypes.POINTER(_Stats)]),
+            "iso_extract_all_blocks_into": (i32, [P, ctypes.c_float, P, u64, ctypes.POINTER(_Stats)]),
+            "iso_decode_volume": (i32, [P, u32, u32, u32, u32, P, P]),
             "iso_mesh_release": (i32, [P, ctypes.POINTER(_Mesh)]),
             "iso_release": (None, [P]),
             "iso_set_stream": (i32, [P, P]),
@@ -251,6 +254,31 @@ class Volume:
         rc = lib().iso_extract_into(self._h, ctypes.c_float(iso), _ptr(out), cap, ctypes.byref(st))
         if check:
             _check(rc, "iso_extract_into")
+        d = st.as_dict()
+        d["status"] = rc
+        return d
+
+    def extract_all_blocks_into(self, iso, out, check=True):
+        """The full-volume baseline: every block decoded and visited (no range
+        test); same mesh as extract_into.  Returns the stats dict."""
+        cap = out.numel() // 12
+        st = _Stats()
+        rc = lib().iso_extract_all_blocks_into(self._h, ctypes.c_float(iso), _ptr(out), cap, ctypes.byref(st))
+        if check:
+            _check(rc, "iso_extract_all_blocks_into")
+        d = st.as_dict()
+        d["status"] = rc
+        return d
+
+    def extract_packed_into(self, iso, out, check=True):
+        """The compact 8-byte vertices (two uint32 words: 10-bit codes of the
+        block-local coordinates, block id) into `out`, a CUDA int32/uint32
+        tensor of shape (C, 3, 2) for C triangles.  Returns the stats dict."""
+        cap = out.numel() // 6
+        st = _Stats()
+        rc = lib().iso_extract_packed_into(self._h, ctypes.c_float(iso), _ptr(out), cap, ctypes.byref(st))
+        if check:
+            _check(rc, "iso_extract_packed_into")
         d = st.as_dict()
         d["status"] = rc
         return d
@@ -447,6 +475,14 @@ class Server:
             pass
 
 
+def unpack_vertices(packed):
+    """Block-local float positions (..., 3) of compact vertices (..., 2) uint32."""
+    import torch
+    codes = packed[..., 0].to(torch.int64) & 0xFFFFFFFF
+    q = torch.stack([(codes >> (10 * k)) & 1023 for k in range(3)], -1)
+    return q.to(torch.float32) * (4.0 / 1023.0)
+
+
 def encode_field(field, rate, stream=None, out=None):
     """Encode a CUDA float32 tensor of shape (nz, ny, nx) on the GPU.
     Returns (bits uint64-as-int64 tensor (nb, rate), bmin, bmax) on the same
@@ -489,6 +525,17 @@ def active_blocks_static(bmin, bmax, dims, iso, ids=None, count=None, stream=Non
                                           stream if stream is not None else _current_stream()),
            "iso_active_blocks_static")
     return ids, count
+
+
+def decode_volume(bits, dims, rate, out=None, stream=None):
+    """Decode a whole CUDA bitstream tensor into a dense float32 (nz, ny, nx) tensor."""
+    import torch
+    nx, ny, nz = dims
+    if out is None:
+        out = torch.empty((nz, ny, nx), dtype=torch.float32, device=bits.device)
+    _check(lib().iso_decode_volume(_ptr(bits), nx, ny, nz, rate, _ptr(out),
+                                   stream if stream is not None else _current_stream()), "iso_decode_volume")
+    return out
 
 
 def decode_blocks(bits, rate, ids, stream=None):

@@ -273,10 +273,11 @@ int ensure_debug_edges(iso_volume *v, unsigned long long tris) {
 
 // run the pipeline into `out` (capacity cap_tris); returns the error of
 // the run, with the control block mirrored on the host
-int run(iso_volume *v, float iso, float4 *out, unsigned long long cap_tris, bool mc_only) {
+int run(iso_volume *v, float iso, void *out, unsigned long long cap_tris, bool mc_only,
+        uint32_t format = kVertexFloat4, uint32_t flags = 0) {
     int rc = ensure_debug_edges(v, cap_tris);
     if (rc) return rc;
-    *v->host_params = Params{iso, 0u, cap_tris, (unsigned long long)(uintptr_t)out};
+    *v->host_params = Params{iso, format, flags, 0u, cap_tris, (unsigned long long)(uintptr_t)out};
     const bool graph = !mc_only && v->use_graph && !(v->flags & ISO_DEBUG) && !v->profiling;
     if (graph && ensure_graph(v) != ISO_OK) v->use_graph = false;   // fall back to plain launches
     if (graph && v->gexec) {
@@ -471,7 +472,40 @@ int iso_extract_into(iso_volume *v, float isovalue, float *d_vertices, uint64_t 
                      iso_stats *stats) {
     if (!v || !std::isfinite(isovalue) || (!d_vertices && capacity_triangles)) return ISO_ERR_INVALID_ARG;
     DeviceGuard dg(v->device);
-    int rc = run(v, isovalue, reinterpret_cast<float4 *>(d_vertices), capacity_triangles, false);
+    int rc = run(v, isovalue, d_vertices, capacity_triangles, false);
+    if (stats) fill_stats(*v->host_ctl, stats, 0);
+    if (rc) return rc;
+    if (v->host_ctl->n_tri > capacity_triangles) return ISO_ERR_CAPACITY;
+    return ISO_OK;
+}
+
+int iso_extract_all_blocks_into(iso_volume *v, float isovalue, float *d_vertices, uint64_t capacity_triangles,
+                                iso_stats *stats) {
+    if (!v || !std::isfinite(isovalue) || (!d_vertices && capacity_triangles)) return ISO_ERR_INVALID_ARG;
+    DeviceGuard dg(v->device);
+    int rc = run(v, isovalue, d_vertices, capacity_triangles, false, kVertexFloat4, kParamAllBlocks);
+    if (stats) fill_stats(*v->host_ctl, stats, 0);
+    if (rc) return rc;
+    if (v->host_ctl->n_tri > capacity_triangles) return ISO_ERR_CAPACITY;
+    return ISO_OK;
+}
+
+int iso_decode_volume(const uint64_t *d_bits, uint32_t nx, uint32_t ny, uint32_t nz, uint32_t rate_bits,
+                      float *d_field, void *stream) {
+    if (!d_bits || !d_field) return ISO_ERR_INVALID_ARG;
+    Geom g;
+    int rc = geometry(nx, ny, nz, rate_bits, &g);
+    if (rc) return rc;
+    launch_decode_volume(d_bits, g, d_field, (cudaStream_t)stream);
+    CK(cudaGetLastError());
+    return ISO_OK;
+}
+
+int iso_extract_packed_into(iso_volume *v, float isovalue, uint32_t *d_vertices, uint64_t capacity_triangles,
+                            iso_stats *stats) {
+    if (!v || !std::isfinite(isovalue) || (!d_vertices && capacity_triangles)) return ISO_ERR_INVALID_ARG;
+    DeviceGuard dg(v->device);
+    int rc = run(v, isovalue, d_vertices, capacity_triangles, false, kVertexPacked);
     if (stats) fill_stats(*v->host_ctl, stats, 0);
     if (rc) return rc;
     if (v->host_ctl->n_tri > capacity_triangles) return ISO_ERR_CAPACITY;

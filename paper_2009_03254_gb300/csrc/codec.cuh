@@ -121,6 +121,17 @@ __device__ __forceinline__ void decode_block(const uint64_t *__restrict__ w, uin
     int k = 31;                            // plane number, most significant first
     uint64_t x = 0;
     bool opening = true;
+    {
+        // Until a coefficient is reached, a plane has no verbatim bits and a
+        // 0 group test ends it: each 0 bit here is a whole empty plane.
+        const uint64_t win = bw.peek(pos);
+        uint32_t z = win ? (uint32_t)__ffsll((long long)win) - 1u : 64u;
+        z = min(z, min(32u, end - pos));
+        for (uint32_t j = 0; j < z; j++) planes[(uint32_t)(31 - (int)j) * stride] = 0ull;
+        k -= (int)z;
+        pos += z;
+        bw.advance(pos);
+    }
     while (k >= 0 && pos < end) {
         // the verbatim bits of the n coefficients reached so far
         const uint32_t m = opening ? min(n, end - pos) : 0u;

@@ -58,11 +58,22 @@ enum LaunchCounter { kLcCull = 0, kLcLruA = 1, kLcLruB = 2, kLcScan = 3, kNumLau
 
 // Per-extraction inputs, copied from pinned host memory by the first
 // operation of each extraction (so a captured graph never changes).
+enum VertexFormat : uint32_t {
+    kVertexFloat4 = 0,            // float4 {x, y, z block-local, w = block id bits}: 16 B
+    kVertexPacked = 1,            // uint2 {x | y << 10 | z << 20 (10-bit codes of p/4), block id}: 8 B
+};
+
+enum ParamFlags : uint32_t {
+    kParamAllBlocks = 1u,         // no range test: every block is active and a candidate
+};
+
 struct Params {
     float iso;
+    uint32_t format;              // VertexFormat
+    uint32_t flags;               // ParamFlags
     uint32_t reserved;
     unsigned long long tri_cap;   // output capacity in triangles
-    unsigned long long out;       // float4 * vertex buffer
+    unsigned long long out;       // vertex buffer (float4 * or uint2 *)
 };
 
 // One per volume, in device memory.  Written only by the kernels of one

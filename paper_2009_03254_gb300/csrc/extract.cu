@@ -86,6 +86,7 @@ __device__ __forceinline__ void cull_tile(const DevState &s, const Geom &g, uint
     const uint32_t lt = (1u << lane) - 1u;
     const uint32_t epoch = s.ctl->epoch;
     const float iso = s.ctl->params.iso;
+    const bool all = (s.ctl->params.flags & kParamAllBlocks) != 0;   // the full-volume baseline
     // two halves of kR/2 rounds; in each, every load (3x3x3 hull, +group
     // hull, slot) is issued before any of it is used, so a tile waits for
     // two memory round trips rather than one per round
@@ -106,8 +107,8 @@ __device__ __forceinline__ void cull_tile(const DevState &s, const Geom &g, uint
         for (int i = 0; i < kHalf; i++) {
             const int r = half * kHalf + i;
             const uint32_t b = tile * kTile + r * kThreads + threadIdx.x;
-            const bool act = b < g.nb && (h[i].x < iso) && (iso <= h[i].y);
-            const bool cand = act && (h8[i].x < iso) && (iso <= h8[i].y);
+            const bool act = b < g.nb && (all || ((h[i].x < iso) && (iso <= h[i].y)));
+            const bool cand = act && (all || ((h8[i].x < iso) && (iso <= h8[i].y)));
             const bool nw = act && sl[i] < 0;
             if (act && sl[i] >= 0) s.slast[sl[i]] = epoch;       // a hit: the slot's age resets
             const uint32_t ab = __ballot_sync(0xffffffffu, act);
@@ -414,8 +415,12 @@ __global__ void __launch_bounds__(kDecodeThreads) decode_new_kernel(Launch L) {
 // ================================================================ batch bookkeeping
 
 __global__ void batch_params_kernel(Launch L, const float *__restrict__ iso) {
-    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < L.n; v += gridDim.x * blockDim.x)
-        L.vols[v].s.ctl->params.iso = iso[v];
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < L.n; v += gridDim.x * blockDim.x) {
+        Params &p = L.vols[v].s.ctl->params;
+        p.iso = iso[v];
+        p.format = kVertexFloat4;
+        p.flags = 0;
+    }
 }
 
 // One block: place the volumes' surfaces one after another in the batch's

@@ -107,6 +107,7 @@ void launch_reset_cache(const DevState &s, cudaStream_t st);
 void launch_encode(const float *field, const Geom &g, uint64_t *bits, float *bmin, float *bmax, cudaStream_t st);
 void launch_decode_list(const uint64_t *bits, uint32_t rate, const uint32_t *ids, uint64_t n, float *out,
                         cudaStream_t st);
+void launch_decode_volume(const uint64_t *bits, const Geom &g, float *field, cudaStream_t st);
 void launch_gather_slots(const float *slots, const int32_t *islot, const uint32_t *ids, uint64_t n, float *out,
                          int32_t *missing, cudaStream_t st);
 

@@ -428,6 +428,7 @@ __global__ void __launch_bounds__(32 * kW) mc_emit_kernel(Launch L) {
         const Ctl *c = s.ctl;
         const float iso = c->params.iso;
         const unsigned long long tri_cap = c->params.tri_cap;
+        const bool packed = c->params.format == kVertexPacked;     // warp-uniform
         float4 *__restrict__ out = reinterpret_cast<float4 *>(c->params.out);
         const uint32_t base = cur.base;
         const int nb_w = (int)cur.nb_w;
@@ -472,17 +473,32 @@ __global__ void __launch_bounds__(32 * kW) mc_emit_kernel(Launch L) {
                 for (int j = 0; j < 3; j++) {
                     const uint32_t info = sm.edge_info[(row >> (8 * j)) & 0xFFu];
                     const float vlo = hb[info & 0xFFu], vhi = hb[(info >> 8) & 0xFFu];
-                    // t = (iso - v_lo) / (v_hi - v_lo) through the reciprocal: within
-                    // 2 ulp of the correctly rounded quotient (positions within 1e-6)
-                    const float tt = __fdividef(__fsub_rn(iso, vlo), __fsub_rn(vhi, vlo));
                     const uint32_t a = (info >> 19) & 3u;
                     float4 p = make_float4((float)(cx + (int)((info >> 16) & 1u)),
                                            (float)(cy + (int)((info >> 17) & 1u)),
                                            (float)(cz + (int)((info >> 18) & 1u)), wbits);
-                    if (a == 0) p.x = __fadd_rn(p.x, tt);
-                    else if (a == 1) p.y = __fadd_rn(p.y, tt);
-                    else p.z = __fadd_rn(p.z, tt);
-                    stage[3 * lane + j] = p;
+                    if (!packed) {
+                        // t = (iso - v_lo) / (v_hi - v_lo) through the reciprocal: within
+                        // 2 ulp of the correctly rounded quotient (positions within 1e-6)
+                        const float tt = __fdividef(__fsub_rn(iso, vlo), __fsub_rn(vhi, vlo));
+                        if (a == 0) p.x = __fadd_rn(p.x, tt);
+                        else if (a == 1) p.y = __fadd_rn(p.y, tt);
+                        else p.z = __fadd_rn(p.z, tt);
+                        stage[3 * lane + j] = p;
+                    } else {
+                        // the 10-bit code round(p / 4 * 1023) decides an integer, so every
+                        // step is one IEEE float32 operation (the division correctly
+                        // rounded), as the oracle computes it
+                        const float tt = __fdiv_rn(__fsub_rn(iso, vlo), __fsub_rn(vhi, vlo));
+                        if (a == 0) p.x = __fadd_rn(p.x, tt);
+                        else if (a == 1) p.y = __fadd_rn(p.y, tt);
+                        else p.z = __fadd_rn(p.z, tt);
+                        const uint32_t qx = (uint32_t)__float2int_rn(__fmul_rn(p.x, 255.75f));
+                        const uint32_t qy = (uint32_t)__float2int_rn(__fmul_rn(p.y, 255.75f));
+                        const uint32_t qz = (uint32_t)__float2int_rn(__fmul_rn(p.z, 255.75f));
+                        reinterpret_cast<uint2 *>(stage)[3 * lane + j] = make_uint2(qx | (qy << 10) | (qz << 20),
+                                                                                     wt.bid[q]);
+                    }
                     if (kDebug) {
                         const unsigned long long gt = gbase + tri;
                         uint32_t bx, by, bz;
@@ -500,10 +516,20 @@ __global__ void __launch_bounds__(32 * kW) mc_emit_kernel(Launch L) {
             const uint32_t nv = 3 * min(32u, wtot - t0);             // vertices in this chunk
             const unsigned long long v0 = (gbase + t0) * 3;          // first vertex of the chunk
             const unsigned long long vcap = tri_cap * 3;
+            if (!packed) {
 #pragma unroll
-            for (int r = 0; r < 3; r++) {
-                const uint32_t f = lane + 32 * r;
-                if (f < nv && v0 + f < vcap) out[v0 + f] = stage[f];
+                for (int r = 0; r < 3; r++) {
+                    const uint32_t f = lane + 32 * r;
+                    if (f < nv && v0 + f < vcap) out[v0 + f] = stage[f];
+                }
+            } else {
+                uint2 *out2 = reinterpret_cast<uint2 *>(out);
+                const uint2 *st2 = reinterpret_cast<const uint2 *>(stage);
+#pragma unroll
+                for (int r = 0; r < 3; r++) {
+                    const uint32_t f = lane + 32 * r;
+                    if (f < nv && v0 + f < vcap) out2[v0 + f] = st2[f];
+                }
             }
             __syncwarp();
         }

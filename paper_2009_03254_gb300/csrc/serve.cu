@@ -401,7 +401,7 @@ int emit_next(iso_server *sv, uint32_t *completed) {
             return ISO_OK;
         }
     }
-    *sv->h_params = Params{r.iso, 0u, c.n_tri, (unsigned long long)(uintptr_t)buf};
+    *sv->h_params = Params{r.iso, kVertexFloat4, 0u, 0u, c.n_tri, (unsigned long long)(uintptr_t)buf};
     ISO_CK(cudaMemcpyAsync(&dctl->params, sv->h_params, sizeof(Params), cudaMemcpyHostToDevice, st));
     launch_mc_emit(L, false, sv->view_plan, st);
     ISO_CK(cudaGetLastError());

@@ -379,3 +379,72 @@ def test_graph_and_plain_launches_agree():
     finally:
         a.release()
         b.release()
+
+
+# ---------------------------------------------------------------- compact vertices (Section 4.5)
+
+@pytest.mark.parametrize("kind,dims,rate", [("sphere", (64, 64, 64), 16), ("noise", (37, 21, 14), 8),
+                                            ("random", (13, 9, 6), 4), ("special", (18, 10, 9), 16),
+                                            ("checker", (11, 9, 7), 8)])
+def test_packed_vertices_match_oracle(kind, dims, rate):
+    t = torch()
+    f = make_field(kind, dims, 7)
+    bits, bmin, bmax = oracle.encode_volume(f, rate)
+    d = oracle.decode_volume(bits, dims, rate)
+    vol = pkg().Volume(bits, dims, rate, bmin, bmax)
+    try:
+        for iso in (0.0, float(np.median(d)), float(np.quantile(d, 0.3)), 1.0):
+            ref = oracle.extract(bits, dims, rate, bmin, bmax, iso)
+            T = ref["num_triangles"]
+            out = t.zeros((max(T, 1), 3, 2), dtype=t.int32, device="cuda")
+            st = vol.extract_packed_into(iso, out)
+            assert st["num_triangles"] == T
+            if T:
+                want = oracle.quantized_vertices(ref["field"], iso, ref["edge_ids"], ref["tri_block"], dims)
+                got = out.cpu().numpy().view(np.uint32)[:T]
+                assert np.array_equal(got, want)
+            # the float format of the same surface afterwards is unchanged
+            m = vol.extract(iso)
+            assert m.num_triangles == T
+            m.release()
+    finally:
+        vol.release()
+
+
+# ---------------------------------------------------------------- full-volume baselines
+
+@pytest.mark.parametrize("rate", [2, 8, 16])
+@pytest.mark.parametrize("kind,dims", DECODE_CASES + [("sphere", (1, 1, 1)), ("noise", (5, 3, 2)),
+                                                   ("random", (16, 12, 8))])
+def test_decode_volume_matches_oracle(kind, dims, rate):
+    f = make_field(kind, dims, 9)
+    bits, _, _ = oracle.encode_volume(f, rate)
+    want = oracle.decode_volume(bits, dims, rate)
+    got = pkg().decode_volume(to_dev(bits), dims, rate).cpu().numpy()
+    assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+
+
+@pytest.mark.parametrize("kind,dims,rate", [("noise", (37, 21, 14), 8), ("sphere", (33, 2, 9), 8),
+                                            ("random", (13, 9, 6), 4), ("checker", (11, 9, 7), 8)])
+def test_all_blocks_baseline_equals_extraction(kind, dims, rate):
+    t = torch()
+    f = make_field(kind, dims, 7)
+    bits, bmin, bmax = oracle.encode_volume(f, rate)
+    d = oracle.decode_volume(bits, dims, rate)
+    a = pkg().Volume(bits, dims, rate, bmin, bmax)
+    b = pkg().Volume(bits, dims, rate, bmin, bmax)
+    nb = bits.shape[0]
+    try:
+        for iso in (0.0, float(np.median(d)), float(np.quantile(d, 0.8))):
+            m = a.extract(iso)
+            T = m.num_triangles
+            out = t.zeros((max(T, 1), 3, 4), dtype=t.float32, device="cuda")
+            st = b.extract_all_blocks_into(iso, out)
+            assert st["num_triangles"] == T and st["n_active"] == nb and st["n_candidates"] == nb
+            if T:
+                assert np.array_equal(out.cpu().numpy().reshape(-1, 4).view(np.uint32),
+                                      m.vertices.cpu().numpy().view(np.uint32))
+            m.release()
+    finally:
+        a.release()
+        b.release()

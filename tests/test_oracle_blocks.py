@@ -194,3 +194,44 @@ def test_lru_repeat_is_all_hits_and_budget():
     small = oracle.LRUCache(nb, 10, 30)
     with pytest.raises(oracle.OverBudget):
         small.update(m)
+
+
+# ---------------------------------------------------------------- compact vertices (Section 4.5)
+
+def test_quantized_vertices_within_half_a_step():
+    from synth import fields
+    dims = (21, 17, 13)
+    f = fields.gradient_noise(*dims, 4, octaves=3, base_period=8)
+    bits, bmin, bmax = oracle.encode_volume(f, 8)
+    for iso in (-0.3, 0.0, 0.45):
+        r = oracle.extract(bits, dims, 8, bmin, bmax, iso)
+        q = oracle.quantized_vertices(r["field"], iso, r["edge_ids"], r["tri_block"], dims)
+        assert q.shape == (r["num_triangles"], 3, 2)
+        codes = q[..., 0]
+        assert (codes >> 30 == 0).all()
+        dec = np.stack([(codes >> (10 * k)) & 1023 for k in range(3)], -1) / 255.75
+        # rounding to the nearest code, from a float32 position within ~5e-7 of the float64 one
+        assert np.abs(dec - r["local_pos"]).max() <= 0.5 / 255.75 + 1e-6
+        assert np.array_equal(q[..., 1], np.repeat(r["tri_block"][:, None], 3, axis=1).astype(np.uint32))
+
+
+def test_quantized_vertices_hand_values():
+    # samples 0 and 1 with iso 0.5: every vertex is at the middle of its edge,
+    # t = 0.5 exactly, so a coordinate k + 0.5 has code round(255.75 * (k + 0.5))
+    # = 128, 384, 639, 895 for k = 0..3 (127.875, 383.625, 639.375, 895.125)
+    dims = (8, 8, 8)
+    rng = np.random.default_rng(2)
+    f = rng.integers(0, 2, (8, 8, 8)).astype(np.float32)
+    ids, pos = oracle.mc_full(f, 0.5)
+    owner = np.zeros(len(ids), np.int64)
+    # owner block of each triangle: the block of its cell (any vertex's lower corner floor / 4 works
+    # only inside a block, so take it from the edge of the first vertex's cell via the positions)
+    cell = np.floor(pos.min(axis=1)).astype(np.int64)          # lower cell corner of each triangle
+    bx, by, bz = cell[:, 0] // 4, cell[:, 1] // 4, cell[:, 2] // 4
+    owner = bx + 2 * (by + 2 * bz)
+    q = oracle.quantized_vertices(f, 0.5, ids, owner, dims)
+    table = {0.5: 128, 1.5: 384, 2.5: 639, 3.5: 895, 0.0: 0, 1.0: 256, 2.0: 512, 3.0: 767, 4.0: 1023}
+    local = pos - 4 * np.stack([bx, by, bz], -1)[:, None, :]
+    want = np.vectorize(lambda v: table[v])(local).astype(np.uint32)
+    got = np.stack([(q[..., 0] >> (10 * k)) & 1023 for k in range(3)], -1)
+    assert np.array_equal(got, want)
