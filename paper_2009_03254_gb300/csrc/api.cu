@@ -181,7 +181,7 @@ int free_volume(iso_volume *v) {
     DevState &s = v->s;
     void *ptrs[] = {v->bits, v->bmin, v->bmax, v->hull, v->hull8, v->tables, s.mactive, s.iactive, s.inew, s.icand,
                     s.islot, s.slast, s.sblock, s.lbuf[0], s.lbuf[1], s.newslot, s.slots, s.desc_cull, s.desc_cand,
-                    s.desc_lru_a, s.desc_lru_b, s.desc_mc, s.ctl, s.counts, s.offsets, s.dbg_cases, s.dbg_edges};
+                    s.desc_lru_a, s.desc_lru_b, s.desc_mc, s.ctl, s.counts, s.offsets, s.cases, s.dbg_edges};
     for (void *p : ptrs) dfree_on(p, v->stream);
     cudaStreamSynchronize(v->stream);
     (void)cudaGetLastError();
@@ -402,7 +402,10 @@ int iso_load_volume(iso_volume **out, const void *compressed, size_t compressed_
     TRY(dalloc(v, &s.ctl, 1));
     TRY(dalloc(v, &s.counts, v->cap));
     TRY(dalloc(v, &s.offsets, v->cap));
-    if (v->flags & ISO_DEBUG) TRY(dalloc(v, &s.dbg_cases, (size_t)g.nb * 64));
+    // the count pass keeps each candidate's cases for the emit pass when they
+    // take at most 8 GB (else emit classifies again); debug volumes always
+    if ((v->flags & ISO_DEBUG) || (uint64_t)s.list_cap * 64 <= (8ull << 30))
+        TRY(dalloc(v, &s.cases, (size_t)s.list_cap * 64));
     if (cudaMallocHost((void **)&v->host_ctl, sizeof(Ctl)) != cudaSuccess ||
         cudaMallocHost((void **)&v->host_params, sizeof(Params)) != cudaSuccess) {
         (void)cudaGetLastError();
@@ -636,7 +639,9 @@ int iso_debug_get(iso_volume *v, int which, void *host_dst, size_t bytes, uint64
         case ISO_DBG_BLOCK_OF_SLOT: src = v->s.sblock; n = v->last_slots; elem = 4; break;
         case ISO_DBG_SLOT_LAST_USE: src = v->s.slast; n = v->last_slots; elem = 4; break;
         case ISO_DBG_ACTIVE_MASK: src = v->s.mactive; n = (v->g.nb + 31) / 32; elem = 4; break;
-        case ISO_DBG_CELL_CASES: if (!dbg) return ISO_ERR_INVALID_ARG; src = v->s.dbg_cases; n = 64ull * v->last_n_cand; elem = 1; break;
+        case ISO_DBG_CELL_CASES:
+            if (!dbg || !v->s.cases) return ISO_ERR_INVALID_ARG;
+            src = v->s.cases; n = 64ull * std::min<uint64_t>(v->last_n_cand, v->s.list_cap); elem = 1; break;
         case ISO_DBG_BLOCK_TRIS: src = v->s.counts; n = v->last_n_cand; elem = 4; break;
         case ISO_DBG_BLOCK_OFFSETS: src = v->s.offsets; n = v->last_n_cand; elem = 8; break;
         case ISO_DBG_CANDIDATES: src = v->s.icand; n = std::min<uint64_t>(v->last_n_cand, v->s.list_cap); elem = 4; break;

@@ -31,8 +31,9 @@ struct DevState {
     const uint8_t *tables;     // num_tri[256] then tri_edges[256][16]
     uint32_t *counts;          // triangles of each candidate
     unsigned long long *offsets; // exclusive prefix of counts: first triangle of each candidate
-    // debug copies (null unless the volume was loaded with ISO_DEBUG)
-    uint8_t *dbg_cases;        // 64 per candidate block
+    uint8_t *cases;            // 64 cell cases per candidate, written by the count pass and read by
+                               // emit instead of classifying again (null: emit classifies)
+    // debug copy (null unless the volume was loaded with ISO_DEBUG)
     unsigned long long *dbg_edges;
 };
 

@@ -125,6 +125,14 @@ struct LaneConst {
     }
 };
 
+// 16-byte global -> shared copy that completes asynchronously (L2 only)
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // the 8-bit case of a cell from the 32 mask bits starting at its lower corner
 // (corner c at bit (c&1) + 5((c>>1)&1) + 25(c>>2))
 __device__ __forceinline__ uint32_t case_bits(uint32_t W) {
@@ -132,17 +140,24 @@ __device__ __forceinline__ uint32_t case_bits(uint32_t W) {
 }
 
 // Phases A-C for the warp tile starting at candidate `base` (nb_w of
-// kBPW slots used).  Leaves cases in wt.cases when kKeepCases and returns
-// the per-cell triangle counts of the lane's two cells, packed one byte
-// per block: n0p for cell lane, n1p for cell lane + 32.
-// `b` is this lane's block (candidate base + lane/8), loaded by the caller
-// one warp tile ahead.
-template <bool kKeepCases, bool kDebug>
+// kBPW slots used).  Returns the per-cell triangle counts of the lane's two
+// cells, packed one byte per block: n0p for cell lane, n1p for cell
+// lane + 32.  The count pass (kEmit false) classifies and, when the volume
+// keeps them (s.cases), stores the cases; the emit pass leaves the cases in
+// wt.cases, reading the stored ones instead of classifying again when
+// there are any.  `b` is this lane's block (candidate base + lane/8),
+// loaded by the caller one warp tile ahead.
+template <bool kEmit>
 __device__ __forceinline__ void stage_and_classify(const DevState &s, const Geom &g, float iso, uint32_t base,
                                                    int nb_w, uint32_t b, WarpTile &wt, const LaneConst &lc,
                                                    const uint8_t *num_tri, uint32_t &n0p, uint32_t &n1p) {
     const int lane = threadIdx.x & 31, bq = lane >> 3, bo = lane & 7;
     const uint32_t slab = g.nbx * g.nby;
+    const bool stored = kEmit && s.cases != nullptr;      // uniform
+    // the stored cases of the tile's blocks, copied to shared memory while
+    // the samples are staged (16 lanes x 16 bytes; both ends 16-byte aligned)
+    if (stored && lane < 4 * nb_w)
+        cp_async16(&wt.cases[lane >> 2][16 * (lane & 3)], s.cases + (size_t)(base + (lane >> 2)) * 64 + 16 * (lane & 3));
     // ---- A: +group slots
     if (bq < nb_w) {
         uint32_t bx, by, bz;
@@ -189,38 +204,49 @@ __device__ __forceinline__ void stage_and_classify(const DevState &s, const Geom
             }
         }
     __syncwarp();
-    // ---- C: classify and count
+    // ---- C: classify (or take the stored cases) and count
     n0p = 0;
     n1p = 0;
 #pragma unroll
     for (int q = 0; q < kBPW; q++) {
         if (q >= nb_w) continue;          // warp-uniform
-        const float *hb = &wt.halo[q][0];
-        uint32_t m[4];
-#pragma unroll
-        for (int r = 0; r < 4; r++) m[r] = __ballot_sync(0xffffffffu, lc.cls[r] >= 0 && hb[lc.cls[r]] < iso);
-        const uint32_t lim = wt.lim[q];
         uint32_t cs[2];
+        if (stored) {
+            if (q == 0) {                 // the copies issued before staging
+                cp_async_wait_all();
+                __syncwarp();
+            }
+            cs[0] = wt.cases[q][lane];
+            cs[1] = wt.cases[q][lane + 32];
+        } else {
+            const float *hb = &wt.halo[q][0];
+            uint32_t m[4];
 #pragma unroll
-        for (int h = 0; h < 2; h++) {
-            const uint32_t lo = lc.up[h] ? m[h + 1] : m[h];
-            const uint32_t hi = lc.up[h] ? m[h + 2] : m[h + 1];
-            cs[h] = case_bits(__funnelshift_r(lo, hi, lc.cshift[h]));
-        }
-        if (lim != 0x444u) {              // warp-uniform: cells past the volume's last sample are empty
+            for (int r = 0; r < 4; r++) m[r] = __ballot_sync(0xffffffffu, lc.cls[r] >= 0 && hb[lc.cls[r]] < iso);
+            const uint32_t lim = wt.lim[q];
 #pragma unroll
             for (int h = 0; h < 2; h++) {
-                const uint32_t cell = (uint32_t)lane + 32u * h;
-                const bool valid = (cell & 3u) < (lim & 15u) && ((cell >> 2) & 3u) < ((lim >> 4) & 15u) &&
-                                   (cell >> 4) < (lim >> 8);
-                cs[h] = valid ? cs[h] : 0u;
+                const uint32_t lo = lc.up[h] ? m[h + 1] : m[h];
+                const uint32_t hi = lc.up[h] ? m[h + 2] : m[h + 1];
+                cs[h] = case_bits(__funnelshift_r(lo, hi, lc.cshift[h]));
+            }
+            if (lim != 0x444u) {          // warp-uniform: cells past the volume's last sample are empty
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    const uint32_t cell = (uint32_t)lane + 32u * h;
+                    const bool valid = (cell & 3u) < (lim & 15u) && ((cell >> 2) & 3u) < ((lim >> 4) & 15u) &&
+                                       (cell >> 4) < (lim >> 8);
+                    cs[h] = valid ? cs[h] : 0u;
+                }
+            }
+            if (!kEmit && s.cases) {      // uniform: keep them for the emit pass
+#pragma unroll
+                for (int h = 0; h < 2; h++) s.cases[(size_t)(base + q) * 64 + lane + 32 * h] = (uint8_t)cs[h];
             }
         }
 #pragma unroll
         for (int h = 0; h < 2; h++) {
-            const int cell = lane + 32 * h;
-            if (kKeepCases) wt.cases[q][cell] = (uint8_t)cs[h];
-            if (kDebug) s.dbg_cases[(size_t)(base + q) * 64 + cell] = (uint8_t)cs[h];
+            if (kEmit && !stored) wt.cases[q][lane + 32 * h] = (uint8_t)cs[h];
             const uint32_t n = num_tri[cs[h]];
             if (h == 0) n0p |= n << (8 * q);
             else n1p |= n << (8 * q);
@@ -264,7 +290,7 @@ __device__ __forceinline__ TileRef locate_tile(const Launch &L, const uint32_t *
 
 // ================================================================ count (Section 4.4)
 
-template <int kW, bool kDebug, bool kOne>
+template <int kW, bool kOne>
 __global__ void __launch_bounds__(32 * kW, 32 / kW) mc_count_kernel(Launch L) {   // 1024 threads per SM
     extern __shared__ __align__(16) unsigned char smem_raw[];
     CountSmem<kW> &sm = *reinterpret_cast<CountSmem<kW> *>(smem_raw);
@@ -294,8 +320,8 @@ __global__ void __launch_bounds__(32 * kW, 32 / kW) mc_count_kernel(Launch L) { 
         const DevState &s = vol_of<kOne>(L, cur.v).s;
         const float iso = s.ctl->params.iso;
         uint32_t n0p, n1p;
-        stage_and_classify<false, kDebug>(s, vol_of<kOne>(L, cur.v).g, iso, cur.base, (int)cur.nb_w, cur.b, wt, lc,
-                                          sm.num_tri, n0p, n1p);
+        stage_and_classify<false>(s, vol_of<kOne>(L, cur.v).g, iso, cur.base, (int)cur.nb_w, cur.b, wt, lc,
+                                  sm.num_tri, n0p, n1p);
         const uint32_t r0 = warp_sum(n0p), r1 = warp_sum(n1p);   // per-byte sums <= 160: no carries
         if (lane < (int)cur.nb_w) {
             const uint32_t cnt = ((r0 >> (8 * lane)) & 0xFFu) + ((r1 >> (8 * lane)) & 0xFFu);
@@ -433,7 +459,7 @@ __global__ void __launch_bounds__(32 * kW) mc_emit_kernel(Launch L) {
         const uint32_t base = cur.base;
         const int nb_w = (int)cur.nb_w;
         uint32_t n0p, n1p;
-        stage_and_classify<true, false>(s, g, iso, base, nb_w, cur.b, wt, lc, sm.num_tri, n0p, n1p);
+        stage_and_classify<true>(s, g, iso, base, nb_w, cur.b, wt, lc, sm.num_tri, n0p, n1p);
         // per-cell offsets inside the warp tile: two packed scans (byte q = block q)
         uint32_t i0 = n0p, i1 = n1p;
 #pragma unroll
@@ -541,9 +567,8 @@ __global__ void __launch_bounds__(32 * kW) mc_emit_kernel(Launch L) {
 namespace {
 
 template <int kW, bool kOne>
-void count_w(const Launch &L, bool debug, int grid, cudaStream_t st) {
-    if (debug) mc_count_kernel<kW, true, kOne><<<grid, 32 * kW, sizeof(CountSmem<kW>), st>>>(L);
-    else mc_count_kernel<kW, false, kOne><<<grid, 32 * kW, sizeof(CountSmem<kW>), st>>>(L);
+void count_w(const Launch &L, int grid, cudaStream_t st) {
+    mc_count_kernel<kW, kOne><<<grid, 32 * kW, sizeof(CountSmem<kW>), st>>>(L);
 }
 
 template <int kW, bool kOne>
@@ -575,25 +600,23 @@ int emit_occupancy(bool single) {
 
 template <int kW>
 int count_occupancy(bool single) {
-    raise_smem(mc_count_kernel<kW, false, false>, sizeof(CountSmem<kW>));
-    raise_smem(mc_count_kernel<kW, true, false>, sizeof(CountSmem<kW>));
-    raise_smem(mc_count_kernel<kW, false, true>, sizeof(CountSmem<kW>));
-    raise_smem(mc_count_kernel<kW, true, true>, sizeof(CountSmem<kW>));
+    raise_smem(mc_count_kernel<kW, false>, sizeof(CountSmem<kW>));
+    raise_smem(mc_count_kernel<kW, true>, sizeof(CountSmem<kW>));
     int occ = 0;
     if (single)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mc_count_kernel<kW, false, true>, 32 * kW,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mc_count_kernel<kW, true>, 32 * kW,
                                                       sizeof(CountSmem<kW>));
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mc_count_kernel<kW, false, false>, 32 * kW,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mc_count_kernel<kW, false>, 32 * kW,
                                                       sizeof(CountSmem<kW>));
     return occ;
 }
 
 template <bool kOne>
-void count_any(const Launch &L, bool debug, const Plan &pl, cudaStream_t st) {
-    if (pl.count_tile == 16) count_w<4, kOne>(L, debug, pl.mc_count, st);
-    else if (pl.count_tile == 64) count_w<16, kOne>(L, debug, pl.mc_count, st);
-    else count_w<8, kOne>(L, debug, pl.mc_count, st);
+void count_any(const Launch &L, const Plan &pl, cudaStream_t st) {
+    if (pl.count_tile == 16) count_w<4, kOne>(L, pl.mc_count, st);
+    else if (pl.count_tile == 64) count_w<16, kOne>(L, pl.mc_count, st);
+    else count_w<8, kOne>(L, pl.mc_count, st);
 }
 
 template <bool kOne>
@@ -613,9 +636,9 @@ void emit_any(const Launch &L, bool debug, const Plan &pl, cudaStream_t st) {
 }  // namespace
 
 // tile = candidates per CTA round = 4 per warp
-void launch_mc_count(const Launch &L, bool debug, const Plan &pl, cudaStream_t st) {
-    if (L.vols) count_any<false>(L, debug, pl, st);
-    else count_any<true>(L, debug, pl, st);
+void launch_mc_count(const Launch &L, bool /*debug*/, const Plan &pl, cudaStream_t st) {
+    if (L.vols) count_any<false>(L, pl, st);
+    else count_any<true>(L, pl, st);
 }
 
 void launch_mc_scan(const Launch &L, const Plan &pl, cudaStream_t st) {

@@ -455,6 +455,7 @@ int iso_server_create(iso_server **out, iso_volume *v, const iso_server_options 
         d.offsets = s.offsets;
         d.desc_cand = s.desc_cand;
         d.desc_mc = s.desc_mc;
+        d.cases = nullptr;                // a request's emit classifies (no per-request case store)
         sv->views[j] = VolEntry{d, v->g, v->n_cull_desc, v->n_lru_desc};
     }
     if (cudaMallocHost((void **)&sv->h_ctl, sizeof(Ctl)) != cudaSuccess ||
