@@ -482,8 +482,12 @@ def run_ours(args):
             h2d = h_bits.numel() * 8 + h_min.numel() * 4 + h_max.numel() * 4
             e2e_steps = max(1, min(args.steps, 5))
 
+            load_s = []
+
             def e2e_step():
+                t1 = time.perf_counter()
                 v = bc.Volume(h_bits, DIMS, RATE, h_min, h_max)
+                load_s.append(time.perf_counter() - t1)
                 n = 0
                 for iso in ISOS:
                     m = v.extract(iso)
@@ -502,6 +506,7 @@ def run_ours(args):
             dt = time.perf_counter() - t0
             e2e = {"value": n_e2e / dt, "unit": "triangles/s", "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": CTL_BYTES * len(ISOS), "ms_per_step": 1000 * dt / e2e_steps,
+                   "load_ms": 1000 * float(np.median(load_s[1:])),
                    "includes": "iso_load_volume from pinned host (upload + allocation + block hulls), "
                                "5 x iso_extract (device-allocated meshes), count readback, release"}
         vol.release()

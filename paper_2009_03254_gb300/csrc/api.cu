@@ -278,7 +278,10 @@ int run(iso_volume *v, float iso, void *out, unsigned long long cap_tris, bool m
     int rc = ensure_debug_edges(v, cap_tris);
     if (rc) return rc;
     *v->host_params = Params{iso, format, flags, 0u, cap_tris, (unsigned long long)(uintptr_t)out};
-    const bool graph = !mc_only && v->use_graph && !(v->flags & ISO_DEBUG) && !v->profiling;
+    // the graph is captured at the second extraction: a volume extracted
+    // once does not pay for capturing and instantiating it
+    const bool graph = !mc_only && v->use_graph && !(v->flags & ISO_DEBUG) && !v->profiling && v->extractions > 0;
+    if (!mc_only) v->extractions++;
     if (graph && ensure_graph(v) != ISO_OK) v->use_graph = false;   // fall back to plain launches
     if (graph && v->gexec) {
         CK(cudaGraphLaunch(v->gexec, v->stream));

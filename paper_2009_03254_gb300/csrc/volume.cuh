@@ -25,6 +25,7 @@ struct iso_volume {
     cudaGraph_t graph = nullptr;      // one extraction: params copy, the stage kernels, count readback
     cudaGraphExec_t gexec = nullptr;
     bool use_graph = true;
+    uint64_t extractions = 0;         // full extractions run so far (the graph is captured at the second)
     // owned device allocations
     uint64_t *bits = nullptr;
     float *bmin = nullptr, *bmax = nullptr;   // staging of host block ranges during the load only
