@@ -85,6 +85,18 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def reduce_over_ranks(seconds, units, device):
+    """Whole-job figures of independent replicas: the slowest rank's time and
+    the units all ranks processed (the process group must be initialised)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(seconds)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    n = torch.tensor([float(units)], device=device, dtype=torch.float64)
+    dist.all_reduce(n)
+    return float(t.item()), float(n.item())
+
+
 # ---------------------------------------------------------------- clocks
 
 class ClockSampler:
@@ -370,12 +382,7 @@ def run_ours(args):
         step_ms = [a.elapsed_time(b) for a, b in ev]
         total_s = sum(step_ms) / 1000.0
         if world > 1:
-            t = torch.tensor([total_s], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_s = float(t.item())
-            n = torch.tensor([total_tris], device="cuda", dtype=torch.float64)
-            dist.all_reduce(n)
-            total_tris = float(n.item())
+            total_s, total_tris = reduce_over_ranks(total_s, total_tris, "cuda")
 
         # per-kernel durations (same steps, events between the kernels)
         vol.set_profiling(True)
