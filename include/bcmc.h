@@ -90,7 +90,8 @@ typedef struct iso_stats {
     uint32_t reruns;           /* 1 if the triangle stage ran twice to fit the output */
     uint32_t n_candidates;     /* active blocks whose 2x2x2 +group range contains iso: the
                                   blocks the triangle stage visits */
-    uint32_t reserved;
+    uint32_t waves;            /* passes: 1, or the number of waves of an extraction whose active
+                                  blocks exceed the cache (see iso_extract) */
 } iso_stats;
 
 typedef struct iso_mesh {
@@ -124,7 +125,17 @@ int iso_load_volume(iso_volume **out, const void *compressed, size_t compressed_
  * buffer is allocated by the library (stream-ordered) and owned by
  * *out until iso_mesh_release.  Blocks until the counts are known.  If
  * the first guess of the output size is too small, the triangle stage runs
- * again into a larger buffer (stats.reruns = 1).  isovalue must be finite. */
+ * again into a larger buffer (stats.reruns = 1).  isovalue must be finite.
+ * Over budget (the paper always grows the cache; this library caps it):
+ * when the surface's active blocks do not fit in the cache even at the
+ * cap, the surface is extracted in waves of consecutive z-layers of blocks,
+ * each wave's active blocks together with those of the layer after it
+ * fitting in the cache; the triangles come out in the same order as from
+ * one pass (stats.waves > 1; stats then sum over the waves, n_active
+ * counting each block once; debug arrays describe the last wave).  Only if
+ * one layer and the next do not fit together is ISO_ERR_BUDGET returned
+ * (and then nothing of the cache changes).  The same holds for the _into
+ * variants, except the all-blocks baseline. */
 int iso_extract(iso_volume *v, float isovalue, iso_mesh *out);
 
 /* As iso_extract, but writes into a caller-owned device buffer of

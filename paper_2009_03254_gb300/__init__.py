@@ -52,7 +52,7 @@ class _Stats(ctypes.Structure):
     _fields_ = [("num_triangles", ctypes.c_uint64), ("n_active", ctypes.c_uint32), ("n_new", ctypes.c_uint32),
                 ("n_occupied", ctypes.c_uint32), ("n_slots", ctypes.c_uint32), ("cache_bytes", ctypes.c_uint64),
                 ("epoch", ctypes.c_uint32), ("reruns", ctypes.c_uint32), ("n_candidates", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32)]
+                ("waves", ctypes.c_uint32)]
 
     def as_dict(self):
         return {name: int(getattr(self, name)) for name, _ in self._fields_}

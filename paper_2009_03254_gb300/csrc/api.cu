@@ -148,7 +148,7 @@ void fill_stats(const Ctl &c, iso_stats *st, uint32_t reruns) {
     st->epoch = c.epoch;
     st->reruns = reruns;
     st->n_candidates = c.n_cand;
-    st->reserved = 0;
+    st->waves = 1;
 }
 
 }  // namespace bcmc_host
@@ -181,7 +181,7 @@ int free_volume(iso_volume *v) {
     DevState &s = v->s;
     void *ptrs[] = {v->bits, v->bmin, v->bmax, v->hull, v->hull8, v->tables, s.mactive, s.iactive, s.inew, s.icand,
                     s.islot, s.slast, s.sblock, s.lbuf[0], s.lbuf[1], s.newslot, s.slots, s.desc_cull, s.desc_cand,
-                    s.desc_lru_a, s.desc_lru_b, s.desc_mc, s.ctl, s.counts, s.offsets, s.cases, s.dbg_edges};
+                    s.desc_lru_a, s.desc_lru_b, s.desc_mc, s.ctl, s.counts, s.offsets, s.iocc, s.cases, s.dbg_edges};
     for (void *p : ptrs) dfree_on(p, v->stream);
     cudaStreamSynchronize(v->stream);
     (void)cudaGetLastError();
@@ -273,11 +273,16 @@ int ensure_debug_edges(iso_volume *v, unsigned long long tris) {
 
 // run the pipeline into `out` (capacity cap_tris); returns the error of
 // the run, with the control block mirrored on the host
+struct Window {                    // a wave: block ids [lo, act_hi) may be active, [lo, cand_hi) candidates
+    uint32_t lo, cand_hi, act_hi;
+};
+
 int run(iso_volume *v, float iso, void *out, unsigned long long cap_tris, bool mc_only,
-        uint32_t format = kVertexFloat4, uint32_t flags = 0) {
+        uint32_t format = kVertexFloat4, uint32_t flags = 0, const Window *w = nullptr) {
     int rc = ensure_debug_edges(v, cap_tris);
     if (rc) return rc;
-    *v->host_params = Params{iso, format, flags, 0u, cap_tris, (unsigned long long)(uintptr_t)out};
+    *v->host_params = Params{iso, format, flags | (w ? (uint32_t)kParamWindow : 0u), w ? w->lo : 0u,
+                             w ? w->cand_hi : 0u, w ? w->act_hi : 0u, cap_tris, (unsigned long long)(uintptr_t)out};
     // the graph is captured at the second extraction: a volume extracted
     // once does not pay for capturing and instantiating it
     const bool graph = !mc_only && v->use_graph && !(v->flags & ISO_DEBUG) && !v->profiling && v->extractions > 0;
@@ -299,6 +304,85 @@ int run(iso_volume *v, float iso, void *out, unsigned long long cap_tris, bool m
     }
     v->last_tris = v->host_ctl->n_tri;
     return status_to_error(v, v->host_ctl->status);
+}
+
+// A surface whose active blocks do not fit in the cache, extracted in
+// waves: consecutive ranges of z-layers of blocks whose active blocks,
+// together with those of the next layer (the +z neighbours of the last
+// layer's candidates), fit in the cache.  Each wave is one extraction
+// restricted to its block-id window; the waves' triangles are appended in
+// order, which is the single-pass order (ascending block id).
+int run_waves(iso_volume *v, float iso, void *out, unsigned long long cap_tris, uint32_t format,
+              unsigned long long *total, iso_stats *st) {
+    const Geom &g = v->g;
+    const uint32_t slab = g.nbx * g.nby;
+    std::vector<uint32_t> layer(g.nbz);
+    {
+        uint32_t *d_layers = nullptr;
+        int rc = dalloc(v, &d_layers, g.nbz);
+        if (rc) return rc;
+        bool ok = cudaMemsetAsync(d_layers, 0, (size_t)g.nbz * 4, v->stream) == cudaSuccess;
+        if (ok) {
+            launch_count_layers(v->hull, g, iso, d_layers, v->stream);
+            ok = cudaMemcpyAsync(layer.data(), d_layers, (size_t)g.nbz * 4, cudaMemcpyDeviceToHost, v->stream) ==
+                     cudaSuccess &&
+                 cudaStreamSynchronize(v->stream) == cudaSuccess;
+        }
+        dfree_on(d_layers, v->stream);
+        if (!ok) {
+            (void)cudaGetLastError();
+            return ISO_ERR_CUDA;
+        }
+    }
+    auto at = [&](uint32_t z) -> uint64_t { return z < g.nbz ? layer[z] : 0; };
+    std::vector<std::pair<uint32_t, uint32_t>> waves;   // candidate layers [z0, z1)
+    for (uint32_t z = 0; z < g.nbz;) {
+        if (at(z) + at(z + 1) > v->cap) return ISO_ERR_BUDGET;   // not even one layer fits
+        uint64_t acc = at(z);
+        uint32_t z1 = z + 1;
+        while (z1 < g.nbz && acc + at(z1) + at(z1 + 1) <= v->cap) acc += at(z1++);
+        waves.emplace_back(z, z1);
+        z = z1;
+    }
+    const size_t vbytes = format == kVertexPacked ? 24 : 48;
+    unsigned long long tot = 0;
+    uint64_t n_active = 0, n_new = 0, n_cand = 0, n_occ = 0;
+    for (uint32_t z = 0; z < g.nbz; z++) n_active += layer[z];
+    for (const auto &wz : waves) {
+        const Window w{wz.first * slab, std::min(g.nb, wz.second * slab), std::min(g.nb, (wz.second + 1) * slab)};
+        const unsigned long long room = cap_tris > tot ? cap_tris - tot : 0ull;
+        void *wout = (out && room) ? static_cast<char *>(out) + tot * vbytes : nullptr;
+        const int rc = run(v, iso, wout, room, false, format, 0u, &w);
+        if (rc) return rc;
+        const Ctl &c = *v->host_ctl;
+        tot += c.n_tri;
+        n_new += c.n_new;
+        n_cand += c.n_cand;
+        n_occ += c.n_occ;
+    }
+    *total = tot;
+    v->last_tris = tot;
+    if (st) {
+        fill_stats(*v->host_ctl, st, 0);
+        st->num_triangles = tot;
+        st->n_active = (uint32_t)std::min<uint64_t>(n_active, 0xFFFFFFFFu);
+        st->n_new = (uint32_t)std::min<uint64_t>(n_new, 0xFFFFFFFFu);
+        st->n_candidates = (uint32_t)std::min<uint64_t>(n_cand, 0xFFFFFFFFu);
+        st->n_occupied = (uint32_t)std::min<uint64_t>(n_occ, 0xFFFFFFFFu);
+        st->waves = (uint32_t)waves.size();
+    }
+    return ISO_OK;
+}
+
+// One extraction into a caller buffer: a single pass, or waves when the
+// surface's active blocks exceed the cache.  *total receives T.
+int extract_to(iso_volume *v, float iso, void *out, unsigned long long cap_tris, uint32_t format, uint32_t flags,
+               iso_stats *stats, unsigned long long *total) {
+    int rc = run(v, iso, out, cap_tris, false, format, flags);
+    if (rc == ISO_ERR_BUDGET && !(flags & kParamAllBlocks)) return run_waves(v, iso, out, cap_tris, format, total, stats);
+    *total = v->host_ctl->n_tri;
+    if (stats) fill_stats(*v->host_ctl, stats, 0);
+    return rc;
 }
 
 bool build_tables_once(McTables *t) {
@@ -401,10 +485,12 @@ int iso_load_volume(iso_volume **out, const void *compressed, size_t compressed_
     TRY(dalloc(v, &s.desc_cand, v->n_cull_desc));
     TRY(dalloc(v, &s.desc_lru_a, v->n_lru_desc));
     TRY(dalloc(v, &s.desc_lru_b, v->n_lru_desc));
-    TRY(dalloc(v, &s.desc_mc, n_mc_desc));
+    TRY(dalloc(v, &s.desc_mc, 2 * (size_t)n_mc_desc));   // triangle offsets, then occupied counts
+    s.desc_occ = s.desc_mc + n_mc_desc;
     TRY(dalloc(v, &s.ctl, 1));
     TRY(dalloc(v, &s.counts, v->cap));
     TRY(dalloc(v, &s.offsets, v->cap));
+    TRY(dalloc(v, &s.iocc, s.list_cap));
     // the count pass keeps each candidate's cases for the emit pass when they
     // take at most 8 GB (else emit classifies again); debug volumes always
     if ((v->flags & ISO_DEBUG) || (uint64_t)s.list_cap * 64 <= (8ull << 30))
@@ -445,7 +531,7 @@ int iso_load_volume(iso_volume **out, const void *compressed, size_t compressed_
     TRYC(cudaMemsetAsync(s.sblock, 0xFF, (size_t)v->cap * 4, st));
     TRYC(cudaMemsetAsync(s.slast, 0, (size_t)v->cap * 4, st));
     TRYC(cudaMemsetAsync(s.mactive, 0, (size_t)nwords * 4, st));
-    TRYC(cudaMemsetAsync(s.desc_mc, 0, (size_t)n_mc_desc * 8, st));
+    TRYC(cudaMemsetAsync(s.desc_mc, 0, (size_t)n_mc_desc * 16, st));
     // index lists start as valid ids, so that even a pass cut short by a
     // device-side timeout only ever indexes inside the volume and the cache
     if (s.iactive) TRYC(cudaMemsetAsync(s.iactive, 0, (size_t)s.list_cap * 4, st));
@@ -478,22 +564,20 @@ int iso_extract_into(iso_volume *v, float isovalue, float *d_vertices, uint64_t 
                      iso_stats *stats) {
     if (!v || !std::isfinite(isovalue) || (!d_vertices && capacity_triangles)) return ISO_ERR_INVALID_ARG;
     DeviceGuard dg(v->device);
-    int rc = run(v, isovalue, d_vertices, capacity_triangles, false);
-    if (stats) fill_stats(*v->host_ctl, stats, 0);
+    unsigned long long total = 0;
+    const int rc = extract_to(v, isovalue, d_vertices, capacity_triangles, kVertexFloat4, 0u, stats, &total);
     if (rc) return rc;
-    if (v->host_ctl->n_tri > capacity_triangles) return ISO_ERR_CAPACITY;
-    return ISO_OK;
+    return total > capacity_triangles ? ISO_ERR_CAPACITY : ISO_OK;
 }
 
 int iso_extract_all_blocks_into(iso_volume *v, float isovalue, float *d_vertices, uint64_t capacity_triangles,
-                                iso_stats *stats) {
+                     iso_stats *stats) {
     if (!v || !std::isfinite(isovalue) || (!d_vertices && capacity_triangles)) return ISO_ERR_INVALID_ARG;
     DeviceGuard dg(v->device);
-    int rc = run(v, isovalue, d_vertices, capacity_triangles, false, kVertexFloat4, kParamAllBlocks);
-    if (stats) fill_stats(*v->host_ctl, stats, 0);
+    unsigned long long total = 0;
+    const int rc = extract_to(v, isovalue, d_vertices, capacity_triangles, kVertexFloat4, kParamAllBlocks, stats, &total);
     if (rc) return rc;
-    if (v->host_ctl->n_tri > capacity_triangles) return ISO_ERR_CAPACITY;
-    return ISO_OK;
+    return total > capacity_triangles ? ISO_ERR_CAPACITY : ISO_OK;
 }
 
 int iso_decode_volume(const uint64_t *d_bits, uint32_t nx, uint32_t ny, uint32_t nz, uint32_t rate_bits,
@@ -508,14 +592,13 @@ int iso_decode_volume(const uint64_t *d_bits, uint32_t nx, uint32_t ny, uint32_t
 }
 
 int iso_extract_packed_into(iso_volume *v, float isovalue, uint32_t *d_vertices, uint64_t capacity_triangles,
-                            iso_stats *stats) {
+                     iso_stats *stats) {
     if (!v || !std::isfinite(isovalue) || (!d_vertices && capacity_triangles)) return ISO_ERR_INVALID_ARG;
     DeviceGuard dg(v->device);
-    int rc = run(v, isovalue, d_vertices, capacity_triangles, false, kVertexPacked);
-    if (stats) fill_stats(*v->host_ctl, stats, 0);
+    unsigned long long total = 0;
+    const int rc = extract_to(v, isovalue, d_vertices, capacity_triangles, kVertexPacked, 0u, stats, &total);
     if (rc) return rc;
-    if (v->host_ctl->n_tri > capacity_triangles) return ISO_ERR_CAPACITY;
-    return ISO_OK;
+    return total > capacity_triangles ? ISO_ERR_CAPACITY : ISO_OK;
 }
 
 int iso_extract(iso_volume *v, float isovalue, iso_mesh *out) {
@@ -533,6 +616,28 @@ int iso_extract(iso_volume *v, float isovalue, iso_mesh *out) {
     }
     int rc = run(v, isovalue, buf, guess, false);
     uint32_t reruns = 0;
+    if (rc == ISO_ERR_BUDGET) {           // too many active blocks for the cache: waves
+        unsigned long long total = 0;
+        rc = run_waves(v, isovalue, buf, guess, kVertexFloat4, &total, &out->stats);
+        if (rc == ISO_OK && total > guess) {   // the waves again into a buffer of the right size
+            cudaFreeAsync(buf, v->stream);
+            buf = nullptr;
+            const int arc = dalloc(v, &buf, std::max(total, 1ull) * 3);
+            if (arc) return arc;
+            guess = std::max(total, 1ull);
+            rc = run_waves(v, isovalue, buf, guess, kVertexFloat4, &total, &out->stats);
+            out->stats.reruns = 1;
+        }
+        if (rc) {
+            cudaFreeAsync(buf, v->stream);
+            cudaStreamSynchronize(v->stream);
+            return rc;
+        }
+        out->d_vertices = reinterpret_cast<float *>(buf);
+        out->num_triangles = total;
+        out->capacity_triangles = guess;
+        return ISO_OK;
+    }
     if (rc == ISO_OK && v->host_ctl->n_tri > guess) {
         const unsigned long long need = v->host_ctl->n_tri;
         cudaFreeAsync(buf, v->stream);

@@ -65,13 +65,15 @@ enum VertexFormat : uint32_t {
 
 enum ParamFlags : uint32_t {
     kParamAllBlocks = 1u,         // no range test: every block is active and a candidate
+    kParamWindow = 2u,            // a wave: only blocks with ids in [win_lo, win_act_hi) may be active,
+                                  // only those in [win_lo, win_cand_hi) candidates
 };
 
 struct Params {
     float iso;
     uint32_t format;              // VertexFormat
     uint32_t flags;               // ParamFlags
-    uint32_t reserved;
+    uint32_t win_lo, win_cand_hi, win_act_hi;
     unsigned long long tri_cap;   // output capacity in triangles
     unsigned long long out;       // vertex buffer (float4 * or uint2 *)
 };

@@ -37,7 +37,10 @@ __global__ void __launch_bounds__(kThreads) prep_kernel(Launch L) {
         const VolEntry &e = vol_of<kOne>(L, v);
         const DevState &s = e.s;
         const uint32_t n_mc_desc = s.ctl->mc_tiles;   // descriptors the last triangle pass used
-        for (uint32_t i = tid; i < n_mc_desc; i += stride) s.desc_mc[i] = 0;
+        for (uint32_t i = tid; i < n_mc_desc; i += stride) {
+            s.desc_mc[i] = 0;
+            s.desc_occ[i] = 0;
+        }
         for (uint32_t i = tid; i < e.n_cull_desc; i += stride) {
             s.desc_cull[i] = 0;
             s.desc_cand[i] = 0;
@@ -86,7 +89,12 @@ __device__ __forceinline__ void cull_tile(const DevState &s, const Geom &g, uint
     const uint32_t lt = (1u << lane) - 1u;
     const uint32_t epoch = s.ctl->epoch;
     const float iso = s.ctl->params.iso;
-    const bool all = (s.ctl->params.flags & kParamAllBlocks) != 0;   // the full-volume baseline
+    const Params &prm = s.ctl->params;
+    const bool all = (prm.flags & kParamAllBlocks) != 0;             // the full-volume baseline
+    // a wave's block-id window (everything outside it is treated as inactive)
+    const bool win = (prm.flags & kParamWindow) != 0;
+    const uint32_t w_lo = win ? prm.win_lo : 0u, w_act = win ? prm.win_act_hi : g.nb,
+                   w_cand = win ? prm.win_cand_hi : g.nb;
     // two halves of kR/2 rounds; in each, every load (3x3x3 hull, +group
     // hull, slot) is issued before any of it is used, so a tile waits for
     // two memory round trips rather than one per round
@@ -107,8 +115,8 @@ __device__ __forceinline__ void cull_tile(const DevState &s, const Geom &g, uint
         for (int i = 0; i < kHalf; i++) {
             const int r = half * kHalf + i;
             const uint32_t b = tile * kTile + r * kThreads + threadIdx.x;
-            const bool act = b < g.nb && (all || ((h[i].x < iso) && (iso <= h[i].y)));
-            const bool cand = act && (all || ((h8[i].x < iso) && (iso <= h8[i].y)));
+            const bool act = b < g.nb && b >= w_lo && b < w_act && (all || ((h[i].x < iso) && (iso <= h[i].y)));
+            const bool cand = act && b < w_cand && (all || ((h8[i].x < iso) && (iso <= h8[i].y)));
             const bool nw = act && sl[i] < 0;
             if (act && sl[i] >= 0) s.slast[sl[i]] = epoch;       // a hit: the slot's age resets
             const uint32_t ab = __ballot_sync(0xffffffffu, act);
@@ -464,6 +472,29 @@ __global__ void batch_gather_kernel(Launch L, Ctl *dst) {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < L.n * kWords; i += gridDim.x * blockDim.x)
         reinterpret_cast<uint32_t *>(dst)[i] =
             reinterpret_cast<const uint32_t *>(L.vols[i / kWords].s.ctl)[i % kWords];
+}
+
+// ================================================================ waves (over-budget extraction)
+
+// Active blocks of each z-layer of blocks (a layer is nbx*nby consecutive
+// ids): the host packs layers into waves whose active blocks fit the cache.
+__global__ void __launch_bounds__(kThreads) count_layers_kernel(const float2 *__restrict__ hull, Geom g, float iso,
+                                                                uint32_t *layer_active) {
+    const uint32_t slab = g.nbx * g.nby;
+    for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < g.nb; b += gridDim.x * blockDim.x) {
+        const float2 h = __ldg(hull + b);
+        const bool act = (h.x < iso) && (iso <= h.y);
+        // lanes of a warp usually share a layer: one atomic per (warp, layer)
+        const uint32_t z = b / slab;
+        const uint32_t peers = __match_any_sync(__activemask(), z);
+        const uint32_t n = __popc(__ballot_sync(__activemask(), act) & peers);
+        if (n && (threadIdx.x & 31) == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&layer_active[z], n);
+    }
+}
+
+void launch_count_layers(const float2 *hull, const Geom &g, float iso, uint32_t *layer_active, cudaStream_t st) {
+    const uint32_t blocks = std::max<uint32_t>(1, std::min<uint32_t>((g.nb + kThreads - 1) / kThreads, 65535u));
+    count_layers_kernel<<<blocks, kThreads, 0, st>>>(hull, g, iso, layer_active);
 }
 
 // ================================================================ load-time and utility kernels

@@ -31,6 +31,8 @@ struct DevState {
     const uint8_t *tables;     // num_tri[256] then tri_edges[256][16]
     uint32_t *counts;          // triangles of each candidate
     unsigned long long *offsets; // exclusive prefix of counts: first triangle of each candidate
+    uint32_t *iocc;            // I_occ: positions in the candidate list of the occupied candidates (ascending)
+    unsigned long long *desc_occ;  // look-back descriptors of the occupied count (next to desc_mc)
     uint8_t *cases;            // 64 cell cases per candidate, written by the count pass and read by
                                // emit instead of classifying again (null: emit classifies)
     // debug copy (null unless the volume was loaded with ISO_DEBUG)
@@ -109,6 +111,8 @@ void launch_encode(const float *field, const Geom &g, uint64_t *bits, float *bmi
 void launch_decode_list(const uint64_t *bits, uint32_t rate, const uint32_t *ids, uint64_t n, float *out,
                         cudaStream_t st);
 void launch_decode_volume(const uint64_t *bits, const Geom &g, float *field, cudaStream_t st);
+// waves: active blocks of each z-layer of blocks (layer_active zeroed by the caller)
+void launch_count_layers(const float2 *hull, const Geom &g, float iso, uint32_t *layer_active, cudaStream_t st);
 void launch_gather_slots(const float *slots, const int32_t *islot, const uint32_t *ids, uint64_t n, float *out,
                          int32_t *missing, cudaStream_t st);
 

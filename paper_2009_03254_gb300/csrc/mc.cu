@@ -12,9 +12,12 @@
 //   count   Section 4.4: stage each candidate's 5x5x5 samples, classify its
 //           64 cells, write its triangle count
 //   scan    prefix sum of the counts over the candidates (block offsets
-//           and the total), single pass with decoupled look-back
-//   emit    Section 4.5: stage and classify again, per-cell offsets by
-//           warp scans, then one triangle (three float4 vertices) per lane
+//           and the total) and compaction of the occupied candidates, one
+//           pass with two decoupled look-backs
+//   emit    Section 4.5, over the occupied candidates only: stage the
+//           samples (the cases kept by count arrive by asynchronous copies),
+//           per-cell offsets by warp scans, then one triangle (three
+//           vertices) per lane
 //
 // Both passes give each warp 4 consecutive candidates at a time (a "warp
 // tile") and no warp ever waits for another one:
@@ -139,25 +142,32 @@ __device__ __forceinline__ uint32_t case_bits(uint32_t W) {
     return (W & 3u) | ((W >> 3) & 0xCu) | ((W >> 21) & 0x30u) | ((W >> 24) & 0xC0u);
 }
 
-// Phases A-C for the warp tile starting at candidate `base` (nb_w of
-// kBPW slots used).  Returns the per-cell triangle counts of the lane's two
-// cells, packed one byte per block: n0p for cell lane, n1p for cell
-// lane + 32.  The count pass (kEmit false) classifies and, when the volume
-// keeps them (s.cases), stores the cases; the emit pass leaves the cases in
-// wt.cases, reading the stored ones instead of classifying again when
-// there are any.  `b` is this lane's block (candidate base + lane/8),
-// loaded by the caller one warp tile ahead.
+// Phases A-C for the warp tile starting at candidate `base` (count pass)
+// or at occupied candidate `base` (emit pass), nb_w of kBPW slots used.
+// Returns the per-cell triangle counts of the lane's two cells, packed one
+// byte per block: n0p for cell lane, n1p for cell lane + 32.  The count
+// pass (kEmit false) classifies and, when the volume keeps them (s.cases),
+// stores the cases; the emit pass leaves the cases in wt.cases, reading
+// the stored ones instead of classifying again when there are any.  `b` is
+// this lane's block (block lane/8 of the tile) and `ci` its position in
+// the candidate list, loaded by the caller one warp tile ahead.
 template <bool kEmit>
 __device__ __forceinline__ void stage_and_classify(const DevState &s, const Geom &g, float iso, uint32_t base,
-                                                   int nb_w, uint32_t b, WarpTile &wt, const LaneConst &lc,
-                                                   const uint8_t *num_tri, uint32_t &n0p, uint32_t &n1p) {
+                                                   int nb_w, uint32_t b, uint32_t ci, WarpTile &wt,
+                                                   const LaneConst &lc, const uint8_t *num_tri, uint32_t &n0p,
+                                                   uint32_t &n1p) {
     const int lane = threadIdx.x & 31, bq = lane >> 3, bo = lane & 7;
     const uint32_t slab = g.nbx * g.nby;
     const bool stored = kEmit && s.cases != nullptr;      // uniform
-    // the stored cases of the tile's blocks, copied to shared memory while
-    // the samples are staged (16 lanes x 16 bytes; both ends 16-byte aligned)
-    if (stored && lane < 4 * nb_w)
-        cp_async16(&wt.cases[lane >> 2][16 * (lane & 3)], s.cases + (size_t)(base + (lane >> 2)) * 64 + 16 * (lane & 3));
+    // The stored cases of the tile's blocks, copied to shared memory while
+    // the samples are staged (16 lanes x 16 bytes; both ends 16-byte
+    // aligned).  The emit pass's blocks are occupied candidates, not
+    // consecutive ones: block q's position in the candidate list is `ci` of
+    // lane 8q.
+    if (stored) {
+        const uint32_t cq = __shfl_sync(0xffffffffu, ci, (lane >> 2) * 8);
+        if (lane < 4 * nb_w) cp_async16(&wt.cases[lane >> 2][16 * (lane & 3)], s.cases + (size_t)cq * 64 + 16 * (lane & 3));
+    }
     // ---- A: +group slots
     if (bq < nb_w) {
         uint32_t bx, by, bz;
@@ -266,23 +276,28 @@ __device__ __forceinline__ uint32_t mc_candidates(const Ctl *c) {
     return (c->status & (kStatusBudget | kStatusTimeout | kStatusTimeoutLru)) ? 0u : c->n_cand;
 }
 
-// A warp tile located in the launch: volume, first candidate, candidates
-// used, and this lane's block id (candidate first + lane/8), read ahead.
+// A warp tile located in the launch: volume, first entry, entries used,
+// and for this lane's block (entry first + lane/8) its position in the
+// candidate list and its block id, read ahead.  The count pass walks the
+// candidates; the emit pass walks the occupied ones (kOcc).
 struct TileRef {
-    uint32_t v, base, nb_w, b;
+    uint32_t v, base, nb_w, b, ci;
 };
 
-template <bool kOne>
+template <bool kOne, bool kOcc = false>
 __device__ __forceinline__ TileRef locate_tile(const Launch &L, const uint32_t *pre, uint32_t t, uint32_t total) {
-    TileRef r{0u, 0u, 0u, 0u};
+    TileRef r{0u, 0u, 0u, 0u, 0u};
     if (t >= total) return r;
     r.v = item_vol<kOne>(pre, L.n, t);
     const DevState &s = vol_of<kOne>(L, r.v).s;
-    const uint32_t n_cand = s.ctl->n_cand;
+    const uint32_t n = kOcc ? s.ctl->n_occ : s.ctl->n_cand;
     r.base = (t - item_base<kOne>(pre, r.v)) * kBPW;
-    r.nb_w = min((uint32_t)kBPW, n_cand - r.base);
+    r.nb_w = min((uint32_t)kBPW, n - r.base);
     const uint32_t i = r.base + ((uint32_t)(threadIdx.x & 31) >> 3);
-    r.b = i < n_cand ? s.icand[i] : 0u;
+    if (i < n) {
+        r.ci = kOcc ? s.iocc[i] : i;
+        r.b = s.icand[r.ci];
+    }
     return r;
 }
 
@@ -307,37 +322,26 @@ __global__ void __launch_bounds__(32 * kW, 32 / kW) mc_count_kernel(Launch L) { 
     const uint32_t stride = gridDim.x * kW;
     uint32_t t = blockIdx.x * kW + warp;
     TileRef nxt = locate_tile<kOne>(L, pre, t, total);
-    uint32_t occ = 0, occ_v = nxt.v;
     for (; t < total; t += stride) {
         const TileRef cur = nxt;
         nxt = locate_tile<kOne>(L, pre, t + stride, total);   // next warp tile's block, loaded early
-        if (!kOne && cur.v != occ_v) {                          // flush the previous volume's occupied count
-            occ = warp_sum(occ);
-            if (lane == 0 && occ) atomicAdd(&vol_of<kOne>(L, occ_v).s.ctl->n_occ, occ);
-            occ = 0;
-            occ_v = cur.v;
-        }
         const DevState &s = vol_of<kOne>(L, cur.v).s;
         const float iso = s.ctl->params.iso;
         uint32_t n0p, n1p;
-        stage_and_classify<false>(s, vol_of<kOne>(L, cur.v).g, iso, cur.base, (int)cur.nb_w, cur.b, wt, lc,
+        stage_and_classify<false>(s, vol_of<kOne>(L, cur.v).g, iso, cur.base, (int)cur.nb_w, cur.b, 0u, wt, lc,
                                   sm.num_tri, n0p, n1p);
         const uint32_t r0 = warp_sum(n0p), r1 = warp_sum(n1p);   // per-byte sums <= 160: no carries
-        if (lane < (int)cur.nb_w) {
-            const uint32_t cnt = ((r0 >> (8 * lane)) & 0xFFu) + ((r1 >> (8 * lane)) & 0xFFu);
-            s.counts[cur.base + lane] = cnt;
-            occ += cnt > 0;
-        }
+        if (lane < (int)cur.nb_w)
+            s.counts[cur.base + lane] = ((r0 >> (8 * lane)) & 0xFFu) + ((r1 >> (8 * lane)) & 0xFFu);
     }
-    occ = warp_sum(occ);
-    if (lane == 0 && occ) atomicAdd(&vol_of<kOne>(L, occ_v).s.ctl->n_occ, occ);
 }
 
 // ================================================================ scan (Section 4.4)
 //
-// Exclusive prefix of the candidates' counts -> 64-bit offsets; the last
-// tile of a volume writes its total.  kScanItems = 256 * kPT counts per
-// tile, kPT per thread.  Every volume has at least one item; its item 0
+// Exclusive prefix of the candidates' counts -> 64-bit offsets, and the
+// compacted positions of the occupied candidates (I_occ: the blocks the
+// emit pass visits, Section 4.4); the last tile of a volume writes both
+// totals.  kScanItems = 256 * kPT counts per tile, kPT per thread.  Every volume has at least one item; its item 0
 // records how many look-back descriptors the volume used (the next prep
 // clears them).
 
@@ -345,8 +349,8 @@ template <int kPT, bool kOne>
 __global__ void __launch_bounds__(kThreads) mc_scan_kernel(Launch L) {
     constexpr int kWarps = kThreads / 32;
     constexpr uint32_t kScanItems = kThreads * kPT;
-    __shared__ uint32_t wsum[kWarps];
-    __shared__ unsigned long long s_excl;
+    __shared__ uint32_t wsum[kWarps], wocc[kWarps];
+    __shared__ unsigned long long s_excl[2];
     __shared__ uint32_t pre[kMaxBatch + 1];
     __shared__ uint32_t s_item;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -368,22 +372,30 @@ __global__ void __launch_bounds__(kThreads) mc_scan_kernel(Launch L) {
         if (tile == 0 && threadIdx.x == 0) c->mc_tiles = ntiles;
         if (ntiles == 0) continue;                        // block-uniform
         const uint32_t i0 = tile * kScanItems + threadIdx.x * kPT;
-        uint32_t v8[kPT], sum = 0;
+        uint32_t v8[kPT], sum = 0, occ = 0;
 #pragma unroll
         for (int k = 0; k < kPT; k++) {
             v8[k] = i0 + k < n ? s.counts[i0 + k] : 0u;
             sum += v8[k];
+            occ += v8[k] != 0u;
         }
-        uint32_t incl = sum;
+        // triangles in the low 20 bits, occupied candidates above (a warp
+        // holds at most 32 * 16 * 320 triangles and 512 candidates: no carry)
+        const uint32_t own = sum | (occ << 20);
+        uint32_t incl = own;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += t;
         }
-        if (lane == 31) wsum[warp] = incl;
+        if (lane == 31) {
+            wsum[warp] = incl & 0xFFFFFu;
+            wocc[warp] = incl >> 20;
+        }
         __syncthreads();
-        if (warp == 0) {
-            const uint32_t w = lane < kWarps ? wsum[lane] : 0u;
+        if (warp < 2) {                   // warp 0: triangle offsets; warp 1: occupied positions
+            uint32_t *ws = warp == 0 ? wsum : wocc;
+            const uint32_t w = lane < kWarps ? ws[lane] : 0u;
             uint32_t wi = w;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -391,18 +403,25 @@ __global__ void __launch_bounds__(kThreads) mc_scan_kernel(Launch L) {
                 if (lane >= o) wi += t;
             }
             const uint32_t tot = __shfl_sync(0xffffffffu, wi, kWarps - 1);
-            if (lane < kWarps) wsum[lane] = wi - w;                      // exclusive warp offsets
-            const unsigned long long excl = lookback_exclusive(s.desc_mc, tile, tot, &c->status, kStatusTimeoutScan);
+            if (lane < kWarps) ws[lane] = wi - w;                        // exclusive warp offsets
+            const unsigned long long excl = lookback_exclusive(warp == 0 ? s.desc_mc : s.desc_occ, tile, tot,
+                                                               &c->status, kStatusTimeoutScan);
             if (lane == 0) {
-                s_excl = excl;
-                if (tile == ntiles - 1) c->n_tri = excl + tot;
+                s_excl[warp] = excl;
+                if (tile == ntiles - 1) {
+                    if (warp == 0) c->n_tri = excl + tot;
+                    else c->n_occ = (uint32_t)(excl + tot);
+                }
             }
         }
         __syncthreads();
-        unsigned long long run = s_excl + wsum[warp] + (incl - sum);
+        const uint32_t before = incl - own;                              // this thread's exclusive prefix in the warp
+        unsigned long long run = s_excl[0] + wsum[warp] + (before & 0xFFFFFu);
+        uint32_t orun = (uint32_t)s_excl[1] + wocc[warp] + (before >> 20);
 #pragma unroll
         for (int k = 0; k < kPT; k++) {
             if (i0 + k < n) s.offsets[i0 + k] = run;
+            if (v8[k]) s.iocc[orun++] = i0 + k;
             run += v8[k];
         }
     }
@@ -434,7 +453,7 @@ __global__ void __launch_bounds__(32 * kW) mc_emit_kernel(Launch L) {
     const uint32_t total = launch_prefix<kOne>(
         L, [&](uint32_t v) {
             const Ctl *c = vol_of<kOne>(L, v).s.ctl;
-            return (c->status & (kStatusBudget | kStatusAnyTimeout)) ? 0u : ceil_div(c->n_cand, kBPW);
+            return (c->status & (kStatusBudget | kStatusAnyTimeout)) ? 0u : ceil_div(c->n_occ, kBPW);
         },
         pre);
     __syncthreads();                                      // the tables
@@ -445,10 +464,10 @@ __global__ void __launch_bounds__(32 * kW) mc_emit_kernel(Launch L) {
     float4 *stage = sm.stage[warp];
     const uint32_t stride = gridDim.x * kW;
     uint32_t t = blockIdx.x * kW + warp;
-    TileRef nxt = locate_tile<kOne>(L, pre, t, total);
+    TileRef nxt = locate_tile<kOne, true>(L, pre, t, total);
     for (; t < total; t += stride) {
         const TileRef cur = nxt;
-        nxt = locate_tile<kOne>(L, pre, t + stride, total);   // next warp tile's block, loaded early
+        nxt = locate_tile<kOne, true>(L, pre, t + stride, total);   // next warp tile's blocks, loaded early
         const DevState &s = vol_of<kOne>(L, cur.v).s;
         const Geom &g = vol_of<kOne>(L, cur.v).g;
         const Ctl *c = s.ctl;
@@ -459,7 +478,10 @@ __global__ void __launch_bounds__(32 * kW) mc_emit_kernel(Launch L) {
         const uint32_t base = cur.base;
         const int nb_w = (int)cur.nb_w;
         uint32_t n0p, n1p;
-        stage_and_classify<true>(s, g, iso, base, nb_w, cur.b, wt, lc, sm.num_tri, n0p, n1p);
+        stage_and_classify<true>(s, g, iso, base, nb_w, cur.b, cur.ci, wt, lc, sm.num_tri, n0p, n1p);
+        // consecutive occupied candidates have adjacent outputs (the empty
+        // ones between them add nothing): the tile starts at its first block's
+        const uint32_t first_ci = __shfl_sync(0xffffffffu, cur.ci, 0);
         // per-cell offsets inside the warp tile: two packed scans (byte q = block q)
         uint32_t i0 = n0p, i1 = n1p;
 #pragma unroll
@@ -481,7 +503,7 @@ __global__ void __launch_bounds__(32 * kW) mc_emit_kernel(Launch L) {
             wtot += b0 + ((s1 >> (8 * q)) & 0xFFu);
         }
         if (wtot == 0) continue;                       // warp-uniform
-        const unsigned long long gbase = s.offsets[base];
+        const unsigned long long gbase = s.offsets[first_ci];
         __syncwarp();
         // one triangle per lane; its three vertices go through the warp's
         // staging area so that each store instruction writes 512

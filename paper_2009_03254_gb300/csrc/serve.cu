@@ -47,6 +47,7 @@ struct ServeArgs {
     uint32_t *icand[kMaxServe];       // per-request candidate lists
     unsigned long long *desc_cand[kMaxServe];
     unsigned long long *desc_mc[kMaxServe];
+    unsigned long long *desc_occ[kMaxServe];
     uint32_t cand_cap;                // room of each candidate list
 };
 
@@ -62,7 +63,10 @@ __global__ void __launch_bounds__(kThreads) serve_prep_kernel(ServeArgs a) {
     for (uint32_t j = 0; j < a.k; j++) {
         for (uint32_t i = tid; i < a.base.n_cull_desc; i += stride) a.desc_cand[j][i] = 0;
         const uint32_t n_mc = a.ctl[j]->mc_tiles;      // descriptors the request slot's last scan used
-        for (uint32_t i = tid; i < n_mc; i += stride) a.desc_mc[j][i] = 0;
+        for (uint32_t i = tid; i < n_mc; i += stride) {
+            a.desc_mc[j][i] = 0;
+            a.desc_occ[j][i] = 0;
+        }
     }
     if (tid == 0) {
         Ctl *c = s.ctl;
@@ -231,7 +235,8 @@ struct Done {
 struct Slot {                           // device state of one request position in a tick
     Ctl *ctl = nullptr;
     uint32_t *icand = nullptr, *counts = nullptr;
-    unsigned long long *offsets = nullptr, *desc_cand = nullptr, *desc_mc = nullptr;
+    unsigned long long *offsets = nullptr, *desc_cand = nullptr, *desc_mc = nullptr, *desc_occ = nullptr;
+    uint32_t *iocc = nullptr;
 };
 
 }  // namespace
@@ -270,6 +275,7 @@ ServeArgs serve_args(const iso_server *sv, const std::vector<Request> &reqs) {
         a.icand[j] = sv->slots[j].icand;
         a.desc_cand[j] = sv->slots[j].desc_cand;
         a.desc_mc[j] = sv->slots[j].desc_mc;
+        a.desc_occ[j] = sv->slots[j].desc_occ;
     }
     a.cand_cap = sv->cand_cap;
     return a;
@@ -281,7 +287,7 @@ void free_server(iso_server *sv) {
     for (auto &kv : sv->done)
         if (kv.second.mesh.d_vertices) dfree_on(kv.second.mesh.d_vertices, sv->stream);
     for (Slot &s : sv->slots) {
-        void *p[] = {s.ctl, s.icand, s.counts, s.offsets, s.desc_cand, s.desc_mc};
+        void *p[] = {s.ctl, s.icand, s.counts, s.offsets, s.desc_cand, s.desc_mc, s.iocc};
         for (void *x : p) dfree_on(x, sv->stream);
     }
     cudaStreamSynchronize(sv->stream);
@@ -401,7 +407,7 @@ int emit_next(iso_server *sv, uint32_t *completed) {
             return ISO_OK;
         }
     }
-    *sv->h_params = Params{r.iso, kVertexFloat4, 0u, 0u, c.n_tri, (unsigned long long)(uintptr_t)buf};
+    *sv->h_params = Params{r.iso, kVertexFloat4, 0u, 0u, 0u, 0u, c.n_tri, (unsigned long long)(uintptr_t)buf};
     ISO_CK(cudaMemcpyAsync(&dctl->params, sv->h_params, sizeof(Params), cudaMemcpyHostToDevice, st));
     launch_mc_emit(L, false, sv->view_plan, st);
     ISO_CK(cudaGetLastError());
@@ -447,7 +453,9 @@ int iso_server_create(iso_server **out, iso_volume *v, const iso_server_options 
         TRY(dalloc_on(&s.counts, cand, sv->device, sv->stream));
         TRY(dalloc_on(&s.offsets, cand, sv->device, sv->stream));
         TRY(dalloc_on(&s.desc_cand, v->n_cull_desc, sv->device, sv->stream));
-        TRY(dalloc_on(&s.desc_mc, n_mc_desc, sv->device, sv->stream));
+        TRY(dalloc_on(&s.desc_mc, 2 * n_mc_desc, sv->device, sv->stream));
+        s.desc_occ = s.desc_mc + n_mc_desc;
+        TRY(dalloc_on(&s.iocc, cand, sv->device, sv->stream));
         DevState d = v->s;                // the volume's cache and geometry, the request's own lists
         d.ctl = s.ctl;
         d.icand = s.icand;
@@ -455,6 +463,8 @@ int iso_server_create(iso_server **out, iso_volume *v, const iso_server_options 
         d.offsets = s.offsets;
         d.desc_cand = s.desc_cand;
         d.desc_mc = s.desc_mc;
+        d.desc_occ = s.desc_occ;
+        d.iocc = s.iocc;
         d.cases = nullptr;                // a request's emit classifies (no per-request case store)
         sv->views[j] = VolEntry{d, v->g, v->n_cull_desc, v->n_lru_desc};
     }
@@ -469,7 +479,7 @@ int iso_server_create(iso_server **out, iso_volume *v, const iso_server_options 
     for (uint32_t j = 0; ok && j < sv->max_batch; j++) {
         ok = cudaMemsetAsync(sv->slots[j].ctl, 0, sizeof(Ctl), st) == cudaSuccess &&
              cudaMemsetAsync(sv->slots[j].icand, 0, cand * 4, st) == cudaSuccess &&
-             cudaMemsetAsync(sv->slots[j].desc_mc, 0, n_mc_desc * 8, st) == cudaSuccess;
+             cudaMemsetAsync(sv->slots[j].desc_mc, 0, n_mc_desc * 16, st) == cudaSuccess;
     }
     ok = ok && cudaStreamSynchronize(st) == cudaSuccess;
     if (!ok) {

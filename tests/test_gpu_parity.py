@@ -448,3 +448,50 @@ def test_all_blocks_baseline_equals_extraction(kind, dims, rate):
     finally:
         a.release()
         b.release()
+
+
+# ---------------------------------------------------------------- over budget: waves
+
+def test_over_budget_extraction_in_waves():
+    p = pkg()
+    t = torch()
+    dims, rate = (40, 36, 96), 8
+    f = fields.gradient_noise(*dims, 6, octaves=4, base_period=16)
+    bits, bmin, bmax = oracle.encode_volume(f, rate)
+    d = oracle.decode_volume(bits, dims, rate)
+    nbx, nby, nbz = oracle.block_dims(dims)
+    iso = float(np.median(d))
+    act = oracle.active_blocks(bmin, bmax, (nbx, nby, nbz), iso).reshape(nbz, nby * nbx).sum(axis=1)
+    budget = int(max(act[z] + (act[z + 1] if z + 1 < nbz else 0) for z in range(nbz))) + 5
+    assert act.sum() > budget                                    # one pass cannot hold the surface
+    small = p.Volume(bits, dims, rate, bmin, bmax, cache_budget_bytes=256 * budget)
+    full = p.Volume(bits, dims, rate, bmin, bmax)
+    try:
+        ref = full.extract(iso)
+        T = ref.num_triangles
+        want = ref.vertices.cpu().numpy().view(np.uint32)
+        out = t.zeros((T, 3, 4), dtype=t.float32, device="cuda")
+        st = small.extract_into(iso, out)
+        assert st["waves"] > 1 and st["num_triangles"] == T and st["n_active"] == int(act.sum())
+        assert np.array_equal(out.cpu().numpy().reshape(-1, 4).view(np.uint32), want)
+        # the library-allocated path, twice (its first guess is the last size)
+        for _ in range(2):
+            m = small.extract(iso)
+            assert m.stats["waves"] > 1
+            assert np.array_equal(m.vertices.cpu().numpy().view(np.uint32), want)
+            m.release()
+        # the oracle agrees too (positions, blocks, count)
+        oref = oracle.extract(bits, dims, rate, bmin, bmax, iso)
+        assert oref["num_triangles"] == T
+        v = out.cpu().numpy()
+        assert np.abs(v[:, :, :3].astype(np.float64) - oref["local_pos"]).max() < POS_TOL
+        # too small for one layer and the next: refused
+        tiny = p.Volume(bits, dims, rate, bmin, bmax, cache_budget_bytes=256 * 10)
+        with pytest.raises(p.IsoError) as e:
+            tiny.extract(iso)
+        assert e.value.code == p.ISO_ERR_BUDGET
+        tiny.release()
+        ref.release()
+    finally:
+        small.release()
+        full.release()
