@@ -182,13 +182,15 @@ def profile_traffic(kernel_file, kernel):
 def stage_bytes(stats, rate, nb):
     """Algorithmic bytes each kernel must move for one surface."""
     na, nn, nc, T = stats["n_active"], stats["n_new"], stats["n_candidates"], stats["num_triangles"]
+    no = stats["n_occupied"]
     return {
         "cull": 8 * nb + nb / 8 + 4 * na + 4 * nn + 8 * na + 4 * nc,   # hulls, mask, I_active, I_new, +group hulls, I_cand
         "cache_update": 0.0,
         "decode": nn * (8 * rate + 256 + 8),                           # compressed in, decoded out, I_new + slot
-        "count": nc * (256 + 4 + 4),                                   # decoded tiles in, id in, count out
-        "scan": nc * (4 + 8),                                          # counts in, offsets out
-        "emit": nc * (256 + 4 + 8) + 48 * T,                           # decoded tiles, id, offset in; vertices out
+        "count": nc * (256 + 4 + 4 + 64),                              # decoded tiles in, id in, count and cases out
+        "scan": nc * (4 + 8) + 4 * no,                                 # counts in, offsets and I_occ out
+        "emit": no * (256 + 4 + 4 + 8 + 64) + 48 * T,                  # per occupied block: decoded tile, I_occ, id,
+                                                                       # offset, cases in; vertices out
     }
 
 

@@ -113,11 +113,14 @@ __device__ __forceinline__ void decode_block(const uint64_t *__restrict__ w, uin
     const uint32_t end = rate * 64u;
     uint32_t pos = 9;
     uint32_t n = 0;                        // coefficients reached by the group tests
-    // One group test per iteration, preceded at the start of a plane by the
-    // plane's verbatim bits (predicated, so every lane runs the same
-    // instructions).  Lanes of a warp decode different blocks; a single
-    // loop of uniform steps keeps them together even when their planes hold
-    // different numbers of group tests.
+    // Up to kTests group tests per iteration, preceded at the start of a
+    // plane by the plane's verbatim bits (predicated, so every lane runs the
+    // same instructions; a lane whose plane has ended sits out the rest of
+    // the iteration).  Lanes of a warp decode different blocks; one loop of
+    // uniform steps keeps them together even when their planes hold
+    // different numbers of group tests, and several tests per step spread
+    // the step's fixed cost.
+    constexpr int kTests = 3;
     int k = 31;                            // plane number, most significant first
     uint64_t x = 0;
     bool opening = true;
@@ -142,7 +145,9 @@ __device__ __forceinline__ void decode_block(const uint64_t *__restrict__ w, uin
         // a plane ends after its verbatim bits when every coefficient is
         // reached or the budget is spent (otherwise n < 64 and pos < end)
         bool plane_done = n >= 64 || pos >= end;
-        if (!plane_done) {
+#pragma unroll
+        for (int test = 0; test < kTests; test++) {
+            if (plane_done) continue;
             const uint64_t win = bw.peek(pos);
             pos += 1;
             if (!(win & 1ull)) {           // no later coefficient has a one here
