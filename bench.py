@@ -53,7 +53,7 @@ CPU_WINDOW = (256, 256, 128)      # oracle sample: a window of the same field
 CPU_ORIGIN = (128, 128, 192)
 REF_WINDOW = (128, 128, 64)       # per-step sample of the reference arm
 L2_FLUSH_BYTES = 512 << 20
-CTL_BYTES = 128                   # control block read back once per surface
+CTL_BYTES = 136                   # control block (struct Ctl) read back once per surface
 KERNELS_PER_SURFACE = 8           # prep, cull, lru_a, lru_b, decode, count, scan, emit
 KERNELS_PER_RESET = 2
 KERNELS = ("cull", "cache_update", "decode", "count", "scan", "emit")
@@ -445,6 +445,44 @@ def run_ours(args):
                           "codes + block id), with per-kernel events on"}
         del outp
 
+        # the same steps writing the within-block indexed mesh (NEXT-3), both
+        # vertex formats: sized by one pass, then timed like the packed ones
+        empty_v = torch.empty((0, 4), dtype=torch.float32, device="cuda")
+        empty_i = torch.empty((0, 3), dtype=torch.int32, device="cuda")
+        vmax = max(vol.extract_indexed_into(iso, empty_v, empty_i, check=False)["num_vertices"] for iso in ISOS)
+        idx_buf = torch.empty((tmax + 1024, 3), dtype=torch.int32, device="cuda")
+        indexed = {}
+        for fmt, width, dt, vbytes in (("float4", 4, torch.float32, 16), ("packed", 2, torch.int32, 8)):
+            vbuf = torch.empty((vmax + 1024, width), dtype=dt, device="cuda")
+            vol.set_profiling(True)
+            i_ms, i_emit, i_count, i_tris, i_verts = 0.0, 0.0, 0.0, 0, 0
+            for _ in range(prof_steps):
+                flush.zero_()
+                vol.cache_reset()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for iso in ISOS:
+                    st = vol.extract_indexed_into(iso, vbuf, idx_buf)
+                    ms = vol.stage_times()
+                    i_emit += ms["emit"]
+                    i_count += ms["count"]
+                    i_tris += st["num_triangles"]
+                    i_verts += st["num_vertices"]
+                e1.record(stream)
+                torch.cuda.synchronize()
+                i_ms += e0.elapsed_time(e1)
+            vol.set_profiling(False)
+            n_s = prof_steps * len(ISOS)
+            indexed[fmt] = {"triangles_per_s": i_tris / (i_ms / 1000.0), "ms_per_step": i_ms / prof_steps,
+                            "emit_ms_per_surface": i_emit / n_s, "count_ms_per_surface": i_count / n_s,
+                            "vertices_per_triangle": i_verts / i_tris,
+                            "bytes_per_triangle": (i_verts * vbytes + 12 * i_tris) / i_tris}
+            del vbuf
+        del idx_buf
+        indexed["what"] = ("the same cold-cache 5-isovalue steps writing the indexed mesh: one vertex per cut edge "
+                           "of each block's window, uint32 index triples, per-kernel events on")
+
         # the full-volume baselines of the paper's comparisons: decode every block
         # into a dense field; and the extraction with the range test off (every
         # block decoded into the cache and visited, from an empty cache)
@@ -563,6 +601,7 @@ def run_ours(args):
                      "alg_bytes_per_launch": stage_b[dominant] / n_launch},
         "roofline_cold_extraction": cold,
         "packed_vertices": packed,
+        "indexed_mesh": indexed,
         "full_volume_baselines": baselines,
         "batch64": batch,
         "stages": stages,

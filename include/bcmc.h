@@ -92,6 +92,7 @@ typedef struct iso_stats {
                                   blocks the triangle stage visits */
     uint32_t waves;            /* passes: 1, or the number of waves of an extraction whose active
                                   blocks exceed the cache (see iso_extract) */
+    uint64_t num_vertices;     /* vertices of an indexed mesh (iso_extract_indexed_into); else 0 */
 } iso_stats;
 
 typedef struct iso_mesh {
@@ -157,6 +158,37 @@ int iso_extract_into(iso_volume *v, float isovalue, float *d_vertices, uint64_t 
  * iso_extract_into. */
 int iso_extract_packed_into(iso_volume *v, float isovalue, uint32_t *d_vertices, uint64_t capacity_triangles,
                             iso_stats *stats);
+
+/* Vertex formats of iso_extract_indexed_into */
+#define ISO_VERTEX_FLOAT4 0    /* float4 {x, y, z block-local in [0, 4], w = block id bits}: 16 bytes */
+#define ISO_VERTEX_PACKED 1    /* uint32 {qx | qy << 10 | qz << 20, block id}: 8 bytes (see
+                                  iso_extract_packed_into for the codes) */
+
+/* The indexed mesh Section 4.5 names as the alternative to the triangle
+ * soup: vertices shared within each block (Flying Edges style, per block).
+ * A block's vertices are the cut edges of its 5x5x5 sample window (edges
+ * of its cells inside the volume whose two samples lie on opposite sides
+ * of the isovalue), one vertex each; a vertex on a block face appears once
+ * in every block whose cells use it.  Blocks come in ascending id (the
+ * candidate order), a block's vertices in ascending global edge id
+ * (3 * (x + nx*(y + ny*z)) + axis of the lower sample), and each vertex
+ * holds the same position as the triangle soup's vertices on that edge
+ * (bit for bit, in either format).  Triangles come in the soup's order, as
+ * three uint32 indices into the vertex buffer, so that gathering the
+ * vertices by index gives iso_extract_into's (or, packed,
+ * iso_extract_packed_into's) output.
+ *   d_vertices   capacity_vertices vertices of vertex_format (16 or 8 bytes)
+ *   d_indices    3 * capacity_triangles uint32
+ * Device pointers owned by the caller.  stats->num_vertices and
+ * stats->num_triangles give V and T; if either buffer is too small, only
+ * what fits is written and ISO_ERR_CAPACITY is returned (the cache update
+ * stands), as also when V exceeds 2^32 - 1 (uint32 indices).  Waves as in
+ * iso_extract: the waves' vertices and triangles are appended in order.
+ * Same errors as iso_extract_into; ISO_ERR_INVALID_ARG for another
+ * vertex_format. */
+int iso_extract_indexed_into(iso_volume *v, float isovalue, int vertex_format, void *d_vertices,
+                             uint64_t capacity_vertices, uint32_t *d_indices, uint64_t capacity_triangles,
+                             iso_stats *stats);
 
 /* The full-volume baseline the paper measures against (the naive
  * data-parallel marching cubes of Section 3 over the whole decompressed
@@ -406,7 +438,8 @@ void iso_server_destroy(iso_server *s);
 #define ISO_DBG_SLOT_LAST_USE 5 /* uint32[n_slots]  epoch of last use (0 = never) */
 #define ISO_DBG_ACTIVE_MASK 6  /* uint32[ceil(nb/32)] M_active bitmask */
 #define ISO_DBG_CELL_CASES 7   /* uint8[n_cand*64] case of each cell of each candidate block */
-#define ISO_DBG_BLOCK_TRIS 8   /* uint32[n_cand]    triangles per candidate block */
+#define ISO_DBG_BLOCK_TRIS 8   /* uint32[n_cand]    triangles per candidate block (after an indexed
+                                  extraction, bits 16-31 hold the block's vertices) */
 #define ISO_DBG_BLOCK_OFFSETS 9 /* uint64[n_cand]   exclusive prefix of BLOCK_TRIS */
 #define ISO_DBG_EDGE_IDS 10    /* uint64[3*T]       global edge id of each vertex:
                                   3*(x + nx*(y + ny*z)) + axis of its lower sample */

@@ -17,6 +17,9 @@ Parity status of each function (what pins it, see ``tests/test_oracle_*``):
               watertightness and Euler characteristic
   active      brute force: every block touched by a crossing cell is active
   mc_blocks   equals mc_full reordered by block
+  indexed_mesh  gathers back to the soup exactly; a block's vertices are
+              the cut edges of its window found by brute force; welded over
+              blocks, a sphere stays closed with Euler characteristic 2
   LRUCache    invariants of the cache on random and sweep sequences
 """
 from __future__ import annotations
@@ -250,6 +253,29 @@ def quantized_vertices(field, iso, edge_ids, tri_block, dims):
         codes |= q << np.uint32(10 * k)
     out = np.stack([codes, blk.astype(np.uint32)], axis=1)
     return out.reshape(-1, 3, 2)
+
+
+def indexed_mesh(edge_ids, tri_block, local_pos):
+    """The within-block indexed mesh (Section 4.5 names it as the
+    alternative to the triangle soup: vertices shared inside each block) of
+    a block-ordered soup.
+
+    A block's vertices are the distinct global edge ids its triangles use,
+    in ascending order; blocks follow the soup's (ascending) block order; a
+    triangle corner becomes the index of its (block, edge) vertex.  Returns
+    a dict: vertex_edge (V,) uint64, vertex_block (V,) uint32, vertex_pos
+    (V, 3) float64 block-local (the position of the vertex's first corner
+    in the soup), indices (T, 3) int64."""
+    e = np.asarray(edge_ids, np.uint64).reshape(-1)
+    blk = np.repeat(np.asarray(tri_block, np.uint64), 3)
+    pos = np.asarray(local_pos, np.float64).reshape(-1, 3)
+    if len(e) == 0:
+        return dict(vertex_edge=np.zeros(0, np.uint64), vertex_block=np.zeros(0, np.uint32),
+                    vertex_pos=np.zeros((0, 3)), indices=np.zeros((0, 3), np.int64))
+    pairs = np.stack([blk, e], axis=1)
+    uniq, first, inv = np.unique(pairs, axis=0, return_index=True, return_inverse=True)
+    return dict(vertex_edge=uniq[:, 1].copy(), vertex_block=uniq[:, 0].astype(np.uint32),
+                vertex_pos=pos[first], indices=inv.reshape(-1, 3).astype(np.int64))
 
 
 # ---------------------------------------------------------------- cache (Algorithm 1)

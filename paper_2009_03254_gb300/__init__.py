@@ -28,6 +28,8 @@ ISO_PENDING = 7
 ISO_INPUT_ON_DEVICE = 1
 ISO_DEBUG = 2
 ISO_NO_GRAPH = 4
+ISO_VERTEX_FLOAT4 = 0
+ISO_VERTEX_PACKED = 1
 
 DBG = {
     "active_ids": (1, np.uint32), "new_ids": (2, np.uint32), "slot_of_block": (3, np.int32),
@@ -52,7 +54,7 @@ class _Stats(ctypes.Structure):
     _fields_ = [("num_triangles", ctypes.c_uint64), ("n_active", ctypes.c_uint32), ("n_new", ctypes.c_uint32),
                 ("n_occupied", ctypes.c_uint32), ("n_slots", ctypes.c_uint32), ("cache_bytes", ctypes.c_uint64),
                 ("epoch", ctypes.c_uint32), ("reruns", ctypes.c_uint32), ("n_candidates", ctypes.c_uint32),
-                ("waves", ctypes.c_uint32)]
+                ("waves", ctypes.c_uint32), ("num_vertices", ctypes.c_uint64)]
 
     def as_dict(self):
         return {name: int(getattr(self, name)) for name, _ in self._fields_}
@@ -95,6 +97,7 @@ def lib():
             "iso_extract_into": (i32, [P, ctypes.c_float, P, u64, ctypes.POINTER(_Stats)]),
             "iso_extract_packed_into": (i32, [P, ctypes.c_float, P, u64, ctypes.POINTER(_Stats)]),
             "iso_extract_all_blocks_into": (i32, [P, ctypes.c_float, P, u64, ctypes.POINTER(_Stats)]),
+            "iso_extract_indexed_into": (i32, [P, ctypes.c_float, i32, P, u64, P, u64, ctypes.POINTER(_Stats)]),
             "iso_decode_volume": (i32, [P, u32, u32, u32, u32, P, P]),
             "iso_mesh_release": (i32, [P, ctypes.POINTER(_Mesh)]),
             "iso_release": (None, [P]),
@@ -282,6 +285,49 @@ class Volume:
         d = st.as_dict()
         d["status"] = rc
         return d
+
+    def extract_indexed_into(self, iso, vertices, indices, check=True):
+        """The indexed mesh (vertices shared within each block) into CUDA
+        tensors: `vertices` float32 (V, 4) {x, y, z block-local, block id
+        bits} or int32/uint32 (V, 2) compact vertices (the format follows the
+        tensor), `indices` int32/uint32 (C, 3) for C triangles.  Gathering
+        the vertices by index gives the triangle soup of extract_into (or
+        extract_packed_into).  Returns the stats dict (num_vertices,
+        num_triangles, status)."""
+        import torch
+        packed = vertices.dtype != torch.float32
+        width = 2 if packed else 4
+        assert vertices.is_cuda and vertices.is_contiguous() and vertices.numel() % width == 0
+        assert indices.is_cuda and indices.is_contiguous() and indices.element_size() == 4
+        st = _Stats()
+        rc = lib().iso_extract_indexed_into(self._h, ctypes.c_float(iso),
+                                            ISO_VERTEX_PACKED if packed else ISO_VERTEX_FLOAT4,
+                                            _ptr(vertices), vertices.numel() // width, _ptr(indices),
+                                            indices.numel() // 3, ctypes.byref(st))
+        if check:
+            _check(rc, "iso_extract_indexed_into")
+        d = st.as_dict()
+        d["status"] = rc
+        return d
+
+    def extract_indexed(self, iso, packed=False, guess_triangles=1 << 16):
+        """The indexed mesh in buffers of its exact size: (vertices (V, 4)
+        float32 or (V, 2) int32, indices (T, 3) int32, stats).  A first
+        extraction into buffers of `guess_triangles` tells the sizes; when
+        they were too small the extraction runs again into exact ones."""
+        import torch
+        width, dt = (2, torch.int32) if packed else (4, torch.float32)
+        cap = max(1, int(guess_triangles))
+        verts = torch.empty((cap, width), dtype=dt, device="cuda")
+        idx = torch.empty((cap, 3), dtype=torch.int32, device="cuda")
+        st = self.extract_indexed_into(iso, verts, idx, check=False)
+        if st["status"] == ISO_ERR_CAPACITY and st["num_vertices"] <= 0xFFFFFFFF:
+            nv, nt = max(1, st["num_vertices"]), max(1, st["num_triangles"])
+            verts = torch.empty((nv, width), dtype=dt, device="cuda")
+            idx = torch.empty((nt, 3), dtype=torch.int32, device="cuda")
+            st = self.extract_indexed_into(iso, verts, idx, check=False)
+        _check(st["status"], "iso_extract_indexed_into")
+        return verts[:st["num_vertices"]], idx[:st["num_triangles"]], st
 
     STAGES = ("prep", "cull", "cache_update", "decode", "count", "scan", "emit")
 

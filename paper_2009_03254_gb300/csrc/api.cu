@@ -149,6 +149,7 @@ void fill_stats(const Ctl &c, iso_stats *st, uint32_t reruns) {
     st->reruns = reruns;
     st->n_candidates = c.n_cand;
     st->waves = 1;
+    st->num_vertices = 0;
 }
 
 }  // namespace bcmc_host
@@ -181,14 +182,17 @@ int free_volume(iso_volume *v) {
     DevState &s = v->s;
     void *ptrs[] = {v->bits, v->bmin, v->bmax, v->hull, v->hull8, v->tables, s.mactive, s.iactive, s.inew, s.icand,
                     s.islot, s.slast, s.sblock, s.lbuf[0], s.lbuf[1], s.newslot, s.slots, s.desc_cull, s.desc_cand,
-                    s.desc_lru_a, s.desc_lru_b, s.desc_mc, s.ctl, s.counts, s.offsets, s.iocc, s.cases, s.dbg_edges};
+                    s.desc_lru_a, s.desc_lru_b, s.desc_mc, s.ctl, s.counts, s.offsets, s.iocc, s.cases, s.dbg_edges,
+                    s.voff};
     for (void *p : ptrs) dfree_on(p, v->stream);
     cudaStreamSynchronize(v->stream);
     (void)cudaGetLastError();
     if (v->host_ctl) cudaFreeHost(v->host_ctl);
     if (v->host_params) cudaFreeHost(v->host_params);
-    if (v->gexec) cudaGraphExecDestroy(v->gexec);
-    if (v->graph) cudaGraphDestroy(v->graph);
+    for (int k = 0; k < 2; k++) {
+        if (v->gexec[k]) cudaGraphExecDestroy(v->gexec[k]);
+        if (v->graph[k]) cudaGraphDestroy(v->graph[k]);
+    }
     if (v->capture_stream) cudaStreamDestroy(v->capture_stream);
     for (cudaEvent_t &e : v->ev)
         if (e) cudaEventDestroy(e);
@@ -201,19 +205,19 @@ int free_volume(iso_volume *v) {
 // copy the control block out.  With mc_only, only the triangle stage runs
 // again (after a larger output buffer was supplied).  Events between the
 // stages are recorded when profiling (never inside a captured graph).
-int enqueue_pipeline(iso_volume *v, cudaStream_t st, bool mc_only, bool prof) {
+int enqueue_pipeline(iso_volume *v, cudaStream_t st, bool mc_only, bool prof, bool indexed) {
     const bool debug = (v->flags & ISO_DEBUG) != 0;
     const Launch L{nullptr, 1u, single_counters(v), VolEntry{v->s, v->g, v->n_cull_desc, v->n_lru_desc}};
     CK(cudaMemcpyAsync(&v->s.ctl->params, v->host_params, sizeof(Params), cudaMemcpyHostToDevice, st));
     if (prof) cudaEventRecord(v->ev[0], st);
     if (!mc_only) {
         launch_front(L, v->plan, st, prof ? v->ev : nullptr);
-        launch_mc_count(L, debug, v->plan, st);
+        launch_mc_count(L, debug, v->plan, st, indexed);
         if (prof) cudaEventRecord(v->ev[5], st);
         launch_mc_scan(L, v->plan, st);
         if (prof) cudaEventRecord(v->ev[6], st);
     }
-    launch_mc_emit(L, debug, v->plan, st);
+    launch_mc_emit(L, debug, v->plan, st, indexed);
     if (prof) cudaEventRecord(v->ev[7], st);
     CK(cudaMemcpyAsync(v->host_ctl, v->s.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
     CK(cudaGetLastError());
@@ -224,11 +228,12 @@ int enqueue_pipeline(iso_volume *v, cudaStream_t st, bool mc_only, bool prof) {
 // default stream cannot be captured); launches then go to the volume's
 // stream.  Every per-extraction input comes through Params, so the graph
 // never needs updating.
-int ensure_graph(iso_volume *v) {
-    if (v->gexec) return ISO_OK;
-    CK(cudaStreamCreateWithFlags(&v->capture_stream, cudaStreamNonBlocking));
+int ensure_graph(iso_volume *v, bool indexed) {
+    const int k = indexed ? 1 : 0;
+    if (v->gexec[k]) return ISO_OK;
+    if (!v->capture_stream) CK(cudaStreamCreateWithFlags(&v->capture_stream, cudaStreamNonBlocking));
     CK(cudaStreamBeginCapture(v->capture_stream, cudaStreamCaptureModeThreadLocal));
-    const int rc = enqueue_pipeline(v, v->capture_stream, false, false);
+    const int rc = enqueue_pipeline(v, v->capture_stream, false, false, indexed);
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(v->capture_stream, &g);
     if (rc != ISO_OK || e != cudaSuccess) {
@@ -236,13 +241,13 @@ int ensure_graph(iso_volume *v) {
         (void)cudaGetLastError();
         return rc != ISO_OK ? rc : ISO_ERR_CUDA;
     }
-    if (cudaGraphInstantiate(&v->gexec, g, 0) != cudaSuccess) {
+    if (cudaGraphInstantiate(&v->gexec[k], g, 0) != cudaSuccess) {
         cudaGraphDestroy(g);
-        v->gexec = nullptr;
+        v->gexec[k] = nullptr;
         (void)cudaGetLastError();
         return ISO_ERR_CUDA;
     }
-    v->graph = g;
+    v->graph[k] = g;
     return ISO_OK;
 }
 
@@ -277,21 +282,46 @@ struct Window {                    // a wave: block ids [lo, act_hi) may be acti
     uint32_t lo, cand_hi, act_hi;
 };
 
+struct Indexed {                   // indexed-mesh outputs of one pass
+    uint32_t *idx;                 // 3 * cap_tris indices
+    unsigned long long vert_cap;   // vertices the vertex buffer holds
+    unsigned long long vtx_base;   // added to every index
+};
+
+// the first-vertex array of the occupied candidates, made at the first
+// indexed extraction
+int ensure_voff(iso_volume *v) {
+    if (v->s.voff) return ISO_OK;
+    return dalloc(v, &v->s.voff, v->s.list_cap);
+}
+
 int run(iso_volume *v, float iso, void *out, unsigned long long cap_tris, bool mc_only,
-        uint32_t format = kVertexFloat4, uint32_t flags = 0, const Window *w = nullptr) {
+        uint32_t format = kVertexFloat4, uint32_t flags = 0, const Window *w = nullptr,
+        const Indexed *ix = nullptr) {
     int rc = ensure_debug_edges(v, cap_tris);
     if (rc) return rc;
-    *v->host_params = Params{iso, format, flags | (w ? (uint32_t)kParamWindow : 0u), w ? w->lo : 0u,
-                             w ? w->cand_hi : 0u, w ? w->act_hi : 0u, cap_tris, (unsigned long long)(uintptr_t)out};
+    if (ix && (rc = ensure_voff(v)) != ISO_OK) return rc;
+    *v->host_params = Params{iso,
+                             format,
+                             flags | (w ? (uint32_t)kParamWindow : 0u) | (ix ? (uint32_t)kParamIndexed : 0u),
+                             w ? w->lo : 0u,
+                             w ? w->cand_hi : 0u,
+                             w ? w->act_hi : 0u,
+                             cap_tris,
+                             (unsigned long long)(uintptr_t)out,
+                             ix ? (unsigned long long)(uintptr_t)ix->idx : 0ull,
+                             ix ? ix->vert_cap : 0ull,
+                             ix ? ix->vtx_base : 0ull};
     // the graph is captured at the second extraction: a volume extracted
     // once does not pay for capturing and instantiating it
+    const bool indexed = ix != nullptr;
     const bool graph = !mc_only && v->use_graph && !(v->flags & ISO_DEBUG) && !v->profiling && v->extractions > 0;
     if (!mc_only) v->extractions++;
-    if (graph && ensure_graph(v) != ISO_OK) v->use_graph = false;   // fall back to plain launches
-    if (graph && v->gexec) {
-        CK(cudaGraphLaunch(v->gexec, v->stream));
+    if (graph && ensure_graph(v, indexed) != ISO_OK) v->use_graph = false;   // fall back to plain launches
+    if (graph && v->gexec[indexed ? 1 : 0]) {
+        CK(cudaGraphLaunch(v->gexec[indexed ? 1 : 0], v->stream));
     } else {
-        rc = enqueue_pipeline(v, v->stream, mc_only, v->profiling && !mc_only);
+        rc = enqueue_pipeline(v, v->stream, mc_only, v->profiling && !mc_only, indexed);
         if (rc) return rc;
     }
     CK(cudaStreamSynchronize(v->stream));
@@ -303,6 +333,7 @@ int run(iso_volume *v, float iso, void *out, unsigned long long cap_tris, bool m
         v->last_slots = v->host_ctl->S;
     }
     v->last_tris = v->host_ctl->n_tri;
+    v->last_vtx = indexed ? v->host_ctl->n_vtx : 0ull;
     return status_to_error(v, v->host_ctl->status);
 }
 
@@ -313,7 +344,7 @@ int run(iso_volume *v, float iso, void *out, unsigned long long cap_tris, bool m
 // restricted to its block-id window; the waves' triangles are appended in
 // order, which is the single-pass order (ascending block id).
 int run_waves(iso_volume *v, float iso, void *out, unsigned long long cap_tris, uint32_t format,
-              unsigned long long *total, iso_stats *st) {
+              unsigned long long *total, iso_stats *st, const Indexed *ix) {
     const Geom &g = v->g;
     const uint32_t slab = g.nbx * g.nby;
     std::vector<uint32_t> layer(g.nbz);
@@ -344,24 +375,36 @@ int run_waves(iso_volume *v, float iso, void *out, unsigned long long cap_tris, 
         waves.emplace_back(z, z1);
         z = z1;
     }
-    const size_t vbytes = format == kVertexPacked ? 24 : 48;
-    unsigned long long tot = 0;
+    // bytes a triangle (soup) or a vertex (indexed) takes in `out`
+    const size_t vbytes = ix ? (format == kVertexPacked ? 8 : 16) : (format == kVertexPacked ? 24 : 48);
+    unsigned long long tot = 0, vtot = 0;
     uint64_t n_active = 0, n_new = 0, n_cand = 0, n_occ = 0;
     for (uint32_t z = 0; z < g.nbz; z++) n_active += layer[z];
     for (const auto &wz : waves) {
         const Window w{wz.first * slab, std::min(g.nb, wz.second * slab), std::min(g.nb, (wz.second + 1) * slab)};
         const unsigned long long room = cap_tris > tot ? cap_tris - tot : 0ull;
-        void *wout = (out && room) ? static_cast<char *>(out) + tot * vbytes : nullptr;
-        const int rc = run(v, iso, wout, room, false, format, 0u, &w);
+        int rc;
+        if (ix) {
+            // this wave's vertices follow the earlier waves' and its indices count them
+            const unsigned long long vroom = ix->vert_cap > vtot ? ix->vert_cap - vtot : 0ull;
+            const Indexed wx{(ix->idx && room) ? ix->idx + 3 * tot : nullptr, vroom, ix->vtx_base + vtot};
+            void *wout = (out && vroom) ? static_cast<char *>(out) + vtot * vbytes : nullptr;
+            rc = run(v, iso, wout, wx.idx ? room : 0ull, false, format, 0u, &w, &wx);
+        } else {
+            void *wout = (out && room) ? static_cast<char *>(out) + tot * vbytes : nullptr;
+            rc = run(v, iso, wout, room, false, format, 0u, &w);
+        }
         if (rc) return rc;
         const Ctl &c = *v->host_ctl;
         tot += c.n_tri;
+        vtot += ix ? c.n_vtx : 0ull;
         n_new += c.n_new;
         n_cand += c.n_cand;
         n_occ += c.n_occ;
     }
     *total = tot;
     v->last_tris = tot;
+    v->last_vtx = vtot;
     if (st) {
         fill_stats(*v->host_ctl, st, 0);
         st->num_triangles = tot;
@@ -370,6 +413,7 @@ int run_waves(iso_volume *v, float iso, void *out, unsigned long long cap_tris, 
         st->n_candidates = (uint32_t)std::min<uint64_t>(n_cand, 0xFFFFFFFFu);
         st->n_occupied = (uint32_t)std::min<uint64_t>(n_occ, 0xFFFFFFFFu);
         st->waves = (uint32_t)waves.size();
+        st->num_vertices = vtot;
     }
     return ISO_OK;
 }
@@ -377,11 +421,15 @@ int run_waves(iso_volume *v, float iso, void *out, unsigned long long cap_tris, 
 // One extraction into a caller buffer: a single pass, or waves when the
 // surface's active blocks exceed the cache.  *total receives T.
 int extract_to(iso_volume *v, float iso, void *out, unsigned long long cap_tris, uint32_t format, uint32_t flags,
-               iso_stats *stats, unsigned long long *total) {
-    int rc = run(v, iso, out, cap_tris, false, format, flags);
-    if (rc == ISO_ERR_BUDGET && !(flags & kParamAllBlocks)) return run_waves(v, iso, out, cap_tris, format, total, stats);
+               iso_stats *stats, unsigned long long *total, const Indexed *ix = nullptr) {
+    int rc = run(v, iso, out, cap_tris, false, format, flags, nullptr, ix);
+    if (rc == ISO_ERR_BUDGET && !(flags & kParamAllBlocks))
+        return run_waves(v, iso, out, cap_tris, format, total, stats, ix);
     *total = v->host_ctl->n_tri;
-    if (stats) fill_stats(*v->host_ctl, stats, 0);
+    if (stats) {
+        fill_stats(*v->host_ctl, stats, 0);
+        stats->num_vertices = ix ? v->host_ctl->n_vtx : 0ull;
+    }
     return rc;
 }
 
@@ -485,8 +533,10 @@ int iso_load_volume(iso_volume **out, const void *compressed, size_t compressed_
     TRY(dalloc(v, &s.desc_cand, v->n_cull_desc));
     TRY(dalloc(v, &s.desc_lru_a, v->n_lru_desc));
     TRY(dalloc(v, &s.desc_lru_b, v->n_lru_desc));
-    TRY(dalloc(v, &s.desc_mc, 2 * (size_t)n_mc_desc));   // triangle offsets, then occupied counts
+    // triangle offsets, then occupied counts, then vertex offsets (indexed meshes)
+    TRY(dalloc(v, &s.desc_mc, 3 * (size_t)n_mc_desc));
     s.desc_occ = s.desc_mc + n_mc_desc;
+    s.desc_vtx = s.desc_occ + n_mc_desc;
     TRY(dalloc(v, &s.ctl, 1));
     TRY(dalloc(v, &s.counts, v->cap));
     TRY(dalloc(v, &s.offsets, v->cap));
@@ -531,7 +581,7 @@ int iso_load_volume(iso_volume **out, const void *compressed, size_t compressed_
     TRYC(cudaMemsetAsync(s.sblock, 0xFF, (size_t)v->cap * 4, st));
     TRYC(cudaMemsetAsync(s.slast, 0, (size_t)v->cap * 4, st));
     TRYC(cudaMemsetAsync(s.mactive, 0, (size_t)nwords * 4, st));
-    TRYC(cudaMemsetAsync(s.desc_mc, 0, (size_t)n_mc_desc * 16, st));
+    TRYC(cudaMemsetAsync(s.desc_mc, 0, (size_t)n_mc_desc * 24, st));
     // index lists start as valid ids, so that even a pass cut short by a
     // device-side timeout only ever indexes inside the volume and the cache
     if (s.iactive) TRYC(cudaMemsetAsync(s.iactive, 0, (size_t)s.list_cap * 4, st));
@@ -580,6 +630,25 @@ int iso_extract_all_blocks_into(iso_volume *v, float isovalue, float *d_vertices
     return total > capacity_triangles ? ISO_ERR_CAPACITY : ISO_OK;
 }
 
+int iso_extract_indexed_into(iso_volume *v, float isovalue, int vertex_format, void *d_vertices,
+                             uint64_t capacity_vertices, uint32_t *d_indices, uint64_t capacity_triangles,
+                             iso_stats *stats) {
+    if (!v || !std::isfinite(isovalue) || (!d_vertices && capacity_vertices) || (!d_indices && capacity_triangles) ||
+        (vertex_format != ISO_VERTEX_FLOAT4 && vertex_format != ISO_VERTEX_PACKED))
+        return ISO_ERR_INVALID_ARG;
+    DeviceGuard dg(v->device);
+    unsigned long long total = 0;
+    const Indexed ix{d_indices, capacity_vertices, 0ull};
+    const uint32_t format = vertex_format == ISO_VERTEX_PACKED ? kVertexPacked : kVertexFloat4;
+    iso_stats local{};
+    iso_stats *st = stats ? stats : &local;
+    const int rc = extract_to(v, isovalue, d_vertices, capacity_triangles, format, 0u, st, &total, &ix);
+    if (rc) return rc;
+    // indices are uint32
+    if (st->num_vertices > 0xFFFFFFFFull) return ISO_ERR_CAPACITY;
+    return (total > capacity_triangles || st->num_vertices > capacity_vertices) ? ISO_ERR_CAPACITY : ISO_OK;
+}
+
 int iso_decode_volume(const uint64_t *d_bits, uint32_t nx, uint32_t ny, uint32_t nz, uint32_t rate_bits,
                       float *d_field, void *stream) {
     if (!d_bits || !d_field) return ISO_ERR_INVALID_ARG;
@@ -618,14 +687,14 @@ int iso_extract(iso_volume *v, float isovalue, iso_mesh *out) {
     uint32_t reruns = 0;
     if (rc == ISO_ERR_BUDGET) {           // too many active blocks for the cache: waves
         unsigned long long total = 0;
-        rc = run_waves(v, isovalue, buf, guess, kVertexFloat4, &total, &out->stats);
+        rc = run_waves(v, isovalue, buf, guess, kVertexFloat4, &total, &out->stats, nullptr);
         if (rc == ISO_OK && total > guess) {   // the waves again into a buffer of the right size
             cudaFreeAsync(buf, v->stream);
             buf = nullptr;
             const int arc = dalloc(v, &buf, std::max(total, 1ull) * 3);
             if (arc) return arc;
             guess = std::max(total, 1ull);
-            rc = run_waves(v, isovalue, buf, guess, kVertexFloat4, &total, &out->stats);
+            rc = run_waves(v, isovalue, buf, guess, kVertexFloat4, &total, &out->stats, nullptr);
             out->stats.reruns = 1;
         }
         if (rc) {

@@ -67,6 +67,8 @@ enum ParamFlags : uint32_t {
     kParamAllBlocks = 1u,         // no range test: every block is active and a candidate
     kParamWindow = 2u,            // a wave: only blocks with ids in [win_lo, win_act_hi) may be active,
                                   // only those in [win_lo, win_cand_hi) candidates
+    kParamIndexed = 4u,           // indexed mesh: one vertex per cut edge of each block's window,
+                                  // triangles as three uint32 vertex indices
 };
 
 struct Params {
@@ -76,6 +78,10 @@ struct Params {
     uint32_t win_lo, win_cand_hi, win_act_hi;
     unsigned long long tri_cap;   // output capacity in triangles
     unsigned long long out;       // vertex buffer (float4 * or uint2 *)
+    // indexed mesh only (kParamIndexed)
+    unsigned long long idx_out;   // uint32 index buffer, 3 per triangle
+    unsigned long long vert_cap;  // vertex buffer capacity in vertices
+    unsigned long long vtx_base;  // added to every index (vertices of earlier waves)
 };
 
 // One per volume, in device memory.  Written only by the kernels of one
@@ -100,6 +106,7 @@ struct Ctl {
     uint32_t mc_tiles;        // look-back descriptors the triangle kernel used (to clear)
     uint32_t ctr[kNumLaunchCounters];   // work counters when the volume is extracted alone
     unsigned long long n_tri; // triangles of the surface
+    unsigned long long n_vtx; // vertices of the indexed mesh (indexed extractions only)
 };
 
 // ---------------------------------------------------------------- memory-model helpers

@@ -40,6 +40,7 @@ __global__ void __launch_bounds__(kThreads) prep_kernel(Launch L) {
         for (uint32_t i = tid; i < n_mc_desc; i += stride) {
             s.desc_mc[i] = 0;
             s.desc_occ[i] = 0;
+            if (s.desc_vtx) s.desc_vtx[i] = 0;
         }
         for (uint32_t i = tid; i < e.n_cull_desc; i += stride) {
             s.desc_cull[i] = 0;
@@ -60,6 +61,7 @@ __global__ void __launch_bounds__(kThreads) prep_kernel(Launch L) {
         c->status = 0;
         c->n_occ = 0;
         c->n_tri = 0;
+        c->n_vtx = 0;
     }
     if (tid < kNumLaunchCounters) L.ctr[tid] = 0;
 }

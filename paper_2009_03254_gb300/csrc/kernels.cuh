@@ -33,6 +33,10 @@ struct DevState {
     unsigned long long *offsets; // exclusive prefix of counts: first triangle of each candidate
     uint32_t *iocc;            // I_occ: positions in the candidate list of the occupied candidates (ascending)
     unsigned long long *desc_occ;  // look-back descriptors of the occupied count (next to desc_mc)
+    unsigned long long *desc_vtx;  // look-back descriptors of the vertex count (next to desc_occ; null
+                                   // where indexed meshes are never made)
+    unsigned long long *voff;      // indexed mesh: first vertex of each occupied candidate (null until
+                                   // the first indexed extraction)
     uint8_t *cases;            // 64 cell cases per candidate, written by the count pass and read by
                                // emit instead of classifying again (null: emit classifies)
     // debug copy (null unless the volume was loaded with ISO_DEBUG)
@@ -90,9 +94,9 @@ void launch_front(const Launch &L, const Plan &pl, cudaStream_t st, cudaEvent_t 
 void launch_cache_update(const Launch &L, const Plan &pl, cudaStream_t st);
 // triangle stage: count, scan, emit.  A batch places the volumes' outputs
 // between scan and emit; a rerun into a larger output runs emit alone.
-void launch_mc_count(const Launch &L, bool debug, const Plan &pl, cudaStream_t st);
+void launch_mc_count(const Launch &L, bool debug, const Plan &pl, cudaStream_t st, bool indexed = false);
 void launch_mc_scan(const Launch &L, const Plan &pl, cudaStream_t st);
-void launch_mc_emit(const Launch &L, bool debug, const Plan &pl, cudaStream_t st);
+void launch_mc_emit(const Launch &L, bool debug, const Plan &pl, cudaStream_t st, bool indexed = false);
 // batches: per-volume isovalues from a packed array; the volumes' outputs
 // placed one after another in `bo->out` (tri_base[v] = first triangle of
 // volume v, tri_base[n] = total); control blocks gathered for one readback

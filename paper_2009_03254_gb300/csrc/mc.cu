@@ -30,6 +30,19 @@
 //
 // Over a batch, warp tiles are numbered volume after volume; a warp tile
 // never spans two volumes.
+//
+// Indexed mesh (the alternative output Section 4.5 mentions: vertices
+// shared within a block).  A block's vertices are the cut edges of its
+// 5x5x5 window: edges between two window samples, exactly one of them
+// below the isovalue, that belong to at least one of the block's cells
+// inside the volume.  The case table uses every cut edge of a cell, so
+// these are exactly the edges the block's triangles use.  An edge is named
+// by its lower sample s = x + 5y + 25z and its axis a, and a block's
+// vertices are ordered by 3s + a, which inside one block is the order of
+// the global edge id.  Count adds the number of cut edges (three shifts
+// of the 125-bit below mask, XOR, popcount), scan a third prefix sum, and
+// emit writes each vertex once (its position by the same arithmetic as the
+// triangle soup) and each triangle corner as the rank of its edge.
 #include <algorithm>
 #include <cstdint>
 
@@ -60,7 +73,7 @@ struct CountSmem {
     uint8_t num_tri[256];
 };
 
-template <int kW>
+template <int kW, bool kIdx>
 struct EmitSmem {
     WarpTile w[kW];
     float4 stage[kW][96];                             // 32 triangles' vertices per warp
@@ -68,6 +81,7 @@ struct EmitSmem {
     uint32_t tri_row[256 * kMaxTriPerCell];           // 3 edge numbers of each table triangle, packed
     uint8_t num_tri[256];
     uint32_t edge_info[12];
+    uint32_t cut[kIdx ? kW : 1][kBPW][16];            // indexed: cut-edge words (3 x 4), then word bases
 };
 
 // Halo load job j of a block (0..63; 50 used): neighbour o, source sample
@@ -142,6 +156,47 @@ __device__ __forceinline__ uint32_t case_bits(uint32_t W) {
     return (W & 3u) | ((W >> 3) & 0xCu) | ((W >> 21) & 0x30u) | ((W >> 24) & 0xC0u);
 }
 
+// the 128-bit below-iso mask of a staged block: bit i of word r says
+// sample s = 32r + i (s = x + 5y + 25z, s < 125) is below the isovalue
+__device__ __forceinline__ void below_mask(const float *hb, const LaneConst &lc, float iso, uint32_t m[4]) {
+#pragma unroll
+    for (int r = 0; r < 4; r++) m[r] = __ballot_sync(0xffffffffu, lc.cls[r] >= 0 && hb[lc.cls[r]] < iso);
+}
+
+// Window rows: word r of row k of axis a has bit i set when sample
+// s = 32r + i (s < 125) has coordinate <= k - 1 along a (row 0: none).
+struct WindowRows {
+    uint32_t w[3][6][4];
+};
+
+__host__ __device__ constexpr WindowRows make_window_rows() {
+    WindowRows t{};
+    for (int a = 0; a < 3; a++)
+        for (int k = 0; k < 6; k++)
+            for (int s = 0; s < 125; s++) {
+                const int c = a == 0 ? s % 5 : (a == 1 ? (s / 5) % 5 : s / 25);
+                if (c <= k - 1) t.w[a][k][s >> 5] |= 1u << (s & 31);
+            }
+    return t;
+}
+
+__constant__ WindowRows kWindowRows = make_window_rows();
+
+// One word of a block's cut edges, from its below mask m: bit i is set
+// when the edge from sample 32r + i along axis a (steps 1, 5, 25) crosses
+// the isovalue and belongs to one of the block's cells inside the volume
+// (lim: cells per axis inside, 4 bits each).  Such an edge exists when
+// every axis has a cell; its samples lie in [0, l] on the other axes and
+// it starts below l along its own.  Warp-uniform inputs and output.
+__device__ __forceinline__ uint32_t cut_word(const uint32_t m[4], int r, int a, uint32_t lim) {
+    const int step = a == 0 ? 1 : (a == 1 ? 5 : 25);
+    const uint32_t far = __funnelshift_r(m[r], r < 3 ? m[r + 1] : 0u, step);   // bit i: sample s + step
+    const uint32_t lx = lim & 15u, ly = (lim >> 4) & 15u, lz = lim >> 8;
+    const uint32_t win = kWindowRows.w[0][a == 0 ? lx : lx + 1][r] & kWindowRows.w[1][a == 1 ? ly : ly + 1][r] &
+                         kWindowRows.w[2][a == 2 ? lz : lz + 1][r];
+    return (lx && ly && lz) ? (m[r] ^ far) & win : 0u;
+}
+
 // Phases A-C for the warp tile starting at candidate `base` (count pass)
 // or at occupied candidate `base` (emit pass), nb_w of kBPW slots used.
 // Returns the per-cell triangle counts of the lane's two cells, packed one
@@ -151,11 +206,14 @@ __device__ __forceinline__ uint32_t case_bits(uint32_t W) {
 // the stored ones instead of classifying again when there are any.  `b` is
 // this lane's block (block lane/8 of the tile) and `ci` its position in
 // the candidate list, loaded by the caller one warp tile ahead.
+//
+// With `indexed` (count pass only), nv_lane receives, in lane q, the number
+// of cut edges (vertices of the indexed mesh) of block q.
 template <bool kEmit>
 __device__ __forceinline__ void stage_and_classify(const DevState &s, const Geom &g, float iso, uint32_t base,
                                                    int nb_w, uint32_t b, uint32_t ci, WarpTile &wt,
                                                    const LaneConst &lc, const uint8_t *num_tri, uint32_t &n0p,
-                                                   uint32_t &n1p) {
+                                                   uint32_t &n1p, bool indexed, uint32_t &nv_lane) {
     const int lane = threadIdx.x & 31, bq = lane >> 3, bo = lane & 7;
     const uint32_t slab = g.nbx * g.nby;
     const bool stored = kEmit && s.cases != nullptr;      // uniform
@@ -229,10 +287,8 @@ __device__ __forceinline__ void stage_and_classify(const DevState &s, const Geom
             cs[0] = wt.cases[q][lane];
             cs[1] = wt.cases[q][lane + 32];
         } else {
-            const float *hb = &wt.halo[q][0];
             uint32_t m[4];
-#pragma unroll
-            for (int r = 0; r < 4; r++) m[r] = __ballot_sync(0xffffffffu, lc.cls[r] >= 0 && hb[lc.cls[r]] < iso);
+            below_mask(&wt.halo[q][0], lc, iso, m);
             const uint32_t lim = wt.lim[q];
 #pragma unroll
             for (int h = 0; h < 2; h++) {
@@ -252,6 +308,14 @@ __device__ __forceinline__ void stage_and_classify(const DevState &s, const Geom
             if (!kEmit && s.cases) {      // uniform: keep them for the emit pass
 #pragma unroll
                 for (int h = 0; h < 2; h++) s.cases[(size_t)(base + q) * 64 + lane + 32 * h] = (uint8_t)cs[h];
+            }
+            if (!kEmit && indexed) {      // uniform
+                uint32_t nv = 0;
+#pragma unroll
+                for (int r = 0; r < 4; r++)
+#pragma unroll
+                    for (int a = 0; a < 3; a++) nv += __popc(cut_word(m, r, a, lim));
+                if (lane == q) nv_lane = nv;
             }
         }
 #pragma unroll
@@ -305,7 +369,7 @@ __device__ __forceinline__ TileRef locate_tile(const Launch &L, const uint32_t *
 
 // ================================================================ count (Section 4.4)
 
-template <int kW, bool kOne>
+template <int kW, bool kOne, bool kIdx>
 __global__ void __launch_bounds__(32 * kW, 32 / kW) mc_count_kernel(Launch L) {   // 1024 threads per SM
     extern __shared__ __align__(16) unsigned char smem_raw[];
     CountSmem<kW> &sm = *reinterpret_cast<CountSmem<kW> *>(smem_raw);
@@ -327,12 +391,12 @@ __global__ void __launch_bounds__(32 * kW, 32 / kW) mc_count_kernel(Launch L) { 
         nxt = locate_tile<kOne>(L, pre, t + stride, total);   // next warp tile's block, loaded early
         const DevState &s = vol_of<kOne>(L, cur.v).s;
         const float iso = s.ctl->params.iso;
-        uint32_t n0p, n1p;
+        uint32_t n0p, n1p, nv = 0;
         stage_and_classify<false>(s, vol_of<kOne>(L, cur.v).g, iso, cur.base, (int)cur.nb_w, cur.b, 0u, wt, lc,
-                                  sm.num_tri, n0p, n1p);
+                                  sm.num_tri, n0p, n1p, kIdx, nv);
         const uint32_t r0 = warp_sum(n0p), r1 = warp_sum(n1p);   // per-byte sums <= 160: no carries
-        if (lane < (int)cur.nb_w)
-            s.counts[cur.base + lane] = ((r0 >> (8 * lane)) & 0xFFu) + ((r1 >> (8 * lane)) & 0xFFu);
+        if (lane < (int)cur.nb_w)       // triangles (<= 320) in the low 16 bits, vertices (<= 300) above
+            s.counts[cur.base + lane] = ((r0 >> (8 * lane)) & 0xFFu) + ((r1 >> (8 * lane)) & 0xFFu) + (nv << 16);
     }
 }
 
@@ -349,8 +413,8 @@ template <int kPT, bool kOne>
 __global__ void __launch_bounds__(kThreads) mc_scan_kernel(Launch L) {
     constexpr int kWarps = kThreads / 32;
     constexpr uint32_t kScanItems = kThreads * kPT;
-    __shared__ uint32_t wsum[kWarps], wocc[kWarps];
-    __shared__ unsigned long long s_excl[2];
+    __shared__ uint32_t wsum[kWarps], wocc[kWarps], wvtx[kWarps];
+    __shared__ unsigned long long s_excl[3];
     __shared__ uint32_t pre[kMaxBatch + 1];
     __shared__ uint32_t s_item;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -371,30 +435,41 @@ __global__ void __launch_bounds__(kThreads) mc_scan_kernel(Launch L) {
         const uint32_t ntiles = ceil_div(n, kScanItems);
         if (tile == 0 && threadIdx.x == 0) c->mc_tiles = ntiles;
         if (ntiles == 0) continue;                        // block-uniform
+        const bool indexed = (c->params.flags & kParamIndexed) != 0;   // block-uniform
         const uint32_t i0 = tile * kScanItems + threadIdx.x * kPT;
-        uint32_t v8[kPT], sum = 0, occ = 0;
+        uint32_t v8[kPT], sum = 0, occ = 0, vsum = 0;
 #pragma unroll
         for (int k = 0; k < kPT; k++) {
-            v8[k] = i0 + k < n ? s.counts[i0 + k] : 0u;
-            sum += v8[k];
-            occ += v8[k] != 0u;
+            v8[k] = i0 + k < n ? s.counts[i0 + k] : 0u;   // triangles | vertices << 16
+            sum += v8[k] & 0xFFFFu;
+            vsum += v8[k] >> 16;
+            occ += (v8[k] & 0xFFFFu) != 0u;
         }
         // triangles in the low 20 bits, occupied candidates above (a warp
         // holds at most 32 * 16 * 320 triangles and 512 candidates: no carry)
         const uint32_t own = sum | (occ << 20);
-        uint32_t incl = own;
+        uint32_t incl = own, vincl = vsum;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += t;
         }
+        if (indexed) {
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, vincl, o);
+                if (lane >= o) vincl += t;
+            }
+        }
         if (lane == 31) {
             wsum[warp] = incl & 0xFFFFFu;
             wocc[warp] = incl >> 20;
+            wvtx[warp] = vincl;
         }
         __syncthreads();
-        if (warp < 2) {                   // warp 0: triangle offsets; warp 1: occupied positions
-            uint32_t *ws = warp == 0 ? wsum : wocc;
+        // warp 0: triangle offsets; warp 1: occupied positions; warp 2: vertex offsets
+        if (warp < 2 || (warp == 2 && indexed)) {
+            uint32_t *ws = warp == 0 ? wsum : (warp == 1 ? wocc : wvtx);
             const uint32_t w = lane < kWarps ? ws[lane] : 0u;
             uint32_t wi = w;
 #pragma unroll
@@ -404,13 +479,14 @@ __global__ void __launch_bounds__(kThreads) mc_scan_kernel(Launch L) {
             }
             const uint32_t tot = __shfl_sync(0xffffffffu, wi, kWarps - 1);
             if (lane < kWarps) ws[lane] = wi - w;                        // exclusive warp offsets
-            const unsigned long long excl = lookback_exclusive(warp == 0 ? s.desc_mc : s.desc_occ, tile, tot,
-                                                               &c->status, kStatusTimeoutScan);
+            unsigned long long *desc = warp == 0 ? s.desc_mc : (warp == 1 ? s.desc_occ : s.desc_vtx);
+            const unsigned long long excl = lookback_exclusive(desc, tile, tot, &c->status, kStatusTimeoutScan);
             if (lane == 0) {
                 s_excl[warp] = excl;
                 if (tile == ntiles - 1) {
                     if (warp == 0) c->n_tri = excl + tot;
-                    else c->n_occ = (uint32_t)(excl + tot);
+                    else if (warp == 1) c->n_occ = (uint32_t)(excl + tot);
+                    else c->n_vtx = excl + tot;
                 }
             }
         }
@@ -418,21 +494,35 @@ __global__ void __launch_bounds__(kThreads) mc_scan_kernel(Launch L) {
         const uint32_t before = incl - own;                              // this thread's exclusive prefix in the warp
         unsigned long long run = s_excl[0] + wsum[warp] + (before & 0xFFFFFu);
         uint32_t orun = (uint32_t)s_excl[1] + wocc[warp] + (before >> 20);
+        if (indexed) {
+            unsigned long long vrun = s_excl[2] + wvtx[warp] + (vincl - vsum);
 #pragma unroll
-        for (int k = 0; k < kPT; k++) {
-            if (i0 + k < n) s.offsets[i0 + k] = run;
-            if (v8[k]) s.iocc[orun++] = i0 + k;
-            run += v8[k];
+            for (int k = 0; k < kPT; k++) {
+                if (i0 + k < n) s.offsets[i0 + k] = run;
+                if (v8[k] & 0xFFFFu) {
+                    s.voff[orun] = vrun;
+                    s.iocc[orun++] = i0 + k;
+                }
+                run += v8[k] & 0xFFFFu;
+                vrun += v8[k] >> 16;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < kPT; k++) {
+                if (i0 + k < n) s.offsets[i0 + k] = run;
+                if (v8[k]) s.iocc[orun++] = i0 + k;
+                run += v8[k];
+            }
         }
     }
 }
 
 // ================================================================ emit (Section 4.5)
 
-template <int kW, bool kDebug, bool kOne>
+template <int kW, bool kDebug, bool kOne, bool kIdx>
 __global__ void __launch_bounds__(32 * kW) mc_emit_kernel(Launch L) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    EmitSmem<kW> &sm = *reinterpret_cast<EmitSmem<kW> *>(smem_raw);
+    EmitSmem<kW, kIdx> &sm = *reinterpret_cast<EmitSmem<kW, kIdx> *>(smem_raw);
     __shared__ uint32_t pre[kMaxBatch + 1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint8_t *tables = vol_of<kOne>(L, 0).s.tables;
@@ -477,8 +567,8 @@ __global__ void __launch_bounds__(32 * kW) mc_emit_kernel(Launch L) {
         float4 *__restrict__ out = reinterpret_cast<float4 *>(c->params.out);
         const uint32_t base = cur.base;
         const int nb_w = (int)cur.nb_w;
-        uint32_t n0p, n1p;
-        stage_and_classify<true>(s, g, iso, base, nb_w, cur.b, cur.ci, wt, lc, sm.num_tri, n0p, n1p);
+        uint32_t n0p, n1p, unused = 0;
+        stage_and_classify<true>(s, g, iso, base, nb_w, cur.b, cur.ci, wt, lc, sm.num_tri, n0p, n1p, false, unused);
         // consecutive occupied candidates have adjacent outputs (the empty
         // ones between them add nothing): the tile starts at its first block's
         const uint32_t first_ci = __shfl_sync(0xffffffffu, cur.ci, 0);
@@ -504,10 +594,94 @@ __global__ void __launch_bounds__(32 * kW) mc_emit_kernel(Launch L) {
         }
         if (wtot == 0) continue;                       // warp-uniform
         const unsigned long long gbase = s.offsets[first_ci];
+        unsigned long long vt = 0;                     // indexed: the tile's first vertex
+        if constexpr (kIdx) {
+            // cut-edge words of each block and, per word, the vertices before it
+            // in the tile (the block's earlier words and the earlier blocks)
+            vt = s.voff[base];
+            uint32_t acc = 0;
+            for (int q = 0; q < nb_w; q++) {
+                uint32_t m[4];
+                below_mask(&wt.halo[q][0], lc, iso, m);
+                const uint32_t lim = wt.lim[q];
+                uint32_t *cw = sm.cut[warp][q];
+#pragma unroll
+                for (int r = 0; r < 4; r++) {
+                    const uint32_t c0 = cut_word(m, r, 0, lim), c1 = cut_word(m, r, 1, lim),
+                                   c2 = cut_word(m, r, 2, lim);
+                    if (lane == 0) {
+                        cw[r] = c0;
+                        cw[4 + r] = c1;
+                        cw[8 + r] = c2;
+                        cw[12 + r] = acc;
+                    }
+                    acc += __popc(c0) + __popc(c1) + __popc(c2);
+                }
+            }
+            __syncwarp();
+            // the tile's vertices, 96 at a time through the staging area; lane
+            // i looks at the edges from samples i, i + 32, i + 64, i + 96
+            const uint32_t nvt = acc;
+            const unsigned long long vcap = c->params.vert_cap;
+            const uint32_t lt = (1u << lane) - 1u;
+            for (uint32_t c0 = 0; c0 < nvt; c0 += 96) {
+                for (int q = 0; q < nb_w; q++) {
+                    const uint32_t *cw = sm.cut[warp][q];
+                    const uint32_t vb = cw[12], ve = q + 1 < nb_w ? sm.cut[warp][q + 1][12] : nvt;
+                    if (ve <= c0 || vb >= c0 + 96) continue;   // warp-uniform
+                    const float *hb = &wt.halo[q][0];
+#pragma unroll 1
+                    for (int r = 0; r < 4; r++) {
+                        const uint32_t w0 = cw[r], w1 = cw[4 + r], w2 = cw[8 + r];
+                        const uint32_t b0 = (w0 >> lane) & 1u, b1 = (w1 >> lane) & 1u, b2 = (w2 >> lane) & 1u;
+                        if (!(b0 | b1 | b2)) continue;
+                        const uint32_t rank = cw[12 + r] + __popc(w0 & lt) + __popc(w1 & lt) + __popc(w2 & lt);
+                        const int smp = lane + 32 * r, sx = smp % 5, sy = (smp / 5) % 5, sz = smp / 25;
+                        const int ho = sx + 8 * sy + 40 * sz;          // padded halo offset of the sample
+                        const float vlo = hb[ho];
+#pragma unroll
+                        for (int a = 0; a < 3; a++) {
+                            const uint32_t bit = a == 0 ? b0 : (a == 1 ? b1 : b2);
+                            const uint32_t k = rank + (a > 0 ? b0 : 0u) + (a > 1 ? b1 : 0u) - c0;
+                            if (!bit || k >= 96u) continue;
+                            const float vhi = hb[ho + (a == 0 ? 1 : (a == 1 ? 8 : 40))];
+                            float4 p = make_float4((float)sx, (float)sy, (float)sz, __uint_as_float(wt.bid[q]));
+                            // the triangle soup's arithmetic, vertex for vertex
+                            const float tt = packed ? __fdiv_rn(__fsub_rn(iso, vlo), __fsub_rn(vhi, vlo))
+                                                    : __fdividef(__fsub_rn(iso, vlo), __fsub_rn(vhi, vlo));
+                            if (a == 0) p.x = __fadd_rn(p.x, tt);
+                            else if (a == 1) p.y = __fadd_rn(p.y, tt);
+                            else p.z = __fadd_rn(p.z, tt);
+                            if (!packed) {
+                                stage[k] = p;
+                            } else {
+                                const uint32_t qx = (uint32_t)__float2int_rn(__fmul_rn(p.x, 255.75f));
+                                const uint32_t qy = (uint32_t)__float2int_rn(__fmul_rn(p.y, 255.75f));
+                                const uint32_t qz = (uint32_t)__float2int_rn(__fmul_rn(p.z, 255.75f));
+                                reinterpret_cast<uint2 *>(stage)[k] = make_uint2(qx | (qy << 10) | (qz << 20), wt.bid[q]);
+                            }
+                        }
+                    }
+                }
+                __syncwarp();
+                const uint32_t nv = min(96u, nvt - c0);
+                const unsigned long long v0 = vt + c0;
+#pragma unroll
+                for (int r = 0; r < 3; r++) {
+                    const uint32_t f = lane + 32 * r;
+                    if (f < nv && v0 + f < vcap) {
+                        if (!packed) out[v0 + f] = stage[f];
+                        else reinterpret_cast<uint2 *>(out)[v0 + f] = reinterpret_cast<const uint2 *>(stage)[f];
+                    }
+                }
+                __syncwarp();
+            }
+            vt += c->params.vtx_base;                  // indices count the vertices of earlier waves
+        }
         __syncwarp();
-        // one triangle per lane; its three vertices go through the warp's
-        // staging area so that each store instruction writes 512
-        // contiguous bytes
+        // one triangle per lane; its three vertices (or, indexed, its three
+        // vertex indices) go through the warp's staging area so that each
+        // store instruction writes contiguous bytes
         for (uint32_t t0 = 0; t0 < wtot; t0 += 32) {
             const uint32_t tri = t0 + lane;
             if (tri < wtot) {
@@ -520,32 +694,45 @@ __global__ void __launch_bounds__(32 * kW) mc_emit_kernel(Launch L) {
 #pragma unroll
                 for (int j = 0; j < 3; j++) {
                     const uint32_t info = sm.edge_info[(row >> (8 * j)) & 0xFFu];
-                    const float vlo = hb[info & 0xFFu], vhi = hb[(info >> 8) & 0xFFu];
                     const uint32_t a = (info >> 19) & 3u;
-                    float4 p = make_float4((float)(cx + (int)((info >> 16) & 1u)),
-                                           (float)(cy + (int)((info >> 17) & 1u)),
-                                           (float)(cz + (int)((info >> 18) & 1u)), wbits);
-                    if (!packed) {
-                        // t = (iso - v_lo) / (v_hi - v_lo) through the reciprocal: within
-                        // 2 ulp of the correctly rounded quotient (positions within 1e-6)
-                        const float tt = __fdividef(__fsub_rn(iso, vlo), __fsub_rn(vhi, vlo));
-                        if (a == 0) p.x = __fadd_rn(p.x, tt);
-                        else if (a == 1) p.y = __fadd_rn(p.y, tt);
-                        else p.z = __fadd_rn(p.z, tt);
-                        stage[3 * lane + j] = p;
+                    if constexpr (kIdx) {
+                        // the rank of the edge among the block's cut edges
+                        const int smp = cx + (int)((info >> 16) & 1u) + 5 * (cy + (int)((info >> 17) & 1u)) +
+                                        25 * (cz + (int)((info >> 18) & 1u));
+                        const uint32_t *cw = sm.cut[warp][q];
+                        const int r = smp >> 5, bit = smp & 31;
+                        const uint32_t w0 = cw[r], w1 = cw[4 + r], w2 = cw[8 + r], below = (1u << bit) - 1u;
+                        const uint32_t rank = cw[12 + r] + __popc(w0 & below) + __popc(w1 & below) +
+                                              __popc(w2 & below) + (a > 0 ? (w0 >> bit) & 1u : 0u) +
+                                              (a > 1 ? (w1 >> bit) & 1u : 0u);
+                        reinterpret_cast<uint32_t *>(stage)[3 * lane + j] = (uint32_t)(vt + rank);
                     } else {
-                        // the 10-bit code round(p / 4 * 1023) decides an integer, so every
-                        // step is one IEEE float32 operation (the division correctly
-                        // rounded), as the oracle computes it
-                        const float tt = __fdiv_rn(__fsub_rn(iso, vlo), __fsub_rn(vhi, vlo));
-                        if (a == 0) p.x = __fadd_rn(p.x, tt);
-                        else if (a == 1) p.y = __fadd_rn(p.y, tt);
-                        else p.z = __fadd_rn(p.z, tt);
-                        const uint32_t qx = (uint32_t)__float2int_rn(__fmul_rn(p.x, 255.75f));
-                        const uint32_t qy = (uint32_t)__float2int_rn(__fmul_rn(p.y, 255.75f));
-                        const uint32_t qz = (uint32_t)__float2int_rn(__fmul_rn(p.z, 255.75f));
-                        reinterpret_cast<uint2 *>(stage)[3 * lane + j] = make_uint2(qx | (qy << 10) | (qz << 20),
-                                                                                     wt.bid[q]);
+                        const float vlo = hb[info & 0xFFu], vhi = hb[(info >> 8) & 0xFFu];
+                        float4 p = make_float4((float)(cx + (int)((info >> 16) & 1u)),
+                                               (float)(cy + (int)((info >> 17) & 1u)),
+                                               (float)(cz + (int)((info >> 18) & 1u)), wbits);
+                        if (!packed) {
+                            // t = (iso - v_lo) / (v_hi - v_lo) through the reciprocal: within
+                            // 2 ulp of the correctly rounded quotient (positions within 1e-6)
+                            const float tt = __fdividef(__fsub_rn(iso, vlo), __fsub_rn(vhi, vlo));
+                            if (a == 0) p.x = __fadd_rn(p.x, tt);
+                            else if (a == 1) p.y = __fadd_rn(p.y, tt);
+                            else p.z = __fadd_rn(p.z, tt);
+                            stage[3 * lane + j] = p;
+                        } else {
+                            // the 10-bit code round(p / 4 * 1023) decides an integer, so every
+                            // step is one IEEE float32 operation (the division correctly
+                            // rounded), as the oracle computes it
+                            const float tt = __fdiv_rn(__fsub_rn(iso, vlo), __fsub_rn(vhi, vlo));
+                            if (a == 0) p.x = __fadd_rn(p.x, tt);
+                            else if (a == 1) p.y = __fadd_rn(p.y, tt);
+                            else p.z = __fadd_rn(p.z, tt);
+                            const uint32_t qx = (uint32_t)__float2int_rn(__fmul_rn(p.x, 255.75f));
+                            const uint32_t qy = (uint32_t)__float2int_rn(__fmul_rn(p.y, 255.75f));
+                            const uint32_t qz = (uint32_t)__float2int_rn(__fmul_rn(p.z, 255.75f));
+                            reinterpret_cast<uint2 *>(stage)[3 * lane + j] = make_uint2(qx | (qy << 10) | (qz << 20),
+                                                                                         wt.bid[q]);
+                        }
                     }
                     if (kDebug) {
                         const unsigned long long gt = gbase + tri;
@@ -561,10 +748,18 @@ __global__ void __launch_bounds__(32 * kW) mc_emit_kernel(Launch L) {
                 }
             }
             __syncwarp();
-            const uint32_t nv = 3 * min(32u, wtot - t0);             // vertices in this chunk
-            const unsigned long long v0 = (gbase + t0) * 3;          // first vertex of the chunk
+            const uint32_t nv = 3 * min(32u, wtot - t0);             // vertices (or indices) in this chunk
+            const unsigned long long v0 = (gbase + t0) * 3;          // first of the chunk
             const unsigned long long vcap = tri_cap * 3;
-            if (!packed) {
+            if constexpr (kIdx) {
+                uint32_t *oi = reinterpret_cast<uint32_t *>(c->params.idx_out);
+                const uint32_t *st = reinterpret_cast<const uint32_t *>(stage);
+#pragma unroll
+                for (int r = 0; r < 3; r++) {
+                    const uint32_t f = lane + 32 * r;
+                    if (f < nv && v0 + f < vcap) oi[v0 + f] = st[f];
+                }
+            } else if (!packed) {
 #pragma unroll
                 for (int r = 0; r < 3; r++) {
                     const uint32_t f = lane + 32 * r;
@@ -588,15 +783,16 @@ __global__ void __launch_bounds__(32 * kW) mc_emit_kernel(Launch L) {
 
 namespace {
 
-template <int kW, bool kOne>
+template <int kW, bool kOne, bool kIdx>
 void count_w(const Launch &L, int grid, cudaStream_t st) {
-    mc_count_kernel<kW, kOne><<<grid, 32 * kW, sizeof(CountSmem<kW>), st>>>(L);
+    mc_count_kernel<kW, kOne, kIdx><<<grid, 32 * kW, sizeof(CountSmem<kW>), st>>>(L);
 }
 
-template <int kW, bool kOne>
+template <int kW, bool kOne, bool kIdx>
 void emit_w(const Launch &L, bool debug, int grid, cudaStream_t st) {
-    if (debug) mc_emit_kernel<kW, true, kOne><<<grid, 32 * kW, sizeof(EmitSmem<kW>), st>>>(L);
-    else mc_emit_kernel<kW, false, kOne><<<grid, 32 * kW, sizeof(EmitSmem<kW>), st>>>(L);
+    constexpr size_t bytes = sizeof(EmitSmem<kW, kIdx>);
+    if (debug) mc_emit_kernel<kW, true, kOne, kIdx><<<grid, 32 * kW, bytes, st>>>(L);
+    else mc_emit_kernel<kW, false, kOne, kIdx><<<grid, 32 * kW, bytes, st>>>(L);
 }
 
 template <class K>
@@ -606,39 +802,42 @@ void raise_smem(K kernel, size_t bytes) {
 
 template <int kW>
 int emit_occupancy(bool single) {
-    raise_smem(mc_emit_kernel<kW, false, false>, sizeof(EmitSmem<kW>));
-    raise_smem(mc_emit_kernel<kW, true, false>, sizeof(EmitSmem<kW>));
-    raise_smem(mc_emit_kernel<kW, false, true>, sizeof(EmitSmem<kW>));
-    raise_smem(mc_emit_kernel<kW, true, true>, sizeof(EmitSmem<kW>));
+    raise_smem(mc_emit_kernel<kW, false, false, false>, sizeof(EmitSmem<kW, false>));
+    raise_smem(mc_emit_kernel<kW, true, false, false>, sizeof(EmitSmem<kW, false>));
+    raise_smem(mc_emit_kernel<kW, false, true, false>, sizeof(EmitSmem<kW, false>));
+    raise_smem(mc_emit_kernel<kW, true, true, false>, sizeof(EmitSmem<kW, false>));
+    raise_smem(mc_emit_kernel<kW, false, true, true>, sizeof(EmitSmem<kW, true>));
+    raise_smem(mc_emit_kernel<kW, true, true, true>, sizeof(EmitSmem<kW, true>));
     int occ = 0;
     if (single)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mc_emit_kernel<kW, false, true>, 32 * kW,
-                                                      sizeof(EmitSmem<kW>));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mc_emit_kernel<kW, false, true, false>, 32 * kW,
+                                                      sizeof(EmitSmem<kW, false>));
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mc_emit_kernel<kW, false, false>, 32 * kW,
-                                                      sizeof(EmitSmem<kW>));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mc_emit_kernel<kW, false, false, false>, 32 * kW,
+                                                      sizeof(EmitSmem<kW, false>));
     return occ;
 }
 
 template <int kW>
 int count_occupancy(bool single) {
-    raise_smem(mc_count_kernel<kW, false>, sizeof(CountSmem<kW>));
-    raise_smem(mc_count_kernel<kW, true>, sizeof(CountSmem<kW>));
+    raise_smem(mc_count_kernel<kW, false, false>, sizeof(CountSmem<kW>));
+    raise_smem(mc_count_kernel<kW, true, false>, sizeof(CountSmem<kW>));
+    raise_smem(mc_count_kernel<kW, true, true>, sizeof(CountSmem<kW>));
     int occ = 0;
     if (single)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mc_count_kernel<kW, true>, 32 * kW,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mc_count_kernel<kW, true, false>, 32 * kW,
                                                       sizeof(CountSmem<kW>));
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mc_count_kernel<kW, false>, 32 * kW,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mc_count_kernel<kW, false, false>, 32 * kW,
                                                       sizeof(CountSmem<kW>));
     return occ;
 }
 
-template <bool kOne>
+template <bool kOne, bool kIdx>
 void count_any(const Launch &L, const Plan &pl, cudaStream_t st) {
-    if (pl.count_tile == 16) count_w<4, kOne>(L, pl.mc_count, st);
-    else if (pl.count_tile == 64) count_w<16, kOne>(L, pl.mc_count, st);
-    else count_w<8, kOne>(L, pl.mc_count, st);
+    if (pl.count_tile == 16) count_w<4, kOne, kIdx>(L, pl.mc_count, st);
+    else if (pl.count_tile == 64) count_w<16, kOne, kIdx>(L, pl.mc_count, st);
+    else count_w<8, kOne, kIdx>(L, pl.mc_count, st);
 }
 
 template <bool kOne>
@@ -648,19 +847,20 @@ void scan_any(const Launch &L, const Plan &pl, cudaStream_t st) {
     else mc_scan_kernel<8, kOne><<<pl.mc_scan, kThreads, 0, st>>>(L);
 }
 
-template <bool kOne>
+template <bool kOne, bool kIdx>
 void emit_any(const Launch &L, bool debug, const Plan &pl, cudaStream_t st) {
-    if (pl.emit_tile == 16) emit_w<4, kOne>(L, debug, pl.mc_emit, st);
-    else if (pl.emit_tile == 64) emit_w<16, kOne>(L, debug, pl.mc_emit, st);
-    else emit_w<8, kOne>(L, debug, pl.mc_emit, st);
+    if (pl.emit_tile == 16) emit_w<4, kOne, kIdx>(L, debug, pl.mc_emit, st);
+    else if (pl.emit_tile == 64) emit_w<16, kOne, kIdx>(L, debug, pl.mc_emit, st);
+    else emit_w<8, kOne, kIdx>(L, debug, pl.mc_emit, st);
 }
 
 }  // namespace
 
 // tile = candidates per CTA round = 4 per warp
-void launch_mc_count(const Launch &L, bool /*debug*/, const Plan &pl, cudaStream_t st) {
-    if (L.vols) count_any<false>(L, pl, st);
-    else count_any<true>(L, pl, st);
+void launch_mc_count(const Launch &L, bool /*debug*/, const Plan &pl, cudaStream_t st, bool indexed) {
+    if (L.vols) count_any<false, false>(L, pl, st);
+    else if (indexed) count_any<true, true>(L, pl, st);
+    else count_any<true, false>(L, pl, st);
 }
 
 void launch_mc_scan(const Launch &L, const Plan &pl, cudaStream_t st) {
@@ -668,9 +868,11 @@ void launch_mc_scan(const Launch &L, const Plan &pl, cudaStream_t st) {
     else scan_any<true>(L, pl, st);
 }
 
-void launch_mc_emit(const Launch &L, bool debug, const Plan &pl, cudaStream_t st) {
-    if (L.vols) emit_any<false>(L, debug, pl, st);
-    else emit_any<true>(L, debug, pl, st);
+// the indexed mesh is made for single volumes only
+void launch_mc_emit(const Launch &L, bool debug, const Plan &pl, cudaStream_t st, bool indexed) {
+    if (L.vols) emit_any<false, false>(L, debug, pl, st);
+    else if (indexed) emit_any<true, true>(L, debug, pl, st);
+    else emit_any<true, false>(L, debug, pl, st);
 }
 
 template <int kPT>

@@ -22,8 +22,10 @@ struct iso_volume {
     bcmc::Ctl *host_ctl = nullptr;    // pinned mirror for the one readback
     bcmc::Params *host_params = nullptr;   // pinned: this extraction's isovalue, output and capacity
     cudaStream_t capture_stream = nullptr;
-    cudaGraph_t graph = nullptr;      // one extraction: params copy, the stage kernels, count readback
-    cudaGraphExec_t gexec = nullptr;
+    // one extraction: params copy, the stage kernels, count readback; one
+    // graph per output kind (0: triangle soup, 1: indexed mesh)
+    cudaGraph_t graph[2] = {};
+    cudaGraphExec_t gexec[2] = {};
     bool use_graph = true;
     uint64_t extractions = 0;         // full extractions run so far (the graph is captured at the second)
     // owned device allocations
@@ -32,6 +34,7 @@ struct iso_volume {
     float2 *hull = nullptr, *hull8 = nullptr;
     uint8_t *tables = nullptr;
     unsigned long long dbg_edges_cap = 0;   // in vertices
+    unsigned long long last_vtx = 0;        // vertices of the last indexed extraction
     bool profiling = false;
     cudaEvent_t ev[ISO_NUM_STAGES + 1] = {};
     float stage_ms[ISO_NUM_STAGES] = {};
