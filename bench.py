@@ -53,7 +53,7 @@ CPU_WINDOW = (256, 256, 128)      # oracle sample: a window of the same field
 CPU_ORIGIN = (128, 128, 192)
 REF_WINDOW = (128, 128, 64)       # per-step sample of the reference arm
 L2_FLUSH_BYTES = 512 << 20
-CTL_BYTES = 136                   # control block (struct Ctl) read back once per surface
+CTL_BYTES = 168                   # control block (struct Ctl) read back once per surface
 KERNELS_PER_SURFACE = 8           # prep, cull, lru_a, lru_b, decode, count, scan, emit
 KERNELS_PER_RESET = 2
 KERNELS = ("cull", "cache_update", "decode", "count", "scan", "emit")

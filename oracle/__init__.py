@@ -260,10 +260,12 @@ def indexed_mesh(edge_ids, tri_block, local_pos):
     alternative to the triangle soup: vertices shared inside each block) of
     a block-ordered soup.
 
-    A block's vertices are the distinct global edge ids its triangles use,
-    in ascending order; blocks follow the soup's (ascending) block order; a
-    triangle corner becomes the index of its (block, edge) vertex.  Returns
-    a dict: vertex_edge (V,) uint64, vertex_block (V,) uint32, vertex_pos
+    A block's vertices are the distinct edges its triangles use, ordered by
+    axis (x-edges, then y-, then z-edges) and, within an axis, by the
+    edge's lower sample (x fastest); blocks follow the soup's (ascending)
+    block order; a triangle corner becomes the index of its (block, edge)
+    vertex.  Global edge id = 3 * (x + nx*(y + ny*z)) + axis.  Returns a
+    dict: vertex_edge (V,) uint64, vertex_block (V,) uint32, vertex_pos
     (V, 3) float64 block-local (the position of the vertex's first corner
     in the soup), indices (T, 3) int64."""
     e = np.asarray(edge_ids, np.uint64).reshape(-1)
@@ -272,9 +274,9 @@ def indexed_mesh(edge_ids, tri_block, local_pos):
     if len(e) == 0:
         return dict(vertex_edge=np.zeros(0, np.uint64), vertex_block=np.zeros(0, np.uint32),
                     vertex_pos=np.zeros((0, 3)), indices=np.zeros((0, 3), np.int64))
-    pairs = np.stack([blk, e], axis=1)
-    uniq, first, inv = np.unique(pairs, axis=0, return_index=True, return_inverse=True)
-    return dict(vertex_edge=uniq[:, 1].copy(), vertex_block=uniq[:, 0].astype(np.uint32),
+    keys = np.stack([blk, e % np.uint64(3), e // np.uint64(3)], axis=1)     # sorted lexicographically
+    uniq, first, inv = np.unique(keys, axis=0, return_index=True, return_inverse=True)
+    return dict(vertex_edge=uniq[:, 2] * np.uint64(3) + uniq[:, 1], vertex_block=uniq[:, 0].astype(np.uint32),
                 vertex_pos=pos[first], indices=inv.reshape(-1, 3).astype(np.int64))
 
 

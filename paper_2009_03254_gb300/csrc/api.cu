@@ -183,7 +183,7 @@ int free_volume(iso_volume *v) {
     void *ptrs[] = {v->bits, v->bmin, v->bmax, v->hull, v->hull8, v->tables, s.mactive, s.iactive, s.inew, s.icand,
                     s.islot, s.slast, s.sblock, s.lbuf[0], s.lbuf[1], s.newslot, s.slots, s.desc_cull, s.desc_cand,
                     s.desc_lru_a, s.desc_lru_b, s.desc_mc, s.ctl, s.counts, s.offsets, s.iocc, s.cases, s.dbg_edges,
-                    s.voff};
+                    s.voff, s.cutw};
     for (void *p : ptrs) dfree_on(p, v->stream);
     cudaStreamSynchronize(v->stream);
     (void)cudaGetLastError();
@@ -288,11 +288,15 @@ struct Indexed {                   // indexed-mesh outputs of one pass
     unsigned long long vtx_base;   // added to every index
 };
 
-// the first-vertex array of the occupied candidates, made at the first
-// indexed extraction
+// the first-vertex array of the occupied candidates and the candidates'
+// cut-edge words, made at the first indexed extraction
 int ensure_voff(iso_volume *v) {
-    if (v->s.voff) return ISO_OK;
-    return dalloc(v, &v->s.voff, v->s.list_cap);
+    if (!v->s.voff) {
+        const int rc = dalloc(v, &v->s.voff, v->s.list_cap);
+        if (rc) return rc;
+    }
+    if (!v->s.cutw) return dalloc(v, &v->s.cutw, (size_t)v->s.list_cap * 12);
+    return ISO_OK;
 }
 
 int run(iso_volume *v, float iso, void *out, unsigned long long cap_tris, bool mc_only,

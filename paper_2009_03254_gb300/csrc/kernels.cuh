@@ -37,6 +37,8 @@ struct DevState {
                                    // where indexed meshes are never made)
     unsigned long long *voff;      // indexed mesh: first vertex of each occupied candidate (null until
                                    // the first indexed extraction)
+    uint32_t *cutw;                // indexed mesh: 12 cut-edge words per candidate, written by count and
+                                   // read by emit (null until the first indexed extraction)
     uint8_t *cases;            // 64 cell cases per candidate, written by the count pass and read by
                                // emit instead of classifying again (null: emit classifies)
     // debug copy (null unless the volume was loaded with ISO_DEBUG)

@@ -37,12 +37,14 @@
 // below the isovalue, that belong to at least one of the block's cells
 // inside the volume.  The case table uses every cut edge of a cell, so
 // these are exactly the edges the block's triangles use.  An edge is named
-// by its lower sample s = x + 5y + 25z and its axis a, and a block's
-// vertices are ordered by 3s + a, which inside one block is the order of
-// the global edge id.  Count adds the number of cut edges (three shifts
-// of the 125-bit below mask, XOR, popcount), scan a third prefix sum, and
-// emit writes each vertex once (its position by the same arithmetic as the
-// triangle soup) and each triangle corner as the rank of its edge.
+// by its axis a and lower sample s = x + 5y + 25z; a block's vertices are
+// ordered by a, then s.  The cut edges of one axis form a 125-bit mask:
+// the below mask XOR itself shifted by the axis step (1, 5, 25), limited
+// to the window; lane 4a + r of a warp holds word r of axis a.  Count adds
+// the number of cut edges, scan a third prefix sum, and emit lists the
+// tile's vertices in shared memory, computes one vertex per lane (the
+// triangle soup's arithmetic) and writes each triangle corner as its
+// edge's rank: the vertices before its word plus a popcount.
 #include <algorithm>
 #include <cstdint>
 
@@ -58,6 +60,8 @@ namespace {
 constexpr int kBPW = 4;                               // candidates per warp tile
 constexpr int kHalo = 200;                            // x + 8y + 40z, x,y,z in [0,5)
 constexpr int kTmap = kBPW * 64 * 5;                  // triangles a warp tile can hold
+constexpr int kWinWords = 3 * 6 * 4;                  // window rows (indexed meshes), then
+constexpr int kWinTable = kWinWords + 32;             // a per-lane word for blocks inside the volume
 
 struct WarpTile {                                     // one warp's shared-memory area
     float halo[kBPW][kHalo];
@@ -70,18 +74,22 @@ struct WarpTile {                                     // one warp's shared-memor
 template <int kW>                                     // warps per CTA
 struct CountSmem {
     WarpTile w[kW];
+    uint32_t win[kWinTable];                          // window rows (indexed meshes)
     uint8_t num_tri[256];
 };
 
 template <int kW, bool kIdx>
 struct EmitSmem {
     WarpTile w[kW];
-    float4 stage[kW][96];                             // 32 triangles' vertices per warp
+    float4 stage[kW][kIdx ? 24 : 96];                 // 32 triangles' vertices (indexed: indices) per warp
     uint16_t tmap[kW][kTmap];                         // block-in-tile (2) | cell (6) | k (3)
     uint32_t tri_row[256 * kMaxTriPerCell];           // 3 edge numbers of each table triangle, packed
     uint8_t num_tri[256];
     uint32_t edge_info[12];
-    uint32_t cut[kIdx ? kW : 1][kBPW][16];            // indexed: cut-edge words (3 x 4), then word bases
+    // indexed: per block, the 12 cut-edge words, then (from word 12) the
+    // vertices of the tile before each word
+    alignas(16) uint32_t cut[kIdx ? kW : 1][kBPW][24];
+    uint32_t win[kIdx ? kWinTable : 1];               // window rows
 };
 
 // Halo load job j of a block (0..63; 50 used): neighbour o, source sample
@@ -165,36 +173,53 @@ __device__ __forceinline__ void below_mask(const float *hb, const LaneConst &lc,
 
 // Window rows: word r of row k of axis a has bit i set when sample
 // s = 32r + i (s < 125) has coordinate <= k - 1 along a (row 0: none).
-struct WindowRows {
-    uint32_t w[3][6][4];
-};
-
-__host__ __device__ constexpr WindowRows make_window_rows() {
-    WindowRows t{};
-    for (int a = 0; a < 3; a++)
-        for (int k = 0; k < 6; k++)
-            for (int s = 0; s < 125; s++) {
-                const int c = a == 0 ? s % 5 : (a == 1 ? (s / 5) % 5 : s / 25);
-                if (c <= k - 1) t.w[a][k][s >> 5] |= 1u << (s & 31);
-            }
-    return t;
+__host__ __device__ constexpr uint32_t window_row_word(int a, int k, int r) {
+    uint32_t w = 0;
+    for (int i = 0; i < 32; i++) {
+        const int s = 32 * r + i, c = a == 0 ? s % 5 : (a == 1 ? (s / 5) % 5 : s / 25);
+        if (s < 125 && c <= k - 1) w |= 1u << i;
+    }
+    return w;
 }
 
-__constant__ WindowRows kWindowRows = make_window_rows();
+// copy of the window rows into shared memory (word a*24 + k*4 + r), then
+// at word 72 + lane the window word lane_cut_word takes for a block with
+// all its cells inside the volume (0 for lanes 12-31)
+__device__ __forceinline__ void load_window_rows(uint32_t *win) {
+    for (int i = threadIdx.x; i < kWinTable; i += blockDim.x) {
+        if (i < kWinWords) {
+            win[i] = window_row_word(i / 24, (i / 4) % 6, i % 4);
+        } else {
+            const int k = i - kWinWords, a = k >> 2, r = k & 3;
+            win[i] = k < 12 ? window_row_word(0, a == 0 ? 4 : 5, r) & window_row_word(1, a == 1 ? 4 : 5, r) &
+                                  window_row_word(2, a == 2 ? 4 : 5, r)
+                            : 0u;
+        }
+    }
+}
 
-// One word of a block's cut edges, from its below mask m: bit i is set
-// when the edge from sample 32r + i along axis a (steps 1, 5, 25) crosses
-// the isovalue and belongs to one of the block's cells inside the volume
-// (lim: cells per axis inside, 4 bits each).  Such an edge exists when
-// every axis has a cell; its samples lie in [0, l] on the other axes and
-// it starts below l along its own.  Warp-uniform inputs and output.
-__device__ __forceinline__ uint32_t cut_word(const uint32_t m[4], int r, int a, uint32_t lim) {
-    const int step = a == 0 ? 1 : (a == 1 ? 5 : 25);
-    const uint32_t far = __funnelshift_r(m[r], r < 3 ? m[r + 1] : 0u, step);   // bit i: sample s + step
-    const uint32_t lx = lim & 15u, ly = (lim >> 4) & 15u, lz = lim >> 8;
-    const uint32_t win = kWindowRows.w[0][a == 0 ? lx : lx + 1][r] & kWindowRows.w[1][a == 1 ? ly : ly + 1][r] &
-                         kWindowRows.w[2][a == 2 ? lz : lz + 1][r];
-    return (lx && ly && lz) ? (m[r] ^ far) & win : 0u;
+// This lane's word of a block's cut edges (lanes 0-11: axis lane / 4,
+// word lane % 4; 0 in the other lanes), from the block's below mask m: bit
+// i is set when the edge from sample 32r + i along axis a (steps 1, 5, 25)
+// crosses the isovalue and belongs to one of the block's cells inside the
+// volume (lim: cells per axis inside, 4 bits each).  Such an edge exists
+// when every axis has a cell; its samples lie in [0, l] on the other axes
+// and it starts below l along its own.
+__device__ __forceinline__ uint32_t lane_cut_word(const uint32_t m[4], uint32_t lim, const uint32_t *win) {
+    const int lane = threadIdx.x & 31, a = min(lane >> 2, 2), r = lane & 3;
+    const uint32_t lo = (r & 2) ? ((r & 1) ? m[3] : m[2]) : ((r & 1) ? m[1] : m[0]);
+    const uint32_t hi = (r & 2) ? ((r & 1) ? 0u : m[3]) : ((r & 1) ? m[2] : m[1]);
+    const uint32_t far = __funnelshift_r(lo, hi, a == 0 ? 1 : (a == 1 ? 5 : 25));   // bit i: sample s + step
+    uint32_t w;
+    if (lim == 0x444u) {                                // warp-uniform: the common case
+        w = win[kWinWords + lane];
+    } else {
+        const uint32_t lx = lim & 15u, ly = (lim >> 4) & 15u, lz = lim >> 8;
+        w = win[(a == 0 ? lx : lx + 1) * 4 + r] & win[24 + (a == 1 ? ly : ly + 1) * 4 + r] &
+            win[48 + (a == 2 ? lz : lz + 1) * 4 + r];
+        w = (lane < 12 && lx && ly && lz) ? w : 0u;
+    }
+    return (lo ^ far) & w;
 }
 
 // Phases A-C for the warp tile starting at candidate `base` (count pass)
@@ -208,12 +233,18 @@ __device__ __forceinline__ uint32_t cut_word(const uint32_t m[4], int r, int a, 
 // the candidate list, loaded by the caller one warp tile ahead.
 //
 // With `indexed` (count pass only), nv_lane receives, in lane q, the number
-// of cut edges (vertices of the indexed mesh) of block q.
+// of cut edges (vertices of the indexed mesh) of block q; `win` is the
+// window-row table in shared memory.
+//
+// With `cut_dst` (emit pass of an indexed extraction), the 12 cut-edge
+// words count kept for each of the tile's blocks are copied to
+// cut_dst + 24q (asynchronously, like the cases; the caller waits).
 template <bool kEmit>
 __device__ __forceinline__ void stage_and_classify(const DevState &s, const Geom &g, float iso, uint32_t base,
                                                    int nb_w, uint32_t b, uint32_t ci, WarpTile &wt,
                                                    const LaneConst &lc, const uint8_t *num_tri, uint32_t &n0p,
-                                                   uint32_t &n1p, bool indexed, uint32_t &nv_lane) {
+                                                   uint32_t &n1p, bool indexed, const uint32_t *win,
+                                                   uint32_t &nv_lane, uint32_t *cut_dst = nullptr) {
     const int lane = threadIdx.x & 31, bq = lane >> 3, bo = lane & 7;
     const uint32_t slab = g.nbx * g.nby;
     const bool stored = kEmit && s.cases != nullptr;      // uniform
@@ -222,9 +253,17 @@ __device__ __forceinline__ void stage_and_classify(const DevState &s, const Geom
     // aligned).  The emit pass's blocks are occupied candidates, not
     // consecutive ones: block q's position in the candidate list is `ci` of
     // lane 8q.
-    if (stored) {
-        const uint32_t cq = __shfl_sync(0xffffffffu, ci, (lane >> 2) * 8);
-        if (lane < 4 * nb_w) cp_async16(&wt.cases[lane >> 2][16 * (lane & 3)], s.cases + (size_t)cq * 64 + 16 * (lane & 3));
+    if (stored || (kEmit && cut_dst)) {   // uniform
+        // lanes 0-15: the cases of block lane / 4; lanes 16-27: the cut-edge
+        // words of block (lane - 16) / 3, 16 bytes each
+        const int qk = (cut_dst && lane >= 16) ? min((lane - 16) / 3, 3) : (lane >> 2);
+        const uint32_t cq = __shfl_sync(0xffffffffu, ci, qk * 8);
+        if (stored && lane < 4 * nb_w)
+            cp_async16(&wt.cases[lane >> 2][16 * (lane & 3)], s.cases + (size_t)cq * 64 + 16 * (lane & 3));
+        if (cut_dst && lane >= 16 && lane < 16 + 3 * nb_w) {
+            const int k = (lane - 16) % 3;
+            cp_async16(cut_dst + 24 * qk + 4 * k, s.cutw + (size_t)cq * 12 + 4 * k);
+        }
     }
     // ---- A: +group slots
     if (bq < nb_w) {
@@ -309,13 +348,11 @@ __device__ __forceinline__ void stage_and_classify(const DevState &s, const Geom
 #pragma unroll
                 for (int h = 0; h < 2; h++) s.cases[(size_t)(base + q) * 64 + lane + 32 * h] = (uint8_t)cs[h];
             }
-            if (!kEmit && indexed) {      // uniform
-                uint32_t nv = 0;
-#pragma unroll
-                for (int r = 0; r < 4; r++)
-#pragma unroll
-                    for (int a = 0; a < 3; a++) nv += __popc(cut_word(m, r, a, lim));
+            if (!kEmit && indexed) {      // uniform: count the cut edges, keep the words for emit
+                const uint32_t w = lane_cut_word(m, lim, win);
+                const uint32_t nv = __reduce_add_sync(0xffffffffu, __popc(w));
                 if (lane == q) nv_lane = nv;
+                if (lane < 12) s.cutw[(size_t)(base + q) * 12 + lane] = w;
             }
         }
 #pragma unroll
@@ -377,6 +414,7 @@ __global__ void __launch_bounds__(32 * kW, 32 / kW) mc_count_kernel(Launch L) { 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint8_t *tables = vol_of<kOne>(L, 0).s.tables;
     for (int i = threadIdx.x; i < 256; i += 32 * kW) sm.num_tri[i] = tables[i];
+    if (kIdx) load_window_rows(sm.win);
     const uint32_t total = launch_prefix<kOne>(
         L, [&](uint32_t v) { return ceil_div(mc_candidates(vol_of<kOne>(L, v).s.ctl), kBPW); }, pre);
     __syncthreads();                                      // the table
@@ -393,7 +431,7 @@ __global__ void __launch_bounds__(32 * kW, 32 / kW) mc_count_kernel(Launch L) { 
         const float iso = s.ctl->params.iso;
         uint32_t n0p, n1p, nv = 0;
         stage_and_classify<false>(s, vol_of<kOne>(L, cur.v).g, iso, cur.base, (int)cur.nb_w, cur.b, 0u, wt, lc,
-                                  sm.num_tri, n0p, n1p, kIdx, nv);
+                                  sm.num_tri, n0p, n1p, kIdx, sm.win, nv);
         const uint32_t r0 = warp_sum(n0p), r1 = warp_sum(n1p);   // per-byte sums <= 160: no carries
         if (lane < (int)cur.nb_w)       // triangles (<= 320) in the low 16 bits, vertices (<= 300) above
             s.counts[cur.base + lane] = ((r0 >> (8 * lane)) & 0xFFu) + ((r1 >> (8 * lane)) & 0xFFu) + (nv << 16);
@@ -520,7 +558,7 @@ __global__ void __launch_bounds__(kThreads) mc_scan_kernel(Launch L) {
 // ================================================================ emit (Section 4.5)
 
 template <int kW, bool kDebug, bool kOne, bool kIdx>
-__global__ void __launch_bounds__(32 * kW) mc_emit_kernel(Launch L) {
+__device__ __forceinline__ void emit_body(const Launch &L) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     EmitSmem<kW, kIdx> &sm = *reinterpret_cast<EmitSmem<kW, kIdx> *>(smem_raw);
     __shared__ uint32_t pre[kMaxBatch + 1];
@@ -531,6 +569,7 @@ __global__ void __launch_bounds__(32 * kW) mc_emit_kernel(Launch L) {
         const uint8_t *e = tables + 256 + (i / kMaxTriPerCell) * 16 + 3 * (i % kMaxTriPerCell);
         sm.tri_row[i] = (uint32_t)e[0] | ((uint32_t)e[1] << 8) | ((uint32_t)e[2] << 16);
     }
+    if (kIdx) load_window_rows(sm.win);
     if (threadIdx.x < 12) {
         // edge e: lower corner (dx,dy,dz), axis a; halo offsets of its two samples
         const int e = threadIdx.x, a = e >> 2, j0 = e & 1, j1 = (e >> 1) & 1;
@@ -568,7 +607,8 @@ __global__ void __launch_bounds__(32 * kW) mc_emit_kernel(Launch L) {
         const uint32_t base = cur.base;
         const int nb_w = (int)cur.nb_w;
         uint32_t n0p, n1p, unused = 0;
-        stage_and_classify<true>(s, g, iso, base, nb_w, cur.b, cur.ci, wt, lc, sm.num_tri, n0p, n1p, false, unused);
+        stage_and_classify<true>(s, g, iso, base, nb_w, cur.b, cur.ci, wt, lc, sm.num_tri, n0p, n1p, false, nullptr,
+                                 unused, kIdx ? &sm.cut[warp][0][0] : nullptr);
         // consecutive occupied candidates have adjacent outputs (the empty
         // ones between them add nothing): the tile starts at its first block's
         const uint32_t first_ci = __shfl_sync(0xffffffffu, cur.ci, 0);
@@ -582,101 +622,82 @@ __global__ void __launch_bounds__(32 * kW) mc_emit_kernel(Launch L) {
         const uint32_t s0 = __shfl_sync(0xffffffffu, i0, 31), s1 = __shfl_sync(0xffffffffu, i1, 31);
         uint32_t wtot = 0;
 #pragma unroll
-        for (int q = 0; q < kBPW; q++) {
-            if (q >= nb_w) continue;
-            const uint32_t n0 = (n0p >> (8 * q)) & 0xFFu, n1 = (n1p >> (8 * q)) & 0xFFu;
-            const uint32_t b0 = (s0 >> (8 * q)) & 0xFFu;
-            const uint32_t o0 = wtot + ((i0 >> (8 * q)) & 0xFFu) - n0;
-            const uint32_t o1 = wtot + b0 + ((i1 >> (8 * q)) & 0xFFu) - n1;
-            for (uint32_t k = 0; k < n0; k++) tm[o0 + k] = (uint16_t)((q << 9) | (lane << 3) | k);
-            for (uint32_t k = 0; k < n1; k++) tm[o1 + k] = (uint16_t)((q << 9) | ((lane + 32) << 3) | k);
-            wtot += b0 + ((s1 >> (8 * q)) & 0xFFu);
-        }
+        for (int q = 0; q < kBPW; q++)
+            if (q < nb_w) wtot += ((s0 >> (8 * q)) & 0xFFu) + ((s1 >> (8 * q)) & 0xFFu);
         if (wtot == 0) continue;                       // warp-uniform
         const unsigned long long gbase = s.offsets[first_ci];
         unsigned long long vt = 0;                     // indexed: the tile's first vertex
         if constexpr (kIdx) {
-            // cut-edge words of each block and, per word, the vertices before it
-            // in the tile (the block's earlier words and the earlier blocks)
+            // Per block, lanes 0-11 take one word each of its cut edges and the
+            // vertices of the tile before it (an exclusive scan over the lanes,
+            // in vertex order: axis, then sample), and list the word's edges
+            // in the vertex map `tm` at their ranks.
             vt = s.voff[base];
-            uint32_t acc = 0;
-            for (int q = 0; q < nb_w; q++) {
-                uint32_t m[4];
-                below_mask(&wt.halo[q][0], lc, iso, m);
-                const uint32_t lim = wt.lim[q];
-                uint32_t *cw = sm.cut[warp][q];
+            cp_async_wait_all();                       // the words (and cases) copied during staging
+            __syncwarp();
+            uint32_t nvt = 0;
+            const int lk = lane % 12, la = lk >> 2, lr = lk & 3;
+            for (int qq = 0; qq < nb_w; qq += 2) {     // lanes 0-11: block qq, lanes 12-23: block qq + 1
+                const int q = qq + (lane >= 12 ? 1 : 0);
+                uint32_t w = (lane < 24 && q < nb_w) ? sm.cut[warp][q][lk] : 0u;
+                const uint32_t n = __popc(w);
+                uint32_t incl = n;
 #pragma unroll
-                for (int r = 0; r < 4; r++) {
-                    const uint32_t c0 = cut_word(m, r, 0, lim), c1 = cut_word(m, r, 1, lim),
-                                   c2 = cut_word(m, r, 2, lim);
-                    if (lane == 0) {
-                        cw[r] = c0;
-                        cw[4 + r] = c1;
-                        cw[8 + r] = c2;
-                        cw[12 + r] = acc;
-                    }
-                    acc += __popc(c0) + __popc(c1) + __popc(c2);
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t x = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += x;
                 }
+                uint32_t rank = nvt + incl - n;        // the tile's vertices before this word
+                if (lane < 24 && q < nb_w) sm.cut[warp][q][12 + lk] = rank;
+                while (w) {                            // this word's edges: (block, sample, axis)
+                    const uint32_t i = __ffs(w) - 1;
+                    w &= w - 1;
+                    tm[rank++] = (uint16_t)((q << 9) | ((32 * lr + i) << 2) | la);
+                }
+                nvt += __shfl_sync(0xffffffffu, incl, 23);
             }
             __syncwarp();
-            // the tile's vertices, 96 at a time through the staging area; lane
-            // i looks at the edges from samples i, i + 32, i + 64, i + 96
-            const uint32_t nvt = acc;
+            // one vertex per lane, the triangle soup's arithmetic; consecutive
+            // lanes write consecutive vertices
             const unsigned long long vcap = c->params.vert_cap;
-            const uint32_t lt = (1u << lane) - 1u;
-            for (uint32_t c0 = 0; c0 < nvt; c0 += 96) {
-                for (int q = 0; q < nb_w; q++) {
-                    const uint32_t *cw = sm.cut[warp][q];
-                    const uint32_t vb = cw[12], ve = q + 1 < nb_w ? sm.cut[warp][q + 1][12] : nvt;
-                    if (ve <= c0 || vb >= c0 + 96) continue;   // warp-uniform
-                    const float *hb = &wt.halo[q][0];
-#pragma unroll 1
-                    for (int r = 0; r < 4; r++) {
-                        const uint32_t w0 = cw[r], w1 = cw[4 + r], w2 = cw[8 + r];
-                        const uint32_t b0 = (w0 >> lane) & 1u, b1 = (w1 >> lane) & 1u, b2 = (w2 >> lane) & 1u;
-                        if (!(b0 | b1 | b2)) continue;
-                        const uint32_t rank = cw[12 + r] + __popc(w0 & lt) + __popc(w1 & lt) + __popc(w2 & lt);
-                        const int smp = lane + 32 * r, sx = smp % 5, sy = (smp / 5) % 5, sz = smp / 25;
-                        const int ho = sx + 8 * sy + 40 * sz;          // padded halo offset of the sample
-                        const float vlo = hb[ho];
-#pragma unroll
-                        for (int a = 0; a < 3; a++) {
-                            const uint32_t bit = a == 0 ? b0 : (a == 1 ? b1 : b2);
-                            const uint32_t k = rank + (a > 0 ? b0 : 0u) + (a > 1 ? b1 : 0u) - c0;
-                            if (!bit || k >= 96u) continue;
-                            const float vhi = hb[ho + (a == 0 ? 1 : (a == 1 ? 8 : 40))];
-                            float4 p = make_float4((float)sx, (float)sy, (float)sz, __uint_as_float(wt.bid[q]));
-                            // the triangle soup's arithmetic, vertex for vertex
-                            const float tt = packed ? __fdiv_rn(__fsub_rn(iso, vlo), __fsub_rn(vhi, vlo))
-                                                    : __fdividef(__fsub_rn(iso, vlo), __fsub_rn(vhi, vlo));
-                            if (a == 0) p.x = __fadd_rn(p.x, tt);
-                            else if (a == 1) p.y = __fadd_rn(p.y, tt);
-                            else p.z = __fadd_rn(p.z, tt);
-                            if (!packed) {
-                                stage[k] = p;
-                            } else {
-                                const uint32_t qx = (uint32_t)__float2int_rn(__fmul_rn(p.x, 255.75f));
-                                const uint32_t qy = (uint32_t)__float2int_rn(__fmul_rn(p.y, 255.75f));
-                                const uint32_t qz = (uint32_t)__float2int_rn(__fmul_rn(p.z, 255.75f));
-                                reinterpret_cast<uint2 *>(stage)[k] = make_uint2(qx | (qy << 10) | (qz << 20), wt.bid[q]);
-                            }
-                        }
+            for (uint32_t k = lane; k < nvt; k += 32) {
+                const uint32_t e = tm[k];
+                const uint32_t q = e >> 9, smp = (e >> 2) & 127u, ax = e & 3u;
+                const uint32_t sx = smp % 5u, sy = (smp / 5u) % 5u, sz = smp / 25u;
+                const float *hp = &wt.halo[q][0] + sx + 8 * sy + 40 * sz;
+                const float vlo = hp[0], vhi = hp[ax == 0 ? 1 : (ax == 1 ? 8 : 40)];
+                float px = (float)sx, py = (float)sy, pz = (float)sz;
+                float tt;
+                if (!packed) tt = __fdividef(__fsub_rn(iso, vlo), __fsub_rn(vhi, vlo));
+                else tt = __fdiv_rn(__fsub_rn(iso, vlo), __fsub_rn(vhi, vlo));
+                if (ax == 0) px = __fadd_rn(px, tt);
+                else if (ax == 1) py = __fadd_rn(py, tt);
+                else pz = __fadd_rn(pz, tt);
+                if (vt + k < vcap) {
+                    if (!packed) {
+                        out[vt + k] = make_float4(px, py, pz, __uint_as_float(wt.bid[q]));
+                    } else {
+                        const uint32_t qx = (uint32_t)__float2int_rn(__fmul_rn(px, 255.75f));
+                        const uint32_t qy = (uint32_t)__float2int_rn(__fmul_rn(py, 255.75f));
+                        const uint32_t qz = (uint32_t)__float2int_rn(__fmul_rn(pz, 255.75f));
+                        reinterpret_cast<uint2 *>(out)[vt + k] = make_uint2(qx | (qy << 10) | (qz << 20), wt.bid[q]);
                     }
                 }
-                __syncwarp();
-                const uint32_t nv = min(96u, nvt - c0);
-                const unsigned long long v0 = vt + c0;
-#pragma unroll
-                for (int r = 0; r < 3; r++) {
-                    const uint32_t f = lane + 32 * r;
-                    if (f < nv && v0 + f < vcap) {
-                        if (!packed) out[v0 + f] = stage[f];
-                        else reinterpret_cast<uint2 *>(out)[v0 + f] = reinterpret_cast<const uint2 *>(stage)[f];
-                    }
-                }
-                __syncwarp();
             }
             vt += c->params.vtx_base;                  // indices count the vertices of earlier waves
+            __syncwarp();                              // the vertex map is read: tm takes the triangles
+        }
+        uint32_t tacc = 0;
+#pragma unroll
+        for (int q = 0; q < kBPW; q++) {
+            if (q >= nb_w) continue;
+            const uint32_t n0 = (n0p >> (8 * q)) & 0xFFu, n1 = (n1p >> (8 * q)) & 0xFFu;
+            const uint32_t b0 = (s0 >> (8 * q)) & 0xFFu;
+            const uint32_t o0 = tacc + ((i0 >> (8 * q)) & 0xFFu) - n0;
+            const uint32_t o1 = tacc + b0 + ((i1 >> (8 * q)) & 0xFFu) - n1;
+            for (uint32_t k = 0; k < n0; k++) tm[o0 + k] = (uint16_t)((q << 9) | (lane << 3) | k);
+            for (uint32_t k = 0; k < n1; k++) tm[o1 + k] = (uint16_t)((q << 9) | ((lane + 32) << 3) | k);
+            tacc += b0 + ((s1 >> (8 * q)) & 0xFFu);
         }
         __syncwarp();
         // one triangle per lane; its three vertices (or, indexed, its three
@@ -696,15 +717,12 @@ __global__ void __launch_bounds__(32 * kW) mc_emit_kernel(Launch L) {
                     const uint32_t info = sm.edge_info[(row >> (8 * j)) & 0xFFu];
                     const uint32_t a = (info >> 19) & 3u;
                     if constexpr (kIdx) {
-                        // the rank of the edge among the block's cut edges
+                        // the rank of the edge among the tile's vertices: those
+                        // before its word, then its word's bits below it
                         const int smp = cx + (int)((info >> 16) & 1u) + 5 * (cy + (int)((info >> 17) & 1u)) +
                                         25 * (cz + (int)((info >> 18) & 1u));
-                        const uint32_t *cw = sm.cut[warp][q];
-                        const int r = smp >> 5, bit = smp & 31;
-                        const uint32_t w0 = cw[r], w1 = cw[4 + r], w2 = cw[8 + r], below = (1u << bit) - 1u;
-                        const uint32_t rank = cw[12 + r] + __popc(w0 & below) + __popc(w1 & below) +
-                                              __popc(w2 & below) + (a > 0 ? (w0 >> bit) & 1u : 0u) +
-                                              (a > 1 ? (w1 >> bit) & 1u : 0u);
+                        const uint32_t *cw = sm.cut[warp][q] + 4 * a + (smp >> 5);
+                        const uint32_t rank = cw[12] + __popc(cw[0] & ((1u << (smp & 31)) - 1u));
                         reinterpret_cast<uint32_t *>(stage)[3 * lane + j] = (uint32_t)(vt + rank);
                     } else {
                         const float vlo = hb[info & 0xFFu], vhi = hb[(info >> 8) & 0xFFu];
@@ -779,6 +797,18 @@ __global__ void __launch_bounds__(32 * kW) mc_emit_kernel(Launch L) {
     }
 }
 
+// the triangle soup
+template <int kW, bool kDebug, bool kOne>
+__global__ void __launch_bounds__(32 * kW) mc_emit_kernel(Launch L) {
+    emit_body<kW, kDebug, kOne, false>(L);
+}
+
+// the indexed mesh (single volumes); registers bounded for 24 warps per SM
+template <int kW, bool kDebug>
+__global__ void __launch_bounds__(32 * kW, 24 / kW) mc_emit_indexed_kernel(Launch L) {
+    emit_body<kW, kDebug, true, true>(L);
+}
+
 // ================================================================ launchers
 
 namespace {
@@ -791,8 +821,13 @@ void count_w(const Launch &L, int grid, cudaStream_t st) {
 template <int kW, bool kOne, bool kIdx>
 void emit_w(const Launch &L, bool debug, int grid, cudaStream_t st) {
     constexpr size_t bytes = sizeof(EmitSmem<kW, kIdx>);
-    if (debug) mc_emit_kernel<kW, true, kOne, kIdx><<<grid, 32 * kW, bytes, st>>>(L);
-    else mc_emit_kernel<kW, false, kOne, kIdx><<<grid, 32 * kW, bytes, st>>>(L);
+    if constexpr (kIdx) {
+        if (debug) mc_emit_indexed_kernel<kW, true><<<grid, 32 * kW, bytes, st>>>(L);
+        else mc_emit_indexed_kernel<kW, false><<<grid, 32 * kW, bytes, st>>>(L);
+    } else {
+        if (debug) mc_emit_kernel<kW, true, kOne><<<grid, 32 * kW, bytes, st>>>(L);
+        else mc_emit_kernel<kW, false, kOne><<<grid, 32 * kW, bytes, st>>>(L);
+    }
 }
 
 template <class K>
@@ -802,18 +837,18 @@ void raise_smem(K kernel, size_t bytes) {
 
 template <int kW>
 int emit_occupancy(bool single) {
-    raise_smem(mc_emit_kernel<kW, false, false, false>, sizeof(EmitSmem<kW, false>));
-    raise_smem(mc_emit_kernel<kW, true, false, false>, sizeof(EmitSmem<kW, false>));
-    raise_smem(mc_emit_kernel<kW, false, true, false>, sizeof(EmitSmem<kW, false>));
-    raise_smem(mc_emit_kernel<kW, true, true, false>, sizeof(EmitSmem<kW, false>));
-    raise_smem(mc_emit_kernel<kW, false, true, true>, sizeof(EmitSmem<kW, true>));
-    raise_smem(mc_emit_kernel<kW, true, true, true>, sizeof(EmitSmem<kW, true>));
+    raise_smem(mc_emit_kernel<kW, false, false>, sizeof(EmitSmem<kW, false>));
+    raise_smem(mc_emit_kernel<kW, true, false>, sizeof(EmitSmem<kW, false>));
+    raise_smem(mc_emit_kernel<kW, false, true>, sizeof(EmitSmem<kW, false>));
+    raise_smem(mc_emit_kernel<kW, true, true>, sizeof(EmitSmem<kW, false>));
+    raise_smem(mc_emit_indexed_kernel<kW, false>, sizeof(EmitSmem<kW, true>));
+    raise_smem(mc_emit_indexed_kernel<kW, true>, sizeof(EmitSmem<kW, true>));
     int occ = 0;
     if (single)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mc_emit_kernel<kW, false, true, false>, 32 * kW,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mc_emit_kernel<kW, false, true>, 32 * kW,
                                                       sizeof(EmitSmem<kW, false>));
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mc_emit_kernel<kW, false, false, false>, 32 * kW,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mc_emit_kernel<kW, false, false>, 32 * kW,
                                                       sizeof(EmitSmem<kW, false>));
     return occ;
 }

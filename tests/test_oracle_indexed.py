@@ -3,7 +3,8 @@
 Section 4.5 names an indexed mesh with vertices shared inside each block
 as the alternative to the triangle soup.  The oracle builds it from the
 block-ordered soup by its plain definition (a block's vertices are the
-distinct edges its triangles use, ascending).  These tests tie it to
+distinct edges its triangles use, by axis, then lower sample).  These
+tests tie it to
 things outside that definition: gathering by index gives the soup back
 exactly; a block's vertices are the cut edges of its 5x5x5 window found by
 brute force over its cells; and with the blocks' vertices welded by edge,
@@ -40,19 +41,21 @@ def test_gather_gives_the_soup(name, make, iso):
     assert np.array_equal(ix["vertex_edge"][idx], ref["edge_ids"])
     assert np.array_equal(ix["vertex_pos"][idx], ref["local_pos"])          # exact: same edge, same position
     assert np.array_equal(ix["vertex_block"][idx], np.repeat(ref["tri_block"][:, None], 3, 1))
-    # every vertex is used, blocks ascend, a block's edges ascend strictly
+    # every vertex is used, blocks ascend, a block's edges ascend strictly by
+    # (axis, lower sample)
     assert len(np.unique(idx)) == len(ix["vertex_edge"])
     vb, ve = ix["vertex_block"].astype(np.int64), ix["vertex_edge"]
     assert np.all(np.diff(vb) >= 0)
     same = np.diff(vb) == 0
-    assert np.all(ve[1:][same] > ve[:-1][same])
+    key = (ve % 3) * (1 << 40) + ve // 3
+    assert np.all(key[1:][same] > key[:-1][same])
     # a triangle's three corners are three different vertices
     assert np.all((idx[:, 0] != idx[:, 1]) & (idx[:, 1] != idx[:, 2]) & (idx[:, 0] != idx[:, 2]))
 
 
 def window_cut_edges(field, iso, dims, b):
     """Brute force: global ids of the cut edges of block b's cells inside
-    the volume (the block's indexed-mesh vertices), sorted."""
+    the volume (the block's indexed-mesh vertices), by axis, then id."""
     nx, ny, nz = dims
     nbx, nby, _ = oracle.block_dims(dims)
     bx, by, bz = b % nbx, (b // nbx) % nby, b // (nbx * nby)
@@ -72,7 +75,7 @@ def window_cut_edges(field, iso, dims, b):
                                     continue
                                 if (field[z, y, x] < iso) != (field[z2, y2, x2] < iso):
                                     found.add(3 * (x + nx * (y + ny * z)) + a)
-    return sorted(found)
+    return sorted(found, key=lambda e: (e % 3, e))
 
 
 @pytest.mark.parametrize("name,make,iso", CASES, ids=[c[0] for c in CASES])
