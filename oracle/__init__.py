@@ -17,6 +17,11 @@ Parity status of each function (what pins it, see ``tests/test_oracle_*``):
               watertightness and Euler characteristic
   active      brute force: every block touched by a crossing cell is active
   mc_blocks   equals mc_full reordered by block
+  raster      hand-enumerated coverage of small triangles (top-left rule
+              on the shared and boundary edges), quads and fans covered
+              exactly once, nearer and lower-id fragments win, a plane's
+              depth equals the projection's closed form, points behind the
+              camera dropped; shade: normal along / across the light
   indexed_mesh  gathers back to the soup exactly; a block's vertices are
               the cut edges of its window found by brute force; welded over
               blocks, a sphere stays closed with Euler characteristic 2
@@ -63,6 +68,8 @@ def lib():
         L.orc_mc_blocks.argtypes = [P, i32, i32, i32, ctypes.c_float, P, P, i64,
                                     P, P, P, P, P, P, P, P, i64]
         L.orc_mc_blocks.restype = i64
+        L.orc_raster.argtypes = [P, i32, P, i64, i32, i32, i32, P, i32, i32, P]
+        L.orc_shade.argtypes = [P, i32, P, i32, i32, i32, P, i32, i32, P, P]
         _lib = L
     return _lib
 
@@ -278,6 +285,45 @@ def indexed_mesh(edge_ids, tri_block, local_pos):
     uniq, first, inv = np.unique(keys, axis=0, return_index=True, return_inverse=True)
     return dict(vertex_edge=uniq[:, 2] * np.uint64(3) + uniq[:, 1], vertex_block=uniq[:, 0].astype(np.uint32),
                 vertex_pos=pos[first], indices=inv.reshape(-1, 3).astype(np.int64))
+
+
+# ---------------------------------------------------------------- rendering (Section 4.6.2)
+
+def _vertex_buffer(vertices):
+    """(array, format): float32 (V, 4) -> format 0; uint32/int32 (V, 2) -> 1."""
+    v = np.ascontiguousarray(vertices)
+    if v.dtype == np.float32:
+        return v.reshape(-1, 4), 0
+    return v.view(np.uint32).reshape(-1, 2), 1
+
+
+def raster(vertices, indices, num_triangles, dims, view_proj, width, height):
+    """Visible fragment of every pixel (oracle/raster.c states the rules):
+    uint64 (height, width), (depth bits << 32) | triangle, all ones where
+    nothing is drawn.  `vertices` float32 (V, 4) block-local + block id bits
+    or uint32 (V, 2) compact; `indices` None for a soup (vertex 3t + j) or
+    uint32 (T, 3); view_proj row-major 4x4 float32."""
+    v, fmt = _vertex_buffer(vertices)
+    idx = None if indices is None else np.ascontiguousarray(indices, np.uint32)
+    m = np.ascontiguousarray(view_proj, np.float32).reshape(16)
+    out = np.zeros((height, width), np.uint64)
+    nx, ny, nz = dims
+    lib().orc_raster(_p(v), fmt, _p(idx), int(num_triangles), nx, ny, nz, _p(m), width, height, _p(out))
+    return out
+
+
+def shade(vertices, indices, dims, light, frag):
+    """RGBA8 (as uint32, r in the low byte) of each pixel of a fragment
+    buffer from raster()."""
+    v, fmt = _vertex_buffer(vertices)
+    idx = None if indices is None else np.ascontiguousarray(indices, np.uint32)
+    f = np.ascontiguousarray(frag, np.uint64)
+    h, w = f.shape
+    out = np.zeros((h, w), np.uint32)
+    l3 = np.ascontiguousarray(light, np.float32).reshape(3)
+    nx, ny, nz = dims
+    lib().orc_shade(_p(v), fmt, _p(idx), nx, ny, nz, _p(l3), w, h, _p(f), _p(out))
+    return out
 
 
 # ---------------------------------------------------------------- cache (Algorithm 1)

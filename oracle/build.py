@@ -10,7 +10,7 @@ import os
 import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["codec.c", "mc.c"]
+SOURCES = ["codec.c", "mc.c", "raster.c"]
 LIB = os.path.join(HERE, "_lib", "liboracle.so")
 
 

@@ -14,6 +14,9 @@
  *            full-volume marching cubes, and the block-level rules of
  *            Sections 4.1-4.5 (active blocks, halo extents, occupied
  *            blocks, per-block counts and offsets, block-ordered output).
+ *   raster.c the rendering step of Section 4.6.2 defined on the CPU:
+ *            rasterisation of a triangle soup or indexed mesh in either
+ *            vertex format to a depth | triangle-id buffer, and shading.
  *
  * Conventions
  *   voxel (x,y,z) of an nx*ny*nz volume sits at x + nx*(y + ny*z);
@@ -54,4 +57,10 @@ int64_t orc_mc_blocks(const float *field, int nx, int ny, int nz, float iso,
                       uint8_t *cell_case, uint8_t *cell_count, uint8_t *complete,
                       uint32_t *block_tri, uint64_t *block_off,
                       uint64_t *edge_ids, double *local_pos, uint32_t *tri_block, int64_t cap);
+
+/* ---- rendering (raster.c) ---- */
+void orc_raster(const void *verts, int format, const uint32_t *idx, int64_t num_tri, int nx, int ny, int nz,
+                const float m[16], int width, int height, uint64_t *frag);
+void orc_shade(const void *verts, int format, const uint32_t *idx, int nx, int ny, int nz, const float light[3],
+               int width, int height, const uint64_t *frag, uint32_t *rgba);
 #endif
