@@ -190,6 +190,50 @@ int iso_extract_indexed_into(iso_volume *v, float isovalue, int vertex_format, v
                              uint64_t capacity_vertices, uint32_t *d_indices, uint64_t capacity_triangles,
                              iso_stats *stats);
 
+/* ---- rendering (Section 4.6.2) ----
+ * The paper draws the triangle soup, in its compressed vertex format, with
+ * WebGPU; here CUDA kernels draw it into headless device buffers.  World
+ * coordinates are voxel coordinates: a vertex is its block's origin
+ * (4 bx, 4 by, 4 bz), from the block id (x fastest over ceil(n/4) blocks
+ * per axis), plus its block-local position (float4) or code * 4/1023
+ * (compact). */
+typedef struct iso_camera {
+    float view_proj[16];       /* row-major 4x4: clip (X, Y, Z, W) = M (x, y, z, 1) */
+    float light[3];            /* direction towards the light (normalised by the library) */
+    uint32_t width, height;    /* pixels, 1..32768 each */
+} iso_camera;
+
+typedef struct iso_render_stats {
+    uint64_t drawn;            /* triangles in front of the camera with non-zero screen area
+                                  whose bounding box meets the viewport */
+    uint64_t big;              /* of them, covered one warp per triangle (bounding box over
+                                  32 pixel centres) */
+} iso_render_stats;
+
+/* Rasterise num_triangles triangles (a soup: vertices 3t, 3t+1, 3t+2 when
+ * d_indices is NULL; else d_indices[3t + j]) of vertex_format
+ * (ISO_VERTEX_FLOAT4 / ISO_VERTEX_PACKED) from a volume of nx*ny*nz
+ * samples.  Rules, every float operation a single IEEE float32 operation:
+ * sx = (X/W * 0.5 + 0.5) * width, sy likewise (y up, row 0 at the bottom),
+ * depth Z/W * 0.5 + 0.5; triangles with a vertex at W <= 0 are not drawn
+ * (no clipping); pixel centres (i + 0.5, j + 0.5) inside the triangle by
+ * edge functions evaluated in a canonical endpoint order, with a top-left
+ * rule on ties (a mesh is drawn without cracks or double hits); depth
+ * interpolated by the edge values, fragments outside [0, 1] dropped.
+ *   d_fragments  uint64[height * width] (row j at j * width): the smallest
+ *                (depth bits << 32 | triangle) per pixel, ~0 where empty
+ *   d_rgba       uint32[height * width] or NULL: r | g << 8 | b << 16 |
+ *                a << 24, two-sided Lambert shading of the visible
+ *                triangle, 0.2 + 0.8 |n.L| / |n| times (0.85, 0.75, 0.55),
+ *                alpha 255; 0 where empty
+ * Device buffers owned by the caller; queued on `stream`.  stats may be
+ * NULL; when given, the call waits for the stream and fills it.
+ * ISO_ERR_INVALID_ARG for a bad format, size, light (zero or not finite) or
+ * a NaN in the matrix; ISO_ERR_OOM if the working list cannot be made. */
+int iso_render(const void *d_vertices, int vertex_format, const uint32_t *d_indices, uint64_t num_triangles,
+               uint32_t nx, uint32_t ny, uint32_t nz, const iso_camera *camera, uint64_t *d_fragments,
+               uint32_t *d_rgba, iso_render_stats *stats, void *stream);
+
 /* The full-volume baseline the paper measures against (the naive
  * data-parallel marching cubes of Section 3 over the whole decompressed
  * volume): the same pipeline with the range test switched off, so every

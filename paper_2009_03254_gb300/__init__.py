@@ -74,6 +74,15 @@ class _ServerOptions(ctypes.Structure):
                 ("vertex_budget_bytes", ctypes.c_uint64), ("stream", ctypes.c_void_p)]
 
 
+class _Camera(ctypes.Structure):
+    _fields_ = [("view_proj", ctypes.c_float * 16), ("light", ctypes.c_float * 3), ("width", ctypes.c_uint32),
+                ("height", ctypes.c_uint32)]
+
+
+class _RenderStats(ctypes.Structure):
+    _fields_ = [("drawn", ctypes.c_uint64), ("big", ctypes.c_uint64)]
+
+
 class _Mesh(ctypes.Structure):
     _fields_ = [("d_vertices", ctypes.c_void_p), ("num_triangles", ctypes.c_uint64),
                 ("capacity_triangles", ctypes.c_uint64), ("stats", _Stats), ("priv", ctypes.c_void_p)]
@@ -98,6 +107,8 @@ def lib():
             "iso_extract_packed_into": (i32, [P, ctypes.c_float, P, u64, ctypes.POINTER(_Stats)]),
             "iso_extract_all_blocks_into": (i32, [P, ctypes.c_float, P, u64, ctypes.POINTER(_Stats)]),
             "iso_extract_indexed_into": (i32, [P, ctypes.c_float, i32, P, u64, P, u64, ctypes.POINTER(_Stats)]),
+            "iso_render": (i32, [P, i32, P, u64, u32, u32, u32, ctypes.POINTER(_Camera), P, P,
+                                 ctypes.POINTER(_RenderStats), P]),
             "iso_decode_volume": (i32, [P, u32, u32, u32, u32, P, P]),
             "iso_mesh_release": (i32, [P, ctypes.POINTER(_Mesh)]),
             "iso_release": (None, [P]),
@@ -519,6 +530,38 @@ class Server:
             self.release()
         except Exception:
             pass
+
+
+def render(vertices, num_triangles, dims, view_proj, light, width, height, indices=None, fragments=None,
+           rgba=None, stream=None, stats=False):
+    """Rasterise a soup (vertices 3t..3t+2) or, with `indices` (uint32/int32
+    CUDA tensor (T, 3)), an indexed mesh into headless CUDA buffers (rules in
+    iso_render).  `vertices`: CUDA float32 (V, 4) or int32 (V, 2) compact.
+    Returns (fragments int64 (height, width): depth bits << 32 | triangle,
+    -1 where empty; rgba int32 (height, width): r | g << 8 | b << 16 | a << 24;
+    stats dict or None).  Pass `rgba=False` to skip shading."""
+    import torch
+    assert vertices.is_cuda and vertices.is_contiguous()
+    fmt = ISO_VERTEX_FLOAT4 if vertices.dtype == torch.float32 else ISO_VERTEX_PACKED
+    if fragments is None:
+        fragments = torch.empty((height, width), dtype=torch.int64, device=vertices.device)
+    if rgba is None:
+        rgba = torch.empty((height, width), dtype=torch.int32, device=vertices.device)
+    cam = _Camera()
+    m = np.ascontiguousarray(view_proj, np.float32).reshape(16)
+    for k in range(16):
+        cam.view_proj[k] = float(m[k])
+    for k in range(3):
+        cam.light[k] = float(light[k])
+    cam.width, cam.height = int(width), int(height)
+    st = _RenderStats()
+    nx, ny, nz = dims
+    rc = lib().iso_render(_ptr(vertices), fmt, _ptr(indices) if indices is not None else None, int(num_triangles),
+                          nx, ny, nz, ctypes.byref(cam), _ptr(fragments), _ptr(rgba) if rgba is not False else None,
+                          ctypes.byref(st) if stats else None,
+                          stream if stream is not None else _current_stream())
+    _check(rc, "iso_render")
+    return fragments, (rgba if rgba is not False else None), ({"drawn": st.drawn, "big": st.big} if stats else None)
 
 
 def unpack_vertices(packed):

@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import oracle
+from synth import cameras
 
 DIMS = (64, 64, 64)
 NONE = np.uint64(0xFFFFFFFFFFFFFFFF)
@@ -30,17 +31,6 @@ def float4_vertices(points):
     return out
 
 
-def ortho(width, height, depth=64.0):
-    """World x in [0, width], y in [0, height] onto the whole viewport;
-    z in [0, depth] onto depth [0, 1]."""
-    m = np.zeros((4, 4), np.float32)
-    m[0, 0], m[0, 3] = 2.0 / width, -1.0
-    m[1, 1], m[1, 3] = 2.0 / height, -1.0
-    m[2, 2], m[2, 3] = 2.0 / depth, -1.0
-    m[3, 3] = 1.0
-    return m
-
-
 def coverage(points, tris, width, height, m=None):
     """Per triangle: boolean (height, width) mask of the pixels it wins
     when drawn alone."""
@@ -48,7 +38,7 @@ def coverage(points, tris, width, height, m=None):
     masks = []
     for t in tris:
         soup = v[list(t)]
-        f = oracle.raster(soup, None, 1, DIMS, ortho(width, height) if m is None else m, width, height)
+        f = oracle.raster(soup, None, 1, DIMS, cameras.orthographic(width, height) if m is None else m, width, height)
         masks.append(f != NONE)
     return masks
 
@@ -61,7 +51,7 @@ def test_right_triangle_hand_enumerated():
         (m,) = coverage(pts, [order], 8, 8)
         want = np.array([[i + j <= 6 for i in range(8)] for j in range(8)])
         assert np.array_equal(m, want)
-    f = oracle.raster(float4_vertices(pts), None, 1, DIMS, ortho(8, 8), 8, 8)
+    f = oracle.raster(float4_vertices(pts), None, 1, DIMS, cameras.orthographic(8, 8), 8, 8)
     d = (f[f != NONE] >> np.uint64(32)).astype(np.uint32).view(np.float32)
     assert np.all(d == np.float32(1.0 / 64.0))           # z = 1 of 64
     assert np.all((f[f != NONE] & np.uint64(0xFFFFFFFF)) == 0)
@@ -111,7 +101,7 @@ def test_nearest_fragment_wins_and_ties_go_to_the_lower_id():
     v = float4_vertices([(0, 0, 10), (8, 0, 10), (0, 8, 10),       # t0 far
                          (0, 0, 5), (8, 0, 5), (0, 8, 5),          # t1 near
                          (0, 0, 5), (8, 0, 5), (0, 8, 5)])         # t2 = t1
-    f = oracle.raster(v, None, 3, DIMS, ortho(8, 8), 8, 8)
+    f = oracle.raster(v, None, 3, DIMS, cameras.orthographic(8, 8), 8, 8)
     drawn = f[f != NONE]
     assert len(drawn) == 28
     assert np.all((drawn & np.uint64(0xFFFFFFFF)) == 1)
@@ -119,18 +109,7 @@ def test_nearest_fragment_wins_and_ties_go_to_the_lower_id():
 
 
 def perspective(fovy_deg, aspect, near, far, eye, target):
-    f = 1.0 / np.tan(np.radians(fovy_deg) / 2)
-    p = np.array([[f / aspect, 0, 0, 0], [0, f, 0, 0],
-                  [0, 0, (far + near) / (near - far), 2 * far * near / (near - far)], [0, 0, -1, 0]])
-    z = np.asarray(eye, float) - np.asarray(target, float)
-    z /= np.linalg.norm(z)
-    x = np.cross([0.0, 1.0, 0.0], z)
-    x /= np.linalg.norm(x)
-    y = np.cross(z, x)
-    v = np.eye(4)
-    v[:3, :3] = np.stack([x, y, z])
-    v[:3, 3] = -v[:3, :3] @ np.asarray(eye, float)
-    return (p @ v).astype(np.float32), (near, far)
+    return cameras.look_at_perspective(fovy_deg, aspect, near, far, eye, target), (near, far)
 
 
 def test_plane_depth_matches_the_projection():
@@ -181,7 +160,7 @@ def test_compact_and_indexed_inputs_draw_the_same():
 def test_shading_by_hand():
     pts = [(0, 0, 1), (8, 0, 1), (0, 8, 1)]                               # normal along +z
     v = float4_vertices(pts)
-    f = oracle.raster(v, None, 1, DIMS, ortho(8, 8), 8, 8)
+    f = oracle.raster(v, None, 1, DIMS, cameras.orthographic(8, 8), 8, 8)
     lit = oracle.shade(v, None, DIMS, (0.0, 0.0, 3.0), f)
     side = oracle.shade(v, None, DIMS, (1.0, 0.0, 0.0), f)
     back = oracle.shade(v, None, DIMS, (0.0, 0.0, -1.0), f)
