@@ -21,6 +21,10 @@ Metric: triangles/s (whole step, all five surfaces), with voxels/s
   roofline the dominant stage's kernel: algorithmic bytes per launch over
            its CUDA-event duration, against the measured HBM copy peak
   cpu_baseline  the plain CPU oracle on a bounded window of the same field
+  packed_vertices / indexed_mesh  the same steps writing the compact
+           8-byte vertices / the within-block indexed mesh
+  render   the isovalue-0 surface drawn at 1920x1080 (iso_render) as the
+           float4 soup, the compact soup and the indexed mesh
 
 --impl reference times the CPU oracle alone (the reference arm: there is no
 other implementation of this method to run).
@@ -319,6 +323,59 @@ def measure_batch64(bc, sg, torch, stream, flush, steps):
 
 # ---------------------------------------------------------------- our arm
 
+RENDER_SIZE = (1920, 1080)
+RENDER_ISO = 0.0
+
+
+def measure_render(bc, vol, torch, stream, tmax, vmax, frames=10):
+    """The rendering step (Section 4.6.2): the isovalue-0 surface drawn at
+    1920x1080 from an orbit camera, as the float4 soup, the compact soup and
+    the indexed mesh.  Each frame is one iso_render call (fragment clear,
+    rasterisation, shading), timed with CUDA events back to back."""
+    from synth import cameras
+    w, h = RENDER_SIZE
+    m = cameras.orbit(DIMS, 30.0, 25.0, distance_factor=1.1, aspect=w / h)
+    light = (0.3, -0.5, 0.8)
+    frag = torch.empty((h, w), dtype=torch.int64, device="cuda")
+    rgba = torch.empty((h, w), dtype=torch.int32, device="cuda")
+    soup = torch.empty((tmax + 1024, 3, 4), dtype=torch.float32, device="cuda")
+    packed = torch.empty((tmax + 1024, 3, 2), dtype=torch.int32, device="cuda")
+    v4 = torch.empty((vmax + 1024, 4), dtype=torch.float32, device="cuda")
+    idx = torch.empty((tmax + 1024, 3), dtype=torch.int32, device="cuda")
+    T = vol.extract_into(RENDER_ISO, soup)["num_triangles"]
+    vol.extract_packed_into(RENDER_ISO, packed)
+    V = vol.extract_indexed_into(RENDER_ISO, v4, idx)["num_vertices"]
+    cases = {"float4_soup": (soup, None, 48.0 * T), "compact_soup": (packed, None, 24.0 * T),
+             "indexed_float4": (v4, idx, 16.0 * V + 12.0 * T)}
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    out = {"workload": f"noise512 isovalue {RENDER_ISO}: {T} triangles, {w}x{h}, orbit camera (azimuth 30, "
+                       f"elevation 25 degrees)", "triangles": T}
+    for name, (verts, ind, vbytes) in cases.items():
+        st = None
+        for _ in range(3):
+            _, _, st = bc.render(verts, T, DIMS, m, light, w, h, indices=ind, fragments=frag, rgba=rgba, stats=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(frames):
+            bc.render(verts, T, DIMS, m, light, w, h, indices=ind, fragments=frag, rgba=rgba)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / frames
+        # vertices read once, fragments cleared and read back by shading, image written
+        nbytes = vbytes + w * h * (8 + 8 + 4)
+        out[name] = {"ms_per_frame": ms, "fps": 1000.0 / ms, "triangles_per_s": T / (ms / 1000.0),
+                     "drawn": st["drawn"], "big": st["big"], "alg_bytes_per_frame": nbytes,
+                     "GBps": nbytes / (ms / 1000.0) / 1e9, "frac_of_measured_hbm": nbytes / (ms / 1000.0) / 1e9 / peak}
+    covered = int((frag != -1).sum())
+    out["pixels_covered"] = covered
+    out["what"] = ("iso_render per frame: fragment clear, one thread per small triangle, one warp per triangle "
+                   "over 32 pixel centres, 64-bit atomicMin on (depth, triangle), Lambert shading to RGBA8")
+    del soup, packed, v4, idx, frag, rgba
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -483,6 +540,8 @@ def run_ours(args):
         indexed["what"] = ("the same cold-cache 5-isovalue steps writing the indexed mesh: one vertex per cut edge "
                            "of each block's window, uint32 index triples, per-kernel events on")
 
+        render = measure_render(bc, vol, torch, stream, tmax, vmax)
+
         # the full-volume baselines of the paper's comparisons: decode every block
         # into a dense field; and the extraction with the range test off (every
         # block decoded into the cache and visited, from an empty cache)
@@ -602,6 +661,7 @@ def run_ours(args):
         "roofline_cold_extraction": cold,
         "packed_vertices": packed,
         "indexed_mesh": indexed,
+        "render": render,
         "full_volume_baselines": baselines,
         "batch64": batch,
         "stages": stages,
