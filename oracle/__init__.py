@@ -22,6 +22,9 @@ Parity status of each function (what pins it, see ``tests/test_oracle_*``):
               exactly once, nearer and lower-id fragments win, a plane's
               depth equals the projection's closed form, points behind the
               camera dropped; shade: normal along / across the light
+  raycast     hits on a plane and a sphere against the closed forms, every
+              hit and miss against a fine float64 march over the trilinear
+              interpolant (no block or cell skipped wrongly), shading by hand
   indexed_mesh  gathers back to the soup exactly; a block's vertices are
               the cut edges of its window found by brute force; welded over
               blocks, a sphere stays closed with Euler characteristic 2
@@ -70,6 +73,7 @@ def lib():
         L.orc_mc_blocks.restype = i64
         L.orc_raster.argtypes = [P, i32, P, i64, i32, i32, i32, P, i32, i32, P]
         L.orc_shade.argtypes = [P, i32, P, i32, i32, i32, P, i32, i32, P, P]
+        L.orc_raycast.argtypes = [P, i32, i32, i32, ctypes.c_float, P, P, P, P, P, i32, i32, P, P]
         _lib = L
     return _lib
 
@@ -324,6 +328,21 @@ def shade(vertices, indices, dims, light, frag):
     nx, ny, nz = dims
     lib().orc_shade(_p(v), fmt, _p(idx), nx, ny, nz, _p(l3), w, h, _p(f), _p(out))
     return out
+
+
+def raycast(field, iso, eye, forward, right, up, light, width, height):
+    """Implicit isosurface ray casting over the block macrocell grid
+    (oracle/raycast.c states the rules).  field float32 (nz, ny, nx), the
+    decoded volume.  Returns (hits uint64 (height, width): t bits << 32 |
+    block id of the first hit, all ones for none; rgba uint32 (height,
+    width))."""
+    f = np.ascontiguousarray(field, np.float32)
+    nz, ny, nx = f.shape
+    vec = [np.ascontiguousarray(x, np.float32).reshape(3) for x in (eye, forward, right, up, light)]
+    hits = np.zeros((height, width), np.uint64)
+    rgba = np.zeros((height, width), np.uint32)
+    lib().orc_raycast(_p(f), nx, ny, nz, float(iso), *[_p(x) for x in vec], width, height, _p(hits), _p(rgba))
+    return hits, rgba
 
 
 # ---------------------------------------------------------------- cache (Algorithm 1)

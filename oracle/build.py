@@ -10,7 +10,7 @@ import os
 import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["codec.c", "mc.c", "raster.c"]
+SOURCES = ["codec.c", "mc.c", "raster.c", "raycast.c"]
 LIB = os.path.join(HERE, "_lib", "liboracle.so")
 
 

@@ -18,6 +18,9 @@
  *            rasterisation of a triangle soup or indexed mesh in either
  *            vertex format to a depth | triangle-id buffer, and shading.
  *
+ *   raycast.c implicit isosurface ray casting with the blocks as a
+ *            macrocell grid (the future work of Section 4.6.2).
+ *
  * Conventions
  *   voxel (x,y,z) of an nx*ny*nz volume sits at x + nx*(y + ny*z);
  *   block (bx,by,bz) has id bx + nbx*(by + nby*bz), nb* = ceil(n* / 4);
@@ -63,4 +66,9 @@ void orc_raster(const void *verts, int format, const uint32_t *idx, int64_t num_
                 const float m[16], int width, int height, uint64_t *frag);
 void orc_shade(const void *verts, int format, const uint32_t *idx, int nx, int ny, int nz, const float light[3],
                int width, int height, const uint64_t *frag, uint32_t *rgba);
+
+/* ---- ray casting over the block macrocell grid (raycast.c) ---- */
+void orc_raycast(const float *field, int nx, int ny, int nz, float iso, const float eye[3], const float fwd[3],
+                 const float right[3], const float up[3], const float light[3], int width, int height,
+                 uint64_t *hits, uint32_t *rgba);
 #endif

@@ -46,3 +46,25 @@ def orbit(dims, azimuth_deg, elevation_deg, distance_factor=1.6, fovy_deg=45.0, 
     eye = c + r * np.array([np.cos(el) * np.cos(az), np.cos(el) * np.sin(az), np.sin(el)])
     up = (0.0, 0.0, 1.0)
     return look_at_perspective(fovy_deg, aspect, 0.05 * r, 3.0 * r, eye, c, up)
+
+
+def pinhole(eye, target, fovy_deg, aspect, up=(0.0, 0.0, 1.0)):
+    """Ray-casting camera: (eye, forward, right, up) as float32 3-vectors;
+    the ray of image point (u, v) in [-1, 1]^2 has direction forward +
+    u * right + v * up (right and up scaled to the half field of view)."""
+    f = np.asarray(target, float) - np.asarray(eye, float)
+    f /= np.linalg.norm(f)
+    r = np.cross(f, np.asarray(up, float))
+    r /= np.linalg.norm(r)
+    u = np.cross(r, f)
+    th = np.tan(np.radians(fovy_deg) / 2)
+    return tuple(np.asarray(x, np.float32) for x in (eye, f, r * th * aspect, u * th))
+
+
+def pinhole_orbit(dims, azimuth_deg, elevation_deg, distance_factor=1.6, fovy_deg=45.0, aspect=16 / 9):
+    """A ray-casting camera on a sphere around the volume's centre."""
+    c = np.asarray(dims, float) / 2
+    r = distance_factor * float(np.linalg.norm(dims))
+    az, el = np.radians(azimuth_deg), np.radians(elevation_deg)
+    eye = c + r * np.array([np.cos(el) * np.cos(az), np.cos(el) * np.sin(az), np.sin(el)])
+    return pinhole(eye, c, fovy_deg, aspect)
