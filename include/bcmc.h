@@ -234,6 +234,50 @@ int iso_render(const void *d_vertices, int vertex_format, const uint32_t *d_indi
                uint32_t nx, uint32_t ny, uint32_t nz, const iso_camera *camera, uint64_t *d_fragments,
                uint32_t *d_rgba, iso_render_stats *stats, void *stream);
 
+/* ---- implicit isosurface ray casting (Section 4.6.2, future work) ----
+ * The blocks serve as a macrocell grid for space skipping and the surface
+ * is the isovalue set of the trilinear interpolant of the decoded samples,
+ * read from the volume's block cache. */
+typedef struct iso_pinhole {
+    float eye[3];              /* ray origin, voxel coordinates */
+    float forward[3];          /* direction through the image centre */
+    float right[3], up[3];     /* image x and y at the image edge: the ray of pixel (i, j) has
+                                  direction forward + u right + v up, u = (i + 0.5) / width * 2 - 1,
+                                  v = (j + 0.5) / height * 2 - 1 (row 0 at the bottom) */
+    float light[3];            /* direction towards the light (normalised by the library) */
+    uint32_t width, height;    /* pixels, 1..32768 each */
+} iso_pinhole;
+
+typedef struct iso_raycast_stats {
+    uint64_t hits;             /* pixels whose ray meets the surface */
+    uint32_t n_active;         /* active blocks of the isovalue (Section 4.1) */
+    uint32_t n_new;            /* of them, decoded into the cache by this call */
+    uint32_t n_slots;          /* cache slots in use */
+    uint32_t reserved;
+} iso_raycast_stats;
+
+/* Ray cast the isosurface at `isovalue` into headless device buffers.
+ * First the extraction's front runs for the isovalue (range test, cache
+ * update, decode: afterwards the cache holds what iso_extract would leave),
+ * then one thread per pixel: rays start at t = 0 or where they enter the
+ * volume box [0, n-1]^3 and visit blocks (the cells of block b span
+ * [4b, min(4b + 4, n - 1)] per axis), then cells, in ray order, each box's
+ * interval by its own slab test and the next box one step along the exit
+ * axis; a block is searched when its 2x2x2 group range holds the isovalue,
+ * a cell when its 8 corners' range does (lo < iso <= hi, a sample equal to
+ * iso counting as above); in a cell the interpolant is sampled at the ends
+ * and 3 interior quarter points of the ray's interval, and 12 bisection
+ * steps refine the first change of side.  Every float operation is one
+ * IEEE float32 operation.
+ *   d_hits  uint64[height * width]: (t bits << 32 | block id) of the first
+ *           hit (t in units of the ray direction's length), ~0 for none
+ *   d_rgba  uint32[height * width] or NULL: two-sided Lambert shading from
+ *           the interpolant's gradient at the hit, as iso_render; 0 for none
+ * Blocks until done.  ISO_ERR_BUDGET when the active blocks do not fit in
+ * the cache (no waves here); other errors as iso_extract. */
+int iso_raycast(iso_volume *v, float isovalue, const iso_pinhole *camera, uint64_t *d_hits, uint32_t *d_rgba,
+                iso_raycast_stats *stats);
+
 /* The full-volume baseline the paper measures against (the naive
  * data-parallel marching cubes of Section 3 over the whole decompressed
  * volume): the same pipeline with the range test switched off, so every

@@ -83,6 +83,17 @@ class _RenderStats(ctypes.Structure):
     _fields_ = [("drawn", ctypes.c_uint64), ("big", ctypes.c_uint64)]
 
 
+class _Pinhole(ctypes.Structure):
+    _fields_ = [("eye", ctypes.c_float * 3), ("forward", ctypes.c_float * 3), ("right", ctypes.c_float * 3),
+                ("up", ctypes.c_float * 3), ("light", ctypes.c_float * 3), ("width", ctypes.c_uint32),
+                ("height", ctypes.c_uint32)]
+
+
+class _CastStats(ctypes.Structure):
+    _fields_ = [("hits", ctypes.c_uint64), ("n_active", ctypes.c_uint32), ("n_new", ctypes.c_uint32),
+                ("n_slots", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
 class _Mesh(ctypes.Structure):
     _fields_ = [("d_vertices", ctypes.c_void_p), ("num_triangles", ctypes.c_uint64),
                 ("capacity_triangles", ctypes.c_uint64), ("stats", _Stats), ("priv", ctypes.c_void_p)]
@@ -109,6 +120,7 @@ def lib():
             "iso_extract_indexed_into": (i32, [P, ctypes.c_float, i32, P, u64, P, u64, ctypes.POINTER(_Stats)]),
             "iso_render": (i32, [P, i32, P, u64, u32, u32, u32, ctypes.POINTER(_Camera), P, P,
                                  ctypes.POINTER(_RenderStats), P]),
+            "iso_raycast": (i32, [P, ctypes.c_float, ctypes.POINTER(_Pinhole), P, P, ctypes.POINTER(_CastStats)]),
             "iso_decode_volume": (i32, [P, u32, u32, u32, u32, P, P]),
             "iso_mesh_release": (i32, [P, ctypes.POINTER(_Mesh)]),
             "iso_release": (None, [P]),
@@ -339,6 +351,27 @@ class Volume:
             st = self.extract_indexed_into(iso, verts, idx, check=False)
         _check(st["status"], "iso_extract_indexed_into")
         return verts[:st["num_vertices"]], idx[:st["num_triangles"]], st
+
+    def raycast(self, iso, eye, forward, right, up, light, width, height, hits=None, rgba=None):
+        """Ray cast the isosurface (rules in iso_raycast) into CUDA buffers:
+        returns (hits int64 (height, width): t bits << 32 | block id, -1 for
+        none; rgba int32 (height, width) or None with rgba=False; stats)."""
+        import torch
+        if hits is None:
+            hits = torch.empty((height, width), dtype=torch.int64, device="cuda")
+        if rgba is None:
+            rgba = torch.empty((height, width), dtype=torch.int32, device="cuda")
+        cam = _Pinhole()
+        for name, vec in (("eye", eye), ("forward", forward), ("right", right), ("up", up), ("light", light)):
+            arr = getattr(cam, name)
+            for k in range(3):
+                arr[k] = float(vec[k])
+        cam.width, cam.height = int(width), int(height)
+        st = _CastStats()
+        _check(lib().iso_raycast(self._h, ctypes.c_float(iso), ctypes.byref(cam), _ptr(hits),
+                                 _ptr(rgba) if rgba is not False else None, ctypes.byref(st)), "iso_raycast")
+        return hits, (rgba if rgba is not False else None), {
+            "hits": int(st.hits), "n_active": int(st.n_active), "n_new": int(st.n_new), "n_slots": int(st.n_slots)}
 
     STAGES = ("prep", "cull", "cache_update", "decode", "count", "scan", "emit")
 

@@ -16,9 +16,10 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libbcmc.so")
 SOURCES = ["api.cu", "batch.cu", "serve.cu", "extract.cu", "mc.cu", "codec.cu", "mc_tables.cu", "static_scratch.cu",
-           "render.cu"]
-# the rasteriser states every float operation (no multiply-add contraction)
-FILE_FLAGS = {"render.cu": ["-fmad=false", "-Xcompiler", "-ffp-contract=off"]}
+           "render.cu", "raycast.cu"]
+# the rasteriser and the ray caster state every float operation (no multiply-add contraction)
+_EXACT = ["-fmad=false", "-Xcompiler", "-ffp-contract=off"]
+FILE_FLAGS = {"render.cu": _EXACT, "raycast.cu": _EXACT}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", CSRC, "-I", os.path.join(ROOT, "include")]
