@@ -370,6 +370,26 @@ def measure_render(bc, vol, torch, stream, tmax, vmax, frames=10):
                      "GBps": nbytes / (ms / 1000.0) / 1e9, "frac_of_measured_hbm": nbytes / (ms / 1000.0) / 1e9 / peak}
     covered = int((frag != -1).sum())
     out["pixels_covered"] = covered
+    # implicit ray casting of the same surface over the block macrocell grid
+    # (the cache already holds the isovalue's blocks: the call's front
+    # decodes nothing new)
+    cam = cameras.pinhole_orbit(DIMS, 30.0, 25.0, distance_factor=1.1, fovy_deg=45.0, aspect=w / h)
+    hits = torch.empty((h, w), dtype=torch.int64, device="cuda")
+    for _ in range(2):
+        _, _, cst = vol.raycast(RENDER_ISO, *cam, light, w, h, hits=hits, rgba=rgba)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(frames):
+        vol.raycast(RENDER_ISO, *cam, light, w, h, hits=hits, rgba=rgba)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / frames
+    out["raycast"] = {"ms_per_frame": ms, "fps": 1000.0 / ms, "rays_per_s": w * h / (ms / 1000.0),
+                      "hits": cst["hits"], "n_active": cst["n_active"], "n_new": cst["n_new"],
+                      "what": "iso_raycast per frame: range test, cache update (no new blocks), one thread per "
+                              "pixel over blocks whose 2x2x2 range holds the isovalue, then cells"}
+    del hits
     out["what"] = ("iso_render per frame: fragment clear, one thread per small triangle, one warp per triangle "
                    "over 32 pixel centres, 64-bit atomicMin on (depth, triangle), Lambert shading to RGBA8")
     del soup, packed, v4, idx, frag, rgba

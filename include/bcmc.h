@@ -262,7 +262,8 @@ typedef struct iso_raycast_stats {
  * then one thread per pixel: rays start at t = 0 or where they enter the
  * volume box [0, n-1]^3 and visit blocks (the cells of block b span
  * [4b, min(4b + 4, n - 1)] per axis), then cells, in ray order, each box's
- * interval by its own slab test and the next box one step along the exit
+ * interval by its own slab test ((bound - origin) times the direction's
+ * reciprocal, taken once per ray) and the next box one step along the exit
  * axis; a block is searched when its 2x2x2 group range holds the isovalue,
  * a cell when its 8 corners' range does (lo < iso <= hi, a sample equal to
  * iso counting as above); in a cell the interpolant is sampled at the ends

@@ -12,9 +12,10 @@
  *              direction d = forward + u * right + v * up, t >= 0
  *   slab       the interval of t inside a box [lo, hi] (per axis: if
  *              d_a == 0 the axis admits every t when lo_a <= o_a <= hi_a,
- *              none otherwise; else (lo_a - o_a) / d_a and (hi_a - o_a) / d_a,
- *              ordered); t_in = max over axes, t_out = min, the exit axis is
- *              the first axis whose upper value is t_out
+ *              none otherwise; else (lo_a - o_a) r_a and (hi_a - o_a) r_a,
+ *              ordered, with r_a = 1 / d_a rounded once per ray); t_in = max
+ *              over axes, t_out = min, the exit axis is the first axis whose
+ *              upper value is t_out
  *   cells      the dual cells of the samples: cell (x, y, z), x in
  *              [0, nx - 2], covers [x, x + 1] x ...; block b holds the cells
  *              x in [4 bx, min(4 bx + 3, nx - 2)], its box [4 bx, min(4 bx + 4,
@@ -44,7 +45,7 @@
 #include <string.h>
 
 typedef struct {
-    float o[3], d[3];
+    float o[3], d[3], inv[3];   /* inv = 1 / d (0 where d == 0: unused) */
 } ray_t;
 
 static uint32_t fbits(float f)
@@ -64,7 +65,7 @@ static int slab(const ray_t *r, const float lo[3], const float hi[3], float *tin
             if (r->o[k] < lo[k] || r->o[k] > hi[k]) return 0;
             continue;
         }
-        float t0 = (lo[k] - r->o[k]) / r->d[k], t1 = (hi[k] - r->o[k]) / r->d[k];
+        float t0 = (lo[k] - r->o[k]) * r->inv[k], t1 = (hi[k] - r->o[k]) * r->inv[k];
         float mn = t0 < t1 ? t0 : t1, mx = t0 < t1 ? t1 : t0;
         if (mn > a) a = mn;
         if (mx < b) {
@@ -232,6 +233,7 @@ void orc_raycast(const float *field, int nx, int ny, int nz, float iso, const fl
             for (int k = 0; k < 3; k++) {
                 r.o[k] = eye[k];
                 r.d[k] = fwd[k] + u * right[k] + v * up[k];
+                r.inv[k] = r.d[k] == 0.0f ? 0.0f : 1.0f / r.d[k];
             }
             int64_t px = (int64_t)j * width + i;
             float t;

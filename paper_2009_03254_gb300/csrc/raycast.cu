@@ -11,8 +11,9 @@
 //   - a slab test against the volume box gives the start; the block, then
 //     the cell, holding the current point starts each level;
 //   - each box's interval comes from its own slab test (not an
-//     incremental update), and the next box is one step along the exit
-//     axis, so the visited boxes and their intervals are fixed by the ray;
+//     incremental update; the direction's reciprocal is taken once per
+//     ray), and the next box is one step along the exit axis, so the
+//     visited boxes and their intervals are fixed by the ray;
 //   - a block is searched when its precomputed group range (hull8) holds
 //     the isovalue; a cell when its 8 corners' range does: 5 samples of the
 //     trilinear interpolant on its interval, then 12 bisection steps at the
@@ -50,7 +51,7 @@ struct CastArgs {
 };
 
 struct Ray {
-    float o[3], d[3];
+    float o[3], d[3], inv[3];     // inv = 1 / d (0 where d == 0: unused)
 };
 
 __device__ __forceinline__ float inf_f() { return __int_as_float(0x7f800000); }
@@ -68,7 +69,7 @@ __device__ __forceinline__ bool slab(const Ray &r, const float lo[3], const floa
             if (r.o[k] < lo[k] || r.o[k] > hi[k]) return false;
             continue;
         }
-        const float t0 = (lo[k] - r.o[k]) / r.d[k], t1 = (hi[k] - r.o[k]) / r.d[k];
+        const float t0 = (lo[k] - r.o[k]) * r.inv[k], t1 = (hi[k] - r.o[k]) * r.inv[k];
         const float mn = t0 < t1 ? t0 : t1, mx = t0 < t1 ? t1 : t0;
         if (mn > a) a = mn;
         if (mx < b) {
@@ -203,13 +204,26 @@ __device__ bool cast(const CastArgs &a, const Ray &r, int32_t *gs, float &thit, 
                         return true;
                     }
                 }
-                c[cax] += r.d[cax] > 0.0f ? 1 : -1;
-                const int last = 4 * b[cax] + 3 < n[cax] - 2 ? 4 * b[cax] + 3 : n[cax] - 2;
-                if (c[cax] < 4 * b[cax] || c[cax] > last) break;
+                // one step along the exit axis (selects, not an indexed array)
+                bool out = false;
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    if (k != cax) continue;
+                    c[k] += r.d[k] > 0.0f ? 1 : -1;
+                    const int last = 4 * b[k] + 3 < n[k] - 2 ? 4 * b[k] + 3 : n[k] - 2;
+                    out = c[k] < 4 * b[k] || c[k] > last;
+                }
+                if (out) break;
             }
         }
-        b[bax] += r.d[bax] > 0.0f ? 1 : -1;
-        if (b[bax] < 0 || b[bax] >= ncb[bax]) return false;
+        bool out = false;
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            if (k != bax) continue;
+            b[k] += r.d[k] > 0.0f ? 1 : -1;
+            out = b[k] < 0 || b[k] >= ncb[k];
+        }
+        if (out) return false;
         t = bout;
     }
 }
@@ -229,6 +243,7 @@ __global__ void __launch_bounds__(kTile * kTile) raycast_kernel(CastArgs a) {
         for (int k = 0; k < 3; k++) {
             r.o[k] = a.eye[k];
             r.d[k] = a.fwd[k] + u * a.right[k] + v * a.up[k];
+            r.inv[k] = r.d[k] == 0.0f ? 0.0f : 1.0f / r.d[k];
         }
         const size_t px = (size_t)j * a.width + i;
         float t, cv[8];
