@@ -57,7 +57,7 @@ CPU_WINDOW = (256, 256, 128)      # oracle sample: a window of the same field
 CPU_ORIGIN = (128, 128, 192)
 REF_WINDOW = (128, 128, 64)       # per-step sample of the reference arm
 L2_FLUSH_BYTES = 512 << 20
-CTL_BYTES = 168                   # control block (struct Ctl) read back once per surface
+CTL_BYTES = 168                   # control block (struct Ctl): iso_extract reads it back after the scan and after the emission
 KERNELS_PER_SURFACE = 8           # prep, cull, lru_a, lru_b, decode, count, scan, emit
 KERNELS_PER_RESET = 2
 KERNELS = ("cull", "cache_update", "decode", "count", "scan", "emit")
@@ -631,7 +631,7 @@ def run_ours(args):
             torch.cuda.synchronize()
             dt = time.perf_counter() - t0
             e2e = {"value": n_e2e / dt, "unit": "triangles/s", "h2d_bytes_per_step": h2d,
-                   "d2h_bytes_per_step": CTL_BYTES * len(ISOS), "ms_per_step": 1000 * dt / e2e_steps,
+                   "d2h_bytes_per_step": 2 * CTL_BYTES * len(ISOS), "ms_per_step": 1000 * dt / e2e_steps,
                    "load_ms": 1000 * float(np.median(load_s[1:])),
                    "includes": "iso_load_volume from pinned host (upload + allocation + block hulls), "
                                "5 x iso_extract (device-allocated meshes), count readback, release"}

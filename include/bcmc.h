@@ -87,7 +87,8 @@ typedef struct iso_stats {
     uint32_t n_slots;          /* cache slots in use after growth */
     uint64_t cache_bytes;      /* n_slots * 256 */
     uint32_t epoch;            /* 1-based count of extractions on this volume */
-    uint32_t reruns;           /* 1 if the triangle stage ran twice to fit the output */
+    uint32_t reruns;           /* 1 if the output was produced twice to fit (only an over-budget
+                                  iso_extract in waves whose first size guess was too small) */
     uint32_t n_candidates;     /* active blocks whose 2x2x2 +group range contains iso: the
                                   blocks the triangle stage visits */
     uint32_t waves;            /* passes: 1, or the number of waves of an extraction whose active
@@ -124,9 +125,9 @@ int iso_load_volume(iso_volume **out, const void *compressed, size_t compressed_
 
 /* Compute the isosurface at `isovalue` (Sections 4.1-4.5).  The vertex
  * buffer is allocated by the library (stream-ordered) and owned by
- * *out until iso_mesh_release.  Blocks until the counts are known.  If
- * the first guess of the output size is too small, the triangle stage runs
- * again into a larger buffer (stats.reruns = 1).  isovalue must be finite.
+ * *out until iso_mesh_release.  Runs the stages up to the prefix sum,
+ * waits for the triangle count, allocates the mesh at its exact size and
+ * runs the emission (blocks until done).  isovalue must be finite.
  * Over budget (the paper always grows the cache; this library caps it):
  * when the surface's active blocks do not fit in the cache even at the
  * cap, the surface is extracted in waves of consecutive z-layers of blocks,

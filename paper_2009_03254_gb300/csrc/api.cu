@@ -189,7 +189,7 @@ int free_volume(iso_volume *v) {
     (void)cudaGetLastError();
     if (v->host_ctl) cudaFreeHost(v->host_ctl);
     if (v->host_params) cudaFreeHost(v->host_params);
-    for (int k = 0; k < 2; k++) {
+    for (int k = 0; k < 4; k++) {
         if (v->gexec[k]) cudaGraphExecDestroy(v->gexec[k]);
         if (v->graph[k]) cudaGraphDestroy(v->graph[k]);
     }
@@ -201,39 +201,49 @@ int free_volume(iso_volume *v) {
     return ISO_OK;
 }
 
-// Queue one extraction on `st`: copy the parameters in, run the stages,
-// copy the control block out.  With mc_only, only the triangle stage runs
-// again (after a larger output buffer was supplied).  Events between the
-// stages are recorded when profiling (never inside a captured graph).
-int enqueue_pipeline(iso_volume *v, cudaStream_t st, bool mc_only, bool prof, bool indexed) {
+// What one queued pass runs: the whole extraction, the stages up to the
+// scan (the size becomes known), or the emission alone (after the count and
+// scan of the same isovalue).
+enum class Phase { kAll, kCount, kEmit };
+
+// Queue one extraction pass on `st`: copy the parameters in, run the
+// stages, copy the control block out.  Events between the stages are
+// recorded when profiling (never inside a captured graph).
+int enqueue_pipeline(iso_volume *v, cudaStream_t st, Phase phase, bool prof, bool indexed) {
     const bool debug = (v->flags & ISO_DEBUG) != 0;
     const Launch L{nullptr, 1u, single_counters(v), VolEntry{v->s, v->g, v->n_cull_desc, v->n_lru_desc}};
     CK(cudaMemcpyAsync(&v->s.ctl->params, v->host_params, sizeof(Params), cudaMemcpyHostToDevice, st));
-    if (prof) cudaEventRecord(v->ev[0], st);
-    if (!mc_only) {
+    if (prof) cudaEventRecord(phase == Phase::kEmit ? v->ev[ISO_NUM_STAGES + 1] : v->ev[0], st);
+    if (phase != Phase::kEmit) {
         launch_front(L, v->plan, st, prof ? v->ev : nullptr);
         launch_mc_count(L, debug, v->plan, st, indexed);
         if (prof) cudaEventRecord(v->ev[5], st);
         launch_mc_scan(L, v->plan, st);
         if (prof) cudaEventRecord(v->ev[6], st);
     }
-    launch_mc_emit(L, debug, v->plan, st, indexed);
-    if (prof) cudaEventRecord(v->ev[7], st);
+    if (phase != Phase::kCount) {
+        launch_mc_emit(L, debug, v->plan, st, indexed);
+        if (prof) cudaEventRecord(v->ev[7], st);
+    }
     CK(cudaMemcpyAsync(v->host_ctl, v->s.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
     CK(cudaGetLastError());
     return ISO_OK;
 }
 
-// Capture the extraction once per volume (on a private stream: the legacy
-// default stream cannot be captured); launches then go to the volume's
-// stream.  Every per-extraction input comes through Params, so the graph
-// never needs updating.
-int ensure_graph(iso_volume *v, bool indexed) {
-    const int k = indexed ? 1 : 0;
+int graph_kind(Phase phase, bool indexed) {
+    return phase == Phase::kAll ? (indexed ? 1 : 0) : (phase == Phase::kCount ? 2 : 3);
+}
+
+// Capture an extraction pass once per volume and kind (on a private stream:
+// the legacy default stream cannot be captured); launches then go to the
+// volume's stream.  Every per-extraction input comes through Params, so a
+// graph never needs updating.
+int ensure_graph(iso_volume *v, Phase phase, bool indexed) {
+    const int k = graph_kind(phase, indexed);
     if (v->gexec[k]) return ISO_OK;
     if (!v->capture_stream) CK(cudaStreamCreateWithFlags(&v->capture_stream, cudaStreamNonBlocking));
     CK(cudaStreamBeginCapture(v->capture_stream, cudaStreamCaptureModeThreadLocal));
-    const int rc = enqueue_pipeline(v, v->capture_stream, false, false, indexed);
+    const int rc = enqueue_pipeline(v, v->capture_stream, phase, false, indexed);
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(v->capture_stream, &g);
     if (rc != ISO_OK || e != cudaSuccess) {
@@ -255,7 +265,9 @@ void collect_stage_times(iso_volume *v) {
     if (!v->profiling) return;
     for (int k = 0; k < ISO_NUM_STAGES; k++) {
         float ms = 0.0f;
-        if (cudaEventElapsedTime(&ms, v->ev[k], v->ev[k + 1]) != cudaSuccess) {
+        // a separate emission is timed from its own start event
+        cudaEvent_t from = (k == ISO_NUM_STAGES - 1 && v->split_emit) ? v->ev[ISO_NUM_STAGES + 1] : v->ev[k];
+        if (cudaEventElapsedTime(&ms, from, v->ev[k + 1]) != cudaSuccess) {
             (void)cudaGetLastError();
             ms = -1.0f;
         }
@@ -299,7 +311,7 @@ int ensure_voff(iso_volume *v) {
     return ISO_OK;
 }
 
-int run(iso_volume *v, float iso, void *out, unsigned long long cap_tris, bool mc_only,
+int run(iso_volume *v, float iso, void *out, unsigned long long cap_tris, Phase phase = Phase::kAll,
         uint32_t format = kVertexFloat4, uint32_t flags = 0, const Window *w = nullptr,
         const Indexed *ix = nullptr) {
     int rc = ensure_debug_edges(v, cap_tris);
@@ -316,21 +328,26 @@ int run(iso_volume *v, float iso, void *out, unsigned long long cap_tris, bool m
                              ix ? (unsigned long long)(uintptr_t)ix->idx : 0ull,
                              ix ? ix->vert_cap : 0ull,
                              ix ? ix->vtx_base : 0ull};
-    // the graph is captured at the second extraction: a volume extracted
-    // once does not pay for capturing and instantiating it
+    // a pass is captured at the second extraction: a volume extracted once
+    // does not pay for capturing and instantiating graphs
     const bool indexed = ix != nullptr;
-    const bool graph = !mc_only && v->use_graph && !(v->flags & ISO_DEBUG) && !v->profiling && v->extractions > 0;
-    if (!mc_only) v->extractions++;
-    if (graph && ensure_graph(v, indexed) != ISO_OK) v->use_graph = false;   // fall back to plain launches
-    if (graph && v->gexec[indexed ? 1 : 0]) {
-        CK(cudaGraphLaunch(v->gexec[indexed ? 1 : 0], v->stream));
+    const uint64_t before = v->extractions - (phase == Phase::kEmit ? 1 : 0);   // extractions before this one
+    const bool graph = v->use_graph && !(v->flags & ISO_DEBUG) && !v->profiling && before > 0;
+    if (phase != Phase::kEmit) v->extractions++;
+    if (graph && ensure_graph(v, phase, indexed) != ISO_OK) v->use_graph = false;   // plain launches
+    const int gk = graph_kind(phase, indexed);
+    if (graph && v->gexec[gk]) {
+        CK(cudaGraphLaunch(v->gexec[gk], v->stream));
     } else {
-        rc = enqueue_pipeline(v, v->stream, mc_only, v->profiling && !mc_only, indexed);
+        rc = enqueue_pipeline(v, v->stream, phase, v->profiling, indexed);
         if (rc) return rc;
     }
     CK(cudaStreamSynchronize(v->stream));
-    if (!mc_only) {
+    if (phase != Phase::kCount) {
+        v->split_emit = phase == Phase::kEmit;
         collect_stage_times(v);
+    }
+    if (phase != Phase::kEmit) {
         v->last_n_active = v->host_ctl->n_active;
         v->last_n_new = v->host_ctl->n_new;
         v->last_n_cand = v->host_ctl->n_cand;
@@ -393,10 +410,10 @@ int run_waves(iso_volume *v, float iso, void *out, unsigned long long cap_tris, 
             const unsigned long long vroom = ix->vert_cap > vtot ? ix->vert_cap - vtot : 0ull;
             const Indexed wx{(ix->idx && room) ? ix->idx + 3 * tot : nullptr, vroom, ix->vtx_base + vtot};
             void *wout = (out && vroom) ? static_cast<char *>(out) + vtot * vbytes : nullptr;
-            rc = run(v, iso, wout, wx.idx ? room : 0ull, false, format, 0u, &w, &wx);
+            rc = run(v, iso, wout, wx.idx ? room : 0ull, Phase::kAll, format, 0u, &w, &wx);
         } else {
             void *wout = (out && room) ? static_cast<char *>(out) + tot * vbytes : nullptr;
-            rc = run(v, iso, wout, room, false, format, 0u, &w);
+            rc = run(v, iso, wout, room, Phase::kAll, format, 0u, &w);
         }
         if (rc) return rc;
         const Ctl &c = *v->host_ctl;
@@ -426,7 +443,7 @@ int run_waves(iso_volume *v, float iso, void *out, unsigned long long cap_tris, 
 // surface's active blocks exceed the cache.  *total receives T.
 int extract_to(iso_volume *v, float iso, void *out, unsigned long long cap_tris, uint32_t format, uint32_t flags,
                iso_stats *stats, unsigned long long *total, const Indexed *ix = nullptr) {
-    int rc = run(v, iso, out, cap_tris, false, format, flags, nullptr, ix);
+    int rc = run(v, iso, out, cap_tris, Phase::kAll, format, flags, nullptr, ix);
     if (rc == ISO_ERR_BUDGET && !(flags & kParamAllBlocks))
         return run_waves(v, iso, out, cap_tris, format, total, stats, ix);
     *total = v->host_ctl->n_tri;
@@ -678,18 +695,21 @@ int iso_extract(iso_volume *v, float isovalue, iso_mesh *out) {
     if (!v || !out || !std::isfinite(isovalue)) return ISO_ERR_INVALID_ARG;
     DeviceGuard dg(v->device);
     std::memset(out, 0, sizeof(*out));
-    // first guess: the last surface's size plus a margin; with no history,
-    // 2 per block up to 2^24 (a larger surface reruns only the emission)
-    unsigned long long guess = v->last_tris ? v->last_tris + v->last_tris / 4 + 4096
-                                            : std::min<unsigned long long>(2ull * v->g.nb + 4096, 1ull << 24);
+    // the stages up to the scan; the mesh is then allocated at its exact size
+    // and the emission runs alone
+    int rc = run(v, isovalue, nullptr, 0, Phase::kCount);
     float4 *buf = nullptr;
-    {
-        const int arc = dalloc(v, &buf, guess * 3);
-        if (arc) return arc;
-    }
-    int rc = run(v, isovalue, buf, guess, false);
     uint32_t reruns = 0;
+    unsigned long long guess = 0;
     if (rc == ISO_ERR_BUDGET) {           // too many active blocks for the cache: waves
+        // first guess: the last surface's size plus a margin; with no history,
+        // 2 per block up to 2^24 (a larger surface runs the waves again)
+        guess = v->last_tris ? v->last_tris + v->last_tris / 4 + 4096
+                             : std::min<unsigned long long>(2ull * v->g.nb + 4096, 1ull << 24);
+        {
+            const int arc = dalloc(v, &buf, guess * 3);
+            if (arc) return arc;
+        }
         unsigned long long total = 0;
         rc = run_waves(v, isovalue, buf, guess, kVertexFloat4, &total, &out->stats, nullptr);
         if (rc == ISO_OK && total > guess) {   // the waves again into a buffer of the right size
@@ -711,20 +731,14 @@ int iso_extract(iso_volume *v, float isovalue, iso_mesh *out) {
         out->capacity_triangles = guess;
         return ISO_OK;
     }
-    if (rc == ISO_OK && v->host_ctl->n_tri > guess) {
-        const unsigned long long need = v->host_ctl->n_tri;
-        cudaFreeAsync(buf, v->stream);
-        buf = nullptr;
-        {
-            const int arc = dalloc(v, &buf, std::max(need, 1ull) * 3);
-            if (arc) return arc;
-        }
-        guess = std::max(need, 1ull);
-        rc = run(v, isovalue, buf, guess, true);
-        reruns = 1;
+    if (rc == ISO_OK) {
+        guess = std::max(v->host_ctl->n_tri, 1ull);
+        const int arc = dalloc(v, &buf, guess * 3);
+        if (arc) return arc;
+        rc = run(v, isovalue, buf, guess, Phase::kEmit);
     }
     if (rc) {
-        cudaFreeAsync(buf, v->stream);
+        if (buf) cudaFreeAsync(buf, v->stream);
         cudaStreamSynchronize(v->stream);
         fill_stats(*v->host_ctl, &out->stats, reruns);
         return rc;

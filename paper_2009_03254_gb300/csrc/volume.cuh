@@ -23,9 +23,10 @@ struct iso_volume {
     bcmc::Params *host_params = nullptr;   // pinned: this extraction's isovalue, output and capacity
     cudaStream_t capture_stream = nullptr;
     // one extraction: params copy, the stage kernels, count readback; one
-    // graph per output kind (0: triangle soup, 1: indexed mesh)
-    cudaGraph_t graph[2] = {};
-    cudaGraphExec_t gexec[2] = {};
+    // graph per kind (0: triangle soup, 1: indexed mesh, 2: the soup up to
+    // the scan, 3: the emission alone)
+    cudaGraph_t graph[4] = {};
+    cudaGraphExec_t gexec[4] = {};
     bool use_graph = true;
     uint64_t extractions = 0;         // full extractions run so far (the graph is captured at the second)
     // owned device allocations
@@ -36,7 +37,8 @@ struct iso_volume {
     unsigned long long dbg_edges_cap = 0;   // in vertices
     unsigned long long last_vtx = 0;        // vertices of the last indexed extraction
     bool profiling = false;
-    cudaEvent_t ev[ISO_NUM_STAGES + 1] = {};
+    cudaEvent_t ev[ISO_NUM_STAGES + 2] = {};   // stage boundaries, then the start of a separate emission
+    bool split_emit = false;                   // the last emission ran apart from the count and scan
     float stage_ms[ISO_NUM_STAGES] = {};
     unsigned long long last_tris = 0;
     uint32_t last_n_active = 0, last_n_new = 0, last_n_cand = 0, last_slots = 0;

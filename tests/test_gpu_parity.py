@@ -276,7 +276,7 @@ def test_budget_exceeded_then_recovers():
         vol.release()
 
 
-def test_extract_into_capacity_and_rerun():
+def test_extract_into_capacity_and_exact_allocation():
     p = pkg()
     t = torch()
     dims, rate = (32, 32, 32), 8
@@ -284,13 +284,20 @@ def test_extract_into_capacity_and_rerun():
     bits, bmin, bmax = oracle.encode_volume(f, rate)
     ref = oracle.extract(bits, dims, rate, bmin, bmax, 0.0)
     T = ref["num_triangles"]
-    assert T > 2 * bits.shape[0] + 4096        # larger than the library's first guess
     vol = p.Volume(bits, dims, rate, bmin, bmax)
     try:
-        mesh = vol.extract(0.0)                # first guess too small: the triangle stage reruns
-        assert mesh.stats["reruns"] == 1 and mesh.num_triangles == T
-        v = mesh.vertices.cpu().numpy().reshape(-1, 3, 4)
-        assert np.abs(v[:, :, :3] - ref["local_pos"]).max() < POS_TOL
+        # the library sizes the mesh from the count: exactly T, no second pass;
+        # three times (plain launches, then the captured count and emit graphs)
+        for _ in range(3):
+            mesh = vol.extract(0.0)
+            assert mesh.stats["reruns"] == 0 and mesh.num_triangles == T
+            v = mesh.vertices.cpu().numpy().reshape(-1, 3, 4)
+            assert np.abs(v[:, :, :3] - ref["local_pos"]).max() < POS_TOL
+            mesh.release()
+        other = oracle.extract(bits, dims, rate, bmin, bmax, 0.5)
+        mesh = vol.extract(0.5)
+        assert mesh.num_triangles == other["num_triangles"]
+        assert np.abs(mesh.vertices.cpu().numpy().reshape(-1, 3, 4)[:, :, :3] - other["local_pos"]).max() < POS_TOL
         mesh.release()
         small = t.zeros((100, 3, 4), dtype=t.float32, device="cuda")
         with pytest.raises(p.IsoError) as e:
