@@ -215,8 +215,8 @@ typedef struct iso_render_stats {
  * d_indices is NULL; else d_indices[3t + j]) of vertex_format
  * (ISO_VERTEX_FLOAT4 / ISO_VERTEX_PACKED) from a volume of nx*ny*nz
  * samples.  Rules, every float operation a single IEEE float32 operation:
- * sx = (X/W * 0.5 + 0.5) * width, sy likewise (y up, row 0 at the bottom),
- * depth Z/W * 0.5 + 0.5; triangles with a vertex at W <= 0 are not drawn
+ * r = 1/W, sx = (X r * 0.5 + 0.5) * width, sy likewise (y up, row 0 at the
+ * bottom), depth Z r * 0.5 + 0.5; triangles with a vertex at W <= 0 are not drawn
  * (no clipping); pixel centres (i + 0.5, j + 0.5) inside the triangle by
  * edge functions evaluated in a canonical endpoint order, with a top-left
  * rule on ties (a mesh is drawn without cracks or double hits); depth

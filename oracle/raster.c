@@ -15,8 +15,8 @@
  *   clip             (X, Y, Z, W) = M (x, y, z, 1), M row-major, each row
  *                    summed left to right; a triangle with a vertex at
  *                    W <= 0 is not drawn (no clipping)
- *   screen           sx = (X / W * 0.5 + 0.5) * width, sy likewise with
- *                    height (y up), depth d = Z / W * 0.5 + 0.5
+ *   screen           r = 1 / W, sx = (X r * 0.5 + 0.5) * width, sy likewise
+ *                    with height (y up), depth d = Z r * 0.5 + 0.5
  *   edge function    E(a, b; p) = (b.x - a.x)(p.y - a.y) - (b.y - a.y)(p.x - a.x),
  *                    always evaluated with the endpoints in ascending
  *                    (x, then y) order and negated when swapped, so that two
@@ -120,9 +120,10 @@ void orc_raster(const void *verts, int format, const uint32_t *idx, int64_t num_
             float Z = m[8] * p[0] + m[9] * p[1] + m[10] * p[2] + m[11];
             float W = m[12] * p[0] + m[13] * p[1] + m[14] * p[2] + m[15];
             if (!(W > 0.0f)) behind = 1;
-            s[j].x = (X / W * 0.5f + 0.5f) * (float)width;
-            s[j].y = (Y / W * 0.5f + 0.5f) * (float)height;
-            d[j] = Z / W * 0.5f + 0.5f;
+            float rw = 1.0f / W;
+            s[j].x = (X * rw * 0.5f + 0.5f) * (float)width;
+            s[j].y = (Y * rw * 0.5f + 0.5f) * (float)height;
+            d[j] = Z * rw * 0.5f + 0.5f;
         }
         if (behind) continue;
         float A = edge(s[0], s[1], s[2].x, s[2].y);

@@ -10,12 +10,13 @@
 //             + code * (4 / 1023) for compact vertices
 //   clip      (X, Y, Z, W) = M (x, y, z, 1), each row summed left to right;
 //             a triangle with a vertex at W <= 0 is not drawn
-//   screen    sx = (X / W * 0.5 + 0.5) * width, sy likewise (y up),
-//             depth d = Z / W * 0.5 + 0.5
+//   screen    r = 1 / W, sx = (X r * 0.5 + 0.5) * width, sy likewise (y up),
+//             depth d = Z r * 0.5 + 0.5
 //   edges     E(a, b; p) = (b.x - a.x)(p.y - a.y) - (b.y - a.y)(p.x - a.x),
 //             evaluated with the endpoints in ascending (x, y) order and
 //             negated when swapped (shared edges see opposite values, so a
-//             mesh has no cracks and no double hits); counter-clockwise
+//             mesh has no cracks and no double hits; the order and the
+//             differences are taken once per triangle); counter-clockwise
 //             orientation by swapping v1 and v2 when A = E(v0, v1; v2) < 0
 //   coverage  pixel centres in the vertices' bounding box with all three
 //             edge values >= 0, zero only on a top-left edge
@@ -49,6 +50,7 @@ struct RasterArgs {
     unsigned long long *ctr;      // [0] listed, [1] drawn, [2] big (as [0])
     uint32_t format;              // 0 float4, 1 compact
     uint32_t nbx, nby;
+    unsigned long long inv_nbx, inv_nby;   // division magic (block id -> coordinates)
     uint32_t width, height;
     float m[16];
 };
@@ -57,8 +59,32 @@ struct P2 {
     float x, y;
 };
 
+// An edge in canonical (ascending x, then y) endpoint order: its value at
+// p is sign * (dx (p.y - a.y) - dy (p.x - a.x)), the same operations as
+// evaluating it from the endpoints.
+struct Edge {
+    float ax, ay, dx, dy;
+    bool neg;
+    __device__ __forceinline__ void set(P2 a, P2 b) {
+        neg = (b.x < a.x) || (b.x == a.x && b.y < a.y);
+        if (neg) {
+            const P2 t = a;
+            a = b;
+            b = t;
+        }
+        ax = a.x;
+        ay = a.y;
+        dx = b.x - a.x;
+        dy = b.y - a.y;
+    }
+    __device__ __forceinline__ float at(float px, float py) const {
+        const float e = dx * (py - ay) - dy * (px - ax);
+        return neg ? -e : e;
+    }
+};
+
 struct Tri {
-    P2 s[3];
+    Edge e[3];                    // v1 -> v2, v2 -> v0, v0 -> v1 of the counter-clockwise triangle
     float d[3];
     float A;
     int i0, i1, j0, j1;
@@ -80,7 +106,8 @@ __device__ __forceinline__ void world(const RasterArgs &a, unsigned long long k,
         for (int c = 0; c < 3; c++) local[c] = (float)((v.x >> (10 * c)) & 1023u) * kCodeScale;
         id = v.y;
     }
-    const uint32_t bx = id % a.nbx, by = (id / a.nbx) % a.nby, bz = id / (a.nbx * a.nby);
+    const uint32_t q = div_by(id, a.nbx, a.inv_nbx), bz = div_by(q, a.nby, a.inv_nby);
+    const uint32_t bx = id - q * a.nbx, by = q - bz * a.nby;
     p[0] = (float)(4 * bx) + local[0];
     p[1] = (float)(4 * by) + local[1];
     p[2] = (float)(4 * bz) + local[2];
@@ -109,6 +136,7 @@ __device__ __forceinline__ bool top_left(P2 a, P2 b) {
 // projection, orientation and pixel range of triangle t; false: not drawn
 __device__ bool setup(const RasterArgs &a, unsigned long long t, Tri &r) {
     bool behind = false;
+    P2 s[3];
 #pragma unroll
     for (int j = 0; j < 3; j++) {
         float p[3];
@@ -119,26 +147,27 @@ __device__ bool setup(const RasterArgs &a, unsigned long long t, Tri &r) {
         const float Z = m[8] * p[0] + m[9] * p[1] + m[10] * p[2] + m[11];
         const float W = m[12] * p[0] + m[13] * p[1] + m[14] * p[2] + m[15];
         if (!(W > 0.0f)) behind = true;
-        r.s[j].x = (X / W * 0.5f + 0.5f) * (float)a.width;
-        r.s[j].y = (Y / W * 0.5f + 0.5f) * (float)a.height;
-        r.d[j] = Z / W * 0.5f + 0.5f;
+        const float rw = 1.0f / W;
+        s[j].x = (X * rw * 0.5f + 0.5f) * (float)a.width;
+        s[j].y = (Y * rw * 0.5f + 0.5f) * (float)a.height;
+        r.d[j] = Z * rw * 0.5f + 0.5f;
     }
     if (behind) return false;
-    float A = edge(r.s[0], r.s[1], r.s[2].x, r.s[2].y);
+    float A = edge(s[0], s[1], s[2].x, s[2].y);
     if (A == 0.0f || A != A) return false;
     if (A < 0.0f) {
-        const P2 ts = r.s[1];
-        r.s[1] = r.s[2];
-        r.s[2] = ts;
+        const P2 ts = s[1];
+        s[1] = s[2];
+        s[2] = ts;
         const float td = r.d[1];
         r.d[1] = r.d[2];
         r.d[2] = td;
-        A = edge(r.s[0], r.s[1], r.s[2].x, r.s[2].y);
+        A = edge(s[0], s[1], s[2].x, s[2].y);
         if (!(A > 0.0f)) return false;
     }
     r.A = A;
-    const float xmin = fminf(fminf(r.s[0].x, r.s[1].x), r.s[2].x), xmax = fmaxf(fmaxf(r.s[0].x, r.s[1].x), r.s[2].x);
-    const float ymin = fminf(fminf(r.s[0].y, r.s[1].y), r.s[2].y), ymax = fmaxf(fmaxf(r.s[0].y, r.s[1].y), r.s[2].y);
+    const float xmin = fminf(fminf(s[0].x, s[1].x), s[2].x), xmax = fmaxf(fmaxf(s[0].x, s[1].x), s[2].x);
+    const float ymin = fminf(fminf(s[0].y, s[1].y), s[2].y), ymax = fmaxf(fmaxf(s[0].y, s[1].y), s[2].y);
     const float fi0 = ceilf(xmin - 0.5f), fi1 = floorf(xmax - 0.5f);
     const float fj0 = ceilf(ymin - 0.5f), fj1 = floorf(ymax - 0.5f);
     const float wl = (float)(a.width - 1), hl = (float)(a.height - 1);
@@ -147,16 +176,19 @@ __device__ bool setup(const RasterArgs &a, unsigned long long t, Tri &r) {
     r.i1 = fi1 > wl ? (int)a.width - 1 : (int)fi1;
     r.j0 = fj0 < 0.0f ? 0 : (int)fj0;
     r.j1 = fj1 > hl ? (int)a.height - 1 : (int)fj1;
-    r.tl[0] = top_left(r.s[1], r.s[2]);
-    r.tl[1] = top_left(r.s[2], r.s[0]);
-    r.tl[2] = top_left(r.s[0], r.s[1]);
+    r.tl[0] = top_left(s[1], s[2]);
+    r.tl[1] = top_left(s[2], s[0]);
+    r.tl[2] = top_left(s[0], s[1]);
+    r.e[0].set(s[1], s[2]);
+    r.e[1].set(s[2], s[0]);
+    r.e[2].set(s[0], s[1]);
     return true;
 }
 
 // test pixel (i, j) against triangle t and keep the nearer fragment
 __device__ __forceinline__ void fragment(const RasterArgs &a, const Tri &r, uint32_t t, int i, int j) {
     const float px = (float)i + 0.5f, py = (float)j + 0.5f;
-    const float e0 = edge(r.s[1], r.s[2], px, py), e1 = edge(r.s[2], r.s[0], px, py), e2 = edge(r.s[0], r.s[1], px, py);
+    const float e0 = r.e[0].at(px, py), e1 = r.e[1].at(px, py), e2 = r.e[2].at(px, py);
     if (e0 < 0.0f || e1 < 0.0f || e2 < 0.0f) return;
     if ((e0 == 0.0f && !r.tl[0]) || (e1 == 0.0f && !r.tl[1]) || (e2 == 0.0f && !r.tl[2])) return;
     const float dd = (e0 * r.d[0] + e1 * r.d[1] + e2 * r.d[2]) / r.A + 0.0f;
@@ -225,6 +257,8 @@ __global__ void __launch_bounds__(256) shade_kernel(ShadeArgs s) {
     a.format = s.format;
     a.nbx = s.nbx;
     a.nby = s.nby;
+    a.inv_nbx = div_magic(s.nbx);
+    a.inv_nby = div_magic(s.nby);
     const float base[3] = {0.85f, 0.75f, 0.55f};
     const float l2 = s.light[0] * s.light[0] + s.light[1] * s.light[1] + s.light[2] * s.light[2];
     const float linv = 1.0f / sqrtf(l2);
@@ -300,6 +334,8 @@ extern "C" int iso_render(const void *d_vertices, int vertex_format, const uint3
     a.format = vertex_format == ISO_VERTEX_PACKED ? 1u : 0u;
     a.nbx = (nx + 3) / 4;
     a.nby = (ny + 3) / 4;
+    a.inv_nbx = div_magic(a.nbx);
+    a.inv_nby = div_magic(a.nby);
     a.width = camera->width;
     a.height = camera->height;
     for (int k = 0; k < 16; k++) a.m[k] = camera->view_proj[k];
