@@ -62,6 +62,7 @@ extern "C" {
 #define ISO_ERR_TIMEOUT 5      /* a device-side wait gave up (bounded spin) */
 #define ISO_ERR_CAPACITY 6     /* the caller's vertex buffer is too small */
 #define ISO_PENDING 7          /* a served request is not finished yet (not an error) */
+#define ISO_ERR_CORRUPT 8      /* the block ranges given at load are not ranges (NaN, or min > max) */
 
 /* iso_options.flags */
 #define ISO_INPUT_ON_DEVICE 1u /* compressed/block_min/block_max are device pointers */
@@ -103,6 +104,21 @@ typedef struct iso_mesh {
     iso_stats stats;
     void *priv;                /* library bookkeeping; do not touch */
 } iso_mesh;
+
+/* Device memory.  By default the library allocates from a stream-ordered
+ * memory pool of its own per device, which keeps freed memory for reuse.
+ * iso_set_allocator routes every later device allocation of the library
+ * (volume state, meshes, scratch of batches, servers and renders) through
+ * the caller: alloc(bytes, device, stream, ctx) returns memory usable in
+ * the order of `stream` (NULL for failure: ISO_ERR_OOM), free(ptr, device,
+ * stream, ctx) takes it back in that stream's order (a PyTorch caching
+ * allocator fits both).  Each allocation is returned to the allocator that
+ * made it, even after the hook changes.  alloc and free must both be set or
+ * both be NULL (NULL: back to the pool).  Process-wide; call it while no
+ * other thread is inside the library. */
+typedef void *(*iso_alloc_fn)(size_t bytes, int device, void *stream, void *ctx);
+typedef void (*iso_free_fn)(void *ptr, int device, void *stream, void *ctx);
+int iso_set_allocator(iso_alloc_fn alloc, iso_free_fn free_fn, void *ctx);
 
 /* Upload a compressed volume and set up its cache (Section 4: "uploading
  * the ZFP fixed-rate compressed data to the GPU"; Section 4.1: "precompute
@@ -513,6 +529,11 @@ int iso_server_queued(const iso_server *s, uint32_t *queued);
  * stats: n_active, n_new, n_slots, cache_bytes and epoch describe the
  * tick's union; num_triangles, n_occupied, n_candidates the request. */
 int iso_server_take(iso_server *s, uint64_t ticket, iso_mesh *out);
+
+/* Step the server until `ticket` is finished or timeout_ms milliseconds
+ * have passed (0: look once, no step), then return as iso_server_take
+ * (ISO_PENDING on timeout; a step's own error is returned as it comes). */
+int iso_server_wait(iso_server *s, uint64_t ticket, uint32_t timeout_ms, iso_mesh *out);
 
 /* Free the server, its queue and any finished meshes not taken. */
 void iso_server_destroy(iso_server *s);

@@ -24,6 +24,7 @@ ISO_ERR_CUDA = 4
 ISO_ERR_TIMEOUT = 5
 ISO_ERR_CAPACITY = 6
 ISO_PENDING = 7
+ISO_ERR_CORRUPT = 8
 
 ISO_INPUT_ON_DEVICE = 1
 ISO_DEBUG = 2
@@ -146,6 +147,8 @@ def lib():
             "iso_server_step": (i32, [P, ctypes.POINTER(u32)]),
             "iso_server_queued": (i32, [P, ctypes.POINTER(u32)]),
             "iso_server_take": (i32, [P, u64, ctypes.POINTER(_Mesh)]),
+            "iso_server_wait": (i32, [P, u64, u32, ctypes.POINTER(_Mesh)]),
+            "iso_set_allocator": (i32, [P, P, P]),
             "iso_server_destroy": (None, [P]),
         }
         for name, (res, args) in sig.items():
@@ -553,6 +556,17 @@ class Server:
             return rc, None
         return rc, Mesh(self.volume, m)
 
+    def wait(self, ticket, timeout_ms=1000):
+        """Step until the ticket is done or the timeout passes: (status, Mesh
+        or None) as take (ISO_PENDING on timeout)."""
+        m = _Mesh()
+        rc = lib().iso_server_wait(self._h, int(ticket), int(timeout_ms), ctypes.byref(m))
+        if rc == ISO_ERR_INVALID_ARG:
+            raise IsoError(rc, "iso_server_wait")
+        if rc != ISO_OK:
+            return rc, None
+        return rc, Mesh(self.volume, m)
+
     def release(self):
         if self._h:
             lib().iso_server_destroy(self._h)
@@ -563,6 +577,38 @@ class Server:
             self.release()
         except Exception:
             pass
+
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p)
+_hooks = []                           # the installed callbacks (kept alive)
+
+
+def use_torch_allocator():
+    """Route the library's device allocations through PyTorch's caching
+    allocator (iso_set_allocator), in the order of the stream each is made
+    on."""
+    import torch
+
+    def alloc(nbytes, device, stream, ctx):
+        try:
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes), device=int(device), stream=int(stream or 0)))
+        except RuntimeError:
+            return None
+
+    def free(ptr, device, stream, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    a, f = _ALLOC_FN(alloc), _FREE_FN(free)
+    _check(lib().iso_set_allocator(ctypes.cast(a, ctypes.c_void_p), ctypes.cast(f, ctypes.c_void_p), None),
+           "iso_set_allocator")
+    _hooks.append((a, f))
+
+
+def use_pool_allocator():
+    """Back to the library's own stream-ordered memory pool (allocations
+    made through an earlier hook still go back to it)."""
+    _check(lib().iso_set_allocator(None, None, None), "iso_set_allocator")
 
 
 def render(vertices, num_triangles, dims, view_proj, light, width, height, indices=None, fragments=None,

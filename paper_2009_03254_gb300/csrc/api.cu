@@ -6,6 +6,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <unordered_map>
 #include <vector>
 
 #include "bcmc.h"
@@ -56,9 +57,35 @@ cudaMemPool_t device_pool(int dev) {
     return g_pool[dev];
 }
 
+// A caller's allocator (iso_set_allocator); every allocation it makes is
+// remembered with its free function and device, so it goes back to it.
+struct HookAllocator {
+    iso_alloc_fn alloc = nullptr;
+    iso_free_fn free = nullptr;
+    void *ctx = nullptr;
+    int device = 0;
+};
+std::mutex g_alloc_mutex;
+HookAllocator g_hook;
+std::unordered_map<void *, HookAllocator> g_hooked;
+
 int dalloc_bytes(void **p, size_t bytes, int dev, cudaStream_t st) {
     *p = nullptr;
     if (bytes == 0) bytes = 1;
+    HookAllocator h;
+    {
+        std::lock_guard<std::mutex> lock(g_alloc_mutex);
+        h = g_hook;
+    }
+    if (h.alloc) {
+        void *q = h.alloc(bytes, dev, st, h.ctx);
+        if (!q) return ISO_ERR_OOM;
+        h.device = dev;
+        std::lock_guard<std::mutex> lock(g_alloc_mutex);
+        g_hooked[q] = h;
+        *p = q;
+        return ISO_OK;
+    }
     cudaMemPool_t pool = device_pool(dev);
     if (pool) {
         ISO_CK(cudaMallocFromPoolAsync(p, bytes, pool, st));
@@ -69,7 +96,20 @@ int dalloc_bytes(void **p, size_t bytes, int dev, cudaStream_t st) {
 }
 
 void dfree_on(void *p, cudaStream_t st) {
-    if (p) cudaFreeAsync(p, st);
+    if (!p) return;
+    HookAllocator h;
+    bool hooked = false;
+    {
+        std::lock_guard<std::mutex> lock(g_alloc_mutex);
+        auto it = g_hooked.find(p);
+        if (it != g_hooked.end()) {
+            h = it->second;
+            g_hooked.erase(it);
+            hooked = true;
+        }
+    }
+    if (hooked) h.free(p, h.device, st, h.ctx);
+    else cudaFreeAsync(p, st);
 }
 
 Plan default_tiles(const Plan *want) {
@@ -467,8 +507,18 @@ bool build_tables_once(McTables *t) {
 
 extern "C" {
 
+int iso_set_allocator(iso_alloc_fn alloc, iso_free_fn free_fn, void *ctx) {
+    if ((alloc == nullptr) != (free_fn == nullptr)) return ISO_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(g_alloc_mutex);
+    g_hook.alloc = alloc;
+    g_hook.free = free_fn;
+    g_hook.ctx = alloc ? ctx : nullptr;
+    return ISO_OK;
+}
+
 const char *iso_error_string(int status) {
     switch (status) {
+        case ISO_ERR_CORRUPT: return "block ranges are not ranges (NaN, or min > max)";
         case ISO_OK: return "ok";
         case ISO_ERR_INVALID_ARG: return "invalid argument";
         case ISO_ERR_OOM: return "out of memory";
@@ -617,12 +667,18 @@ int iso_load_volume(iso_volume **out, const void *compressed, size_t compressed_
     *v->host_ctl = c0;
     TRYC(cudaMemcpyAsync(s.ctl, v->host_ctl, sizeof(Ctl), cudaMemcpyHostToDevice, st));
     // the ranges are needed only for the hulls (device inputs are read in place)
-    launch_hull(on_device ? block_min : v->bmin, on_device ? block_max : v->bmax, v->hull, v->hull8, g, st);
+    launch_hull(on_device ? block_min : v->bmin, on_device ? block_max : v->bmax, v->hull, v->hull8, g,
+                &s.ctl->status, st);
     TRYC(cudaGetLastError());
     dfree_on(v->bmin, st);
     dfree_on(v->bmax, st);
     v->bmin = v->bmax = nullptr;
+    TRYC(cudaMemcpyAsync(v->host_ctl, s.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
     TRYC(cudaStreamSynchronize(st));
+    if (v->host_ctl->status & kStatusCorrupt) {   // ranges that are not ranges: nothing to cull with
+        free_volume(v);
+        return ISO_ERR_CORRUPT;
+    }
     v->plan = launch_plan(nullptr, v->device, g.nb, v->cap, 1, true);
     TRYC(cudaGetLastError());
     *out = v;
@@ -713,7 +769,7 @@ int iso_extract(iso_volume *v, float isovalue, iso_mesh *out) {
         unsigned long long total = 0;
         rc = run_waves(v, isovalue, buf, guess, kVertexFloat4, &total, &out->stats, nullptr);
         if (rc == ISO_OK && total > guess) {   // the waves again into a buffer of the right size
-            cudaFreeAsync(buf, v->stream);
+            dfree_on(buf, v->stream);
             buf = nullptr;
             const int arc = dalloc(v, &buf, std::max(total, 1ull) * 3);
             if (arc) return arc;
@@ -722,7 +778,7 @@ int iso_extract(iso_volume *v, float isovalue, iso_mesh *out) {
             out->stats.reruns = 1;
         }
         if (rc) {
-            cudaFreeAsync(buf, v->stream);
+            dfree_on(buf, v->stream);
             cudaStreamSynchronize(v->stream);
             return rc;
         }
@@ -738,7 +794,7 @@ int iso_extract(iso_volume *v, float isovalue, iso_mesh *out) {
         rc = run(v, isovalue, buf, guess, Phase::kEmit);
     }
     if (rc) {
-        if (buf) cudaFreeAsync(buf, v->stream);
+        dfree_on(buf, v->stream);
         cudaStreamSynchronize(v->stream);
         fill_stats(*v->host_ctl, &out->stats, reruns);
         return rc;
@@ -755,7 +811,8 @@ int iso_mesh_release(iso_volume *v, iso_mesh *m) {
     if (!m->d_vertices) return ISO_OK;
     if (!v) return ISO_ERR_INVALID_ARG;
     DeviceGuard dg(v->device);
-    CK(cudaFreeAsync(m->d_vertices, v->stream));
+    dfree_on(m->d_vertices, v->stream);
+    CK(cudaGetLastError());
     m->d_vertices = nullptr;
     m->num_triangles = 0;
     m->capacity_triangles = 0;

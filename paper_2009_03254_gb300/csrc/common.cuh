@@ -50,6 +50,7 @@ enum Status : uint32_t {
     kStatusBudget = 2u,       // new blocks do not fit in the slot cap
     kStatusTimeoutLru = 4u,   // cache-update look-back gave up
     kStatusTimeoutScan = 8u,  // triangle-offset look-back gave up
+    kStatusCorrupt = 16u,     // a block range given at load is not a range (set by the hull kernel)
 };
 constexpr uint32_t kStatusAnyTimeout = kStatusTimeout | kStatusTimeoutLru | kStatusTimeoutScan;
 

@@ -504,11 +504,12 @@ void launch_count_layers(const float2 *hull, const Geom &g, float iso, uint32_t 
 // per block: min/max of the block ranges over its 3x3x3 block neighbourhood
 // (hull) and over its 2x2x2 +group (hull8)
 __global__ void hull_kernel(const float *__restrict__ bmin, const float *__restrict__ bmax, float2 *hull,
-                            float2 *hull8, Geom g) {
+                            float2 *hull8, Geom g, uint32_t *status) {
     const uint32_t slab = g.nbx * g.nby;
     for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < g.nb; b += gridDim.x * blockDim.x) {
         const int bx = (int)(b % g.nbx), by = (int)((b / g.nbx) % g.nby), bz = (int)(b / slab);
         float lo = bmin[b], hi = bmax[b], lo8 = lo, hi8 = hi;
+        if (!(lo <= hi)) atomicOr(status, (uint32_t)kStatusCorrupt);   // NaN, or min > max
         for (int dz = -1; dz <= 1; dz++) {
             const int z = bz + dz;
             if (z < 0 || z >= (int)g.nbz) continue;
@@ -612,9 +613,9 @@ void launch_batch_gather(const Launch &L, Ctl *dst, cudaStream_t st) {
 }
 
 void launch_hull(const float *bmin, const float *bmax, float2 *hull, float2 *hull8, const Geom &g,
-                 cudaStream_t st) {
+                 uint32_t *status, cudaStream_t st) {
     const uint32_t blocks = std::min<uint32_t>((g.nb + 255) / 256, 65535u * 4);
-    hull_kernel<<<blocks, 256, 0, st>>>(bmin, bmax, hull, hull8, g);
+    hull_kernel<<<blocks, 256, 0, st>>>(bmin, bmax, hull, hull8, g, status);
 }
 
 void launch_reset_cache(const DevState &s, cudaStream_t st) {

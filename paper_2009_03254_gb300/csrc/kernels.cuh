@@ -111,7 +111,7 @@ void launch_batch_offsets(const Launch &L, const BatchOut *bo, unsigned long lon
 void launch_batch_gather(const Launch &L, Ctl *dst, cudaStream_t st);
 
 void launch_hull(const float *bmin, const float *bmax, float2 *hull, float2 *hull8, const Geom &g,
-                 cudaStream_t st);
+                 uint32_t *status, cudaStream_t st);
 void launch_reset_cache(const DevState &s, cudaStream_t st);
 void launch_encode(const float *field, const Geom &g, uint64_t *bits, float *bmin, float *bmax, cudaStream_t st);
 void launch_decode_list(const uint64_t *bits, uint32_t rate, const uint32_t *ids, uint64_t n, float *out,

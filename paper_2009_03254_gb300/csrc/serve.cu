@@ -21,6 +21,7 @@
 // tick's requests go back to the queue and the next ticks take half as
 // many (down to one).
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <deque>
@@ -539,6 +540,20 @@ int iso_server_take(iso_server *sv, uint64_t ticket, iso_mesh *out) {
     if (out->d_vertices) sv->held_bytes -= 48ull * out->num_triangles;
     sv->done.erase(it);
     return status;
+}
+
+int iso_server_wait(iso_server *sv, uint64_t ticket, uint32_t timeout_ms, iso_mesh *out) {
+    if (!sv || !out) return ISO_ERR_INVALID_ARG;
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        const int rc = iso_server_take(sv, ticket, out);
+        if (rc != ISO_PENDING) return rc;
+        const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0);
+        if ((uint64_t)ms.count() >= timeout_ms) return ISO_PENDING;
+        uint32_t n = 0;
+        const int src = iso_server_step(sv, &n);
+        if (src != ISO_OK) return src;
+    }
 }
 
 void iso_server_destroy(iso_server *sv) { free_server(sv); }

@@ -1,0 +1,119 @@
+"""GPU tests of the boundary's remaining calls: the caller-supplied
+allocator (PyTorch's caching allocator through iso_set_allocator), block
+ranges that are not ranges (ISO_ERR_CORRUPT at load), and waiting on a
+served request (iso_server_wait).  Meshes are checked against the oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from synth import fields
+
+pytestmark = pytest.mark.gpu
+
+POS_TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def pkg():
+    import paper_2009_03254_gb300 as p
+    return p
+
+
+def volume_data(dims=(40, 36, 30), rate=8, seed=3):
+    f = fields.gradient_noise(*dims, seed, octaves=4, base_period=16)
+    bits, bmin, bmax = oracle.encode_volume(f, rate)
+    return dims, rate, bits, bmin, bmax
+
+
+def test_torch_allocator_serves_every_allocation():
+    import torch
+    p = pkg()
+    dims, rate, bits, bmin, bmax = volume_data()
+    ref = oracle.extract(bits, dims, rate, bmin, bmax, 0.0)
+    torch.cuda.synchronize()
+    base = torch.cuda.memory_allocated()
+    p.use_torch_allocator()
+    try:
+        vol = p.Volume(bits, dims, rate, bmin, bmax)
+        torch.cuda.synchronize()
+        held = torch.cuda.memory_allocated() - base
+        assert held >= bits.nbytes                    # the volume's state came from PyTorch
+        m = vol.extract(0.0)
+        assert m.num_triangles == ref["num_triangles"]
+        v = m.vertices.cpu().numpy().reshape(-1, 3, 4)
+        assert np.abs(v[:, :, :3] - ref["local_pos"]).max() < POS_TOL
+        assert torch.cuda.memory_allocated() - base >= held + 48 * m.num_triangles
+    finally:
+        p.use_pool_allocator()
+    # made under the hook, freed after switching back: still returned to PyTorch
+    m.release()
+    vol.release()
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() == base
+    # and the pool serves again
+    vol = p.Volume(bits, dims, rate, bmin, bmax)
+    m = vol.extract(0.0)
+    assert m.num_triangles == ref["num_triangles"]
+    m.release()
+    vol.release()
+    assert torch.cuda.memory_allocated() == base
+    # an allocation function without a free function is refused (and never called)
+    import ctypes
+    assert p.lib().iso_set_allocator(ctypes.c_void_p(1), None, None) == p.ISO_ERR_INVALID_ARG
+
+
+def test_ranges_that_are_not_ranges_are_refused():
+    import torch
+    p = pkg()
+    dims, rate, bits, bmin, bmax = volume_data(dims=(20, 20, 20))
+    for broken in ("swap", "nan_min", "nan_max"):
+        lo, hi = bmin.copy(), bmax.copy()
+        k = 17
+        if broken == "swap":
+            lo[k], hi[k] = hi[k] + 1.0, lo[k]
+        elif broken == "nan_min":
+            lo[k] = np.nan
+        else:
+            hi[k] = np.nan
+        for on_device in (False, True):
+            args = (bits, lo, hi)
+            if on_device:
+                args = (torch.from_numpy(bits.view(np.int64)).cuda(), torch.from_numpy(lo).cuda(),
+                        torch.from_numpy(hi).cuda())
+            with pytest.raises(p.IsoError) as e:
+                p.Volume(args[0], dims, rate, args[1], args[2])
+            assert e.value.code == p.ISO_ERR_CORRUPT
+    vol = p.Volume(bits, dims, rate, bmin, bmax)                   # the real ranges load
+    vol.release()
+
+
+def test_server_wait():
+    p = pkg()
+    dims, rate, bits, bmin, bmax = volume_data(seed=5)
+    vol = p.Volume(bits, dims, rate, bmin, bmax)
+    alone = p.Volume(bits, dims, rate, bmin, bmax)
+    srv = p.Server(vol, max_batch=4)
+    try:
+        isos = [-0.3, 0.0, 0.4]
+        tickets = [srv.submit(x) for x in isos]
+        assert srv.wait(tickets[2], timeout_ms=0) == (p.ISO_PENDING, None)    # look once, no step
+        for t, x in zip(reversed(tickets), reversed(isos)):                   # the last one first
+            status, m = srv.wait(t, timeout_ms=10000)
+            assert status == p.ISO_OK
+            ref = alone.extract(x)
+            assert m.num_triangles == ref.num_triangles
+            assert np.array_equal(m.vertices.cpu().numpy().view(np.uint32), ref.vertices.cpu().numpy().view(np.uint32))
+            m.release()
+            ref.release()
+        with pytest.raises(p.IsoError):
+            srv.wait(tickets[0], timeout_ms=10)                              # already taken
+    finally:
+        srv.release()
+        vol.release()
+        alone.release()
