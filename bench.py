@@ -53,8 +53,8 @@ ISOS = (-1.0, -0.5, 0.0, 0.5, 1.0)
 METRIC = "triangles/s and voxels/s per isosurface on 1 GB300; p50/p99 isovalue-change latency"
 WORKLOAD = ("noise512: 512^3 float32 6-octave gradient noise (seed 1), fixed rate 8 bits/value in 4^3 blocks, "
             "isovalues -1,-0.5,0,0.5,1 extracted in sequence from a cold decoded-block cache")
-CPU_WINDOW = (256, 256, 128)      # oracle sample: a window of the same field
-CPU_ORIGIN = (128, 128, 192)
+CPU_WINDOW = (512, 512, 128)      # oracle sample: a window of the same field (about 11 s on one core)
+CPU_ORIGIN = (0, 0, 192)
 REF_WINDOW = (128, 128, 64)       # per-step sample of the reference arm
 L2_FLUSH_BYTES = 512 << 20
 CTL_BYTES = 168                   # control block (struct Ctl): iso_extract reads it back after the scan and after the emission
@@ -212,11 +212,28 @@ def bytes_full(stats, rate, nb):
 
 # ---------------------------------------------------------------- CPU oracle baseline
 
-def cpu_oracle_sample(window, origin, isos):
+def cpu_sample_volume(window, origin):
+    """The oracle's input for the CPU baseline: the window of the benchmark
+    field (the seeded input generator, on the GPU when there is one: it is
+    bit-identical to the NumPy generator and much faster), encoded by the
+    oracle's own encoder."""
     import oracle
     from synth import fields
-    f = fields.gradient_noise(*window, SEED, origin=origin)
-    bits, bmin, bmax = oracle.encode_volume(f, RATE)
+    try:
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError
+        import synth.gpu as sg
+        sg.build()
+        f = sg.gradient_noise(*window, SEED, origin=origin).cpu().numpy()
+    except (ImportError, RuntimeError):
+        f = fields.gradient_noise(*window, SEED, origin=origin)
+    return oracle.encode_volume(f, RATE)
+
+
+def cpu_oracle_sample(window, origin, isos, volume=None):
+    import oracle
+    bits, bmin, bmax = volume if volume is not None else cpu_sample_volume(window, origin)
     tris, t = 0, 0.0
     for iso in isos:
         t0 = time.perf_counter()
@@ -227,15 +244,10 @@ def cpu_oracle_sample(window, origin, isos):
 
 
 def _oracle_slab(args):
-    """One z-slab of the sample window: samples [z0, z1] (the slabs share
-    their boundary plane, so each cell belongs to exactly one), encoded and
-    extracted by the oracle as it stands; returns (triangles, seconds)."""
-    window, origin, z0, z1, isos = args
+    """The oracle, as it stands, on one slab of block layers; returns
+    (triangles, seconds)."""
+    bits, bmin, bmax, dims, isos = args
     import oracle
-    from synth import fields
-    dims = (window[0], window[1], z1 - z0 + 1)
-    f = fields.gradient_noise(*dims, SEED, origin=(origin[0], origin[1], origin[2] + z0))
-    bits, bmin, bmax = oracle.encode_volume(f, RATE)
     tris, t = 0, 0.0
     for iso in isos:
         t0 = time.perf_counter()
@@ -244,21 +256,31 @@ def _oracle_slab(args):
     return tris, t
 
 
-def cpu_oracle_parallel(window, origin, isos):
-    """The same sample split into z-slabs of whole blocks, one process per
-    core (spawned: the parent holds a CUDA context), the oracle unchanged.
-    Returns (triangles, wall seconds of the extraction, processes).  Each
-    slab's last sample plane sits in a padded block of its own, so a few
-    boundary triangles can differ from the single-process run; the
-    throughput is what is measured."""
+def cpu_oracle_parallel(window, isos, volume):
+    """The same sample on all cores: the encoded window split into slabs of
+    whole block layers, one spawned process each (the parent holds a CUDA
+    context), the oracle unchanged.  A slab also gets the first sample plane
+    of the next slab's blocks, so its cells are exactly its own layers' and
+    the triangles add up to the single-process count.  Returns (triangles,
+    wall seconds of the extraction, processes)."""
     import concurrent.futures
     import multiprocessing as mp
-    cores = max(1, min(os.cpu_count() or 1, window[2] // 4))
-    per = -(-(window[2] // 4) // cores) * 4                 # whole blocks per slab
-    bounds = [(z, min(z + per, window[2] - 1)) for z in range(0, window[2] - 1, per)]
-    jobs = [(window, origin, z0, z1, isos) for z0, z1 in bounds]
+    import oracle
+    bits, bmin, bmax = volume
+    nbx, nby, nbz = oracle.block_dims(window)
+    layer = nbx * nby
+    cores = max(1, min(os.cpu_count() or 1, nbz))
+    per = -(-nbz // cores)
+    jobs = []
+    for bz0 in range(0, nbz, per):
+        bz1 = min(bz0 + per, nbz) - 1
+        last = min(bz1 + 1, nbz - 1)
+        zs = min(4 * (bz1 - bz0 + 1) + 1, window[2] - 4 * bz0)
+        rows = slice(bz0 * layer, (last + 1) * layer)
+        jobs.append((bits[rows], bmin[rows], bmax[rows], (window[0], window[1], zs), isos))
     with concurrent.futures.ProcessPoolExecutor(len(jobs), mp_context=mp.get_context("spawn")) as ex:
-        list(ex.map(_oracle_slab, [(window, origin, 0, 4, isos[:1])] * len(jobs)))   # start every worker first
+        warm = [(j[0][:layer], j[1][:layer], j[2][:layer], (window[0], window[1], 4), isos[:1]) for j in jobs]
+        list(ex.map(_oracle_slab, warm))                 # start every worker first
         t0 = time.perf_counter()
         out = list(ex.map(_oracle_slab, jobs))
         wall = time.perf_counter() - t0
@@ -746,17 +768,19 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     if not args.no_cpu_baseline and world == 1:
-        tris, dt = cpu_oracle_sample(CPU_WINDOW, CPU_ORIGIN, ISOS)
+        sample = cpu_sample_volume(CPU_WINDOW, CPU_ORIGIN)
+        tris, dt = cpu_oracle_sample(CPU_WINDOW, CPU_ORIGIN, ISOS, volume=sample)
         line["cpu_baseline"] = {
             "value": tris / dt, "unit": "triangles/s", "cores": 1, "kind": "oracle",
             "sample": f"{CPU_WINDOW[0]}x{CPU_WINDOW[1]}x{CPU_WINDOW[2]} window at {CPU_ORIGIN} of the same field, "
                       f"5 isovalues, {dt:.1f} s single-threaded (decode every block, range test, block MC)",
             "voxels_per_s": len(ISOS) * float(np.prod(CPU_WINDOW)) / dt}
-        ptris, pdt, procs = cpu_oracle_parallel(CPU_WINDOW, CPU_ORIGIN, ISOS)
+        ptris, pdt, procs = cpu_oracle_parallel(CPU_WINDOW, ISOS, sample)
         line["cpu_baseline"]["all_cores"] = {
             "value": ptris / pdt, "unit": "triangles/s", "cores": procs,
-            "sample": f"the same window in {procs} z-slabs of whole blocks, one spawned process each running the "
-                      f"oracle unchanged, {pdt:.1f} s wall",
+            "sample": f"the same encoded window in {procs} slabs of whole block layers, one spawned process each "
+                      f"running the oracle unchanged, {pdt:.1f} s wall, {ptris} triangles "
+                      f"({'equal to' if ptris == tris else 'differing from'} the single-process count)",
             "voxels_per_s": len(ISOS) * float(np.prod(CPU_WINDOW)) / pdt}
     print(json.dumps(line), flush=True)
 
