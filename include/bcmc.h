@@ -228,7 +228,9 @@ typedef struct iso_render_stats {
 } iso_render_stats;
 
 /* Rasterise num_triangles triangles (a soup: vertices 3t, 3t+1, 3t+2 when
- * d_indices is NULL; else d_indices[3t + j]) of vertex_format
+ * d_indices is NULL, which needs num_vertices >= 3 * num_triangles; else
+ * d_indices[3t + j], and a triangle with an index >= num_vertices is not
+ * drawn) of vertex_format
  * (ISO_VERTEX_FLOAT4 / ISO_VERTEX_PACKED) from a volume of nx*ny*nz
  * samples.  Rules, every float operation a single IEEE float32 operation:
  * r = 1/W, sx = (X r * 0.5 + 0.5) * width, sy likewise (y up, row 0 at the
@@ -247,9 +249,9 @@ typedef struct iso_render_stats {
  * NULL; when given, the call waits for the stream and fills it.
  * ISO_ERR_INVALID_ARG for a bad format, size, light (zero or not finite) or
  * a NaN in the matrix; ISO_ERR_OOM if the working list cannot be made. */
-int iso_render(const void *d_vertices, int vertex_format, const uint32_t *d_indices, uint64_t num_triangles,
-               uint32_t nx, uint32_t ny, uint32_t nz, const iso_camera *camera, uint64_t *d_fragments,
-               uint32_t *d_rgba, iso_render_stats *stats, void *stream);
+int iso_render(const void *d_vertices, int vertex_format, const uint32_t *d_indices, uint64_t num_vertices,
+               uint64_t num_triangles, uint32_t nx, uint32_t ny, uint32_t nz, const iso_camera *camera,
+               uint64_t *d_fragments, uint32_t *d_rgba, iso_render_stats *stats, void *stream);
 
 /* ---- implicit isosurface ray casting (Section 4.6.2, future work) ----
  * The blocks serve as a macrocell grid for space skipping and the surface

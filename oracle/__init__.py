@@ -71,7 +71,7 @@ def lib():
         L.orc_mc_blocks.argtypes = [P, i32, i32, i32, ctypes.c_float, P, P, i64,
                                     P, P, P, P, P, P, P, P, i64]
         L.orc_mc_blocks.restype = i64
-        L.orc_raster.argtypes = [P, i32, P, i64, i32, i32, i32, P, i32, i32, P]
+        L.orc_raster.argtypes = [P, i32, P, i64, i64, i32, i32, i32, P, i32, i32, P]
         L.orc_shade.argtypes = [P, i32, P, i32, i32, i32, P, i32, i32, P, P]
         L.orc_raycast.argtypes = [P, i32, i32, i32, ctypes.c_float, P, P, P, P, P, i32, i32, P, P]
         _lib = L
@@ -306,13 +306,14 @@ def raster(vertices, indices, num_triangles, dims, view_proj, width, height):
     uint64 (height, width), (depth bits << 32) | triangle, all ones where
     nothing is drawn.  `vertices` float32 (V, 4) block-local + block id bits
     or uint32 (V, 2) compact; `indices` None for a soup (vertex 3t + j) or
-    uint32 (T, 3); view_proj row-major 4x4 float32."""
+    uint32 (T, 3) (a triangle with an index past the vertices is not
+    drawn); view_proj row-major 4x4 float32."""
     v, fmt = _vertex_buffer(vertices)
     idx = None if indices is None else np.ascontiguousarray(indices, np.uint32)
     m = np.ascontiguousarray(view_proj, np.float32).reshape(16)
     out = np.zeros((height, width), np.uint64)
     nx, ny, nz = dims
-    lib().orc_raster(_p(v), fmt, _p(idx), int(num_triangles), nx, ny, nz, _p(m), width, height, _p(out))
+    lib().orc_raster(_p(v), fmt, _p(idx), len(v), int(num_triangles), nx, ny, nz, _p(m), width, height, _p(out))
     return out
 
 

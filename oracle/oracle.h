@@ -62,8 +62,8 @@ int64_t orc_mc_blocks(const float *field, int nx, int ny, int nz, float iso,
                       uint64_t *edge_ids, double *local_pos, uint32_t *tri_block, int64_t cap);
 
 /* ---- rendering (raster.c) ---- */
-void orc_raster(const void *verts, int format, const uint32_t *idx, int64_t num_tri, int nx, int ny, int nz,
-                const float m[16], int width, int height, uint64_t *frag);
+void orc_raster(const void *verts, int format, const uint32_t *idx, int64_t num_vtx, int64_t num_tri, int nx,
+                int ny, int nz, const float m[16], int width, int height, uint64_t *frag);
 void orc_shade(const void *verts, int format, const uint32_t *idx, int nx, int ny, int nz, const float light[3],
                int width, int height, const uint64_t *frag, uint32_t *rgba);
 

@@ -34,6 +34,8 @@
  *   depth            d = ((e0 d0 + e1 d1) + e2 d2) / A, + 0 (no negative
  *                    zero); fragments with d outside [0, 1] are dropped
  *   visibility       per pixel the smallest (depth bits << 32 | triangle)
+ *   indexed input    a triangle with an index past the vertex count is not
+ *                    drawn
  *   shading          n = (p1 - p0) x (p2 - p0) in world space;
  *                    intensity = 0.2 + 0.8 |n . L| / |n| (0.2 when |n| = 0,
  *                    L normalised), rgb = floor(intensity * base * 255 + 0.5)
@@ -103,8 +105,8 @@ static int64_t vertex_index(const uint32_t *idx, int64_t t, int j)
     return idx ? (int64_t)idx[3 * t + j] : 3 * t + j;
 }
 
-void orc_raster(const void *verts, int format, const uint32_t *idx, int64_t num_tri, int nx, int ny, int nz,
-                const float m[16], int width, int height, uint64_t *frag)
+void orc_raster(const void *verts, int format, const uint32_t *idx, int64_t num_vtx, int64_t num_tri, int nx,
+                int ny, int nz, const float m[16], int width, int height, uint64_t *frag)
 {
     (void)nz;
     for (int64_t i = 0; i < (int64_t)width * height; i++) frag[i] = ~0ull;
@@ -112,6 +114,8 @@ void orc_raster(const void *verts, int format, const uint32_t *idx, int64_t num_
         pt2 s[3];
         float d[3];
         int behind = 0;
+        if (idx && (idx[3 * t] >= num_vtx || idx[3 * t + 1] >= num_vtx || idx[3 * t + 2] >= num_vtx))
+            continue;                            /* an index past the vertex buffer: not drawn */
         for (int j = 0; j < 3; j++) {
             float p[3];
             world(verts, format, vertex_index(idx, t, j), nx, ny, p);

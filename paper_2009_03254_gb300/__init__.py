@@ -119,7 +119,7 @@ def lib():
             "iso_extract_packed_into": (i32, [P, ctypes.c_float, P, u64, ctypes.POINTER(_Stats)]),
             "iso_extract_all_blocks_into": (i32, [P, ctypes.c_float, P, u64, ctypes.POINTER(_Stats)]),
             "iso_extract_indexed_into": (i32, [P, ctypes.c_float, i32, P, u64, P, u64, ctypes.POINTER(_Stats)]),
-            "iso_render": (i32, [P, i32, P, u64, u32, u32, u32, ctypes.POINTER(_Camera), P, P,
+            "iso_render": (i32, [P, i32, P, u64, u64, u32, u32, u32, ctypes.POINTER(_Camera), P, P,
                                  ctypes.POINTER(_RenderStats), P]),
             "iso_raycast": (i32, [P, ctypes.c_float, ctypes.POINTER(_Pinhole), P, P, ctypes.POINTER(_CastStats)]),
             "iso_decode_volume": (i32, [P, u32, u32, u32, u32, P, P]),
@@ -635,8 +635,9 @@ def render(vertices, num_triangles, dims, view_proj, light, width, height, indic
     cam.width, cam.height = int(width), int(height)
     st = _RenderStats()
     nx, ny, nz = dims
-    rc = lib().iso_render(_ptr(vertices), fmt, _ptr(indices) if indices is not None else None, int(num_triangles),
-                          nx, ny, nz, ctypes.byref(cam), _ptr(fragments), _ptr(rgba) if rgba is not False else None,
+    nv = vertices.numel() // (4 if fmt == ISO_VERTEX_FLOAT4 else 2)
+    rc = lib().iso_render(_ptr(vertices), fmt, _ptr(indices) if indices is not None else None, nv,
+                          int(num_triangles), nx, ny, nz, ctypes.byref(cam), _ptr(fragments), _ptr(rgba) if rgba is not False else None,
                           ctypes.byref(st) if stats else None,
                           stream if stream is not None else _current_stream())
     _check(rc, "iso_render")

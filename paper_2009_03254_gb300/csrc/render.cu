@@ -44,6 +44,7 @@ constexpr float kCodeScale = 0.0039100684f;          // 4 / 1023 rounded to floa
 struct RasterArgs {
     const void *verts;
     const uint32_t *idx;          // null: soup (vertex 3t + j)
+    unsigned long long num_vtx;   // vertices in the buffer (indexed: a triangle reaching past them is not drawn)
     unsigned long long num_tri;
     unsigned long long *frag;
     uint32_t *big;                // triangles left for the warp kernel
@@ -135,6 +136,11 @@ __device__ __forceinline__ bool top_left(P2 a, P2 b) {
 
 // projection, orientation and pixel range of triangle t; false: not drawn
 __device__ bool setup(const RasterArgs &a, unsigned long long t, Tri &r) {
+    if (a.idx) {                                       // indices past the vertex buffer: not drawn
+#pragma unroll
+        for (int j = 0; j < 3; j++)
+            if (a.idx[3 * t + j] >= a.num_vtx) return false;
+    }
     bool behind = false;
     P2 s[3];
 #pragma unroll
@@ -307,14 +313,16 @@ int grid_for(unsigned long long work, int device) {
 }  // namespace bcmc
 
 extern "C" int iso_render(const void *d_vertices, int vertex_format, const uint32_t *d_indices,
-                          uint64_t num_triangles, uint32_t nx, uint32_t ny, uint32_t nz, const iso_camera *camera,
-                          uint64_t *d_fragments, uint32_t *d_rgba, iso_render_stats *stats, void *stream) {
+                          uint64_t num_vertices, uint64_t num_triangles, uint32_t nx, uint32_t ny, uint32_t nz,
+                          const iso_camera *camera, uint64_t *d_fragments, uint32_t *d_rgba,
+                          iso_render_stats *stats, void *stream) {
     using namespace bcmc;
     using namespace bcmc_host;
     if (!camera || !d_fragments || camera->width == 0 || camera->height == 0 || camera->width > 32768 ||
         camera->height > 32768 || nx == 0 || ny == 0 || nz == 0 ||
         (vertex_format != ISO_VERTEX_FLOAT4 && vertex_format != ISO_VERTEX_PACKED) ||
-        (num_triangles && !d_vertices) || num_triangles > 0xFFFFFFFFull)
+        (num_triangles && !d_vertices) || num_triangles > 0xFFFFFFFFull ||
+        (!d_indices && num_vertices < 3 * num_triangles))      // a soup needs its 3T vertices
         return ISO_ERR_INVALID_ARG;
     const float *L = camera->light;
     const double l2 = (double)L[0] * L[0] + (double)L[1] * L[1] + (double)L[2] * L[2];
@@ -329,6 +337,7 @@ extern "C" int iso_render(const void *d_vertices, int vertex_format, const uint3
     RasterArgs a{};
     a.verts = d_vertices;
     a.idx = d_indices;
+    a.num_vtx = num_vertices;
     a.num_tri = num_triangles;
     a.frag = reinterpret_cast<unsigned long long *>(d_fragments);
     a.format = vertex_format == ISO_VERTEX_PACKED ? 1u : 0u;

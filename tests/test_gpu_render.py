@@ -145,6 +145,18 @@ def test_hand_meshes_and_ties():
     assert st["big"] == 2 and np.all((f & np.uint64(0xFFFFFFFF)) == 0)
 
 
+def test_index_past_the_vertices_is_not_drawn(surface):
+    s = surface
+    idx = s["idx"].copy()
+    rng = np.random.default_rng(6)
+    bad = rng.choice(len(idx), 50, replace=False)
+    idx[bad, rng.integers(0, 3, 50)] = len(s["iv"]) + rng.integers(0, 1 << 30, 50).astype(np.uint32)
+    m = CAMERAS["far"](s["dims"])
+    f, st = check(s["iv"], idx, s["T"], s["dims"], m, (0.3, -0.5, 0.8), 160, 96)
+    assert st["drawn"] <= s["T"] - 50
+    assert not np.isin((f[f != NONE] & np.uint64(0xFFFFFFFF)).astype(np.int64), bad).any()
+
+
 def test_empty_and_invalid():
     p = pkg()
     t = torch()
@@ -153,7 +165,8 @@ def test_empty_and_invalid():
     v = t.zeros((3, 4), dtype=t.float32, device="cuda")
     frag, rgba, st = p.render(v, 0, dims, m, (0, 0, 1), 16, 8, stats=True)
     assert (frag == -1).all() and (rgba == 0).all() and st == {"drawn": 0, "big": 0}
-    for kw in (dict(light=(0, 0, 0)), dict(width=0), dict(view_proj=np.full(16, np.nan, np.float32))):
+    for kw in (dict(light=(0, 0, 0)), dict(width=0), dict(view_proj=np.full(16, np.nan, np.float32)),
+               dict(num_triangles=2)):                  # a soup of 2 triangles needs 6 vertices
         args = dict(vertices=v, num_triangles=1, dims=dims, view_proj=m, light=(0, 0, 1), width=16, height=8)
         args.update(kw)
         with pytest.raises(p.IsoError) as e:

@@ -169,3 +169,14 @@ def test_shading_by_hand():
     assert np.all(lit[f != NONE] == full) and np.all(back[f != NONE] == full)   # two-sided
     assert np.all(side[f != NONE] == dim)
     assert np.all(lit[f == NONE] == 0)
+
+
+def test_index_past_the_vertices_is_not_drawn():
+    v = float4_vertices([(0, 0, 1), (8, 0, 1), (0, 8, 1)])
+    good = np.array([[0, 1, 2]], np.uint32)
+    bad = np.array([[0, 1, 3], [0, 1, 2]], np.uint32)        # the first reaches past the 3 vertices
+    a = oracle.raster(v, good, 1, DIMS, cameras.orthographic(8, 8), 8, 8)
+    b = oracle.raster(v, bad, 2, DIMS, cameras.orthographic(8, 8), 8, 8)
+    assert (a != NONE).sum() == 28
+    assert np.array_equal(b & np.uint64(0xFFFFFFFF00000000), a & np.uint64(0xFFFFFFFF00000000))
+    assert np.all((b[b != NONE] & np.uint64(0xFFFFFFFF)) == 1)   # only triangle 1 is drawn
