@@ -500,8 +500,10 @@ typedef struct iso_server iso_server;
 
 typedef struct iso_server_options {
     uint32_t max_batch;            /* requests per tick, 1..8; 0 = 4 */
-    uint32_t reserved;
-    uint64_t vertex_budget_bytes;  /* limit on held mesh bytes (48 per triangle); 0 = none */
+    uint32_t vertex_format;        /* ISO_VERTEX_FLOAT4 (0, 48 bytes a triangle) or ISO_VERTEX_PACKED
+                                      (24 bytes a triangle: the meshes' d_vertices then hold the compact
+                                      uint32 pairs of iso_extract_packed_into) */
+    uint64_t vertex_budget_bytes;  /* limit on held mesh bytes (48 or 24 per triangle); 0 = none */
     void *stream;                  /* cudaStream_t of the server's device work; NULL = default */
 } iso_server_options;
 

@@ -71,7 +71,7 @@ class _Shape(ctypes.Structure):
 
 
 class _ServerOptions(ctypes.Structure):
-    _fields_ = [("max_batch", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+    _fields_ = [("max_batch", ctypes.c_uint32), ("vertex_format", ctypes.c_uint32),
                 ("vertex_budget_bytes", ctypes.c_uint64), ("stream", ctypes.c_void_p)]
 
 
@@ -204,21 +204,24 @@ class _DeviceArray:
 
 
 class Mesh:
-    """A surface computed by Volume.extract.  `vertices` is a (3T, 4) float32
-    CUDA tensor viewing library-owned memory: valid until release()."""
+    """A surface computed by Volume.extract (or served).  `vertices` is a
+    (3T, 4) float32 CUDA tensor, or for compact meshes a (3T, 2) int32 one,
+    viewing library-owned memory: valid until release()."""
 
-    def __init__(self, volume, m):
+    def __init__(self, volume, m, packed=False):
         self._volume = volume
         self._m = m
+        self.packed = bool(packed)
         self.num_triangles = int(m.num_triangles)
         self.stats = m.stats.as_dict()
 
     @property
     def vertices(self):
         import torch
+        width, typestr, dt = (2, "<i4", torch.int32) if self.packed else (4, "<f4", torch.float32)
         if not self._m.d_vertices:
-            return torch.zeros((0, 4), dtype=torch.float32, device="cuda")
-        arr = _DeviceArray(int(self._m.d_vertices), (3 * self.num_triangles, 4), "<f4")
+            return torch.zeros((0, width), dtype=dt, device="cuda")
+        arr = _DeviceArray(int(self._m.d_vertices), (3 * self.num_triangles, width), typestr)
         return torch.as_tensor(arr, device="cuda")
 
     def release(self):
@@ -518,11 +521,13 @@ class Server:
     all, one cache update for their union, one launch per triangle stage).
     See iso_server_* in include/bcmc.h.  The volume must outlive the server."""
 
-    def __init__(self, volume, *, max_batch=4, vertex_budget_bytes=0, stream=None):
+    def __init__(self, volume, *, max_batch=4, vertex_budget_bytes=0, stream=None, packed=False):
         self._h = None
         self.volume = volume
+        self.packed = bool(packed)
         opt = _ServerOptions()
         opt.max_batch = int(max_batch)
+        opt.vertex_format = ISO_VERTEX_PACKED if packed else ISO_VERTEX_FLOAT4
         opt.vertex_budget_bytes = int(vertex_budget_bytes)
         opt.stream = stream if stream is not None else _current_stream()
         h = ctypes.c_void_p()
@@ -554,7 +559,7 @@ class Server:
             raise IsoError(rc, "iso_server_take")
         if rc != ISO_OK:
             return rc, None
-        return rc, Mesh(self.volume, m)
+        return rc, Mesh(self.volume, m, self.packed)
 
     def wait(self, ticket, timeout_ms=1000):
         """Step until the ticket is done or the timeout passes: (status, Mesh
@@ -565,7 +570,7 @@ class Server:
             raise IsoError(rc, "iso_server_wait")
         if rc != ISO_OK:
             return rc, None
-        return rc, Mesh(self.volume, m)
+        return rc, Mesh(self.volume, m, self.packed)
 
     def release(self):
         if self._h:

@@ -248,6 +248,8 @@ struct iso_server {
     cudaStream_t stream = nullptr;
     uint32_t max_batch = 4, limit = 4;  // requests per tick; current limit after budget failures
     uint64_t vertex_budget = 0;         // 0 = none
+    uint32_t format = kVertexFloat4;    // vertex format of the meshes
+    uint64_t tri_bytes = 48;            // their bytes per triangle
     uint32_t cand_cap = 0;              // room of each request's candidate list
     uint64_t held_bytes = 0;            // finished meshes not yet taken
     Slot slots[kMaxServe];
@@ -311,7 +313,7 @@ void finish(iso_server *sv, const Request &r, int status, const Ctl *c, float *b
         s.n_cand = c->n_cand;
         fill_stats(s, &d.mesh.stats, 0);
     }
-    if (buf) sv->held_bytes += 48ull * c->n_tri;
+    if (buf) sv->held_bytes += sv->tri_bytes * c->n_tri;
     sv->done[r.ticket] = d;
 }
 
@@ -393,14 +395,14 @@ int emit_next(iso_server *sv, uint32_t *completed) {
         *completed += 1;
         return ISO_OK;
     }
-    const uint64_t bytes = 48ull * c.n_tri;
+    const uint64_t bytes = sv->tri_bytes * c.n_tri;
     if (sv->vertex_budget && sv->held_bytes > 0 && sv->held_bytes + bytes > sv->vertex_budget) {
         requeue_rest(sv);                 // wait until the held meshes are taken
         return ISO_OK;
     }
     float *buf = nullptr;
     if (c.n_tri) {
-        const int rc = dalloc_on(&buf, (size_t)c.n_tri * 12, sv->device, st);
+        const int rc = dalloc_on(&buf, (size_t)c.n_tri * (sv->tri_bytes / 4), sv->device, st);
         if (rc) {
             finish(sv, r, rc, &c, nullptr);
             sv->tick_next++;
@@ -408,7 +410,7 @@ int emit_next(iso_server *sv, uint32_t *completed) {
             return ISO_OK;
         }
     }
-    *sv->h_params = Params{r.iso, kVertexFloat4, 0u, 0u, 0u, 0u, c.n_tri, (unsigned long long)(uintptr_t)buf};
+    *sv->h_params = Params{r.iso, sv->format, 0u, 0u, 0u, 0u, c.n_tri, (unsigned long long)(uintptr_t)buf};
     ISO_CK(cudaMemcpyAsync(&dctl->params, sv->h_params, sizeof(Params), cudaMemcpyHostToDevice, st));
     launch_mc_emit(L, false, sv->view_plan, st);
     ISO_CK(cudaGetLastError());
@@ -429,6 +431,7 @@ int iso_server_create(iso_server **out, iso_volume *v, const iso_server_options 
     iso_server_options o{};
     if (opt) o = *opt;
     if (o.max_batch > (uint32_t)kMaxServe) return ISO_ERR_INVALID_ARG;
+    if (o.vertex_format != ISO_VERTEX_FLOAT4 && o.vertex_format != ISO_VERTEX_PACKED) return ISO_ERR_INVALID_ARG;
     DeviceGuard dg(v->device);
     iso_server *sv = new (std::nothrow) iso_server();
     if (!sv) return ISO_ERR_OOM;
@@ -438,6 +441,8 @@ int iso_server_create(iso_server **out, iso_volume *v, const iso_server_options 
     sv->max_batch = o.max_batch ? o.max_batch : 4;
     sv->limit = sv->max_batch;
     sv->vertex_budget = o.vertex_budget_bytes;
+    sv->format = o.vertex_format == ISO_VERTEX_PACKED ? kVertexPacked : kVertexFloat4;
+    sv->tri_bytes = o.vertex_format == ISO_VERTEX_PACKED ? 24 : 48;
     const size_t cand = std::min<size_t>(v->cap, v->g.nb);       // candidates of an admitted tick <= cap
     sv->cand_cap = (uint32_t)cand;
     const size_t n_mc_desc = (cand + kMinMcScanTile - 1) / kMinMcScanTile;
@@ -537,7 +542,7 @@ int iso_server_take(iso_server *sv, uint64_t ticket, iso_mesh *out) {
     }
     *out = it->second.mesh;
     const int status = it->second.status;
-    if (out->d_vertices) sv->held_bytes -= 48ull * out->num_triangles;
+    if (out->d_vertices) sv->held_bytes -= sv->tri_bytes * out->num_triangles;
     sv->done.erase(it);
     return status;
 }

@@ -200,3 +200,42 @@ def test_request_loop_against_plain_path():
         srv.release()
         vol.release()
         alone.release()
+
+
+def test_compact_vertices_served():
+    # the compact 8-byte format: the same codes as extracting it alone, half
+    # the bytes against the vertex budget
+    import torch
+    p = pkg()
+    data, vol, alone = volume_pair(seed=11)
+    d = data[5]
+    isos = [float(x) for x in np.quantile(d, [0.3, 0.5, 0.7])]
+    srv = p.Server(vol, max_batch=4, packed=True)
+    try:
+        tickets = [srv.submit(x) for x in isos]
+        while srv.queued():
+            srv.step()
+        for t, x in zip(tickets, isos):
+            status, m = srv.take(t)
+            assert status == p.ISO_OK and m.packed
+            T = m.num_triangles
+            want = torch.zeros((max(T, 1), 3, 2), dtype=torch.int32, device="cuda")
+            st = alone.extract_packed_into(x, want)
+            assert st["num_triangles"] == T
+            assert np.array_equal(m.vertices.cpu().numpy().reshape(-1, 3, 2), want.cpu().numpy()[:T])
+            m.release()
+    finally:
+        srv.release()
+        vol.release()
+        alone.release()
+    # a vertex format that is neither is refused
+    import ctypes
+    data2, v2, a2 = volume_pair(dims=(20, 20, 20))
+    try:
+        bad = p._ServerOptions()
+        bad.vertex_format = 7
+        h = ctypes.c_void_p()
+        assert p.lib().iso_server_create(ctypes.byref(h), v2._h, ctypes.byref(bad)) == p.ISO_ERR_INVALID_ARG
+    finally:
+        v2.release()
+        a2.release()
