@@ -434,6 +434,15 @@ typedef struct iso_launch_shape {
     uint32_t emit_tile;          /* candidate blocks per emit CTA: 16, 32 (default) or 64 */
 } iso_launch_shape;
 
+/* The launch shape of a single volume's extractions (same fields and
+ * rules as a batch's; every shape computes the same results).  Takes
+ * effect from the next call; the volume's captured graphs are rebuilt.  A
+ * volume starts with 4096-count scan tiles at one CTA per SM and 256-block
+ * decode CTAs, the rest at the defaults (zeros in a shape passed here mean
+ * the general defaults). */
+int iso_set_shape(iso_volume *v, const iso_launch_shape *shape);
+int iso_get_shape(const iso_volume *v, iso_launch_shape *shape);
+
 /* volumes[0..n), 1 <= n <= 1024; stream: cudaStream_t (NULL = default). */
 int iso_batch_create(iso_batch **out, iso_volume *const *volumes, uint32_t n, void *stream);
 

@@ -139,6 +139,8 @@ def lib():
             "iso_batch_create": (i32, [ctypes.POINTER(P), P, u32, P]),
             "iso_batch_extract": (i32, [P, P, P, u64, P, P, P]),
             "iso_batch_set_shape": (i32, [P, ctypes.POINTER(_Shape)]),
+            "iso_set_shape": (i32, [P, ctypes.POINTER(_Shape)]),
+            "iso_get_shape": (i32, [P, ctypes.POINTER(_Shape)]),
             "iso_batch_get_shape": (i32, [P, ctypes.POINTER(_Shape)]),
             "iso_batch_tune": (i32, [P, P, P, u64, i32, ctypes.POINTER(_Shape), P]),
             "iso_batch_release": (None, [P]),
@@ -378,6 +380,19 @@ class Volume:
                                  _ptr(rgba) if rgba is not False else None, ctypes.byref(st)), "iso_raycast")
         return hits, (rgba if rgba is not False else None), {
             "hits": int(st.hits), "n_active": int(st.n_active), "n_new": int(st.n_new), "n_slots": int(st.n_slots)}
+
+    def set_shape(self, **shape):
+        """The launch shape of this volume's extractions (iso_set_shape):
+        keyword fields of iso_launch_shape, the rest 0 (defaults)."""
+        sh = _Shape()
+        for k, val in shape.items():
+            setattr(sh, k, int(val))
+        _check(lib().iso_set_shape(self._h, ctypes.byref(sh)), "iso_set_shape")
+
+    def get_shape(self):
+        sh = _Shape()
+        _check(lib().iso_get_shape(self._h, ctypes.byref(sh)), "iso_get_shape")
+        return sh.as_dict()
 
     STAGES = ("prep", "cull", "cache_update", "decode", "count", "scan", "emit")
 

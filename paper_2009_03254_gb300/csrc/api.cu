@@ -112,6 +112,40 @@ void dfree_on(void *p, cudaStream_t st) {
     else cudaFreeAsync(p, st);
 }
 
+int shape_to_want(const iso_launch_shape *shape, Plan *out) {
+    Plan w{};
+    // CTAs per SM beyond any occupancy limit mean "the limit"; tile sizes
+    // are checked exactly (values that do not fit an int are invalid)
+    auto c = [](uint32_t x) { return (int)std::min<uint32_t>(x, 1024u); };
+    auto t = [](uint32_t x) { return x > 65536u ? -1 : (int)x; };
+    w.cull = c(shape->cull_ctas);
+    w.cull_tile = t(shape->cull_tile);
+    w.lru_a = w.lru_b = c(shape->cache_update_ctas);
+    w.decode = c(shape->decode_ctas);
+    w.decode_tile = t(shape->decode_tile);
+    w.mc_count = c(shape->count_ctas);
+    w.count_tile = t(shape->count_tile);
+    w.mc_scan = c(shape->scan_ctas);
+    w.scan_tile = t(shape->scan_tile);
+    w.mc_emit = c(shape->emit_ctas);
+    w.emit_tile = t(shape->emit_tile);
+    if (!valid_tiles(default_tiles(&w))) return ISO_ERR_INVALID_ARG;
+    *out = w;
+    return ISO_OK;
+}
+
+iso_launch_shape shape_of(const Plan &want, int device, bool single) {
+    // CTAs per SM that run: the requested number clamped to the occupancy limit
+    const Plan tiles = default_tiles(&want);
+    const Plan lim = occupancy_limits_of(device, tiles, single);
+    auto run = [](int w, int mx) { return (uint32_t)(w > 0 ? std::min(w, mx) : mx); };
+    return iso_launch_shape{run(want.cull, lim.cull), (uint32_t)tiles.cull_tile, run(want.lru_a, lim.lru_a),
+                            run(want.decode, lim.decode), (uint32_t)tiles.decode_tile,
+                            run(want.mc_count, lim.mc_count), (uint32_t)tiles.count_tile,
+                            run(want.mc_scan, lim.mc_scan), (uint32_t)tiles.scan_tile,
+                            run(want.mc_emit, lim.mc_emit), (uint32_t)tiles.emit_tile};
+}
+
 Plan default_tiles(const Plan *want) {
     Plan t{};
     t.cull_tile = want && want->cull_tile ? want->cull_tile : kDefaultCullTile;
@@ -507,6 +541,32 @@ bool build_tables_once(McTables *t) {
 
 extern "C" {
 
+int iso_set_shape(iso_volume *v, const iso_launch_shape *shape) {
+    if (!v || !shape) return ISO_ERR_INVALID_ARG;
+    Plan w{};
+    const int rc = shape_to_want(shape, &w);
+    if (rc) return rc;
+    DeviceGuard dg(v->device);
+    CK(cudaStreamSynchronize(v->stream));
+    v->want = w;
+    v->plan = launch_plan(&v->want, v->device, v->g.nb, v->cap, 1, true);
+    for (int k = 0; k < 4; k++) {            // the captured passes hold the old launch shape
+        if (v->gexec[k]) cudaGraphExecDestroy(v->gexec[k]);
+        if (v->graph[k]) cudaGraphDestroy(v->graph[k]);
+        v->gexec[k] = nullptr;
+        v->graph[k] = nullptr;
+    }
+    CK(cudaGetLastError());
+    return ISO_OK;
+}
+
+int iso_get_shape(const iso_volume *v, iso_launch_shape *shape) {
+    if (!v || !shape) return ISO_ERR_INVALID_ARG;
+    DeviceGuard dg(v->device);
+    *shape = shape_of(v->want, v->device, true);
+    return ISO_OK;
+}
+
 int iso_set_allocator(iso_alloc_fn alloc, iso_free_fn free_fn, void *ctx) {
     if ((alloc == nullptr) != (free_fn == nullptr)) return ISO_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lock(g_alloc_mutex);
@@ -679,7 +739,14 @@ int iso_load_volume(iso_volume **out, const void *compressed, size_t compressed_
         free_volume(v);
         return ISO_ERR_CORRUPT;
     }
-    v->plan = launch_plan(nullptr, v->device, g.nb, v->cap, 1, true);
+    // single-volume defaults from a sweep of every tile variant and CTA count
+    // on the 512^3 benchmark: 4096-count scan tiles at one CTA per SM and
+    // 256-block decode CTAs (the other kernels' defaults were already best)
+    v->want = Plan{};
+    v->want.scan_tile = 4096;
+    v->want.mc_scan = 1;
+    v->want.decode_tile = 256;
+    v->plan = launch_plan(&v->want, v->device, g.nb, v->cap, 1, true);
     TRYC(cudaGetLastError());
     *out = v;
     return ISO_OK;

@@ -296,40 +296,15 @@ int iso_batch_set_shape(iso_batch *b, const iso_launch_shape *shape) {
     if (!b || !shape) return ISO_ERR_INVALID_ARG;
     DeviceGuard dg(b->device);
     Plan w{};
-    // CTAs per SM beyond any occupancy limit mean "the limit"; tile sizes
-    // are checked exactly (values that do not fit an int are invalid)
-    auto c = [](uint32_t x) { return (int)std::min<uint32_t>(x, 1024u); };
-    auto t = [](uint32_t x) { return x > 65536u ? -1 : (int)x; };
-    w.cull = c(shape->cull_ctas);
-    w.cull_tile = t(shape->cull_tile);
-    set_ctas(w, 1, c(shape->cache_update_ctas));
-    w.decode = c(shape->decode_ctas);
-    w.decode_tile = t(shape->decode_tile);
-    w.mc_count = c(shape->count_ctas);
-    w.count_tile = t(shape->count_tile);
-    w.mc_scan = c(shape->scan_ctas);
-    w.scan_tile = t(shape->scan_tile);
-    w.mc_emit = c(shape->emit_ctas);
-    w.emit_tile = t(shape->emit_tile);
-    if (!valid_tiles(default_tiles(&w))) return ISO_ERR_INVALID_ARG;
+    const int rc = shape_to_want(shape, &w);
+    if (rc) return rc;
     apply_shape(b, w);
     return ISO_OK;
 }
 
 int iso_batch_get_shape(const iso_batch *b, iso_launch_shape *shape) {
     if (!b || !shape) return ISO_ERR_INVALID_ARG;
-    // CTAs per SM that run: the requested number clamped to the occupancy limit
-    const Plan tiles = default_tiles(&b->want);
-    Plan lim = occupancy_limits_of(b->device, tiles, false);
-    Plan want = b->want;
-    uint32_t ctas[kKernels];
-    for (int k = 0; k < kKernels; k++) {
-        const int w = *ctas_field(want, k), mx = *ctas_field(lim, k);
-        ctas[k] = (uint32_t)(w > 0 ? std::min(w, mx) : mx);
-    }
-    *shape = iso_launch_shape{ctas[0], (uint32_t)tiles.cull_tile, ctas[1], ctas[2], (uint32_t)tiles.decode_tile,
-                              ctas[3], (uint32_t)tiles.count_tile, ctas[4], (uint32_t)tiles.scan_tile,
-                              ctas[5], (uint32_t)tiles.emit_tile};
+    *shape = shape_of(b->want, b->device, false);
     return ISO_OK;
 }
 

@@ -17,6 +17,7 @@ struct iso_volume {
     uint32_t flags = 0;
     bcmc::DevState s{};
     bcmc::Plan plan{};                // CTAs and tile sizes of the launches
+    bcmc::Plan want{};                // the launch shape asked for (iso_set_shape; zeros: defaults)
     uint32_t cap = 0;                 // physical slots
     uint32_t n_cull_desc = 0, n_lru_desc = 0;
     bcmc::Ctl *host_ctl = nullptr;    // pinned mirror for the one readback
@@ -94,6 +95,12 @@ bcmc::Plan launch_plan(const bcmc::Plan *want, int device, uint64_t total_blocks
 
 // the tile fields of `want`, defaults where 0
 bcmc::Plan default_tiles(const bcmc::Plan *want);
+
+// a launch shape as a requested plan (ISO_ERR_INVALID_ARG for tiles no kernel has)
+int shape_to_want(const iso_launch_shape *shape, bcmc::Plan *out);
+
+// the launch shape that runs for a requested plan (CTAs clamped to the occupancy limits)
+iso_launch_shape shape_of(const bcmc::Plan &want, int device, bool single);
 
 // largest CTAs per SM of each kernel for these tile sizes, in single-volume
 // or batch launches (cached per device)

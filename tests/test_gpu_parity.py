@@ -502,3 +502,30 @@ def test_over_budget_extraction_in_waves():
     finally:
         small.release()
         full.release()
+
+
+def test_launch_shapes_agree():
+    # every launch shape of a single volume computes the same bytes
+    p = pkg()
+    dims, rate = (37, 33, 29), 8
+    f = make_field("noise", dims, 12)
+    bits, bmin, bmax = oracle.encode_volume(f, rate)
+    vol = p.Volume(bits, dims, rate, bmin, bmax)
+    try:
+        start = vol.get_shape()
+        assert start["scan_tile"] == 4096 and start["decode_tile"] == 256
+        ref = vol.extract(0.1)
+        want = ref.vertices.cpu().numpy().view(np.uint32)
+        ref.release()
+        for shape in (dict(), dict(cull_tile=2048, decode_tile=64, count_tile=16, scan_tile=1024, emit_tile=16),
+                      dict(count_tile=64, emit_tile=64, scan_ctas=1, emit_ctas=1, decode_ctas=2)):
+            vol.set_shape(**shape)
+            for _ in range(2):                      # plain launches, then the captured graph
+                vol.cache_reset()
+                m = vol.extract(0.1)
+                assert np.array_equal(m.vertices.cpu().numpy().view(np.uint32), want)
+                m.release()
+        with pytest.raises(p.IsoError):
+            vol.set_shape(count_tile=48)
+    finally:
+        vol.release()
