@@ -216,3 +216,21 @@ def test_indexed_debug_volume_edge_ids():
                                                         minlength=len(cnt)))
     finally:
         vol.release()
+
+
+@pytest.mark.parametrize("dims", [(1, 1, 1), (2, 2, 2), (5, 2, 3), (4, 4, 4), (9, 1, 9), (3, 3, 17)])
+def test_indexed_degenerate_volumes(dims):
+    # single samples, single cells, flat volumes (a dimension of 1: no cells)
+    # and exact multiples of 4: same mesh as the oracle, empty where it is
+    f = make_field("random", dims, 21)
+    bits, bmin, bmax = oracle.encode_volume(f, 12)
+    d = oracle.decode_volume(bits, dims, 12)
+    vol = pkg().Volume(bits, dims, 12, bmin, bmax)
+    try:
+        iso = float(np.median(d))
+        ref, ix = oracle_indexed(bits, dims, 12, bmin, bmax, iso)
+        check_float(vol, ref, ix, iso)
+        if 1 in dims:
+            assert ref["num_triangles"] == 0 and len(ix["vertex_edge"]) == 0
+    finally:
+        vol.release()

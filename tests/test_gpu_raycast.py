@@ -108,3 +108,22 @@ def test_over_budget_and_invalid():
             assert e.value.code == p.ISO_ERR_INVALID_ARG
     finally:
         small.release()
+
+
+@pytest.mark.parametrize("dims", [(2, 2, 2), (5, 2, 3), (1, 6, 6), (4, 4, 4), (9, 3, 17)])
+def test_degenerate_volumes_match_oracle(dims):
+    # a single cell, thin and flat volumes (a dimension of 1: no cells, no
+    # hits), exact multiples of 4
+    rng = np.random.default_rng(3)
+    f = rng.standard_normal((dims[2], dims[1], dims[0])).astype(np.float32)
+    bits, bmin, bmax = oracle.encode_volume(f, 12)
+    d = oracle.decode_volume(bits, dims, 12)
+    vol = pkg().Volume(bits, dims, 12, bmin, bmax)
+    try:
+        c = (np.asarray(dims, float) - 1) / 2
+        cam = cameras.pinhole(c + np.array([-3.0, -2.0, 4.0]) * max(dims), c, 40.0, 1.0)
+        st = check(vol, d, float(np.median(d)), cam, (0.3, -0.5, 0.8), 21, 21)
+        if 1 in dims:
+            assert st["hits"] == 0
+    finally:
+        vol.release()
