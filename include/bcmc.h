@@ -68,7 +68,7 @@ extern "C" {
 #define ISO_INPUT_ON_DEVICE 1u /* compressed/block_min/block_max are device pointers */
 #define ISO_DEBUG 2u           /* keep per-stage debug copies (see iso_debug_get) */
 #define ISO_NO_GRAPH 4u        /* launch each extraction's kernels one by one instead of
-                                  replaying the CUDA graph captured at the second extraction */
+                                  replaying the CUDA graphs captured once a volume has been extracted 8 times */
 
 typedef struct iso_volume iso_volume;
 

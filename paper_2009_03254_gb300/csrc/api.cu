@@ -275,6 +275,8 @@ int free_volume(iso_volume *v) {
     return ISO_OK;
 }
 
+constexpr uint64_t kGraphAfter = 8;   // extractions of a volume before its passes are captured as graphs
+
 // What one queued pass runs: the whole extraction, the stages up to the
 // scan (the size becomes known), or the emission alone (after the count and
 // scan of the same isovalue).
@@ -402,11 +404,12 @@ int run(iso_volume *v, float iso, void *out, unsigned long long cap_tris, Phase 
                              ix ? (unsigned long long)(uintptr_t)ix->idx : 0ull,
                              ix ? ix->vert_cap : 0ull,
                              ix ? ix->vtx_base : 0ull};
-    // a pass is captured at the second extraction: a volume extracted once
-    // does not pay for capturing and instantiating graphs
+    // a pass is captured once the volume has been extracted kGraphAfter
+    // times: capturing and instantiating costs about as much as four graph
+    // launches save, so a volume extracted only a few times runs plain
     const bool indexed = ix != nullptr;
     const uint64_t before = v->extractions - (phase == Phase::kEmit ? 1 : 0);   // extractions before this one
-    const bool graph = v->use_graph && !(v->flags & ISO_DEBUG) && !v->profiling && before > 0;
+    const bool graph = v->use_graph && !(v->flags & ISO_DEBUG) && !v->profiling && before >= kGraphAfter;
     if (phase != Phase::kEmit) v->extractions++;
     if (graph && ensure_graph(v, phase, indexed) != ISO_OK) v->use_graph = false;   // plain launches
     const int gk = graph_kind(phase, indexed);

@@ -29,7 +29,7 @@ struct iso_volume {
     cudaGraph_t graph[4] = {};
     cudaGraphExec_t gexec[4] = {};
     bool use_graph = true;
-    uint64_t extractions = 0;         // full extractions run so far (the graph is captured at the second)
+    uint64_t extractions = 0;         // full extractions run so far (graphs are captured after kGraphAfter)
     // owned device allocations
     uint64_t *bits = nullptr;
     float *bmin = nullptr, *bmax = nullptr;   // staging of host block ranges during the load only

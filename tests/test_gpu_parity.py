@@ -287,8 +287,8 @@ def test_extract_into_capacity_and_exact_allocation():
     vol = p.Volume(bits, dims, rate, bmin, bmax)
     try:
         # the library sizes the mesh from the count: exactly T, no second pass;
-        # three times (plain launches, then the captured count and emit graphs)
-        for _ in range(3):
+        # ten times (plain launches, then the captured count and emit graphs)
+        for _ in range(10):
             mesh = vol.extract(0.0)
             assert mesh.stats["reruns"] == 0 and mesh.num_triangles == T
             v = mesh.vertices.cpu().numpy().reshape(-1, 3, 4)
@@ -368,13 +368,22 @@ def test_graph_and_plain_launches_agree():
     bits, bmin, bmax = oracle.encode_volume(f, rate)
     a = p.Volume(bits, dims, rate, bmin, bmax, graph=True, initial_cache_fraction=0.05)
     b = p.Volume(bits, dims, rate, bmin, bmax, graph=False, initial_cache_fraction=0.05)
+    t = torch()
     try:
-        for iso in (0.0, 0.3, -0.4, 0.3, 0.1):
+        # two extractions per isovalue and volume (the exact-size and the
+        # single-pass path): graphs are captured after eight, so the later
+        # isovalues replay them
+        for iso in (0.0, 0.3, -0.4, 0.3, 0.1, -0.2, 0.5, 0.0):
             ma, mb = a.extract(iso), b.extract(iso)
             assert ma.num_triangles == mb.num_triangles
             assert ma.stats == mb.stats
             va, vb = ma.vertices.cpu().numpy(), mb.vertices.cpu().numpy()
             assert np.array_equal(va.view(np.uint32), vb.view(np.uint32))
+            oa = t.zeros((ma.num_triangles + 1, 3, 4), dtype=t.float32, device="cuda")
+            ob = t.zeros_like(oa)
+            sa, sb = a.extract_into(iso, oa), b.extract_into(iso, ob)
+            assert sa == sb and sa["num_triangles"] == ma.num_triangles
+            assert np.array_equal(oa.cpu().numpy().view(np.uint32), ob.cpu().numpy().view(np.uint32))
             ma.release()
             mb.release()
         ref = oracle.extract(bits, dims, rate, bmin, bmax, 0.1)
@@ -520,7 +529,7 @@ def test_launch_shapes_agree():
         for shape in (dict(), dict(cull_tile=2048, decode_tile=64, count_tile=16, scan_tile=1024, emit_tile=16),
                       dict(count_tile=64, emit_tile=64, scan_ctas=1, emit_ctas=1, decode_ctas=2)):
             vol.set_shape(**shape)
-            for _ in range(2):                      # plain launches, then the captured graph
+            for _ in range(4):                      # plain launches, later the captured graphs
                 vol.cache_reset()
                 m = vol.extract(0.1)
                 assert np.array_equal(m.vertices.cpu().numpy().view(np.uint32), want)
