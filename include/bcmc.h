@@ -67,6 +67,11 @@ extern "C" {
 /* iso_options.flags */
 #define ISO_INPUT_ON_DEVICE 1u /* compressed/block_min/block_max are device pointers */
 #define ISO_DEBUG 2u           /* keep per-stage debug copies (see iso_debug_get) */
+#define ISO_ASYNC_UPLOAD 8u    /* host inputs: return once the bitstream's copy is queued (on a
+                                  stream of the library's); the first extraction's range test and
+                                  cache update overlap the copy and its decode waits for it.  The
+                                  caller keeps `compressed` valid until the first call on the
+                                  volume returns (pinned memory makes the copy asynchronous) */
 #define ISO_NO_GRAPH 4u        /* launch each extraction's kernels one by one instead of
                                   replaying the CUDA graphs captured once a volume has been extracted 8 times */
 

@@ -29,6 +29,7 @@ ISO_ERR_CORRUPT = 8
 ISO_INPUT_ON_DEVICE = 1
 ISO_DEBUG = 2
 ISO_NO_GRAPH = 4
+ISO_ASYNC_UPLOAD = 8
 ISO_VERTEX_FLOAT4 = 0
 ISO_VERTEX_PACKED = 1
 
@@ -249,7 +250,7 @@ class Volume:
     """
 
     def __init__(self, bits, dims, rate, bmin, bmax, *, stream=None, debug=False, initial_cache_fraction=0.1,
-                 cache_budget_bytes=0, graph=True):
+                 cache_budget_bytes=0, graph=True, async_upload=False):
         self._h = None
         on_device = not isinstance(bits, np.ndarray) and bool(getattr(bits, "is_cuda", False))
         if not isinstance(bits, np.ndarray) and not on_device:       # CPU (e.g. pinned) torch tensors
@@ -263,7 +264,9 @@ class Volume:
         self.nb = int(np.prod(block_dims(self.dims)))
         opt = _Options()
         opt.flags = (ISO_INPUT_ON_DEVICE if on_device else 0) | (ISO_DEBUG if debug else 0) | \
-            (0 if graph else ISO_NO_GRAPH)
+            (0 if graph else ISO_NO_GRAPH) | (ISO_ASYNC_UPLOAD if async_upload else 0)
+        # with async_upload the bitstream is copied after this returns: keep it alive
+        self._upload_source = bits if async_upload else None
         opt.stream = stream if stream is not None else _current_stream()
         opt.initial_cache_fraction = float(initial_cache_fraction)
         opt.cache_budget_bytes = int(cache_budget_bytes)

@@ -146,6 +146,13 @@ iso_launch_shape shape_of(const Plan &want, int device, bool single) {
                             run(want.mc_emit, lim.mc_emit), (uint32_t)tiles.emit_tile};
 }
 
+int finish_upload(iso_volume *v) {
+    if (!v || !v->upload_pending) return ISO_OK;
+    v->upload_pending = false;
+    ISO_CK(cudaEventSynchronize(v->uploaded));
+    return ISO_OK;
+}
+
 Plan default_tiles(const Plan *want) {
     Plan t{};
     t.cull_tile = want && want->cull_tile ? want->cull_tile : kDefaultCullTile;
@@ -253,6 +260,7 @@ int free_volume(iso_volume *v) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaSetDevice(v->device);
+    if (v->uploaded) cudaEventSynchronize(v->uploaded);   // nothing is freed under a copy in flight
     DevState &s = v->s;
     void *ptrs[] = {v->bits, v->bmin, v->bmax, v->hull, v->hull8, v->tables, s.mactive, s.iactive, s.inew, s.icand,
                     s.islot, s.slast, s.sblock, s.lbuf[0], s.lbuf[1], s.newslot, s.slots, s.desc_cull, s.desc_cand,
@@ -268,6 +276,8 @@ int free_volume(iso_volume *v) {
         if (v->graph[k]) cudaGraphDestroy(v->graph[k]);
     }
     if (v->capture_stream) cudaStreamDestroy(v->capture_stream);
+    if (v->upload_stream) cudaStreamDestroy(v->upload_stream);
+    if (v->uploaded) cudaEventDestroy(v->uploaded);
     for (cudaEvent_t &e : v->ev)
         if (e) cudaEventDestroy(e);
     cudaSetDevice(dev);
@@ -291,7 +301,7 @@ int enqueue_pipeline(iso_volume *v, cudaStream_t st, Phase phase, bool prof, boo
     CK(cudaMemcpyAsync(&v->s.ctl->params, v->host_params, sizeof(Params), cudaMemcpyHostToDevice, st));
     if (prof) cudaEventRecord(phase == Phase::kEmit ? v->ev[ISO_NUM_STAGES + 1] : v->ev[0], st);
     if (phase != Phase::kEmit) {
-        launch_front(L, v->plan, st, prof ? v->ev : nullptr);
+        launch_front(L, v->plan, st, prof ? v->ev : nullptr, v->upload_pending ? v->uploaded : nullptr);
         launch_mc_count(L, debug, v->plan, st, indexed);
         if (prof) cudaEventRecord(v->ev[5], st);
         launch_mc_scan(L, v->plan, st);
@@ -420,6 +430,7 @@ int run(iso_volume *v, float iso, void *out, unsigned long long cap_tris, Phase 
         if (rc) return rc;
     }
     CK(cudaStreamSynchronize(v->stream));
+    v->upload_pending = false;                   // the decode waited for it
     if (phase != Phase::kCount) {
         v->split_emit = phase == Phase::kEmit;
         collect_stage_times(v);
@@ -705,11 +716,28 @@ int iso_load_volume(iso_volume **out, const void *compressed, size_t compressed_
         if (e_ != cudaSuccess) { (void)cudaGetLastError(); free_volume(v); \
             return e_ == cudaErrorMemoryAllocation ? ISO_ERR_OOM : ISO_ERR_CUDA; } \
     } while (0)
-    TRYC(cudaMemcpyAsync(v->bits, compressed, words * 8, kind, st));
     if (!on_device) {
         TRYC(cudaMemcpyAsync(v->bmin, block_min, (size_t)g.nb * 4, kind, st));
         TRYC(cudaMemcpyAsync(v->bmax, block_max, (size_t)g.nb * 4, kind, st));
     }
+    // the bitstream after the ranges (which the hulls need first)
+    if ((o.flags & ISO_ASYNC_UPLOAD) && !on_device) {
+        // the bitstream on a stream of its own, after the allocations queued on `st`
+        cudaEvent_t allocated = nullptr;
+        TRYC(cudaStreamCreateWithFlags(&v->upload_stream, cudaStreamNonBlocking));
+        TRYC(cudaEventCreateWithFlags(&v->uploaded, cudaEventDisableTiming));
+        TRYC(cudaEventCreateWithFlags(&allocated, cudaEventDisableTiming));
+        const cudaError_t e1 = cudaEventRecord(allocated, st);
+        const cudaError_t e2 = e1 == cudaSuccess ? cudaStreamWaitEvent(v->upload_stream, allocated, 0) : e1;
+        cudaEventDestroy(allocated);
+        TRYC(e2);
+        TRYC(cudaMemcpyAsync(v->bits, compressed, words * 8, kind, v->upload_stream));
+        TRYC(cudaEventRecord(v->uploaded, v->upload_stream));
+        v->upload_pending = true;
+    } else {
+        TRYC(cudaMemcpyAsync(v->bits, compressed, words * 8, kind, st));
+    }
+
     TRYC(cudaMemcpyAsync(v->tables, table_bytes, sizeof(table_bytes), cudaMemcpyHostToDevice, st));
     TRYC(cudaMemsetAsync(s.islot, 0xFF, (size_t)g.nb * 4, st));
     TRYC(cudaMemsetAsync(s.sblock, 0xFF, (size_t)v->cap * 4, st));

@@ -218,6 +218,7 @@ int iso_batch_create(iso_batch **out, iso_volume *const *volumes, uint32_t n, vo
         std::sort(sorted.begin(), sorted.end());
         if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end()) return ISO_ERR_INVALID_ARG;
     }
+    for (iso_volume *v : vols) ISO_CK_RC(finish_upload(v));   // batches read the bitstreams on their own stream
     iso_batch *b = new (std::nothrow) iso_batch();
     if (!b) return ISO_ERR_OOM;
     b->device = dev;

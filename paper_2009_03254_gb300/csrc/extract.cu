@@ -569,10 +569,11 @@ constexpr size_t decode_smem(int threads) { return 32u * 8u * (size_t)threads; }
 
 // Algorithm 1 after the cull (both list kernels), then the decode
 template <bool kOne>
-void cache_update(const Launch &L, const Plan &pl, cudaStream_t st, cudaEvent_t *ev) {
+void cache_update(const Launch &L, const Plan &pl, cudaStream_t st, cudaEvent_t *ev, cudaEvent_t bits_ready) {
     lru_a_kernel<kOne><<<pl.lru_a, kThreads, 0, st>>>(L);
     lru_b_kernel<kOne><<<pl.lru_b, kThreads, 0, st>>>(L);
     if (ev) cudaEventRecord(ev[3], st);
+    if (bits_ready) cudaStreamWaitEvent(st, bits_ready, 0);   // the bitstream may still be on its way
     if (pl.decode_tile == 64) decode_new_kernel<64, kOne><<<pl.decode, 64, decode_smem(64), st>>>(L);
     else if (pl.decode_tile == 256) decode_new_kernel<256, kOne><<<pl.decode, 256, decode_smem(256), st>>>(L);
     else decode_new_kernel<128, kOne><<<pl.decode, 128, decode_smem(128), st>>>(L);
@@ -580,23 +581,23 @@ void cache_update(const Launch &L, const Plan &pl, cudaStream_t st, cudaEvent_t 
 }
 
 template <bool kOne>
-void front(const Launch &L, const Plan &pl, cudaStream_t st, cudaEvent_t *ev) {
+void front(const Launch &L, const Plan &pl, cudaStream_t st, cudaEvent_t *ev, cudaEvent_t bits_ready) {
     prep_kernel<kOne><<<pl.prep, kThreads, 0, st>>>(L);
     if (ev) cudaEventRecord(ev[1], st);
     if (pl.cull_tile == 2048) cull_kernel<8, kOne><<<pl.cull, kThreads, 0, st>>>(L);
     else cull_kernel<16, kOne><<<pl.cull, kThreads, 0, st>>>(L);
     if (ev) cudaEventRecord(ev[2], st);
-    cache_update<kOne>(L, pl, st, ev);
+    cache_update<kOne>(L, pl, st, ev, bits_ready);
 }
 
-void launch_front(const Launch &L, const Plan &pl, cudaStream_t st, cudaEvent_t *ev) {
-    if (L.vols) front<false>(L, pl, st, ev);
-    else front<true>(L, pl, st, ev);
+void launch_front(const Launch &L, const Plan &pl, cudaStream_t st, cudaEvent_t *ev, cudaEvent_t bits_ready) {
+    if (L.vols) front<false>(L, pl, st, ev, bits_ready);
+    else front<true>(L, pl, st, ev, bits_ready);
 }
 
 void launch_cache_update(const Launch &L, const Plan &pl, cudaStream_t st) {
-    if (L.vols) cache_update<false>(L, pl, st, nullptr);
-    else cache_update<true>(L, pl, st, nullptr);
+    if (L.vols) cache_update<false>(L, pl, st, nullptr, nullptr);
+    else cache_update<true>(L, pl, st, nullptr, nullptr);
 }
 
 void launch_batch_params(const Launch &L, const float *d_iso, cudaStream_t st) {

@@ -91,7 +91,9 @@ constexpr int kDefaultCullTile = 4096, kDefaultDecodeTile = 128, kDefaultCountTi
 // Front of the pipeline: prep, cull, cache update (two kernels), decode.
 // With `ev`, events ev[1..4] are recorded after prep, cull, cache update
 // and decode.
-void launch_front(const Launch &L, const Plan &pl, cudaStream_t st, cudaEvent_t *ev);
+// (with bits_ready, the decode waits for that event: an upload still in flight)
+void launch_front(const Launch &L, const Plan &pl, cudaStream_t st, cudaEvent_t *ev,
+                  cudaEvent_t bits_ready = nullptr);
 // the cache update and decode alone (after a cull that set n_active/n_new)
 void launch_cache_update(const Launch &L, const Plan &pl, cudaStream_t st);
 // triangle stage: count, scan, emit.  A batch places the volumes' outputs

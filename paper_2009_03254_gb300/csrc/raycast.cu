@@ -309,6 +309,7 @@ extern "C" int iso_raycast(iso_volume *v, float isovalue, const iso_pinhole *cam
                       (double)cam->light[2] * cam->light[2];
     if (!(l2 > 1e-30) || !(l2 < 1e30)) return ISO_ERR_INVALID_ARG;
     DeviceGuard dg(v->device);
+    ISO_CK_RC(finish_upload(v));
     cudaStream_t st = v->stream;
     // the extraction's front for this isovalue: range test, cache update, decode
     *v->host_params = Params{isovalue, kVertexFloat4, 0u, 0u, 0u, 0u, 0ull, 0ull, 0ull, 0ull, 0ull};

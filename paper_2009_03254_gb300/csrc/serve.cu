@@ -433,6 +433,7 @@ int iso_server_create(iso_server **out, iso_volume *v, const iso_server_options 
     if (o.max_batch > (uint32_t)kMaxServe) return ISO_ERR_INVALID_ARG;
     if (o.vertex_format != ISO_VERTEX_FLOAT4 && o.vertex_format != ISO_VERTEX_PACKED) return ISO_ERR_INVALID_ARG;
     DeviceGuard dg(v->device);
+    ISO_CK_RC(finish_upload(v));             // the server reads the bitstream on its own stream
     iso_server *sv = new (std::nothrow) iso_server();
     if (!sv) return ISO_ERR_OOM;
     sv->v = v;

@@ -23,6 +23,12 @@ struct iso_volume {
     bcmc::Ctl *host_ctl = nullptr;    // pinned mirror for the one readback
     bcmc::Params *host_params = nullptr;   // pinned: this extraction's isovalue, output and capacity
     cudaStream_t capture_stream = nullptr;
+    // ISO_ASYNC_UPLOAD: the bitstream's copy runs on its own stream; the
+    // first extraction's decode waits for `uploaded`, every other call waits
+    // on the host (upload_pending until then)
+    cudaStream_t upload_stream = nullptr;
+    cudaEvent_t uploaded = nullptr;
+    bool upload_pending = false;
     // one extraction: params copy, the stage kernels, count readback; one
     // graph per kind (0: triangle soup, 1: indexed mesh, 2: the soup up to
     // the scan, 3: the emission alone)
@@ -65,6 +71,12 @@ int dalloc_on(T **p, size_t count, int dev, cudaStream_t st) {
     return dalloc_bytes(reinterpret_cast<void **>(p), count * sizeof(T), dev, st);
 }
 
+#define ISO_CK_RC(call)          \
+    do {                         \
+        const int rc_ = (call);  \
+        if (rc_) return rc_;     \
+    } while (0)
+
 struct DeviceGuard {              // make a device current for the call
     int prev = -1;
     explicit DeviceGuard(int dev) {
@@ -105,6 +117,9 @@ iso_launch_shape shape_of(const bcmc::Plan &want, int device, bool single);
 // largest CTAs per SM of each kernel for these tile sizes, in single-volume
 // or batch launches (cached per device)
 bcmc::Plan occupancy_limits_of(int device, const bcmc::Plan &tiles, bool single);
+
+// wait on the host for an asynchronous upload still in flight
+int finish_upload(iso_volume *v);
 
 // device address of the single-volume work counters (inside the control block)
 inline uint32_t *single_counters(const iso_volume *v) {

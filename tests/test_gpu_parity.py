@@ -538,3 +538,50 @@ def test_launch_shapes_agree():
             vol.set_shape(count_tile=48)
     finally:
         vol.release()
+
+
+def test_async_upload():
+    # the bitstream's copy overlaps the first extraction's front; every entry
+    # point sees the whole volume (extraction, ray casting, batches, servers,
+    # release before any use)
+    import torch as t
+    p = pkg()
+    dims, rate = (44, 38, 31), 8
+    f = make_field("noise", dims, 14)
+    bits, bmin, bmax = oracle.encode_volume(f, rate)
+    hb = t.from_numpy(bits.view(np.int64)).pin_memory()
+    hmin, hmax = t.from_numpy(bmin).pin_memory(), t.from_numpy(bmax).pin_memory()
+    sync = p.Volume(bits, dims, rate, bmin, bmax)
+    try:
+        ref = sync.extract(0.05)
+        want = ref.vertices.cpu().numpy().view(np.uint32)
+        ref.release()
+        for first in ("extract", "extract_into", "batch", "server", "release"):
+            v = p.Volume(hb, dims, rate, hmin, hmax, async_upload=True)
+            try:
+                if first == "extract":
+                    m = v.extract(0.05)
+                    assert np.array_equal(m.vertices.cpu().numpy().view(np.uint32), want)
+                    m.release()
+                elif first == "extract_into":
+                    out = t.zeros((len(want) // 3 + 1, 3, 4), dtype=t.float32, device="cuda")
+                    st = v.extract_into(0.05, out)
+                    got = out.cpu().numpy().reshape(-1, 4)[:3 * st["num_triangles"]].view(np.uint32)
+                    assert np.array_equal(got, want)
+                elif first == "batch":
+                    b = p.Batch([v])
+                    verts, offs, _ = b.extract(np.array([0.05], np.float32))
+                    assert int(offs[1]) * 3 == len(want)
+                    assert np.array_equal(verts.cpu().numpy().reshape(-1, 4).view(np.uint32)[:len(want)], want)
+                    b.release()
+                elif first == "server":
+                    srv = p.Server(v)
+                    status, m = srv.wait(srv.submit(0.05), timeout_ms=10000)
+                    assert status == p.ISO_OK
+                    assert np.array_equal(m.vertices.cpu().numpy().view(np.uint32), want)
+                    m.release()
+                    srv.release()
+            finally:
+                v.release()
+    finally:
+        sync.release()
