@@ -58,7 +58,7 @@ namespace bcmc {
 namespace {
 
 constexpr int kBPW = 4;                               // candidates per warp tile
-constexpr int kHalo = 200;                            // x + 8y + 40z, x,y,z in [0,5)
+constexpr int kHalo = 128;                            // x + 5y + 25z, x,y,z in [0,5)
 constexpr int kTmap = kBPW * 64 * 5;                  // triangles a warp tile can hold
 constexpr int kWinWords = 3 * 6 * 4;                  // window rows (indexed meshes), then
 constexpr int kWinTable = kWinWords + 32;             // a per-lane word for blocks inside the volume
@@ -83,7 +83,7 @@ struct EmitSmem {
     WarpTile w[kW];
     float4 stage[kW][kIdx ? 24 : 96];                 // 32 triangles' vertices (indexed: indices) per warp
     uint16_t tmap[kW][kTmap];                         // block-in-tile (2) | cell (6) | k (3)
-    uint32_t tri_row[256 * kMaxTriPerCell];           // 3 edge numbers of each table triangle, packed
+    uint16_t tri_row[256 * kMaxTriPerCell];           // 3 edge numbers of each table triangle, 4 bits each
     uint8_t num_tri[256];
     uint32_t edge_info[12];
     // indexed: per block, the 12 cut-edge words, then (from word 12) the
@@ -93,44 +93,42 @@ struct EmitSmem {
 };
 
 // Halo load job j of a block (0..63; 50 used): neighbour o, source sample
-// index inside that block, destination in the padded halo, float4 or not.
+// index inside that block, destination sample x + 5y + 25z of the window,
+// a row of 4 samples (one float4 load, four stores) or one sample.
 // Packed: valid(1) | vec(1) | o(3) | src(6) | dst(8).
 __device__ __forceinline__ uint32_t halo_job(int j) {
     int o = 0, src = 0, dst = 0, vec = 0;
     if (j < 16) {                       // own rows (y, z) = (j & 3, j >> 2)
-        o = 0; src = 4 * j; dst = 8 * (j & 3) + 40 * (j >> 2); vec = 1;
+        o = 0; src = 4 * j; dst = 5 * (j & 3) + 25 * (j >> 2); vec = 1;
     } else if (j < 32) {                // +x face: sample (0, y, z) -> halo (4, y, z)
         const int r = j - 16;
-        o = 1; src = 4 * r; dst = 4 + 8 * (r & 3) + 40 * (r >> 2);
+        o = 1; src = 4 * r; dst = 4 + 5 * (r & 3) + 25 * (r >> 2);
     } else if (j < 36) {                // +y rows: (x, 0, z) -> (x, 4, z)
         const int z = j - 32;
-        o = 2; src = 16 * z; dst = 32 + 40 * z; vec = 1;
+        o = 2; src = 16 * z; dst = 20 + 25 * z; vec = 1;
     } else if (j < 40) {                // +z rows: (x, y, 0) -> (x, y, 4)
         const int y = j - 36;
-        o = 4; src = 4 * y; dst = 8 * y + 160; vec = 1;
+        o = 4; src = 4 * y; dst = 5 * y + 100; vec = 1;
     } else if (j < 44) {                // +xy edge: (0, 0, z) -> (4, 4, z)
         const int z = j - 40;
-        o = 3; src = 16 * z; dst = 36 + 40 * z;
+        o = 3; src = 16 * z; dst = 24 + 25 * z;
     } else if (j < 48) {                // +xz edge: (0, y, 0) -> (4, y, 4)
         const int y = j - 44;
-        o = 5; src = 4 * y; dst = 164 + 8 * y;
+        o = 5; src = 4 * y; dst = 104 + 5 * y;
     } else if (j == 48) {               // +yz row: (x, 0, 0) -> (x, 4, 4)
-        o = 6; src = 0; dst = 192; vec = 1;
+        o = 6; src = 0; dst = 120; vec = 1;
     } else if (j == 49) {               // corner: (0, 0, 0) -> (4, 4, 4)
-        o = 7; src = 0; dst = 196;
+        o = 7; src = 0; dst = 124;
     } else {
         return 0;
     }
     return 1u | ((uint32_t)vec << 1) | ((uint32_t)o << 2) | ((uint32_t)src << 5) | ((uint32_t)dst << 11);
 }
 
-// padded halo offset of logical sample s = x + 5y + 25z
-__device__ __forceinline__ int halo_off(int s) { return (s % 5) + 8 * ((s / 5) % 5) + 40 * (s / 25); }
-
 // Per-lane constants of phases B and C.
 struct LaneConst {
     uint32_t job0, job1;                // halo jobs lane and lane + 32
-    int cls[4];                         // halo offsets of samples lane + 32r (or -1)
+    int cls[4];                         // samples lane + 32r (or -1 past the window)
     // where each of the lane's two cells starts in the 128-bit mask: cell
     // lane (z 0..1) starts in word 0 or 1, cell lane + 32 (z 2..3) in word
     // 1 or 2; `up` says the later of the two, `cshift` the bit in it
@@ -140,7 +138,7 @@ struct LaneConst {
         job0 = halo_job(lane);
         job1 = halo_job(lane + 32);
 #pragma unroll
-        for (int r = 0; r < 4; r++) cls[r] = lane + 32 * r < 125 ? halo_off(lane + 32 * r) : -1;
+        for (int r = 0; r < 4; r++) cls[r] = lane + 32 * r < 125 ? lane + 32 * r : -1;
 #pragma unroll
         for (int h = 0; h < 2; h++) {
             const int cell = lane + 32 * h, base = (cell & 3) + 5 * ((cell >> 2) & 3) + 25 * (cell >> 4);
@@ -306,8 +304,12 @@ __device__ __forceinline__ void stage_and_classify(const DevState &s, const Geom
             const uint32_t job = h ? lc.job1 : lc.job0;
             if (q < nb_w && (job & 1u)) {
                 float *d = &wt.halo[q][0] + (job >> 11);
-                if (job & 2u) *reinterpret_cast<float4 *>(d) = v[2 * q + h];
-                else *d = v[2 * q + h].x;
+                d[0] = v[2 * q + h].x;
+                if (job & 2u) {
+                    d[1] = v[2 * q + h].y;
+                    d[2] = v[2 * q + h].z;
+                    d[3] = v[2 * q + h].w;
+                }
             }
         }
     __syncwarp();
@@ -567,14 +569,14 @@ __device__ __forceinline__ void emit_body(const Launch &L) {
     for (int i = threadIdx.x; i < 256; i += 32 * kW) sm.num_tri[i] = tables[i];
     for (int i = threadIdx.x; i < 256 * kMaxTriPerCell; i += 32 * kW) {
         const uint8_t *e = tables + 256 + (i / kMaxTriPerCell) * 16 + 3 * (i % kMaxTriPerCell);
-        sm.tri_row[i] = (uint32_t)e[0] | ((uint32_t)e[1] << 8) | ((uint32_t)e[2] << 16);
+        sm.tri_row[i] = (uint16_t)(e[0] | (e[1] << 4) | (e[2] << 8));
     }
     if (kIdx) load_window_rows(sm.win);
     if (threadIdx.x < 12) {
         // edge e: lower corner (dx,dy,dz), axis a; halo offsets of its two samples
         const int e = threadIdx.x, a = e >> 2, j0 = e & 1, j1 = (e >> 1) & 1;
         const int dx = a == 0 ? 0 : j0, dy = a == 0 ? j0 : (a == 1 ? 0 : j1), dz = a == 2 ? 0 : j1;
-        const int lo = dx + 8 * dy + 40 * dz, hi = lo + (a == 0 ? 1 : (a == 1 ? 8 : 40));
+        const int lo = dx + 5 * dy + 25 * dz, hi = lo + (a == 0 ? 1 : (a == 1 ? 5 : 25));
         sm.edge_info[e] = (uint32_t)lo | ((uint32_t)hi << 8) | ((uint32_t)dx << 16) | ((uint32_t)dy << 17) |
                           ((uint32_t)dz << 18) | ((uint32_t)a << 19);
     }
@@ -664,8 +666,8 @@ __device__ __forceinline__ void emit_body(const Launch &L) {
                 const uint32_t e = tm[k];
                 const uint32_t q = e >> 9, smp = (e >> 2) & 127u, ax = e & 3u;
                 const uint32_t sx = smp % 5u, sy = (smp / 5u) % 5u, sz = smp / 25u;
-                const float *hp = &wt.halo[q][0] + sx + 8 * sy + 40 * sz;
-                const float vlo = hp[0], vhi = hp[ax == 0 ? 1 : (ax == 1 ? 8 : 40)];
+                const float *hp = &wt.halo[q][0] + smp;
+                const float vlo = hp[0], vhi = hp[ax == 0 ? 1 : (ax == 1 ? 5 : 25)];
                 float px = (float)sx, py = (float)sy, pz = (float)sz;
                 float tt;
                 if (!packed) tt = __fdividef(__fsub_rn(iso, vlo), __fsub_rn(vhi, vlo));
@@ -687,16 +689,20 @@ __device__ __forceinline__ void emit_body(const Launch &L) {
             vt += c->params.vtx_base;                  // indices count the vertices of earlier waves
             __syncwarp();                              // the vertex map is read: tm takes the triangles
         }
+        // each lane lists its two cells' triangles at their offsets (unrolled,
+        // predicated stores: the counts differ from lane to lane)
         uint32_t tacc = 0;
-#pragma unroll
-        for (int q = 0; q < kBPW; q++) {
-            if (q >= nb_w) continue;
+#pragma unroll 1
+        for (int q = 0; q < nb_w; q++) {
             const uint32_t n0 = (n0p >> (8 * q)) & 0xFFu, n1 = (n1p >> (8 * q)) & 0xFFu;
             const uint32_t b0 = (s0 >> (8 * q)) & 0xFFu;
             const uint32_t o0 = tacc + ((i0 >> (8 * q)) & 0xFFu) - n0;
             const uint32_t o1 = tacc + b0 + ((i1 >> (8 * q)) & 0xFFu) - n1;
-            for (uint32_t k = 0; k < n0; k++) tm[o0 + k] = (uint16_t)((q << 9) | (lane << 3) | k);
-            for (uint32_t k = 0; k < n1; k++) tm[o1 + k] = (uint16_t)((q << 9) | ((lane + 32) << 3) | k);
+#pragma unroll
+            for (uint32_t k = 0; k < kMaxTriPerCell; k++) {
+                if (k < n0) tm[o0 + k] = (uint16_t)((q << 9) | (lane << 3) | k);
+                if (k < n1) tm[o1 + k] = (uint16_t)((q << 9) | ((lane + 32) << 3) | k);
+            }
             tacc += b0 + ((s1 >> (8 * q)) & 0xFFu);
         }
         __syncwarp();
@@ -710,11 +716,11 @@ __device__ __forceinline__ void emit_body(const Launch &L) {
                 const uint32_t q = e16 >> 9, cell = (e16 >> 3) & 63u, k = e16 & 7u;
                 const uint32_t row = sm.tri_row[wt.cases[q][cell] * kMaxTriPerCell + k];
                 const int cx = (int)(cell & 3u), cy = (int)((cell >> 2) & 3u), cz = (int)(cell >> 4);
-                const float *hb = &wt.halo[q][0] + cx + 8 * cy + 40 * cz;
+                const float *hb = &wt.halo[q][0] + cx + 5 * cy + 25 * cz;
                 const float wbits = __uint_as_float(wt.bid[q]);
 #pragma unroll
                 for (int j = 0; j < 3; j++) {
-                    const uint32_t info = sm.edge_info[(row >> (8 * j)) & 0xFFu];
+                    const uint32_t info = sm.edge_info[(row >> (4 * j)) & 0xFu];
                     const uint32_t a = (info >> 19) & 3u;
                     if constexpr (kIdx) {
                         // the rank of the edge among the tile's vertices: those
@@ -797,9 +803,10 @@ __device__ __forceinline__ void emit_body(const Launch &L) {
     }
 }
 
-// the triangle soup
+// the triangle soup; registers bounded for 24 warps per SM (32 warps fit in
+// shared memory, but at 64 registers the kernel spills and runs slower)
 template <int kW, bool kDebug, bool kOne>
-__global__ void __launch_bounds__(32 * kW) mc_emit_kernel(Launch L) {
+__global__ void __launch_bounds__(32 * kW, 24 / kW) mc_emit_kernel(Launch L) {
     emit_body<kW, kDebug, kOne, false>(L);
 }
 
