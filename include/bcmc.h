@@ -33,7 +33,11 @@
  *     block origin 4*(bx,by,bz), w = the block id as uint32 bits; three
  *     consecutive vertices form one triangle whose right-hand normal
  *     points toward increasing values; triangles are ordered by block id,
- *     then cell (x fastest), then case-table order.
+ *     then cell (x fastest), then case-table order;
+ *   - caller device buffers the library writes or reads as arrays must be
+ *     aligned to their element: 16 bytes for float4 vertices, 8 for compact
+ *     vertices, fragments and hits, 4 for indices and RGBA pixels; a
+ *     misaligned one is refused with ISO_ERR_INVALID_ARG.
  *
  * Errors: every int-returning call returns ISO_OK or one of ISO_ERR_*;
  * no call throws or aborts.  A failed call leaves its outputs unspecified

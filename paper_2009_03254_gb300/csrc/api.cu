@@ -787,7 +787,8 @@ int iso_load_volume(iso_volume **out, const void *compressed, size_t compressed_
 
 int iso_extract_into(iso_volume *v, float isovalue, float *d_vertices, uint64_t capacity_triangles,
                      iso_stats *stats) {
-    if (!v || !std::isfinite(isovalue) || (!d_vertices && capacity_triangles)) return ISO_ERR_INVALID_ARG;
+    if (!v || !std::isfinite(isovalue) || (!d_vertices && capacity_triangles) || misaligned(d_vertices, 16))
+        return ISO_ERR_INVALID_ARG;
     DeviceGuard dg(v->device);
     unsigned long long total = 0;
     const int rc = extract_to(v, isovalue, d_vertices, capacity_triangles, kVertexFloat4, 0u, stats, &total);
@@ -797,7 +798,8 @@ int iso_extract_into(iso_volume *v, float isovalue, float *d_vertices, uint64_t 
 
 int iso_extract_all_blocks_into(iso_volume *v, float isovalue, float *d_vertices, uint64_t capacity_triangles,
                      iso_stats *stats) {
-    if (!v || !std::isfinite(isovalue) || (!d_vertices && capacity_triangles)) return ISO_ERR_INVALID_ARG;
+    if (!v || !std::isfinite(isovalue) || (!d_vertices && capacity_triangles) || misaligned(d_vertices, 16))
+        return ISO_ERR_INVALID_ARG;
     DeviceGuard dg(v->device);
     unsigned long long total = 0;
     const int rc = extract_to(v, isovalue, d_vertices, capacity_triangles, kVertexFloat4, kParamAllBlocks, stats, &total);
@@ -809,7 +811,8 @@ int iso_extract_indexed_into(iso_volume *v, float isovalue, int vertex_format, v
                              uint64_t capacity_vertices, uint32_t *d_indices, uint64_t capacity_triangles,
                              iso_stats *stats) {
     if (!v || !std::isfinite(isovalue) || (!d_vertices && capacity_vertices) || (!d_indices && capacity_triangles) ||
-        (vertex_format != ISO_VERTEX_FLOAT4 && vertex_format != ISO_VERTEX_PACKED))
+        (vertex_format != ISO_VERTEX_FLOAT4 && vertex_format != ISO_VERTEX_PACKED) ||
+        misaligned(d_vertices, vertex_format == ISO_VERTEX_FLOAT4 ? 16 : 8) || misaligned(d_indices, 4))
         return ISO_ERR_INVALID_ARG;
     DeviceGuard dg(v->device);
     unsigned long long total = 0;
@@ -837,7 +840,8 @@ int iso_decode_volume(const uint64_t *d_bits, uint32_t nx, uint32_t ny, uint32_t
 
 int iso_extract_packed_into(iso_volume *v, float isovalue, uint32_t *d_vertices, uint64_t capacity_triangles,
                      iso_stats *stats) {
-    if (!v || !std::isfinite(isovalue) || (!d_vertices && capacity_triangles)) return ISO_ERR_INVALID_ARG;
+    if (!v || !std::isfinite(isovalue) || (!d_vertices && capacity_triangles) || misaligned(d_vertices, 8))
+        return ISO_ERR_INVALID_ARG;
     DeviceGuard dg(v->device);
     unsigned long long total = 0;
     const int rc = extract_to(v, isovalue, d_vertices, capacity_triangles, kVertexPacked, 0u, stats, &total);

@@ -193,7 +193,7 @@ void free_batch(iso_batch *b) {
 }
 
 int set_inputs(iso_batch *b, const float *isovalues, float *d_vertices, uint64_t capacity_triangles) {
-    if (!isovalues || (!d_vertices && capacity_triangles)) return ISO_ERR_INVALID_ARG;
+    if (!isovalues || (!d_vertices && capacity_triangles) || misaligned(d_vertices, 16)) return ISO_ERR_INVALID_ARG;
     for (uint32_t i = 0; i < b->n; i++)
         if (!std::isfinite(isovalues[i])) return ISO_ERR_INVALID_ARG;
     std::memcpy(b->h_iso, isovalues, b->n * sizeof(float));

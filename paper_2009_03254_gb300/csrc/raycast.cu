@@ -299,7 +299,7 @@ extern "C" int iso_raycast(iso_volume *v, float isovalue, const iso_pinhole *cam
     using namespace bcmc;
     using namespace bcmc_host;
     if (!v || !cam || !d_hits || !std::isfinite(isovalue) || cam->width == 0 || cam->height == 0 ||
-        cam->width > 32768 || cam->height > 32768)
+        cam->width > 32768 || cam->height > 32768 || misaligned(d_hits, 8) || misaligned(d_rgba, 4))
         return ISO_ERR_INVALID_ARG;
     const float *vecs[5] = {cam->eye, cam->forward, cam->right, cam->up, cam->light};
     for (const float *p : vecs)

@@ -322,7 +322,9 @@ extern "C" int iso_render(const void *d_vertices, int vertex_format, const uint3
         camera->height > 32768 || nx == 0 || ny == 0 || nz == 0 ||
         (vertex_format != ISO_VERTEX_FLOAT4 && vertex_format != ISO_VERTEX_PACKED) ||
         (num_triangles && !d_vertices) || num_triangles > 0xFFFFFFFFull ||
-        (!d_indices && num_vertices < 3 * num_triangles))      // a soup needs its 3T vertices
+        (!d_indices && num_vertices < 3 * num_triangles) ||    // a soup needs its 3T vertices
+        misaligned(d_vertices, vertex_format == ISO_VERTEX_FLOAT4 ? 16 : 8) || misaligned(d_indices, 4) ||
+        misaligned(d_fragments, 8) || misaligned(d_rgba, 4))
         return ISO_ERR_INVALID_ARG;
     const float *L = camera->light;
     const double l2 = (double)L[0] * L[0] + (double)L[1] * L[1] + (double)L[2] * L[2];

@@ -62,6 +62,10 @@ namespace bcmc_host {
         }                                                                     \
     } while (0)
 
+// A caller's device pointer that its element type (or the vector stores
+// and bulk copies that write it) cannot use: not a multiple of `align` bytes.
+inline bool misaligned(const void *p, uintptr_t align) { return ((uintptr_t)p & (align - 1)) != 0; }
+
 // Stream-ordered allocation from the library's pool of `dev`, ordered on `st`.
 int dalloc_bytes(void **p, size_t bytes, int dev, cudaStream_t st);
 void dfree_on(void *p, cudaStream_t st);

@@ -117,3 +117,36 @@ def test_server_wait():
         srv.release()
         vol.release()
         alone.release()
+
+
+def test_misaligned_outputs_are_refused():
+    # the checks run on the host before any launch: nothing is written
+    import ctypes
+    import torch
+    p = pkg()
+    dims, rate, bits, bmin, bmax = volume_data(dims=(20, 20, 20))
+    vol = p.Volume(bits, dims, rate, bmin, bmax)
+    try:
+        buf = torch.zeros(20000 * 12 + 16, dtype=torch.float32, device="cuda")
+        base = buf.data_ptr()
+        st = p._Stats()
+        L = p.lib()
+        for off in (4, 8):
+            ptr = ctypes.c_void_p(base + off)
+            assert L.iso_extract_into(vol._h, ctypes.c_float(0.0), ptr, 4096, ctypes.byref(st)) == p.ISO_ERR_INVALID_ARG
+            assert L.iso_extract_all_blocks_into(vol._h, ctypes.c_float(0.0), ptr, 4096,
+                                                 ctypes.byref(st)) == p.ISO_ERR_INVALID_ARG
+        ptr4 = ctypes.c_void_p(base + 4)
+        assert L.iso_extract_packed_into(vol._h, ctypes.c_float(0.0), ptr4, 4096, ctypes.byref(st)) == \
+            p.ISO_ERR_INVALID_ARG
+        assert L.iso_extract_indexed_into(vol._h, ctypes.c_float(0.0), p.ISO_VERTEX_FLOAT4, ctypes.c_void_p(base + 8),
+                                          1024, ctypes.c_void_p(base), 1024, ctypes.byref(st)) == p.ISO_ERR_INVALID_ARG
+        assert L.iso_extract_indexed_into(vol._h, ctypes.c_float(0.0), p.ISO_VERTEX_PACKED, ctypes.c_void_p(base),
+                                          1024, ctypes.c_void_p(base + 2), 1024, ctypes.byref(st)) == p.ISO_ERR_INVALID_ARG
+        assert torch.count_nonzero(buf).item() == 0
+        # the aligned pointer works
+        assert L.iso_extract_into(vol._h, ctypes.c_float(0.0), ctypes.c_void_p(base + 16), 20000,
+                                  ctypes.byref(st)) == p.ISO_OK
+        assert st.num_triangles > 0
+    finally:
+        vol.release()
