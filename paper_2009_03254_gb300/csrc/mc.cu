@@ -85,7 +85,7 @@ struct EmitSmem {
     uint16_t tmap[kW][kTmap];                         // block-in-tile (2) | cell (6) | k (3)
     uint16_t tri_row[256 * kMaxTriPerCell];           // 3 edge numbers of each table triangle, 4 bits each
     uint8_t num_tri[256];
-    uint32_t edge_info[12];
+    float4 edge_f[12];                                // (dx, dy, dz) and, as bits, the packed edge info
     // indexed: per block, the 12 cut-edge words, then (from word 12) the
     // vertices of the tile before each word
     alignas(16) uint32_t cut[kIdx ? kW : 1][kBPW][24];
@@ -577,8 +577,9 @@ __device__ __forceinline__ void emit_body(const Launch &L) {
         const int e = threadIdx.x, a = e >> 2, j0 = e & 1, j1 = (e >> 1) & 1;
         const int dx = a == 0 ? 0 : j0, dy = a == 0 ? j0 : (a == 1 ? 0 : j1), dz = a == 2 ? 0 : j1;
         const int lo = dx + 5 * dy + 25 * dz, hi = lo + (a == 0 ? 1 : (a == 1 ? 5 : 25));
-        sm.edge_info[e] = (uint32_t)lo | ((uint32_t)hi << 8) | ((uint32_t)dx << 16) | ((uint32_t)dy << 17) |
-                          ((uint32_t)dz << 18) | ((uint32_t)a << 19);
+        sm.edge_f[e] = make_float4((float)dx, (float)dy, (float)dz,
+                                   __uint_as_float((uint32_t)lo | ((uint32_t)hi << 8) | ((uint32_t)dx << 16) |
+                                                   ((uint32_t)dy << 17) | ((uint32_t)dz << 18) | ((uint32_t)a << 19)));
     }
     // all failure bits are final before this kernel starts
     const uint32_t total = launch_prefix<kOne>(
@@ -718,9 +719,11 @@ __device__ __forceinline__ void emit_body(const Launch &L) {
                 const int cx = (int)(cell & 3u), cy = (int)((cell >> 2) & 3u), cz = (int)(cell >> 4);
                 const float *hb = &wt.halo[q][0] + cx + 5 * cy + 25 * cz;
                 const float wbits = __uint_as_float(wt.bid[q]);
+                const float fx = (float)cx, fy = (float)cy, fz = (float)cz;
 #pragma unroll
                 for (int j = 0; j < 3; j++) {
-                    const uint32_t info = sm.edge_info[(row >> (4 * j)) & 0xFu];
+                    const float4 ef = sm.edge_f[(row >> (4 * j)) & 0xFu];
+                    const uint32_t info = __float_as_uint(ef.w);
                     const uint32_t a = (info >> 19) & 3u;
                     if constexpr (kIdx) {
                         // the rank of the edge among the tile's vertices: those
@@ -732,9 +735,7 @@ __device__ __forceinline__ void emit_body(const Launch &L) {
                         reinterpret_cast<uint32_t *>(stage)[3 * lane + j] = (uint32_t)(vt + rank);
                     } else {
                         const float vlo = hb[info & 0xFFu], vhi = hb[(info >> 8) & 0xFFu];
-                        float4 p = make_float4((float)(cx + (int)((info >> 16) & 1u)),
-                                               (float)(cy + (int)((info >> 17) & 1u)),
-                                               (float)(cz + (int)((info >> 18) & 1u)), wbits);
+                        float4 p = make_float4(__fadd_rn(fx, ef.x), __fadd_rn(fy, ef.y), __fadd_rn(fz, ef.z), wbits);
                         if (!packed) {
                             // t = (iso - v_lo) / (v_hi - v_lo) through the reciprocal: within
                             // 2 ulp of the correctly rounded quotient (positions within 1e-6)
@@ -784,10 +785,18 @@ __device__ __forceinline__ void emit_body(const Launch &L) {
                     if (f < nv && v0 + f < vcap) oi[v0 + f] = st[f];
                 }
             } else if (!packed) {
+                if (v0 + 96 <= vcap) {                 // warp-uniform: the whole chunk fits
 #pragma unroll
-                for (int r = 0; r < 3; r++) {
-                    const uint32_t f = lane + 32 * r;
-                    if (f < nv && v0 + f < vcap) out[v0 + f] = stage[f];
+                    for (int r = 0; r < 3; r++) {
+                        const uint32_t f = lane + 32 * r;
+                        if (f < nv) out[v0 + f] = stage[f];
+                    }
+                } else {
+#pragma unroll
+                    for (int r = 0; r < 3; r++) {
+                        const uint32_t f = lane + 32 * r;
+                        if (f < nv && v0 + f < vcap) out[v0 + f] = stage[f];
+                    }
                 }
             } else {
                 uint2 *out2 = reinterpret_cast<uint2 *>(out);
