@@ -17,7 +17,10 @@ Metric: triangles/s (whole step, all five surfaces), with voxels/s
   e2e      the same step through the public API from host memory: upload
            the compressed volume and ranges from pinned host buffers
            (iso_load_volume), five iso_extract calls (library-allocated
-           meshes), read back the counts, release
+           meshes), read back the counts, release; volumes are streamed
+           with double buffering (the next volume's upload overlaps this
+           volume's surfaces), and the one-at-a-time figure is reported
+           beside it as e2e.serial
   roofline the dominant stage's kernel: algorithmic bytes per launch over
            its CUDA-event duration, against the measured HBM copy peak
   cpu_baseline  the plain CPU oracle on a bounded window of the same field
@@ -678,34 +681,68 @@ def run_ours(args):
 
             load_s = []
 
-            def e2e_step():
+            def load():
                 t1 = time.perf_counter()
-                # the bitstream's copy overlaps the first extraction's range test
-                # and cache update (ISO_ASYNC_UPLOAD)
+                # the bitstream's copy is queued on the volume's upload stream
+                # (ISO_ASYNC_UPLOAD); the call returns after the ranges and hulls
                 v = bc.Volume(h_bits, DIMS, RATE, h_min, h_max, async_upload=True)
                 load_s.append(time.perf_counter() - t1)
+                return v
+
+            def extract_all(v):
                 n = 0
                 for iso in ISOS:
                     m = v.extract(iso)
                     n += m.num_triangles
                     m.release()
-                v.release()
                 return n
 
-            e2e_step()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            n_e2e = 0
-            for _ in range(e2e_steps):
-                n_e2e += e2e_step()
-            torch.cuda.synchronize()
-            dt = time.perf_counter() - t0
-            e2e = {"value": n_e2e / dt, "unit": "triangles/s", "h2d_bytes_per_step": h2d,
-                   "d2h_bytes_per_step": 2 * CTL_BYTES * len(ISOS), "ms_per_step": 1000 * dt / e2e_steps,
-                   "load_ms": 1000 * float(np.median(load_s[1:])),
-                   "includes": "iso_load_volume from pinned host (ranges, allocation, block hulls; the "
-                               "bitstream's upload queued and overlapped with the first extraction's front), "
-                               "5 x iso_extract (exact-size device meshes), count readbacks, release"}
+            def serial(k):
+                # load, five surfaces, release; one volume at a time
+                n = 0
+                for _ in range(k):
+                    v = load()
+                    n += extract_all(v)
+                    v.release()
+                return n
+
+            def streamed(k):
+                # double buffering: volume i + 1 is loaded (its bitstream
+                # uploading on the copy engine) before volume i's surfaces are
+                # extracted, so each upload overlaps the previous volume's work;
+                # every volume is still uploaded and read back inside the run
+                n = 0
+                nxt = load()
+                for i in range(k):
+                    cur = nxt
+                    if i + 1 < k:
+                        nxt = load()
+                    n += extract_all(cur)
+                    cur.release()
+                return n
+
+            def timed(fn, k):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                n = fn(k)
+                torch.cuda.synchronize()
+                return n, time.perf_counter() - t0
+
+            serial(1)
+            streamed(2)
+            load_s.clear()
+            n_ser, dt_ser = timed(serial, e2e_steps)
+            n_str, dt_str = timed(streamed, e2e_steps)
+            e2e = {"value": n_str / dt_str, "unit": "triangles/s", "h2d_bytes_per_step": h2d,
+                   "d2h_bytes_per_step": 2 * CTL_BYTES * len(ISOS), "ms_per_step": 1000 * dt_str / e2e_steps,
+                   "steps": e2e_steps, "load_ms": 1000 * float(np.median(load_s)),
+                   "includes": "per step: iso_load_volume from pinned host buffers (ranges, allocation, block "
+                               "hulls; the bitstream's upload queued on the copy engine), 5 x iso_extract "
+                               "(exact-size device meshes, count readbacks), release; volume i + 1 is loaded "
+                               "before volume i's surfaces are extracted, so its upload overlaps them (the "
+                               "first volume's upload is not overlapped and is inside the timed run)",
+                   "serial": {"value": n_ser / dt_ser, "ms_per_step": 1000 * dt_ser / e2e_steps,
+                              "what": "the same steps one volume at a time: load, five surfaces, release"}}
         vol.release()
         batch = None if args.no_batch else measure_batch64(bc, sg, torch, stream, flush, args.steps)
 

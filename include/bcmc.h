@@ -66,16 +66,22 @@ extern "C" {
 #define ISO_ERR_TIMEOUT 5      /* a device-side wait gave up (bounded spin) */
 #define ISO_ERR_CAPACITY 6     /* the caller's vertex buffer is too small */
 #define ISO_PENDING 7          /* a served request is not finished yet (not an error) */
-#define ISO_ERR_CORRUPT 8      /* the block ranges given at load are not ranges (NaN, or min > max) */
+#define ISO_ERR_CORRUPT 8      /* the block ranges given at load are not ranges (NaN, or min > max);
+                                  from iso_load_volume, or with ISO_ASYNC_UPLOAD from the calls on
+                                  the volume */
 
 /* iso_options.flags */
 #define ISO_INPUT_ON_DEVICE 1u /* compressed/block_min/block_max are device pointers */
 #define ISO_DEBUG 2u           /* keep per-stage debug copies (see iso_debug_get) */
-#define ISO_ASYNC_UPLOAD 8u    /* host inputs: return once the bitstream's copy is queued (on a
-                                  stream of the library's); the first extraction's range test and
-                                  cache update overlap the copy and its decode waits for it.  The
-                                  caller keeps `compressed` valid until the first call on the
-                                  volume returns (pinned memory makes the copy asynchronous) */
+#define ISO_ASYNC_UPLOAD 8u    /* host inputs: return once the load's work and the bitstream's copy
+                                  are queued (the copy on a stream of the library's, after the
+                                  ranges); the first extraction's range test and cache update
+                                  overlap the copy and its decode waits for it.  The caller keeps
+                                  `compressed` valid until the first call on the volume returns
+                                  (pinned memory makes the copies asynchronous).  Ranges that are
+                                  not ranges are then reported as ISO_ERR_CORRUPT by the first
+                                  call on the volume, and by every call after it, instead of by
+                                  iso_load_volume; iso_release still frees the volume */
 #define ISO_NO_GRAPH 4u        /* launch each extraction's kernels one by one instead of
                                   replaying the CUDA graphs captured once a volume has been extracted 8 times */
 

@@ -146,8 +146,19 @@ iso_launch_shape shape_of(const Plan &want, int device, bool single) {
                             run(want.mc_emit, lim.mc_emit), (uint32_t)tiles.emit_tile};
 }
 
+int check_load(iso_volume *v) {
+    if (v->check_pending) {
+        v->check_pending = false;
+        ISO_CK(cudaStreamSynchronize(v->stream));        // the hulls and the readback of their verdict
+        if (v->host_ctl->status & kStatusCorrupt) v->corrupt = true;
+    }
+    return v->corrupt ? ISO_ERR_CORRUPT : ISO_OK;
+}
+
 int finish_upload(iso_volume *v) {
-    if (!v || !v->upload_pending) return ISO_OK;
+    if (!v) return ISO_OK;
+    const int rc = check_load(v);
+    if (rc || !v->upload_pending) return rc;
     v->upload_pending = false;
     ISO_CK(cudaEventSynchronize(v->uploaded));
     return ISO_OK;
@@ -260,7 +271,7 @@ int free_volume(iso_volume *v) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaSetDevice(v->device);
-    if (v->uploaded) cudaEventSynchronize(v->uploaded);   // nothing is freed under a copy in flight
+    if (v->upload_stream) cudaStreamSynchronize(v->upload_stream);   // nothing is freed under a copy in flight
     DevState &s = v->s;
     void *ptrs[] = {v->bits, v->bmin, v->bmax, v->hull, v->hull8, v->tables, s.mactive, s.iactive, s.inew, s.icand,
                     s.islot, s.slast, s.sblock, s.lbuf[0], s.lbuf[1], s.newslot, s.slots, s.desc_cull, s.desc_cand,
@@ -400,7 +411,9 @@ int ensure_voff(iso_volume *v) {
 int run(iso_volume *v, float iso, void *out, unsigned long long cap_tris, Phase phase = Phase::kAll,
         uint32_t format = kVertexFloat4, uint32_t flags = 0, const Window *w = nullptr,
         const Indexed *ix = nullptr) {
-    int rc = ensure_debug_edges(v, cap_tris);
+    int rc = check_load(v);
+    if (rc) return rc;
+    rc = ensure_debug_edges(v, cap_tris);
     if (rc) return rc;
     if (ix && (rc = ensure_voff(v)) != ISO_OK) return rc;
     *v->host_params = Params{iso,
@@ -720,23 +733,11 @@ int iso_load_volume(iso_volume **out, const void *compressed, size_t compressed_
         TRYC(cudaMemcpyAsync(v->bmin, block_min, (size_t)g.nb * 4, kind, st));
         TRYC(cudaMemcpyAsync(v->bmax, block_max, (size_t)g.nb * 4, kind, st));
     }
-    // the bitstream after the ranges (which the hulls need first)
-    if ((o.flags & ISO_ASYNC_UPLOAD) && !on_device) {
-        // the bitstream on a stream of its own, after the allocations queued on `st`
-        cudaEvent_t allocated = nullptr;
-        TRYC(cudaStreamCreateWithFlags(&v->upload_stream, cudaStreamNonBlocking));
-        TRYC(cudaEventCreateWithFlags(&v->uploaded, cudaEventDisableTiming));
-        TRYC(cudaEventCreateWithFlags(&allocated, cudaEventDisableTiming));
-        const cudaError_t e1 = cudaEventRecord(allocated, st);
-        const cudaError_t e2 = e1 == cudaSuccess ? cudaStreamWaitEvent(v->upload_stream, allocated, 0) : e1;
-        cudaEventDestroy(allocated);
-        TRYC(e2);
-        TRYC(cudaMemcpyAsync(v->bits, compressed, words * 8, kind, v->upload_stream));
-        TRYC(cudaEventRecord(v->uploaded, v->upload_stream));
-        v->upload_pending = true;
-    } else {
-        TRYC(cudaMemcpyAsync(v->bits, compressed, words * 8, kind, st));
-    }
+    // the bitstream after the ranges (which the hulls need first); an
+    // asynchronous upload is queued last, once the load's own work is done,
+    // so that no copy of the load waits behind it on the copy engine
+    const bool async_bits = (o.flags & ISO_ASYNC_UPLOAD) && !on_device;
+    if (!async_bits) TRYC(cudaMemcpyAsync(v->bits, compressed, words * 8, kind, st));
 
     TRYC(cudaMemcpyAsync(v->tables, table_bytes, sizeof(table_bytes), cudaMemcpyHostToDevice, st));
     TRYC(cudaMemsetAsync(s.islot, 0xFF, (size_t)g.nb * 4, st));
@@ -765,10 +766,29 @@ int iso_load_volume(iso_volume **out, const void *compressed, size_t compressed_
     dfree_on(v->bmax, st);
     v->bmin = v->bmax = nullptr;
     TRYC(cudaMemcpyAsync(v->host_ctl, s.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
-    TRYC(cudaStreamSynchronize(st));
-    if (v->host_ctl->status & kStatusCorrupt) {   // ranges that are not ranges: nothing to cull with
-        free_volume(v);
-        return ISO_ERR_CORRUPT;
+    if (async_bits) {
+        // Nothing waits here: the range check's verdict is read by the first
+        // call on the volume (check_load), and the bitstream goes on a stream
+        // of its own after the load's work on `st` (so no copy of the load
+        // queues behind it); the first extraction's decode waits for it.
+        cudaEvent_t queued = nullptr;
+        TRYC(cudaStreamCreateWithFlags(&v->upload_stream, cudaStreamNonBlocking));
+        TRYC(cudaEventCreateWithFlags(&v->uploaded, cudaEventDisableTiming));
+        TRYC(cudaEventCreateWithFlags(&queued, cudaEventDisableTiming));
+        const cudaError_t e1 = cudaEventRecord(queued, st);
+        const cudaError_t e2 = e1 == cudaSuccess ? cudaStreamWaitEvent(v->upload_stream, queued, 0) : e1;
+        cudaEventDestroy(queued);
+        TRYC(e2);
+        TRYC(cudaMemcpyAsync(v->bits, compressed, words * 8, kind, v->upload_stream));
+        TRYC(cudaEventRecord(v->uploaded, v->upload_stream));
+        v->upload_pending = true;
+        v->check_pending = true;
+    } else {
+        TRYC(cudaStreamSynchronize(st));
+        if (v->host_ctl->status & kStatusCorrupt) {   // ranges that are not ranges: nothing to cull with
+            free_volume(v);
+            return ISO_ERR_CORRUPT;
+        }
     }
     // single-volume defaults from a sweep of every tile variant and CTA count
     // on the 512^3 benchmark: 4096-count scan tiles at one CTA per SM and

@@ -29,6 +29,10 @@ struct iso_volume {
     cudaStream_t upload_stream = nullptr;
     cudaEvent_t uploaded = nullptr;
     bool upload_pending = false;
+    // ISO_ASYNC_UPLOAD: the load's range check is read by the first call on
+    // the volume (check_pending until then); `corrupt` makes every call fail
+    bool check_pending = false;
+    bool corrupt = false;
     // one extraction: params copy, the stage kernels, count readback; one
     // graph per kind (0: triangle soup, 1: indexed mesh, 2: the soup up to
     // the scan, 3: the emission alone)
@@ -122,7 +126,12 @@ iso_launch_shape shape_of(const bcmc::Plan &want, int device, bool single);
 // or batch launches (cached per device)
 bcmc::Plan occupancy_limits_of(int device, const bcmc::Plan &tiles, bool single);
 
-// wait on the host for an asynchronous upload still in flight
+// the verdict of an asynchronous load's range check (waits for the load's
+// own work, not for the bitstream): ISO_ERR_CORRUPT for ranges that are not
+// ranges, from then on for every call
+int check_load(iso_volume *v);
+
+// check_load, then wait on the host for an asynchronous upload still in flight
 int finish_upload(iso_volume *v);
 
 // device address of the single-volume work counters (inside the control block)

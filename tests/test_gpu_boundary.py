@@ -150,3 +150,30 @@ def test_misaligned_outputs_are_refused():
         assert st.num_triangles > 0
     finally:
         vol.release()
+
+
+def test_async_load_reports_bad_ranges_on_first_call():
+    # ISO_ASYNC_UPLOAD: the load returns at once; the range check's verdict
+    # comes with the first call on the volume, and with every call after it
+    p = pkg()
+    dims, rate, bits, bmin, bmax = volume_data(dims=(20, 20, 20))
+    lo, hi = bmin.copy(), bmax.copy()
+    lo[5], hi[5] = hi[5] + 1.0, lo[5]
+    vol = p.Volume(bits, dims, rate, lo, hi, async_upload=True)
+    try:
+        for _ in range(2):
+            with pytest.raises(p.IsoError) as e:
+                vol.extract(0.0)
+            assert e.value.code == p.ISO_ERR_CORRUPT
+    finally:
+        vol.release()
+    ref = oracle.extract(bits, dims, rate, bmin, bmax, 0.0)
+    vol = p.Volume(bits, dims, rate, bmin, bmax, async_upload=True)     # the real ranges
+    try:
+        m = vol.extract(0.0)
+        assert m.num_triangles == ref["num_triangles"]
+        v = m.vertices.cpu().numpy().reshape(-1, 3, 4)
+        assert np.abs(v[:, :, :3] - ref["local_pos"]).max() < POS_TOL
+        m.release()
+    finally:
+        vol.release()
