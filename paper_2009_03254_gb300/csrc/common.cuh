@@ -202,11 +202,25 @@ __device__ __forceinline__ unsigned long long lookback_exclusive(unsigned long l
 
 // In-place transpose of a 32x32 bit matrix held in 32 words: afterwards
 // bit j of a[i] is what bit i of a[j] was.  Five rounds of swapping the
-// off-diagonal sub-blocks (16x16, 8x8, ..., 1x1).
+// off-diagonal sub-blocks (16x16, 8x8, ..., 1x1); the 16- and 8-bit rounds
+// move whole bytes, one byte permute per word.
 __device__ __forceinline__ void transpose32(uint32_t (&a)[32]) {
+#pragma unroll
+    for (int j = 0; j < 16; j++) {        // (a, b) -> (a.lo16 | b.lo16 << 16, a.hi16 | b.hi16 << 16)
+        const uint32_t x = a[j], y = a[j + 16];
+        a[j] = __byte_perm(x, y, 0x5410);
+        a[j + 16] = __byte_perm(x, y, 0x7632);
+    }
+#pragma unroll
+    for (int j = 0; j < 32; j++) {        // bytes (a0 b0 a2 b2), (a1 b1 a3 b3)
+        if (j & 8) continue;
+        const uint32_t x = a[j], y = a[j + 8];
+        a[j] = __byte_perm(x, y, 0x6240);
+        a[j + 8] = __byte_perm(x, y, 0x7351);
+    }
     const uint32_t masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
 #pragma unroll
-    for (int r = 0; r < 5; r++) {
+    for (int r = 2; r < 5; r++) {
         const int s = 16 >> r;
         const uint32_t m = masks[r];
 #pragma unroll

@@ -392,7 +392,7 @@ __global__ void __launch_bounds__(kThreads) lru_b_kernel(Launch L) {
 // cache update.
 
 template <int kDecodeThreads, bool kOne>
-__global__ void __launch_bounds__(kDecodeThreads) decode_new_kernel(Launch L) {
+__global__ void __launch_bounds__(kDecodeThreads, 768 / kDecodeThreads) decode_new_kernel(Launch L) {   // 24 warps/SM
     extern __shared__ uint64_t planes[];              // 32 * kDecodeThreads words (dynamic)
     __shared__ uint32_t pre[kMaxBatch + 1];
     const uint32_t total = launch_prefix<kOne>(
