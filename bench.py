@@ -24,6 +24,9 @@ Metric: triangles/s (whole step, all five surfaces), with voxels/s
   roofline the dominant stage's kernel: algorithmic bytes per launch over
            its CUDA-event duration, against the measured HBM copy peak
   cpu_baseline  the plain CPU oracle on a bounded window of the same field
+  parity   the library on that window against the oracle's surfaces:
+           triangle counts, order and block ids exact, and the largest
+           float32-vs-float64 position difference
   packed_vertices / indexed_mesh  the same steps writing the compact
            8-byte vertices / the within-block indexed mesh
   render   the isovalue-0 surface drawn at 1920x1080 (iso_render) as the
@@ -234,7 +237,9 @@ def cpu_sample_volume(window, origin):
     return oracle.encode_volume(f, RATE)
 
 
-def cpu_oracle_sample(window, origin, isos, volume=None):
+def cpu_oracle_sample(window, origin, isos, volume=None, check=None):
+    """The oracle timed on the sample; `check(iso, result)` (untimed) sees
+    each surface."""
     import oracle
     bits, bmin, bmax = volume if volume is not None else cpu_sample_volume(window, origin)
     tris, t = 0, 0.0
@@ -243,7 +248,36 @@ def cpu_oracle_sample(window, origin, isos, volume=None):
         r = oracle.extract(bits, window, RATE, bmin, bmax, iso)
         t += time.perf_counter() - t0
         tris += r["num_triangles"]
+        if check is not None:
+            check(iso, r)
     return tris, t
+
+
+def parity_checker(bc, window, volume):
+    """The library on the same encoded sample, compared surface by surface
+    with the oracle's: triangle counts, order and block ids exactly, and the
+    largest distance between the library's float32 positions and the
+    oracle's float64 interpolation of the same decoded samples."""
+    bits, bmin, bmax = volume
+    vol = bc.Volume(bits, window, RATE, bmin, bmax)
+    out = {"triangles_equal": True, "blocks_equal": True, "max_abs_position_error_vs_fp64": 0.0, "triangles": 0}
+
+    def check(iso, ref):
+        m = vol.extract(iso)
+        try:
+            same = m.num_triangles == ref["num_triangles"]
+            out["triangles_equal"] &= bool(same)
+            out["triangles"] += int(m.num_triangles)
+            if same and m.num_triangles:
+                v = m.vertices.cpu().numpy().reshape(-1, 3, 4)
+                err = float(np.abs(v[:, :, :3].astype(np.float64) - ref["local_pos"]).max())
+                out["max_abs_position_error_vs_fp64"] = max(out["max_abs_position_error_vs_fp64"], err)
+                out["blocks_equal"] &= bool(np.array_equal(v[:, :, 3].view(np.uint32),
+                                                           np.repeat(ref["tri_block"][:, None], 3, axis=1)))
+        finally:
+            m.release()
+
+    return vol, out, check
 
 
 def _oracle_slab(args):
@@ -809,7 +843,12 @@ def run_ours(args):
         dist.barrier()
     if not args.no_cpu_baseline and world == 1:
         sample = cpu_sample_volume(CPU_WINDOW, CPU_ORIGIN)
-        tris, dt = cpu_oracle_sample(CPU_WINDOW, CPU_ORIGIN, ISOS, volume=sample)
+        pvol, parity, check = parity_checker(bc, CPU_WINDOW, sample)
+        tris, dt = cpu_oracle_sample(CPU_WINDOW, CPU_ORIGIN, ISOS, volume=sample, check=check)
+        pvol.release()
+        line["parity"] = dict(parity, unit="voxel", sample=f"the CPU baseline's {CPU_WINDOW[0]}x{CPU_WINDOW[1]}x"
+                              f"{CPU_WINDOW[2]} window, 5 isovalues, through iso_extract",
+                              tolerance=1e-5)
         line["cpu_baseline"] = {
             "value": tris / dt, "unit": "triangles/s", "cores": 1, "kind": "oracle",
             "sample": f"{CPU_WINDOW[0]}x{CPU_WINDOW[1]}x{CPU_WINDOW[2]} window at {CPU_ORIGIN} of the same field, "
