@@ -585,3 +585,40 @@ def test_async_upload():
                 v.release()
     finally:
         sync.release()
+
+
+def test_async_loads_double_buffered():
+    # volumes streamed as the benchmark's end-to-end run does: volume i + 1 is
+    # loaded (its bitstream still copying) before volume i's surfaces, and
+    # three volumes of different sizes and rates are alive at once
+    import torch as t
+    p = pkg()
+    cases = [((44, 38, 31), 8, 21), ((29, 33, 40), 12, 22), ((37, 21, 14), 4, 23)]
+    data = []
+    for dims, rate, seed in cases:
+        f = make_field("noise", dims, seed)
+        bits, bmin, bmax = oracle.encode_volume(f, rate)
+        want = oracle.extract(bits, dims, rate, bmin, bmax, 0.0)
+        data.append((dims, rate, t.from_numpy(bits.view(np.int64)).pin_memory(), t.from_numpy(bmin).pin_memory(),
+                     t.from_numpy(bmax).pin_memory(), want))
+    vols = []
+    try:
+        nxt = p.Volume(data[0][2], data[0][0], data[0][1], data[0][3], data[0][4], async_upload=True)
+        for i, (dims, rate, _, _, _, want) in enumerate(data):
+            cur = nxt
+            vols.append(cur)
+            if i + 1 < len(data):
+                d = data[i + 1]
+                nxt = p.Volume(d[2], d[0], d[1], d[3], d[4], async_upload=True)
+            for iso in (0.0, -0.3):
+                m = cur.extract(iso)
+                if iso == 0.0:
+                    assert m.num_triangles == want["num_triangles"]
+                    v = m.vertices.cpu().numpy().reshape(-1, 3, 4)
+                    assert np.abs(v[:, :, :3].astype(np.float64) - want["local_pos"]).max() < POS_TOL
+                    assert np.array_equal(v[:, :, 3].view(np.uint32),
+                                          np.repeat(want["tri_block"][:, None], 3, axis=1))
+                m.release()
+    finally:
+        for v in vols:
+            v.release()
