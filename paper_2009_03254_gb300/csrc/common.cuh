@@ -105,10 +105,12 @@ struct Ctl {
     uint32_t n_occ;           // occupied blocks
     uint32_t status;          // Status bits
     uint32_t mc_tiles;        // look-back descriptors the triangle kernel used (to clear)
+    uint32_t lpar_next;       // the list buffer this update fills (lru_a sets it; the commit adopts it)
     uint32_t ctr[kNumLaunchCounters];   // work counters when the volume is extracted alone
     unsigned long long n_tri; // triangles of the surface
     unsigned long long n_vtx; // vertices of the indexed mesh (indexed extractions only)
 };
+static_assert(sizeof(Ctl) == 168, "the control block is read back every extraction: keep it at 168 bytes");
 
 // ---------------------------------------------------------------- memory-model helpers
 

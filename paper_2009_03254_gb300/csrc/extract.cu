@@ -269,6 +269,7 @@ __global__ void __launch_bounds__(kThreads) lru_a_kernel(Launch L) {
         const uint32_t epoch = c->epoch, u = c->u;
         if (item == 0) {                                // the plan
             if (threadIdx.x == 0) {
+                c->lpar_next = c->lpar ^ 1u;
                 if (c->status & kStatusTimeout) {
                     c->S_next = c->S;
                     c->u_next = u;
@@ -333,11 +334,13 @@ __global__ void __launch_bounds__(kThreads) lru_a_kernel(Launch L) {
     }
 }
 
+// lru_b's work: every slot stamped this epoch (hits and new assignments),
+// by index, appended after the list's surviving part.  Run by its own
+// kernel, or by the 256-thread decode kernel once its blocks are decoded
+// (the decode commits the update meanwhile: nothing here reads what the
+// commit changes).  Called by all threads of the block.
 template <bool kOne>
-__global__ void __launch_bounds__(kThreads) lru_b_kernel(Launch L) {
-    __shared__ TileScan<kRounds> ts;
-    __shared__ uint32_t pre[kMaxBatch + 1];
-    __shared__ uint32_t slot_x;
+__device__ __forceinline__ void lru_b_work(const Launch &L, TileScan<kRounds> &ts, uint32_t *pre, uint32_t *slot_x) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
     // after a cull timeout the volume's cache is emptied by the host: no tiles
@@ -348,14 +351,14 @@ __global__ void __launch_bounds__(kThreads) lru_b_kernel(Launch L) {
         },
         pre);
     while (true) {
-        const uint32_t x = next_item(&L.ctr[kLcLruB], &slot_x);
+        const uint32_t x = next_item(&L.ctr[kLcLruB], slot_x);
         if (x >= total) break;
         const uint32_t v = item_vol<kOne>(pre, L.n, x);
         const DevState &s = vol_of<kOne>(L, v).s;
         Ctl *c = s.ctl;
         const uint32_t tile = x - item_base<kOne>(pre, v);
         const uint32_t epoch = c->epoch, S2 = c->S_next, keep = c->keep_base;
-        uint32_t *Ln = s.lbuf[c->lpar ^ 1u];
+        uint32_t *Ln = s.lbuf[c->lpar_next];
         uint32_t bits[kRounds], last[kRounds];
 #pragma unroll
         for (int r = 0; r < kRounds; r++) {   // all loads first
@@ -385,16 +388,32 @@ __global__ void __launch_bounds__(kThreads) lru_b_kernel(Launch L) {
     }
 }
 
+template <bool kOne>
+__global__ void __launch_bounds__(kThreads) lru_b_kernel(Launch L) {
+    __shared__ TileScan<kRounds> ts;
+    __shared__ uint32_t pre[kMaxBatch + 1];
+    __shared__ uint32_t slot_x;
+    lru_b_work<kOne>(L, ts, pre, &slot_x);
+}
+
 // ================================================================ decode (Section 4.2.1)
 //
 // Chunks of kDecodeThreads new blocks, one block per thread.  Chunk 0 of
 // every volume (each volume has at least one) also commits the volume's
-// cache update.
+// cache update.  With 256-thread blocks the kernel then does lru_b's work
+// (the list for the next update, which nothing before then reads): its
+// memory latency hides behind the decoding and one launch and grid-wide
+// wait fewer run per extraction.
+
+template <int kDecodeThreads>
+constexpr bool decode_runs_lru_b() { return kDecodeThreads == kThreads; }
 
 template <int kDecodeThreads, bool kOne>
 __global__ void __launch_bounds__(kDecodeThreads, 768 / kDecodeThreads) decode_new_kernel(Launch L) {   // 24 warps/SM
     extern __shared__ uint64_t planes[];              // 32 * kDecodeThreads words (dynamic)
     __shared__ uint32_t pre[kMaxBatch + 1];
+    __shared__ TileScan<kRounds> ts;                  // lru_b's work
+    __shared__ uint32_t slot_x;
     const uint32_t total = launch_prefix<kOne>(
         L, [&](uint32_t v) { return max(1u, ceil_div(vol_of<kOne>(L, v).s.ctl->n_assign, kDecodeThreads)); },
         pre);
@@ -407,7 +426,7 @@ __global__ void __launch_bounds__(kDecodeThreads, 768 / kDecodeThreads) decode_n
         if (chunk == 0 && threadIdx.x == 0) {         // commit the cache update
             c->S = c->S_next;
             c->u = c->u_next;
-            c->lpar ^= 1u;
+            c->lpar = c->lpar_next;
         }
         const uint32_t r = chunk * kDecodeThreads + threadIdx.x;
         if (r >= c->n_assign) continue;
@@ -419,6 +438,10 @@ __global__ void __launch_bounds__(kDecodeThreads, 768 / kDecodeThreads) decode_n
         float4 *dst = reinterpret_cast<float4 *>(s.slots + (size_t)slot * 64);
 #pragma unroll
         for (int i = 0; i < 16; i++) dst[i] = make_float4(val[4 * i], val[4 * i + 1], val[4 * i + 2], val[4 * i + 3]);
+    }
+    if constexpr (decode_runs_lru_b<kDecodeThreads>()) {
+        __syncthreads();                              // `pre` is lru_b's from here
+        lru_b_work<kOne>(L, ts, pre, &slot_x);
     }
 }
 
@@ -571,7 +594,7 @@ constexpr size_t decode_smem(int threads) { return 32u * 8u * (size_t)threads; }
 template <bool kOne>
 void cache_update(const Launch &L, const Plan &pl, cudaStream_t st, cudaEvent_t *ev, cudaEvent_t bits_ready) {
     lru_a_kernel<kOne><<<pl.lru_a, kThreads, 0, st>>>(L);
-    lru_b_kernel<kOne><<<pl.lru_b, kThreads, 0, st>>>(L);
+    if (pl.decode_tile != kThreads) lru_b_kernel<kOne><<<pl.lru_b, kThreads, 0, st>>>(L);   // else the decode's
     if (ev) cudaEventRecord(ev[3], st);
     if (bits_ready) cudaStreamWaitEvent(st, bits_ready, 0);   // the bitstream may still be on its way
     if (pl.decode_tile == 64) decode_new_kernel<64, kOne><<<pl.decode, 64, decode_smem(64), st>>>(L);
