@@ -24,7 +24,8 @@
 //   A  slots of each block's 8 blocks of the +group (8 lanes per block)
 //   B  stage the samples in shared memory: 16 float4 rows of the block,
 //      its +x face, +y/+z rows, edges and corner (50 loads per block, 2
-//      per lane, issued together)
+//      per lane, issued two blocks at a time), unpadded: sample
+//      x + 5y + 25z
 //   C  classify: four ballots give the 125 below-iso bits; each cell's
 //      case is 8 bits picked from them; counts from the case table
 //
@@ -280,38 +281,44 @@ __device__ __forceinline__ void stage_and_classify(const DevState &s, const Geom
         }
     }
     __syncwarp();
-    // ---- B: stage samples (all loads first, then all stores)
-    float4 v[2 * kBPW];
+    // ---- B: stage samples, two blocks at a time (all their loads first,
+    // then all their stores)
 #pragma unroll
-    for (int q = 0; q < kBPW; q++)
+    for (int half = 0; half < 2; half++) {
+        float4 v[kBPW];
 #pragma unroll
-        for (int h = 0; h < 2; h++) {
-            const uint32_t job = h ? lc.job1 : lc.job0;
-            v[2 * q + h] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (q < nb_w && (job & 1u)) {
-                const int32_t sl = wt.nslot[q][(job >> 2) & 7u];
-                if (sl >= 0) {
-                    const float *p = s.slots + (size_t)sl * 64 + ((job >> 5) & 63u);
-                    if (job & 2u) v[2 * q + h] = __ldg(reinterpret_cast<const float4 *>(p));
-                    else v[2 * q + h].x = __ldg(p);
+        for (int qq = 0; qq < kBPW / 2; qq++)
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int q = 2 * half + qq;
+                const uint32_t job = h ? lc.job1 : lc.job0;
+                v[2 * qq + h] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (q < nb_w && (job & 1u)) {
+                    const int32_t sl = wt.nslot[q][(job >> 2) & 7u];
+                    if (sl >= 0) {
+                        const float *p = s.slots + (size_t)sl * 64 + ((job >> 5) & 63u);
+                        if (job & 2u) v[2 * qq + h] = __ldg(reinterpret_cast<const float4 *>(p));
+                        else v[2 * qq + h].x = __ldg(p);
+                    }
                 }
             }
-        }
 #pragma unroll
-    for (int q = 0; q < kBPW; q++)
+        for (int qq = 0; qq < kBPW / 2; qq++)
 #pragma unroll
-        for (int h = 0; h < 2; h++) {
-            const uint32_t job = h ? lc.job1 : lc.job0;
-            if (q < nb_w && (job & 1u)) {
-                float *d = &wt.halo[q][0] + (job >> 11);
-                d[0] = v[2 * q + h].x;
-                if (job & 2u) {
-                    d[1] = v[2 * q + h].y;
-                    d[2] = v[2 * q + h].z;
-                    d[3] = v[2 * q + h].w;
+            for (int h = 0; h < 2; h++) {
+                const int q = 2 * half + qq;
+                const uint32_t job = h ? lc.job1 : lc.job0;
+                if (q < nb_w && (job & 1u)) {
+                    float *d = &wt.halo[q][0] + (job >> 11);
+                    d[0] = v[2 * qq + h].x;
+                    if (job & 2u) {
+                        d[1] = v[2 * qq + h].y;
+                        d[2] = v[2 * qq + h].z;
+                        d[3] = v[2 * qq + h].w;
+                    }
                 }
             }
-        }
+    }
     __syncwarp();
     // ---- C: classify (or take the stored cases) and count
     n0p = 0;
@@ -409,7 +416,7 @@ __device__ __forceinline__ TileRef locate_tile(const Launch &L, const uint32_t *
 // ================================================================ count (Section 4.4)
 
 template <int kW, bool kOne, bool kIdx>
-__global__ void __launch_bounds__(32 * kW, 32 / kW) mc_count_kernel(Launch L) {   // 1024 threads per SM
+__global__ void __launch_bounds__(32 * kW, 40 / kW) mc_count_kernel(Launch L) {   // 1280 threads per SM
     extern __shared__ __align__(16) unsigned char smem_raw[];
     CountSmem<kW> &sm = *reinterpret_cast<CountSmem<kW> *>(smem_raw);
     __shared__ uint32_t pre[kMaxBatch + 1];
@@ -812,10 +819,10 @@ __device__ __forceinline__ void emit_body(const Launch &L) {
     }
 }
 
-// the triangle soup; registers bounded for 24 warps per SM (32 warps fit in
-// shared memory, but at 64 registers the kernel spills and runs slower)
+// the triangle soup; registers bounded for 32 warps per SM (the staging
+// holds two blocks' loads at a time, so 64 registers suffice)
 template <int kW, bool kDebug, bool kOne>
-__global__ void __launch_bounds__(32 * kW, 24 / kW) mc_emit_kernel(Launch L) {
+__global__ void __launch_bounds__(32 * kW, 32 / kW) mc_emit_kernel(Launch L) {
     emit_body<kW, kDebug, kOne, false>(L);
 }
 
