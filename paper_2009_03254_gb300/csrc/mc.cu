@@ -716,7 +716,9 @@ __device__ __forceinline__ void emit_body(const Launch &L) {
         __syncwarp();
         // one triangle per lane; its three vertices (or, indexed, its three
         // vertex indices) go through the warp's staging area so that each
-        // store instruction writes contiguous bytes
+        // store instruction writes contiguous bytes; vertices are stored evict-first
+        // (a surface is several times the L2, and the hulls, slot map and
+        // cached blocks the next extraction reads should stay there)
         for (uint32_t t0 = 0; t0 < wtot; t0 += 32) {
             const uint32_t tri = t0 + lane;
             if (tri < wtot) {
@@ -796,13 +798,13 @@ __device__ __forceinline__ void emit_body(const Launch &L) {
 #pragma unroll
                     for (int r = 0; r < 3; r++) {
                         const uint32_t f = lane + 32 * r;
-                        if (f < nv) out[v0 + f] = stage[f];
+                        if (f < nv) __stcs(&out[v0 + f], stage[f]);
                     }
                 } else {
 #pragma unroll
                     for (int r = 0; r < 3; r++) {
                         const uint32_t f = lane + 32 * r;
-                        if (f < nv && v0 + f < vcap) out[v0 + f] = stage[f];
+                        if (f < nv && v0 + f < vcap) __stcs(&out[v0 + f], stage[f]);
                     }
                 }
             } else {
@@ -811,7 +813,7 @@ __device__ __forceinline__ void emit_body(const Launch &L) {
 #pragma unroll
                 for (int r = 0; r < 3; r++) {
                     const uint32_t f = lane + 32 * r;
-                    if (f < nv && v0 + f < vcap) out2[v0 + f] = st2[f];
+                    if (f < nv && v0 + f < vcap) __stcs(&out2[v0 + f], st2[f]);
                 }
             }
             __syncwarp();
