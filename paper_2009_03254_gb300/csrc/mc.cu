@@ -357,7 +357,10 @@ __device__ __forceinline__ void stage_and_classify(const DevState &s, const Geom
 #pragma unroll
                 for (int h = 0; h < 2; h++) s.cases[(size_t)(base + q) * 64 + lane + 32 * h] = (uint8_t)cs[h];
             }
-            if (!kEmit && indexed) {      // uniform: count the cut edges, keep the words for emit
+            // uniform: count the cut edges, keep the words for emit; a block
+            // without triangles has none (a cut edge makes its cell cross),
+            // and nothing reads its words
+            if (!kEmit && indexed && __any_sync(0xffffffffu, (num_tri[cs[0]] | num_tri[cs[1]]) != 0u)) {
                 const uint32_t w = lane_cut_word(m, lim, win);
                 const uint32_t nv = __reduce_add_sync(0xffffffffu, __popc(w));
                 if (lane == q) nv_lane = nv;
