@@ -411,6 +411,8 @@ int ensure_voff(iso_volume *v) {
 int run(iso_volume *v, float iso, void *out, unsigned long long cap_tris, Phase phase = Phase::kAll,
         uint32_t format = kVertexFloat4, uint32_t flags = 0, const Window *w = nullptr,
         const Indexed *ix = nullptr) {
+    NvtxRange nvtx(phase == Phase::kCount ? "iso_extract count" : (phase == Phase::kEmit ? "iso_extract emit"
+                                                                                        : "iso_extract"));
     int rc = check_load(v);
     if (rc) return rc;
     rc = ensure_debug_edges(v, cap_tris);
@@ -630,6 +632,7 @@ int iso_mc_case_table(uint8_t *num_tri, uint8_t *tri_edges) {
 int iso_load_volume(iso_volume **out, const void *compressed, size_t compressed_bytes, uint32_t nx, uint32_t ny,
                     uint32_t nz, uint32_t rate_bits, const float *block_min, const float *block_max,
                     const iso_options *opt) {
+    NvtxRange nvtx("iso_load_volume");
     if (!out || !compressed || !block_min || !block_max) return ISO_ERR_INVALID_ARG;
     *out = nullptr;
     Geom g;

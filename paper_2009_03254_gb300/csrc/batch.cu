@@ -281,6 +281,7 @@ int iso_batch_create(iso_batch **out, iso_volume *const *volumes, uint32_t n, vo
 
 int iso_batch_extract(iso_batch *b, const float *isovalues, float *d_vertices, uint64_t capacity_triangles,
                       uint64_t *tri_offsets, iso_stats *stats, int *status) {
+    NvtxRange nvtx("iso_batch_extract");
     if (!b || !tri_offsets) return ISO_ERR_INVALID_ARG;
     DeviceGuard dg(b->device);
     int rc = set_inputs(b, isovalues, d_vertices, capacity_triangles);

@@ -298,6 +298,7 @@ extern "C" int iso_raycast(iso_volume *v, float isovalue, const iso_pinhole *cam
                            iso_raycast_stats *stats) {
     using namespace bcmc;
     using namespace bcmc_host;
+    NvtxRange nvtx("iso_raycast");
     if (!v || !cam || !d_hits || !std::isfinite(isovalue) || cam->width == 0 || cam->height == 0 ||
         cam->width > 32768 || cam->height > 32768 || misaligned(d_hits, 8) || misaligned(d_rgba, 4))
         return ISO_ERR_INVALID_ARG;

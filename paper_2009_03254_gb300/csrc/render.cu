@@ -318,6 +318,7 @@ extern "C" int iso_render(const void *d_vertices, int vertex_format, const uint3
                           iso_render_stats *stats, void *stream) {
     using namespace bcmc;
     using namespace bcmc_host;
+    NvtxRange nvtx("iso_render");
     if (!camera || !d_fragments || camera->width == 0 || camera->height == 0 || camera->width > 32768 ||
         camera->height > 32768 || nx == 0 || ny == 0 || nz == 0 ||
         (vertex_format != ISO_VERTEX_FLOAT4 && vertex_format != ISO_VERTEX_PACKED) ||

@@ -508,6 +508,7 @@ int iso_server_submit(iso_server *sv, float isovalue, uint64_t *ticket) {
 }
 
 int iso_server_step(iso_server *sv, uint32_t *completed) {
+    NvtxRange nvtx("iso_server_step");
     if (!sv) return ISO_ERR_INVALID_ARG;
     uint32_t n = 0;
     if (completed) *completed = 0;

@@ -5,6 +5,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "bcmc.h"
 #include "common.cuh"
@@ -56,6 +57,17 @@ struct iso_volume {
 };
 
 namespace bcmc_host {
+
+// An NVTX range over a library call or one of its phases, so that a
+// profiler can group and filter the kernels each one launches (e.g. ncu
+// --nvtx --nvtx-include "iso_extract emit/"); without a tool attached the
+// push and pop return at once.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 #define ISO_CK(call)                                                          \
     do {                                                                      \
