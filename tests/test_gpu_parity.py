@@ -256,6 +256,44 @@ def test_cache_matches_algorithm1(kind):
         vol.release()
 
 
+def test_capped_cache_matches_algorithm1():
+    # a budget of 1.25x the largest active set: the cache grows to its cap,
+    # then every update evicts among the inactive slots; each step must
+    # match the simulator of Algorithm 1 with the same cap
+    dims, rate = (64, 64, 64), 8                 # spherical shells: the active set moves through the volume
+    f = make_field("sphere", dims)
+    bits, bmin, bmax = oracle.encode_volume(f, rate)
+    d = oracle.decode_volume(bits, dims, rate)
+    nb = bits.shape[0]
+    nbd = oracle.block_dims(dims)
+    lo, hi = np.quantile(d, [0.05, 0.95])
+    isos = np.random.default_rng(33).uniform(lo, hi, 60).astype(np.float32)
+    acts = [oracle.active_blocks(bmin, bmax, nbd, float(x)) for x in isos]
+    cap = int(np.ceil(1.25 * max(int(a.sum()) for a in acts)))
+    assert cap < nb
+    frac = 0.02
+    vol = pkg().Volume(bits, dims, rate, bmin, bmax, debug=True, initial_cache_fraction=frac,
+                       cache_budget_bytes=256 * cap)
+    cache = oracle.LRUCache(nb, int(np.ceil(frac * nb)), cap)
+    evicted = 0
+    try:
+        for iso, act in zip(isos, acts):
+            before = cache.I_slot >= 0
+            mesh = vol.extract(float(iso))
+            I_new, _ = cache.update(act)
+            evicted += int((before & (cache.I_slot < 0)).sum())
+            assert np.array_equal(vol.debug("new_ids"), I_new.astype(np.uint32))
+            assert mesh.stats["n_slots"] == cache.num_slots <= cap
+            assert np.array_equal(vol.debug("slot_of_block"), cache.I_slot.astype(np.int32))
+            assert np.array_equal(vol.debug("block_of_slot"), cache.S_block.astype(np.int32))
+            assert np.array_equal(vol.debug("slot_last_use"), cache.last_use().astype(np.uint32))
+            mesh.release()
+        assert cache.num_slots == cap and evicted > 1000
+        check_surface(vol, bits, dims, rate, bmin, bmax, float(np.median(d)))
+    finally:
+        vol.release()
+
+
 def test_budget_exceeded_then_recovers():
     p = pkg()
     dims, rate = (40, 40, 40), 8
