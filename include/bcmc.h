@@ -66,6 +66,9 @@ extern "C" {
 #define ISO_ERR_TIMEOUT 5      /* a device-side wait gave up (bounded spin) */
 #define ISO_ERR_CAPACITY 6     /* the caller's vertex buffer is too small */
 #define ISO_PENDING 7          /* a served request is not finished yet (not an error) */
+#define ISO_ERR_BOUNDS 9       /* checked builds only (BCMC_CHECKED): a device index fell outside its
+                                  array; the access was skipped and the results are invalid (a
+                                  library defect, reported instead of a memory fault) */
 #define ISO_ERR_CORRUPT 8      /* the block ranges given at load are not ranges (NaN, or min > max);
                                   from iso_load_volume, or with ISO_ASYNC_UPLOAD from the calls on
                                   the volume */

@@ -14,7 +14,8 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_lib", "libbcmc.so")
+# BCMC_CHECKED=1 loads the checked build (device-side bounds checks, see build.py)
+LIB_PATH = os.path.join(HERE, "_lib_checked" if os.environ.get("BCMC_CHECKED") == "1" else "_lib", "libbcmc.so")
 
 ISO_OK = 0
 ISO_ERR_INVALID_ARG = 1
@@ -25,6 +26,7 @@ ISO_ERR_TIMEOUT = 5
 ISO_ERR_CAPACITY = 6
 ISO_PENDING = 7
 ISO_ERR_CORRUPT = 8
+ISO_ERR_BOUNDS = 9
 
 ISO_INPUT_ON_DEVICE = 1
 ISO_DEBUG = 2

@@ -220,6 +220,7 @@ Plan launch_plan(const Plan *want, int device, uint64_t total_blocks, uint64_t t
 // After a timeout the cache bookkeeping may be inconsistent: empty it so
 // the next extraction starts from a clean state.
 int status_to_error(iso_volume *v, uint32_t st) {
+    if (st & kStatusBounds) return ISO_ERR_BOUNDS;
     if (st & kStatusAnyTimeout) {
         launch_reset_cache(v->s, v->stream);
         cudaStreamSynchronize(v->stream);
@@ -608,6 +609,7 @@ int iso_set_allocator(iso_alloc_fn alloc, iso_free_fn free_fn, void *ctx) {
 const char *iso_error_string(int status) {
     switch (status) {
         case ISO_ERR_CORRUPT: return "block ranges are not ranges (NaN, or min > max)";
+        case ISO_ERR_BOUNDS: return "a device index failed its bounds check (checked build)";
         case ISO_OK: return "ok";
         case ISO_ERR_INVALID_ARG: return "invalid argument";
         case ISO_ERR_OOM: return "out of memory";

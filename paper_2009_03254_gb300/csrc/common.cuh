@@ -51,8 +51,23 @@ enum Status : uint32_t {
     kStatusTimeoutLru = 4u,   // cache-update look-back gave up
     kStatusTimeoutScan = 8u,  // triangle-offset look-back gave up
     kStatusCorrupt = 16u,     // a block range given at load is not a range (set by the hull kernel)
+    kStatusBounds = 32u,      // checked builds: an index failed its bounds check (the access was skipped)
 };
 constexpr uint32_t kStatusAnyTimeout = kStatusTimeout | kStatusTimeoutLru | kStatusTimeoutScan;
+
+// Checked builds (compiled with BCMC_CHECKED): an index is tested before
+// the access it guards; a failed test sets kStatusBounds in the volume's
+// status and the caller skips the access, so a defect surfaces as
+// ISO_ERR_BOUNDS rather than as a memory fault.  In normal builds the test
+// is compiled out (true).
+#ifdef BCMC_CHECKED
+__device__ __forceinline__ bool in_bounds(bool ok, uint32_t *status) {
+    if (!ok) atomicOr(status, kStatusBounds);
+    return ok;
+}
+#else
+__device__ __forceinline__ bool in_bounds(bool, uint32_t *) { return true; }
+#endif
 
 // dynamic work counters of one launch sequence (tiles handed out in order)
 enum LaunchCounter { kLcCull = 0, kLcLruA = 1, kLcLruB = 2, kLcScan = 3, kNumLaunchCounters = 4 };

@@ -208,10 +208,12 @@ __global__ void __launch_bounds__(kThreads) cull_kernel(Launch L) {
 // max(2S, S + n_new - n_avail) slots, capped; new slots count as never
 // used, i.e. they have the highest age.
 
-__device__ __forceinline__ void assign_slot(const DevState &s, uint32_t slot, uint32_t r, uint32_t epoch) {
+__device__ __forceinline__ void assign_slot(const DevState &s, uint32_t slot, uint32_t r, uint32_t epoch,
+                                            uint32_t nb) {
     const uint32_t b = s.inew[r];
+    if (!in_bounds(slot < s.ctl->cap && b < nb && r < s.list_cap, &s.ctl->status)) return;
     const int32_t old = s.sblock[slot];
-    if (old >= 0) s.islot[old] = -1;           // evict
+    if (old >= 0 && in_bounds((uint32_t)old < nb, &s.ctl->status)) s.islot[old] = -1;   // evict
     s.sblock[slot] = (int32_t)b;
     s.islot[b] = (int32_t)slot;
     s.slast[slot] = epoch;
@@ -266,7 +268,7 @@ __global__ void __launch_bounds__(kThreads) lru_a_kernel(Launch L) {
         const DevState &s = vol_of<kOne>(L, v).s;
         Ctl *c = s.ctl;
         const uint32_t item = x - item_base<kOne>(pre, v);
-        const uint32_t epoch = c->epoch, u = c->u;
+        const uint32_t epoch = c->epoch, u = c->u, nb = vol_of<kOne>(L, v).g.nb;
         if (item == 0) {                                // the plan
             if (threadIdx.x == 0) {
                 c->lpar_next = c->lpar ^ 1u;
@@ -323,13 +325,13 @@ __global__ void __launch_bounds__(kThreads) lru_a_kernel(Launch L) {
             for (int r = 0; r < kRounds; r++) {
                 if (!((bits[r] >> lane) & 1u)) continue;
                 const uint32_t rank = base + ts.cnt[r][warp] + __popc(bits[r] & lt);
-                if (rank < p.from_used) assign_slot(s, slot[r], p.from_unused + rank, epoch);
-                else Ln[rank - p.from_used] = slot[r];
+                if (rank < p.from_used) assign_slot(s, slot[r], p.from_unused + rank, epoch, nb);
+                else if (in_bounds(rank - p.from_used < c->cap, &c->status)) Ln[rank - p.from_used] = slot[r];
             }
             __syncthreads();
         } else {                                        // never-used slots go straight to new blocks
             const uint32_t r0 = (item - 1 - ntiles) * kAssignChunk, r1 = min(p.from_unused, r0 + kAssignChunk);
-            for (uint32_t r = r0 + threadIdx.x; r < r1; r += kThreads) assign_slot(s, u + r, r, epoch);
+            for (uint32_t r = r0 + threadIdx.x; r < r1; r += kThreads) assign_slot(s, u + r, r, epoch, nb);
         }
     }
 }
@@ -382,7 +384,8 @@ __device__ __forceinline__ void lru_b_work(const Launch &L, TileScan<kRounds> &t
         for (int r = 0; r < kRounds; r++) {
             if (!((bits[r] >> lane) & 1u)) continue;
             const uint32_t i = tile * kScanTile + r * kThreads + threadIdx.x;
-            Ln[base + ts.cnt[r][warp] + __popc(bits[r] & lt)] = i;
+            const uint32_t at = base + ts.cnt[r][warp] + __popc(bits[r] & lt);
+            if (in_bounds(at < c->cap, &c->status)) Ln[at] = i;
         }
         __syncthreads();
     }
@@ -433,6 +436,7 @@ __global__ void __launch_bounds__(kDecodeThreads, 768 / kDecodeThreads) decode_n
         const uint32_t rate = vol_of<kOne>(L, v).g.rate;
         const uint32_t b = s.inew[r];
         const uint32_t slot = s.newslot[r];
+        if (!in_bounds(b < vol_of<kOne>(L, v).g.nb && slot < c->cap, &c->status)) continue;
         float val[64];
         decode_block(s.bits + (size_t)b * rate, rate, val, planes + threadIdx.x, kDecodeThreads);
         float4 *dst = reinterpret_cast<float4 *>(s.slots + (size_t)slot * 64);

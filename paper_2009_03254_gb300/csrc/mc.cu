@@ -271,7 +271,7 @@ __device__ __forceinline__ void stage_and_classify(const DevState &s, const Geom
         const bool ex = bx + 1 < g.nbx, ey = by + 1 < g.nby, ez = bz + 1 < g.nbz;
         const bool exists = (!(bo & 1) || ex) && (!(bo & 2) || ey) && (!(bo & 4) || ez);
         const uint32_t nbid = b + ((bo & 1) ? 1u : 0u) + ((bo & 2) ? g.nbx : 0u) + ((bo & 4) ? slab : 0u);
-        wt.nslot[bq][bo] = exists ? s.islot[nbid] : -1;
+        wt.nslot[bq][bo] = exists && in_bounds(nbid < g.nb, &s.ctl->status) ? s.islot[nbid] : -1;
         if (bo == 0) {
             wt.bid[bq] = b;
             const uint32_t lx = min(4u, g.nx - 1 - min(g.nx - 1, 4 * bx));
@@ -295,7 +295,7 @@ __device__ __forceinline__ void stage_and_classify(const DevState &s, const Geom
                 v[2 * qq + h] = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (q < nb_w && (job & 1u)) {
                     const int32_t sl = wt.nslot[q][(job >> 2) & 7u];
-                    if (sl >= 0) {
+                    if (sl >= 0 && in_bounds((uint32_t)sl < s.ctl->cap, &s.ctl->status)) {
                         const float *p = s.slots + (size_t)sl * 64 + ((job >> 5) & 63u);
                         if (job & 2u) v[2 * qq + h] = __ldg(reinterpret_cast<const float4 *>(p));
                         else v[2 * qq + h].x = __ldg(p);
@@ -355,7 +355,9 @@ __device__ __forceinline__ void stage_and_classify(const DevState &s, const Geom
             }
             if (!kEmit && s.cases) {      // uniform: keep them for the emit pass
 #pragma unroll
-                for (int h = 0; h < 2; h++) s.cases[(size_t)(base + q) * 64 + lane + 32 * h] = (uint8_t)cs[h];
+                for (int h = 0; h < 2; h++)
+                    if (in_bounds(base + q < s.list_cap, &s.ctl->status))
+                        s.cases[(size_t)(base + q) * 64 + lane + 32 * h] = (uint8_t)cs[h];
             }
             // uniform: count the cut edges, keep the words for emit; a block
             // without triangles has none (a cut edge makes its cell cross),
@@ -364,7 +366,8 @@ __device__ __forceinline__ void stage_and_classify(const DevState &s, const Geom
                 const uint32_t w = lane_cut_word(m, lim, win);
                 const uint32_t nv = __reduce_add_sync(0xffffffffu, __popc(w));
                 if (lane == q) nv_lane = nv;
-                if (lane < 12) s.cutw[(size_t)(base + q) * 12 + lane] = w;
+                if (lane < 12 && in_bounds(base + q < s.list_cap, &s.ctl->status))
+                    s.cutw[(size_t)(base + q) * 12 + lane] = w;
             }
         }
 #pragma unroll
@@ -549,7 +552,7 @@ __global__ void __launch_bounds__(kThreads) mc_scan_kernel(Launch L) {
 #pragma unroll
             for (int k = 0; k < kPT; k++) {
                 if (i0 + k < n) s.offsets[i0 + k] = run;
-                if (v8[k] & 0xFFFFu) {
+                if ((v8[k] & 0xFFFFu) && in_bounds(orun < s.list_cap, &c->status)) {
                     s.voff[orun] = vrun;
                     s.iocc[orun++] = i0 + k;
                 }
@@ -560,7 +563,7 @@ __global__ void __launch_bounds__(kThreads) mc_scan_kernel(Launch L) {
 #pragma unroll
             for (int k = 0; k < kPT; k++) {
                 if (i0 + k < n) s.offsets[i0 + k] = run;
-                if (v8[k]) s.iocc[orun++] = i0 + k;
+                if (v8[k] && in_bounds(orun < s.list_cap, &c->status)) s.iocc[orun++] = i0 + k;
                 run += v8[k];
             }
         }

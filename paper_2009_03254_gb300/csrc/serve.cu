@@ -83,6 +83,7 @@ __global__ void __launch_bounds__(kThreads) serve_prep_kernel(ServeArgs a) {
     }
     if (tid < a.k) {
         Ctl *c = a.ctl[tid];
+        c->cap = s.ctl->cap;                            // the shared cache's slot capacity
         c->n_cand = 0;
         c->n_tri = 0;
         c->n_occ = 0;
@@ -389,8 +390,8 @@ int emit_next(iso_server *sv, uint32_t *completed) {
     ISO_CK(cudaGetLastError());
     ISO_CK(cudaStreamSynchronize(st));
     const Ctl c = *sv->h_ctl;
-    if (c.status & kStatusAnyTimeout) {
-        finish(sv, r, ISO_ERR_TIMEOUT, &c, nullptr);
+    if (c.status & (kStatusAnyTimeout | kStatusBounds)) {
+        finish(sv, r, (c.status & kStatusBounds) ? ISO_ERR_BOUNDS : ISO_ERR_TIMEOUT, &c, nullptr);
         sv->tick_next++;
         *completed += 1;
         return ISO_OK;
@@ -456,6 +457,8 @@ int iso_server_create(iso_server **out, iso_volume *v, const iso_server_options 
     for (uint32_t j = 0; j < sv->max_batch; j++) {
         Slot &s = sv->slots[j];
         TRY(dalloc_on(&s.ctl, 1, sv->device, sv->stream));
+        TRY(cudaMemsetAsync(s.ctl, 0, sizeof(Ctl), sv->stream) == cudaSuccess ? ISO_OK   // no field undefined
+                                                                              : ((void)cudaGetLastError(), ISO_ERR_CUDA));
         TRY(dalloc_on(&s.icand, cand, sv->device, sv->stream));
         TRY(dalloc_on(&s.counts, cand, sv->device, sv->stream));
         TRY(dalloc_on(&s.offsets, cand, sv->device, sv->stream));
