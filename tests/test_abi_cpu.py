@@ -41,8 +41,17 @@ def test_every_declared_symbol_is_exported(L):
 def test_error_strings(L):
     import paper_2009_03254_gb300 as pkg
     assert pkg.error_string(0) == "ok"
-    for code in range(1, 7):
-        assert pkg.error_string(code) not in ("ok", "unknown status")
+    codes = (pkg.ISO_ERR_INVALID_ARG, pkg.ISO_ERR_OOM, pkg.ISO_ERR_BUDGET, pkg.ISO_ERR_CUDA, pkg.ISO_ERR_TIMEOUT,
+             pkg.ISO_ERR_CAPACITY, pkg.ISO_PENDING, pkg.ISO_ERR_CORRUPT, pkg.ISO_ERR_BOUNDS)
+    texts = [pkg.error_string(code) for code in codes]
+    assert all(t not in ("ok", "unknown status") for t in texts)
+    assert len(set(texts)) == len(texts)                 # each code has its own message
+    assert pkg.error_string(99) == "unknown status"
+    # the binding's constants are the header's
+    header = open(os.path.join(ROOT, "include", "bcmc.h")).read()
+    for name in ("ISO_ERR_INVALID_ARG", "ISO_ERR_OOM", "ISO_ERR_BUDGET", "ISO_ERR_CUDA", "ISO_ERR_TIMEOUT",
+                 "ISO_ERR_CAPACITY", "ISO_PENDING", "ISO_ERR_CORRUPT", "ISO_ERR_BOUNDS"):
+        assert f"#define {name} {getattr(pkg, name)} " in header, name
 
 
 def test_library_table_equals_oracle_table(L):
