@@ -63,3 +63,15 @@ def test_library_table_equals_oracle_table(L):
     for cs in range(256):
         n = int(num[cs])
         assert np.array_equal(tri[cs, :3 * n], otri[cs, :3 * n]), cs
+
+
+def test_checked_build_compiles_and_exports_the_same_calls():
+    # the bounds-checked variant of the library (BCMC_CHECKED) keeps building
+    # and exports every call the header declares
+    import ctypes
+    from paper_2009_03254_gb300 import build
+    lib = build.build(checked=True)
+    assert os.path.exists(lib) and "_lib_checked" in lib
+    L = ctypes.CDLL(lib)
+    for name in declared_functions():
+        assert hasattr(L, name), name
