@@ -348,6 +348,18 @@ int iso_set_stream(iso_volume *v, void *stream);
  * extraction decodes all of its active blocks. */
 int iso_cache_reset(iso_volume *v);
 
+/* Test hook for the failure path of the device-side waits (the paper has no
+ * counterpart).  With what = ISO_TEST_WITHHOLD_PREFIX, every later
+ * extraction's range test (Section 4.1) runs with its first tile never
+ * publishing its prefix sums, so each later tile's bounded wait gives up
+ * after 1024 polls (about a millisecond); the extraction then returns
+ * ISO_ERR_TIMEOUT and, as after any timeout, empties the cache.  what = 0
+ * restores normal operation; the volume stays usable throughout.  It lets
+ * a test drive a wait to its limit without hanging or faulting the GPU.
+ * Any other value of `what` is ISO_ERR_INVALID_ARG. */
+#define ISO_TEST_WITHHOLD_PREFIX 1u
+int iso_set_test_fault(iso_volume *v, uint32_t what);
+
 /* Per-stage timing.  With profiling on, each extraction records CUDA
  * events on the volume's stream between its kernels; iso_stage_times then
  * returns the last extraction's durations in milliseconds, in this order:
@@ -394,27 +406,30 @@ int iso_decode_blocks(const uint64_t *d_bits, uint32_t rate_bits, const uint32_t
 
 /* Active-block selection without any allocation.  The paper has no
  * counterpart: this exists for callers that cannot allocate device memory
- * -- code running while its stream is captured into a CUDA graph, plug-ins
- * inside an application whose allocator already owns the device memory,
- * and latency-critical loops that must not meet an allocation's implicit
- * synchronisation.
+ * -- plug-ins inside an application whose allocator already owns the
+ * device memory, and latency-critical loops that must not meet an
+ * allocation's implicit synchronisation.
  * It performs the range test of the cull stage (a block is active when
  * lo < iso <= hi for the min/max of block_min/block_max over its 3x3x3
  * block neighbourhood) and writes the active block ids in ascending order,
  * like the ids iso_extract selects for the same ranges.
  *   d_bmin, d_bmax  device, nb floats each (ranges of the decoded samples)
  *   d_ids           device, room for `capacity` ids; ids past it are dropped
- *   d_count         device uint32: the number of active blocks (may exceed
- *                   capacity), or 0xFFFFFFFF if a device-side wait timed out
- * Its scratch is a fixed file-scope device array of about 256 KiB, held by
- * every GPU that loads the library until the process exits; volumes of
- * more than 2^26 blocks (2^32 samples) are refused with
- * ISO_ERR_INVALID_ARG.  The first call on a device looks the array's
- * address up with that device current: make that first call before any
- * stream capture.  All calls share the array and it keeps the previous
- * call's contents; each call clears what it needs, so calls that overlap
- * on the GPU (different streams at once) race and must be avoided.  The
- * work is queued on `stream`; the call does not block. */
+ *   d_count         device uint32, written after every id: the number of
+ *                   active blocks (may exceed capacity), 0xFFFFFFFF if a
+ *                   device-side wait timed out, or 0xFFFFFFFE if some
+ *                   block's range is not a range (NaN, or min > max; the
+ *                   ids are then unspecified)
+ * All four buffers must be 4-byte aligned (else ISO_ERR_INVALID_ARG); the
+ * call cannot check their lengths.  Its scratch is a fixed file-scope
+ * device array of about 256 KiB, held by every GPU that loads the library
+ * until the process exits; volumes of more than 2^26 blocks (2^32 samples)
+ * are refused with ISO_ERR_INVALID_ARG.  The first call on a device looks
+ * the array's address up with that device current: make that first call
+ * before any stream capture.  All calls share the array and it keeps the
+ * previous call's contents; each call clears what it needs, so calls that
+ * overlap on the GPU (different streams at once) race and must be avoided.
+ * The work is queued on `stream`; the call does not block. */
 int iso_active_blocks_static(const float *d_bmin, const float *d_bmax, uint32_t nx, uint32_t ny, uint32_t nz,
                              float isovalue, uint32_t *d_ids, uint64_t capacity, uint32_t *d_count, void *stream);
 

@@ -241,7 +241,12 @@ def quantized_vertices(field, iso, edge_ids, tri_block, dims):
     coordinate p in [0, 4] is round(p / 4 * 1023); because rounding decides
     an integer, the position is taken in float32 with one IEEE rounding per
     operation: t = (iso - v_lo) / (v_hi - v_lo), p = lower corner + t, and
-    q = the nearest integer (ties to even) to p * 255.75."""
+    q = the nearest integer (ties to even) to p * 255.75.  When
+    |v_hi - v_lo| is 2^125 or more (samples near +-FLT_MAX, where the float32
+    difference can overflow to infinity), both differences are taken of the
+    samples times 2^-4, which leaves the quotient's real value unchanged
+    (scaling samples that small differences is exact, and the tiny ones it
+    rounds are far below the difference)."""
     f = np.ascontiguousarray(field, np.float32)
     nx, ny, nz = dims
     e = np.asarray(edge_ids, np.uint64).reshape(-1)
@@ -251,8 +256,13 @@ def quantized_vertices(field, iso, edge_ids, tri_block, dims):
     vlo = f[z, y, x]
     vhi = f[z + (axis == 2), y + (axis == 1), x + (axis == 0)]
     iso32 = np.float32(iso)
-    with np.errstate(divide="ignore", invalid="ignore"):
-        t = (iso32 - vlo) / (vhi - vlo)                    # float32 operations
+    with np.errstate(divide="ignore", invalid="ignore", over="ignore"):
+        a, b = iso32 - vlo, vhi - vlo                      # float32 operations
+        big = ~(np.abs(b) < np.float32(2.0 ** 125))        # includes an overflow to infinity
+        s = np.float32(2.0 ** -4)
+        a = np.where(big, iso32 * s - vlo * s, a).astype(np.float32)
+        b = np.where(big, vhi * s - vlo * s, b).astype(np.float32)
+        t = a / b
     blk = np.repeat(np.asarray(tri_block, np.int64), 3)
     nbx, nby, _ = block_dims(dims)
     bx, by, bz = blk % nbx, (blk // nbx) % nby, blk // (nbx * nby)

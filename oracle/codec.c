@@ -250,6 +250,9 @@ done:;
     int64_t q[64];
     for (int p = 0; p < 64; p++) q[perm[p]] = orc_from_negabinary(u[p]);
     orc_inverse_lift(q);
+    /* the integer becomes a float32 first (round to nearest even), then is
+     * scaled by 2^(emax - P): exact while the result is normal, a second
+     * rounding when it is subnormal (as ZFP dequantises) */
     for (int i = 0; i < 64; i++)
         v[i] = ldexpf((float)(int32_t)q[i], emax - ORC_PRECISION);
 }

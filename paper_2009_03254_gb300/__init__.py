@@ -32,6 +32,7 @@ ISO_INPUT_ON_DEVICE = 1
 ISO_DEBUG = 2
 ISO_NO_GRAPH = 4
 ISO_ASYNC_UPLOAD = 8
+ISO_TEST_WITHHOLD_PREFIX = 1
 ISO_VERTEX_FLOAT4 = 0
 ISO_VERTEX_PACKED = 1
 
@@ -130,6 +131,7 @@ def lib():
             "iso_release": (None, [P]),
             "iso_set_stream": (i32, [P, P]),
             "iso_cache_reset": (i32, [P]),
+            "iso_set_test_fault": (i32, [P, u32]),
             "iso_error_string": (ctypes.c_char_p, [i32]),
             "iso_mc_case_table": (i32, [P, P]),
             "iso_encode_field": (i32, [P, u32, u32, u32, u32, P, P, P, P]),
@@ -414,6 +416,12 @@ class Volume:
     def cache_reset(self):
         _check(lib().iso_cache_reset(self._h), "iso_cache_reset")
 
+    def set_test_fault(self, what):
+        """Test hook (iso_set_test_fault): ISO_TEST_WITHHOLD_PREFIX makes every
+        later extraction's range-test wait run out and return ISO_ERR_TIMEOUT;
+        0 restores normal operation."""
+        _check(lib().iso_set_test_fault(self._h, what), "iso_set_test_fault")
+
     def set_stream(self, stream):
         _check(lib().iso_set_stream(self._h, stream), "iso_set_stream")
 
@@ -669,14 +677,6 @@ def render(vertices, num_triangles, dims, view_proj, light, width, height, indic
     return fragments, (rgba if rgba is not False else None), ({"drawn": st.drawn, "big": st.big} if stats else None)
 
 
-def unpack_vertices(packed):
-    """Block-local float positions (..., 3) of compact vertices (..., 2) uint32."""
-    import torch
-    codes = packed[..., 0].to(torch.int64) & 0xFFFFFFFF
-    q = torch.stack([(codes >> (10 * k)) & 1023 for k in range(3)], -1)
-    return q.to(torch.float32) * (4.0 / 1023.0)
-
-
 def encode_field(field, rate, stream=None, out=None):
     """Encode a CUDA float32 tensor of shape (nz, ny, nx) on the GPU.
     Returns (bits uint64-as-int64 tensor (nb, rate), bmin, bmax) on the same
@@ -701,24 +701,60 @@ def encode_field(field, rate, stream=None, out=None):
 
 def active_blocks_static(bmin, bmax, dims, iso, ids=None, count=None, stream=None):
     """Active block ids for `iso` from device ranges, through the entry point
-    that allocates nothing (its scratch is a fixed device array inside the
-    library).  For callers that cannot allocate device memory, `ids` (CUDA
-    int32 tensor with room for every block) and `count` (CUDA int32, one
-    element) may be passed in; when omitted they are made here by torch,
-    outside the library call.  Returns (ids, count) tensors; count holds the
-    number of active blocks."""
+    that allocates nothing (iso_active_blocks_static: its scratch is a fixed
+    device array inside the library).
+
+    bmin, bmax  CUDA float32 tensors, contiguous, one value per block (at least
+                nb = prod(block_dims(dims)) each), on the current device
+    ids         CUDA int32 tensor, contiguous: room for ids.numel() ids (ids past
+                that are dropped, while count still counts them)
+    count       CUDA int32 tensor of at least one element
+
+    When ids or count are omitted they are made here by torch, outside the
+    library call.  Returns (ids, count).  After the stream has run, count[0]
+    holds the number of active blocks (it may exceed ids.numel()), or -1
+    (0xFFFFFFFF) when a device-side wait timed out, or -2 (0xFFFFFFFE) when a
+    range is not a range (NaN, or min > max); ``static_count`` reads it and
+    raises IsoError for the two failures.  The buffers are checked here
+    because the C call cannot check lengths: a short or host buffer would be
+    read or written out of bounds on the device."""
     import torch
     nx, ny, nz = dims
     nb = int(np.prod(block_dims(dims)))
+    dev = torch.device("cuda", torch.cuda.current_device())
     if ids is None:
-        ids = torch.empty(max(nb, 1), dtype=torch.int32, device=bmin.device)
+        ids = torch.empty(max(nb, 1), dtype=torch.int32, device=dev)
     if count is None:
-        count = torch.empty(1, dtype=torch.int32, device=bmin.device)
+        count = torch.empty(1, dtype=torch.int32, device=dev)
+    for name, t, dtypes, need in (("bmin", bmin, (torch.float32,), nb), ("bmax", bmax, (torch.float32,), nb),
+                                  ("ids", ids, (torch.int32,), 0), ("count", count, (torch.int32,), 1)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.device != dev:
+            raise ValueError(f"{name} must be a CUDA tensor on the current device")
+        if not t.is_contiguous() or t.dtype not in dtypes:
+            raise ValueError(f"{name} must be contiguous with dtype {dtypes[0]}")
+        if t.numel() < need:
+            raise ValueError(f"{name} holds {t.numel()} elements, needs {need}")
     _check(lib().iso_active_blocks_static(_ptr(bmin), _ptr(bmax), nx, ny, nz, ctypes.c_float(iso), _ptr(ids),
                                           ids.numel(), _ptr(count),
                                           stream if stream is not None else _current_stream()),
            "iso_active_blocks_static")
     return ids, count
+
+
+STATIC_COUNT_TIMEOUT = 0xFFFFFFFF
+STATIC_COUNT_CORRUPT = 0xFFFFFFFE
+
+
+def static_count(count):
+    """The block count an active_blocks_static call wrote (waits for its
+    stream); IsoError(ISO_ERR_TIMEOUT) or IsoError(ISO_ERR_CORRUPT) for the
+    two failure codes."""
+    n = int(count[0].item()) & 0xFFFFFFFF
+    if n == STATIC_COUNT_TIMEOUT:
+        raise IsoError(ISO_ERR_TIMEOUT, "iso_active_blocks_static")
+    if n == STATIC_COUNT_CORRUPT:
+        raise IsoError(ISO_ERR_CORRUPT, "iso_active_blocks_static")
+    return n
 
 
 def decode_volume(bits, dims, rate, out=None, stream=None):

@@ -421,7 +421,8 @@ int run(iso_volume *v, float iso, void *out, unsigned long long cap_tris, Phase 
     if (ix && (rc = ensure_voff(v)) != ISO_OK) return rc;
     *v->host_params = Params{iso,
                              format,
-                             flags | (w ? (uint32_t)kParamWindow : 0u) | (ix ? (uint32_t)kParamIndexed : 0u),
+                             flags | v->test_flags | (w ? (uint32_t)kParamWindow : 0u) |
+                                 (ix ? (uint32_t)kParamIndexed : 0u),
                              w ? w->lo : 0u,
                              w ? w->cand_hi : 0u,
                              w ? w->act_hi : 0u,
@@ -969,6 +970,12 @@ int iso_set_profiling(iso_volume *v, int on) {
 int iso_stage_times(iso_volume *v, float *ms, int n) {
     if (!v || !ms || n < ISO_NUM_STAGES) return ISO_ERR_INVALID_ARG;
     for (int k = 0; k < ISO_NUM_STAGES; k++) ms[k] = v->profiling ? v->stage_ms[k] : 0.0f;
+    return ISO_OK;
+}
+
+int iso_set_test_fault(iso_volume *v, uint32_t what) {
+    if (!v || (what & ~ISO_TEST_WITHHOLD_PREFIX)) return ISO_ERR_INVALID_ARG;
+    v->test_flags = (what & ISO_TEST_WITHHOLD_PREFIX) ? (uint32_t)kParamTestWithhold : 0u;
     return ISO_OK;
 }
 

@@ -85,6 +85,8 @@ enum ParamFlags : uint32_t {
                                   // only those in [win_lo, win_cand_hi) candidates
     kParamIndexed = 4u,           // indexed mesh: one vertex per cut edge of each block's window,
                                   // triangles as three uint32 vertex indices
+    kParamTestWithhold = 8u,      // test hook: the range test's first tile never publishes its prefix,
+                                  // and the other tiles wait kTestSpinLimit polls before giving up
 };
 
 struct Params {
@@ -154,6 +156,7 @@ constexpr unsigned long long kFlagAgg = 1ull << 62;
 constexpr unsigned long long kFlagPrefix = 2ull << 62;
 constexpr unsigned long long kValueMask = (1ull << 62) - 1;
 constexpr int kSpinLimit = 1 << 23;   // with at most 128 ns between polls: about a second
+constexpr int kTestSpinLimit = 1 << 10;   // the test hook's shorter wait (kParamTestWithhold)
 
 // Called by all 32 lanes of one warp.  Returns the exclusive prefix of
 // `tile` (same value in every lane) and publishes the inclusive one.  Each
@@ -164,7 +167,8 @@ constexpr int kLookbackPerLane = 4;
 
 __device__ __forceinline__ unsigned long long lookback_exclusive(unsigned long long *desc, uint32_t tile,
                                                                   unsigned long long aggregate,
-                                                                  uint32_t *status, uint32_t timeout_bit) {
+                                                                  uint32_t *status, uint32_t timeout_bit,
+                                                                  int spin_limit = kSpinLimit) {
     const int lane = threadIdx.x & 31;
     if (tile == 0) {
         if (lane == 0) st_relaxed(desc, kFlagPrefix | aggregate);
@@ -196,8 +200,14 @@ __device__ __forceinline__ unsigned long long lookback_exclusive(unsigned long l
         const unsigned pref = __ballot_sync(0xffffffffu, has_prefix && ready);
         const unsigned need = pref ? ((pref & (0u - pref)) << 1) - 1u : 0xffffffffu;   // lanes up to the first prefix
         if ((rdy & need) != need) {
-            if (++spins > kSpinLimit) {
-                if (lane == 0) atomicOr(status, timeout_bit);
+            if (++spins > spin_limit) {
+                // the status bit becomes visible before the (partial) prefix
+                // published below, so a reader that sees the prefix and then
+                // reads the status sees the bit too
+                if (lane == 0) {
+                    atomicOr(status, timeout_bit);
+                    __threadfence();
+                }
                 break;
             }
             __nanosleep(sleep_ns);

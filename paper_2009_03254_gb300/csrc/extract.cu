@@ -136,10 +136,16 @@ __device__ __forceinline__ void cull_tile(const DevState &s, const Geom &g, uint
         }
     }
     __syncthreads();
+    // test hook: tile 0 keeps its prefixes to itself, so the other tiles'
+    // waits run out (after a short limit) and the extraction reports a timeout
+    const bool withhold = (prm.flags & kParamTestWithhold) != 0;
+    const bool publish = !(withhold && tile == 0);
+    const int spin_limit = withhold ? kTestSpinLimit : kSpinLimit;
     if (warp == 0) {                       // active and new counts
         const uint32_t tot = scan_tile_counts(sm.ts);
         const unsigned long long agg = ((unsigned long long)(tot >> 16) << 31) | (tot & 0xFFFFu);
-        const unsigned long long excl = lookback_exclusive(s.desc_cull, tile, agg, &s.ctl->status, kStatusTimeout);
+        const unsigned long long excl =
+            publish ? lookback_exclusive(s.desc_cull, tile, agg, &s.ctl->status, kStatusTimeout, spin_limit) : 0ull;
         if (lane == 0) {
             sm.ts.excl = excl;
             if (tile == ntiles - 1) {
@@ -150,7 +156,8 @@ __device__ __forceinline__ void cull_tile(const DevState &s, const Geom &g, uint
         }
     } else if (warp == 1) {                // candidate count, in parallel
         const uint32_t totc = scan_tile_counts(sm.tc);
-        const unsigned long long exclc = lookback_exclusive(s.desc_cand, tile, totc, &s.ctl->status, kStatusTimeout);
+        const unsigned long long exclc =
+            publish ? lookback_exclusive(s.desc_cand, tile, totc, &s.ctl->status, kStatusTimeout, spin_limit) : 0ull;
         if (lane == 0) {
             sm.tc.excl = exclc;
             if (tile == ntiles - 1) s.ctl->n_cand = (uint32_t)(exclc + totc);

@@ -380,6 +380,28 @@ __device__ __forceinline__ void stage_and_classify(const DevState &s, const Geom
     }
 }
 
+// t = (iso - v_lo) / (v_hi - v_lo) on a cut edge (iso lies between the two
+// samples, so |iso - v_lo| <= |v_hi - v_lo|), each difference rounded once.
+// The quotient goes through the reciprocal (kExact false: within 2 ulp for
+// divisors in [2^-126, 2^126]) or is correctly rounded (kExact true).  A
+// difference outside [2^-100, 2^125) -- samples near +-FLT_MAX, whose
+// difference can even overflow, or samples so close that it is tiny -- is
+// formed from the samples scaled by 2^-4 or 2^64: the scaling is exact up to
+// underflow of samples far below the difference, the quotient stays the same
+// real number, and the divisor lands inside the reciprocal's range.
+template <bool kExact>
+__device__ __forceinline__ float edge_fraction(float iso, float vlo, float vhi) {
+    float a = __fsub_rn(iso, vlo), b = __fsub_rn(vhi, vlo);
+    const float mb = fabsf(b);
+    if (!(mb >= 0x1p-100f && mb < 0x1p125f)) {
+        const float sc = mb >= 0x1p125f ? 0x1p-4f : 0x1p64f;
+        const float slo = __fmul_rn(vlo, sc);
+        a = __fsub_rn(__fmul_rn(iso, sc), slo);
+        b = __fsub_rn(__fmul_rn(vhi, sc), slo);
+    }
+    return kExact ? __fdiv_rn(a, b) : __fdividef(a, b);
+}
+
 __device__ __forceinline__ uint32_t warp_sum(uint32_t x) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
@@ -684,8 +706,8 @@ __device__ __forceinline__ void emit_body(const Launch &L) {
                 const float vlo = hp[0], vhi = hp[ax == 0 ? 1 : (ax == 1 ? 5 : 25)];
                 float px = (float)sx, py = (float)sy, pz = (float)sz;
                 float tt;
-                if (!packed) tt = __fdividef(__fsub_rn(iso, vlo), __fsub_rn(vhi, vlo));
-                else tt = __fdiv_rn(__fsub_rn(iso, vlo), __fsub_rn(vhi, vlo));
+                if (!packed) tt = edge_fraction<false>(iso, vlo, vhi);
+                else tt = edge_fraction<true>(iso, vlo, vhi);
                 if (ax == 0) px = __fadd_rn(px, tt);
                 else if (ax == 1) py = __fadd_rn(py, tt);
                 else pz = __fadd_rn(pz, tt);
@@ -752,9 +774,9 @@ __device__ __forceinline__ void emit_body(const Launch &L) {
                         const float vlo = hb[info & 0xFFu], vhi = hb[(info >> 8) & 0xFFu];
                         float4 p = make_float4(__fadd_rn(fx, ef.x), __fadd_rn(fy, ef.y), __fadd_rn(fz, ef.z), wbits);
                         if (!packed) {
-                            // t = (iso - v_lo) / (v_hi - v_lo) through the reciprocal: within
-                            // 2 ulp of the correctly rounded quotient (positions within 1e-6)
-                            const float tt = __fdividef(__fsub_rn(iso, vlo), __fsub_rn(vhi, vlo));
+                            // t through the reciprocal: within 2 ulp of the correctly
+                            // rounded quotient (positions within 1e-6)
+                            const float tt = edge_fraction<false>(iso, vlo, vhi);
                             if (a == 0) p.x = __fadd_rn(p.x, tt);
                             else if (a == 1) p.y = __fadd_rn(p.y, tt);
                             else p.z = __fadd_rn(p.z, tt);
@@ -763,7 +785,7 @@ __device__ __forceinline__ void emit_body(const Launch &L) {
                             // the 10-bit code round(p / 4 * 1023) decides an integer, so every
                             // step is one IEEE float32 operation (the division correctly
                             // rounded), as the oracle computes it
-                            const float tt = __fdiv_rn(__fsub_rn(iso, vlo), __fsub_rn(vhi, vlo));
+                            const float tt = edge_fraction<true>(iso, vlo, vhi);
                             if (a == 0) p.x = __fadd_rn(p.x, tt);
                             else if (a == 1) p.y = __fadd_rn(p.y, tt);
                             else p.z = __fadd_rn(p.z, tt);

@@ -1,15 +1,15 @@
 // Active-block selection that allocates no memory at all.
 //
-// Some callers cannot call cudaMalloc: code that runs while its stream is
-// being captured into a CUDA graph (an allocation there is not a stream
-// operation and can stall or break the capture), plug-ins living inside an
-// application whose own allocator has already reserved the device memory,
-// and latency-critical loops where an allocation's implicit device
-// synchronisation would stall other work.  For them this file provides
-// iso_active_blocks_static: the range test and ordered compaction of the
-// cull stage, taking the per-block ranges straight from the caller, with
-// its only scratch (look-back descriptors, a tile counter and a status
-// word) in a fixed file-scope device array.
+// Some callers cannot call cudaMalloc: plug-ins living inside an
+// application whose own allocator has already reserved the device memory
+// (a second allocator in the same process would fail, or fragment what the
+// host application manages), and latency-critical loops where an
+// allocation's implicit device synchronisation would stall other work.
+// For them this file provides iso_active_blocks_static: the range test and
+// ordered compaction of the cull stage, taking the per-block ranges
+// straight from the caller, with its only scratch (look-back descriptors, a
+// tile counter, a status word and the total) in a fixed file-scope device
+// array.
 //
 // The array is part of the loaded module, so every GPU that loads the
 // library holds it (about 256 KiB) until the process exits.  All calls
@@ -29,7 +29,10 @@ constexpr uint32_t kTileBlocks = 2048;                 // 256 threads x 8 rounds
 constexpr uint32_t kMaxTiles = 32768;
 constexpr uint64_t kMaxBlocks = (uint64_t)kTileBlocks * kMaxTiles;   // 2^26 blocks = 2^32 samples
 constexpr uint32_t kCounterSlot = kMaxTiles;           // tile counter
-constexpr uint32_t kStatusSlot = kMaxTiles + 1;        // bounded-wait status
+constexpr uint32_t kStatusSlot = kMaxTiles + 1;        // bounded-wait timeout and corrupt-range bits
+constexpr uint32_t kTotalSlot = kMaxTiles + 2;         // active blocks, written by the last tile
+constexpr uint32_t kCountTimeout = 0xFFFFFFFFu;        // *count after a look-back wait gave up
+constexpr uint32_t kCountCorrupt = 0xFFFFFFFEu;        // *count when a range is NaN or has min > max
 
 static __device__ __align__(256) unsigned long long g_scratch[kMaxTiles + 4];
 
@@ -65,14 +68,24 @@ __global__ void clear_scratch_kernel(unsigned long long *scratch, uint32_t ntile
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         scratch[kCounterSlot] = 0;
         scratch[kStatusSlot] = 0;
+        scratch[kTotalSlot] = 0;
     }
+}
+
+// After every tile has finished (stream order): the count, or the code of
+// the failure any tile recorded.
+__global__ void finish_count_kernel(const unsigned long long *scratch, uint32_t *count) {
+    const uint32_t status = (uint32_t)scratch[kStatusSlot];
+    *count = (status & bcmc::kStatusTimeout) ? kCountTimeout
+             : (status & bcmc::kStatusCorrupt) ? kCountCorrupt
+                                                : (uint32_t)scratch[kTotalSlot];
 }
 
 // The active test of the cull kernel, with the 3x3x3 min/max taken on the
 // fly from the caller's ranges instead of a precomputed hull.
 __global__ void __launch_bounds__(256) select_static_kernel(const float *__restrict__ bmin,
                                                             const float *__restrict__ bmax, bcmc::Geom g, float iso,
-                                                            uint32_t *ids, uint64_t capacity, uint32_t *count,
+                                                            uint32_t *ids, uint64_t capacity,
                                                             unsigned long long *scratch, uint32_t ntiles) {
     __shared__ uint32_t cnt[8][8];
     __shared__ unsigned long long s_excl;
@@ -95,6 +108,10 @@ __global__ void __launch_bounds__(256) select_static_kernel(const float *__restr
             if (b < g.nb) {
                 const int bx = (int)(b % g.nbx), by = (int)((b / g.nbx) % g.nby), bz = (int)(b / slab);
                 float lo = bmin[b], hi = bmax[b];
+                // a range that is not a range (NaN, or min > max) is reported,
+                // as iso_load_volume reports it; the neighbours' ranges are
+                // each checked by their own thread
+                if (!(lo <= hi)) atomicOr(status, bcmc::kStatusCorrupt);
                 for (int dz = -1; dz <= 1; dz++)
                     for (int dy = -1; dy <= 1; dy++)
                         for (int dx = -1; dx <= 1; dx++) {
@@ -126,7 +143,7 @@ __global__ void __launch_bounds__(256) select_static_kernel(const float *__restr
             const unsigned long long excl = bcmc::lookback_exclusive(scratch, tile, tot, status, bcmc::kStatusTimeout);
             if (lane == 0) {
                 s_excl = excl;
-                if (tile == ntiles - 1) *count = (*status != 0) ? 0xFFFFFFFFu : (uint32_t)(excl + tot);
+                if (tile == ntiles - 1) scratch[kTotalSlot] = excl + tot;
             }
         }
         __syncthreads();
@@ -148,6 +165,9 @@ extern "C" int iso_active_blocks_static(const float *d_bmin, const float *d_bmax
     if (!d_bmin || !d_bmax || !d_count || (capacity && !d_ids) || !std::isfinite(isovalue) || nx == 0 || ny == 0 ||
         nz == 0)
         return ISO_ERR_INVALID_ARG;
+    const auto misaligned = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 3u) != 0; };
+    if (misaligned(d_bmin) || misaligned(d_bmax) || misaligned(d_count) || (capacity && misaligned(d_ids)))
+        return ISO_ERR_INVALID_ARG;
     const uint64_t nbx = (nx + 3ull) / 4, nby = (ny + 3ull) / 4, nbz = (nz + 3ull) / 4;
     const uint64_t nb = nbx * nby * nbz;
     if (nb > kMaxBlocks) return ISO_ERR_INVALID_ARG;   // more blocks than the fixed scratch covers
@@ -165,7 +185,8 @@ extern "C" int iso_active_blocks_static(const float *d_bmin, const float *d_bmax
         return ISO_ERR_CUDA;
     }
     const uint32_t grid = ntiles < (uint32_t)(4 * sms) ? ntiles : (uint32_t)(4 * sms);
-    select_static_kernel<<<grid, 256, 0, st>>>(d_bmin, d_bmax, g, isovalue, d_ids, capacity, d_count, scratch, ntiles);
+    select_static_kernel<<<grid, 256, 0, st>>>(d_bmin, d_bmax, g, isovalue, d_ids, capacity, scratch, ntiles);
+    finish_count_kernel<<<1, 1, 0, st>>>(scratch, d_count);
     if (cudaGetLastError() != cudaSuccess) return ISO_ERR_CUDA;
     return ISO_OK;
 }

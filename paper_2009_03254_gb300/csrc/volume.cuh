@@ -40,6 +40,7 @@ struct iso_volume {
     cudaGraph_t graph[4] = {};
     cudaGraphExec_t gexec[4] = {};
     bool use_graph = true;
+    uint32_t test_flags = 0;          // ParamFlags of the test hook (iso_set_test_fault)
     uint64_t extractions = 0;         // full extractions run so far (graphs are captured after kGraphAfter)
     // owned device allocations
     uint64_t *bits = nullptr;

@@ -49,6 +49,9 @@ def make_field(kind, dims, seed):
         return rng.standard_normal((nz, ny, nx)).astype(np.float32)
     if kind == "checker":
         return rng.integers(0, 2, (nz, ny, nx)).astype(np.float32)
+    if kind == "wide":      # samples up to +-3e38: differences beyond 2^125 and past FLT_MAX, and tiny ones
+        vals = np.array([3e38, -3e38, 1e38, -1e38, 2e37, -5e36, 0.5, -0.25, 1e-39, -2e-39, 0.0], np.float32)
+        return rng.choice(vals, size=(nz, ny, nx)).astype(np.float32)
     raise ValueError(kind)
 
 
@@ -93,6 +96,7 @@ def check_packed(vol, ref, ix, iso, dims):
 @pytest.mark.parametrize("kind,dims,rate", [
     ("sphere", (24, 20, 18), 16), ("noise", (33, 29, 21), 8), ("noise", (41, 17, 9), 8),
     ("noise", (17, 12, 13), 12), ("random", (19, 14, 11), 8), ("checker", (11, 9, 7), 8),
+    ("wide", (19, 14, 11), 16),
 ])
 def test_indexed_matches_oracle(kind, dims, rate):
     t = torch()
@@ -104,6 +108,8 @@ def test_indexed_matches_oracle(kind, dims, rate):
         isos = [float(np.median(d)), float(np.quantile(d, 0.3)), float(d.max()) + 1.0]
         if kind == "sphere":
             isos = [0.0, 1.5] + isos
+        if kind == "wide":
+            isos = [0.0, 1e37, -1.5e38] + isos
         for iso in isos:
             ref, ix = oracle_indexed(bits, dims, rate, bmin, bmax, iso)
             gv, gi = check_float(vol, ref, ix, iso)

@@ -51,6 +51,9 @@ def make_field(kind, dims, seed=0):
         return f
     if kind == "checker":
         return rng.integers(0, 2, (nz, ny, nx)).astype(np.float32)
+    if kind == "wide":      # samples up to +-3e38: differences beyond 2^125 and past FLT_MAX, and tiny ones
+        vals = np.array([3e38, -3e38, 1e38, -1e38, 2e37, -5e36, 0.5, -0.25, 1e-39, -2e-39, 0.0], np.float32)
+        return rng.choice(vals, size=(nz, ny, nx)).astype(np.float32)
     raise ValueError(kind)
 
 
@@ -182,7 +185,8 @@ def check_surface(vol, bits, dims, rate, bmin, bmax, iso, mesh=None):
 EXTRACT_CASES = [("sphere", (64, 64, 64), 16), ("noise", (37, 21, 14), 8), ("random", (13, 9, 6), 4),
                  ("noise", (33, 20, 17), 12), ("random", (5, 5, 5), 3), ("random", (2, 3, 5), 8),
                  ("noise", (4, 4, 4), 2), ("random", (3, 2, 2), 16), ("sphere", (33, 2, 9), 8),
-                 ("random", (1, 1, 1), 8), ("special", (18, 10, 9), 16), ("checker", (11, 9, 7), 8)]
+                 ("random", (1, 1, 1), 8), ("special", (18, 10, 9), 16), ("checker", (11, 9, 7), 8),
+                 ("wide", (18, 10, 9), 16), ("wide", (13, 9, 6), 32)]
 
 
 @pytest.mark.parametrize("kind,dims,rate", EXTRACT_CASES)
@@ -191,6 +195,9 @@ def test_extract_matches_oracle(kind, dims, rate):
     bits, bmin, bmax = oracle.encode_volume(f, rate)
     d = oracle.decode_volume(bits, dims, rate)
     isos = [0.0, float(np.median(d)), float(np.quantile(d, 0.2)), float(d.min()), float(d.max()), 1.0, -1e9, 1e9]
+    if kind == "wide":
+        assert np.isfinite(d).all()
+        isos += [1e37, -1.5e38, 2e38]
     vol = pkg().Volume(bits, dims, rate, bmin, bmax, debug=True)
     try:
         for iso in isos:
@@ -439,7 +446,7 @@ def test_graph_and_plain_launches_agree():
 
 @pytest.mark.parametrize("kind,dims,rate", [("sphere", (64, 64, 64), 16), ("noise", (37, 21, 14), 8),
                                             ("random", (13, 9, 6), 4), ("special", (18, 10, 9), 16),
-                                            ("checker", (11, 9, 7), 8)])
+                                            ("checker", (11, 9, 7), 8), ("wide", (18, 10, 9), 16)])
 def test_packed_vertices_match_oracle(kind, dims, rate):
     t = torch()
     f = make_field(kind, dims, 7)
@@ -447,7 +454,10 @@ def test_packed_vertices_match_oracle(kind, dims, rate):
     d = oracle.decode_volume(bits, dims, rate)
     vol = pkg().Volume(bits, dims, rate, bmin, bmax)
     try:
-        for iso in (0.0, float(np.median(d)), float(np.quantile(d, 0.3)), 1.0):
+        isos = [0.0, float(np.median(d)), float(np.quantile(d, 0.3)), 1.0]
+        if kind == "wide":
+            isos += [1e37, -1.5e38, 2e38]
+        for iso in isos:
             ref = oracle.extract(bits, dims, rate, bmin, bmax, iso)
             T = ref["num_triangles"]
             out = t.zeros((max(T, 1), 3, 2), dtype=t.int32, device="cuda")

@@ -177,3 +177,54 @@ def test_corrupt_stream_stays_in_bounds():
             w = rng.integers(0, 1 << 63, rate, dtype=np.uint64) * np.uint64(2) + np.uint64(1)
             d = oracle.decode_block(w, rate)
             assert d.shape == (64,) and not np.isnan(d).any()
+
+
+def _dc_only_stream(q, emax, rate):
+    """A block whose only non-zero coefficient is the DC, q, written bit by bit
+    from the format: the non-zero flag, emax + 127 in 8 bits, then for each
+    plane k = 31..0 (n = coefficients reached so far): n verbatim bits, then
+    group tests.  Before the DC is reached a plane is one test bit (its DC
+    bit); the plane that reaches it is 1 (test), 1 (the DC's one), 0 (no
+    later ones); every later plane is the DC's bit and a 0 test."""
+    bits = [1] + [(emax + 127) >> b & 1 for b in range(8)]
+    u = ((q + 0xAAAAAAAA) & 0xFFFFFFFF) ^ 0xAAAAAAAA      # negabinary digits of q
+    reached = False
+    for k in range(31, -1, -1):
+        d = u >> k & 1
+        if reached:
+            bits += [d, 0]
+        elif d:
+            bits += [1, 1, 0]
+            reached = True
+        else:
+            bits += [0]
+    assert len(bits) <= 64 * rate
+    w = np.zeros(rate, np.uint64)
+    for i, b in enumerate(bits):
+        w[i >> 6] |= np.uint64(b) << np.uint64(i & 63)
+    return w
+
+
+@pytest.mark.parametrize("q, emax, want", [
+    # 2^26 + 9 becomes 2^26 + 8 as a float32 (spacing 8 there); times
+    # 2^(-126-27) that is 2^22 + 0.5 subnormal steps of 2^-149, a tie, which
+    # goes to the even 2^22: exactly 2^-127.  (Rounding the exact product
+    # q * 2^-153 once would give 2^22 + 1 steps: the format's decoder rounds
+    # the integer first, then scales, as ZFP's dequantisation does.)
+    (2 ** 26 + 9, -126, 2.0 ** -127),
+    (-(2 ** 26 + 9), -126, -(2.0 ** -127)),
+    # 2^26 + 17 -> 2^26 + 16 as a float32, times 2^-153: 2^22 + 1 steps exactly
+    (2 ** 26 + 17, -126, (2 ** 22 + 1) * 2.0 ** -149),
+    # emax -110 and -100: the scaled value stays normal, the product is exact
+    (2 ** 26 + 9, -110, (2 ** 26 + 8) * 2.0 ** -137),
+    (2 ** 26 + 9, -100, (2 ** 26 + 8) * 2.0 ** -127),
+    (12345, -120, 12345 * 2.0 ** -147),
+])
+def test_hand_built_stream_tiny_exponents(q, emax, want):
+    # every sample of a DC-only block is the DC (the inverse transform of
+    # (q, 0, ..., 0) is constant), so the decoder's last step, the int32 ->
+    # float32 conversion and the scaling by 2^(emax - 27), is seen directly
+    w = _dc_only_stream(q, emax, 2)
+    d = oracle.decode_block(w, 2)
+    assert np.array_equal(d, np.full(64, want, np.float32)), (d[0], want)
+    assert np.float32(want) == want                          # the hand value is a float32
