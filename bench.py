@@ -64,7 +64,7 @@ CPU_ORIGIN = (0, 0, 192)
 REF_WINDOW = (128, 128, 64)       # per-step sample of the reference arm
 L2_FLUSH_BYTES = 512 << 20
 CTL_BYTES = 168                   # control block (struct Ctl): iso_extract reads it back after the scan and after the emission
-KERNELS_PER_SURFACE = 7           # prep, cull, lru_a, decode (with the list append), count, scan, emit
+KERNELS_PER_SURFACE = 8           # prep, cull, lru_a, lru_b (list append), decode, count, scan, emit
 KERNELS_PER_RESET = 2
 KERNELS = ("cull", "cache_update", "decode", "count", "scan", "emit")
 KERNEL_OF = {"cull": ("cull_kernel", "extract.cu"), "cache_update": ("lru_a_kernel+lru_b_kernel", "extract.cu"),

@@ -31,7 +31,7 @@ std::mutex g_pool_mutex;
 cudaMemPool_t g_pool[kMaxPoolDevices] = {};
 struct OccEntry {
     int device;
-    int key[6];                   // tile sizes and single/batch
+    int key[7];                   // tile sizes, single/batch, largest rate
     Plan limits;
 };
 std::vector<OccEntry> g_occ;      // occupancy limits per (device, tile variants)
@@ -134,10 +134,10 @@ int shape_to_want(const iso_launch_shape *shape, Plan *out) {
     return ISO_OK;
 }
 
-iso_launch_shape shape_of(const Plan &want, int device, bool single) {
+iso_launch_shape shape_of(const Plan &want, int device, bool single, uint32_t max_rate) {
     // CTAs per SM that run: the requested number clamped to the occupancy limit
     const Plan tiles = default_tiles(&want);
-    const Plan lim = occupancy_limits_of(device, tiles, single);
+    const Plan lim = occupancy_limits_of(device, tiles, single, max_rate);
     auto run = [](int w, int mx) { return (uint32_t)(w > 0 ? std::min(w, mx) : mx); };
     return iso_launch_shape{run(want.cull, lim.cull), (uint32_t)tiles.cull_tile, run(want.lru_a, lim.lru_a),
                             run(want.decode, lim.decode), (uint32_t)tiles.decode_tile,
@@ -174,21 +174,22 @@ Plan default_tiles(const Plan *want) {
     return t;
 }
 
-Plan occupancy_limits_of(int device, const Plan &tiles, bool single) {
-    const int key[6] = {tiles.cull_tile, tiles.decode_tile, tiles.count_tile, tiles.scan_tile, tiles.emit_tile,
-                        single ? 1 : 0};
+Plan occupancy_limits_of(int device, const Plan &tiles, bool single, uint32_t max_rate) {
+    const int key[7] = {tiles.cull_tile, tiles.decode_tile, tiles.count_tile, tiles.scan_tile, tiles.emit_tile,
+                        single ? 1 : 0, (int)max_rate};
     std::lock_guard<std::mutex> lock(g_pool_mutex);
     for (const OccEntry &e : g_occ)
-        if (e.device == device && std::equal(key, key + 6, e.key)) return e.limits;
-    OccEntry e{device, {key[0], key[1], key[2], key[3], key[4], key[5]}, occupancy_limits(tiles, single)};
+        if (e.device == device && std::equal(key, key + 7, e.key)) return e.limits;
+    OccEntry e{device, {key[0], key[1], key[2], key[3], key[4], key[5], key[6]},
+               occupancy_limits(tiles, single, max_rate)};
     g_occ.push_back(e);
     return e.limits;
 }
 
 Plan launch_plan(const Plan *want, int device, uint64_t total_blocks, uint64_t total_slots, uint32_t n_vols,
-                 bool single) {
+                 bool single, uint32_t max_rate) {
     const Plan tiles = default_tiles(want);
-    const Plan lim = occupancy_limits_of(device, tiles, single);
+    const Plan lim = occupancy_limits_of(device, tiles, single, max_rate);
     Plan use = lim;
     if (want) {
         int *dst = &use.prep;
@@ -580,7 +581,7 @@ int iso_set_shape(iso_volume *v, const iso_launch_shape *shape) {
     DeviceGuard dg(v->device);
     CK(cudaStreamSynchronize(v->stream));
     v->want = w;
-    v->plan = launch_plan(&v->want, v->device, v->g.nb, v->cap, 1, true);
+    v->plan = launch_plan(&v->want, v->device, v->g.nb, v->cap, 1, true, v->g.rate);
     for (int k = 0; k < 4; k++) {            // the captured passes hold the old launch shape
         if (v->gexec[k]) cudaGraphExecDestroy(v->gexec[k]);
         if (v->graph[k]) cudaGraphDestroy(v->graph[k]);
@@ -594,7 +595,7 @@ int iso_set_shape(iso_volume *v, const iso_launch_shape *shape) {
 int iso_get_shape(const iso_volume *v, iso_launch_shape *shape) {
     if (!v || !shape) return ISO_ERR_INVALID_ARG;
     DeviceGuard dg(v->device);
-    *shape = shape_of(v->want, v->device, true);
+    *shape = shape_of(v->want, v->device, true, v->g.rate);
     return ISO_OK;
 }
 
@@ -797,13 +798,14 @@ int iso_load_volume(iso_volume **out, const void *compressed, size_t compressed_
         }
     }
     // single-volume defaults from a sweep of every tile variant and CTA count
-    // on the 512^3 benchmark: 4096-count scan tiles at one CTA per SM and
-    // 256-block decode CTAs (the other kernels' defaults were already best)
+    // on the 512^3 benchmark: 4096-count scan tiles at one CTA per SM (the
+    // other kernels' defaults were already best; 128-block decode CTAs, with
+    // the list append in its own kernel, beat 256-block CTAs that append
+    // after decoding: 91.0 + 8.5 against 103.8 us per surface)
     v->want = Plan{};
     v->want.scan_tile = 4096;
     v->want.mc_scan = 1;
-    v->want.decode_tile = 256;
-    v->plan = launch_plan(&v->want, v->device, g.nb, v->cap, 1, true);
+    v->plan = launch_plan(&v->want, v->device, g.nb, v->cap, 1, true, g.rate);
     TRYC(cudaGetLastError());
     *out = v;
     return ISO_OK;

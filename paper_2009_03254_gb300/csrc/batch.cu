@@ -45,6 +45,7 @@ struct iso_batch {
     Plan want{};                          // launch shape: CTAs per SM and tiles, 0 = default
     Plan plan{};                          // what runs
     uint64_t total_blocks = 0, total_slots = 0;
+    uint32_t max_rate = 1;                // the largest rate among the volumes
     cudaStream_t capture_stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -54,7 +55,7 @@ struct iso_batch {
 
 namespace {
 
-Launch launch_of(const iso_batch *b) { return Launch{b->d_entries, b->n, b->d_ctr, VolEntry{}}; }
+Launch launch_of(const iso_batch *b) { return Launch{b->d_entries, b->n, b->d_ctr, VolEntry{}, b->max_rate}; }
 
 // per tuned kernel: its CTA field and tile field in a Plan (tile: null
 // for the cache update, which has one tile size), and the tile variants
@@ -86,7 +87,7 @@ void drop_graph(iso_batch *b) {
 
 void apply_shape(iso_batch *b, const Plan &want) {
     b->want = want;
-    b->plan = launch_plan(&b->want, b->device, b->total_blocks, b->total_slots, b->n, false);
+    b->plan = launch_plan(&b->want, b->device, b->total_blocks, b->total_slots, b->n, false, b->max_rate);
     drop_graph(b);
 }
 
@@ -257,6 +258,7 @@ int iso_batch_create(iso_batch **out, iso_volume *const *volumes, uint32_t n, vo
         entries[i] = VolEntry{v->s, v->g, v->n_cull_desc, v->n_lru_desc};
         b->total_blocks += v->g.nb;
         b->total_slots += v->cap;
+        b->max_rate = std::max(b->max_rate, v->g.rate);
     }
     // the volumes' own streams may still hold work (a cache reset, a free)
     for (iso_volume *v : vols)
@@ -306,7 +308,7 @@ int iso_batch_set_shape(iso_batch *b, const iso_launch_shape *shape) {
 
 int iso_batch_get_shape(const iso_batch *b, iso_launch_shape *shape) {
     if (!b || !shape) return ISO_ERR_INVALID_ARG;
-    *shape = shape_of(b->want, b->device, false);
+    *shape = shape_of(b->want, b->device, false, b->max_rate);
     return ISO_OK;
 }
 
@@ -319,7 +321,7 @@ int iso_batch_tune(iso_batch *b, const float *isovalues, float *d_vertices, uint
     const Plan keep = b->want;
     // one cold run with `want`: per-kernel times (ms) and the total
     auto timed = [&](const Plan &want, float *kernel_ms, float *total_ms) -> int {
-        b->plan = launch_plan(&want, b->device, b->total_blocks, b->total_slots, b->n, false);
+        b->plan = launch_plan(&want, b->device, b->total_blocks, b->total_slots, b->n, false, b->max_rate);
         int r = reset_caches(b);
         if (r) return r;
         r = run_batch(b, true);
@@ -345,7 +347,7 @@ int iso_batch_tune(iso_batch *b, const float *isovalues, float *d_vertices, uint
         Plan tiles{};
         for (int k = 0; k < kKernels; k++)
             if (tile_field(tiles, k)) *tile_field(tiles, k) = kTileVariants[k][std::min(i, kNumVariants[k] - 1)];
-        Plan lim = occupancy_limits_of(b->device, default_tiles(&tiles), false);
+        Plan lim = occupancy_limits_of(b->device, default_tiles(&tiles), false, b->max_rate);
         int cmax = 1;
         for (int k = 0; k < kKernels; k++) cmax = std::max(cmax, *ctas_field(lim, k));
         for (int c = 1; c <= cmax; c++) {

@@ -17,8 +17,9 @@
 //              block's bits are used up; unread bits count as zero.
 // Samples are q = trunc(v * 2^(27 - emax)) integers, decorrelated by a
 // two-level integer S-transform along x, then y, then z; the decoder runs
-// the exact inverse in 32-bit wrap-around arithmetic and returns
-// (float)q * 2^(emax - 27), correctly rounded.
+// the exact inverse in 32-bit wrap-around arithmetic and returns the
+// float32 of q (rounded to nearest even) times 2^(emax - 27): exact while
+// the result is normal, rounded once more when it is subnormal.
 #pragma once
 
 #include "common.cuh"
@@ -35,35 +36,71 @@ __device__ __forceinline__ uint64_t load_word(const uint64_t *p) {
     else return *p;
 }
 
-// A 128-bit window over a block's stream: bits [base, base+128) of the
-// block in two words, refilled one word at a time, so each word of the
-// block is loaded once.
+// ---------------------------------------------------------------- staging
+//
+// A warp decodes up to 32 blocks at a time, one per lane (Section 4.2.1
+// decodes one block per thread).  The blocks' words are first copied into
+// a per-warp staging area of shared memory by coalesced loads: in each
+// round consecutive lanes load consecutive 8-byte words, block after block,
+// so a warp instruction reads 256 contiguous bytes of every block it
+// touches.  Each lane then parses its own block from shared memory.
+//
+// A staged block takes 2R + 1 32-bit words (its 2R words, then a zero pad
+// word; the odd stride spreads the lanes' reads over the banks), and the
+// area ends with two more words, so a window may read up to two words past
+// the block's last one (bits past the budget are never used).
+
+__host__ __device__ constexpr uint32_t stage_words(uint32_t rate) { return 32u * (2u * rate + 1u) + 2u; }
+
+// Copy block `id` of each lane that has one (`have`) into the warp's
+// staging area `stage` (stage_words(rate) words).  Called by all 32 lanes.
 template <bool kReadOnly>
-struct BitWindow {
-    const uint64_t *w;
-    uint32_t nwords, next, base;
-    uint64_t w0, w1;
-    __device__ __forceinline__ void init(const uint64_t *words, uint32_t n) {
-        w = words;
-        nwords = n;
-        w0 = load_word<kReadOnly>(w);
-        w1 = n > 1 ? load_word<kReadOnly>(w + 1) : 0ull;
-        next = 2;
-        base = 0;
+__device__ __forceinline__ void stage_blocks(const uint64_t *__restrict__ bits, uint32_t rate, uint32_t id, bool have,
+                                             uint32_t *stage) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t stride = 2u * rate + 1u;
+    const uint32_t magic = (65535u + rate) / rate;          // ceil(2^16 / rate): j / rate = (j * magic) >> 16, j < 1024
+    const uint32_t have_mask = __ballot_sync(0xffffffffu, have);
+    for (uint32_t j = lane; j < 32u * rate; j += 32u) {      // the same number of rounds in every lane
+        const uint32_t q = (j * magic) >> 16, w = j - q * rate;
+        const uint32_t bq = __shfl_sync(0xffffffffu, id, (int)q);
+        uint64_t v = 0ull;
+        if ((have_mask >> q) & 1u) v = load_word<kReadOnly>(bits + (size_t)bq * rate + w);
+        stage[q * stride + 2u * w] = (uint32_t)v;
+        stage[q * stride + 2u * w + 1u] = (uint32_t)(v >> 32);
     }
-    // 64 bits starting at pos (pos - base < 64 is kept by advance)
-    __device__ __forceinline__ uint64_t peek(uint32_t pos) const {
-        const uint32_t sh = pos - base;
-        return sh ? (w0 >> sh) | (w1 << (64 - sh)) : w0;
+    stage[lane * stride + 2u * rate] = 0u;
+    if (lane < 2) stage[32u * stride + lane] = 0u;
+    __syncwarp();
+}
+
+// Shared-memory accesses by 32-bit shared-window address (the decoder's
+// loops address the staging area and plane columns this way, so every
+// access is a plain shared-memory load or store).
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint32_t lds_u32(uint32_t a) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ void sts_u64(uint32_t a, uint32_t lo, uint32_t hi) {
+    asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(a), "r"(lo), "r"(hi));
+}
+
+// Bit windows over a staged block at shared address `w` (32-bit words).
+struct StagedBits {
+    uint32_t w;
+    // 32 bits starting at bit pos
+    __device__ __forceinline__ uint32_t win32(uint32_t pos) const {
+        const uint32_t a = w + ((pos >> 5) << 2);
+        return __funnelshift_r(lds_u32(a), lds_u32(a + 4), pos & 31u);
     }
-    // call after pos moved forward by at most 64 bits
-    __device__ __forceinline__ void advance(uint32_t pos) {
-        if (pos - base >= 64) {
-            w0 = w1;
-            w1 = next < nwords ? load_word<kReadOnly>(w + next) : 0ull;
-            next++;
-            base += 64;
-        }
+    // 64 bits starting at bit pos, as two halves
+    __device__ __forceinline__ void win64(uint32_t pos, uint32_t &lo, uint32_t &hi) const {
+        const uint32_t a = w + ((pos >> 5) << 2), sh = pos & 31u;
+        const uint32_t x = lds_u32(a), y = lds_u32(a + 4), z = lds_u32(a + 8);
+        lo = __funnelshift_r(x, y, sh);
+        hi = __funnelshift_r(y, z, sh);
     }
 };
 
@@ -79,6 +116,18 @@ __device__ __forceinline__ void inv_lift4(int32_t &p0, int32_t &p1, int32_t &p2,
     p0 = a; p1 = b; p2 = c; p3 = d;
 }
 
+// the same on two's-complement words held as uint32 (wrap-around arithmetic)
+__device__ __forceinline__ void inv_lift4u(uint32_t &p0, uint32_t &p1, uint32_t &p2, uint32_t &p3) {
+    const uint32_t ll = p0, hh = p1, h0 = p2, h1 = p3;
+    const uint32_t l1 = ll - (uint32_t)((int32_t)hh >> 1);
+    const uint32_t l0 = hh + l1;
+    const uint32_t b = l0 - (uint32_t)((int32_t)h0 >> 1);
+    const uint32_t a = h0 + b;
+    const uint32_t d = l1 - (uint32_t)((int32_t)h1 >> 1);
+    const uint32_t c = h1 + d;
+    p0 = a; p1 = b; p2 = c; p3 = d;
+}
+
 // forward step (a, b, c, d) -> (ll, hh, h0, h1); inputs |x| < 2^29
 __device__ __forceinline__ void fwd_lift4(int32_t &p0, int32_t &p1, int32_t &p2, int32_t &p3) {
     const int32_t a = p0, b = p1, c = p2, d = p3;
@@ -88,124 +137,248 @@ __device__ __forceinline__ void fwd_lift4(int32_t &p0, int32_t &p1, int32_t &p2,
     p0 = ll; p1 = hh; p2 = h0; p3 = h1;
 }
 
-// (float)q * 2^e with one rounding; e in [-154, 101]
-__device__ __forceinline__ float scale_pow2(int32_t q, int e) {
-    const float f = __int2float_rn(q);
-    if (e >= -126) return __fmul_rn(f, __int_as_float((e + 127) << 23));   // exact unless it overflows
-    // f * 2^(e+64) is exact and normal; the final multiply rounds once
-    return __fmul_rn(__fmul_rn(f, __int_as_float((e + 64 + 127) << 23)), __int_as_float((127 - 64) << 23));
+// out[l] = float32(q[l]) * 2^e, e in [-154, 101]: the conversion rounds to
+// nearest even; the scaling is exact while the result is normal and rounds
+// once more when it is subnormal.  One branch per block (uniform in a warp
+// unless some of its blocks have tiny exponents).
+__device__ __forceinline__ void scale_block(const uint32_t (&q)[64], int e, float (&out)[64]) {
+    if (e >= -126) {
+        const float sc = __int_as_float((e + 127) << 23);
+#pragma unroll
+        for (int l = 0; l < 64; l++) out[l] = __fmul_rn(__int2float_rn((int32_t)q[l]), sc);
+    } else {
+        // f * 2^(e+64) is exact and normal; the final multiply rounds once
+        const float sc = __int_as_float((e + 64 + 127) << 23), down = __int_as_float((127 - 64) << 23);
+#pragma unroll
+        for (int l = 0; l < 64; l++) out[l] = __fmul_rn(__fmul_rn(__int2float_rn((int32_t)q[l]), sc), down);
+    }
 }
 
-// Decode one block of `rate` words into out[64] (block-local order).
-// `planes` is this thread's column of a shared-memory scratch area:
-// plane k lives at planes[k * stride].
-template <bool kReadOnly = true>
-__device__ __forceinline__ void decode_block(const uint64_t *__restrict__ w, uint32_t rate, float (&out)[64],
-                                             uint64_t *planes, uint32_t stride) {
-    BitWindow<kReadOnly> bw;
-    bw.init(w, rate);
-    if (!(bw.w0 & 1ull)) {
-#pragma unroll
-        for (int i = 0; i < 64; i++) out[i] = 0.0f;
-        return;
+// ---------------------------------------------------------------- group-test steps
+//
+// The group tests of a plane (after its verbatim bits) are read eight bits
+// at a time through a 512-entry table: for a state (0: the next bit is a
+// group test, 1: it is a run bit) and a byte of the stream, the entry holds
+// what reading those bits one by one does --
+//   bits 0-7    the run bits met, in order (coefficient n, n + 1, ...)
+//   bits 8-11   how many run bits that is
+//   bits 12-15  bits consumed (8, or fewer when a 0 test ends the plane)
+//   bit 16      a 0 test ended the plane
+//   bit 17      the state after the consumed bits
+// A group test is a 1 followed by the run of later coefficients' bits up to
+// and including the next one, or the 0 that ends the plane, so without the
+// budget and coefficient 63's implied one the table step is exactly eight
+// steps of that rule.  The decoder checks the two exceptions around it.
+__host__ __device__ constexpr uint32_t group_step_entry(uint32_t state, uint32_t byte) {
+    uint32_t runbits = 0, count = 0, consumed = 8, ended = 0;
+    for (uint32_t i = 0; i < 8; i++) {
+        const uint32_t bit = (byte >> i) & 1u;
+        if (state == 0) {
+            if (!bit) {
+                ended = 1;
+                consumed = i + 1;
+                break;
+            }
+            state = 1;
+        } else {
+            runbits |= bit << count;
+            count++;
+            if (bit) state = 0;
+        }
     }
-    const int emax = (int)((bw.w0 >> 1) & 0xFFu) - 127;
-    const uint32_t end = rate * 64u;
-    uint32_t pos = 9;
-    uint32_t n = 0;                        // coefficients reached by the group tests
-    // Up to kTests group tests per iteration, preceded at the start of a
-    // plane by the plane's verbatim bits (predicated, so every lane runs the
-    // same instructions; a lane whose plane has ended sits out the rest of
-    // the iteration).  Lanes of a warp decode different blocks; one loop of
-    // uniform steps keeps them together even when their planes hold
-    // different numbers of group tests, and several tests per step spread
-    // the step's fixed cost.  Fixed-rate noise blocks at 8 bits/value code
-    // about 16 planes with 1.6 group tests each on average: two tests per
-    // step measured fastest (one: 4% slower, three: 1.5% slower).
-    constexpr int kTests = 2;
-    int k = 31;                            // plane number, most significant first
-    uint64_t x = 0;
-    bool opening = true;
-    {
+    return runbits | (count << 8) | (consumed << 12) | (ended << 16) | (state << 17);
+}
+
+constexpr uint32_t kGroupTableEntries = 512;
+
+// fill a block's copy of the table (all threads; the caller synchronises)
+__device__ __forceinline__ void load_group_table(uint32_t *tab) {
+    for (uint32_t i = threadIdx.x; i < kGroupTableEntries; i += blockDim.x) tab[i] = group_step_entry(i >> 8, i & 255u);
+}
+
+// One group-test event read bit by bit, with every rule: from state 0 a
+// test bit (a 0 ends the plane), then (or from state 1) the rest of a run,
+// at most 63 - n run bits (coefficient 63's one is implied) and no bit past
+// the budget.  Updates pos, n, the plane (xlo, xhi) and `ended`.
+__device__ __forceinline__ void group_event_exact(const StagedBits &st, uint32_t end, uint32_t &pos, uint32_t &n,
+                                                  uint32_t &xlo, uint32_t &xhi, uint32_t state, bool &ended) {
+    if (state == 0) {
+        const uint32_t g = st.win32(pos);
+        pos += 1;
+        if (!(g & 1u)) {
+            ended = true;
+            return;
+        }
+    }
+    const uint32_t lim = 63u - n;                // run bits that may be sent
+    const uint32_t scan = min(lim, end - min(end, pos));   // of which the budget holds
+    uint32_t z = 64u;                            // zeros before the run's one (64: none)
+    for (uint32_t off = 0; off < scan; off += 32) {
+        uint32_t w = st.win32(pos + off);
+        if (scan - off < 32u) w &= (1u << (scan - off)) - 1u;
+        if (w) {
+            z = off + (uint32_t)__ffs(w) - 1u;
+            break;
+        }
+    }
+    if (z < 64u) {                               // z zeros, then coefficient n + z's one
+        pos += z + 1;
+        n += z;
+        if (n < 32u) xlo |= 1u << n;
+        else xhi |= 1u << (n - 32u);
+        n += 1;
+    } else if (scan == lim) {                    // zeros up to coefficient 62: 63's one is implied
+        pos += lim;
+        xhi |= 1u << 31;
+        n = 64;
+    } else {
+        pos = end;                               // the budget ran out inside the run
+    }
+}
+
+// Parse the bit planes of a staged block of `rate` words: plane k (most
+// significant first) goes to shared address planes + k * stride as a 64-bit
+// word whose bit i belongs to the i-th coded coefficient.  A zero block (flag bit 0: the
+// rest is not read) has all planes zero.  Sets emax.
+//
+// The lanes of a warp parse different blocks.  One loop of uniform steps
+// keeps them together: a step takes the plane's verbatim bits when it opens
+// a plane, then up to kSteps table steps of its group tests, all
+// predicated; a lane whose block is done sits the remaining steps out.
+// Once every coefficient is reached (n = 64) a plane is its 64 verbatim
+// bits, which a short loop of its own copies.
+template <int kSteps = 2>
+__device__ __forceinline__ void parse_planes(const StagedBits &st, uint32_t rate, uint32_t tab, uint32_t planes,
+                                             uint32_t stride, int &emax) {
+    const uint32_t head = lds_u32(st.w);
+    emax = (int)((head >> 1) & 0xFFu) - 127;
+    const uint32_t end = (head & 1u) ? rate * 64u : 0u;
+    uint32_t pos = 9, n = 0;               // n: coefficients reached by the group tests
+    int k = 31;                            // plane, most significant first
+    if (end) {
         // Until a coefficient is reached, a plane has no verbatim bits and a
-        // 0 group test ends it: each 0 bit here is a whole empty plane.
-        const uint64_t win = bw.peek(pos);
-        uint32_t z = win ? (uint32_t)__ffsll((long long)win) - 1u : 64u;
-        z = min(z, min(32u, end - pos));
-        for (uint32_t j = 0; j < z; j++) planes[(uint32_t)(31 - (int)j) * stride] = 0ull;
+        // 0 group test ends it: each 0 bit here is a whole empty plane
+        // (end - pos >= 55 at every rate, so the window is inside the budget).
+        const uint32_t win = st.win32(pos);
+        const uint32_t z = win ? (uint32_t)__ffs(win) - 1u : 32u;
+        for (uint32_t j = 0; j < z; j++) sts_u64(planes + (31u - j) * stride, 0u, 0u);
         k -= (int)z;
         pos += z;
-        bw.advance(pos);
     }
-    while (k >= 0 && pos < end) {
-        // the verbatim bits of the n coefficients reached so far
-        const uint32_t m = opening ? min(n, end - pos) : 0u;
-        const uint64_t pk = bw.peek(pos);
-        x = opening ? (pk & low_mask(m)) : x;
-        pos += m;
-        bw.advance(pos);
-        // a plane ends after its verbatim bits when every coefficient is
-        // reached or the budget is spent (otherwise n < 64 and pos < end)
-        bool plane_done = n >= 64 || pos >= end;
-#pragma unroll
-        for (int test = 0; test < kTests; test++) {
-            if (plane_done) continue;
-            const uint64_t win = bw.peek(pos);
-            pos += 1;
-            if (!(win & 1ull)) {           // no later coefficient has a one here
-                plane_done = true;
-            } else {
-                const uint32_t limit = 63u - n;                 // bits that may be sent
-                const uint32_t cnt = min(limit, end - pos);
-                const uint64_t y = (win >> 1) & low_mask(cnt);
-                if (y) {
-                    const uint32_t z = (uint32_t)__ffsll((long long)y) - 1u;
-                    pos += z + 1;
-                    n += z;
-                    x |= 1ull << n;
-                    n += 1;
-                } else if (cnt == limit) {
-                    pos += limit;
-                    x |= 1ull << 63;
-                    n = 64;
-                } else {
-                    pos = end;             // the budget ran out inside the scan
-                }
-                plane_done = n >= 64 || pos >= end;
-            }
-            bw.advance(pos);
+    uint32_t xlo = 0u, xhi = 0u, state = 0u;
+    bool opening = true, exact = false;    // exact: the next event is read bit by bit
+    while (k >= 0 && pos < end && n < 64u) {
+        if (opening) {                     // the verbatim bits of the n coefficients reached so far
+            const uint32_t m = min(n, end - pos);
+            uint32_t wlo, whi;
+            st.win64(pos, wlo, whi);
+            xlo = m >= 32u ? wlo : (wlo & ((1u << m) - 1u));
+            xhi = m > 32u ? (whi & ((1u << (m - 32u)) - 1u)) : 0u;   // m < 64 here
+            pos += m;
+            state = 0u;
         }
-        if (plane_done) {
-            planes[(uint32_t)k * stride] = x;
+        bool done = pos >= end;
+        if (exact && !done) {              // the run reaches coefficient 63 inside the next byte
+            bool ended = false;
+            group_event_exact(st, end, pos, n, xlo, xhi, state, ended);
+            state = 0u;
+            exact = false;
+            done = ended || pos >= end || n >= 64u;
+        }
+#pragma unroll
+        for (int t = 0; t < kSteps; t++) {
+            if (done || exact) continue;
+            uint32_t byte = st.win32(pos) & 0xFFu;
+            if (end - pos < 8u) byte &= (1u << (end - pos)) - 1u;   // no bit past the budget
+            const uint32_t e = lds_u32(tab + (((state << 8) | byte) << 2));
+            const uint32_t cnt = (e >> 8) & 15u;
+            if (n + cnt > 63u) {           // a run bit for coefficient 63 or later: not a table step
+                exact = true;
+                continue;
+            }
+            const uint64_t bits = (uint64_t)(e & 0xFFu) << n;
+            xlo |= (uint32_t)bits;
+            xhi |= (uint32_t)(bits >> 32);
+            n += cnt;
+            pos += (e >> 12) & 15u;
+            state = (e >> 17) & 1u;
+            if (state && n == 63u && pos <= end) {   // the run reached coefficient 63: its one is implied
+                xhi |= 1u << 31;
+                n = 64;
+                state = 0u;
+            }
+            done = ((e >> 16) & 1u) != 0u || pos >= end || n >= 64u;
+        }
+        if (done) {
+            sts_u64(planes + (uint32_t)k * stride, xlo, xhi);
             k--;
         }
-        opening = plane_done;
+        opening = done;
     }
-    for (; k >= 0; k--) planes[(uint32_t)k * stride] = 0ull;
+    // every coefficient reached: each remaining plane is the next 64 bits
+    for (; k >= 0 && pos < end; k--) {
+        const uint32_t m = min(64u, end - pos);
+        uint32_t wlo, whi;
+        st.win64(pos, wlo, whi);
+        if (m < 64u) {
+            wlo = m >= 32u ? wlo : (wlo & ((1u << m) - 1u));
+            whi = m > 32u ? (whi & ((1u << (m - 32u)) - 1u)) : 0u;
+        }
+        sts_u64(planes + (uint32_t)k * stride, wlo, whi);
+        pos += m;
+    }
+    for (; k >= 0; k--) sts_u64(planes + (uint32_t)k * stride, 0u, 0u);
+}
+
+// Decode a staged block of `rate` words into out[64] (block-local order).
+// `planes` is this thread's column of a shared-memory area: plane k lives at
+// planes[k * stride].
+__device__ __forceinline__ void decode_staged(const uint32_t *staged, uint32_t rate, const uint32_t *tab,
+                                              float (&out)[64], uint64_t *planes, uint32_t stride) {
+    int emax = 0;
+    // a zero block: all planes 0, every sample +0
+    const uint32_t pa = smem_u32(planes), ps = stride * 8u;
+    parse_planes(StagedBits{smem_u32(staged)}, rate, smem_u32(tab), pa, ps, emax);
     constexpr CodingOrder order = make_coding_order();
-    int32_t q[64];
+    uint32_t q[64];
     uint32_t a[32];
 #pragma unroll
-    for (int j = 0; j < 32; j++) a[j] = (uint32_t)planes[(uint32_t)j * stride];
-    transpose32(a);                        // a[i] = negabinary coefficient i
+    for (int j = 0; j < 32; j++) a[j] = lds_u32(pa + (uint32_t)j * ps);
+    transpose32(a);                        // a[p] = negabinary coefficient p (coded order)
 #pragma unroll
-    for (int p = 0; p < 32; p++) q[order.perm[p]] = (int32_t)((a[p] ^ kNegaMask) - kNegaMask);
+    for (int p = 0; p < 32; p++) q[order.perm[p]] = (a[p] ^ kNegaMask) - kNegaMask;
 #pragma unroll
-    for (int j = 0; j < 32; j++) a[j] = (uint32_t)(planes[(uint32_t)j * stride] >> 32);
-    transpose32(a);                        // a[i] = coefficient 32 + i
+    for (int j = 0; j < 32; j++) a[j] = lds_u32(pa + (uint32_t)j * ps + 4u);
+    transpose32(a);                        // a[p] = coefficient 32 + p
 #pragma unroll
-    for (int p = 0; p < 32; p++) q[order.perm[32 + p]] = (int32_t)((a[p] ^ kNegaMask) - kNegaMask);
+    for (int p = 0; p < 32; p++) q[order.perm[32 + p]] = (a[p] ^ kNegaMask) - kNegaMask;
 #pragma unroll
-    for (int i = 0; i < 16; i++) inv_lift4(q[i], q[i + 16], q[i + 32], q[i + 48]);             // z
+    for (int i = 0; i < 16; i++) inv_lift4u(q[i], q[i + 16], q[i + 32], q[i + 48]);             // z
 #pragma unroll
     for (int z = 0; z < 4; z++)
 #pragma unroll
-        for (int x = 0; x < 4; x++) inv_lift4(q[x + 16 * z], q[x + 4 + 16 * z], q[x + 8 + 16 * z], q[x + 12 + 16 * z]);  // y
+        for (int x = 0; x < 4; x++) inv_lift4u(q[x + 16 * z], q[x + 4 + 16 * z], q[x + 8 + 16 * z], q[x + 12 + 16 * z]);  // y
 #pragma unroll
-    for (int i = 0; i < 16; i++) inv_lift4(q[4 * i], q[4 * i + 1], q[4 * i + 2], q[4 * i + 3]);  // x
-    const int e = emax - kPrecision;
-#pragma unroll
-    for (int i = 0; i < 64; i++) out[i] = scale_pow2(q[i], e);
+    for (int i = 0; i < 16; i++) inv_lift4u(q[4 * i], q[4 * i + 1], q[4 * i + 2], q[4 * i + 3]);  // x
+    scale_block(q, emax - kPrecision, out);
+}
+
+// Dynamic shared memory of a decoding kernel of `threads` threads: the
+// plane columns (32 words of 8 bytes per thread), the group-step table, then
+// one staging area per warp for blocks of up to `rate` words.
+struct DecodeSmem {
+    uint64_t *planes;
+    uint32_t *tab;
+    uint32_t *stage;          // this warp's staging area
+};
+
+__host__ __device__ constexpr size_t decode_smem_bytes(uint32_t threads, uint32_t rate) {
+    return 32u * 8u * (size_t)threads + kGroupTableEntries * 4u + (size_t)(threads / 32u) * stage_words(rate) * 4u;
+}
+
+__device__ __forceinline__ DecodeSmem decode_smem_layout(uint64_t *base, uint32_t threads, uint32_t rate) {
+    uint32_t *tab = reinterpret_cast<uint32_t *>(base + 32u * threads);
+    return DecodeSmem{base, tab, tab + kGroupTableEntries + (threadIdx.x >> 5) * stage_words(rate)};
 }
 
 // ---------------------------------------------------------------- encoder (input generation)

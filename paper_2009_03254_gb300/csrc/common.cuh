@@ -227,6 +227,13 @@ __device__ __forceinline__ unsigned long long lookback_exclusive(unsigned long l
 
 // ---------------------------------------------------------------- bit tools
 
+// (x & ~m) | (y & m) as one three-input logic instruction
+__device__ __forceinline__ uint32_t select_bits(uint32_t x, uint32_t y, uint32_t m) {
+    uint32_t r;
+    asm("lop3.b32 %0, %1, %2, %3, 0xD8;" : "=r"(r) : "r"(x), "r"(y), "r"(m));   // LUT of (c ? b : a): 0xD8
+    return r;
+}
+
 // In-place transpose of a 32x32 bit matrix held in 32 words: afterwards
 // bit j of a[i] is what bit i of a[j] was.  Five rounds of swapping the
 // off-diagonal sub-blocks (16x16, 8x8, ..., 1x1); the 16- and 8-bit rounds
@@ -249,13 +256,15 @@ __device__ __forceinline__ void transpose32(uint32_t (&a)[32]) {
 #pragma unroll
     for (int r = 2; r < 5; r++) {
         const int s = 16 >> r;
-        const uint32_t m = masks[r];
+        const uint32_t m = masks[r], mh = m << s;
 #pragma unroll
         for (int j = 0; j < 32; j++) {
             if (j & s) continue;
-            uint32_t t = ((a[j] >> s) ^ a[j + s]) & m;
-            a[j + s] ^= t;
-            a[j] ^= t << s;
+            // swap the bits of a[j] under mh with those of a[j + s] under m,
+            // each word as one shift and one three-input select
+            const uint32_t x = a[j], y = a[j + s];
+            a[j] = select_bits(x, y << s, mh);
+            a[j + s] = select_bits(y, x >> s, m);
         }
     }
 }
@@ -279,6 +288,17 @@ __host__ __device__ constexpr CodingOrder make_coding_order() {
         for (int l = 0; l < 64; l++)
             if (axis_sequency(l & 3) + axis_sequency((l >> 2) & 3) + axis_sequency(l >> 4) == level) o.perm[n++] = l;
     return o;
+}
+
+// pos[l] = place of linear index l in the coded order (the inverse of perm)
+struct CodingInverse {
+    int pos[64];
+};
+
+__host__ __device__ constexpr CodingInverse make_coding_inverse(const CodingOrder &o) {
+    CodingInverse v{};
+    for (int p = 0; p < 64; p++) v.pos[o.perm[p]] = p;
+    return v;
 }
 
 constexpr int kPrecision = 27;        // integer bits of the block-floating-point form

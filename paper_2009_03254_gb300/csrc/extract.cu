@@ -408,22 +408,29 @@ __global__ void __launch_bounds__(kThreads) lru_b_kernel(Launch L) {
 
 // ================================================================ decode (Section 4.2.1)
 //
-// Chunks of kDecodeThreads new blocks, one block per thread.  Chunk 0 of
-// every volume (each volume has at least one) also commits the volume's
-// cache update.  With 256-thread blocks the kernel then does lru_b's work
-// (the list for the next update, which nothing before then reads): its
-// memory latency hides behind the decoding and one launch and grid-wide
-// wait fewer run per extraction.
+// Chunks of kDecodeThreads new blocks; each warp of a chunk stages its 32
+// blocks' words in shared memory with coalesced loads and decodes them one
+// per lane (codec.cuh).  Chunk 0 of every volume (each volume has at least
+// one) also commits the volume's cache update.  With 256-thread blocks the
+// kernel then does lru_b's work (the list for the next update, which
+// nothing before then reads): its memory latency hides behind the decoding
+// and one launch and grid-wide wait fewer run per extraction.
 
 template <int kDecodeThreads>
 constexpr bool decode_runs_lru_b() { return kDecodeThreads == kThreads; }
 
 template <int kDecodeThreads, bool kOne>
 __global__ void __launch_bounds__(kDecodeThreads, 768 / kDecodeThreads) decode_new_kernel(Launch L) {   // 24 warps/SM
-    extern __shared__ uint64_t planes[];              // 32 * kDecodeThreads words (dynamic)
+    // dynamic: the plane columns (32 words per thread), then one staging
+    // area per warp for the launch's largest rate
+    extern __shared__ uint64_t dsm[];
     __shared__ uint32_t pre[kMaxBatch + 1];
     __shared__ TileScan<kRounds> ts;                  // lru_b's work
     __shared__ uint32_t slot_x;
+    const uint32_t warp = threadIdx.x >> 5;
+    const DecodeSmem sm = decode_smem_layout(dsm, kDecodeThreads, kOne ? L.one.g.rate : L.max_rate);
+    load_group_table(sm.tab);
+    __syncthreads();
     const uint32_t total = launch_prefix<kOne>(
         L, [&](uint32_t v) { return max(1u, ceil_div(vol_of<kOne>(L, v).s.ctl->n_assign, kDecodeThreads)); },
         pre);
@@ -432,20 +439,26 @@ __global__ void __launch_bounds__(kDecodeThreads, 768 / kDecodeThreads) decode_n
         const DevState &s = vol_of<kOne>(L, v).s;
         Ctl *c = s.ctl;
         const uint32_t chunk = x - item_base<kOne>(pre, v);
-        if (c->status & kStatusAnyTimeout) continue;  // no barrier in this loop: per-thread skips are safe
+        if (c->status & kStatusAnyTimeout) continue;  // block-uniform: no barrier in this loop
         if (chunk == 0 && threadIdx.x == 0) {         // commit the cache update
             c->S = c->S_next;
             c->u = c->u_next;
             c->lpar = c->lpar_next;
         }
-        const uint32_t r = chunk * kDecodeThreads + threadIdx.x;
-        if (r >= c->n_assign) continue;
+        const uint32_t n_assign = c->n_assign;
+        const uint32_t r0 = chunk * kDecodeThreads + warp * 32u;
+        if (r0 >= n_assign) continue;                 // warp-uniform
+        const uint32_t r = r0 + (threadIdx.x & 31u);
         const uint32_t rate = vol_of<kOne>(L, v).g.rate;
-        const uint32_t b = s.inew[r];
-        const uint32_t slot = s.newslot[r];
-        if (!in_bounds(b < vol_of<kOne>(L, v).g.nb && slot < c->cap, &c->status)) continue;
+        bool have = r < n_assign;
+        const uint32_t b = have ? s.inew[r] : 0u;
+        const uint32_t slot = have ? s.newslot[r] : 0u;
+        have = have && in_bounds(b < vol_of<kOne>(L, v).g.nb && slot < c->cap, &c->status);
+        stage_blocks<true>(s.bits, rate, b, have, sm.stage);
+        if (!have) continue;
         float val[64];
-        decode_block(s.bits + (size_t)b * rate, rate, val, planes + threadIdx.x, kDecodeThreads);
+        decode_staged(sm.stage + (threadIdx.x & 31u) * (2u * rate + 1u), rate, sm.tab, val, sm.planes + threadIdx.x,
+                      kDecodeThreads);
         float4 *dst = reinterpret_cast<float4 *>(s.slots + (size_t)slot * 64);
 #pragma unroll
         for (int i = 0; i < 16; i++) dst[i] = make_float4(val[4 * i], val[4 * i + 1], val[4 * i + 2], val[4 * i + 3]);
@@ -599,7 +612,10 @@ __global__ void gather_slots_kernel(const float *__restrict__ slots, const int32
 
 // ================================================================ launchers
 
-constexpr size_t decode_smem(int threads) { return 32u * 8u * (size_t)threads; }
+// the decode kernel's dynamic shared memory for a launch
+size_t decode_smem(const Launch &L, int threads) {
+    return decode_smem_bytes((uint32_t)threads, L.vols ? L.max_rate : L.one.g.rate);
+}
 
 // Algorithm 1 after the cull (both list kernels), then the decode
 template <bool kOne>
@@ -608,9 +624,9 @@ void cache_update(const Launch &L, const Plan &pl, cudaStream_t st, cudaEvent_t 
     if (pl.decode_tile != kThreads) lru_b_kernel<kOne><<<pl.lru_b, kThreads, 0, st>>>(L);   // else the decode's
     if (ev) cudaEventRecord(ev[3], st);
     if (bits_ready) cudaStreamWaitEvent(st, bits_ready, 0);   // the bitstream may still be on its way
-    if (pl.decode_tile == 64) decode_new_kernel<64, kOne><<<pl.decode, 64, decode_smem(64), st>>>(L);
-    else if (pl.decode_tile == 256) decode_new_kernel<256, kOne><<<pl.decode, 256, decode_smem(256), st>>>(L);
-    else decode_new_kernel<128, kOne><<<pl.decode, 128, decode_smem(128), st>>>(L);
+    if (pl.decode_tile == 64) decode_new_kernel<64, kOne><<<pl.decode, 64, decode_smem(L, 64), st>>>(L);
+    else if (pl.decode_tile == 256) decode_new_kernel<256, kOne><<<pl.decode, 256, decode_smem(L, 256), st>>>(L);
+    else decode_new_kernel<128, kOne><<<pl.decode, 128, decode_smem(L, 128), st>>>(L);
     if (ev) cudaEventRecord(ev[4], st);
 }
 
@@ -665,18 +681,19 @@ void launch_gather_slots(const float *slots, const int32_t *islot, const uint32_
     gather_slots_kernel<<<(unsigned)blocks, 256, 0, st>>>(slots, islot, ids, n, out, missing);
 }
 
+// the limit is set for the largest rate, so any launch fits
 template <bool kOne>
 void set_decode_attributes() {
     cudaFuncSetAttribute(decode_new_kernel<64, kOne>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)decode_smem(64));
+                         (int)decode_smem_bytes(64, 32));
     cudaFuncSetAttribute(decode_new_kernel<128, kOne>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)decode_smem(128));
+                         (int)decode_smem_bytes(128, 32));
     cudaFuncSetAttribute(decode_new_kernel<256, kOne>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)decode_smem(256));
+                         (int)decode_smem_bytes(256, 32));
 }
 
 template <bool kOne>
-Plan limits_of(const Plan &tiles) {
+Plan limits_of(const Plan &tiles, uint32_t rate) {
     Plan pl = tiles;
     int occ = 0;
     if (tiles.cull_tile == 2048) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cull_kernel<8, kOne>, kThreads, 0);
@@ -689,18 +706,20 @@ Plan limits_of(const Plan &tiles) {
     set_decode_attributes<false>();
     set_decode_attributes<true>();
     if (tiles.decode_tile == 64)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, decode_new_kernel<64, kOne>, 64, decode_smem(64));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, decode_new_kernel<64, kOne>, 64, decode_smem_bytes(64, rate));
     else if (tiles.decode_tile == 256)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, decode_new_kernel<256, kOne>, 256, decode_smem(256));
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, decode_new_kernel<128, kOne>, 128, decode_smem(128));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, decode_new_kernel<256, kOne>, 256,
+                                                      decode_smem_bytes(256, rate));
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, decode_new_kernel<128, kOne>, 128,
+                                                       decode_smem_bytes(128, rate));
     pl.decode = std::max(1, occ);
     mc_occupancy(&pl, kOne);
     pl.prep = 2;
     return pl;
 }
 
-Plan occupancy_limits(const Plan &tiles, bool single) {
-    return single ? limits_of<true>(tiles) : limits_of<false>(tiles);
+Plan occupancy_limits(const Plan &tiles, bool single, uint32_t rate) {
+    return single ? limits_of<true>(tiles, rate) : limits_of<false>(tiles, rate);
 }
 
 bool valid_tiles(const Plan &pl) {

@@ -66,6 +66,7 @@ struct Launch {
     uint32_t n;
     uint32_t *ctr;
     VolEntry one;
+    uint32_t max_rate = 0;   // batches: the largest rate among the volumes (sizes the decoder's staging)
 };
 
 // How a launch sequence runs: the CTAs of each persistent kernel and the
@@ -128,7 +129,7 @@ void launch_gather_slots(const float *slots, const int32_t *islot, const uint32_
 // `tiles`, in single-volume or batch launches (CTA fields of the result;
 // tile fields copied).  Also raises the shared-memory limits of every
 // kernel that needs more than the default.
-Plan occupancy_limits(const Plan &tiles, bool single);
+Plan occupancy_limits(const Plan &tiles, bool single, uint32_t rate);
 void mc_occupancy(Plan *pl, bool single);
 // tile sizes that the kernels are compiled for
 bool valid_tiles(const Plan &pl);

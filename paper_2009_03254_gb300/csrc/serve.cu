@@ -498,7 +498,7 @@ int iso_server_create(iso_server **out, iso_volume *v, const iso_server_options 
         return ISO_ERR_CUDA;
     }
 #undef TRY
-    sv->view_plan = launch_plan(nullptr, sv->device, v->g.nb, cand, 1, true);
+    sv->view_plan = launch_plan(nullptr, sv->device, v->g.nb, cand, 1, true, v->g.rate);
     *out = sv;
     return ISO_OK;
 }

@@ -570,7 +570,7 @@ def test_launch_shapes_agree():
     vol = p.Volume(bits, dims, rate, bmin, bmax)
     try:
         start = vol.get_shape()
-        assert start["scan_tile"] == 4096 and start["decode_tile"] == 256
+        assert start["scan_tile"] == 4096 and start["decode_tile"] == 128
         ref = vol.extract(0.1)
         want = ref.vertices.cpu().numpy().view(np.uint32)
         ref.release()
