@@ -21,8 +21,15 @@ Metric: triangles/s (whole step, all five surfaces), with voxels/s
            with double buffering (the next volume's upload overlaps this
            volume's surfaces), and the one-at-a-time figure is reported
            beside it as e2e.serial
-  roofline the dominant stage's kernel: algorithmic bytes per launch over
-           its CUDA-event duration, against the measured HBM copy peak
+  roofline one whole extraction from an empty cache (every kernel, the
+           count readback): the bytes the method must move per surface,
+           n_new * (8R + 256) + 48T, over its CUDA-event duration, against
+           the measured HBM copy peak; the dominant kernel's own figure
+           (algorithmic bytes per launch over its duration) nested in it
+  serving  the request loop on a quarter-scale channel-flow volume:
+           Poisson isovalue requests served by the batched server (max_batch
+           2, 4, 8) and by the plain per-request path, p50/p99 latency and
+           triangles/s; a warm single request both ways
   cpu_baseline  the plain CPU oracle on a bounded window of the same field
   parity   the library on that window against the oracle's surfaces:
            triangle counts, order and block ids exact, and the largest
@@ -81,11 +88,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-volume batch comparison")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving leg of the default run")
     ap.add_argument("--workload", default="noise512", choices=["noise512", "serve"],
                     help="serve: the request loop on the 10240x7680x1536 channel volume")
     ap.add_argument("--serve-scale", type=float, default=1.0,
                     help="fraction of the serving volume's x and y extent (1 = full size)")
-    ap.add_argument("--requests", type=int, default=1000)
+    ap.add_argument("--requests", type=int, default=1000,
+                    help="requests of --workload serve (the default run's serving leg takes 200)")
     ap.add_argument("--dims", type=int, default=512,
                     help="cube edge of the noise volume (default 512; smaller sizes are for profiling captures)")
     return ap.parse_args()
@@ -185,6 +194,28 @@ def profile_traffic(kernel_file, kernel):
         if line.startswith("traffic_per_launch_bytes:"):
             parts = line.split()
             if len(parts) >= 4 and parts[2] == "source_sha256_16:" and parts[3] == sha:
+                return float(parts[1])
+    return None
+
+
+def extraction_traffic():
+    """DRAM bytes of one cold isovalue-0 extraction (all its kernels) from the
+    committed ncu summary, if it was taken on the current kernel sources
+    (else None)."""
+    path = os.path.join(ROOT, "profiles", "extraction_cold_noise512.md")
+    srcs = [os.path.join(ROOT, "paper_2009_03254_gb300", "csrc", f) for f in ("extract.cu", "mc.cu", "codec.cuh")]
+    try:
+        text = open(path).read()
+        h = hashlib.sha256()
+        for f in srcs:
+            h.update(open(f, "rb").read())
+        sha = h.hexdigest()[:16]
+    except OSError:
+        return None
+    for line in text.splitlines():
+        if line.startswith("traffic_per_extraction_bytes:"):
+            parts = line.split()
+            if len(parts) >= 4 and parts[2] == "sources_sha256_16:" and parts[3] == sha:
                 return float(parts[1])
     return None
 
@@ -779,6 +810,12 @@ def run_ours(args):
                               "what": "the same steps one volume at a time: load, five surfaces, release"}}
         vol.release()
         batch = None if args.no_batch else measure_batch64(bc, sg, torch, stream, flush, args.steps)
+        del out, flush
+        torch.cuda.empty_cache()
+        serve = None
+        if not args.no_serve and rank == 0:
+            serve = serving_summary(measure_serving(bc, torch, SERVE_LEG_SCALE, SERVE_LEG_REQUESTS,
+                                                    batches=(2, 4, 8), sweeps=False))
 
     if rank != 0:
         dist.barrier() if world > 1 else None
@@ -824,10 +861,15 @@ def run_ours(args):
                    "cache_hit_rate_per_surface_in_a_step": [
                        round(1.0 - st["n_new"] / st["n_active"], 4) if st["n_active"] else None for st in stats],
                    "parallelism": f"{world} independent replica(s)"},
-        "roofline": {"bound": "hbm", "kernel": KERNEL_OF[dominant][0], "achieved": ach, "peak": peak, "unit": "GB/s",
-                     "frac": ach / peak, "peak_source": f"{peak_src} hbm_gbs (copy)",
-                     "traffic": profile_traffic(KERNEL_OF[dominant][1], KERNEL_OF[dominant][0]),
-                     "alg_bytes_per_launch": stage_b[dominant] / n_launch},
+        "roofline": {"bound": "hbm", "what": "one whole extraction from an empty cache (every kernel, count "
+                     "readback), device time, against n_new*(8R + 256) + 48T bytes per surface",
+                     "achieved": cold_gbs, "peak": peak, "unit": "GB/s", "frac": cold_gbs / peak,
+                     "peak_source": f"{peak_src} hbm_gbs (copy)",
+                     "traffic": extraction_traffic(),
+                     "alg_bytes_per_launch": cold_b / n_cold,
+                     "dominant_kernel": {"kernel": KERNEL_OF[dominant][0], "achieved": ach, "frac": ach / peak,
+                                         "alg_bytes_per_launch": stage_b[dominant] / n_launch,
+                                         "traffic": profile_traffic(KERNEL_OF[dominant][1], KERNEL_OF[dominant][0])}},
         "roofline_cold_extraction": cold,
         "packed_vertices": packed,
         "indexed_mesh": indexed,
@@ -835,6 +877,7 @@ def run_ours(args):
         "full_volume_baselines": baselines,
         "batch64": batch,
         "stages": stages,
+        "serving": serve,
         "gpu_launches": args.steps * (KERNELS_PER_RESET + KERNELS_PER_SURFACE * len(ISOS)),
         "clocks": clk.summary(),
         "e2e": e2e,
@@ -866,30 +909,28 @@ def run_ours(args):
 
 # ---------------------------------------------------------------- serving
 
-SERVE_BUDGET_BYTES = 64e9          # decoded-block cache budget of the serving volume
-SERVE_VERTEX_BUDGET = 48e9         # finished meshes held by the server at once
+SERVE_BUDGET_BYTES = 64e9          # decoded-block cache budget of the serving volume (scaled with its area)
+SERVE_LEG_SCALE = 0.25             # the default run's serving leg: x and y at a quarter (1/16 of the samples)
+SERVE_LEG_REQUESTS = 200
+SERVE_VERTEX_BUDGET = 48e9         # finished meshes held by the server at once (not scaled with the volume)
 
 
-def run_serve(args):
-    """Request loop on the serving volume: Poisson arrivals (rate 0.8 / the
-    plain path's median service time), isovalues a reflecting random walk
-    over the [p5, p95] decoded percentiles (step 0.02 of the range), served
-    by the batched server and, on the same schedule, by the plain
-    per-request path; then sweeps up and down the same range."""
+def measure_serving(bc, torch, scale, n, batches=(4,), sweeps=True):
+    """The request loop on the serving volume (the channel-flow recipe, x and
+    y scaled by `scale`): Poisson arrivals at 0.8 / the plain path's median
+    service time, isovalues a reflecting random walk over the [p5, p95]
+    decoded percentiles (step 0.02 of the range), served by the batched
+    server (each max_batch in `batches`) and, on the same schedule, by the
+    plain per-request path; a warm single request both ways; optionally
+    sweeps up and down the same range."""
     import dataclasses
-    import torch
-    import __graft_entry__
-    __graft_entry__.build()
-    import paper_2009_03254_gb300 as bc
     from paper_2009_03254_gb300 import serving
-    import synth.gpu as sg
     from synth import recipes, volumes
-    sg.build()
     rec = recipes.SERVE_DNS
-    if args.serve_scale != 1.0:
+    if scale != 1.0:
         nx, ny, nz = rec.dims
-        sx = max(4, int(round(nx * args.serve_scale / 4)) * 4)
-        sy = max(4, int(round(ny * args.serve_scale / 4)) * 4)
+        sx = max(4, int(round(nx * scale / 4)) * 4)
+        sy = max(4, int(round(ny * scale / 4)) * 4)
         rec = dataclasses.replace(rec, dims=(sx, sy, nz))
     scale_area = rec.dims[0] * rec.dims[1] / float(recipes.SERVE_DNS.dims[0] * recipes.SERVE_DNS.dims[1])
     t0 = time.time()
@@ -897,7 +938,7 @@ def run_serve(args):
     t_gen = time.time() - t0
     p5, p50, p95 = (volumes.percentile_isovalue(bits, rec.dims, rec.rate, q, seed=3) for q in (0.05, 0.5, 0.95))
     budget = int(SERVE_BUDGET_BYTES * scale_area)
-    stream = torch.cuda.current_stream()
+    vertex_budget = int(SERVE_VERTEX_BUDGET)       # a memory cap: the same at every scale
     vol = bc.Volume(bits, rec.dims, rec.rate, bmin, bmax, cache_budget_bytes=budget, initial_cache_fraction=0.01)
     compressed = bits.numel() * 8
     del bits, bmin, bmax
@@ -912,9 +953,10 @@ def run_serve(args):
         m.release()
     median_svc = float(np.median(svc[1:]))
     rate = 0.8 / median_svc
-    n = args.requests
     isos = serving.random_walk_isovalues(n, p5, p95, 5)
     arrivals = serving.poisson_arrivals(n, rate, 1)
+    over_rate = 1.25 / median_svc                  # more than the plain path can serve
+    over_arrivals = serving.poisson_arrivals(n, over_rate, 2)
 
     def drive(backend, arr, iso_list):
         torch.cuda.synchronize()
@@ -927,63 +969,116 @@ def run_serve(args):
                     "failed": sum(1 for r in res if r["status"] not in (serving.ISO_OK, serving.REJECTED))})
         return out
 
-    # one request alone, warm cache: the plain call against a one-request tick;
-    # then a four-request tick step by step (its first step runs the front)
-    probe = bc.Server(vol, max_batch=4, vertex_budget_bytes=int(SERVE_VERTEX_BUDGET))
-
-    def served_steps(iso_list):
-        tickets = [probe.submit(float(x)) for x in iso_list]
-        times = []
-        for _ in iso_list:
-            t1 = time.perf_counter()
-            probe.step()
-            times.append(1e3 * (time.perf_counter() - t1))
-        for t in tickets:
-            st, m = probe.take(t)
-            if m is not None:
-                m.release()
-        return times
-
+    # one request alone, warm cache: the plain call against a one-request tick
     single = {"plain_ms": [], "served_ms": []}
-    for _ in range(3):
+    probe = bc.Server(vol, max_batch=1, vertex_budget_bytes=vertex_budget)
+    for _ in range(5):
         t1 = time.perf_counter()
         m = vol.extract(p50)
         single["plain_ms"].append(1e3 * (time.perf_counter() - t1))
         m.release()
-        single["served_ms"] += served_steps([p50])
-    tick4 = served_steps([p50, p50 * 0.98, p50 * 1.02, p50 * 0.96])
+        tk = probe.submit(float(p50))
+        t1 = time.perf_counter()
+        probe.step()
+        single["served_ms"].append(1e3 * (time.perf_counter() - t1))
+        st, m = probe.take(tk)
+        if m is not None:
+            m.release()
     probe.release()
+    single = {"plain_ms": float(np.median(single["plain_ms"][1:])), "served_ms": float(np.median(single["served_ms"][1:]))}
     vol.cache_reset()
     plain = drive(serving.PlainBackend(vol), arrivals, isos)
+    served = {}
+    for mb in batches:
+        vol.cache_reset()
+        srv = bc.Server(vol, max_batch=mb, vertex_budget_bytes=vertex_budget)
+        served[mb] = drive(srv, arrivals, isos)
+        srv.release()
+    # overload: arrivals at 1.25x the plain path's service rate
     vol.cache_reset()
-    srv = bc.Server(vol, max_batch=4, vertex_budget_bytes=int(SERVE_VERTEX_BUDGET))
-    served = drive(srv, arrivals, isos)
-    sweeps = {}
-    for name, seq in (("sweep_up", np.linspace(p5, p95, 100)), ("sweep_down", np.linspace(p95, p5, 100))):
-        seq = seq.astype(np.float32)
-        burst = np.zeros(len(seq))                   # all queued at once: throughput of each path
-        vol.cache_reset()
-        sp = drive(serving.PlainBackend(vol), burst, seq)
-        vol.cache_reset()
-        ss = drive(srv, burst, seq)
-        sweeps[name] = {"plain_triangles_per_s": sp["triangles_per_s"], "served_triangles_per_s": ss["triangles_per_s"],
-                        "plain_wall_s": sp["wall_s"], "served_wall_s": ss["wall_s"]}
+    over = {"arrival_rate_per_s": over_rate, "plain": drive(serving.PlainBackend(vol), over_arrivals, isos)}
+    mb = batches[-1]
+    vol.cache_reset()
+    srv = bc.Server(vol, max_batch=mb, vertex_budget_bytes=vertex_budget)
+    over["served"] = drive(srv, over_arrivals, isos)
+    over["max_batch"] = mb
     srv.release()
+    sw = {}
+    if sweeps:
+        mb = batches[len(batches) // 2]
+        srv = bc.Server(vol, max_batch=mb, vertex_budget_bytes=vertex_budget)
+        for name, seq in (("sweep_up", np.linspace(p5, p95, 100)), ("sweep_down", np.linspace(p95, p5, 100))):
+            seq = seq.astype(np.float32)
+            burst = np.zeros(len(seq))                   # all queued at once: throughput of each path
+            vol.cache_reset()
+            sp = drive(serving.PlainBackend(vol), burst, seq)
+            vol.cache_reset()
+            ss = drive(srv, burst, seq)
+            sw[name] = {"plain_triangles_per_s": sp["triangles_per_s"], "served_triangles_per_s": ss["triangles_per_s"],
+                        "plain_wall_s": sp["wall_s"], "served_wall_s": ss["wall_s"]}
+        srv.release()
     vol.release()
+    torch.cuda.empty_cache()
+    return {"workload": f"serve_dns: {rec.dims[0]}x{rec.dims[1]}x{rec.dims[2]} channel-flow field (seed {rec.seed}, "
+                        f"{rec.octaves} octaves, coarsest period {rec.base_period}), {rec.rate} bits/value, cache "
+                        f"budget {budget / 1e9:.1f} GB",
+            "requests": n, "arrival_rate_per_s": rate, "plain_median_service_ms": 1e3 * median_svc,
+            "isovalue_range": [p5, p95], "median_isovalue": p50, "triangles_at_median": t_med,
+            "compressed_bytes": compressed, "generate_encode_s": t_gen, "vertex_budget_bytes": vertex_budget,
+            "plain": plain, "served": served, "overload": over, "single_request_warm": single, "sweeps": sw}
+
+
+def serving_summary(sv):
+    """The served-vs-plain figures of measure_serving, compact."""
+    best = min(sv["served"], key=lambda mb: sv["served"][mb].get("p99_ms", float("inf")))
+    s, p = sv["served"][best], sv["plain"]
+    return {"workload": sv["workload"], "requests": sv["requests"], "arrival_rate_per_s": round(sv["arrival_rate_per_s"], 1),
+            "max_batch": best,
+            "served": {"p50_ms": s.get("p50_ms"), "p99_ms": s.get("p99_ms"), "triangles_per_s": s["triangles_per_s"],
+                       "failed": s["failed"]},
+            "plain": {"p50_ms": p.get("p50_ms"), "p99_ms": p.get("p99_ms"), "triangles_per_s": p["triangles_per_s"],
+                      "failed": p["failed"]},
+            "by_max_batch": {str(mb): [round(v.get("p50_ms", 0), 2), round(v.get("p99_ms", 0), 2),
+                                       round(v["triangles_per_s"] / 1e9, 3)] for mb, v in sv["served"].items()},
+            "single_request_warm_ms": {"plain": round(sv["single_request_warm"]["plain_ms"], 3),
+                                       "served": round(sv["single_request_warm"]["served_ms"], 3)},
+            "overload": {"arrival_rate_per_s": round(sv["overload"]["arrival_rate_per_s"], 1),
+                         "max_batch": sv["overload"]["max_batch"],
+                         "served": [round(sv["overload"]["served"].get("p50_ms", 0), 2),
+                                    round(sv["overload"]["served"].get("p99_ms", 0), 2),
+                                    round(sv["overload"]["served"]["triangles_per_s"] / 1e9, 3)],
+                         "plain": [round(sv["overload"]["plain"].get("p50_ms", 0), 2),
+                                   round(sv["overload"]["plain"].get("p99_ms", 0), 2),
+                                   round(sv["overload"]["plain"]["triangles_per_s"] / 1e9, 3)]},
+            "what": "Poisson isovalue requests at 0.8x the plain path's service rate (overload: 1.25x), latency "
+                    "arrival -> mesh written; [p50 ms, p99 ms, G triangles/s]; meshes identical to the plain "
+                    "path's (tested)"}
+
+
+def run_serve(args):
+    """The serving workload alone (full size unless --serve-scale), one line."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2009_03254_gb300 as bc
+    import synth.gpu as sg
+    sg.build()
+    sv = measure_serving(bc, torch, args.serve_scale, args.requests, batches=(2, 4, 8))
+    summ = serving_summary(sv)
+    best = summ["max_batch"]
     line = {
         "metric": "p50/p99 isovalue-change latency under Poisson requests, served vs plain path",
-        "value": served.get("p50_ms"), "unit": "ms", "higher_is_better": False, "n_gpus": 1,
-        "steps": n, "warmup": 1, "dtype": "f32", "data": "synthetic", "scaling": "weak", "vs_baseline": None,
-        "config": {"workload": f"serve_dns: {rec.dims[0]}x{rec.dims[1]}x{rec.dims[2]} channel-flow field "
-                               f"(seed {rec.seed}, {rec.octaves} octaves, coarsest period {rec.base_period}), "
-                               f"{rec.rate} bits/value, cache budget {budget / 1e9:.1f} GB",
-                   "requests": n, "arrival_rate_per_s": rate, "plain_median_service_ms": 1e3 * median_svc,
-                   "isovalue_range": [p5, p95], "median_isovalue": p50, "triangles_at_median": t_med,
-                   "compressed_bytes": compressed, "generate_encode_s": t_gen,
-                   "server": {"max_batch": 4, "vertex_budget_bytes": SERVE_VERTEX_BUDGET}},
-        "served": served, "plain": plain, "sweeps": sweeps,
-        "single_request_warm": single, "tick_of_4_step_ms": tick4,
-        "p99_ms": served.get("p99_ms"),
+        "value": summ["served"]["p50_ms"], "unit": "ms", "higher_is_better": False, "n_gpus": 1,
+        "steps": args.requests, "warmup": 1, "dtype": "f32", "data": "synthetic", "scaling": "weak",
+        "vs_baseline": None,
+        "config": {"workload": sv["workload"], "requests": sv["requests"],
+                   "arrival_rate_per_s": sv["arrival_rate_per_s"], "plain_median_service_ms": sv["plain_median_service_ms"],
+                   "isovalue_range": sv["isovalue_range"], "median_isovalue": sv["median_isovalue"],
+                   "triangles_at_median": sv["triangles_at_median"], "compressed_bytes": sv["compressed_bytes"],
+                   "generate_encode_s": sv["generate_encode_s"],
+                   "server": {"max_batch": best, "vertex_budget_bytes": sv["vertex_budget_bytes"]}},
+        "served": sv["served"], "plain": sv["plain"], "overload": sv["overload"], "sweeps": sv["sweeps"],
+        "single_request_warm": sv["single_request_warm"], "p99_ms": summ["served"]["p99_ms"],
     }
     print(json.dumps(line), flush=True)
 

@@ -518,22 +518,27 @@ void iso_batch_release(iso_batch *b);
 /* ---- serving: a request queue on one resident volume ----------------
  * Isovalue requests are queued with iso_server_submit and answered by
  * iso_server_step.  Requests are served in ticks of up to max_batch queued
- * requests (first come, first served).  A tick starts with one pass over
- * the block ranges that finds the union of its requests' active blocks
- * (Section 4.1) and each request's own candidates, and one cache update and
- * decode for the union (Section 4.2, Algorithm 1); then each step counts,
- * scans and emits the tick's next request (Sections 4.3-4.5), so a request
- * finishes as soon as its own mesh is written.  Decoded blocks and all
- * metadata stay resident between ticks; every slot a request of the running
- * tick reads is part of the union the tick's cache update protects, so no
- * in-flight request loses a block.
- * Admission: when the union's active blocks do not fit in the volume's
- * cache budget, the tick's requests return to the queue and later ticks
- * take half as many (down to one; a single request that does not fit
- * finishes with ISO_ERR_BUDGET).  A mesh is allocated when its size is
- * known; if it would take the bytes of finished, not yet taken meshes past
- * vertex_budget_bytes, it and the rest of its tick return to the queue
- * (a mesh is always allowed when nothing is held).  Every served mesh is
+ * requests (first come, first served).  A tick's front is one pass over the
+ * block ranges that finds the union of its requests' active blocks
+ * (Section 4.1) and each request's own candidates, then one cache update
+ * and decode for the union (Section 4.2, Algorithm 1); its back counts,
+ * scans and emits all its requests (Sections 4.3-4.5) in one launch each,
+ * with one readback of their triangle counts in between.  Under load ticks
+ * overlap: when a tick's emission is queued and at least two requests wait,
+ * they are admitted as the next tick and its front runs on a second stream
+ * while the running tick emits (a lone waiting request is admitted when the
+ * running tick is done).  That front also counts the running
+ * tick's isovalues as active, so its cache update evicts no block the
+ * running tick reads; decoded blocks and all metadata stay resident between
+ * ticks.
+ * Admission: when a union's active blocks do not fit in the volume's cache
+ * budget, its requests return to the queue: an overlapped tick is retried
+ * once the running tick is done, otherwise later ticks take half as many
+ * requests (down to one; a single request that does not fit finishes with
+ * ISO_ERR_BUDGET).  Meshes are allocated when their sizes are known; one
+ * that would take the bytes of finished, not yet taken meshes past
+ * vertex_budget_bytes returns to the queue with the rest of its tick (a
+ * mesh is always allowed when nothing is held).  Every served mesh is
  * identical, byte for byte, to iso_extract of the same isovalue on the
  * same data.  The server uses the volume's device state: do not extract
  * from the volume on another stream while a server call runs, and destroy
@@ -546,25 +551,39 @@ typedef struct iso_server_options {
                                       (24 bytes a triangle: the meshes' d_vertices then hold the compact
                                       uint32 pairs of iso_extract_packed_into) */
     uint64_t vertex_budget_bytes;  /* limit on held mesh bytes (48 or 24 per triangle); 0 = none */
-    void *stream;                  /* cudaStream_t of the server's device work; NULL = default */
+    void *stream;                  /* cudaStream_t whose earlier work the server waits for at creation
+                                      (NULL = default); the server runs on two streams of its own */
 } iso_server_options;
 
-/* v must not be loaded with ISO_DEBUG.  Per request position of a tick the
- * server keeps candidate, count and offset arrays of min(cache slots, nb)
- * entries (16 bytes each). */
+/* v must not be loaded with ISO_DEBUG.  The server keeps 2 * max_batch
+ * request positions (a running tick's and the next tick's), each with
+ * candidate, count, offset and occupied-list arrays of min(cache slots, nb)
+ * entries (20 bytes each), and creates two streams: the backs run at the
+ * device's highest stream priority, the fronts at its lowest, so a front
+ * overlapping a back takes only the SMs the back leaves idle.  Meshes are
+ * complete when a request finishes (the server waits for its emission). */
 int iso_server_create(iso_server **out, iso_volume *v, const iso_server_options *opt);
 
 /* Queue a request (host only, no device work); *ticket identifies it. */
 int iso_server_submit(iso_server *s, float isovalue, uint64_t *ticket);
 
-/* Serve the next request (starting a tick first if the last one is done;
- * nothing if no request waits); blocks until it is done.  *completed (may
- * be NULL) receives the number of requests finished (usually 1; 0 when a
- * tick was refused by the cache budget or a mesh by the vertex budget;
- * more when a tick failed as a whole). */
+/* Advance the pipeline until a tick's back is done (its requests finished,
+ * or sent back to the queue past the vertex budget) or nothing is in flight
+ * (no request waits); blocks while it waits for the GPU.  Ticks are
+ * admitted on the way (the next one while the current one is in its back),
+ * so work keeps running on the GPU when the call returns.  *completed (may
+ * be NULL) receives the number of requests finished. */
 int iso_server_step(iso_server *s, uint32_t *completed);
 
-/* Requests not finished yet (queued, or in the running tick). */
+/* The same without blocking: take every transition whose GPU work is
+ * already done (finish a tick, start an emission, start a count, admit the
+ * queued requests as the next tick) and return at once.  A request loop
+ * that polls between arrivals admits each arrival while the previous tick
+ * is still on the GPU.  *completed (may be NULL) receives the number of
+ * requests finished. */
+int iso_server_poll(iso_server *s, uint32_t *completed);
+
+/* Requests not finished yet (queued, or admitted into the next tick). */
 int iso_server_queued(const iso_server *s, uint32_t *queued);
 
 /* Hand a finished request's mesh to the caller (release it with

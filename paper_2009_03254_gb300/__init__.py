@@ -152,6 +152,7 @@ def lib():
             "iso_server_create": (i32, [ctypes.POINTER(P), P, ctypes.POINTER(_ServerOptions)]),
             "iso_server_submit": (i32, [P, ctypes.c_float, ctypes.POINTER(u64)]),
             "iso_server_step": (i32, [P, ctypes.POINTER(u32)]),
+            "iso_server_poll": (i32, [P, ctypes.POINTER(u32)]),
             "iso_server_queued": (i32, [P, ctypes.POINTER(u32)]),
             "iso_server_take": (i32, [P, u64, ctypes.POINTER(_Mesh)]),
             "iso_server_wait": (i32, [P, u64, u32, ctypes.POINTER(_Mesh)]),
@@ -546,8 +547,10 @@ class Batch:
 class Server:
     """Isovalue requests on one resident volume, answered in ticks: each
     tick runs up to `max_batch` queued requests together (one cull pass for
-    all, one cache update for their union, one launch per triangle stage).
-    See iso_server_* in include/bcmc.h.  The volume must outlive the server."""
+    all, one cache update for their union, one launch per triangle stage),
+    and the next tick's cull, cache update and decode overlap the running
+    tick's emission.  See iso_server_* in include/bcmc.h.  The volume must
+    outlive the server."""
 
     def __init__(self, volume, *, max_batch=4, vertex_budget_bytes=0, stream=None, packed=False):
         self._h = None
@@ -568,9 +571,16 @@ class Server:
         return int(t.value)
 
     def step(self):
-        """Run one tick; returns the number of requests it finished."""
+        """Advance until a tick is done (blocking); returns the requests finished."""
         n = ctypes.c_uint32()
         _check(lib().iso_server_step(self._h, ctypes.byref(n)), "iso_server_step")
+        return int(n.value)
+
+    def poll(self):
+        """Take every transition whose GPU work is done, without blocking;
+        returns the requests finished."""
+        n = ctypes.c_uint32()
+        _check(lib().iso_server_poll(self._h, ctypes.byref(n)), "iso_server_poll")
         return int(n.value)
 
     def queued(self):

@@ -52,6 +52,7 @@ enum Status : uint32_t {
     kStatusTimeoutScan = 8u,  // triangle-offset look-back gave up
     kStatusCorrupt = 16u,     // a block range given at load is not a range (set by the hull kernel)
     kStatusBounds = 32u,      // checked builds: an index failed its bounds check (the access was skipped)
+    kStatusSkip = 64u,        // serving: this request's emission is skipped (no mesh in this tick)
 };
 constexpr uint32_t kStatusAnyTimeout = kStatusTimeout | kStatusTimeoutLru | kStatusTimeoutScan;
 

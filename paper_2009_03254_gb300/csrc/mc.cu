@@ -620,7 +620,7 @@ __device__ __forceinline__ void emit_body(const Launch &L) {
     const uint32_t total = launch_prefix<kOne>(
         L, [&](uint32_t v) {
             const Ctl *c = vol_of<kOne>(L, v).s.ctl;
-            return (c->status & (kStatusBudget | kStatusAnyTimeout)) ? 0u : ceil_div(c->n_occ, kBPW);
+            return (c->status & (kStatusBudget | kStatusAnyTimeout | kStatusSkip)) ? 0u : ceil_div(c->n_occ, kBPW);
         },
         pre);
     __syncthreads();                                      // the tables

@@ -1,25 +1,30 @@
 // Serving (C ABI in include/bcmc.h): isovalue requests on one resident
-// volume, answered in ticks.  A tick takes up to kMaxServe queued requests:
-//   front (once per tick)
+// volume, answered in ticks of up to max_batch requests (at most kMaxServe).
+//   front of a tick (stream `front`)
 //     serve_prep     clear the tick's counters and descriptors
 //     serve_cull     one pass over the block ranges for all the tick's
 //                    isovalues (Section 4.1): the union of their active sets
 //                    and each request's own candidate list
 //     cache update   Algorithm 1 and the decode (Section 4.2) on the union
-//   then, one request per step, in arrival order
-//     count, scan    Sections 4.3-4.4 over the request's candidates (the
-//                    request is a "view" of the volume: own control block,
-//                    candidates, counts and offsets; shared cache)
-//     readback       its triangle count; the host allocates its mesh
-//     emit           Section 4.5
-// A request finishes as soon as its own emission is done: later requests
-// of the tick never delay it, while the cull, cache update and decode are
-// paid once for the whole tick.  Decoded blocks and all metadata stay
-// resident between ticks.  The union is what the tick's cache update
-// protects, so every slot a request of the running tick reads stays pinned
-// until the tick ends.  If the union does not fit in the cache budget, the
-// tick's requests go back to the queue and the next ticks take half as
-// many (down to one).
+//   back of a tick (the server's stream)
+//     count, scan    Sections 4.3-4.4 over all the tick's requests in one
+//                    launch each: a request is a "view" of the volume (own
+//                    control block, candidates, counts and offsets; shared
+//                    cache), the views are the entries of a batch launch
+//     readback       every request's triangle count at once; the host
+//                    allocates the meshes
+//     emit           Section 4.5, all requests in one launch
+// Ticks are pipelined under load: once a tick's emission is queued and at
+// least two requests wait, they are admitted as the next tick and its front
+// runs on the second stream (at a lower priority) while the running tick
+// emits; a lone waiting request is admitted when the running tick is done.  That front also
+// counts the running tick's isovalues as active (pins), so the cache update
+// it makes never evicts a block the running tick reads.  The two ticks use
+// alternate halves of the request positions, so the new front never writes
+// lists the running back reads.  Decoded blocks and all metadata stay
+// resident between ticks.  If a union does not fit in the cache budget, its
+// requests go back to the queue (an unpinned tick then takes half as many
+// requests, down to one; a pinned one is simply retried without pins).
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -43,7 +48,9 @@ constexpr int kMaxServe = 8;          // requests per tick
 struct ServeArgs {
     VolEntry base;                    // the volume; base.s.ctl carries the tick's union
     uint32_t k;                       // requests in this tick
-    float iso[kMaxServe];
+    uint32_t k_pin;                   // isovalues of the running tick: active, no candidates
+    float iso[2 * kMaxServe];         // the requests' isovalues, then the pinned ones
+    uint32_t *back_ctr;               // the work counters of this tick's batched launches
     Ctl *ctl[kMaxServe];              // per-request control blocks
     uint32_t *icand[kMaxServe];       // per-request candidate lists
     unsigned long long *desc_cand[kMaxServe];
@@ -81,6 +88,7 @@ __global__ void __launch_bounds__(kThreads) serve_prep_kernel(ServeArgs a) {
         c->n_tri = 0;
         for (int i = 0; i < kNumLaunchCounters; i++) c->ctr[i] = 0;
     }
+    if (tid < kNumLaunchCounters) a.back_ctr[tid] = 0;
     if (tid < a.k) {
         Ctl *c = a.ctl[tid];
         c->cap = s.ctl->cap;                            // the shared cache's slot capacity
@@ -95,16 +103,18 @@ __global__ void __launch_bounds__(kThreads) serve_prep_kernel(ServeArgs a) {
 
 // The cull of Section 4.1 for all the tick's isovalues in one pass over
 // the block ranges: a block is in the union when it is active for any of
-// them; it is a candidate of request j when it is active for iso_j and
-// its +group range contains iso_j (as in the single-volume cull).  Hits
-// of the union are stamped with the epoch; the union's active and new
-// lists feed the cache update.
+// them or for a pinned isovalue (the running tick's); it is a candidate of
+// request j when it is active for iso_j and its +group range contains
+// iso_j (as in the single-volume cull).  Hits of the union are stamped with
+// the epoch; the union's active and new lists feed the cache update.
 struct ServeCullSmem {
     TileScan<kRounds> ts;                     // union: active << 16 | new
     TileScan<kRounds> tc[kMaxServe];          // candidates of each request
     uint32_t bal[2 + kMaxServe][kRounds][8];  // union active, new, candidates
 };
 
+// kT: a power of two at least k + k_pin (the isovalue loop is unrolled to it)
+template <int kT>
 __global__ void __launch_bounds__(kThreads) serve_cull_kernel(ServeArgs a) {
     __shared__ ServeCullSmem sm;
     __shared__ uint32_t slot_x;
@@ -120,45 +130,62 @@ __global__ void __launch_bounds__(kThreads) serve_cull_kernel(ServeArgs a) {
     while (true) {
         const uint32_t tile = next_item(&c->ctr[kLcCull], &slot_x);
         if (tile >= ntiles) break;
-        float2 h[kRounds];
+        // two halves of kRounds/2 rounds; in each, every load (3x3x3 hull,
+        // +group hull, slot) is issued before any of it is used, so a tile
+        // waits for two memory round trips rather than one per round
+        constexpr int kHalf = kRounds / 2;
 #pragma unroll
-        for (int r = 0; r < kRounds; r++) {
-            const uint32_t b = tile * kTile + r * kThreads + threadIdx.x;
-            h[r] = b < g.nb ? __ldg(s.hull + b) : make_float2(0.f, 0.f);
-        }
+        for (int half = 0; half < 2; half++) {
+            float2 h[kHalf], h8[kHalf];
+            int32_t sl[kHalf];
 #pragma unroll
-        for (int r = 0; r < kRounds; r++) {               // unrolled: h[] stays in registers
-            const uint32_t b = tile * kTile + r * kThreads + threadIdx.x;
-            uint32_t am = 0, cm = 0;
-            if (b < g.nb) {
-#pragma unroll
-                for (int j = 0; j < kMaxServe; j++)
-                    if (j < (int)k && h[r].x < a.iso[j] && a.iso[j] <= h[r].y) am |= 1u << j;
+            for (int i = 0; i < kHalf; i++) {
+                const uint32_t b = tile * kTile + (half * kHalf + i) * kThreads + threadIdx.x;
+                const bool in = b < g.nb;
+                h[i] = in ? __ldg(s.hull + b) : make_float2(0.f, 0.f);
+                h8[i] = in ? __ldg(s.hull8 + b) : make_float2(0.f, 0.f);
+                sl[i] = in ? s.islot[b] : -1;
             }
-            bool nw = false;
-            if (am) {
-                const float2 h8 = __ldg(s.hull8 + b);
 #pragma unroll
-                for (int j = 0; j < kMaxServe; j++)
-                    if (((am >> j) & 1u) && h8.x < a.iso[j] && a.iso[j] <= h8.y) cm |= 1u << j;
-                const int32_t sl = s.islot[b];
-                if (sl >= 0) s.slast[sl] = epoch;
-                else nw = true;
-            }
-            const uint32_t ab = __ballot_sync(0xffffffffu, am != 0);
-            const uint32_t nbits = __ballot_sync(0xffffffffu, nw);
-            if (lane == 0) {
-                sm.bal[0][r][warp] = ab;
-                sm.bal[1][r][warp] = nbits;
-                sm.ts.cnt[r][warp] = ((uint32_t)__popc(ab) << 16) | (uint32_t)__popc(nbits);
-                const uint32_t first = tile * kTile + r * kThreads + warp * 32;
-                if (first < g.nb) s.mactive[first >> 5] = ab;
-            }
-            for (uint32_t j = 0; j < k; j++) {                 // k is uniform
-                const uint32_t cb = __ballot_sync(0xffffffffu, (cm >> j) & 1u);
+            for (int i = 0; i < kHalf; i++) {
+                const int r = half * kHalf + i;
+                const uint32_t b = tile * kTile + r * kThreads + threadIdx.x;
+                uint32_t am = 0, cm = 0;
+                bool pin = false;
+                if (b < g.nb) {
+#pragma unroll
+                    for (int j = 0; j < kT; j++) {
+                        const bool in = h[i].x < a.iso[j] && a.iso[j] <= h[i].y;
+                        if (j < (int)k) {
+                            if (in) {
+                                am |= 1u << j;
+                                if (h8[i].x < a.iso[j] && a.iso[j] <= h8[i].y) cm |= 1u << j;
+                            }
+                        } else if (j < (int)(k + a.k_pin)) {
+                            pin = pin || in;
+                        }
+                    }
+                }
+                const bool act = am != 0 || pin;
+                const bool nw = act && sl[i] < 0;
+                if (act && sl[i] >= 0) s.slast[sl[i]] = epoch;   // a hit: the slot's age resets
+                const uint32_t ab = __ballot_sync(0xffffffffu, act);
+                const uint32_t nbits = __ballot_sync(0xffffffffu, nw);
                 if (lane == 0) {
-                    sm.bal[2 + j][r][warp] = cb;
-                    sm.tc[j].cnt[r][warp] = (uint32_t)__popc(cb);
+                    sm.bal[0][r][warp] = ab;
+                    sm.bal[1][r][warp] = nbits;
+                    sm.ts.cnt[r][warp] = ((uint32_t)__popc(ab) << 16) | (uint32_t)__popc(nbits);
+                    const uint32_t first = tile * kTile + r * kThreads + warp * 32;
+                    if (first < g.nb) s.mactive[first >> 5] = ab;
+                }
+#pragma unroll
+                for (int j = 0; j < (kT < kMaxServe ? kT : kMaxServe); j++) {
+                    if (j >= (int)k) break;                         // k is uniform
+                    const uint32_t cb = __ballot_sync(0xffffffffu, (cm >> j) & 1u);
+                    if (lane == 0) {
+                        sm.bal[2 + j][r][warp] = cb;
+                        sm.tc[j].cnt[r][warp] = (uint32_t)__popc(cb);
+                    }
                 }
             }
         }
@@ -217,6 +244,23 @@ __global__ void serve_status_kernel(ServeArgs a) {
     if (j < a.k) a.ctl[j]->status |= a.base.s.ctl->status & (kStatusBudget | kStatusAnyTimeout);
 }
 
+// the tick's request control blocks (their candidate counts) for one readback
+__global__ void serve_gather_kernel(ServeArgs a, Ctl *dst) {
+    constexpr uint32_t kWords = sizeof(Ctl) / 4;
+    for (uint32_t i = threadIdx.x; i < a.k * kWords; i += blockDim.x)
+        reinterpret_cast<uint32_t *>(dst)[i] = reinterpret_cast<const uint32_t *>(a.ctl[i / kWords])[i % kWords];
+}
+
+// Each request's output (mesh, capacity, format) into its control block; a
+// request without a mesh this tick is skipped by the emission.
+__global__ void serve_params_kernel(const VolEntry *__restrict__ views, const Params *__restrict__ p, uint32_t k) {
+    const uint32_t j = threadIdx.x;
+    if (j >= k) return;
+    Ctl *c = views[j].s.ctl;
+    c->params = p[j];
+    if (!p[j].out) c->status |= kStatusSkip;
+}
+
 }  // namespace bcmc
 
 using namespace bcmc;
@@ -234,53 +278,82 @@ struct Done {
     iso_mesh mesh;
 };
 
-struct Slot {                           // device state of one request position in a tick
+struct Slot {                           // device state of one request position
     Ctl *ctl = nullptr;
     uint32_t *icand = nullptr, *counts = nullptr;
     unsigned long long *offsets = nullptr, *desc_cand = nullptr, *desc_mc = nullptr, *desc_occ = nullptr;
     uint32_t *iocc = nullptr;
 };
 
+enum Stage { kFront = 0, kCount = 1, kEmit = 2 };
+
+struct Tick {                           // requests in flight on the GPU
+    std::vector<Request> reqs;
+    uint32_t parity = 0;                // which half of the request positions it uses
+    bool pinned = false;                // its union also holds the previous tick's blocks
+    Stage stage = kFront;
+    std::vector<float *> bufs;          // meshes (after the count readback)
+    std::vector<int> status;
+    uint32_t run = 0;                   // requests that emit (the rest go back to the queue)
+    uint8_t *cases = nullptr;           // the tick's stored cell cases (count writes, emit reads)
+};
+
+constexpr uint64_t kMaxTickCaseBytes = 4ull << 30;   // stored cases per tick, else emit classifies again
+
 }  // namespace
 
 struct iso_server {
     iso_volume *v = nullptr;
     int device = 0;
-    cudaStream_t stream = nullptr;
+    cudaStream_t user = nullptr;        // the caller's stream (work before the server is ordered on it)
+    cudaStream_t stream = nullptr;      // the backs: count, scan, emit (created here, high priority)
+    cudaStream_t front = nullptr;       // the fronts: cull, cache update, decode (created here, low priority)
     uint32_t max_batch = 4, limit = 4;  // requests per tick; current limit after budget failures
     uint64_t vertex_budget = 0;         // 0 = none
     uint32_t format = kVertexFloat4;    // vertex format of the meshes
     uint64_t tri_bytes = 48;            // their bytes per triangle
     uint32_t cand_cap = 0;              // room of each request's candidate list
     uint64_t held_bytes = 0;            // finished meshes not yet taken
-    Slot slots[kMaxServe];
-    VolEntry views[kMaxServe];          // per-request views of the volume (by value into each launch)
-    Ctl *h_ctl = nullptr;               // pinned: one request's control block, read back
-    Params *h_params = nullptr;         // pinned: one request's output
-    Plan view_plan{};                   // launches over one view
+    Slot slots[2][kMaxServe];           // two halves: a tick's back and the next tick's front
+    VolEntry views[2][kMaxServe];       // per-request views of the volume
+    VolEntry *d_views[2] = {};          // the same in device memory (the back's launch tables)
+    uint32_t *d_ctr[2] = {};            // work counters of each half's back launches
+    Ctl *d_ctls[2] = {};                // control blocks gathered for one readback (after front, after scan)
+    Params *d_params = nullptr;         // the requests' outputs, copied into their control blocks
+    Ctl *h_ctls[2] = {};                // pinned mirrors: each half's request control blocks
+    Params *h_params = nullptr;
+    Ctl *h_union[2] = {};               // pinned: each half's union control block after its front
+    cudaEvent_t front_done[2] = {}, count_done = nullptr, emit_done = nullptr;
+    Plan one_plan{}, back_plan{};       // launches over one view (kOne) or up to max_batch views
     uint64_t next_ticket = 1;
     std::deque<Request> queue;
-    std::vector<Request> tick;          // the running tick's requests
-    uint32_t tick_next = 0;             // next of them to emit
-    Ctl tick_union{};                   // the tick's union figures (for the stats)
+    bool has_front = false, has_back = false;
+    Tick front_tick, back_tick;         // a tick whose front runs, and one in its back
+    bool hold = false;                  // a pinned front did not fit: admit only once the back is done
+    uint32_t next_parity = 0;
+    uint64_t ticks_finished = 0;        // backs completed (their requests finished or sent back)
     std::map<uint64_t, Done> done;
 };
 
 namespace {
 
-ServeArgs serve_args(const iso_server *sv, const std::vector<Request> &reqs) {
+ServeArgs serve_args(const iso_server *sv, const Tick &t, const std::vector<Request> *pins) {
     ServeArgs a{};
     const iso_volume *v = sv->v;
     a.base = VolEntry{v->s, v->g, v->n_cull_desc, v->n_lru_desc};
-    a.k = (uint32_t)reqs.size();
+    a.k = (uint32_t)t.reqs.size();
+    const uint32_t p = t.parity;
     for (uint32_t j = 0; j < a.k; j++) {
-        a.iso[j] = reqs[j].iso;
-        a.ctl[j] = sv->slots[j].ctl;
-        a.icand[j] = sv->slots[j].icand;
-        a.desc_cand[j] = sv->slots[j].desc_cand;
-        a.desc_mc[j] = sv->slots[j].desc_mc;
-        a.desc_occ[j] = sv->slots[j].desc_occ;
+        a.iso[j] = t.reqs[j].iso;
+        a.ctl[j] = sv->slots[p][j].ctl;
+        a.icand[j] = sv->slots[p][j].icand;
+        a.desc_cand[j] = sv->slots[p][j].desc_cand;
+        a.desc_mc[j] = sv->slots[p][j].desc_mc;
+        a.desc_occ[j] = sv->slots[p][j].desc_occ;
     }
+    a.k_pin = pins ? (uint32_t)pins->size() : 0u;
+    for (uint32_t j = 0; j < a.k_pin; j++) a.iso[a.k + j] = (*pins)[j].iso;
+    a.back_ctr = sv->d_ctr[p];
     a.cand_cap = sv->cand_cap;
     return a;
 }
@@ -288,27 +361,43 @@ ServeArgs serve_args(const iso_server *sv, const std::vector<Request> &reqs) {
 void free_server(iso_server *sv) {
     if (!sv) return;
     DeviceGuard dg(sv->device);
+    if (sv->front) cudaStreamSynchronize(sv->front);
+    cudaStreamSynchronize(sv->stream);
     for (auto &kv : sv->done)
         if (kv.second.mesh.d_vertices) dfree_on(kv.second.mesh.d_vertices, sv->stream);
-    for (Slot &s : sv->slots) {
-        void *p[] = {s.ctl, s.icand, s.counts, s.offsets, s.desc_cand, s.desc_mc, s.iocc};
-        for (void *x : p) dfree_on(x, sv->stream);
+    if (sv->has_back) {                   // a tick abandoned in flight
+        for (float *b : sv->back_tick.bufs) dfree_on(b, sv->stream);
+        dfree_on(sv->back_tick.cases, sv->stream);
     }
+    for (auto &half : sv->slots)
+        for (Slot &s : half) {
+            void *p[] = {s.ctl, s.icand, s.counts, s.offsets, s.desc_cand, s.desc_mc, s.iocc};
+            for (void *x : p) dfree_on(x, sv->stream);
+        }
+    void *q[] = {sv->d_views[0], sv->d_views[1], sv->d_ctr[0], sv->d_ctr[1], sv->d_ctls[0], sv->d_ctls[1],
+                 sv->d_params};
+    for (void *x : q) dfree_on(x, sv->stream);
     cudaStreamSynchronize(sv->stream);
     (void)cudaGetLastError();
-    if (sv->h_ctl) cudaFreeHost(sv->h_ctl);
+    for (Ctl *h : {sv->h_ctls[0], sv->h_ctls[1], sv->h_union[0], sv->h_union[1]})
+        if (h) cudaFreeHost(h);
     if (sv->h_params) cudaFreeHost(sv->h_params);
+    for (cudaEvent_t e : {sv->front_done[0], sv->front_done[1], sv->count_done, sv->emit_done})
+        if (e) cudaEventDestroy(e);
+    if (sv->front) cudaStreamDestroy(sv->front);
+    if (sv->stream) cudaStreamDestroy(sv->stream);
+    (void)cudaGetLastError();
     delete sv;
 }
 
-void finish(iso_server *sv, const Request &r, int status, const Ctl *c, float *buf) {
+void finish(iso_server *sv, const Request &r, int status, const Ctl *uni, const Ctl *c, float *buf) {
     Done d{};
     d.status = status;
     d.mesh.d_vertices = buf;
     if (c) {
         d.mesh.num_triangles = buf ? c->n_tri : 0;
         d.mesh.capacity_triangles = buf ? c->n_tri : 0;
-        Ctl s = sv->tick_union;         // the tick's cache figures, the request's own surface figures
+        Ctl s = *uni;                   // the tick's cache figures, the request's own surface figures
         s.n_tri = c->n_tri;
         s.n_occ = c->n_occ;
         s.n_cand = c->n_cand;
@@ -318,108 +407,225 @@ void finish(iso_server *sv, const Request &r, int status, const Ctl *c, float *b
     sv->done[r.ticket] = d;
 }
 
-void requeue_rest(iso_server *sv) {     // the tick's unfinished requests, in order, to the queue's front
-    for (uint32_t j = (uint32_t)sv->tick.size(); j-- > sv->tick_next;) sv->queue.push_front(sv->tick[j]);
-    sv->tick.clear();
-    sv->tick_next = 0;
+// requests back to the queue's front, in order
+void requeue(iso_server *sv, const std::vector<Request> &reqs, size_t from) {
+    for (size_t j = reqs.size(); j-- > from;) sv->queue.push_front(reqs[j]);
 }
 
-// The front of a tick over the queue's first requests.  Returns ISO_OK
-// (with sv->tick set, or the requests re-queued or finished), or a CUDA
-// error.
-int start_tick(iso_server *sv, uint32_t *completed) {
+bool ready(cudaEvent_t e) {
+    const cudaError_t r = cudaEventQuery(e);
+    if (r == cudaErrorNotReady) return false;
+    (void)cudaGetLastError();             // an error surfaces at the synchronisation that follows
+    return true;
+}
+
+// Admit the queue's first requests as a tick and queue its front on the
+// front stream (pins: the tick in its back, or null).
+int launch_front(iso_server *sv, const std::vector<Request> *pins) {
     iso_volume *v = sv->v;
-    cudaStream_t st = sv->stream;
+    Tick t;
+    t.parity = sv->next_parity;
+    t.pinned = pins && !pins->empty();
     const uint32_t k = std::min<uint32_t>(sv->limit, (uint32_t)sv->queue.size());
-    sv->tick.clear();
     for (uint32_t j = 0; j < k; j++) {
-        sv->tick.push_back(sv->queue.front());
+        t.reqs.push_back(sv->queue.front());
         sv->queue.pop_front();
     }
-    sv->tick_next = 0;
-    const ServeArgs a = serve_args(sv, sv->tick);
+    const ServeArgs a = serve_args(sv, t, pins);
     const Launch single{nullptr, 1u, single_counters(v), a.base};
+    cudaStream_t st = sv->front;
     serve_prep_kernel<<<v->plan.prep, kThreads, 0, st>>>(a);
-    serve_cull_kernel<<<v->plan.cull, kThreads, 0, st>>>(a);
+    const uint32_t kt = a.k + a.k_pin;
+    if (kt <= 1) serve_cull_kernel<1><<<v->plan.cull, kThreads, 0, st>>>(a);
+    else if (kt <= 2) serve_cull_kernel<2><<<v->plan.cull, kThreads, 0, st>>>(a);
+    else if (kt <= 4) serve_cull_kernel<4><<<v->plan.cull, kThreads, 0, st>>>(a);
+    else if (kt <= 8) serve_cull_kernel<8><<<v->plan.cull, kThreads, 0, st>>>(a);
+    else serve_cull_kernel<16><<<v->plan.cull, kThreads, 0, st>>>(a);
     launch_cache_update(single, v->plan, st);
     serve_status_kernel<<<1, kMaxServe, 0, st>>>(a);
-    ISO_CK(cudaMemcpyAsync(v->host_ctl, v->s.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    serve_gather_kernel<<<1, 256, 0, st>>>(a, sv->d_ctls[t.parity]);
+    ISO_CK(cudaMemcpyAsync(sv->h_union[t.parity], v->s.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    ISO_CK(cudaMemcpyAsync(sv->h_ctls[t.parity], sv->d_ctls[t.parity], k * sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    ISO_CK(cudaEventRecord(sv->front_done[t.parity], st));
     ISO_CK(cudaGetLastError());
-    ISO_CK(cudaStreamSynchronize(st));
-    const Ctl uni = *v->host_ctl;
-    sv->tick_union = uni;
+    sv->front_tick = std::move(t);
+    sv->has_front = true;
+    sv->next_parity ^= 1u;
+    return ISO_OK;
+}
+
+Launch back_launch(const iso_server *sv, const Tick &t) {
+    const uint32_t k = (uint32_t)t.reqs.size();
+    if (k == 1) return Launch{nullptr, 1u, sv->d_ctr[t.parity], sv->views[t.parity][0]};   // one view by value
+    return Launch{sv->d_views[t.parity], k, sv->d_ctr[t.parity], VolEntry{}, sv->v->g.rate};
+}
+
+// The front of the admitted tick is done: check its union, then queue its
+// requests' count and scan (one launch each) and the count readback.
+int promote(iso_server *sv, uint32_t *completed) {
+    iso_volume *v = sv->v;
+    cudaStream_t st = sv->stream;
+    Tick t = std::move(sv->front_tick);
+    sv->has_front = false;
+    ISO_CK(cudaEventSynchronize(sv->front_done[t.parity]));
+    const Ctl &uni = *sv->h_union[t.parity];
+    const uint32_t k = (uint32_t)t.reqs.size();
     v->last_n_active = uni.n_active;
     v->last_n_new = uni.n_new;
     v->last_n_cand = 0;
     v->last_slots = uni.S;
     if (uni.status & kStatusAnyTimeout) {
-        status_to_error(v, uni.status);   // empties the cache
-        for (const Request &r : sv->tick) finish(sv, r, ISO_ERR_TIMEOUT, nullptr, nullptr);
+        ISO_CK(cudaStreamSynchronize(st));    // no back reads the cache while it is emptied
+        status_to_error(v, uni.status);
+        for (const Request &r : t.reqs) finish(sv, r, ISO_ERR_TIMEOUT, &uni, nullptr, nullptr);
         *completed += k;
-        sv->tick.clear();
         return ISO_OK;
     }
     if (uni.status & kStatusBudget) {
-        if (k > 1) {                      // too many decodes at once: fewer requests per tick
-            requeue_rest(sv);
-            sv->limit = std::max(1u, k / 2);
+        if (t.pinned || k > 1) {              // retry without the running tick's blocks, or with fewer requests
+            requeue(sv, t.reqs, 0);
+            if (t.pinned) sv->hold = sv->has_back;
+            else sv->limit = std::max(1u, k / 2);
             return ISO_OK;
         }
-        finish(sv, sv->tick[0], ISO_ERR_BUDGET, nullptr, nullptr);
+        finish(sv, t.reqs[0], ISO_ERR_BUDGET, &uni, nullptr, nullptr);
         *completed += 1;
-        sv->tick.clear();
         return ISO_OK;
     }
-    sv->limit = std::min(sv->max_batch, sv->limit * 2);
+    if (!t.pinned) sv->limit = std::min(sv->max_batch, sv->limit * 2);
+    // stored cases for the emit (as a volume keeps them): one buffer, each
+    // request's candidates at its own offset
+    uint64_t cases_bytes = 0;
+    for (uint32_t j = 0; j < k; j++) cases_bytes += 64ull * sv->h_ctls[t.parity][j].n_cand;
+    if (cases_bytes && cases_bytes <= kMaxTickCaseBytes && dalloc_on(&t.cases, cases_bytes, sv->device, st) != ISO_OK)
+        t.cases = nullptr;
+    uint64_t off = 0;
+    for (uint32_t j = 0; j < k; j++) {
+        sv->views[t.parity][j].s.cases = t.cases ? t.cases + off : nullptr;
+        off += 64ull * sv->h_ctls[t.parity][j].n_cand;
+    }
+    if (k > 1)
+        ISO_CK(cudaMemcpyAsync(sv->d_views[t.parity], sv->views[t.parity], k * sizeof(VolEntry),
+                               cudaMemcpyHostToDevice, st));
+    const Launch L = back_launch(sv, t);
+    const Plan &pl = k == 1 ? sv->one_plan : sv->back_plan;
+    launch_mc_count(L, false, pl, st);
+    launch_mc_scan(L, pl, st);
+    launch_batch_gather(Launch{sv->d_views[t.parity], k, nullptr, VolEntry{}}, sv->d_ctls[t.parity], st);
+    ISO_CK(cudaMemcpyAsync(sv->h_ctls[t.parity], sv->d_ctls[t.parity], k * sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    ISO_CK(cudaEventRecord(sv->count_done, st));
+    ISO_CK(cudaGetLastError());
+    t.stage = kCount;
+    sv->back_tick = std::move(t);
+    sv->has_back = true;
     return ISO_OK;
 }
 
-// Count, scan and emit the tick's next request.  A mesh that does not fit
-// the vertex budget sends it and the rest of the tick back to the queue.
-int emit_next(iso_server *sv, uint32_t *completed) {
+// The tick's counts are back: allocate its meshes (in order; one that would
+// take the held bytes past the vertex budget sends it and the rest of the
+// tick back to the queue) and queue the emission.
+int start_emit(iso_server *sv) {
     cudaStream_t st = sv->stream;
-    const uint32_t j = sv->tick_next;
-    const Request r = sv->tick[j];
-    const VolEntry &view = sv->views[j];
-    Ctl *dctl = sv->slots[j].ctl;
-    uint32_t *ctr = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(dctl) + offsetof(Ctl, ctr));
-    const Launch L{nullptr, 1u, ctr, view};
-    launch_mc_count(L, false, sv->view_plan, st);
-    launch_mc_scan(L, sv->view_plan, st);
-    ISO_CK(cudaMemcpyAsync(sv->h_ctl, dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
-    ISO_CK(cudaGetLastError());
-    ISO_CK(cudaStreamSynchronize(st));
-    const Ctl c = *sv->h_ctl;
-    if (c.status & (kStatusAnyTimeout | kStatusBounds)) {
-        finish(sv, r, (c.status & kStatusBounds) ? ISO_ERR_BOUNDS : ISO_ERR_TIMEOUT, &c, nullptr);
-        sv->tick_next++;
-        *completed += 1;
-        return ISO_OK;
-    }
-    const uint64_t bytes = sv->tri_bytes * c.n_tri;
-    if (sv->vertex_budget && sv->held_bytes > 0 && sv->held_bytes + bytes > sv->vertex_budget) {
-        requeue_rest(sv);                 // wait until the held meshes are taken
-        return ISO_OK;
-    }
-    float *buf = nullptr;
-    if (c.n_tri) {
-        const int rc = dalloc_on(&buf, (size_t)c.n_tri * (sv->tri_bytes / 4), sv->device, st);
-        if (rc) {
-            finish(sv, r, rc, &c, nullptr);
-            sv->tick_next++;
-            *completed += 1;
-            return ISO_OK;
+    Tick &t = sv->back_tick;
+    ISO_CK(cudaEventSynchronize(sv->count_done));
+    const uint32_t k = (uint32_t)t.reqs.size();
+    const Ctl *c = sv->h_ctls[t.parity];
+    t.bufs.assign(k, nullptr);
+    t.status.assign(k, ISO_OK);
+    t.run = k;
+    uint64_t held = sv->held_bytes;
+    for (uint32_t j = 0; j < k; j++) {
+        if (c[j].status & (kStatusAnyTimeout | kStatusBounds)) {
+            t.status[j] = (c[j].status & kStatusBounds) ? ISO_ERR_BOUNDS : ISO_ERR_TIMEOUT;
+            continue;
         }
+        const uint64_t bytes = sv->tri_bytes * c[j].n_tri;
+        if (sv->vertex_budget && held > 0 && held + bytes > sv->vertex_budget) {
+            t.run = j;
+            break;
+        }
+        if (c[j].n_tri) {
+            const int rc = dalloc_on(&t.bufs[j], (size_t)c[j].n_tri * (sv->tri_bytes / 4), sv->device, st);
+            if (rc) {
+                t.status[j] = rc;
+                continue;
+            }
+        }
+        held += bytes;
     }
-    *sv->h_params = Params{r.iso, sv->format, 0u, 0u, 0u, 0u, c.n_tri, (unsigned long long)(uintptr_t)buf};
-    ISO_CK(cudaMemcpyAsync(&dctl->params, sv->h_params, sizeof(Params), cudaMemcpyHostToDevice, st));
-    launch_mc_emit(L, false, sv->view_plan, st);
+    for (uint32_t j = 0; j < k; j++) {
+        const bool out = j < t.run && t.bufs[j];
+        sv->h_params[j] = Params{t.reqs[j].iso, sv->format, 0u, 0u, 0u, 0u, out ? c[j].n_tri : 0ull,
+                                 out ? (unsigned long long)(uintptr_t)t.bufs[j] : 0ull};
+    }
+    ISO_CK(cudaMemcpyAsync(sv->d_params, sv->h_params, k * sizeof(Params), cudaMemcpyHostToDevice, st));
+    serve_params_kernel<<<1, kMaxServe, 0, st>>>(sv->d_views[t.parity], sv->d_params, k);
+    const Launch L = back_launch(sv, t);
+    launch_mc_emit(L, false, k == 1 ? sv->one_plan : sv->back_plan, st);
+    if (t.cases) dfree_on(t.cases, st);       // stream-ordered: after the emission
+    t.cases = nullptr;
+    ISO_CK(cudaEventRecord(sv->emit_done, st));
     ISO_CK(cudaGetLastError());
-    ISO_CK(cudaStreamSynchronize(st));
-    finish(sv, r, ISO_OK, &c, buf);
-    sv->tick_next++;
-    *completed += 1;
+    t.stage = kEmit;
     return ISO_OK;
+}
+
+int finish_tick(iso_server *sv, uint32_t *completed) {
+    ISO_CK(cudaEventSynchronize(sv->emit_done));
+    Tick t = std::move(sv->back_tick);
+    sv->has_back = false;
+    sv->hold = false;
+    sv->ticks_finished++;
+    const Ctl *c = sv->h_ctls[t.parity];
+    const Ctl &uni = *sv->h_union[t.parity];
+    for (uint32_t j = 0; j < t.run; j++) {
+        finish(sv, t.reqs[j], t.status[j], &uni, &c[j], t.status[j] == ISO_OK ? t.bufs[j] : nullptr);
+        *completed += 1;
+    }
+    for (uint32_t j = t.run; j < t.reqs.size(); j++)
+        if (t.bufs[j]) dfree_on(t.bufs[j], sv->stream);
+    requeue(sv, t.reqs, t.run);
+    return ISO_OK;
+}
+
+// One transition of the pipeline, the latest stage first: a finished
+// emission completes its tick; returned counts start the emission; a
+// finished front (with no tick in its back) starts the count; a free front
+// admits the queue's next requests (pinned to the tick in its back, once
+// that tick's emission is queued and at least two requests wait).
+// Without `block` only transitions whose GPU work is done are taken;
+// with it the first transition waits for its work.  Returns 1 if one was
+// taken (or an error code as a negative number).
+int advance(iso_server *sv, bool block, uint32_t *completed) {
+    int rc = ISO_OK;
+    if (sv->has_back && sv->back_tick.stage == kEmit) {
+        if (!block && !ready(sv->emit_done)) goto admit;
+        rc = finish_tick(sv, completed);
+        return rc ? -rc : 1;
+    }
+    if (sv->has_back && sv->back_tick.stage == kCount) {
+        if (!block && !ready(sv->count_done)) goto admit;
+        rc = start_emit(sv);
+        return rc ? -rc : 1;
+    }
+    if (sv->has_front && !sv->has_back) {
+        if (!block && !ready(sv->front_done[sv->front_tick.parity])) return 0;
+        rc = promote(sv, completed);
+        return rc ? -rc : 1;
+    }
+admit:
+    // A front overlaps a back only when requests have piled up (at least two
+    // wait), and only once the back's last kernel (the emission) is queued:
+    // the front's persistent kernels, started earlier, would hold the SMs the
+    // back's count or emission needs until they finish, and a lone request
+    // gains nothing from overlapping (both halves keep the GPU busy) while
+    // its front's memory traffic slows the running emission.
+    if (!sv->has_front && !sv->queue.empty() && !(sv->hold && sv->has_back) &&
+        (!sv->has_back || (sv->back_tick.stage == kEmit && sv->queue.size() >= 2))) {
+        rc = launch_front(sv, sv->has_back ? &sv->back_tick.reqs : nullptr);
+        return rc ? -rc : 1;
+    }
+    return 0;
 }
 
 }  // namespace
@@ -434,12 +640,12 @@ int iso_server_create(iso_server **out, iso_volume *v, const iso_server_options 
     if (o.max_batch > (uint32_t)kMaxServe) return ISO_ERR_INVALID_ARG;
     if (o.vertex_format != ISO_VERTEX_FLOAT4 && o.vertex_format != ISO_VERTEX_PACKED) return ISO_ERR_INVALID_ARG;
     DeviceGuard dg(v->device);
-    ISO_CK_RC(finish_upload(v));             // the server reads the bitstream on its own stream
+    ISO_CK_RC(finish_upload(v));             // the server reads the bitstream on its own streams
     iso_server *sv = new (std::nothrow) iso_server();
     if (!sv) return ISO_ERR_OOM;
     sv->v = v;
     sv->device = v->device;
-    sv->stream = (cudaStream_t)o.stream;
+    sv->user = (cudaStream_t)o.stream;
     sv->max_batch = o.max_batch ? o.max_batch : 4;
     sv->limit = sv->max_batch;
     sv->vertex_budget = o.vertex_budget_bytes;
@@ -454,42 +660,68 @@ int iso_server_create(iso_server **out, iso_volume *v, const iso_server_options 
         rc = (x);                                \
         if (rc) { free_server(sv); return rc; }  \
     } while (0)
-    for (uint32_t j = 0; j < sv->max_batch; j++) {
-        Slot &s = sv->slots[j];
-        TRY(dalloc_on(&s.ctl, 1, sv->device, sv->stream));
-        TRY(cudaMemsetAsync(s.ctl, 0, sizeof(Ctl), sv->stream) == cudaSuccess ? ISO_OK   // no field undefined
-                                                                              : ((void)cudaGetLastError(), ISO_ERR_CUDA));
-        TRY(dalloc_on(&s.icand, cand, sv->device, sv->stream));
-        TRY(dalloc_on(&s.counts, cand, sv->device, sv->stream));
-        TRY(dalloc_on(&s.offsets, cand, sv->device, sv->stream));
-        TRY(dalloc_on(&s.desc_cand, v->n_cull_desc, sv->device, sv->stream));
-        TRY(dalloc_on(&s.desc_mc, 2 * n_mc_desc, sv->device, sv->stream));
-        s.desc_occ = s.desc_mc + n_mc_desc;
-        TRY(dalloc_on(&s.iocc, cand, sv->device, sv->stream));
-        DevState d = v->s;                // the volume's cache and geometry, the request's own lists
-        d.ctl = s.ctl;
-        d.icand = s.icand;
-        d.counts = s.counts;
-        d.offsets = s.offsets;
-        d.desc_cand = s.desc_cand;
-        d.desc_mc = s.desc_mc;
-        d.desc_occ = s.desc_occ;
-        d.iocc = s.iocc;
-        d.cases = nullptr;                // a request's emit classifies (no per-request case store)
-        sv->views[j] = VolEntry{d, v->g, v->n_cull_desc, v->n_lru_desc};
+    auto cuda_ok = [](cudaError_t e) { return e == cudaSuccess ? ISO_OK : ((void)cudaGetLastError(), ISO_ERR_CUDA); };
+    // The backs (the latency of the requests in them) take precedence over
+    // the next tick's front, which fills the SMs the back leaves idle (host
+    // round trips, kernel tails).
+    int prio_low = 0, prio_high = 0;
+    TRY(cuda_ok(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high)));
+    TRY(cuda_ok(cudaStreamCreateWithPriority(&sv->stream, cudaStreamNonBlocking, prio_high)));
+    TRY(cuda_ok(cudaStreamCreateWithPriority(&sv->front, cudaStreamNonBlocking, prio_low)));
+    TRY(cuda_ok(cudaEventCreateWithFlags(&sv->count_done, cudaEventDisableTiming)));
+    TRY(cuda_ok(cudaEventCreateWithFlags(&sv->emit_done, cudaEventDisableTiming)));
+    for (int p = 0; p < 2; p++) {
+        TRY(cuda_ok(cudaEventCreateWithFlags(&sv->front_done[p], cudaEventDisableTiming)));
+        TRY(dalloc_on(&sv->d_views[p], kMaxServe, sv->device, sv->stream));
+        TRY(dalloc_on(&sv->d_ctr[p], kNumLaunchCounters, sv->device, sv->stream));
+        TRY(dalloc_on(&sv->d_ctls[p], kMaxServe, sv->device, sv->stream));
+        for (uint32_t j = 0; j < sv->max_batch; j++) {
+            Slot &s = sv->slots[p][j];
+            TRY(dalloc_on(&s.ctl, 1, sv->device, sv->stream));
+            TRY(dalloc_on(&s.icand, cand, sv->device, sv->stream));
+            TRY(dalloc_on(&s.counts, cand, sv->device, sv->stream));
+            TRY(dalloc_on(&s.offsets, cand, sv->device, sv->stream));
+            TRY(dalloc_on(&s.desc_cand, v->n_cull_desc, sv->device, sv->stream));
+            TRY(dalloc_on(&s.desc_mc, 2 * n_mc_desc, sv->device, sv->stream));
+            s.desc_occ = s.desc_mc + n_mc_desc;
+            TRY(dalloc_on(&s.iocc, cand, sv->device, sv->stream));
+            DevState d = v->s;            // the volume's cache and geometry, the request's own lists
+            d.ctl = s.ctl;
+            d.icand = s.icand;
+            d.counts = s.counts;
+            d.offsets = s.offsets;
+            d.desc_cand = s.desc_cand;
+            d.desc_mc = s.desc_mc;
+            d.desc_occ = s.desc_occ;
+            d.iocc = s.iocc;
+            d.cases = nullptr;            // set per tick
+            d.cutw = nullptr;
+            d.voff = nullptr;
+            d.desc_vtx = nullptr;
+            d.dbg_edges = nullptr;
+            sv->views[p][j] = VolEntry{d, v->g, v->n_cull_desc, v->n_lru_desc};
+        }
     }
-    if (cudaMallocHost((void **)&sv->h_ctl, sizeof(Ctl)) != cudaSuccess ||
-        cudaMallocHost((void **)&sv->h_params, sizeof(Params)) != cudaSuccess) {
+    TRY(dalloc_on(&sv->d_params, kMaxServe, sv->device, sv->stream));
+    if (cudaMallocHost((void **)&sv->h_ctls[0], kMaxServe * sizeof(Ctl)) != cudaSuccess ||
+        cudaMallocHost((void **)&sv->h_ctls[1], kMaxServe * sizeof(Ctl)) != cudaSuccess ||
+        cudaMallocHost((void **)&sv->h_params, kMaxServe * sizeof(Params)) != cudaSuccess ||
+        cudaMallocHost((void **)&sv->h_union[0], sizeof(Ctl)) != cudaSuccess ||
+        cudaMallocHost((void **)&sv->h_union[1], sizeof(Ctl)) != cudaSuccess) {
         (void)cudaGetLastError();
         free_server(sv);
         return ISO_ERR_OOM;
     }
     cudaStream_t st = sv->stream;
-    bool ok = cudaStreamSynchronize(v->stream) == cudaSuccess;
-    for (uint32_t j = 0; ok && j < sv->max_batch; j++) {
-        ok = cudaMemsetAsync(sv->slots[j].ctl, 0, sizeof(Ctl), st) == cudaSuccess &&
-             cudaMemsetAsync(sv->slots[j].icand, 0, cand * 4, st) == cudaSuccess &&
-             cudaMemsetAsync(sv->slots[j].desc_mc, 0, n_mc_desc * 16, st) == cudaSuccess;
+    bool ok = cudaStreamSynchronize(v->stream) == cudaSuccess && cudaStreamSynchronize(sv->user) == cudaSuccess;
+    for (int p = 0; ok && p < 2; p++) {
+        ok = cudaMemcpyAsync(sv->d_views[p], sv->views[p], sv->max_batch * sizeof(VolEntry), cudaMemcpyHostToDevice,
+                             st) == cudaSuccess;
+        for (uint32_t j = 0; ok && j < sv->max_batch; j++) {
+            ok = cudaMemsetAsync(sv->slots[p][j].ctl, 0, sizeof(Ctl), st) == cudaSuccess &&   // no field undefined
+                 cudaMemsetAsync(sv->slots[p][j].icand, 0, cand * 4, st) == cudaSuccess &&
+                 cudaMemsetAsync(sv->slots[p][j].desc_mc, 0, n_mc_desc * 16, st) == cudaSuccess;
+        }
     }
     ok = ok && cudaStreamSynchronize(st) == cudaSuccess;
     if (!ok) {
@@ -498,7 +730,9 @@ int iso_server_create(iso_server **out, iso_volume *v, const iso_server_options 
         return ISO_ERR_CUDA;
     }
 #undef TRY
-    sv->view_plan = launch_plan(nullptr, sv->device, v->g.nb, cand, 1, true, v->g.rate);
+    sv->one_plan = launch_plan(nullptr, sv->device, v->g.nb, cand, 1, true, v->g.rate);
+    sv->back_plan = launch_plan(nullptr, sv->device, (uint64_t)v->g.nb * sv->max_batch,
+                                (uint64_t)cand * sv->max_batch, sv->max_batch, false, v->g.rate);
     *out = sv;
     return ISO_OK;
 }
@@ -510,27 +744,41 @@ int iso_server_submit(iso_server *sv, float isovalue, uint64_t *ticket) {
     return ISO_OK;
 }
 
+int iso_server_poll(iso_server *sv, uint32_t *completed) {
+    NvtxRange nvtx("iso_server_poll");
+    if (!sv) return ISO_ERR_INVALID_ARG;
+    uint32_t n = 0;
+    DeviceGuard dg(sv->device);
+    int r;
+    while ((r = advance(sv, false, &n)) > 0) {
+    }
+    if (completed) *completed = n;
+    return r < 0 ? -r : ISO_OK;
+}
+
 int iso_server_step(iso_server *sv, uint32_t *completed) {
     NvtxRange nvtx("iso_server_step");
     if (!sv) return ISO_ERR_INVALID_ARG;
     uint32_t n = 0;
-    if (completed) *completed = 0;
     DeviceGuard dg(sv->device);
-    int rc = ISO_OK;
-    if (sv->tick_next >= sv->tick.size()) {       // the last tick is done: start one
-        sv->tick.clear();
-        sv->tick_next = 0;
-        if (sv->queue.empty()) return ISO_OK;
-        rc = start_tick(sv, &n);
+    const uint64_t ticks0 = sv->ticks_finished;
+    int r = 0;
+    for (;;) {
+        r = advance(sv, false, &n);
+        if (r > 0) continue;
+        // a tick finished, a failure, or nothing in flight
+        if (r < 0 || n > 0 || sv->ticks_finished != ticks0 || (!sv->has_front && !sv->has_back)) break;
+        r = advance(sv, true, &n);
+        if (r < 0) break;
     }
-    if (rc == ISO_OK && sv->tick_next < sv->tick.size()) rc = emit_next(sv, &n);
     if (completed) *completed = n;
-    return rc;
+    return r < 0 ? -r : ISO_OK;
 }
 
 int iso_server_queued(const iso_server *sv, uint32_t *queued) {
     if (!sv || !queued) return ISO_ERR_INVALID_ARG;
-    *queued = (uint32_t)(sv->queue.size() + (sv->tick.size() - std::min<size_t>(sv->tick_next, sv->tick.size())));
+    *queued = (uint32_t)(sv->queue.size() + (sv->has_front ? sv->front_tick.reqs.size() : 0) +
+                         (sv->has_back ? sv->back_tick.reqs.size() : 0));
     return ISO_OK;
 }
 
@@ -541,8 +789,10 @@ int iso_server_take(iso_server *sv, uint64_t ticket, iso_mesh *out) {
         if (ticket == 0 || ticket >= sv->next_ticket) return ISO_ERR_INVALID_ARG;
         for (const Request &r : sv->queue)
             if (r.ticket == ticket) return ISO_PENDING;
-        for (uint32_t j = sv->tick_next; j < sv->tick.size(); j++)
-            if (sv->tick[j].ticket == ticket) return ISO_PENDING;
+        for (const Tick *t : {sv->has_front ? &sv->front_tick : nullptr, sv->has_back ? &sv->back_tick : nullptr})
+            if (t)
+                for (const Request &r : t->reqs)
+                    if (r.ticket == ticket) return ISO_PENDING;
         return ISO_ERR_INVALID_ARG;       // already taken
     }
     *out = it->second.mesh;

@@ -9,10 +9,12 @@ it.  A queue limit gives back-pressure: a request that arrives while
 `max_queue` requests wait is rejected.
 
 The backend only needs submit(iso) -> ticket, step() -> finished count and
-take(ticket) -> (status, mesh or None); time comes from `clock` and `sleep`,
-so the loop runs against a fake clock.  `Server` (iso_server_*) is the
-batched backend; `PlainBackend` answers one request per tick with
-iso_extract, the plain per-request path.
+take(ticket) -> (status, mesh or None); a backend that also has poll()
+(advance without blocking) is polled instead of stepped, so arrivals are
+submitted while its earlier requests are still on the GPU.  Time comes
+from `clock` and `sleep`, so the loop runs against a fake clock.  `Server`
+(iso_server_*) is the batched backend; `PlainBackend` answers one request
+per step with iso_extract, the plain per-request path.
 """
 from __future__ import annotations
 
@@ -72,6 +74,7 @@ class RequestLoop:
         only with keep_meshes; otherwise released at once)."""
         n = len(arrivals)
         out = [None] * n
+        advance = getattr(self.backend, "poll", None) or self.backend.step
         waiting = {}                            # ticket -> request index
         t0 = self.clock()
         i, finished, ticks = 0, 0, 0
@@ -85,7 +88,8 @@ class RequestLoop:
                     waiting[self.backend.submit(isos[i])] = i
                 i += 1
             if waiting:
-                self.backend.step()
+                if not advance() and advance is not self.backend.step:
+                    continue                    # polled, nothing finished: look for arrivals again
                 t_end = self.clock() - t0
                 for ticket in list(waiting):
                     status, mesh = self.backend.take(ticket)

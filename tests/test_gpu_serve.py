@@ -1,9 +1,11 @@
 """GPU parity of the serving path: requests answered in ticks on one
 resident volume (one shared cull and cache update per tick, then one
-request per step) must give meshes identical, byte for byte, to extracting
-each isovalue alone; admission splits ticks whose union of active blocks
-exceeds the cache budget, defers meshes past the vertex budget, and a
-single request over budget fails alone."""
+batched count, scan and emit over the tick's requests; the next tick's
+cull, cache update and decode overlapping the running tick's emission) must
+give meshes identical, byte for byte, to extracting each isovalue alone;
+admission splits ticks whose union of active blocks exceeds the cache
+budget, defers meshes past the vertex budget, and a single request over
+budget fails alone."""
 import numpy as np
 import pytest
 
@@ -45,20 +47,28 @@ def drain(srv):
 
 
 def test_served_meshes_equal_alone():
+    # A step runs one tick: its requests' count, scan and emission as batched
+    # launches; when at least two requests wait as that tick's emission is
+    # queued they are admitted as the next tick, whose cull, cache update and
+    # decode run on a second stream during this tick's emission, with this
+    # tick's blocks pinned.  Every mesh must equal extracting its isovalue alone, whether
+    # its tick ran alone or overlapped another.
     p = pkg()
     data, vol, alone = volume_pair()
     d = data[5]
     rng = np.random.default_rng(4)
-    isos = list(rng.uniform(*np.quantile(d, [0.1, 0.9]), 9).astype(np.float32))
+    isos = list(rng.uniform(*np.quantile(d, [0.1, 0.9]), 13).astype(np.float32))
     isos += [isos[2], float(d.max()) + 1.0, float(d.min()) - 1.0]     # a repeat, two empty surfaces
     srv = p.Server(vol, max_batch=4)
     try:
-        tickets = [srv.submit(float(x)) for x in isos]
-        steps = 0
+        tickets = [srv.submit(float(x)) for x in isos[:6]]
+        assert srv.step() == 4                                # the first tick, admitted at once
+        assert srv.queued() == 2                              # the next tick's front is already queued
+        tickets += [srv.submit(float(x)) for x in isos[6:]]   # arrivals while it runs
+        finished = [4]
         while srv.queued():
-            assert srv.step() == 1                            # one request finishes per step
-            steps += 1
-        assert steps == len(isos)
+            finished.append(srv.step())
+        assert sum(finished) == len(isos) and max(finished) <= 4
         for t, x in zip(tickets, isos):
             status, m = srv.take(t)
             assert status == p.ISO_OK
@@ -70,6 +80,44 @@ def test_served_meshes_equal_alone():
             ref.release()
             with pytest.raises(p.IsoError):
                 srv.take(t)                                   # already taken
+    finally:
+        srv.release()
+        vol.release()
+        alone.release()
+
+
+def test_overlapped_ticks_keep_the_running_ticks_blocks():
+    # a cache too small for two distant isovalues' blocks at once: the second
+    # tick's front, pinned to the first tick's blocks, cannot fit and waits
+    # until the first tick is done (then runs unpinned); the meshes are
+    # unaffected
+    p = pkg()
+    dims, rate = (48, 40, 36), 8
+    f = fields.gradient_noise(*dims, 7, octaves=4, base_period=16)
+    bits, bmin, bmax = oracle.encode_volume(f, rate)
+    d = oracle.decode_volume(bits, dims, rate)
+    nbd = oracle.block_dims(dims)
+    lo, hi = (float(x) for x in np.quantile(d, [0.2, 0.8]))
+    a1 = oracle.active_blocks(bmin, bmax, nbd, lo)
+    a2 = oracle.active_blocks(bmin, bmax, nbd, hi)
+    budget = int(max(a1.sum(), a2.sum()))
+    assert (a1 | a2).sum() > budget
+    vol = p.Volume(bits, dims, rate, bmin, bmax, cache_budget_bytes=256 * budget, initial_cache_fraction=1.0)
+    alone = p.Volume(bits, dims, rate, bmin, bmax)
+    srv = p.Server(vol, max_batch=1)
+    try:
+        t1, t2, t3 = srv.submit(lo), srv.submit(hi), srv.submit(lo)
+        done = []
+        while srv.queued():
+            done.append(srv.step())
+        assert sum(done) == 3                                 # refused pinned fronts were retried
+        for t, x in ((t1, lo), (t2, hi), (t3, lo)):
+            status, m = srv.take(t)
+            assert status == p.ISO_OK
+            ref = alone.extract(x)
+            same_mesh(m, ref)
+            m.release()
+            ref.release()
     finally:
         srv.release()
         vol.release()
@@ -93,7 +141,7 @@ def test_union_over_budget_splits_the_tick():
     srv = p.Server(vol, max_batch=2)
     try:
         t1, t2 = srv.submit(float(lo)), srv.submit(float(hi))
-        assert srv.step() == 0 and srv.queued() == 2          # the union was refused: both wait
+        assert srv.step() == 1                                # the union was refused: one at a time
         drain(srv)
         for t, x in ((t1, lo), (t2, hi)):
             status, m = srv.take(t)
@@ -128,7 +176,7 @@ def test_vertex_budget_defers_until_meshes_are_taken():
     try:
         tickets = [srv.submit(x) for x in isos]
         assert srv.step() == 1                                # the first fits (nothing held)
-        assert srv.queued() == 2
+        assert srv.queued() == 2                              # the other two went back to the queue
         assert srv.step() == 0                                # the held mesh blocks the rest
         st0, m0 = srv.take(tickets[0])
         assert st0 == p.ISO_OK
