@@ -333,6 +333,35 @@ int iso_extract_all_blocks_into(iso_volume *v, float isovalue, float *d_vertices
 int iso_decode_volume(const uint64_t *d_bits, uint32_t nx, uint32_t ny, uint32_t nz, uint32_t rate_bits,
                       float *d_field, void *stream);
 
+/* Naive data-parallel marching cubes over a dense field: the baseline of
+ * Section 3.3.3 (Table "mc_naive_parallel_perf") that the block method is
+ * measured against.  A pass over every cell classifies it and compacts the
+ * cells the surface crosses (0 < case < 255) in ascending order; their
+ * triangle counts (from the case table) are prefix-summed into output
+ * offsets; a second pass over the crossing cells writes the triangles.  No
+ * blocks, ranges or cache take part.
+ *   d_field       device, nx*ny*nz float32 samples, x fastest (for instance
+ *                 iso_decode_volume's output); 4-byte aligned
+ *   d_vertices    device float4[3 * capacity_triangles], 16-byte aligned:
+ *                 the triangle soup in full-volume marching-cubes order
+ *                 (cells ascending, then table order), each vertex in the
+ *                 format of iso_extract ({x, y, z} relative to the origin of
+ *                 the 4x4x4 block holding the cell, w = that block's id), the
+ *                 same bytes the block path writes for the same triangle
+ *   d_edge_ids    optional (may be NULL) device uint64[3 * capacity]: the
+ *                 global edge id 3*(x + nx*(y + ny*z)) + axis of each vertex
+ *   stats         num_triangles and n_active_cells, filled also when the
+ *                 triangles do not fit (ISO_ERR_CAPACITY: nothing written)
+ * The volume may hold at most 2^32 - 1 cells.  Scratch (5 bytes per cell,
+ * 8 per crossing cell) comes from the library's allocator.  Queued on
+ * `stream`; the call blocks until it is done (it reads back two counts). */
+typedef struct iso_dense_stats {
+    uint64_t num_triangles;
+    uint64_t n_active_cells;       /* cells the surface crosses */
+} iso_dense_stats;
+int iso_mc_dense(const float *d_field, uint32_t nx, uint32_t ny, uint32_t nz, float isovalue, float *d_vertices,
+                 uint64_t capacity_triangles, uint64_t *d_edge_ids, iso_dense_stats *stats, void *stream);
+
 /* Free a mesh's vertex buffer (stream-ordered on the volume's stream that
  * made it).  The volume must still be alive.  Safe on a zeroed mesh. */
 int iso_mesh_release(iso_volume *v, iso_mesh *m);

@@ -99,6 +99,10 @@ class _CastStats(ctypes.Structure):
                 ("n_slots", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
+class _DenseStats(ctypes.Structure):
+    _fields_ = [("num_triangles", ctypes.c_uint64), ("n_active_cells", ctypes.c_uint64)]
+
+
 class _Mesh(ctypes.Structure):
     _fields_ = [("d_vertices", ctypes.c_void_p), ("num_triangles", ctypes.c_uint64),
                 ("capacity_triangles", ctypes.c_uint64), ("stats", _Stats), ("priv", ctypes.c_void_p)]
@@ -127,6 +131,7 @@ def lib():
                                  ctypes.POINTER(_RenderStats), P]),
             "iso_raycast": (i32, [P, ctypes.c_float, ctypes.POINTER(_Pinhole), P, P, ctypes.POINTER(_CastStats)]),
             "iso_decode_volume": (i32, [P, u32, u32, u32, u32, P, P]),
+            "iso_mc_dense": (i32, [P, u32, u32, u32, ctypes.c_float, P, u64, P, ctypes.POINTER(_DenseStats), P]),
             "iso_mesh_release": (i32, [P, ctypes.POINTER(_Mesh)]),
             "iso_release": (None, [P]),
             "iso_set_stream": (i32, [P, P]),
@@ -776,6 +781,36 @@ def decode_volume(bits, dims, rate, out=None, stream=None):
     _check(lib().iso_decode_volume(_ptr(bits), nx, ny, nz, rate, _ptr(out),
                                    stream if stream is not None else _current_stream()), "iso_decode_volume")
     return out
+
+
+def mc_dense(field, iso, out=None, edge_ids=False, stream=None):
+    """Naive data-parallel marching cubes over a dense CUDA float32 field of
+    shape (nz, ny, nx) (iso_mc_dense).  Returns (vertices, stats, edges):
+    vertices a (T, 3, 4) float32 view (of `out` when it is given and large
+    enough, else a new tensor), stats a dict, edges the (T, 3) global edge ids
+    (int64 tensor) when edge_ids is set, else None."""
+    import torch
+    nz, ny, nx = field.shape
+    st = _DenseStats()
+    strm = stream if stream is not None else _current_stream()
+
+    def call(buf, cap, ebuf):
+        return lib().iso_mc_dense(_ptr(field), nx, ny, nz, ctypes.c_float(iso), _ptr(buf), cap, _ptr(ebuf),
+                                  ctypes.byref(st), strm)
+
+    cap = 0 if out is None else out.numel() // 12
+    ebuf = torch.empty((max(cap, 1), 3), dtype=torch.int64, device=field.device) if edge_ids else None
+    rc = call(out if cap else None, cap, ebuf if cap else None)
+    if rc == ISO_ERR_CAPACITY:
+        cap = int(st.num_triangles)
+        out = torch.empty((cap, 3, 4), dtype=torch.float32, device=field.device)
+        ebuf = torch.empty((cap, 3), dtype=torch.int64, device=field.device) if edge_ids else None
+        rc = call(out, cap, ebuf)
+    _check(rc, "iso_mc_dense")
+    T = int(st.num_triangles)
+    verts = out.reshape(-1)[:12 * T].view(T, 3, 4) if T else torch.empty((0, 3, 4), device=field.device)
+    edges = ebuf[:T] if (edge_ids and T) else (torch.empty((0, 3), dtype=torch.int64) if edge_ids else None)
+    return verts, {"num_triangles": T, "n_active_cells": int(st.n_active_cells)}, edges
 
 
 def decode_blocks(bits, rate, ids, stream=None):

@@ -20,7 +20,7 @@ LIB = os.path.join(OUT_DIR, "libbcmc.so")
 CHECKED_DIR = os.path.join(HERE, "_lib_checked")
 CHECKED_LIB = os.path.join(CHECKED_DIR, "libbcmc.so")
 SOURCES = ["api.cu", "batch.cu", "serve.cu", "extract.cu", "mc.cu", "codec.cu", "mc_tables.cu", "static_scratch.cu",
-           "render.cu", "raycast.cu"]
+           "render.cu", "raycast.cu", "dense.cu"]
 # the rasteriser and the ray caster state every float operation (no multiply-add contraction)
 _EXACT = ["-fmad=false", "-Xcompiler", "-ffp-contract=off"]
 FILE_FLAGS = {"render.cu": _EXACT, "raycast.cu": _EXACT}

@@ -380,28 +380,6 @@ __device__ __forceinline__ void stage_and_classify(const DevState &s, const Geom
     }
 }
 
-// t = (iso - v_lo) / (v_hi - v_lo) on a cut edge (iso lies between the two
-// samples, so |iso - v_lo| <= |v_hi - v_lo|), each difference rounded once.
-// The quotient goes through the reciprocal (kExact false: within 2 ulp for
-// divisors in [2^-126, 2^126]) or is correctly rounded (kExact true).  A
-// difference outside [2^-100, 2^125) -- samples near +-FLT_MAX, whose
-// difference can even overflow, or samples so close that it is tiny -- is
-// formed from the samples scaled by 2^-4 or 2^64: the scaling is exact up to
-// underflow of samples far below the difference, the quotient stays the same
-// real number, and the divisor lands inside the reciprocal's range.
-template <bool kExact>
-__device__ __forceinline__ float edge_fraction(float iso, float vlo, float vhi) {
-    float a = __fsub_rn(iso, vlo), b = __fsub_rn(vhi, vlo);
-    const float mb = fabsf(b);
-    if (!(mb >= 0x1p-100f && mb < 0x1p125f)) {
-        const float sc = mb >= 0x1p125f ? 0x1p-4f : 0x1p64f;
-        const float slo = __fmul_rn(vlo, sc);
-        a = __fsub_rn(__fmul_rn(iso, sc), slo);
-        b = __fsub_rn(__fmul_rn(vhi, sc), slo);
-    }
-    return kExact ? __fdiv_rn(a, b) : __fdividef(a, b);
-}
-
 __device__ __forceinline__ uint32_t warp_sum(uint32_t x) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
