@@ -61,13 +61,30 @@ __device__ __forceinline__ void stage_blocks(const uint64_t *__restrict__ bits, 
     const uint32_t stride = 2u * rate + 1u;
     const uint32_t magic = (65535u + rate) / rate;          // ceil(2^16 / rate): j / rate = (j * magic) >> 16, j < 1024
     const uint32_t have_mask = __ballot_sync(0xffffffffu, have);
-    for (uint32_t j = lane; j < 32u * rate; j += 32u) {      // the same number of rounds in every lane
-        const uint32_t q = (j * magic) >> 16, w = j - q * rate;
-        const uint32_t bq = __shfl_sync(0xffffffffu, id, (int)q);
-        uint64_t v = 0ull;
-        if ((have_mask >> q) & 1u) v = load_word<kReadOnly>(bits + (size_t)bq * rate + w);
-        stage[q * stride + 2u * w] = (uint32_t)v;
-        stage[q * stride + 2u * w + 1u] = (uint32_t)(v >> 32);
+    // Rounds of kInFlight words per lane: every load of a round is issued
+    // before the first shared store, so a lane waits for one memory latency
+    // per round rather than one per word.  Round k of lane j copies word
+    // j + 32k of the warp's 32 * rate, i.e. word w of block q.
+    constexpr uint32_t kInFlight = 8;
+    for (uint32_t k0 = 0; k0 < rate; k0 += kInFlight) {      // the same number of rounds in every lane
+        uint64_t v[kInFlight];
+#pragma unroll
+        for (uint32_t k = 0; k < kInFlight; k++) {
+            const uint32_t j = lane + 32u * (k0 + k);
+            const uint32_t q = (j * magic) >> 16, w = j - q * rate;
+            const uint32_t bq = __shfl_sync(0xffffffffu, id, (int)(q & 31u));
+            v[k] = 0ull;
+            if (k0 + k < rate && ((have_mask >> q) & 1u)) v[k] = load_word<kReadOnly>(bits + (size_t)bq * rate + w);
+        }
+#pragma unroll
+        for (uint32_t k = 0; k < kInFlight; k++) {
+            const uint32_t j = lane + 32u * (k0 + k);
+            const uint32_t q = (j * magic) >> 16, w = j - q * rate;
+            if (k0 + k < rate) {
+                stage[q * stride + 2u * w] = (uint32_t)v[k];
+                stage[q * stride + 2u * w + 1u] = (uint32_t)(v[k] >> 32);
+            }
+        }
     }
     stage[lane * stride + 2u * rate] = 0u;
     if (lane < 2) stage[32u * stride + lane] = 0u;
@@ -330,15 +347,12 @@ __device__ __forceinline__ void parse_planes(const StagedBits &st, uint32_t rate
     for (; k >= 0; k--) sts_u64(planes + (uint32_t)k * stride, 0u, 0u);
 }
 
-// Decode a staged block of `rate` words into out[64] (block-local order).
-// `planes` is this thread's column of a shared-memory area: plane k lives at
-// planes[k * stride].
-__device__ __forceinline__ void decode_staged(const uint32_t *staged, uint32_t rate, const uint32_t *tab,
-                                              float (&out)[64], uint64_t *planes, uint32_t stride) {
-    int emax = 0;
-    // a zero block: all planes 0, every sample +0
-    const uint32_t pa = smem_u32(planes), ps = stride * 8u;
-    parse_planes(StagedBits{smem_u32(staged)}, rate, smem_u32(tab), pa, ps, emax);
+// The second half of decoding a block, after parse_planes has written its
+// bit planes (plane k at planes + k * stride bytes, shared-window address)
+// and its exponent: two 32x32 bit transposes turn the planes into the 64
+// negabinary coefficients, which are mapped back to integers, put in
+// block order, inverse-lifted along z, y and x and scaled into out[64].
+__device__ __forceinline__ void finish_planes(uint32_t pa, uint32_t ps, int emax, float (&out)[64]) {
     constexpr CodingOrder order = make_coding_order();
     uint32_t q[64];
     uint32_t a[32];
@@ -361,6 +375,17 @@ __device__ __forceinline__ void decode_staged(const uint32_t *staged, uint32_t r
 #pragma unroll
     for (int i = 0; i < 16; i++) inv_lift4u(q[4 * i], q[4 * i + 1], q[4 * i + 2], q[4 * i + 3]);  // x
     scale_block(q, emax - kPrecision, out);
+}
+
+// Decode a staged block of `rate` words into out[64] (block-local order).
+// `planes` is this thread's column of a shared-memory area: plane k lives at
+// planes[k * stride].  A zero block decodes to 64 samples of +0.
+__device__ __forceinline__ void decode_staged(const uint32_t *staged, uint32_t rate, const uint32_t *tab,
+                                              float (&out)[64], uint64_t *planes, uint32_t stride) {
+    int emax = 0;
+    const uint32_t pa = smem_u32(planes), ps = stride * 8u;
+    parse_planes(StagedBits{smem_u32(staged)}, rate, smem_u32(tab), pa, ps, emax);
+    finish_planes(pa, ps, emax, out);
 }
 
 // Dynamic shared memory of a decoding kernel of `threads` threads: the
