@@ -552,7 +552,9 @@ void iso_batch_release(iso_batch *b);
  * (Section 4.1) and each request's own candidates, then one cache update
  * and decode for the union (Section 4.2, Algorithm 1); its back counts,
  * scans and emits all its requests (Sections 4.3-4.5) in one launch each,
- * with one readback of their triangle counts in between.  Under load ticks
+ * with one readback of their triangle counts in between (the count follows
+ * the front on the device, with no host round trip; the union's budget is
+ * checked at that readback).  Under load ticks
  * overlap: when a tick's emission is queued and at least two requests wait,
  * they are admitted as the next tick and its front runs on a second stream
  * while the running tick emits (a lone waiting request is admitted when the
@@ -582,12 +584,17 @@ typedef struct iso_server_options {
     uint64_t vertex_budget_bytes;  /* limit on held mesh bytes (48 or 24 per triangle); 0 = none */
     void *stream;                  /* cudaStream_t whose earlier work the server waits for at creation
                                       (NULL = default); the server runs on two streams of its own */
+    uint64_t case_bytes;           /* room for the requests' stored cell cases, 64 bytes a candidate:
+                                      0 = max_batch full candidate lists, at most 4 GiB; below 64 = none
+                                      (every emission classifies again); the meshes are the same */
 } iso_server_options;
 
 /* v must not be loaded with ISO_DEBUG.  The server keeps 2 * max_batch
  * request positions (a running tick's and the next tick's), each with
  * candidate, count, offset and occupied-list arrays of min(cache slots, nb)
- * entries (20 bytes each), and creates two streams: the backs run at the
+ * entries (20 bytes each), a buffer for the requests' stored cell cases
+ * (case_bytes; a request whose cases do not fit is classified again by its
+ * emission), and creates two streams: the backs run at the
  * device's highest stream priority, the fronts at its lowest, so a front
  * overlapping a back takes only the SMs the back leaves idle.  Meshes are
  * complete when a request finishes (the server waits for its emission). */

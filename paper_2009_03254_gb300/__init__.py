@@ -76,7 +76,7 @@ class _Shape(ctypes.Structure):
 
 class _ServerOptions(ctypes.Structure):
     _fields_ = [("max_batch", ctypes.c_uint32), ("vertex_format", ctypes.c_uint32),
-                ("vertex_budget_bytes", ctypes.c_uint64), ("stream", ctypes.c_void_p)]
+                ("vertex_budget_bytes", ctypes.c_uint64), ("stream", ctypes.c_void_p), ("case_bytes", ctypes.c_uint64)]
 
 
 class _Camera(ctypes.Structure):
@@ -557,7 +557,7 @@ class Server:
     tick's emission.  See iso_server_* in include/bcmc.h.  The volume must
     outlive the server."""
 
-    def __init__(self, volume, *, max_batch=4, vertex_budget_bytes=0, stream=None, packed=False):
+    def __init__(self, volume, *, max_batch=4, vertex_budget_bytes=0, stream=None, packed=False, case_bytes=0):
         self._h = None
         self.volume = volume
         self.packed = bool(packed)
@@ -566,6 +566,7 @@ class Server:
         opt.vertex_format = ISO_VERTEX_PACKED if packed else ISO_VERTEX_FLOAT4
         opt.vertex_budget_bytes = int(vertex_budget_bytes)
         opt.stream = stream if stream is not None else _current_stream()
+        opt.case_bytes = int(case_bytes)
         h = ctypes.c_void_p()
         _check(lib().iso_server_create(ctypes.byref(h), volume._h, ctypes.byref(opt)), "iso_server_create")
         self._h = h

@@ -6,12 +6,17 @@
 //                    isovalues (Section 4.1): the union of their active sets
 //                    and each request's own candidate list
 //     cache update   Algorithm 1 and the decode (Section 4.2) on the union
-//   back of a tick (the server's stream)
+//     front tail     the union's failures become every request's; each
+//                    request gets its region of the stored-cases buffer
+//   back of a tick (the server's stream, queued behind the front's event
+//   without a host round trip)
 //     count, scan    Sections 4.3-4.4 over all the tick's requests in one
 //                    launch each: a request is a "view" of the volume (own
 //                    control block, candidates, counts and offsets; shared
 //                    cache), the views are the entries of a batch launch
-//     readback       every request's triangle count at once; the host
+//                    (they find no work if the union failed)
+//     readback       every request's control block and the union's at once;
+//                    the host checks the union (budget, timeouts) and
 //                    allocates the meshes
 //     emit           Section 4.5, all requests in one launch
 // Ticks are pipelined under load: once a tick's emission is queued and at
@@ -57,6 +62,9 @@ struct ServeArgs {
     unsigned long long *desc_mc[kMaxServe];
     unsigned long long *desc_occ[kMaxServe];
     uint32_t cand_cap;                // room of each candidate list
+    VolEntry *views;                  // the tick's views in device memory (the back's launch table)
+    uint8_t *cases;                   // the server's stored-cases buffer (or null)
+    unsigned long long case_cap;      // its room, in candidates (64 bytes each)
 };
 
 __global__ void __launch_bounds__(kThreads) serve_prep_kernel(ServeArgs a) {
@@ -238,17 +246,33 @@ __global__ void __launch_bounds__(kThreads) serve_cull_kernel(ServeArgs a) {
     }
 }
 
-// the union's failures (budget, a timeout) are every request's
-__global__ void serve_status_kernel(ServeArgs a) {
-    const uint32_t j = threadIdx.x;
-    if (j < a.k) a.ctl[j]->status |= a.base.s.ctl->status & (kStatusBudget | kStatusAnyTimeout);
+// The end of a tick's front (one thread: k <= 8).  The union's failures
+// (budget, a timeout) become every request's, so the back finds no work;
+// each request, in order, gets the next region of the stored-cases buffer
+// while its candidates fit (a request without one has its cases
+// classified again by the emission, which reads the same pointer).
+__global__ void serve_front_tail_kernel(ServeArgs a) {
+    if (threadIdx.x != 0) return;
+    const uint32_t fail = a.base.s.ctl->status & (kStatusBudget | kStatusAnyTimeout);
+    unsigned long long used = 0;
+    for (uint32_t j = 0; j < a.k; j++) {
+        Ctl *c = a.ctl[j];
+        c->status |= fail;
+        const unsigned long long n = c->n_cand;
+        const bool fits = a.cases != nullptr && used + n <= a.case_cap;
+        a.views[j].s.cases = fits ? a.cases + 64ull * used : nullptr;
+        if (fits) used += n;
+    }
 }
 
-// the tick's request control blocks (their candidate counts) for one readback
+// the tick's request control blocks, then the union's, for one readback
 __global__ void serve_gather_kernel(ServeArgs a, Ctl *dst) {
     constexpr uint32_t kWords = sizeof(Ctl) / 4;
-    for (uint32_t i = threadIdx.x; i < a.k * kWords; i += blockDim.x)
-        reinterpret_cast<uint32_t *>(dst)[i] = reinterpret_cast<const uint32_t *>(a.ctl[i / kWords])[i % kWords];
+    for (uint32_t i = threadIdx.x; i < (a.k + 1) * kWords; i += blockDim.x) {
+        const uint32_t j = i / kWords;
+        const Ctl *src = j < a.k ? a.ctl[j] : a.base.s.ctl;
+        reinterpret_cast<uint32_t *>(dst)[i] = reinterpret_cast<const uint32_t *>(src)[i % kWords];
+    }
 }
 
 // Each request's output (mesh, capacity, format) into its control block; a
@@ -295,10 +319,10 @@ struct Tick {                           // requests in flight on the GPU
     std::vector<float *> bufs;          // meshes (after the count readback)
     std::vector<int> status;
     uint32_t run = 0;                   // requests that emit (the rest go back to the queue)
-    uint8_t *cases = nullptr;           // the tick's stored cell cases (count writes, emit reads)
+    ServeArgs args{};                   // its front's arguments (the back's gather reads them too)
 };
 
-constexpr uint64_t kMaxTickCaseBytes = 4ull << 30;   // stored cases per tick, else emit classifies again
+constexpr uint64_t kMaxTickCaseBytes = 4ull << 30;   // stored cases of a tick, else emit classifies again
 
 }  // namespace
 
@@ -318,11 +342,13 @@ struct iso_server {
     VolEntry views[2][kMaxServe];       // per-request views of the volume
     VolEntry *d_views[2] = {};          // the same in device memory (the back's launch tables)
     uint32_t *d_ctr[2] = {};            // work counters of each half's back launches
-    Ctl *d_ctls[2] = {};                // control blocks gathered for one readback (after front, after scan)
+    Ctl *d_ctls[2] = {};                // control blocks gathered for one readback: k requests, then the union
     Params *d_params = nullptr;         // the requests' outputs, copied into their control blocks
-    Ctl *h_ctls[2] = {};                // pinned mirrors: each half's request control blocks
+    Ctl *h_ctls[2] = {};                // pinned mirrors of d_ctls
     Params *h_params = nullptr;
-    Ctl *h_union[2] = {};               // pinned: each half's union control block after its front
+    uint8_t *cases = nullptr;           // stored cell cases of a tick's requests (count writes, emit reads)
+    uint64_t case_cap = 0;              // its room in candidates
+    bool one_by_value = true;           // a one-request tick launches its view by value
     cudaEvent_t front_done[2] = {}, count_done = nullptr, emit_done = nullptr;
     Plan one_plan{}, back_plan{};       // launches over one view (kOne) or up to max_batch views
     uint64_t next_ticket = 1;
@@ -355,6 +381,9 @@ ServeArgs serve_args(const iso_server *sv, const Tick &t, const std::vector<Requ
     for (uint32_t j = 0; j < a.k_pin; j++) a.iso[a.k + j] = (*pins)[j].iso;
     a.back_ctr = sv->d_ctr[p];
     a.cand_cap = sv->cand_cap;
+    a.views = sv->d_views[p];
+    a.cases = sv->cases;
+    a.case_cap = sv->case_cap;
     return a;
 }
 
@@ -365,21 +394,19 @@ void free_server(iso_server *sv) {
     cudaStreamSynchronize(sv->stream);
     for (auto &kv : sv->done)
         if (kv.second.mesh.d_vertices) dfree_on(kv.second.mesh.d_vertices, sv->stream);
-    if (sv->has_back) {                   // a tick abandoned in flight
+    if (sv->has_back)                     // a tick abandoned in flight
         for (float *b : sv->back_tick.bufs) dfree_on(b, sv->stream);
-        dfree_on(sv->back_tick.cases, sv->stream);
-    }
     for (auto &half : sv->slots)
         for (Slot &s : half) {
             void *p[] = {s.ctl, s.icand, s.counts, s.offsets, s.desc_cand, s.desc_mc, s.iocc};
             for (void *x : p) dfree_on(x, sv->stream);
         }
     void *q[] = {sv->d_views[0], sv->d_views[1], sv->d_ctr[0], sv->d_ctr[1], sv->d_ctls[0], sv->d_ctls[1],
-                 sv->d_params};
+                 sv->d_params, sv->cases};
     for (void *x : q) dfree_on(x, sv->stream);
     cudaStreamSynchronize(sv->stream);
     (void)cudaGetLastError();
-    for (Ctl *h : {sv->h_ctls[0], sv->h_ctls[1], sv->h_union[0], sv->h_union[1]})
+    for (Ctl *h : {sv->h_ctls[0], sv->h_ctls[1]})
         if (h) cudaFreeHost(h);
     if (sv->h_params) cudaFreeHost(sv->h_params);
     for (cudaEvent_t e : {sv->front_done[0], sv->front_done[1], sv->count_done, sv->emit_done})
@@ -442,12 +469,10 @@ int launch_front(iso_server *sv, const std::vector<Request> *pins) {
     else if (kt <= 8) serve_cull_kernel<8><<<v->plan.cull, kThreads, 0, st>>>(a);
     else serve_cull_kernel<16><<<v->plan.cull, kThreads, 0, st>>>(a);
     launch_cache_update(single, v->plan, st);
-    serve_status_kernel<<<1, kMaxServe, 0, st>>>(a);
-    serve_gather_kernel<<<1, 256, 0, st>>>(a, sv->d_ctls[t.parity]);
-    ISO_CK(cudaMemcpyAsync(sv->h_union[t.parity], v->s.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
-    ISO_CK(cudaMemcpyAsync(sv->h_ctls[t.parity], sv->d_ctls[t.parity], k * sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    serve_front_tail_kernel<<<1, 32, 0, st>>>(a);
     ISO_CK(cudaEventRecord(sv->front_done[t.parity], st));
     ISO_CK(cudaGetLastError());
+    t.args = a;
     sv->front_tick = std::move(t);
     sv->has_front = true;
     sv->next_parity ^= 1u;
@@ -456,63 +481,32 @@ int launch_front(iso_server *sv, const std::vector<Request> *pins) {
 
 Launch back_launch(const iso_server *sv, const Tick &t) {
     const uint32_t k = (uint32_t)t.reqs.size();
-    if (k == 1) return Launch{nullptr, 1u, sv->d_ctr[t.parity], sv->views[t.parity][0]};   // one view by value
+    if (k == 1 && sv->one_by_value)
+        return Launch{nullptr, 1u, sv->d_ctr[t.parity], sv->views[t.parity][0]};   // one view by value
     return Launch{sv->d_views[t.parity], k, sv->d_ctr[t.parity], VolEntry{}, sv->v->g.rate};
 }
 
-// The front of the admitted tick is done: check its union, then queue its
-// requests' count and scan (one launch each) and the count readback.
-int promote(iso_server *sv, uint32_t *completed) {
-    iso_volume *v = sv->v;
+const Plan &back_plan(const iso_server *sv, const Tick &t) {
+    return t.reqs.size() == 1 && sv->one_by_value ? sv->one_plan : sv->back_plan;
+}
+
+// Queue the count and scan of the tick whose front was just queued (or is
+// running) behind the front's event, then one readback of every request's
+// control block and the union's.  Nothing waits on the host: the union is
+// checked when the counts are back (a failed union leaves the back no work).
+int queue_back(iso_server *sv) {
     cudaStream_t st = sv->stream;
     Tick t = std::move(sv->front_tick);
     sv->has_front = false;
-    ISO_CK(cudaEventSynchronize(sv->front_done[t.parity]));
-    const Ctl &uni = *sv->h_union[t.parity];
     const uint32_t k = (uint32_t)t.reqs.size();
-    v->last_n_active = uni.n_active;
-    v->last_n_new = uni.n_new;
-    v->last_n_cand = 0;
-    v->last_slots = uni.S;
-    if (uni.status & kStatusAnyTimeout) {
-        ISO_CK(cudaStreamSynchronize(st));    // no back reads the cache while it is emptied
-        status_to_error(v, uni.status);
-        for (const Request &r : t.reqs) finish(sv, r, ISO_ERR_TIMEOUT, &uni, nullptr, nullptr);
-        *completed += k;
-        return ISO_OK;
-    }
-    if (uni.status & kStatusBudget) {
-        if (t.pinned || k > 1) {              // retry without the running tick's blocks, or with fewer requests
-            requeue(sv, t.reqs, 0);
-            if (t.pinned) sv->hold = sv->has_back;
-            else sv->limit = std::max(1u, k / 2);
-            return ISO_OK;
-        }
-        finish(sv, t.reqs[0], ISO_ERR_BUDGET, &uni, nullptr, nullptr);
-        *completed += 1;
-        return ISO_OK;
-    }
-    if (!t.pinned) sv->limit = std::min(sv->max_batch, sv->limit * 2);
-    // stored cases for the emit (as a volume keeps them): one buffer, each
-    // request's candidates at its own offset
-    uint64_t cases_bytes = 0;
-    for (uint32_t j = 0; j < k; j++) cases_bytes += 64ull * sv->h_ctls[t.parity][j].n_cand;
-    if (cases_bytes && cases_bytes <= kMaxTickCaseBytes && dalloc_on(&t.cases, cases_bytes, sv->device, st) != ISO_OK)
-        t.cases = nullptr;
-    uint64_t off = 0;
-    for (uint32_t j = 0; j < k; j++) {
-        sv->views[t.parity][j].s.cases = t.cases ? t.cases + off : nullptr;
-        off += 64ull * sv->h_ctls[t.parity][j].n_cand;
-    }
-    if (k > 1)
-        ISO_CK(cudaMemcpyAsync(sv->d_views[t.parity], sv->views[t.parity], k * sizeof(VolEntry),
-                               cudaMemcpyHostToDevice, st));
+    ISO_CK(cudaStreamWaitEvent(st, sv->front_done[t.parity], 0));
     const Launch L = back_launch(sv, t);
-    const Plan &pl = k == 1 ? sv->one_plan : sv->back_plan;
+    const Plan &pl = back_plan(sv, t);
     launch_mc_count(L, false, pl, st);
     launch_mc_scan(L, pl, st);
-    launch_batch_gather(Launch{sv->d_views[t.parity], k, nullptr, VolEntry{}}, sv->d_ctls[t.parity], st);
-    ISO_CK(cudaMemcpyAsync(sv->h_ctls[t.parity], sv->d_ctls[t.parity], k * sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    serve_gather_kernel<<<1, 256, 0, st>>>(t.args, sv->d_ctls[t.parity]);
+    ISO_CK(cudaMemcpyAsync(sv->h_ctls[t.parity], sv->d_ctls[t.parity], (k + 1) * sizeof(Ctl), cudaMemcpyDeviceToHost,
+                           st));
     ISO_CK(cudaEventRecord(sv->count_done, st));
     ISO_CK(cudaGetLastError());
     t.stage = kCount;
@@ -521,15 +515,41 @@ int promote(iso_server *sv, uint32_t *completed) {
     return ISO_OK;
 }
 
-// The tick's counts are back: allocate its meshes (in order; one that would
-// take the held bytes past the vertex budget sends it and the rest of the
-// tick back to the queue) and queue the emission.
-int start_emit(iso_server *sv) {
+// The tick's counts are back.  A failed union ends the tick (a timeout
+// fails its requests; over the budget, its requests go back to the queue
+// and an unpinned tick halves the tick size).  Otherwise allocate its
+// meshes (in order; one that would take the held bytes past the vertex
+// budget sends it and the rest of the tick back to the queue) and queue the
+// emission.
+int start_emit(iso_server *sv, uint32_t *completed) {
+    iso_volume *v = sv->v;
     cudaStream_t st = sv->stream;
     Tick &t = sv->back_tick;
     ISO_CK(cudaEventSynchronize(sv->count_done));
     const uint32_t k = (uint32_t)t.reqs.size();
     const Ctl *c = sv->h_ctls[t.parity];
+    const Ctl &uni = c[k];
+    v->last_n_active = uni.n_active;
+    v->last_n_new = uni.n_new;
+    v->last_n_cand = 0;
+    v->last_slots = uni.S;
+    if (uni.status & (kStatusAnyTimeout | kStatusBudget)) {
+        Tick done = std::move(sv->back_tick);   // not a finished back: a step goes on with the queue
+        sv->has_back = false;
+        if (uni.status & kStatusAnyTimeout) {
+            status_to_error(v, uni.status);
+            for (const Request &r : done.reqs) finish(sv, r, ISO_ERR_TIMEOUT, &uni, nullptr, nullptr);
+            *completed += k;
+        } else if (done.pinned || k > 1) {    // retry without the running tick's blocks, or with fewer requests
+            requeue(sv, done.reqs, 0);
+            if (!done.pinned) sv->limit = std::max(1u, k / 2);
+        } else {
+            finish(sv, done.reqs[0], ISO_ERR_BUDGET, &uni, nullptr, nullptr);
+            *completed += 1;
+        }
+        return ISO_OK;
+    }
+    if (!t.pinned) sv->limit = std::min(sv->max_batch, sv->limit * 2);
     t.bufs.assign(k, nullptr);
     t.status.assign(k, ISO_OK);
     t.run = k;
@@ -560,10 +580,7 @@ int start_emit(iso_server *sv) {
     }
     ISO_CK(cudaMemcpyAsync(sv->d_params, sv->h_params, k * sizeof(Params), cudaMemcpyHostToDevice, st));
     serve_params_kernel<<<1, kMaxServe, 0, st>>>(sv->d_views[t.parity], sv->d_params, k);
-    const Launch L = back_launch(sv, t);
-    launch_mc_emit(L, false, k == 1 ? sv->one_plan : sv->back_plan, st);
-    if (t.cases) dfree_on(t.cases, st);       // stream-ordered: after the emission
-    t.cases = nullptr;
+    launch_mc_emit(back_launch(sv, t), false, back_plan(sv, t), st);
     ISO_CK(cudaEventRecord(sv->emit_done, st));
     ISO_CK(cudaGetLastError());
     t.stage = kEmit;
@@ -577,7 +594,7 @@ int finish_tick(iso_server *sv, uint32_t *completed) {
     sv->hold = false;
     sv->ticks_finished++;
     const Ctl *c = sv->h_ctls[t.parity];
-    const Ctl &uni = *sv->h_union[t.parity];
+    const Ctl &uni = c[t.reqs.size()];
     for (uint32_t j = 0; j < t.run; j++) {
         finish(sv, t.reqs[j], t.status[j], &uni, &c[j], t.status[j] == ISO_OK ? t.bufs[j] : nullptr);
         *completed += 1;
@@ -605,12 +622,11 @@ int advance(iso_server *sv, bool block, uint32_t *completed) {
     }
     if (sv->has_back && sv->back_tick.stage == kCount) {
         if (!block && !ready(sv->count_done)) goto admit;
-        rc = start_emit(sv);
+        rc = start_emit(sv, completed);
         return rc ? -rc : 1;
     }
-    if (sv->has_front && !sv->has_back) {
-        if (!block && !ready(sv->front_done[sv->front_tick.parity])) return 0;
-        rc = promote(sv, completed);
+    if (sv->has_front && !sv->has_back) {          // the back follows the front on the device
+        rc = queue_back(sv);
         return rc ? -rc : 1;
     }
 admit:
@@ -674,7 +690,7 @@ int iso_server_create(iso_server **out, iso_volume *v, const iso_server_options 
         TRY(cuda_ok(cudaEventCreateWithFlags(&sv->front_done[p], cudaEventDisableTiming)));
         TRY(dalloc_on(&sv->d_views[p], kMaxServe, sv->device, sv->stream));
         TRY(dalloc_on(&sv->d_ctr[p], kNumLaunchCounters, sv->device, sv->stream));
-        TRY(dalloc_on(&sv->d_ctls[p], kMaxServe, sv->device, sv->stream));
+        TRY(dalloc_on(&sv->d_ctls[p], kMaxServe + 1, sv->device, sv->stream));
         for (uint32_t j = 0; j < sv->max_batch; j++) {
             Slot &s = sv->slots[p][j];
             TRY(dalloc_on(&s.ctl, 1, sv->device, sv->stream));
@@ -694,7 +710,7 @@ int iso_server_create(iso_server **out, iso_volume *v, const iso_server_options 
             d.desc_mc = s.desc_mc;
             d.desc_occ = s.desc_occ;
             d.iocc = s.iocc;
-            d.cases = nullptr;            // set per tick
+            d.cases = nullptr;            // set below; a batch launch's per tick by the front
             d.cutw = nullptr;
             d.voff = nullptr;
             d.desc_vtx = nullptr;
@@ -703,11 +719,24 @@ int iso_server_create(iso_server **out, iso_volume *v, const iso_server_options 
         }
     }
     TRY(dalloc_on(&sv->d_params, kMaxServe, sv->device, sv->stream));
-    if (cudaMallocHost((void **)&sv->h_ctls[0], kMaxServe * sizeof(Ctl)) != cudaSuccess ||
-        cudaMallocHost((void **)&sv->h_ctls[1], kMaxServe * sizeof(Ctl)) != cudaSuccess ||
-        cudaMallocHost((void **)&sv->h_params, kMaxServe * sizeof(Params)) != cudaSuccess ||
-        cudaMallocHost((void **)&sv->h_union[0], sizeof(Ctl)) != cudaSuccess ||
-        cudaMallocHost((void **)&sv->h_union[1], sizeof(Ctl)) != cudaSuccess) {
+    // Stored cases (the count pass keeps each candidate's 64 cell cases for
+    // the emission, as a volume does): by default for up to max_batch full
+    // candidate lists, at most kMaxTickCaseBytes; without room the emission
+    // classifies again.  A one-request tick launches its view by value when
+    // a full list fits (or nothing is stored), else through the launch
+    // table like a batch.
+    {
+        const uint64_t want = o.case_bytes ? o.case_bytes / 64 * 64
+                                           : std::min<uint64_t>(kMaxTickCaseBytes, 64ull * cand * sv->max_batch);
+        if (want && dalloc_on(&sv->cases, want, sv->device, sv->stream) == ISO_OK) sv->case_cap = want / 64;
+        else sv->cases = nullptr;
+        (void)cudaGetLastError();
+        sv->one_by_value = sv->cases == nullptr || 64ull * cand <= want;
+        for (int p = 0; p < 2; p++) sv->views[p][0].s.cases = sv->one_by_value ? sv->cases : nullptr;
+    }
+    if (cudaMallocHost((void **)&sv->h_ctls[0], (kMaxServe + 1) * sizeof(Ctl)) != cudaSuccess ||
+        cudaMallocHost((void **)&sv->h_ctls[1], (kMaxServe + 1) * sizeof(Ctl)) != cudaSuccess ||
+        cudaMallocHost((void **)&sv->h_params, kMaxServe * sizeof(Params)) != cudaSuccess) {
         (void)cudaGetLastError();
         free_server(sv);
         return ISO_ERR_OOM;

@@ -46,20 +46,42 @@ def drain(srv):
         srv.step()
 
 
-def test_served_meshes_equal_alone():
+# room for the stored cell cases: the default (every request's), "one"
+# (the largest request's candidates: the first requests of a tick only, and
+# less than a full candidate list, so one-request ticks take the launch
+# table), and none
+CASE_ROOM = ["default", "one", "none"]
+
+
+def case_bytes_for(room, alone, isos):
+    if room == "default":
+        return 0
+    if room == "none":
+        return 1
+    most = 0
+    for x in isos:
+        m = alone.extract(float(x))
+        most = max(most, m.stats["n_candidates"])
+        m.release()
+    return 64 * (most + 1)
+
+
+@pytest.mark.parametrize("room", CASE_ROOM)
+def test_served_meshes_equal_alone(room):
     # A step runs one tick: its requests' count, scan and emission as batched
     # launches; when at least two requests wait as that tick's emission is
     # queued they are admitted as the next tick, whose cull, cache update and
     # decode run on a second stream during this tick's emission, with this
     # tick's blocks pinned.  Every mesh must equal extracting its isovalue alone, whether
-    # its tick ran alone or overlapped another.
+    # its tick ran alone or overlapped another, and whether its cases were
+    # stored by the count pass or classified again by the emission.
     p = pkg()
     data, vol, alone = volume_pair()
     d = data[5]
     rng = np.random.default_rng(4)
     isos = list(rng.uniform(*np.quantile(d, [0.1, 0.9]), 13).astype(np.float32))
     isos += [isos[2], float(d.max()) + 1.0, float(d.min()) - 1.0]     # a repeat, two empty surfaces
-    srv = p.Server(vol, max_batch=4)
+    srv = p.Server(vol, max_batch=4, case_bytes=case_bytes_for(room, alone, isos))
     try:
         tickets = [srv.submit(float(x)) for x in isos[:6]]
         assert srv.step() == 4                                # the first tick, admitted at once
@@ -80,6 +102,42 @@ def test_served_meshes_equal_alone():
             ref.release()
             with pytest.raises(p.IsoError):
                 srv.take(t)                                   # already taken
+    finally:
+        srv.release()
+        vol.release()
+        alone.release()
+
+
+@pytest.mark.parametrize("room", CASE_ROOM)
+def test_one_request_ticks_equal_alone(room):
+    # one request a tick: its view travels by value, or through the launch
+    # table when a full candidate list does not fit the stored-cases room
+    # (a smooth field: about 70% of the blocks active)
+    p = pkg()
+    dims, rate = (64, 48, 40), 8
+    f = fields.gradient_noise(*dims, 5, octaves=3, base_period=48)
+    bits, bmin, bmax = oracle.encode_volume(f, rate)
+    d = oracle.decode_volume(bits, dims, rate)
+    vol = p.Volume(bits, dims, rate, bmin, bmax)
+    alone = p.Volume(bits, dims, rate, bmin, bmax)
+    isos = [float(x) for x in np.quantile(d, [0.3, 0.5, 0.7, 0.5])]
+    case_bytes = case_bytes_for(room, alone, isos)
+    assert room != "one" or case_bytes < 64 * int(np.prod(oracle.block_dims(dims)))
+    srv = p.Server(vol, max_batch=1, case_bytes=case_bytes)
+    try:
+        tickets = [srv.submit(x) for x in isos]
+        done = []
+        while srv.queued():
+            done.append(srv.step())
+        assert sum(done) == len(isos) and max(done) == 1
+        for t, x in zip(tickets, isos):
+            status, m = srv.take(t)
+            assert status == p.ISO_OK
+            ref = alone.extract(x)
+            same_mesh(m, ref)
+            assert m.stats["n_candidates"] == ref.stats["n_candidates"]
+            m.release()
+            ref.release()
     finally:
         srv.release()
         vol.release()
