@@ -566,10 +566,12 @@ void iso_batch_release(iso_batch *b);
  * budget, its requests return to the queue: an overlapped tick is retried
  * once the running tick is done, otherwise later ticks take half as many
  * requests (down to one; a single request that does not fit finishes with
- * ISO_ERR_BUDGET).  Meshes are allocated when their sizes are known; one
- * that would take the bytes of finished, not yet taken meshes past
- * vertex_budget_bytes returns to the queue with the rest of its tick (a
- * mesh is always allowed when nothing is held).  Every served mesh is
+ * ISO_ERR_BUDGET).  Meshes are allocated when their sizes are known, in
+ * request order: a tick emits in rounds, each taking the waiting requests
+ * whose meshes fit together with the finished, not yet taken meshes under
+ * vertex_budget_bytes (a mesh is always allowed when nothing is held); the
+ * rest wait in the tick, their counts kept, until meshes are taken.  Every
+ * served mesh is
  * identical, byte for byte, to iso_extract of the same isovalue on the
  * same data.  The server uses the volume's device state: do not extract
  * from the volume on another stream while a server call runs, and destroy
@@ -603,9 +605,11 @@ int iso_server_create(iso_server **out, iso_volume *v, const iso_server_options 
 /* Queue a request (host only, no device work); *ticket identifies it. */
 int iso_server_submit(iso_server *s, float isovalue, uint64_t *ticket);
 
-/* Advance the pipeline until a tick's back is done (its requests finished,
- * or sent back to the queue past the vertex budget) or nothing is in flight
- * (no request waits); blocks while it waits for the GPU.  Ticks are
+/* Advance the pipeline until requests finish (a tick's emission round is
+ * done), a union over the cache budget has gone back to the queue and
+ * nothing else moved, the next mesh waits for meshes to be taken (vertex
+ * budget: returns at once with none finished), or nothing is in flight (no
+ * request waits); blocks while it waits for the GPU.  Ticks are
  * admitted on the way (the next one while the current one is in its back),
  * so work keeps running on the GPU when the call returns.  *completed (may
  * be NULL) receives the number of requests finished. */

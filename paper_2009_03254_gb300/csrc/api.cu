@@ -708,8 +708,10 @@ int iso_load_volume(iso_volume **out, const void *compressed, size_t compressed_
     TRY(dalloc(v, &s.iocc, s.list_cap));
     // the count pass keeps each candidate's cases for the emit pass when they
     // take at most 8 GB (else emit classifies again); debug volumes always
-    if ((v->flags & ISO_DEBUG) || (uint64_t)s.list_cap * 64 <= (8ull << 30))
+    if ((v->flags & ISO_DEBUG) || (uint64_t)s.list_cap * 64 <= (8ull << 30)) {
         TRY(dalloc(v, &s.cases, (size_t)s.list_cap * 64));
+        s.case_cap = s.list_cap;
+    }
     if (cudaMallocHost((void **)&v->host_ctl, sizeof(Ctl)) != cudaSuccess ||
         cudaMallocHost((void **)&v->host_params, sizeof(Params)) != cudaSuccess) {
         (void)cudaGetLastError();

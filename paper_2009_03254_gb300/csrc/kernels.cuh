@@ -41,6 +41,7 @@ struct DevState {
                                    // read by emit (null until the first indexed extraction)
     uint8_t *cases;            // 64 cell cases per candidate, written by the count pass and read by
                                // emit instead of classifying again (null: emit classifies)
+    unsigned long long case_cap;   // candidates `cases` holds: with more, both passes act as if it were null
     // debug copy (null unless the volume was loaded with ISO_DEBUG)
     unsigned long long *dbg_edges;
 };

@@ -238,6 +238,12 @@ __device__ __forceinline__ uint32_t lane_cut_word(const uint32_t m[4], uint32_t 
 // With `cut_dst` (emit pass of an indexed extraction), the 12 cut-edge
 // words count kept for each of the tile's blocks are copied to
 // cut_dst + 24q (asynchronously, like the cases; the caller waits).
+// whether the count pass keeps the cases (and the emit pass reads them):
+// there is room for all of them (n_cand is final before the count starts)
+__device__ __forceinline__ bool keeps_cases(const DevState &s) {
+    return s.cases != nullptr && s.ctl->n_cand <= s.case_cap;
+}
+
 template <bool kEmit>
 __device__ __forceinline__ void stage_and_classify(const DevState &s, const Geom &g, float iso, uint32_t base,
                                                    int nb_w, uint32_t b, uint32_t ci, WarpTile &wt,
@@ -246,7 +252,8 @@ __device__ __forceinline__ void stage_and_classify(const DevState &s, const Geom
                                                    uint32_t &nv_lane, uint32_t *cut_dst = nullptr) {
     const int lane = threadIdx.x & 31, bq = lane >> 3, bo = lane & 7;
     const uint32_t slab = g.nbx * g.nby;
-    const bool stored = kEmit && s.cases != nullptr;      // uniform
+    const bool keep = keeps_cases(s);                     // uniform
+    const bool stored = kEmit && keep;
     // The stored cases of the tile's blocks, copied to shared memory while
     // the samples are staged (16 lanes x 16 bytes; both ends 16-byte
     // aligned).  The emit pass's blocks are occupied candidates, not
@@ -353,7 +360,7 @@ __device__ __forceinline__ void stage_and_classify(const DevState &s, const Geom
                     cs[h] = valid ? cs[h] : 0u;
                 }
             }
-            if (!kEmit && s.cases) {      // uniform: keep them for the emit pass
+            if (!kEmit && keep) {         // uniform: keep them for the emit pass
 #pragma unroll
                 for (int h = 0; h < 2; h++)
                     if (in_bounds(base + q < s.list_cap, &s.ctl->status))

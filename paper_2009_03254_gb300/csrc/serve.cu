@@ -18,7 +18,10 @@
 //     readback       every request's control block and the union's at once;
 //                    the host checks the union (budget, timeouts) and
 //                    allocates the meshes
-//     emit           Section 4.5, all requests in one launch
+//     emit           Section 4.5, all requests in one launch; requests whose
+//                    meshes would pass the vertex budget wait in the tick
+//                    (their counts and lists kept) and emit in a later round
+//                    once meshes are taken
 // Ticks are pipelined under load: once a tick's emission is queued and at
 // least two requests wait, they are admitted as the next tick and its front
 // runs on the second stream (at a lower priority) while the running tick
@@ -261,6 +264,7 @@ __global__ void serve_front_tail_kernel(ServeArgs a) {
         const unsigned long long n = c->n_cand;
         const bool fits = a.cases != nullptr && used + n <= a.case_cap;
         a.views[j].s.cases = fits ? a.cases + 64ull * used : nullptr;
+        a.views[j].s.case_cap = fits ? n : 0ull;
         if (fits) used += n;
     }
 }
@@ -276,13 +280,13 @@ __global__ void serve_gather_kernel(ServeArgs a, Ctl *dst) {
 }
 
 // Each request's output (mesh, capacity, format) into its control block; a
-// request without a mesh this tick is skipped by the emission.
+// request without a mesh in this emission round is skipped by it.
 __global__ void serve_params_kernel(const VolEntry *__restrict__ views, const Params *__restrict__ p, uint32_t k) {
     const uint32_t j = threadIdx.x;
     if (j >= k) return;
     Ctl *c = views[j].s.ctl;
     c->params = p[j];
-    if (!p[j].out) c->status |= kStatusSkip;
+    c->status = p[j].out ? (c->status & ~(uint32_t)kStatusSkip) : (c->status | kStatusSkip);
 }
 
 }  // namespace bcmc
@@ -316,9 +320,11 @@ struct Tick {                           // requests in flight on the GPU
     uint32_t parity = 0;                // which half of the request positions it uses
     bool pinned = false;                // its union also holds the previous tick's blocks
     Stage stage = kFront;
-    std::vector<float *> bufs;          // meshes (after the count readback)
+    bool checked = false;               // its union was checked (at the count readback)
+    std::vector<float *> bufs;          // meshes (allocated round by round)
     std::vector<int> status;
-    uint32_t run = 0;                   // requests that emit (the rest go back to the queue)
+    uint32_t emitted = 0;               // requests finished by earlier emission rounds
+    uint32_t run_to = 0;                // the running round takes requests [emitted, run_to)
     ServeArgs args{};                   // its front's arguments (the back's gather reads them too)
 };
 
@@ -348,7 +354,7 @@ struct iso_server {
     Params *h_params = nullptr;
     uint8_t *cases = nullptr;           // stored cell cases of a tick's requests (count writes, emit reads)
     uint64_t case_cap = 0;              // its room in candidates
-    bool one_by_value = true;           // a one-request tick launches its view by value
+    bool blocked = false;               // the back waits for meshes to be taken (vertex budget)
     cudaEvent_t front_done[2] = {}, count_done = nullptr, emit_done = nullptr;
     Plan one_plan{}, back_plan{};       // launches over one view (kOne) or up to max_batch views
     uint64_t next_ticket = 1;
@@ -481,13 +487,12 @@ int launch_front(iso_server *sv, const std::vector<Request> *pins) {
 
 Launch back_launch(const iso_server *sv, const Tick &t) {
     const uint32_t k = (uint32_t)t.reqs.size();
-    if (k == 1 && sv->one_by_value)
-        return Launch{nullptr, 1u, sv->d_ctr[t.parity], sv->views[t.parity][0]};   // one view by value
+    if (k == 1) return Launch{nullptr, 1u, sv->d_ctr[t.parity], sv->views[t.parity][0]};   // one view by value
     return Launch{sv->d_views[t.parity], k, sv->d_ctr[t.parity], VolEntry{}, sv->v->g.rate};
 }
 
 const Plan &back_plan(const iso_server *sv, const Tick &t) {
-    return t.reqs.size() == 1 && sv->one_by_value ? sv->one_plan : sv->back_plan;
+    return t.reqs.size() == 1 ? sv->one_plan : sv->back_plan;
 }
 
 // Queue the count and scan of the tick whose front was just queued (or is
@@ -517,53 +522,57 @@ int queue_back(iso_server *sv) {
 
 // The tick's counts are back.  A failed union ends the tick (a timeout
 // fails its requests; over the budget, its requests go back to the queue
-// and an unpinned tick halves the tick size).  Otherwise allocate its
-// meshes (in order; one that would take the held bytes past the vertex
-// budget sends it and the rest of the tick back to the queue) and queue the
-// emission.
+// and an unpinned tick halves the tick size).  Otherwise start an emission
+// round: allocate the meshes of the waiting requests, in order, while they
+// fit the vertex budget (a mesh is always allowed when nothing is held),
+// and queue one emission for them.  Returns kBlocked, with nothing queued,
+// when the next mesh must wait for meshes to be taken.
+constexpr int kBlocked = -1;
+
 int start_emit(iso_server *sv, uint32_t *completed) {
     iso_volume *v = sv->v;
     cudaStream_t st = sv->stream;
     Tick &t = sv->back_tick;
-    ISO_CK(cudaEventSynchronize(sv->count_done));
     const uint32_t k = (uint32_t)t.reqs.size();
     const Ctl *c = sv->h_ctls[t.parity];
-    const Ctl &uni = c[k];
-    v->last_n_active = uni.n_active;
-    v->last_n_new = uni.n_new;
-    v->last_n_cand = 0;
-    v->last_slots = uni.S;
-    if (uni.status & (kStatusAnyTimeout | kStatusBudget)) {
-        Tick done = std::move(sv->back_tick);   // not a finished back: a step goes on with the queue
-        sv->has_back = false;
-        if (uni.status & kStatusAnyTimeout) {
-            status_to_error(v, uni.status);
-            for (const Request &r : done.reqs) finish(sv, r, ISO_ERR_TIMEOUT, &uni, nullptr, nullptr);
-            *completed += k;
-        } else if (done.pinned || k > 1) {    // retry without the running tick's blocks, or with fewer requests
-            requeue(sv, done.reqs, 0);
-            if (!done.pinned) sv->limit = std::max(1u, k / 2);
-        } else {
-            finish(sv, done.reqs[0], ISO_ERR_BUDGET, &uni, nullptr, nullptr);
-            *completed += 1;
+    if (!t.checked) {
+        ISO_CK(cudaEventSynchronize(sv->count_done));
+        const Ctl &uni = c[k];
+        v->last_n_active = uni.n_active;
+        v->last_n_new = uni.n_new;
+        v->last_n_cand = 0;
+        v->last_slots = uni.S;
+        if (uni.status & (kStatusAnyTimeout | kStatusBudget)) {
+            Tick done = std::move(sv->back_tick);   // not a finished back: a step goes on with the queue
+            sv->has_back = false;
+            if (uni.status & kStatusAnyTimeout) {
+                status_to_error(v, uni.status);
+                for (const Request &r : done.reqs) finish(sv, r, ISO_ERR_TIMEOUT, &uni, nullptr, nullptr);
+                *completed += k;
+            } else if (done.pinned || k > 1) {    // retry without the running tick's blocks, or with fewer requests
+                requeue(sv, done.reqs, 0);
+                if (!done.pinned) sv->limit = std::max(1u, k / 2);
+            } else {
+                finish(sv, done.reqs[0], ISO_ERR_BUDGET, &uni, nullptr, nullptr);
+                *completed += 1;
+            }
+            return ISO_OK;
         }
-        return ISO_OK;
+        if (!t.pinned) sv->limit = std::min(sv->max_batch, sv->limit * 2);
+        t.checked = true;
+        t.bufs.assign(k, nullptr);
+        t.status.assign(k, ISO_OK);
+        t.emitted = 0;
+        for (uint32_t j = 0; j < k; j++)
+            if (c[j].status & (kStatusAnyTimeout | kStatusBounds))
+                t.status[j] = (c[j].status & kStatusBounds) ? ISO_ERR_BOUNDS : ISO_ERR_TIMEOUT;
     }
-    if (!t.pinned) sv->limit = std::min(sv->max_batch, sv->limit * 2);
-    t.bufs.assign(k, nullptr);
-    t.status.assign(k, ISO_OK);
-    t.run = k;
     uint64_t held = sv->held_bytes;
-    for (uint32_t j = 0; j < k; j++) {
-        if (c[j].status & (kStatusAnyTimeout | kStatusBounds)) {
-            t.status[j] = (c[j].status & kStatusBounds) ? ISO_ERR_BOUNDS : ISO_ERR_TIMEOUT;
-            continue;
-        }
+    uint32_t j = t.emitted;
+    for (; j < k; j++) {
+        if (t.status[j] != ISO_OK) continue;  // fails without a mesh
         const uint64_t bytes = sv->tri_bytes * c[j].n_tri;
-        if (sv->vertex_budget && held > 0 && held + bytes > sv->vertex_budget) {
-            t.run = j;
-            break;
-        }
+        if (sv->vertex_budget && held > 0 && held + bytes > sv->vertex_budget) break;
         if (c[j].n_tri) {
             const int rc = dalloc_on(&t.bufs[j], (size_t)c[j].n_tri * (sv->tri_bytes / 4), sv->device, st);
             if (rc) {
@@ -573,10 +582,16 @@ int start_emit(iso_server *sv, uint32_t *completed) {
         }
         held += bytes;
     }
-    for (uint32_t j = 0; j < k; j++) {
-        const bool out = j < t.run && t.bufs[j];
-        sv->h_params[j] = Params{t.reqs[j].iso, sv->format, 0u, 0u, 0u, 0u, out ? c[j].n_tri : 0ull,
-                                 out ? (unsigned long long)(uintptr_t)t.bufs[j] : 0ull};
+    if (j == t.emitted) {                     // the next mesh waits for meshes to be taken
+        sv->blocked = true;
+        return kBlocked;
+    }
+    sv->blocked = false;
+    t.run_to = j;
+    for (uint32_t i = 0; i < k; i++) {
+        const bool out = i >= t.emitted && i < t.run_to && t.bufs[i];
+        sv->h_params[i] = Params{t.reqs[i].iso, sv->format, 0u, 0u, 0u, 0u, out ? c[i].n_tri : 0ull,
+                                 out ? (unsigned long long)(uintptr_t)t.bufs[i] : 0ull};
     }
     ISO_CK(cudaMemcpyAsync(sv->d_params, sv->h_params, k * sizeof(Params), cudaMemcpyHostToDevice, st));
     serve_params_kernel<<<1, kMaxServe, 0, st>>>(sv->d_views[t.parity], sv->d_params, k);
@@ -587,21 +602,28 @@ int start_emit(iso_server *sv, uint32_t *completed) {
     return ISO_OK;
 }
 
+// An emission round is done: its requests finish.  The tick leaves the back
+// once every request has; otherwise its next round waits for the budget.
 int finish_tick(iso_server *sv, uint32_t *completed) {
     ISO_CK(cudaEventSynchronize(sv->emit_done));
-    Tick t = std::move(sv->back_tick);
+    Tick &t = sv->back_tick;
+    const Ctl *c = sv->h_ctls[t.parity];
+    const Ctl &uni = c[t.reqs.size()];
+    for (uint32_t j = t.emitted; j < t.run_to; j++) {
+        finish(sv, t.reqs[j], t.status[j], &uni, &c[j], t.status[j] == ISO_OK ? t.bufs[j] : nullptr);
+        if (t.status[j] != ISO_OK && t.bufs[j]) dfree_on(t.bufs[j], sv->stream);
+        t.bufs[j] = nullptr;                  // the mesh is the finished request's now
+        *completed += 1;
+    }
+    t.emitted = t.run_to;
+    if (t.emitted < t.reqs.size()) {
+        t.stage = kCount;                     // counted, waiting for its next round
+        return ISO_OK;
+    }
     sv->has_back = false;
     sv->hold = false;
     sv->ticks_finished++;
-    const Ctl *c = sv->h_ctls[t.parity];
-    const Ctl &uni = c[t.reqs.size()];
-    for (uint32_t j = 0; j < t.run; j++) {
-        finish(sv, t.reqs[j], t.status[j], &uni, &c[j], t.status[j] == ISO_OK ? t.bufs[j] : nullptr);
-        *completed += 1;
-    }
-    for (uint32_t j = t.run; j < t.reqs.size(); j++)
-        if (t.bufs[j]) dfree_on(t.bufs[j], sv->stream);
-    requeue(sv, t.reqs, t.run);
+    sv->back_tick = Tick{};
     return ISO_OK;
 }
 
@@ -623,6 +645,7 @@ int advance(iso_server *sv, bool block, uint32_t *completed) {
     if (sv->has_back && sv->back_tick.stage == kCount) {
         if (!block && !ready(sv->count_done)) goto admit;
         rc = start_emit(sv, completed);
+        if (rc == kBlocked) return 0;              // nothing moves until meshes are taken
         return rc ? -rc : 1;
     }
     if (sv->has_front && !sv->has_back) {          // the back follows the front on the device
@@ -711,6 +734,7 @@ int iso_server_create(iso_server **out, iso_volume *v, const iso_server_options 
             d.desc_occ = s.desc_occ;
             d.iocc = s.iocc;
             d.cases = nullptr;            // set below; a batch launch's per tick by the front
+            d.case_cap = 0;
             d.cutw = nullptr;
             d.voff = nullptr;
             d.desc_vtx = nullptr;
@@ -722,17 +746,18 @@ int iso_server_create(iso_server **out, iso_volume *v, const iso_server_options 
     // Stored cases (the count pass keeps each candidate's 64 cell cases for
     // the emission, as a volume does): by default for up to max_batch full
     // candidate lists, at most kMaxTickCaseBytes; without room the emission
-    // classifies again.  A one-request tick launches its view by value when
-    // a full list fits (or nothing is stored), else through the launch
-    // table like a batch.
+    // classifies again.  A one-request tick's view (by value) holds the whole
+    // buffer, a batch's views their regions (set by the front).
     {
         const uint64_t want = o.case_bytes ? o.case_bytes / 64 * 64
                                            : std::min<uint64_t>(kMaxTickCaseBytes, 64ull * cand * sv->max_batch);
         if (want && dalloc_on(&sv->cases, want, sv->device, sv->stream) == ISO_OK) sv->case_cap = want / 64;
         else sv->cases = nullptr;
         (void)cudaGetLastError();
-        sv->one_by_value = sv->cases == nullptr || 64ull * cand <= want;
-        for (int p = 0; p < 2; p++) sv->views[p][0].s.cases = sv->one_by_value ? sv->cases : nullptr;
+        for (int p = 0; p < 2; p++) {
+            sv->views[p][0].s.cases = sv->cases;
+            sv->views[p][0].s.case_cap = sv->case_cap;
+        }
     }
     if (cudaMallocHost((void **)&sv->h_ctls[0], (kMaxServe + 1) * sizeof(Ctl)) != cudaSuccess ||
         cudaMallocHost((void **)&sv->h_ctls[1], (kMaxServe + 1) * sizeof(Ctl)) != cudaSuccess ||
@@ -796,7 +821,8 @@ int iso_server_step(iso_server *sv, uint32_t *completed) {
         r = advance(sv, false, &n);
         if (r > 0) continue;
         // a tick finished, a failure, or nothing in flight
-        if (r < 0 || n > 0 || sv->ticks_finished != ticks0 || (!sv->has_front && !sv->has_back)) break;
+        if (r < 0 || n > 0 || sv->ticks_finished != ticks0 || (!sv->has_front && !sv->has_back) || sv->blocked)
+            break;
         r = advance(sv, true, &n);
         if (r < 0) break;
     }
@@ -807,7 +833,7 @@ int iso_server_step(iso_server *sv, uint32_t *completed) {
 int iso_server_queued(const iso_server *sv, uint32_t *queued) {
     if (!sv || !queued) return ISO_ERR_INVALID_ARG;
     *queued = (uint32_t)(sv->queue.size() + (sv->has_front ? sv->front_tick.reqs.size() : 0) +
-                         (sv->has_back ? sv->back_tick.reqs.size() : 0));
+                         (sv->has_back ? sv->back_tick.reqs.size() - sv->back_tick.emitted : 0));
     return ISO_OK;
 }
 

@@ -234,8 +234,9 @@ def test_vertex_budget_defers_until_meshes_are_taken():
     try:
         tickets = [srv.submit(x) for x in isos]
         assert srv.step() == 1                                # the first fits (nothing held)
-        assert srv.queued() == 2                              # the other two went back to the queue
+        assert srv.queued() == 2                              # the other two wait in the tick, counted
         assert srv.step() == 0                                # the held mesh blocks the rest
+        assert srv.step() == 0                                # (returning at once each time)
         st0, m0 = srv.take(tickets[0])
         assert st0 == p.ISO_OK
         same_mesh(m0, ref[0])
