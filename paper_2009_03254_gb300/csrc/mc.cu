@@ -498,10 +498,23 @@ __global__ void __launch_bounds__(kThreads) mc_scan_kernel(Launch L) {
         const bool indexed = (c->params.flags & kParamIndexed) != 0;   // block-uniform
         const uint32_t i0 = tile * kScanItems + threadIdx.x * kPT;
         uint32_t v8[kPT], sum = 0, occ = 0, vsum = 0;
+        const bool full = i0 + kPT <= n;                  // the thread's counts in 16-byte loads
+        if (full) {
+#pragma unroll
+            for (int k = 0; k < kPT / 4; k++) {
+                const uint4 q = __ldg(reinterpret_cast<const uint4 *>(s.counts + i0) + k);
+                v8[4 * k] = q.x;
+                v8[4 * k + 1] = q.y;
+                v8[4 * k + 2] = q.z;
+                v8[4 * k + 3] = q.w;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < kPT; k++) v8[k] = i0 + k < n ? s.counts[i0 + k] : 0u;
+        }
 #pragma unroll
         for (int k = 0; k < kPT; k++) {
-            v8[k] = i0 + k < n ? s.counts[i0 + k] : 0u;   // triangles | vertices << 16
-            sum += v8[k] & 0xFFFFu;
+            sum += v8[k] & 0xFFFFu;                       // triangles | vertices << 16
             vsum += v8[k] >> 16;
             occ += (v8[k] & 0xFFFFu) != 0u;
         }
@@ -567,11 +580,21 @@ __global__ void __launch_bounds__(kThreads) mc_scan_kernel(Launch L) {
                 vrun += v8[k] >> 16;
             }
         } else {
+            unsigned long long ofs[kPT];
 #pragma unroll
             for (int k = 0; k < kPT; k++) {
-                if (i0 + k < n) s.offsets[i0 + k] = run;
+                ofs[k] = run;
                 if (v8[k] && in_bounds(orun < s.list_cap, &c->status)) s.iocc[orun++] = i0 + k;
                 run += v8[k];
+            }
+            if (full) {
+#pragma unroll
+                for (int k = 0; k < kPT / 2; k++)
+                    reinterpret_cast<ulonglong2 *>(s.offsets + i0)[k] = make_ulonglong2(ofs[2 * k], ofs[2 * k + 1]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < kPT; k++)
+                    if (i0 + k < n) s.offsets[i0 + k] = ofs[k];
             }
         }
     }
