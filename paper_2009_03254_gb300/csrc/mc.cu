@@ -225,9 +225,10 @@ __device__ __forceinline__ uint32_t lane_cut_word(const uint32_t m[4], uint32_t 
 // or at occupied candidate `base` (emit pass), nb_w of kBPW slots used.
 // Returns the per-cell triangle counts of the lane's two cells, packed one
 // byte per block: n0p for cell lane, n1p for cell lane + 32.  The count
-// pass (kEmit false) classifies and, when the volume keeps them (s.cases),
-// stores the cases; the emit pass leaves the cases in wt.cases, reading
-// the stored ones instead of classifying again when there are any.  `b` is
+// pass (kEmit false) classifies and, when there is room for them
+// (keeps_cases), stores the cases; the emit pass leaves the cases in
+// wt.cases, reading the stored ones instead of classifying again under the
+// same test.  `b` is
 // this lane's block (block lane/8 of the tile) and `ci` its position in
 // the candidate list, loaded by the caller one warp tile ahead.
 //
