@@ -181,7 +181,7 @@ def measured_peaks():
         return None
 
 
-PROFILE_SOURCES = ("extract.cu", "mc.cu", "codec.cuh", "common.cuh")
+PROFILE_SOURCES = ("extract.cu", "mc.cu", "codec.cuh", "common.cuh", "kernels.cuh", "launch.cuh", "tile_scan.cuh")
 
 
 def profile_sources_sha():
