@@ -138,6 +138,15 @@ typedef void *(*iso_alloc_fn)(size_t bytes, int device, void *stream, void *ctx)
 typedef void (*iso_free_fn)(void *ptr, int device, void *stream, void *ctx);
 int iso_set_allocator(iso_alloc_fn alloc, iso_free_fn free_fn, void *ctx);
 
+/* Give the freed memory the library's pool keeps on `device` back to the
+ * device, so that other allocators (a PyTorch caching allocator, cudaMalloc)
+ * can use it; memory in use is untouched.  Waits for all work on the device
+ * first (cudaDeviceSynchronize).  An allocation the pool cannot satisfy does
+ * the same once by itself and retries before it reports ISO_ERR_OOM.
+ * ISO_ERR_INVALID_ARG for a device without a pool of the library (nothing
+ * was ever allocated there from it). */
+int iso_release_cached_memory(int device);
+
 /* Upload a compressed volume and set up its cache (Section 4: "uploading
  * the ZFP fixed-rate compressed data to the GPU"; Section 4.1: "precompute
  * and store the value range of each block when loading the data").

@@ -162,6 +162,7 @@ def lib():
             "iso_server_take": (i32, [P, u64, ctypes.POINTER(_Mesh)]),
             "iso_server_wait": (i32, [P, u64, u32, ctypes.POINTER(_Mesh)]),
             "iso_set_allocator": (i32, [P, P, P]),
+            "iso_release_cached_memory": (i32, [i32]),
             "iso_server_destroy": (None, [P]),
         }
         for name, (res, args) in sig.items():
@@ -658,6 +659,20 @@ def use_pool_allocator():
     """Back to the library's own stream-ordered memory pool (allocations
     made through an earlier hook still go back to it)."""
     _check(lib().iso_set_allocator(None, None, None), "iso_set_allocator")
+
+
+def release_cached_memory(device=None):
+    """Give the freed memory the library's pool keeps on `device` (default:
+    the current CUDA device) back to the device (iso_release_cached_memory);
+    waits for the device first.  False if the library never allocated from
+    its pool there."""
+    import torch
+    dev = torch.cuda.current_device() if device is None else int(device)
+    rc = lib().iso_release_cached_memory(dev)
+    if rc == ISO_ERR_INVALID_ARG:
+        return False
+    _check(rc, "iso_release_cached_memory")
+    return True
 
 
 def render(vertices, num_triangles, dims, view_proj, light, width, height, indices=None, fragments=None,

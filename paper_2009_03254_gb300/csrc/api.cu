@@ -88,7 +88,22 @@ int dalloc_bytes(void **p, size_t bytes, int dev, cudaStream_t st) {
     }
     cudaMemPool_t pool = device_pool(dev);
     if (pool) {
-        ISO_CK(cudaMallocFromPoolAsync(p, bytes, pool, st));
+        cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool, st);
+        if (e == cudaErrorMemoryAllocation) {   // what the pool keeps may be what is missing: trim, retry once
+            (void)cudaGetLastError();
+            int cur = 0;
+            cudaGetDevice(&cur);
+            cudaSetDevice(dev);
+            const bool ok = cudaDeviceSynchronize() == cudaSuccess && cudaMemPoolTrimTo(pool, 0) == cudaSuccess;
+            cudaSetDevice(cur);
+            (void)cudaGetLastError();
+            if (ok) e = cudaMallocFromPoolAsync(p, bytes, pool, st);
+        }
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            *p = nullptr;
+            return e == cudaErrorMemoryAllocation ? ISO_ERR_OOM : ISO_ERR_CUDA;
+        }
     } else {
         ISO_CK(cudaMalloc(p, bytes));
     }
@@ -605,6 +620,22 @@ int iso_set_allocator(iso_alloc_fn alloc, iso_free_fn free_fn, void *ctx) {
     g_hook.alloc = alloc;
     g_hook.free = free_fn;
     g_hook.ctx = alloc ? ctx : nullptr;
+    return ISO_OK;
+}
+
+int iso_release_cached_memory(int device) {
+    if (device < 0 || device >= kMaxPoolDevices) return ISO_ERR_INVALID_ARG;
+    cudaMemPool_t pool = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_pool_mutex);
+        pool = g_pool[device];
+    }
+    if (!pool) return ISO_ERR_INVALID_ARG;
+    DeviceGuard dg(device);
+    if (cudaDeviceSynchronize() != cudaSuccess || cudaMemPoolTrimTo(pool, 0) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return ISO_ERR_CUDA;
+    }
     return ISO_OK;
 }
 

@@ -9,6 +9,8 @@
 * An allocation that fails: an allocator hook that refuses every request
   must turn into ISO_ERR_OOM from the load, from an extraction (its mesh)
   and from creating a server, and leave the library usable.
+* Memory the library's pool keeps after a release goes back to the device
+  with iso_release_cached_memory.
 """
 import ctypes
 
@@ -98,3 +100,32 @@ def test_refused_allocations_are_reported_as_oom():
         _check_against_oracle(pkg, vol, bits, dims, rate, bmin, bmax, 0.0)
     finally:
         vol.release()
+
+
+def test_release_cached_memory_returns_the_pool():
+    # a 512^3 volume of zero blocks at 2 bits/value reserves its whole slot
+    # pool at load (2,097,152 slots, 537 MB); released, the memory stays in
+    # the library's pool until iso_release_cached_memory gives it back
+    import torch
+    import paper_2009_03254_gb300 as pkg
+    dims, rate = (512, 512, 512), 2
+    nb = int(np.prod(oracle.block_dims(dims)))
+    bits = torch.zeros(nb * rate, dtype=torch.int64, device="cuda")
+    rng = torch.zeros(nb, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    vol = pkg.Volume(bits, dims, rate, rng, rng)
+    m = vol.extract(0.5)                                      # nothing crosses: an empty mesh
+    assert m.num_triangles == 0
+    m.release()
+    vol.release()
+    torch.cuda.synchronize()
+    kept = torch.cuda.mem_get_info()[0]
+    assert pkg.release_cached_memory() is True
+    freed = torch.cuda.mem_get_info()[0] - kept
+    assert freed >= 500 * 10**6, freed
+    # the library allocates again as before
+    vol = pkg.Volume(bits, dims, rate, rng, rng)
+    m = vol.extract(0.5)
+    assert m.num_triangles == 0
+    m.release()
+    vol.release()

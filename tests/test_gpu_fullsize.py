@@ -1,9 +1,11 @@
 """GPU parity at full size, on sampled blocks the oracle computes one by one.
 
 The benchmark's 512^3 noise volume (all five isovalues, default launch
-plan, CUDA graph, cold cache then warm) and the 2048 x 2048 x 1024
-channel volume (isovalue at the 70th percentile of the decoded data) are
-extracted whole on the GPU.  For a sample of blocks (candidates, occupied
+plan, CUDA graph, cold cache then warm), the 2048 x 2048 x 1024 channel
+volume (isovalue at the 70th percentile of the decoded data) and the
+10240 x 7680 x 1536 serving volume (1.89e9 blocks; three isovalues, also
+served, each served mesh equal to the plain one) are extracted whole on
+the GPU.  For a sample of blocks (candidates, occupied
 blocks, blocks on the volume's far faces, and blocks the triangle stage
 skips), the oracle runs plain marching cubes over the block's decoded
 5x5x5 window (the block and its +x/+y/+z neighbours, clipped at the
@@ -130,4 +132,69 @@ def test_channel2k_sampled():
         assert n > 300
         m.release()
     finally:
+        vol.release()
+
+
+def mesh_digest(mesh, chunk=1 << 28):
+    """Two 64-bit sums over the mesh's 32-bit words (plain, and weighted by
+    position), taken on the device in chunks: equal meshes give equal
+    digests; a changed, moved or missing word changes them."""
+    import torch
+    w = mesh.vertices.reshape(-1).view(torch.int32)
+    plain = torch.zeros((), dtype=torch.int64, device=w.device)
+    weighted = torch.zeros((), dtype=torch.int64, device=w.device)
+    for i in range(0, w.numel(), chunk):
+        x = w[i:i + chunk].to(torch.int64)
+        idx = torch.arange(i, i + x.numel(), dtype=torch.int64, device=w.device)
+        plain += x.sum()
+        weighted += (x * (idx % 1000003 + 1)).sum()
+    return mesh.num_triangles, int(plain), int(weighted)
+
+
+def test_serve_dns_full_size_sampled():
+    # the serving volume at its full size: 10240 x 7680 x 1536 at 2 bits/value
+    # (1.89e9 blocks, 30.2 GB compressed), 64 GB cache budget.  Three
+    # isovalues through the plain path, checked on sampled blocks against the
+    # oracle, then through the server (two requests a tick under a 48 GB
+    # vertex budget, meshes taken as they finish), each served mesh equal to
+    # the plain one
+    import torch
+    import paper_2009_03254_gb300 as bc
+    from synth import recipes, volumes
+    rec = recipes.SERVE_DNS
+    bc.release_cached_memory()                    # what earlier volumes left in the library's pool
+    torch.cuda.empty_cache()
+    bits, bmin, bmax = volumes.encode_recipe(rec)
+    isos = [volumes.percentile_isovalue(bits, rec.dims, rec.rate, q, seed=3) for q in (0.3, 0.5, 0.7)]
+    vol = bc.Volume(bits, rec.dims, rec.rate, bmin, bmax, cache_budget_bytes=64 * 10**9, initial_cache_fraction=0.01)
+    del bmin, bmax
+    torch.cuda.empty_cache()
+    srv = None
+    try:
+        rng = np.random.default_rng(29)
+        want = {}
+        for iso in isos:
+            m = vol.extract(iso)
+            assert m.num_triangles > 10_000_000
+            check_sampled(vol, m, bits, rec.dims, rec.rate, iso, rng, n_each=60)
+            want[iso] = mesh_digest(m)
+            m.release()
+        srv = bc.Server(vol, max_batch=2, vertex_budget_bytes=48 * 10**9)
+        pending = {srv.submit(x): x for x in isos}
+        for _ in range(100):                          # each step finishes a request or admits one
+            if not pending:
+                break
+            srv.step()
+            for t in list(pending):
+                status, m = srv.take(t)
+                if status == bc.ISO_PENDING:
+                    continue
+                x = pending.pop(t)
+                assert status == bc.ISO_OK
+                assert mesh_digest(m) == want[x]
+                m.release()
+        assert not pending
+    finally:
+        if srv is not None:
+            srv.release()
         vol.release()
