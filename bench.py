@@ -90,6 +90,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-volume batch comparison")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg of the default run")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other single-volume configurations (sphere64, channel2k) of the default run")
     ap.add_argument("--workload", default="noise512", choices=["noise512", "serve"],
                     help="serve: the request loop on the 10240x7680x1536 channel volume")
     ap.add_argument("--serve-scale", type=float, default=1.0,
@@ -844,6 +846,7 @@ def run_ours(args):
         if not args.no_serve and rank == 0:
             serve = serving_summary(measure_serving(bc, torch, SERVE_LEG_SCALE, SERVE_LEG_REQUESTS,
                                                     batches=(2, 4, 8), sweeps=False))
+        configs = None if (args.no_configs or rank != 0) else measure_configs(bc, torch)
 
     if rank != 0:
         dist.barrier() if world > 1 else None
@@ -906,6 +909,7 @@ def run_ours(args):
         "batch64": batch,
         "stages": stages,
         "serving": serve,
+        "configs": configs,
         "gpu_launches": args.steps * (KERNELS_PER_RESET + KERNELS_PER_SURFACE * len(ISOS)),
         "clocks": clk.summary(),
         "e2e": e2e,
@@ -941,6 +945,67 @@ SERVE_BUDGET_BYTES = 64e9          # decoded-block cache budget of the serving v
 SERVE_LEG_SCALE = 0.25             # the default run's serving leg: x and y at a quarter (1/16 of the samples)
 SERVE_LEG_REQUESTS = 200
 SERVE_VERTEX_BUDGET = 48e9         # finished meshes held by the server at once (not scaled with the volume)
+
+
+def measure_configs(bc, torch, reps=4):
+    """The other single-volume configurations, each extracted whole through
+    iso_extract_into (device time, CUDA events on the volume's stream):
+    sphere64 (64^3 sphere distance field, 16 bits/value, isovalue 0: the
+    correctness case) and channel2k (2048 x 2048 x 1024 channel-flow field,
+    4 bits/value, isovalue at the 70th percentile of the decoded data).  For
+    each: the surface from an empty cache (median of `reps`, the cache reset
+    before each) and warm (the same isovalue again), triangles and voxels
+    per second, and the cold extraction against n_new*(8R + 256) + 48T bytes
+    and the measured copy peak."""
+    from synth import recipes, volumes
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    res = {}
+    for rec in (recipes.SPHERE64, recipes.CHANNEL2K):
+        bits, bmin, bmax = volumes.encode_recipe(rec)
+        iso = rec.isovalues[0] if rec.isovalues else volumes.percentile_isovalue(bits, rec.dims, rec.rate,
+                                                                                 rec.percentile, seed=3)
+        vol = bc.Volume(bits, rec.dims, rec.rate, bmin, bmax)
+        del bits, bmin, bmax
+        torch.cuda.empty_cache()
+        st = vol.extract_into(iso, torch.empty((1, 3, 4), dtype=torch.float32, device="cuda"), check=False)
+        T = st["num_triangles"]
+        out = torch.empty((max(T, 1), 3, 4), dtype=torch.float32, device="cuda")
+        stream = torch.cuda.current_stream()
+
+        def timed(cold):
+            ms = []
+            for _ in range(reps):
+                if cold:
+                    vol.cache_reset()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                s2 = vol.extract_into(iso, out)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            return float(np.median(ms)), s2
+
+        cold_ms, sc = timed(True)
+        warm_ms, _ = timed(False)
+        nvox = float(np.prod(rec.dims))
+        nb = int(np.prod(bc.block_dims(rec.dims)))
+        alg = sc["n_new"] * (8 * rec.rate + 256) + 48 * sc["num_triangles"]
+        res[rec.name] = {
+            "dims": list(rec.dims), "rate_bits": rec.rate, "isovalue": iso, "triangles": sc["num_triangles"],
+            "active_fraction": round(sc["n_active"] / nb, 4), "cold_ms": cold_ms, "warm_ms": warm_ms,
+            "cold_triangles_per_s": sc["num_triangles"] / (cold_ms / 1000.0),
+            "warm_triangles_per_s": sc["num_triangles"] / (warm_ms / 1000.0),
+            "cold_voxels_per_s": nvox / (cold_ms / 1000.0), "warm_voxels_per_s": nvox / (warm_ms / 1000.0),
+            "cold_alg_bytes": alg, "cold_GBps": alg / (cold_ms / 1000.0) / 1e9,
+            "cold_frac_of_measured_hbm": alg / (cold_ms / 1000.0) / 1e9 / peak}
+        del out
+        vol.release()
+        torch.cuda.empty_cache()
+    res["what"] = ("other single-volume configurations through iso_extract_into, device time: the surface from an "
+                   "empty cache and warm, and the cold extraction against n_new*(8R + 256) + 48T bytes")
+    return res
 
 
 def measure_serving(bc, torch, scale, n, batches=(4,), sweeps=True):
