@@ -615,7 +615,7 @@ int iso_server_create(iso_server **out, iso_volume *v, const iso_server_options 
 int iso_server_submit(iso_server *s, float isovalue, uint64_t *ticket);
 
 /* Advance the pipeline until requests finish (a tick's emission round is
- * done), a union over the cache budget has gone back to the queue and
+ * done: every request of the round has finished), a union over the cache budget has gone back to the queue and
  * nothing else moved, the next mesh waits for meshes to be taken (vertex
  * budget: returns at once with none finished), or nothing is in flight (no
  * request waits); blocks while it waits for the GPU.  Ticks are
@@ -625,8 +625,9 @@ int iso_server_submit(iso_server *s, float isovalue, uint64_t *ticket);
 int iso_server_step(iso_server *s, uint32_t *completed);
 
 /* The same without blocking: take every transition whose GPU work is
- * already done (finish a tick, start an emission, start a count, admit the
- * queued requests as the next tick) and return at once.  A request loop
+ * already done (finish the requests whose emissions are done, start an
+ * emission, start a count, admit the queued requests as the next tick) and
+ * return at once.  A request loop
  * that polls between arrivals admits each arrival while the previous tick
  * is still on the GPU.  *completed (may be NULL) receives the number of
  * requests finished. */

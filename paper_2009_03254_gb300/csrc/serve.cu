@@ -18,10 +18,13 @@
 //     readback       every request's control block and the union's at once;
 //                    the host checks the union (budget, timeouts) and
 //                    allocates the meshes
-//     emit           Section 4.5, all requests in one launch; requests whose
-//                    meshes would pass the vertex budget wait in the tick
-//                    (their counts and lists kept) and emit in a later round
-//                    once meshes are taken
+//     emit           Section 4.5: at light load (a round of one or two
+//                    requests, none waiting) one launch per request, each
+//                    finishing as its own emission ends; otherwise one
+//                    launch for the round; requests
+//                    whose meshes would pass the vertex budget wait
+//                    in the tick (their counts and lists kept) and emit in a
+//                    later round once meshes are taken
 // Ticks are pipelined under load: once a tick's emission is queued and at
 // least two requests wait, they are admitted as the next tick and its front
 // runs on the second stream (at a lower priority) while the running tick
@@ -355,7 +358,8 @@ struct iso_server {
     uint8_t *cases = nullptr;           // stored cell cases of a tick's requests (count writes, emit reads)
     uint64_t case_cap = 0;              // its room in candidates
     bool blocked = false;               // the back waits for meshes to be taken (vertex budget)
-    cudaEvent_t front_done[2] = {}, count_done = nullptr, emit_done = nullptr;
+    cudaEvent_t front_done[2] = {}, count_done = nullptr;
+    cudaEvent_t emit_done[kMaxServe] = {};   // each request's emission in the running round
     Plan one_plan{}, back_plan{};       // launches over one view (kOne) or up to max_batch views
     uint64_t next_ticket = 1;
     std::deque<Request> queue;
@@ -364,6 +368,7 @@ struct iso_server {
     bool hold = false;                  // a pinned front did not fit: admit only once the back is done
     uint32_t next_parity = 0;
     uint64_t ticks_finished = 0;        // backs completed (their requests finished or sent back)
+    uint64_t rounds_finished = 0;       // emission rounds completed (every request of the round finished)
     std::map<uint64_t, Done> done;
 };
 
@@ -415,7 +420,9 @@ void free_server(iso_server *sv) {
     for (Ctl *h : {sv->h_ctls[0], sv->h_ctls[1]})
         if (h) cudaFreeHost(h);
     if (sv->h_params) cudaFreeHost(sv->h_params);
-    for (cudaEvent_t e : {sv->front_done[0], sv->front_done[1], sv->count_done, sv->emit_done})
+    for (cudaEvent_t e : {sv->front_done[0], sv->front_done[1], sv->count_done})
+        if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : sv->emit_done)
         if (e) cudaEventDestroy(e);
     if (sv->front) cudaStreamDestroy(sv->front);
     if (sv->stream) cudaStreamDestroy(sv->stream);
@@ -528,6 +535,7 @@ int queue_back(iso_server *sv) {
 // and queue one emission for them.  Returns kBlocked, with nothing queued,
 // when the next mesh must wait for meshes to be taken.
 constexpr int kBlocked = -1;
+constexpr uint32_t kEachEmitMax = 2;   // light-load rounds of at most this many emit request by request
 
 int start_emit(iso_server *sv, uint32_t *completed) {
     iso_volume *v = sv->v;
@@ -595,27 +603,59 @@ int start_emit(iso_server *sv, uint32_t *completed) {
     }
     ISO_CK(cudaMemcpyAsync(sv->d_params, sv->h_params, k * sizeof(Params), cudaMemcpyHostToDevice, st));
     serve_params_kernel<<<1, kMaxServe, 0, st>>>(sv->d_views[t.parity], sv->d_params, k);
-    launch_mc_emit(back_launch(sv, t), false, back_plan(sv, t), st);
-    ISO_CK(cudaEventRecord(sv->emit_done, st));
+    // At light load (a round of one or two requests and no request waiting):
+    // one emission per request, its view by value, in order, so a request
+    // finishes as soon as its own vertices are written.  Otherwise (a
+    // backlog) one emission for all, whose single tail costs less than one
+    // per request.  A view's stored cases are where the front's tail put
+    // them (the same rule, on the host, from the same candidate counts).
+    if (t.run_to - t.emitted > kEachEmitMax || !sv->queue.empty()) {
+        launch_mc_emit(back_launch(sv, t), false, back_plan(sv, t), st);
+        for (uint32_t i = t.emitted; i < t.run_to; i++) ISO_CK(cudaEventRecord(sv->emit_done[i], st));
+        ISO_CK(cudaGetLastError());
+        t.stage = kEmit;
+        return ISO_OK;
+    }
+    uint64_t used = 0;
+    for (uint32_t i = 0; i < k; i++) {
+        VolEntry view = sv->views[t.parity][i];
+        if (k > 1) {
+            const uint64_t n = c[i].n_cand;
+            const bool fits = sv->cases != nullptr && used + n <= sv->case_cap;
+            view.s.cases = fits ? sv->cases + 64ull * used : nullptr;
+            view.s.case_cap = fits ? n : 0ull;
+            if (fits) used += n;
+        }
+        if (i < t.emitted || i >= t.run_to) continue;
+        if (t.bufs[i]) launch_mc_emit(Launch{nullptr, 1u, sv->d_ctr[t.parity], view}, false, sv->one_plan, st);
+        ISO_CK(cudaEventRecord(sv->emit_done[i], st));
+    }
     ISO_CK(cudaGetLastError());
     t.stage = kEmit;
     return ISO_OK;
 }
 
-// An emission round is done: its requests finish.  The tick leaves the back
-// once every request has; otherwise its next round waits for the budget.
-int finish_tick(iso_server *sv, uint32_t *completed) {
-    ISO_CK(cudaEventSynchronize(sv->emit_done));
+// Requests of the running emission round whose emissions are done finish,
+// in order (with `block`, waiting for the first of them).  The tick leaves
+// the back once every request has; after a round, the next one waits for
+// the budget.
+int finish_round(iso_server *sv, bool block, uint32_t *completed) {
     Tick &t = sv->back_tick;
     const Ctl *c = sv->h_ctls[t.parity];
     const Ctl &uni = c[t.reqs.size()];
-    for (uint32_t j = t.emitted; j < t.run_to; j++) {
+    while (t.emitted < t.run_to) {
+        const uint32_t j = t.emitted;
+        if (block) ISO_CK(cudaEventSynchronize(sv->emit_done[j]));
+        else if (!ready(sv->emit_done[j])) break;
+        block = false;
         finish(sv, t.reqs[j], t.status[j], &uni, &c[j], t.status[j] == ISO_OK ? t.bufs[j] : nullptr);
         if (t.status[j] != ISO_OK && t.bufs[j]) dfree_on(t.bufs[j], sv->stream);
         t.bufs[j] = nullptr;                  // the mesh is the finished request's now
         *completed += 1;
+        t.emitted++;
     }
-    t.emitted = t.run_to;
+    if (t.emitted < t.run_to) return ISO_OK;  // the round goes on
+    sv->rounds_finished++;
     if (t.emitted < t.reqs.size()) {
         t.stage = kCount;                     // counted, waiting for its next round
         return ISO_OK;
@@ -638,8 +678,8 @@ int finish_tick(iso_server *sv, uint32_t *completed) {
 int advance(iso_server *sv, bool block, uint32_t *completed) {
     int rc = ISO_OK;
     if (sv->has_back && sv->back_tick.stage == kEmit) {
-        if (!block && !ready(sv->emit_done)) goto admit;
-        rc = finish_tick(sv, completed);
+        if (!block && !ready(sv->emit_done[sv->back_tick.emitted])) goto admit;
+        rc = finish_round(sv, block, completed);
         return rc ? -rc : 1;
     }
     if (sv->has_back && sv->back_tick.stage == kCount) {
@@ -708,7 +748,7 @@ int iso_server_create(iso_server **out, iso_volume *v, const iso_server_options 
     TRY(cuda_ok(cudaStreamCreateWithPriority(&sv->stream, cudaStreamNonBlocking, prio_high)));
     TRY(cuda_ok(cudaStreamCreateWithPriority(&sv->front, cudaStreamNonBlocking, prio_low)));
     TRY(cuda_ok(cudaEventCreateWithFlags(&sv->count_done, cudaEventDisableTiming)));
-    TRY(cuda_ok(cudaEventCreateWithFlags(&sv->emit_done, cudaEventDisableTiming)));
+    for (cudaEvent_t &e : sv->emit_done) TRY(cuda_ok(cudaEventCreateWithFlags(&e, cudaEventDisableTiming)));
     for (int p = 0; p < 2; p++) {
         TRY(cuda_ok(cudaEventCreateWithFlags(&sv->front_done[p], cudaEventDisableTiming)));
         TRY(dalloc_on(&sv->d_views[p], kMaxServe, sv->device, sv->stream));
@@ -815,13 +855,16 @@ int iso_server_step(iso_server *sv, uint32_t *completed) {
     if (!sv) return ISO_ERR_INVALID_ARG;
     uint32_t n = 0;
     DeviceGuard dg(sv->device);
-    const uint64_t ticks0 = sv->ticks_finished;
+    const uint64_t ticks0 = sv->ticks_finished, rounds0 = sv->rounds_finished;
     int r = 0;
     for (;;) {
         r = advance(sv, false, &n);
         if (r > 0) continue;
-        // a tick finished, a failure, or nothing in flight
-        if (r < 0 || n > 0 || sv->ticks_finished != ticks0 || (!sv->has_front && !sv->has_back) || sv->blocked)
+        // an emission round finished, a tick ended otherwise (its requests
+        // failed), a failure, the budget blocks, or nothing is in flight
+        const bool mid_round = sv->has_back && sv->back_tick.stage == kEmit;
+        if (r < 0 || sv->rounds_finished != rounds0 || sv->ticks_finished != ticks0 || (n > 0 && !mid_round) ||
+            (!sv->has_front && !sv->has_back) || sv->blocked)
             break;
         r = advance(sv, true, &n);
         if (r < 0) break;
