@@ -87,11 +87,20 @@ extern "C" {
                                   iso_load_volume; iso_release still frees the volume */
 #define ISO_NO_GRAPH 4u        /* launch each extraction's kernels one by one instead of
                                   replaying the CUDA graphs captured once a volume has been extracted 8 times */
+#define ISO_SEGMENT_CULL 16u   /* keep a range per segment of 64 consecutive blocks (the hull of their
+                                  3x3x3 ranges, 8 bytes per segment); the range test reads it first and
+                                  skips the per-block reads of segments whose range cannot hold the
+                                  isovalue (the same active set: a block's range lies within its
+                                  segment's).  One more dependent read per tile: by default on only for
+                                  volumes of at least 2^28 blocks, where most of the range test's time
+                                  is those reads */
+#define ISO_NO_SEGMENT_CULL 32u /* never keep segment ranges (ISO_SEGMENT_CULL wins if both are set) */
 
 typedef struct iso_volume iso_volume;
 
 typedef struct iso_options {
-    uint32_t flags;            /* ISO_INPUT_ON_DEVICE | ISO_DEBUG | ISO_NO_GRAPH */
+    uint32_t flags;            /* ISO_INPUT_ON_DEVICE | ISO_DEBUG | ISO_NO_GRAPH | ISO_ASYNC_UPLOAD |
+                                  ISO_SEGMENT_CULL | ISO_NO_SEGMENT_CULL */
     uint32_t reserved;
     void *stream;              /* cudaStream_t for all device work; NULL = default stream */
     double initial_cache_fraction; /* initial slots as a fraction of nb; <= 0 means 0.1 (Section 4.2) */

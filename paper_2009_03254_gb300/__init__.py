@@ -32,6 +32,8 @@ ISO_INPUT_ON_DEVICE = 1
 ISO_DEBUG = 2
 ISO_NO_GRAPH = 4
 ISO_ASYNC_UPLOAD = 8
+ISO_SEGMENT_CULL = 16
+ISO_NO_SEGMENT_CULL = 32
 ISO_TEST_WITHHOLD_PREFIX = 1
 ISO_VERTEX_FLOAT4 = 0
 ISO_VERTEX_PACKED = 1
@@ -258,10 +260,12 @@ class Volume:
     dims       (nx, ny, nz)
     rate       bits per sample
     bmin/bmax  per-block ranges of the decoded samples (nb floats each)
+    segment_cull  None: segment ranges for volumes of 2^28 blocks or more;
+               True / False: always / never (ISO_SEGMENT_CULL, ISO_NO_SEGMENT_CULL)
     """
 
     def __init__(self, bits, dims, rate, bmin, bmax, *, stream=None, debug=False, initial_cache_fraction=0.1,
-                 cache_budget_bytes=0, graph=True, async_upload=False):
+                 cache_budget_bytes=0, graph=True, async_upload=False, segment_cull=None):
         self._h = None
         on_device = not isinstance(bits, np.ndarray) and bool(getattr(bits, "is_cuda", False))
         if not isinstance(bits, np.ndarray) and not on_device:       # CPU (e.g. pinned) torch tensors
@@ -275,7 +279,8 @@ class Volume:
         self.nb = int(np.prod(block_dims(self.dims)))
         opt = _Options()
         opt.flags = (ISO_INPUT_ON_DEVICE if on_device else 0) | (ISO_DEBUG if debug else 0) | \
-            (0 if graph else ISO_NO_GRAPH) | (ISO_ASYNC_UPLOAD if async_upload else 0)
+            (0 if graph else ISO_NO_GRAPH) | (ISO_ASYNC_UPLOAD if async_upload else 0) | \
+            ({None: 0, True: ISO_SEGMENT_CULL, False: ISO_NO_SEGMENT_CULL}[segment_cull])
         # with async_upload the bitstream is copied after this returns: keep it alive
         self._upload_source = bits if async_upload else None
         opt.stream = stream if stream is not None else _current_stream()

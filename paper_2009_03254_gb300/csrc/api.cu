@@ -31,7 +31,7 @@ std::mutex g_pool_mutex;
 cudaMemPool_t g_pool[kMaxPoolDevices] = {};
 struct OccEntry {
     int device;
-    int key[7];                   // tile sizes, single/batch, largest rate
+    int key[8];                   // tile sizes, single/batch, largest rate, segment ranges
     Plan limits;
 };
 std::vector<OccEntry> g_occ;      // occupancy limits per (device, tile variants)
@@ -149,10 +149,10 @@ int shape_to_want(const iso_launch_shape *shape, Plan *out) {
     return ISO_OK;
 }
 
-iso_launch_shape shape_of(const Plan &want, int device, bool single, uint32_t max_rate) {
+iso_launch_shape shape_of(const Plan &want, int device, bool single, uint32_t max_rate, bool seg) {
     // CTAs per SM that run: the requested number clamped to the occupancy limit
     const Plan tiles = default_tiles(&want);
-    const Plan lim = occupancy_limits_of(device, tiles, single, max_rate);
+    const Plan lim = occupancy_limits_of(device, tiles, single, max_rate, seg);
     auto run = [](int w, int mx) { return (uint32_t)(w > 0 ? std::min(w, mx) : mx); };
     return iso_launch_shape{run(want.cull, lim.cull), (uint32_t)tiles.cull_tile, run(want.lru_a, lim.lru_a),
                             run(want.decode, lim.decode), (uint32_t)tiles.decode_tile,
@@ -189,22 +189,22 @@ Plan default_tiles(const Plan *want) {
     return t;
 }
 
-Plan occupancy_limits_of(int device, const Plan &tiles, bool single, uint32_t max_rate) {
-    const int key[7] = {tiles.cull_tile, tiles.decode_tile, tiles.count_tile, tiles.scan_tile, tiles.emit_tile,
-                        single ? 1 : 0, (int)max_rate};
+Plan occupancy_limits_of(int device, const Plan &tiles, bool single, uint32_t max_rate, bool seg) {
+    const int key[8] = {tiles.cull_tile, tiles.decode_tile, tiles.count_tile, tiles.scan_tile, tiles.emit_tile,
+                        single ? 1 : 0, (int)max_rate, seg ? 1 : 0};
     std::lock_guard<std::mutex> lock(g_pool_mutex);
     for (const OccEntry &e : g_occ)
-        if (e.device == device && std::equal(key, key + 7, e.key)) return e.limits;
-    OccEntry e{device, {key[0], key[1], key[2], key[3], key[4], key[5], key[6]},
-               occupancy_limits(tiles, single, max_rate)};
+        if (e.device == device && std::equal(key, key + 8, e.key)) return e.limits;
+    OccEntry e{device, {key[0], key[1], key[2], key[3], key[4], key[5], key[6], key[7]},
+               occupancy_limits(tiles, single, max_rate, seg)};
     g_occ.push_back(e);
     return e.limits;
 }
 
 Plan launch_plan(const Plan *want, int device, uint64_t total_blocks, uint64_t total_slots, uint32_t n_vols,
-                 bool single, uint32_t max_rate) {
+                 bool single, uint32_t max_rate, bool seg) {
     const Plan tiles = default_tiles(want);
-    const Plan lim = occupancy_limits_of(device, tiles, single, max_rate);
+    const Plan lim = occupancy_limits_of(device, tiles, single, max_rate, seg);
     Plan use = lim;
     if (want) {
         int *dst = &use.prep;
@@ -290,7 +290,7 @@ int free_volume(iso_volume *v) {
     cudaSetDevice(v->device);
     if (v->upload_stream) cudaStreamSynchronize(v->upload_stream);   // nothing is freed under a copy in flight
     DevState &s = v->s;
-    void *ptrs[] = {v->bits, v->bmin, v->bmax, v->hull, v->hull8, v->tables, s.mactive, s.iactive, s.inew, s.icand,
+    void *ptrs[] = {v->bits, v->bmin, v->bmax, v->hull, v->hull8, v->seg, v->tables, s.mactive, s.iactive, s.inew, s.icand,
                     s.islot, s.slast, s.sblock, s.lbuf[0], s.lbuf[1], s.newslot, s.slots, s.desc_cull, s.desc_cand,
                     s.desc_lru_a, s.desc_lru_b, s.desc_mc, s.ctl, s.counts, s.offsets, s.iocc, s.cases, s.dbg_edges,
                     s.voff, s.cutw};
@@ -596,7 +596,7 @@ int iso_set_shape(iso_volume *v, const iso_launch_shape *shape) {
     DeviceGuard dg(v->device);
     CK(cudaStreamSynchronize(v->stream));
     v->want = w;
-    v->plan = launch_plan(&v->want, v->device, v->g.nb, v->cap, 1, true, v->g.rate);
+    v->plan = launch_plan(&v->want, v->device, v->g.nb, v->cap, 1, true, v->g.rate, v->seg != nullptr);
     for (int k = 0; k < 4; k++) {            // the captured passes hold the old launch shape
         if (v->gexec[k]) cudaGraphExecDestroy(v->gexec[k]);
         if (v->graph[k]) cudaGraphDestroy(v->graph[k]);
@@ -610,7 +610,7 @@ int iso_set_shape(iso_volume *v, const iso_launch_shape *shape) {
 int iso_get_shape(const iso_volume *v, iso_launch_shape *shape) {
     if (!v || !shape) return ISO_ERR_INVALID_ARG;
     DeviceGuard dg(v->device);
-    *shape = shape_of(v->want, v->device, true, v->g.rate);
+    *shape = shape_of(v->want, v->device, true, v->g.rate, v->seg != nullptr);
     return ISO_OK;
 }
 
@@ -712,6 +712,9 @@ int iso_load_volume(iso_volume **out, const void *compressed, size_t compressed_
     }
     TRY(dalloc(v, &v->hull, g.nb));
     TRY(dalloc(v, &v->hull8, g.nb));
+    const bool segments = (o.flags & ISO_SEGMENT_CULL) ||
+                          (!(o.flags & ISO_NO_SEGMENT_CULL) && (uint64_t)g.nb >= kSegmentCullMinBlocks);
+    if (segments) TRY(dalloc(v, &v->seg, (g.nb + kSegBlocks - 1) / kSegBlocks));
     TRY(dalloc(v, &v->tables, 256 + 256 * 16));
     TRY(dalloc(v, &s.mactive, nwords));
     s.list_cap = std::min<uint32_t>(g.nb, v->cap);
@@ -753,6 +756,7 @@ int iso_load_volume(iso_volume **out, const void *compressed, size_t compressed_
     s.bits = v->bits;
     s.hull = v->hull;
     s.hull8 = v->hull8;
+    s.seg = v->seg;
     s.tables = v->tables;
 
     McTables t;
@@ -799,7 +803,7 @@ int iso_load_volume(iso_volume **out, const void *compressed, size_t compressed_
     *v->host_ctl = c0;
     TRYC(cudaMemcpyAsync(s.ctl, v->host_ctl, sizeof(Ctl), cudaMemcpyHostToDevice, st));
     // the ranges are needed only for the hulls (device inputs are read in place)
-    launch_hull(on_device ? block_min : v->bmin, on_device ? block_max : v->bmax, v->hull, v->hull8, g,
+    launch_hull(on_device ? block_min : v->bmin, on_device ? block_max : v->bmax, v->hull, v->hull8, v->seg, g,
                 &s.ctl->status, st);
     TRYC(cudaGetLastError());
     dfree_on(v->bmin, st);
@@ -838,7 +842,7 @@ int iso_load_volume(iso_volume **out, const void *compressed, size_t compressed_
     v->want = Plan{};
     v->want.scan_tile = 4096;
     v->want.mc_scan = 1;
-    v->plan = launch_plan(&v->want, v->device, g.nb, v->cap, 1, true, g.rate);
+    v->plan = launch_plan(&v->want, v->device, g.nb, v->cap, 1, true, g.rate, v->seg != nullptr);
     TRYC(cudaGetLastError());
     *out = v;
     return ISO_OK;

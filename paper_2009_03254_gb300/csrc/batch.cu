@@ -46,6 +46,7 @@ struct iso_batch {
     Plan plan{};                          // what runs
     uint64_t total_blocks = 0, total_slots = 0;
     uint32_t max_rate = 1;                // the largest rate among the volumes
+    uint32_t seg_any = 0;                 // some volume has segment ranges
     cudaStream_t capture_stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -55,7 +56,9 @@ struct iso_batch {
 
 namespace {
 
-Launch launch_of(const iso_batch *b) { return Launch{b->d_entries, b->n, b->d_ctr, VolEntry{}, b->max_rate}; }
+Launch launch_of(const iso_batch *b) {
+    return Launch{b->d_entries, b->n, b->d_ctr, VolEntry{}, b->max_rate, b->seg_any};
+}
 
 // per tuned kernel: its CTA field and tile field in a Plan (tile: null
 // for the cache update, which has one tile size), and the tile variants
@@ -87,7 +90,8 @@ void drop_graph(iso_batch *b) {
 
 void apply_shape(iso_batch *b, const Plan &want) {
     b->want = want;
-    b->plan = launch_plan(&b->want, b->device, b->total_blocks, b->total_slots, b->n, false, b->max_rate);
+    b->plan = launch_plan(&b->want, b->device, b->total_blocks, b->total_slots, b->n, false, b->max_rate,
+                          b->seg_any != 0);
     drop_graph(b);
 }
 
@@ -259,6 +263,7 @@ int iso_batch_create(iso_batch **out, iso_volume *const *volumes, uint32_t n, vo
         b->total_blocks += v->g.nb;
         b->total_slots += v->cap;
         b->max_rate = std::max(b->max_rate, v->g.rate);
+        if (v->seg) b->seg_any = 1;
     }
     // the volumes' own streams may still hold work (a cache reset, a free)
     for (iso_volume *v : vols)
@@ -308,7 +313,7 @@ int iso_batch_set_shape(iso_batch *b, const iso_launch_shape *shape) {
 
 int iso_batch_get_shape(const iso_batch *b, iso_launch_shape *shape) {
     if (!b || !shape) return ISO_ERR_INVALID_ARG;
-    *shape = shape_of(b->want, b->device, false, b->max_rate);
+    *shape = shape_of(b->want, b->device, false, b->max_rate, b->seg_any != 0);
     return ISO_OK;
 }
 
@@ -321,7 +326,8 @@ int iso_batch_tune(iso_batch *b, const float *isovalues, float *d_vertices, uint
     const Plan keep = b->want;
     // one cold run with `want`: per-kernel times (ms) and the total
     auto timed = [&](const Plan &want, float *kernel_ms, float *total_ms) -> int {
-        b->plan = launch_plan(&want, b->device, b->total_blocks, b->total_slots, b->n, false, b->max_rate);
+        b->plan = launch_plan(&want, b->device, b->total_blocks, b->total_slots, b->n, false, b->max_rate,
+                              b->seg_any != 0);
         int r = reset_caches(b);
         if (r) return r;
         r = run_batch(b, true);
@@ -347,7 +353,7 @@ int iso_batch_tune(iso_batch *b, const float *isovalues, float *d_vertices, uint
         Plan tiles{};
         for (int k = 0; k < kKernels; k++)
             if (tile_field(tiles, k)) *tile_field(tiles, k) = kTileVariants[k][std::min(i, kNumVariants[k] - 1)];
-        Plan lim = occupancy_limits_of(b->device, default_tiles(&tiles), false, b->max_rate);
+        Plan lim = occupancy_limits_of(b->device, default_tiles(&tiles), false, b->max_rate, b->seg_any != 0);
         int cmax = 1;
         for (int k = 0; k < kKernels; k++) cmax = std::max(cmax, *ctas_field(lim, k));
         for (int c = 1; c <= cmax; c++) {

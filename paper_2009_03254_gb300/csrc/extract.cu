@@ -83,7 +83,8 @@ struct CullSmem {
     uint32_t bal[3][kR][8];           // active, new, candidate ballots
 };
 
-template <int kR>
+// kSeg: the variant that reads segment ranges first (where a volume has them)
+template <int kR, bool kSeg>
 __device__ __forceinline__ void cull_tile(const DevState &s, const Geom &g, uint32_t tile, uint32_t ntiles,
                                           CullSmem<kR> &sm) {
     constexpr uint32_t kTile = kR * kThreads;
@@ -103,12 +104,27 @@ __device__ __forceinline__ void cull_tile(const DevState &s, const Geom &g, uint
     constexpr int kHalf = kR / 2;
 #pragma unroll
     for (int half = 0; half < 2; half++) {
+        // with segment ranges, a block's reads are skipped when its segment's
+        // range cannot hold the isovalue (a whole round of 256 blocks spans 4
+        // segments: the warp's 32 lanes read one, a broadcast)
+        uint32_t live = ~0u;
+        if (kSeg && s.seg != nullptr && !all) {   // uniform
+            float2 sh[kHalf];
+#pragma unroll
+            for (int i = 0; i < kHalf; i++) {
+                const uint32_t b = tile * kTile + (half * kHalf + i) * kThreads + threadIdx.x;
+                sh[i] = b < g.nb ? __ldg(s.seg + b / kSegBlocks) : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int i = 0; i < kHalf; i++)
+                if (!((sh[i].x < iso) && (iso <= sh[i].y))) live &= ~(1u << i);
+        }
         float2 h[kHalf], h8[kHalf];
         int32_t sl[kHalf];
 #pragma unroll
         for (int i = 0; i < kHalf; i++) {
             const uint32_t b = tile * kTile + (half * kHalf + i) * kThreads + threadIdx.x;
-            const bool in = b < g.nb;
+            const bool in = b < g.nb && (!kSeg || ((live >> i) & 1u));
             h[i] = in ? __ldg(s.hull + b) : make_float2(0.f, 0.f);
             h8[i] = in ? __ldg(s.hull8 + b) : make_float2(0.f, 0.f);
             sl[i] = in ? s.islot[b] : -1;
@@ -181,7 +197,7 @@ __device__ __forceinline__ void cull_tile(const DevState &s, const Geom &g, uint
     __syncthreads();
 }
 
-template <int kR, bool kOne>
+template <int kR, bool kOne, bool kSeg>
 __global__ void __launch_bounds__(kThreads) cull_kernel(Launch L) {
     __shared__ CullSmem<kR> sm;
     __shared__ uint32_t pre[kMaxBatch + 1];
@@ -193,7 +209,7 @@ __global__ void __launch_bounds__(kThreads) cull_kernel(Launch L) {
         if (x >= total) break;
         const uint32_t v = item_vol<kOne>(pre, L.n, x);
         const VolEntry &e = vol_of<kOne>(L, v);
-        cull_tile(e.s, e.g, x - item_base<kOne>(pre, v), vol_items<kOne>(pre, v, total), sm);
+        cull_tile<kR, kSeg>(e.s, e.g, x - item_base<kOne>(pre, v), vol_items<kOne>(pre, v, total), sm);
     }
 }
 
@@ -581,6 +597,31 @@ __global__ void hull_kernel(const float *__restrict__ bmin, const float *__restr
     }
 }
 
+// One warp per segment of kSegBlocks consecutive blocks: the min of their
+// hulls' lows and the max of their highs.  A block is active only if
+// lo < iso <= hi for its own hull, which lies within its segment's.
+__global__ void seg_hull_kernel(const float2 *__restrict__ hull, float2 *seg, uint32_t nb) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t nseg = (nb + kSegBlocks - 1) / kSegBlocks;
+    for (uint32_t q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nseg; q += (gridDim.x * blockDim.x) >> 5) {
+        float lo = INFINITY, hi = -INFINITY;
+        for (uint32_t k = lane; k < kSegBlocks; k += 32) {
+            const uint64_t b = (uint64_t)q * kSegBlocks + k;
+            if (b < nb) {
+                const float2 h = hull[b];
+                lo = fminf(lo, h.x);
+                hi = fmaxf(hi, h.y);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+            hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        }
+        if (lane == 0) seg[q] = make_float2(lo, hi);
+    }
+}
+
 __global__ void reset_cache_kernel(DevState s) {
     Ctl *c = s.ctl;
     const uint32_t cap = c->cap;
@@ -634,8 +675,14 @@ template <bool kOne>
 void front(const Launch &L, const Plan &pl, cudaStream_t st, cudaEvent_t *ev, cudaEvent_t bits_ready) {
     prep_kernel<kOne><<<pl.prep, kThreads, 0, st>>>(L);
     if (ev) cudaEventRecord(ev[1], st);
-    if (pl.cull_tile == 2048) cull_kernel<8, kOne><<<pl.cull, kThreads, 0, st>>>(L);
-    else cull_kernel<16, kOne><<<pl.cull, kThreads, 0, st>>>(L);
+    const bool seg = kOne ? L.one.s.seg != nullptr : L.seg_any != 0;
+    if (pl.cull_tile == 2048) {
+        if (seg) cull_kernel<8, kOne, true><<<pl.cull, kThreads, 0, st>>>(L);
+        else cull_kernel<8, kOne, false><<<pl.cull, kThreads, 0, st>>>(L);
+    } else {
+        if (seg) cull_kernel<16, kOne, true><<<pl.cull, kThreads, 0, st>>>(L);
+        else cull_kernel<16, kOne, false><<<pl.cull, kThreads, 0, st>>>(L);
+    }
     if (ev) cudaEventRecord(ev[2], st);
     cache_update<kOne>(L, pl, st, ev, bits_ready);
 }
@@ -663,10 +710,14 @@ void launch_batch_gather(const Launch &L, Ctl *dst, cudaStream_t st) {
     batch_gather_kernel<<<(words + 255) / 256, 256, 0, st>>>(L, dst);
 }
 
-void launch_hull(const float *bmin, const float *bmax, float2 *hull, float2 *hull8, const Geom &g,
+void launch_hull(const float *bmin, const float *bmax, float2 *hull, float2 *hull8, float2 *seg, const Geom &g,
                  uint32_t *status, cudaStream_t st) {
     const uint32_t blocks = std::min<uint32_t>((g.nb + 255) / 256, 65535u * 4);
     hull_kernel<<<blocks, 256, 0, st>>>(bmin, bmax, hull, hull8, g, status);
+    if (seg) {
+        const uint32_t nseg = (g.nb + kSegBlocks - 1) / kSegBlocks;
+        seg_hull_kernel<<<std::min<uint32_t>((nseg + 7) / 8, 65535u * 4), 256, 0, st>>>(hull, seg, g.nb);
+    }
 }
 
 void launch_reset_cache(const DevState &s, cudaStream_t st) {
@@ -693,11 +744,15 @@ void set_decode_attributes() {
 }
 
 template <bool kOne>
-Plan limits_of(const Plan &tiles, uint32_t rate) {
+Plan limits_of(const Plan &tiles, uint32_t rate, bool seg) {
     Plan pl = tiles;
     int occ = 0;
-    if (tiles.cull_tile == 2048) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cull_kernel<8, kOne>, kThreads, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cull_kernel<16, kOne>, kThreads, 0);
+    if (tiles.cull_tile == 2048)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, seg ? cull_kernel<8, kOne, true> : cull_kernel<8, kOne, false>,
+                                                      kThreads, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &occ, seg ? cull_kernel<16, kOne, true> : cull_kernel<16, kOne, false>, kThreads, 0);
     pl.cull = std::max(1, occ);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lru_a_kernel<kOne>, kThreads, 0);
     pl.lru_a = std::max(1, occ);
@@ -718,8 +773,8 @@ Plan limits_of(const Plan &tiles, uint32_t rate) {
     return pl;
 }
 
-Plan occupancy_limits(const Plan &tiles, bool single, uint32_t rate) {
-    return single ? limits_of<true>(tiles, rate) : limits_of<false>(tiles, rate);
+Plan occupancy_limits(const Plan &tiles, bool single, uint32_t rate, bool seg) {
+    return single ? limits_of<true>(tiles, rate, seg) : limits_of<false>(tiles, rate, seg);
 }
 
 bool valid_tiles(const Plan &pl) {

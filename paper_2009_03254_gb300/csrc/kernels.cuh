@@ -14,6 +14,8 @@ struct DevState {
     const uint64_t *bits;      // nb * rate words
     const float2 *hull;        // per block: min/max over its 3x3x3 block neighbourhood
     const float2 *hull8;       // per block: min/max over its 2x2x2 +group
+    const float2 *seg;         // per segment of 64 consecutive blocks: the hull of their hulls (null:
+                               // the range test reads every block's hull)
     uint32_t *mactive;         // M_active bitmask, ceil(nb/32) words
     uint32_t *iactive;         // I_active (kept only for debugging: nothing downstream reads it; else null)
     uint32_t *inew;            // I_new
@@ -68,6 +70,7 @@ struct Launch {
     uint32_t *ctr;
     VolEntry one;
     uint32_t max_rate = 0;   // batches: the largest rate among the volumes (sizes the decoder's staging)
+    uint32_t seg_any = 0;    // batches: some volume has segment ranges (the range test's segment variant)
 };
 
 // How a launch sequence runs: the CTAs of each persistent kernel and the
@@ -114,8 +117,11 @@ void launch_batch_params(const Launch &L, const float *d_iso, cudaStream_t st);
 void launch_batch_offsets(const Launch &L, const BatchOut *bo, unsigned long long *tri_base, cudaStream_t st);
 void launch_batch_gather(const Launch &L, Ctl *dst, cudaStream_t st);
 
-void launch_hull(const float *bmin, const float *bmax, float2 *hull, float2 *hull8, const Geom &g,
+// the blocks' hulls and, with `seg`, the segments' (64 consecutive blocks each)
+void launch_hull(const float *bmin, const float *bmax, float2 *hull, float2 *hull8, float2 *seg, const Geom &g,
                  uint32_t *status, cudaStream_t st);
+constexpr uint32_t kSegBlocks = 64;                  // blocks per segment of the segment ranges
+constexpr uint64_t kSegmentCullMinBlocks = 1ull << 28;   // default: segment ranges from this many blocks
 void launch_reset_cache(const DevState &s, cudaStream_t st);
 void launch_encode(const float *field, const Geom &g, uint64_t *bits, float *bmin, float *bmax, cudaStream_t st);
 void launch_decode_list(const uint64_t *bits, uint32_t rate, const uint32_t *ids, uint64_t n, float *out,
@@ -130,7 +136,7 @@ void launch_gather_slots(const float *slots, const int32_t *islot, const uint32_
 // `tiles`, in single-volume or batch launches (CTA fields of the result;
 // tile fields copied).  Also raises the shared-memory limits of every
 // kernel that needs more than the default.
-Plan occupancy_limits(const Plan &tiles, bool single, uint32_t rate);
+Plan occupancy_limits(const Plan &tiles, bool single, uint32_t rate, bool seg = false);
 void mc_occupancy(Plan *pl, bool single);
 // tile sizes that the kernels are compiled for
 bool valid_tiles(const Plan &pl);

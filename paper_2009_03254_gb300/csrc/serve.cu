@@ -127,8 +127,9 @@ struct ServeCullSmem {
     uint32_t bal[2 + kMaxServe][kRounds][8];  // union active, new, candidates
 };
 
-// kT: a power of two at least k + k_pin (the isovalue loop is unrolled to it)
-template <int kT>
+// kT: a power of two at least k + k_pin (the isovalue loop is unrolled to it);
+// kSeg: the volume has segment ranges
+template <int kT, bool kSeg>
 __global__ void __launch_bounds__(kThreads) serve_cull_kernel(ServeArgs a) {
     __shared__ ServeCullSmem sm;
     __shared__ uint32_t slot_x;
@@ -150,12 +151,31 @@ __global__ void __launch_bounds__(kThreads) serve_cull_kernel(ServeArgs a) {
         constexpr int kHalf = kRounds / 2;
 #pragma unroll
         for (int half = 0; half < 2; half++) {
+            // with segment ranges, a block's reads are skipped when its
+            // segment's range holds none of the tick's isovalues
+            uint32_t live = ~0u;
+            if (kSeg) {
+                float2 sh[kHalf];
+#pragma unroll
+                for (int i = 0; i < kHalf; i++) {
+                    const uint32_t b = tile * kTile + (half * kHalf + i) * kThreads + threadIdx.x;
+                    sh[i] = b < g.nb ? __ldg(s.seg + b / kSegBlocks) : make_float2(0.f, 0.f);
+                }
+#pragma unroll
+                for (int i = 0; i < kHalf; i++) {
+                    bool any = false;
+#pragma unroll
+                    for (int j = 0; j < kT; j++)
+                        if (j < (int)(k + a.k_pin)) any = any || (sh[i].x < a.iso[j] && a.iso[j] <= sh[i].y);
+                    if (!any) live &= ~(1u << i);
+                }
+            }
             float2 h[kHalf], h8[kHalf];
             int32_t sl[kHalf];
 #pragma unroll
             for (int i = 0; i < kHalf; i++) {
                 const uint32_t b = tile * kTile + (half * kHalf + i) * kThreads + threadIdx.x;
-                const bool in = b < g.nb;
+                const bool in = b < g.nb && (!kSeg || ((live >> i) & 1u));
                 h[i] = in ? __ldg(s.hull + b) : make_float2(0.f, 0.f);
                 h8[i] = in ? __ldg(s.hull8 + b) : make_float2(0.f, 0.f);
                 sl[i] = in ? s.islot[b] : -1;
@@ -459,6 +479,15 @@ bool ready(cudaEvent_t e) {
     return true;
 }
 
+template <bool kSeg>
+void launch_serve_cull(uint32_t kt, int ctas, const ServeArgs &a, cudaStream_t st) {
+    if (kt <= 1) serve_cull_kernel<1, kSeg><<<ctas, kThreads, 0, st>>>(a);
+    else if (kt <= 2) serve_cull_kernel<2, kSeg><<<ctas, kThreads, 0, st>>>(a);
+    else if (kt <= 4) serve_cull_kernel<4, kSeg><<<ctas, kThreads, 0, st>>>(a);
+    else if (kt <= 8) serve_cull_kernel<8, kSeg><<<ctas, kThreads, 0, st>>>(a);
+    else serve_cull_kernel<16, kSeg><<<ctas, kThreads, 0, st>>>(a);
+}
+
 // Admit the queue's first requests as a tick and queue its front on the
 // front stream (pins: the tick in its back, or null).
 int launch_front(iso_server *sv, const std::vector<Request> *pins) {
@@ -476,11 +505,8 @@ int launch_front(iso_server *sv, const std::vector<Request> *pins) {
     cudaStream_t st = sv->front;
     serve_prep_kernel<<<v->plan.prep, kThreads, 0, st>>>(a);
     const uint32_t kt = a.k + a.k_pin;
-    if (kt <= 1) serve_cull_kernel<1><<<v->plan.cull, kThreads, 0, st>>>(a);
-    else if (kt <= 2) serve_cull_kernel<2><<<v->plan.cull, kThreads, 0, st>>>(a);
-    else if (kt <= 4) serve_cull_kernel<4><<<v->plan.cull, kThreads, 0, st>>>(a);
-    else if (kt <= 8) serve_cull_kernel<8><<<v->plan.cull, kThreads, 0, st>>>(a);
-    else serve_cull_kernel<16><<<v->plan.cull, kThreads, 0, st>>>(a);
+    if (v->seg) launch_serve_cull<true>(kt, v->plan.cull, a, st);
+    else launch_serve_cull<false>(kt, v->plan.cull, a, st);
     launch_cache_update(single, v->plan, st);
     serve_front_tail_kernel<<<1, 32, 0, st>>>(a);
     ISO_CK(cudaEventRecord(sv->front_done[t.parity], st));

@@ -46,6 +46,7 @@ struct iso_volume {
     uint64_t *bits = nullptr;
     float *bmin = nullptr, *bmax = nullptr;   // staging of host block ranges during the load only
     float2 *hull = nullptr, *hull8 = nullptr;
+    float2 *seg = nullptr;            // segment ranges (ISO_SEGMENT_CULL, or large volumes by default)
     uint8_t *tables = nullptr;
     unsigned long long dbg_edges_cap = 0;   // in vertices
     unsigned long long last_vtx = 0;        // vertices of the last indexed extraction
@@ -124,7 +125,7 @@ void fill_stats(const bcmc::Ctl &c, iso_stats *st, uint32_t reruns);
 // launch (times the SM count, but no more than the launch can have work
 // items) and the tile sizes.
 bcmc::Plan launch_plan(const bcmc::Plan *want, int device, uint64_t total_blocks, uint64_t total_slots,
-                       uint32_t n_vols, bool single, uint32_t max_rate);
+                       uint32_t n_vols, bool single, uint32_t max_rate, bool seg = false);
 
 // the tile fields of `want`, defaults where 0
 bcmc::Plan default_tiles(const bcmc::Plan *want);
@@ -133,11 +134,12 @@ bcmc::Plan default_tiles(const bcmc::Plan *want);
 int shape_to_want(const iso_launch_shape *shape, bcmc::Plan *out);
 
 // the launch shape that runs for a requested plan (CTAs clamped to the occupancy limits)
-iso_launch_shape shape_of(const bcmc::Plan &want, int device, bool single, uint32_t max_rate);
+iso_launch_shape shape_of(const bcmc::Plan &want, int device, bool single, uint32_t max_rate, bool seg = false);
 
 // largest CTAs per SM of each kernel for these tile sizes, in single-volume
 // or batch launches whose largest rate is max_rate (cached per device)
-bcmc::Plan occupancy_limits_of(int device, const bcmc::Plan &tiles, bool single, uint32_t max_rate);
+bcmc::Plan occupancy_limits_of(int device, const bcmc::Plan &tiles, bool single, uint32_t max_rate,
+                               bool seg = false);
 
 // the verdict of an asynchronous load's range check (waits for the load's
 // own work, not for the bitstream): ISO_ERR_CORRUPT for ranges that are not

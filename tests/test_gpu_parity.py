@@ -206,6 +206,73 @@ def test_extract_matches_oracle(kind, dims, rate):
         vol.release()
 
 
+SEGMENT_CASES = [("sphere", (64, 64, 64), 16), ("noise", (96, 80, 72), 8), ("sphere", (130, 70, 36), 4),
+                 ("special", (18, 10, 9), 16), ("wide", (13, 9, 6), 32), ("random", (2, 3, 5), 8)]
+
+
+@pytest.mark.parametrize("kind,dims,rate", SEGMENT_CASES)
+def test_segment_cull_matches_oracle(kind, dims, rate):
+    # segment ranges forced on: the range test reads a segment's range first
+    # and skips the blocks of segments that cannot hold the isovalue; the
+    # active set, candidates and surface are the oracle's (the sphere and the
+    # isovalues far in the tails leave most segments skipped)
+    f = make_field(kind, dims, 7)
+    bits, bmin, bmax = oracle.encode_volume(f, rate)
+    d = oracle.decode_volume(bits, dims, rate)
+    isos = [0.0, float(np.median(d)), float(np.quantile(d, 0.02)), float(np.quantile(d, 0.98)), float(d.min()),
+            float(d.max()), 1e9]
+    vol = pkg().Volume(bits, dims, rate, bmin, bmax, debug=True, segment_cull=True)
+    try:
+        for iso in isos:
+            check_surface(vol, bits, dims, rate, bmin, bmax, iso)
+    finally:
+        vol.release()
+
+
+def test_segment_cull_serving_and_batch_equal_plain():
+    # the serving cull and a batch over segment-cull volumes give the plain
+    # volume's meshes byte for byte
+    p = pkg()
+    dims, rate = (96, 80, 72), 8
+    f = make_field("noise", dims, 11)
+    bits, bmin, bmax = oracle.encode_volume(f, rate)
+    d = oracle.decode_volume(bits, dims, rate)
+    isos = [float(x) for x in np.quantile(d, [0.05, 0.5, 0.95])]
+    plain = p.Volume(bits, dims, rate, bmin, bmax, segment_cull=False)
+    seg = p.Volume(bits, dims, rate, bmin, bmax, segment_cull=True)
+    srv = p.Server(seg, max_batch=2)
+    try:
+        tickets = [srv.submit(x) for x in isos]
+        while srv.queued():
+            srv.step()
+        for t, x in zip(tickets, isos):
+            status, m = srv.take(t)
+            assert status == p.ISO_OK
+            ref = plain.extract(x)
+            assert m.num_triangles == ref.num_triangles
+            if ref.num_triangles:
+                assert np.array_equal(m.vertices.cpu().numpy().view(np.uint32),
+                                      ref.vertices.cpu().numpy().view(np.uint32))
+            m.release()
+            ref.release()
+        srv.release()
+        srv = None
+        batch = p.Batch([seg, plain])
+        try:
+            verts, offs, _ = batch.extract([isos[1], isos[1]])
+            v = verts.cpu().numpy().view(np.uint32).reshape(-1, 3, 4)
+            a, b = v[int(offs[0]):int(offs[1])], v[int(offs[1]):int(offs[2])]
+            assert len(a) == len(b) > 0
+            assert np.array_equal(a, b)
+        finally:
+            batch.release()
+    finally:
+        if srv is not None:
+            srv.release()
+        seg.release()
+        plain.release()
+
+
 def test_sphere64_closed_surface_on_gpu():
     # the 64^3 sphere distance field at 16 bits/value: watertight, genus 0
     f = fields.sphere_sdf(64, 64, 64, 20.0)
