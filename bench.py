@@ -26,11 +26,13 @@ Metric: triangles/s (whole step, all five surfaces), with voxels/s
            n_new * (8R + 256) + 48T, over its CUDA-event duration, against
            the measured HBM copy peak; the dominant kernel's own figure
            (algorithmic bytes per launch over its duration) nested in it
-  serving  the request loop on the full-size serving volume (10240 x 7680
-           x 1536 channel flow, 2 bits/value, 64 GB cache budget): Poisson
-           isovalue requests served by the batched server (max_batch 2) and
-           by the plain per-request path, and both under overload; p50/p99
-           latency and triangles/s; a warm single request both ways
+  serving  the request loop on the serving volume at a quarter of its x
+           and y extent (2560 x 1920 x 1536 channel flow, 2 bits/value,
+           4 GB cache budget): Poisson isovalue requests served by the
+           batched server (max_batch 2 and 8) and by the plain per-request
+           path, and both under overload; p50/p99 latency and triangles/s;
+           a warm single request both ways (--workload serve runs the full
+           size)
   configs  sphere64 and channel2k extracted whole, cold and warm
   cpu_baseline  the plain CPU oracle on a bounded window of the same field
   parity   the library on that window against the oracle's surfaces:
@@ -850,7 +852,7 @@ def run_ours(args):
             torch.cuda.empty_cache()
             try:
                 serve = serving_summary(measure_serving(bc, torch, SERVE_LEG_SCALE, SERVE_LEG_REQUESTS,
-                                                        batches=(2,), sweeps=False))
+                                                        batches=(2, 8), sweeps=False))
             except Exception as e:                  # reported in the line; the other legs stand
                 serve = {"error": f"{type(e).__name__}: {e}"}
             bc.release_cached_memory()
@@ -951,8 +953,8 @@ def run_ours(args):
 # ---------------------------------------------------------------- serving
 
 SERVE_BUDGET_BYTES = 64e9          # decoded-block cache budget of the serving volume (scaled with its area)
-SERVE_LEG_SCALE = 1.0              # the default run's serving leg: the full-size volume
-SERVE_LEG_REQUESTS = 150
+SERVE_LEG_SCALE = 0.25             # the default run's serving leg: x and y at a quarter (1/16 of the samples)
+SERVE_LEG_REQUESTS = 300
 SERVE_VERTEX_BUDGET = 48e9         # finished meshes held by the server at once (not scaled with the volume)
 
 

@@ -98,12 +98,13 @@ __device__ __forceinline__ void cull_tile(const DevState &s, const Geom &g, uint
     const bool win = (prm.flags & kParamWindow) != 0;
     const uint32_t w_lo = win ? prm.win_lo : 0u, w_act = win ? prm.win_act_hi : g.nb,
                    w_cand = win ? prm.win_cand_hi : g.nb;
-    // two halves of kR/2 rounds; in each, every load (3x3x3 hull, +group
-    // hull, slot) is issued before any of it is used, so a tile waits for
-    // two memory round trips rather than one per round
-    constexpr int kHalf = kR / 2;
+    // groups of kHalf rounds (two groups for tiles of 2048 and 4096 blocks,
+    // four for 8192); in each, every load (3x3x3 hull, +group hull, slot)
+    // is issued before any of it is used, so a tile waits for one memory
+    // round trip per group rather than one per round
+    constexpr int kHalf = kR >= 16 ? 8 : kR / 2;
 #pragma unroll
-    for (int half = 0; half < 2; half++) {
+    for (int half = 0; half < kR / kHalf; half++) {
         // with segment ranges, a block's reads are skipped when its segment's
         // range cannot hold the isovalue (a whole round of 256 blocks spans 4
         // segments: the warp's 32 lanes read one, a broadcast)
@@ -675,14 +676,12 @@ template <bool kOne>
 void front(const Launch &L, const Plan &pl, cudaStream_t st, cudaEvent_t *ev, cudaEvent_t bits_ready) {
     prep_kernel<kOne><<<pl.prep, kThreads, 0, st>>>(L);
     if (ev) cudaEventRecord(ev[1], st);
-    const bool seg = kOne ? L.one.s.seg != nullptr : L.seg_any != 0;
-    if (pl.cull_tile == 2048) {
-        if (seg) cull_kernel<8, kOne, true><<<pl.cull, kThreads, 0, st>>>(L);
-        else cull_kernel<8, kOne, false><<<pl.cull, kThreads, 0, st>>>(L);
-    } else {
-        if (seg) cull_kernel<16, kOne, true><<<pl.cull, kThreads, 0, st>>>(L);
-        else cull_kernel<16, kOne, false><<<pl.cull, kThreads, 0, st>>>(L);
-    }
+    // volumes with segment ranges (the largest) take 8192-block tiles: half
+    // the look-back walks of 4096-block tiles, whose depth grows with the
+    // tiles in flight
+    if (kOne ? L.one.s.seg != nullptr : L.seg_any != 0) cull_kernel<32, kOne, true><<<pl.cull, kThreads, 0, st>>>(L);
+    else if (pl.cull_tile == 2048) cull_kernel<8, kOne, false><<<pl.cull, kThreads, 0, st>>>(L);
+    else cull_kernel<16, kOne, false><<<pl.cull, kThreads, 0, st>>>(L);
     if (ev) cudaEventRecord(ev[2], st);
     cache_update<kOne>(L, pl, st, ev, bits_ready);
 }
@@ -747,12 +746,9 @@ template <bool kOne>
 Plan limits_of(const Plan &tiles, uint32_t rate, bool seg) {
     Plan pl = tiles;
     int occ = 0;
-    if (tiles.cull_tile == 2048)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, seg ? cull_kernel<8, kOne, true> : cull_kernel<8, kOne, false>,
-                                                      kThreads, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &occ, seg ? cull_kernel<16, kOne, true> : cull_kernel<16, kOne, false>, kThreads, 0);
+    if (seg) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cull_kernel<32, kOne, true>, kThreads, 0);
+    else if (tiles.cull_tile == 2048) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cull_kernel<8, kOne, false>, kThreads, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cull_kernel<16, kOne, false>, kThreads, 0);
     pl.cull = std::max(1, occ);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lru_a_kernel<kOne>, kThreads, 0);
     pl.lru_a = std::max(1, occ);

@@ -121,19 +121,22 @@ __global__ void __launch_bounds__(kThreads) serve_prep_kernel(ServeArgs a) {
 // request j when it is active for iso_j and its +group range contains
 // iso_j (as in the single-volume cull).  Hits of the union are stamped with
 // the epoch; the union's active and new lists feed the cache update.
+template <int kR>
 struct ServeCullSmem {
-    TileScan<kRounds> ts;                     // union: active << 16 | new
-    TileScan<kRounds> tc[kMaxServe];          // candidates of each request
-    uint32_t bal[2 + kMaxServe][kRounds][8];  // union active, new, candidates
+    TileScan<kR> ts;                          // union: active << 16 | new
+    TileScan<kR> tc[kMaxServe];               // candidates of each request
+    uint32_t bal[2 + kMaxServe][kR][8];       // union active, new, candidates
 };
 
 // kT: a power of two at least k + k_pin (the isovalue loop is unrolled to it);
-// kSeg: the volume has segment ranges
+// kSeg: the volume has segment ranges (and, like the single-volume range
+// test, then takes tiles of 8192 blocks: 32 rounds)
 template <int kT, bool kSeg>
 __global__ void __launch_bounds__(kThreads) serve_cull_kernel(ServeArgs a) {
-    __shared__ ServeCullSmem sm;
+    constexpr int kR = kSeg ? 32 : kRounds;
+    __shared__ ServeCullSmem<kR> sm;
     __shared__ uint32_t slot_x;
-    constexpr uint32_t kTile = kRounds * kThreads;
+    constexpr uint32_t kTile = kR * kThreads;
     const DevState &s = a.base.s;
     const Geom &g = a.base.g;
     Ctl *c = s.ctl;
@@ -145,12 +148,12 @@ __global__ void __launch_bounds__(kThreads) serve_cull_kernel(ServeArgs a) {
     while (true) {
         const uint32_t tile = next_item(&c->ctr[kLcCull], &slot_x);
         if (tile >= ntiles) break;
-        // two halves of kRounds/2 rounds; in each, every load (3x3x3 hull,
-        // +group hull, slot) is issued before any of it is used, so a tile
-        // waits for two memory round trips rather than one per round
-        constexpr int kHalf = kRounds / 2;
+        // groups of kHalf rounds; in each, every load (3x3x3 hull, +group
+        // hull, slot) is issued before any of it is used, so a tile waits
+        // for one memory round trip per group rather than one per round
+        constexpr int kHalf = kR >= 16 ? 8 : kR / 2;
 #pragma unroll
-        for (int half = 0; half < 2; half++) {
+        for (int half = 0; half < kR / kHalf; half++) {
             // with segment ranges, a block's reads are skipped when its
             // segment's range holds none of the tick's isovalues
             uint32_t live = ~0u;
@@ -252,7 +255,7 @@ __global__ void __launch_bounds__(kThreads) serve_cull_kernel(ServeArgs a) {
         __syncthreads();
         const uint32_t act_base = (uint32_t)(sm.ts.excl >> 31), new_base = (uint32_t)(sm.ts.excl & 0x7FFFFFFFu);
 #pragma unroll 2
-        for (int r = 0; r < kRounds; r++) {
+        for (int r = 0; r < kR; r++) {
             const uint32_t b = tile * kTile + r * kThreads + threadIdx.x;
             const uint32_t ab = sm.bal[0][r][warp], nbits = sm.bal[1][r][warp];
             const uint32_t off = sm.ts.cnt[r][warp];
@@ -528,6 +531,22 @@ const Plan &back_plan(const iso_server *sv, const Tick &t) {
     return t.reqs.size() == 1 ? sv->one_plan : sv->back_plan;
 }
 
+// On a volume with segment ranges (the largest), a tick's count, scan and
+// emission run one launch per request, each view by value with its own
+// work counters and no stored cases: there a launch over one view is
+// faster per view than one over the table (measured 3.8 against 5.0 ms of
+// count per request of a 10240 x 7680 x 1536 volume), a launch's tail is
+// negligible against its work, and stored cases gain nothing.
+bool per_view(const iso_server *sv) { return sv->v->seg != nullptr; }
+
+Launch view_launch(const iso_server *sv, const Tick &t, uint32_t j) {
+    VolEntry view = sv->views[t.parity][j];
+    view.s.cases = nullptr;
+    view.s.case_cap = 0;
+    uint32_t *ctr = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(view.s.ctl) + offsetof(Ctl, ctr));
+    return Launch{nullptr, 1u, ctr, view};
+}
+
 // Queue the count and scan of the tick whose front was just queued (or is
 // running) behind the front's event, then one readback of every request's
 // control block and the union's.  Nothing waits on the host: the union is
@@ -538,10 +557,18 @@ int queue_back(iso_server *sv) {
     sv->has_front = false;
     const uint32_t k = (uint32_t)t.reqs.size();
     ISO_CK(cudaStreamWaitEvent(st, sv->front_done[t.parity], 0));
-    const Launch L = back_launch(sv, t);
-    const Plan &pl = back_plan(sv, t);
-    launch_mc_count(L, false, pl, st);
-    launch_mc_scan(L, pl, st);
+    if (per_view(sv)) {
+        for (uint32_t j = 0; j < k; j++) {
+            const Launch L = view_launch(sv, t, j);
+            launch_mc_count(L, false, sv->one_plan, st);
+            launch_mc_scan(L, sv->one_plan, st);
+        }
+    } else {
+        const Launch L = back_launch(sv, t);
+        const Plan &pl = back_plan(sv, t);
+        launch_mc_count(L, false, pl, st);
+        launch_mc_scan(L, pl, st);
+    }
     serve_gather_kernel<<<1, 256, 0, st>>>(t.args, sv->d_ctls[t.parity]);
     ISO_CK(cudaMemcpyAsync(sv->h_ctls[t.parity], sv->d_ctls[t.parity], (k + 1) * sizeof(Ctl), cudaMemcpyDeviceToHost,
                            st));
@@ -635,7 +662,7 @@ int start_emit(iso_server *sv, uint32_t *completed) {
     // backlog) one emission for all, whose single tail costs less than one
     // per request.  A view's stored cases are where the front's tail put
     // them (the same rule, on the host, from the same candidate counts).
-    if (t.run_to - t.emitted > kEachEmitMax || !sv->queue.empty()) {
+    if (!per_view(sv) && (t.run_to - t.emitted > kEachEmitMax || !sv->queue.empty())) {
         launch_mc_emit(back_launch(sv, t), false, back_plan(sv, t), st);
         for (uint32_t i = t.emitted; i < t.run_to; i++) ISO_CK(cudaEventRecord(sv->emit_done[i], st));
         ISO_CK(cudaGetLastError());
@@ -653,7 +680,10 @@ int start_emit(iso_server *sv, uint32_t *completed) {
             if (fits) used += n;
         }
         if (i < t.emitted || i >= t.run_to) continue;
-        if (t.bufs[i]) launch_mc_emit(Launch{nullptr, 1u, sv->d_ctr[t.parity], view}, false, sv->one_plan, st);
+        if (t.bufs[i]) {
+            const Launch L = per_view(sv) ? view_launch(sv, t, i) : Launch{nullptr, 1u, sv->d_ctr[t.parity], view};
+            launch_mc_emit(L, false, sv->one_plan, st);
+        }
         ISO_CK(cudaEventRecord(sv->emit_done[i], st));
     }
     ISO_CK(cudaGetLastError());
@@ -693,6 +723,16 @@ int finish_round(iso_server *sv, bool block, uint32_t *completed) {
     return ISO_OK;
 }
 
+// A front may overlap the running tick (its isovalues pinned in the new
+// union) only when that tick's union takes at most half the cache: a union
+// with the pins is then likely to fit, while one that does not fit wastes
+// the whole front (its cull reads the ranges for every pinned isovalue too)
+// before going back to the queue.
+bool room_to_pin(const iso_server *sv) {
+    const Tick &t = sv->back_tick;
+    return (uint64_t)sv->h_ctls[t.parity][t.reqs.size()].n_active * 2 <= sv->v->cap;
+}
+
 // One transition of the pipeline, the latest stage first: a finished
 // emission completes its tick; returned counts start the emission; a
 // finished front (with no tick in its back) starts the count; a free front
@@ -726,7 +766,7 @@ admit:
     // gains nothing from overlapping (both halves keep the GPU busy) while
     // its front's memory traffic slows the running emission.
     if (!sv->has_front && !sv->queue.empty() && !(sv->hold && sv->has_back) &&
-        (!sv->has_back || (sv->back_tick.stage == kEmit && sv->queue.size() >= 2))) {
+        (!sv->has_back || (sv->back_tick.stage == kEmit && sv->queue.size() >= 2 && room_to_pin(sv)))) {
         rc = launch_front(sv, sv->has_back ? &sv->back_tick.reqs : nullptr);
         return rc ? -rc : 1;
     }
