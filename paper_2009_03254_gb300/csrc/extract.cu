@@ -673,17 +673,27 @@ void cache_update(const Launch &L, const Plan &pl, cudaStream_t st, cudaEvent_t 
 }
 
 template <bool kOne>
-void front(const Launch &L, const Plan &pl, cudaStream_t st, cudaEvent_t *ev, cudaEvent_t bits_ready) {
-    prep_kernel<kOne><<<pl.prep, kThreads, 0, st>>>(L);
-    if (ev) cudaEventRecord(ev[1], st);
+void cull_only(const Launch &L, const Plan &pl, cudaStream_t st) {
     // volumes with segment ranges (the largest) take 8192-block tiles: half
     // the look-back walks of 4096-block tiles, whose depth grows with the
     // tiles in flight
     if (kOne ? L.one.s.seg != nullptr : L.seg_any != 0) cull_kernel<32, kOne, true><<<pl.cull, kThreads, 0, st>>>(L);
     else if (pl.cull_tile == 2048) cull_kernel<8, kOne, false><<<pl.cull, kThreads, 0, st>>>(L);
     else cull_kernel<16, kOne, false><<<pl.cull, kThreads, 0, st>>>(L);
+}
+
+template <bool kOne>
+void front(const Launch &L, const Plan &pl, cudaStream_t st, cudaEvent_t *ev, cudaEvent_t bits_ready) {
+    prep_kernel<kOne><<<pl.prep, kThreads, 0, st>>>(L);
+    if (ev) cudaEventRecord(ev[1], st);
+    cull_only<kOne>(L, pl, st);
     if (ev) cudaEventRecord(ev[2], st);
     cache_update<kOne>(L, pl, st, ev, bits_ready);
+}
+
+void launch_cull(const Launch &L, const Plan &pl, cudaStream_t st) {
+    if (L.vols) cull_only<false>(L, pl, st);
+    else cull_only<true>(L, pl, st);
 }
 
 void launch_front(const Launch &L, const Plan &pl, cudaStream_t st, cudaEvent_t *ev, cudaEvent_t bits_ready) {

@@ -101,6 +101,8 @@ void launch_front(const Launch &L, const Plan &pl, cudaStream_t st, cudaEvent_t 
                   cudaEvent_t bits_ready = nullptr);
 // the cache update and decode alone (after a cull that set n_active/n_new)
 void launch_cache_update(const Launch &L, const Plan &pl, cudaStream_t st);
+// the range test alone (Ctl counters and look-back descriptors cleared by the caller)
+void launch_cull(const Launch &L, const Plan &pl, cudaStream_t st);
 // triangle stage: count, scan, emit.  A batch places the volumes' outputs
 // between scan and emit; a rerun into a larger output runs emit alone.
 void launch_mc_count(const Launch &L, bool debug, const Plan &pl, cudaStream_t st, bool indexed = false);

@@ -69,6 +69,7 @@ struct ServeArgs {
     unsigned long long *desc_occ[kMaxServe];
     uint32_t cand_cap;                // room of each candidate list
     VolEntry *views;                  // the tick's views in device memory (the back's launch table)
+    uint32_t single_cull;             // one request, no pins: the single-volume range test runs instead
     uint8_t *cases;                   // the server's stored-cases buffer (or null)
     unsigned long long case_cap;      // its room, in candidates (64 bytes each)
 };
@@ -92,6 +93,10 @@ __global__ void __launch_bounds__(kThreads) serve_prep_kernel(ServeArgs a) {
     }
     if (tid == 0) {
         Ctl *c = s.ctl;
+        if (a.single_cull) {                            // the single-volume range test reads them
+            c->params.iso = a.iso[0];
+            c->params.flags = 0;
+        }
         c->epoch += 1;
         c->n_active = 0;
         c->n_new = 0;
@@ -282,6 +287,7 @@ __global__ void __launch_bounds__(kThreads) serve_cull_kernel(ServeArgs a) {
 // classified again by the emission, which reads the same pointer).
 __global__ void serve_front_tail_kernel(ServeArgs a) {
     if (threadIdx.x != 0) return;
+    if (a.single_cull) a.ctl[0]->n_cand = a.base.s.ctl->n_cand;   // counted by the single-volume range test
     const uint32_t fail = a.base.s.ctl->status & (kStatusBudget | kStatusAnyTimeout);
     unsigned long long used = 0;
     for (uint32_t j = 0; j < a.k; j++) {
@@ -417,6 +423,7 @@ ServeArgs serve_args(const iso_server *sv, const Tick &t, const std::vector<Requ
     a.cand_cap = sv->cand_cap;
     a.views = sv->d_views[p];
     a.cases = sv->cases;
+    a.single_cull = (a.k == 1 && a.k_pin == 0) ? 1u : 0u;
     a.case_cap = sv->case_cap;
     return a;
 }
@@ -508,8 +515,20 @@ int launch_front(iso_server *sv, const std::vector<Request> *pins) {
     cudaStream_t st = sv->front;
     serve_prep_kernel<<<v->plan.prep, kThreads, 0, st>>>(a);
     const uint32_t kt = a.k + a.k_pin;
-    if (v->seg) launch_serve_cull<true>(kt, v->plan.cull, a, st);
-    else launch_serve_cull<false>(kt, v->plan.cull, a, st);
+    if (a.single_cull) {
+        // one request and no pins: its active set is the union, so the
+        // single-volume range test serves, writing the volume's lists and
+        // the request's candidates (its counters in the volume's control
+        // block, which the prep cleared)
+        VolEntry view = a.base;
+        view.s.icand = a.icand[0];
+        view.s.desc_cand = a.desc_cand[0];
+        launch_cull(Launch{nullptr, 1u, single_counters(v), view}, v->plan, st);
+    } else if (v->seg) {
+        launch_serve_cull<true>(kt, v->plan.cull, a, st);
+    } else {
+        launch_serve_cull<false>(kt, v->plan.cull, a, st);
+    }
     launch_cache_update(single, v->plan, st);
     serve_front_tail_kernel<<<1, 32, 0, st>>>(a);
     ISO_CK(cudaEventRecord(sv->front_done[t.parity], st));
