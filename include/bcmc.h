@@ -576,7 +576,9 @@ void iso_batch_release(iso_batch *b);
  * overlap: when a tick's emission is queued and at least two requests wait,
  * they are admitted as the next tick and its front runs on a second stream
  * while the running tick emits (a lone waiting request is admitted when the
- * running tick is done).  That front also counts the running
+ * running tick is done; no overlap on volumes with segment ranges, see
+ * ISO_SEGMENT_CULL, nor while the running tick's union takes more than half
+ * the cache).  That front also counts the running
  * tick's isovalues as active, so its cache update evicts no block the
  * running tick reads; decoded blocks and all metadata stay resident between
  * ticks.

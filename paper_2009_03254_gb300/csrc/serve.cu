@@ -28,7 +28,8 @@
 // Ticks are pipelined under load: once a tick's emission is queued and at
 // least two requests wait, they are admitted as the next tick and its front
 // runs on the second stream (at a lower priority) while the running tick
-// emits; a lone waiting request is admitted when the running tick is done.  That front also
+// emits; a lone waiting request is admitted when the running tick is done
+// (and on a volume with segment ranges every tick waits: room_to_pin).  That front also
 // counts the running tick's isovalues as active (pins), so the cache update
 // it makes never evicts a block the running tick reads.  The two ticks use
 // alternate halves of the request positions, so the new front never writes
