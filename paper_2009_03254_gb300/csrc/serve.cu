@@ -395,7 +395,6 @@ struct iso_server {
     std::deque<Request> queue;
     bool has_front = false, has_back = false;
     Tick front_tick, back_tick;         // a tick whose front runs, and one in its back
-    bool hold = false;                  // a pinned front did not fit: admit only once the back is done
     uint32_t next_parity = 0;
     uint64_t ticks_finished = 0;        // backs completed (their requests finished or sent back)
     uint64_t rounds_finished = 0;       // emission rounds completed (every request of the round finished)
@@ -737,7 +736,6 @@ int finish_round(iso_server *sv, bool block, uint32_t *completed) {
         return ISO_OK;
     }
     sv->has_back = false;
-    sv->hold = false;
     sv->ticks_finished++;
     sv->back_tick = Tick{};
     return ISO_OK;
@@ -791,7 +789,7 @@ admit:
     // back's count or emission needs until they finish, and a lone request
     // gains nothing from overlapping (both halves keep the GPU busy) while
     // its front's memory traffic slows the running emission.
-    if (!sv->has_front && !sv->queue.empty() && !(sv->hold && sv->has_back) &&
+    if (!sv->has_front && !sv->queue.empty() &&
         (!sv->has_back || (sv->back_tick.stage == kEmit && sv->queue.size() >= 2 && room_to_pin(sv)))) {
         rc = launch_front(sv, sv->has_back ? &sv->back_tick.reqs : nullptr);
         return rc ? -rc : 1;
