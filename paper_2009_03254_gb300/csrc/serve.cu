@@ -4,7 +4,8 @@
 //     serve_prep     clear the tick's counters and descriptors
 //     serve_cull     one pass over the block ranges for all the tick's
 //                    isovalues (Section 4.1): the union of their active sets
-//                    and each request's own candidate list
+//                    and each request's own candidate list (a tick of one
+//                    request without pins runs the single-volume range test)
 //     cache update   Algorithm 1 and the decode (Section 4.2) on the union
 //     front tail     the union's failures become every request's; each
 //                    request gets its region of the stored-cases buffer
@@ -14,29 +15,32 @@
 //                    launch each: a request is a "view" of the volume (own
 //                    control block, candidates, counts and offsets; shared
 //                    cache), the views are the entries of a batch launch
-//                    (they find no work if the union failed)
+//                    (they find no work if the union failed); on a volume
+//                    with segment ranges one launch per request (per_view)
 //     readback       every request's control block and the union's at once;
 //                    the host checks the union (budget, timeouts) and
 //                    allocates the meshes
 //     emit           Section 4.5: at light load (a round of one or two
-//                    requests, none waiting) one launch per request, each
-//                    finishing as its own emission ends; otherwise one
-//                    launch for the round; requests
-//                    whose meshes would pass the vertex budget wait
+//                    requests, none waiting) or on a volume with segment
+//                    ranges one launch per request, each finishing as its
+//                    own emission ends; otherwise one launch for the round.
+//                    Requests whose meshes would pass the vertex budget wait
 //                    in the tick (their counts and lists kept) and emit in a
-//                    later round once meshes are taken
+//                    later round once meshes are taken.
 // Ticks are pipelined under load: once a tick's emission is queued and at
 // least two requests wait, they are admitted as the next tick and its front
 // runs on the second stream (at a lower priority) while the running tick
-// emits; a lone waiting request is admitted when the running tick is done
-// (and on a volume with segment ranges every tick waits: room_to_pin).  That front also
-// counts the running tick's isovalues as active (pins), so the cache update
-// it makes never evicts a block the running tick reads.  The two ticks use
-// alternate halves of the request positions, so the new front never writes
-// lists the running back reads.  Decoded blocks and all metadata stay
-// resident between ticks.  If a union does not fit in the cache budget, its
-// requests go back to the queue (an unpinned tick then takes half as many
-// requests, down to one; a pinned one is simply retried without pins).
+// emits; a lone waiting request is admitted when the running tick is done,
+// and so is every tick on a volume with segment ranges or while the running
+// tick's union takes more than half the cache (room_to_pin).  An overlapping
+// front also counts the running tick's isovalues as active (pins), so the
+// cache update it makes never evicts a block the running tick reads.  The
+// two ticks use alternate halves of the request positions, so the new front
+// never writes lists the running back reads.  Decoded blocks and all
+// metadata stay resident between ticks.  If a union does not fit in the
+// cache budget, its requests go back to the queue (an unpinned tick then
+// takes half as many requests, down to one; a pinned one is simply retried
+// without pins).
 #include <algorithm>
 #include <chrono>
 #include <cmath>
