@@ -305,8 +305,9 @@ __device__ __forceinline__ void parse_planes(const StagedBits &st, uint32_t rate
 #pragma unroll
         for (int t = 0; t < kSteps; t++) {
             if (done || exact) continue;
-            uint32_t byte = st.win32(pos) & 0xFFu;
-            if (end - pos < 8u) byte &= (1u << (end - pos)) - 1u;   // no bit past the budget
+            // bits past the budget read as zero: the staged block is followed
+            // by a zero pad word, and a step reads at most 8 bits on
+            const uint32_t byte = st.win32(pos) & 0xFFu;
             const uint32_t e = lds_u32(tab + (((state << 8) | byte) << 2));
             const uint32_t cnt = (e >> 8) & 15u;
             if (n + cnt > 63u) {           // a run bit for coefficient 63 or later: not a table step
