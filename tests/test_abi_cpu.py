@@ -75,3 +75,51 @@ def test_checked_build_compiles_and_exports_the_same_calls():
     L = ctypes.CDLL(lib)
     for name in declared_functions():
         assert hasattr(L, name), name
+
+
+def test_arguments_refused_before_any_device_work(L):
+    # argument rules of the boundary that need no GPU: every case below is
+    # refused by host arithmetic before the first CUDA call, so it runs on
+    # any machine (and never allocates)
+    import ctypes
+    import paper_2009_03254_gb300 as pkg
+    bad = pkg.ISO_ERR_INVALID_ARG
+    dummy = np.zeros(64, dtype=np.uint64)
+    rng = np.zeros(64, dtype=np.float32)
+    p_bits, p_rng = ctypes.c_void_p(dummy.ctypes.data), ctypes.c_void_p(rng.ctypes.data)
+
+    def load(dims, rate, nbytes, bits=p_bits, lo=p_rng, hi=p_rng, out=True):
+        h = ctypes.c_void_p()
+        return L.iso_load_volume(ctypes.byref(h) if out else None, bits, nbytes, *dims, rate, lo, hi, None)
+
+    def size_of(dims, rate):
+        nb = ((dims[0] + 3) // 4) * ((dims[1] + 3) // 4) * ((dims[2] + 3) // 4)
+        return nb * rate * 8
+
+    ok_dims = (8, 8, 8)
+    for rate in (0, 33, 64):                                     # rate_bits outside [1, 32]
+        assert load(ok_dims, rate, size_of(ok_dims, 4)) == bad
+    for dims in ((0, 8, 8), (8, 0, 8), (8, 8, 0)):               # a dimension of 0
+        assert load(dims, 4, 0) == bad
+    # 2^31 blocks (2048 x 1024 x 1024): ids and packed counters are 31-bit
+    big = (4 * 2048, 4 * 1024, 4 * 1024)
+    assert load(big, 1, size_of(big, 1)) == bad
+    big_ragged = (4 * 2048 - 3, 4 * 1024 - 3, 4 * 1024 - 3)     # the same block grid, partial blocks
+    assert load(big_ragged, 1, size_of(big_ragged, 1)) == bad
+    # a bitstream whose size is not nb * R * 8 bytes
+    for nbytes in (size_of(ok_dims, 4) - 8, size_of(ok_dims, 4) + 8, 0):
+        assert load(ok_dims, 4, nbytes) == bad
+    # missing pointers
+    n = size_of(ok_dims, 4)
+    assert load(ok_dims, 4, n, bits=None) == bad
+    assert load(ok_dims, 4, n, lo=None) == bad
+    assert load(ok_dims, 4, n, hi=None) == bad
+    assert load(ok_dims, 4, n, out=False) == bad
+    # calls on no volume
+    m = pkg._Mesh()
+    assert L.iso_extract(None, ctypes.c_float(0.0), ctypes.byref(m)) == bad
+    st = pkg._Stats()
+    assert L.iso_extract_into(None, ctypes.c_float(0.0), None, 0, ctypes.byref(st)) == bad
+    # the dense decoder: no input, or a block grid past 2^31 blocks
+    assert L.iso_decode_volume(None, 8, 8, 8, 4, p_bits, None) == bad
+    assert L.iso_decode_volume(p_bits, *big, 1, p_bits, None) == bad
