@@ -535,8 +535,13 @@ int launch_front(iso_server *sv, const std::vector<Request> *pins) {
     }
     launch_cache_update(single, v->plan, st);
     serve_front_tail_kernel<<<1, 32, 0, st>>>(a);
-    ISO_CK(cudaEventRecord(sv->front_done[t.parity], st));
-    ISO_CK(cudaGetLastError());
+    cudaError_t e = cudaEventRecord(sv->front_done[t.parity], st);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {               // the requests wait in the queue again
+        (void)cudaGetLastError();
+        requeue(sv, t.reqs, 0);
+        return e == cudaErrorMemoryAllocation ? ISO_ERR_OOM : ISO_ERR_CUDA;
+    }
     t.args = a;
     sv->front_tick = std::move(t);
     sv->has_front = true;
@@ -579,7 +584,13 @@ int queue_back(iso_server *sv) {
     Tick t = std::move(sv->front_tick);
     sv->has_front = false;
     const uint32_t k = (uint32_t)t.reqs.size();
-    ISO_CK(cudaStreamWaitEvent(st, sv->front_done[t.parity], 0));
+    auto failed = [&](cudaError_t e) {    // the requests wait in the queue again
+        (void)cudaGetLastError();
+        requeue(sv, t.reqs, 0);
+        return e == cudaErrorMemoryAllocation ? ISO_ERR_OOM : ISO_ERR_CUDA;
+    };
+    cudaError_t e = cudaStreamWaitEvent(st, sv->front_done[t.parity], 0);
+    if (e != cudaSuccess) return failed(e);
     if (per_view(sv)) {
         for (uint32_t j = 0; j < k; j++) {
             const Launch L = view_launch(sv, t, j);
@@ -593,10 +604,10 @@ int queue_back(iso_server *sv) {
         launch_mc_scan(L, pl, st);
     }
     serve_gather_kernel<<<1, 256, 0, st>>>(t.args, sv->d_ctls[t.parity]);
-    ISO_CK(cudaMemcpyAsync(sv->h_ctls[t.parity], sv->d_ctls[t.parity], (k + 1) * sizeof(Ctl), cudaMemcpyDeviceToHost,
-                           st));
-    ISO_CK(cudaEventRecord(sv->count_done, st));
-    ISO_CK(cudaGetLastError());
+    e = cudaMemcpyAsync(sv->h_ctls[t.parity], sv->d_ctls[t.parity], (k + 1) * sizeof(Ctl), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaEventRecord(sv->count_done, st);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return failed(e);
     t.stage = kCount;
     sv->back_tick = std::move(t);
     sv->has_back = true;
@@ -657,7 +668,7 @@ int start_emit(iso_server *sv, uint32_t *completed) {
         if (t.status[j] != ISO_OK) continue;  // fails without a mesh
         const uint64_t bytes = sv->tri_bytes * c[j].n_tri;
         if (sv->vertex_budget && held > 0 && held + bytes > sv->vertex_budget) break;
-        if (c[j].n_tri) {
+        if (c[j].n_tri && !t.bufs[j]) {   // (a round retried after an error keeps its meshes)
             const int rc = dalloc_on(&t.bufs[j], (size_t)c[j].n_tri * (sv->tri_bytes / 4), sv->device, st);
             if (rc) {
                 t.status[j] = rc;
@@ -756,7 +767,7 @@ int finish_round(iso_server *sv, bool block, uint32_t *completed) {
 // with overlap the served path sustained 13.9 against the plain path's
 // 17.2 G triangles/s on a 10240 x 7680 x 1536 volume).
 bool room_to_pin(const iso_server *sv) {
-    if (per_view(sv)) return false;           // see below
+    if (per_view(sv)) return false;
     const Tick &t = sv->back_tick;
     return (uint64_t)sv->h_ctls[t.parity][t.reqs.size()].n_active * 2 <= sv->v->cap;
 }
