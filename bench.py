@@ -767,7 +767,7 @@ def run_ours(args):
             h_min = bmin.cpu().pin_memory()
             h_max = bmax.cpu().pin_memory()
             h2d = h_bits.numel() * 8 + h_min.numel() * 4 + h_max.numel() * 4
-            e2e_steps = max(1, min(args.steps, 5))
+            e2e_steps = max(2, args.steps)
 
             load_s = []
 

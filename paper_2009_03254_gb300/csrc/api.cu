@@ -575,12 +575,20 @@ int extract_to(iso_volume *v, float iso, void *out, unsigned long long cap_tris,
     return rc;
 }
 
+// built once per process (a function-local static: thread-safe initialisation,
+// so volumes may be loaded from several threads)
 bool build_tables_once(McTables *t) {
-    static McTables cached;
-    static int state = 0;     // 0 unbuilt, 1 ok, -1 failed
-    if (state == 0) state = build_mc_tables(&cached) && cached.max_tri <= kMaxTriPerCell ? 1 : -1;
-    if (state < 0) return false;
-    *t = cached;
+    struct Built {
+        bool ok;
+        McTables tables;
+    };
+    static const Built built = [] {
+        Built b{};
+        b.ok = build_mc_tables(&b.tables) && b.tables.max_tri <= kMaxTriPerCell;
+        return b;
+    }();
+    if (!built.ok) return false;
+    *t = built.tables;
     return true;
 }
 
