@@ -7,6 +7,7 @@
 #include <mutex>
 #include <new>
 #include <unordered_map>
+#include <utility>
 #include <vector>
 
 #include "bcmc.h"
@@ -68,6 +69,77 @@ struct HookAllocator {
 std::mutex g_alloc_mutex;
 HookAllocator g_hook;
 std::unordered_map<void *, HookAllocator> g_hooked;
+
+// A volume's pinned host mirrors (control block and parameters, one block)
+// and its upload stream are kept for the next volume when it is released:
+// pinning and unpinning host memory and creating a stream each cost tens of
+// microseconds, which a loop that loads and releases volumes one after
+// another would otherwise pay with the GPU idle.
+constexpr size_t kParamsOffset = (sizeof(Ctl) + 255) / 256 * 256;
+constexpr size_t kPinnedBlockBytes = kParamsOffset + (sizeof(Params) + 255) / 256 * 256;
+constexpr size_t kPinnedKeep = 64;                 // blocks kept (a few KB each)
+constexpr size_t kStreamsKeep = 8;                 // upload streams kept per device
+std::mutex g_reuse_mutex;
+std::vector<void *> g_pinned_free;
+std::vector<std::pair<int, cudaStream_t>> g_streams_free;   // (device, stream)
+
+void *pinned_take() {
+    {
+        std::lock_guard<std::mutex> lock(g_reuse_mutex);
+        if (!g_pinned_free.empty()) {
+            void *p = g_pinned_free.back();
+            g_pinned_free.pop_back();
+            return p;
+        }
+    }
+    void *p = nullptr;
+    if (cudaMallocHost(&p, kPinnedBlockBytes) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void pinned_give(void *p) {
+    if (!p) return;
+    {
+        std::lock_guard<std::mutex> lock(g_reuse_mutex);
+        if (g_pinned_free.size() < kPinnedKeep) {
+            g_pinned_free.push_back(p);
+            return;
+        }
+    }
+    cudaFreeHost(p);
+}
+
+// a non-blocking stream of the current device (`dev`)
+cudaError_t stream_take(int dev, cudaStream_t *st) {
+    {
+        std::lock_guard<std::mutex> lock(g_reuse_mutex);
+        for (size_t i = g_streams_free.size(); i-- > 0;)
+            if (g_streams_free[i].first == dev) {
+                *st = g_streams_free[i].second;
+                g_streams_free.erase(g_streams_free.begin() + (long)i);
+                return cudaSuccess;
+            }
+    }
+    return cudaStreamCreateWithFlags(st, cudaStreamNonBlocking);
+}
+
+// an idle stream (the caller synchronised it) of device `dev`
+void stream_give(int dev, cudaStream_t st) {
+    if (!st) return;
+    {
+        std::lock_guard<std::mutex> lock(g_reuse_mutex);
+        size_t n = 0;
+        for (const auto &e : g_streams_free) n += e.first == dev;
+        if (n < kStreamsKeep) {
+            g_streams_free.emplace_back(dev, st);
+            return;
+        }
+    }
+    cudaStreamDestroy(st);
+}
 
 int dalloc_bytes(void **p, size_t bytes, int dev, cudaStream_t st) {
     *p = nullptr;
@@ -297,14 +369,13 @@ int free_volume(iso_volume *v) {
     for (void *p : ptrs) dfree_on(p, v->stream);
     cudaStreamSynchronize(v->stream);
     (void)cudaGetLastError();
-    if (v->host_ctl) cudaFreeHost(v->host_ctl);
-    if (v->host_params) cudaFreeHost(v->host_params);
+    pinned_give(v->host_ctl);            // the block that also holds host_params
     for (int k = 0; k < 4; k++) {
         if (v->gexec[k]) cudaGraphExecDestroy(v->gexec[k]);
         if (v->graph[k]) cudaGraphDestroy(v->graph[k]);
     }
     if (v->capture_stream) cudaStreamDestroy(v->capture_stream);
-    if (v->upload_stream) cudaStreamDestroy(v->upload_stream);
+    stream_give(v->device, v->upload_stream);   // synchronised above
     if (v->uploaded) cudaEventDestroy(v->uploaded);
     for (cudaEvent_t &e : v->ev)
         if (e) cudaEventDestroy(e);
@@ -754,11 +825,14 @@ int iso_load_volume(iso_volume **out, const void *compressed, size_t compressed_
         TRY(dalloc(v, &s.cases, (size_t)s.list_cap * 64));
         s.case_cap = s.list_cap;
     }
-    if (cudaMallocHost((void **)&v->host_ctl, sizeof(Ctl)) != cudaSuccess ||
-        cudaMallocHost((void **)&v->host_params, sizeof(Params)) != cudaSuccess) {
-        (void)cudaGetLastError();
-        free_volume(v);
-        return ISO_ERR_OOM;
+    {
+        char *block = static_cast<char *>(pinned_take());
+        if (!block) {
+            free_volume(v);
+            return ISO_ERR_OOM;
+        }
+        v->host_ctl = reinterpret_cast<Ctl *>(block);
+        v->host_params = reinterpret_cast<Params *>(block + kParamsOffset);
     }
     v->use_graph = !(o.flags & ISO_NO_GRAPH);
     s.bits = v->bits;
@@ -824,7 +898,7 @@ int iso_load_volume(iso_volume **out, const void *compressed, size_t compressed_
         // of its own after the load's work on `st` (so no copy of the load
         // queues behind it); the first extraction's decode waits for it.
         cudaEvent_t queued = nullptr;
-        TRYC(cudaStreamCreateWithFlags(&v->upload_stream, cudaStreamNonBlocking));
+        TRYC(stream_take(v->device, &v->upload_stream));
         TRYC(cudaEventCreateWithFlags(&v->uploaded, cudaEventDisableTiming));
         TRYC(cudaEventCreateWithFlags(&queued, cudaEventDisableTiming));
         const cudaError_t e1 = cudaEventRecord(queued, st);
