@@ -568,11 +568,14 @@ void iso_batch_release(iso_batch *b);
  * requests (first come, first served).  A tick's front is one pass over the
  * block ranges that finds the union of its requests' active blocks
  * (Section 4.1) and each request's own candidates, then one cache update
- * and decode for the union (Section 4.2, Algorithm 1); its back counts,
- * scans and emits all its requests (Sections 4.3-4.5) in one launch each,
- * with one readback of their triangle counts in between (the count follows
- * the front on the device, with no host round trip; the union's budget is
- * checked at that readback).  Under load ticks
+ * and decode for the union (Section 4.2, Algorithm 1); its back counts and
+ * scans all its requests (Sections 4.3-4.4) in one launch each, then, after
+ * one readback of their triangle counts (the count follows the front on the
+ * device, with no host round trip; the union's budget is checked at that
+ * readback), emits them (Section 4.5) in one launch, or request by request
+ * at light load (a round of one or two requests, none waiting) so that each
+ * finishes as soon as its own emission does.  On a volume with segment
+ * ranges every request's count, scan and emission is a launch of its own.  Under load ticks
  * overlap: when a tick's emission is queued and at least two requests wait,
  * they are admitted as the next tick and its front runs on a second stream
  * while the running tick emits (a lone waiting request is admitted when the
@@ -632,7 +635,9 @@ int iso_server_submit(iso_server *s, float isovalue, uint64_t *ticket);
  * request waits); blocks while it waits for the GPU.  Ticks are
  * admitted on the way (the next one while the current one is in its back),
  * so work keeps running on the GPU when the call returns.  *completed (may
- * be NULL) receives the number of requests finished. */
+ * be NULL) receives the number of requests finished.  If queuing a tick's
+ * work fails (ISO_ERR_CUDA, ISO_ERR_OOM), its requests return to the queue
+ * and the call returns that error. */
 int iso_server_step(iso_server *s, uint32_t *completed);
 
 /* The same without blocking: take every transition whose GPU work is
@@ -650,8 +655,9 @@ int iso_server_queued(const iso_server *s, uint32_t *queued);
 /* Hand a finished request's mesh to the caller (release it with
  * iso_mesh_release on the server's volume).  Returns ISO_PENDING if the
  * request is still queued, the request's own status if it finished
- * (ISO_OK, ISO_ERR_BUDGET, ISO_ERR_TIMEOUT, ISO_ERR_OOM; no mesh unless
- * ISO_OK), ISO_ERR_INVALID_ARG for an unknown or already taken ticket.
+ * (ISO_OK, ISO_ERR_BUDGET, ISO_ERR_TIMEOUT, ISO_ERR_OOM, or ISO_ERR_BOUNDS
+ * from the checked build; no mesh unless ISO_OK), ISO_ERR_INVALID_ARG for
+ * an unknown or already taken ticket.
  * stats: n_active, n_new, n_slots, cache_bytes and epoch describe the
  * tick's union; num_triangles, n_occupied, n_candidates the request. */
 int iso_server_take(iso_server *s, uint64_t ticket, iso_mesh *out);
