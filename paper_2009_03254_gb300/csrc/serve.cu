@@ -686,7 +686,7 @@ int start_emit(iso_server *sv, uint32_t *completed) {
     for (uint32_t i = 0; i < k; i++) {
         const bool out = i >= t.emitted && i < t.run_to && t.bufs[i];
         sv->h_params[i] = Params{t.reqs[i].iso, sv->format, 0u, 0u, 0u, 0u, out ? c[i].n_tri : 0ull,
-                                 out ? (unsigned long long)(uintptr_t)t.bufs[i] : 0ull};
+                                 out ? (unsigned long long)(uintptr_t)t.bufs[i] : 0ull, 0ull, 0ull, 0ull};
     }
     ISO_CK(cudaMemcpyAsync(sv->d_params, sv->h_params, k * sizeof(Params), cudaMemcpyHostToDevice, st));
     serve_params_kernel<<<1, kMaxServe, 0, st>>>(sv->d_views[t.parity], sv->d_params, k);
