@@ -177,3 +177,44 @@ def test_async_load_reports_bad_ranges_on_first_call():
         m.release()
     finally:
         vol.release()
+
+
+def test_load_release_cycles_reuse_host_mirrors_and_streams():
+    # released volumes hand their pinned host mirrors and upload stream to
+    # the next load: many volumes loaded and released in interleaved order
+    # (more at once than one, fewer than the kept set, then more than it),
+    # with asynchronous uploads on two caller streams, all extract the same
+    # surface as the oracle
+    import torch
+    p = pkg()
+    dims, rate, bits, bmin, bmax = volume_data(dims=(24, 20, 18))
+    ref = oracle.extract(bits, dims, rate, bmin, bmax, 0.0)
+    h_bits = torch.from_numpy(bits.view(np.int64)).pin_memory()
+    h_min = torch.from_numpy(bmin).pin_memory()
+    h_max = torch.from_numpy(bmax).pin_memory()
+    lanes = [torch.cuda.Stream(), torch.cuda.Stream()]
+    import ctypes
+
+    def load(i):
+        return p.Volume(h_bits, dims, rate, h_min, h_max, async_upload=True,
+                        stream=ctypes.c_void_p(lanes[i % 2].cuda_stream))
+
+    def check(vol):
+        m = vol.extract(0.0)
+        assert m.num_triangles == ref["num_triangles"]
+        if m.num_triangles:
+            v = m.vertices.cpu().numpy().reshape(-1, 3, 4)
+            assert np.abs(v[:, :, :3] - ref["local_pos"]).max() < POS_TOL
+        m.release()
+
+    live = []
+    for i in range(40):
+        live.append(load(i))
+        check(live[-1])
+        if len(live) > 3:                       # release out of load order
+            live.pop(1 if i % 3 else 0).release()
+    many = [load(i) for i in range(80)]         # more at once than are kept for reuse
+    for vol in many[::7]:
+        check(vol)
+    for vol in many + live:
+        vol.release()
