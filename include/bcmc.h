@@ -149,8 +149,9 @@ int iso_set_allocator(iso_alloc_fn alloc, iso_free_fn free_fn, void *ctx);
 
 /* Give the freed memory the library's pool keeps on `device` back to the
  * device, so that other allocators (a PyTorch caching allocator, cudaMalloc)
- * can use it; memory in use is untouched.  Waits for all work on the device
- * first (cudaDeviceSynchronize).  An allocation the pool cannot satisfy does
+ * can use it; memory in use is untouched.  The small pinned host buffers
+ * and the streams that released volumes left for later loads are freed
+ * too.  Waits for all work on the device first (cudaDeviceSynchronize).  An allocation the pool cannot satisfy does
  * the same once by itself and retries before it reports ISO_ERR_OOM.
  * ISO_ERR_INVALID_ARG for a device without a pool of the library (nothing
  * was ever allocated there from it). */
@@ -384,7 +385,10 @@ int iso_mc_dense(const float *d_field, uint32_t nx, uint32_t ny, uint32_t nz, fl
  * made it).  The volume must still be alive.  Safe on a zeroed mesh. */
 int iso_mesh_release(iso_volume *v, iso_mesh *m);
 
-/* Free every device and host resource of the volume. NULL is a no-op. */
+/* Free every device and host resource of the volume (device memory goes
+ * back to the library's pool; its small pinned host buffers and its upload
+ * stream are kept, a few dozen at most, for the next load: see
+ * iso_release_cached_memory).  NULL is a no-op. */
 void iso_release(iso_volume *v);
 
 /* Change the stream used by later calls on v (the previous stream is

@@ -715,6 +715,21 @@ int iso_release_cached_memory(int device) {
         (void)cudaGetLastError();
         return ISO_ERR_CUDA;
     }
+    // and the pinned host mirrors and upload streams kept for later loads
+    std::vector<void *> pinned;
+    std::vector<cudaStream_t> streams;
+    {
+        std::lock_guard<std::mutex> lock(g_reuse_mutex);
+        pinned.swap(g_pinned_free);
+        for (size_t i = g_streams_free.size(); i-- > 0;)
+            if (g_streams_free[i].first == device) {
+                streams.push_back(g_streams_free[i].second);
+                g_streams_free.erase(g_streams_free.begin() + (long)i);
+            }
+    }
+    for (void *p : pinned) cudaFreeHost(p);
+    for (cudaStream_t st : streams) cudaStreamDestroy(st);
+    (void)cudaGetLastError();
     return ISO_OK;
 }
 
